@@ -1,0 +1,882 @@
+/*
+ * cgdem_oracle.c -- plain FP64 CPU oracle of the coarse-grained CFD-DEM step
+ * (arXiv 2211.06142).  TEST INFRASTRUCTURE ONLY: tests, the package smoke
+ * check and the benchmark's CPU baseline call it; the CUDA library never does.
+ *
+ * Written from the paper's equations, in the paper's order, without blocking,
+ * fusion or reordering.  Compile with -ffp-contract=off so that every product
+ * and sum is rounded as written.
+ *
+ * Readings of the paper that this file relies on (the paper is silent,
+ * garbled or ambiguous at these points):
+ *   - Normal elastic force: Eq. 12 on bonded contacts, Hertz (Eq. 12 with
+ *     gamma = 0) on unbonded ones; the linear spring of Eq. 3 is not used.
+ *   - Normal damping: Eq. 32 read as -beta*sqrt(20/3 E* a m*) * u_n, i.e.
+ *     gamma_n = 2 sqrt(5/6) beta sqrt(2 E* a m*), with beta from Eq. 33 with
+ *     the squared logarithm restored, taken positive.
+ *   - Tangential: Hertz-Mindlin k_t = 8 G* a, gamma_t = 2 sqrt(5/6) beta
+ *     sqrt(k_t m*), spring history rotated into the tangent plane, Coulomb
+ *     magnitude cap (Eq. 4 and Eq. 35) with F_lim = F_ne + 2 F_C on bonds.
+ *   - Torque arm: the particle radius along the normal (Eq. 5).
+ *   - Bonds break at Table 1 point C (delta < delta_C) and never reform.
+ *   - Drag: Eq. 8-11 with u the interstitial velocity U_s / n.
+ *   - Rayleigh step Eq. 37-38 with G = E / (2 (1 + nu)).
+ */
+#include "cgdem_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* (C_C)^3 * pi^2 where C_C = (81/16)^(1/3) - 12^(1/3) = delta_C / xi (Table 1,
+ * point C, exact form of the printed -0.57).  Nearest double to the real
+ * number; pinned against the closed form by the oracle tests. */
+#define ORA_KC (-1.8505508252042548)
+/* (pi/6)^(1/3): side of the cube with the volume of a unit-diameter sphere. */
+#define ORA_CUBE_SIDE (0.8059959770082348)
+#define ORA_TWO_M40 (9.094947017729282379150390625e-13) /* 2^-40 */
+
+/* ------------------------------------------------------------------ */
+/* material laws                                                       */
+/* ------------------------------------------------------------------ */
+
+double ora_estar(double E, double nu) {
+    /* Eq. 12 definitions: 1/E* = (1-nu1^2)/E1 + (1-nu2^2)/E2 with equal materials */
+    return E / (2.0 * (1.0 - nu * nu));
+}
+
+static double ora_gstar(double E, double nu) {
+    /* shear modulus G = E / (2(1+nu)); Mindlin G* = G / (2(2-nu)) for equal materials */
+    double G = E / (2.0 * (1.0 + nu));
+    return G / (2.0 * (2.0 - nu));
+}
+
+double ora_beta(double e) {
+    /* Eq. 33 with ln^2 e in the root; sign chosen so that beta > 0 damps */
+    double l = log(e);
+    return -l / sqrt(l * l + M_PI * M_PI);
+}
+
+double ora_jkr_overlap(double a, double Rs, double Es, double gamma) {
+    /* Eq. 13 */
+    return a * a / Rs - sqrt(4.0 * M_PI * gamma * a / Es);
+}
+
+double ora_jkr_force(double a, double Rs, double Es, double gamma) {
+    /* Eq. 12, positive = repulsive */
+    return 4.0 * Es * a * a * a / (3.0 * Rs) - sqrt(16.0 * M_PI * gamma * Es * a * a * a);
+}
+
+static double ora_a_c(double Rs, double Es, double gamma) {
+    /* Table 1, contact radius at point C */
+    return cbrt(9.0 * M_PI * gamma * Rs * Rs / (4.0 * Es));
+}
+
+double ora_delta_c(double Rs, double Es, double gamma) {
+    /* Table 1, overlap at point C (Eq. 13 evaluated at a_C) */
+    return ora_jkr_overlap(ora_a_c(Rs, Es, gamma), Rs, Es, gamma);
+}
+
+int ora_bond_breaks(double delta, double Rs, double Es, double gamma) {
+    /* delta < delta_C with delta_C = C_C (pi^2 gamma^2 Rs / Es^2)^(1/3) <= 0.
+     * Cubing both sides keeps the order, so the test is
+     *   delta^3 * Es^2 < C_C^3 pi^2 * gamma^2 * Rs
+     * evaluated left to right in IEEE double. */
+    if (!(delta < 0.0)) return 0;
+    double lhs = delta * delta * delta * (Es * Es);
+    double rhs = ORA_KC * (gamma * gamma) * Rs;
+    return lhs < rhs;
+}
+
+double ora_jkr_contact_radius(double delta, double Rs, double Es, double gamma) {
+    /* Solve Eq. 13 for a on the stable branch a >= a_C by bisection to 1 ulp. */
+    double lo = ora_a_c(Rs, Es, gamma);
+    double hi = lo;
+    double base = sqrt(Rs * fabs(delta));
+    if (base > hi) hi = base;
+    if (hi <= 0.0) hi = 1e-300;
+    while (ora_jkr_overlap(hi, Rs, Es, gamma) < delta) hi *= 2.0;
+    if (ora_jkr_overlap(lo, Rs, Es, gamma) >= delta) return lo;
+    for (;;) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (ora_jkr_overlap(mid, Rs, Es, gamma) < delta) lo = mid;
+        else hi = mid;
+    }
+    double flo = fabs(ora_jkr_overlap(lo, Rs, Es, gamma) - delta);
+    double fhi = fabs(ora_jkr_overlap(hi, Rs, Es, gamma) - delta);
+    return flo < fhi ? lo : hi;
+}
+
+double ora_rayleigh_dt(double Rbar, double rho, double E, double nu) {
+    /* Eq. 37-38 */
+    double G = E / (2.0 * (1.0 + nu));
+    double beta = 0.8766 + 0.163 * nu;
+    return M_PI * Rbar / beta * sqrt(rho / G);
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry helpers                                                    */
+/* ------------------------------------------------------------------ */
+
+static double min_image(double d, double L) {
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
+static void cross(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static double sphere_volume(double R) {
+    /* ((4/3) pi) R R R, left to right */
+    return 4.0 / 3.0 * M_PI * R * R * R;
+}
+
+static int fluid_cell_axis(const ora_params* p, int ax, double x) {
+    double t = floor((x - p->f_lo[ax]) * p->inv_hf[ax]);
+    if (t < 0.0) t = 0.0;
+    if (t > (double)(p->nf[ax] - 1)) t = (double)(p->nf[ax] - 1);
+    return (int)t;
+}
+
+static int64_t fluid_cell(const ora_params* p, const double x[3]) {
+    int cx = fluid_cell_axis(p, 0, x[0]);
+    int cy = fluid_cell_axis(p, 1, x[1]);
+    int cz = fluid_cell_axis(p, 2, x[2]);
+    return ((int64_t)cz * p->nf[1] + cy) * p->nf[0] + cx;
+}
+
+/* ------------------------------------------------------------------ */
+/* one contact: normal (Eq. 12-13, Table 1, modified JKR), damping     */
+/* (Eq. 32-33), tangential (Eq. 4, 35) and torque (Eq. 5)              */
+/* ------------------------------------------------------------------ */
+
+/* Contact law shared by particle-particle and particle-wall contacts.
+ * n: unit normal from i towards j.  delta: overlap.  vrel_c: velocity of
+ * j's surface relative to i's surface at the contact point.
+ * Returns the force on i in Fi (normal + tangential) and the tangential
+ * force on i in Ft; updates xi and bonded.  Returns 1 if a force acts. */
+static int contact_law(const ora_params* p, double delta, int touching, const double n[3],
+                       const double vrel[3], const double vrel_c[3],
+                       double Rs, double ms, double gamma,
+                       double xi[3], int* bonded, double Fi[3], double Ft_out[3],
+                       double* Fne_out, double* a_out) {
+    double Es = ora_estar(p->E, p->nu);
+    double Gs = ora_gstar(p->E, p->nu);
+    double beta = ora_beta(p->e);
+    double a, Fne;
+    if (*bonded) {
+        if (ora_bond_breaks(delta, Rs, Es, gamma)) {
+            *bonded = 0; /* modified JKR: break at C, no new bond */
+        }
+    }
+    if (*bonded) {
+        a = ora_jkr_contact_radius(delta, Rs, Es, gamma);
+        Fne = ora_jkr_force(a, Rs, Es, gamma);
+    } else if (touching) {
+        a = delta > 0.0 ? sqrt(Rs * delta) : 0.0; /* Hertz: Eq. 13 with gamma = 0 */
+        Fne = ora_jkr_force(a, Rs, Es, 0.0); /* Eq. 12 with gamma = 0 */
+    } else {
+        xi[0] = xi[1] = xi[2] = 0.0;
+        return 0;
+    }
+    /* normal damping, Eq. 32 */
+    double Sn = 2.0 * Es * a;
+    double gn = 2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * ms);
+    double vn = dot(vrel, n);
+    double Fn = Fne - gn * vn;
+
+    /* tangential: relative surface velocity projected on the tangent plane */
+    double vcn = dot(vrel_c, n);
+    double vt[3] = {vrel_c[0] - vcn * n[0], vrel_c[1] - vcn * n[1], vrel_c[2] - vcn * n[2]};
+    /* rotate the spring into the current tangent plane, keeping its length */
+    double old = sqrt(dot(xi, xi));
+    double xn = dot(xi, n);
+    xi[0] -= xn * n[0];
+    xi[1] -= xn * n[1];
+    xi[2] -= xn * n[2];
+    double nw = sqrt(dot(xi, xi));
+    if (nw > 0.0) {
+        double sc = old / nw;
+        xi[0] *= sc;
+        xi[1] *= sc;
+        xi[2] *= sc;
+    } else {
+        xi[0] = xi[1] = xi[2] = 0.0;
+    }
+    xi[0] += vt[0] * p->dt;
+    xi[1] += vt[1] * p->dt;
+    xi[2] += vt[2] * p->dt;
+    double kt = 8.0 * Gs * a;
+    double gt = 2.0 * sqrt(5.0 / 6.0) * beta * sqrt(kt * ms);
+    double Ft[3] = {kt * xi[0] + gt * vt[0], kt * xi[1] + gt * vt[1], kt * xi[2] + gt * vt[2]};
+    double FC = 3.0 * M_PI * gamma * Rs; /* Table 1, |F_C| */
+    double Flim;
+    if (p->coulomb_mode == 1) Flim = fabs(Fne);
+    else Flim = *bonded ? Fne + 2.0 * FC : Fne;
+    if (Flim < 0.0) Flim = 0.0;
+    double ftm = sqrt(dot(Ft, Ft));
+    double cap = p->mu * Flim; /* Eq. 35 */
+    if (ftm > cap) {
+        double sc = ftm > 0.0 ? cap / ftm : 0.0;
+        Ft[0] *= sc;
+        Ft[1] *= sc;
+        Ft[2] *= sc;
+        if (kt > 0.0) {
+            xi[0] = (Ft[0] - gt * vt[0]) / kt;
+            xi[1] = (Ft[1] - gt * vt[1]) / kt;
+            xi[2] = (Ft[2] - gt * vt[2]) / kt;
+        }
+    }
+    Fi[0] = -Fn * n[0] + Ft[0];
+    Fi[1] = -Fn * n[1] + Ft[1];
+    Fi[2] = -Fn * n[2] + Ft[2];
+    Ft_out[0] = Ft[0];
+    Ft_out[1] = Ft[1];
+    Ft_out[2] = Ft[2];
+    if (Fne_out) *Fne_out = Fne;
+    if (a_out) *a_out = a;
+    return 1;
+}
+
+/* pair geometry and law; returns 1 if active */
+static int pair_eval(const ora_params* p, const double* xi_p, const double* vi, const double* wi,
+                     double Ri, double mi, const double* xj_p, const double* vj, const double* wj,
+                     double Rj, double mj, double hist[3], int* bonded, double Fi[3],
+                     double Ti[3], double Tj[3], double* Fne, double* a_out, double* delta_out) {
+    double d[3];
+    for (int k = 0; k < 3; ++k) {
+        d[k] = xj_p[k] - xi_p[k];
+        if (p->kind == 0) d[k] = min_image(d[k], p->L[k]);
+    }
+    double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double S = Ri + Rj;
+    double dist = sqrt(d2);
+    double delta = S - dist;
+    if (delta_out) *delta_out = delta;
+    if (!(*bonded) && !(d2 < S * S)) {
+        hist[0] = hist[1] = hist[2] = 0.0;
+        return 0;
+    }
+    if (!(dist > 0.0)) return 0;
+    double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+    double Rs = Ri * Rj / (Ri + Rj);
+    double ms = mi * mj / (mi + mj);
+    double vrel[3] = {vj[0] - vi[0], vj[1] - vi[1], vj[2] - vi[2]};
+    double rw[3] = {Ri * wi[0] + Rj * wj[0], Ri * wi[1] + Rj * wj[1], Ri * wi[2] + Rj * wj[2]};
+    double rwn[3];
+    cross(rw, n, rwn);
+    double vc[3] = {vrel[0] - rwn[0], vrel[1] - rwn[1], vrel[2] - rwn[2]};
+    double Ft[3];
+    int act = contact_law(p, delta, d2 < S * S, n, vrel, vc, Rs, ms, p->gamma, hist, bonded, Fi, Ft,
+                          Fne, a_out);
+    if (!act) return 0;
+    double nFt[3];
+    cross(n, Ft, nFt);
+    for (int k = 0; k < 3; ++k) {
+        Ti[k] = Ri * nFt[k];
+        Tj[k] = Rj * nFt[k];
+    }
+    return 1;
+}
+
+int ora_pair_contact(const ora_params* p, const double xi_pos[3], const double vi[3],
+                     const double wi[3], double Ri, double mi, const double xj_pos[3],
+                     const double vj[3], const double wj[3], double Rj, double mj,
+                     double xi_inout[3], int* bonded_inout, double out[12]) {
+    double Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0}, Tj[3] = {0, 0, 0}, Fne = 0, a = 0, delta = 0;
+    int act = pair_eval(p, xi_pos, vi, wi, Ri, mi, xj_pos, vj, wj, Rj, mj, xi_inout,
+                        bonded_inout, Fi, Ti, Tj, &Fne, &a, &delta);
+    for (int k = 0; k < 3; ++k) {
+        out[k] = act ? Fi[k] : 0.0;
+        out[3 + k] = act ? Ti[k] : 0.0;
+        out[6 + k] = act ? Tj[k] : 0.0;
+    }
+    out[9] = act ? Fne : 0.0;
+    out[10] = act ? a : 0.0;
+    out[11] = delta;
+    return act;
+}
+
+/* ------------------------------------------------------------------ */
+/* fluid: Eq. 8-11                                                     */
+/* ------------------------------------------------------------------ */
+
+void ora_drag(double rho_f, double mu_f, double d, const double u[3], const double v[3],
+              double n, double f_out[3]) {
+    double w[3] = {u[0] - v[0], u[1] - v[1], u[2] - v[2]};
+    double wm = sqrt(dot(w, w));
+    double Re = rho_f * d * wm / mu_f; /* Eq. 11 */
+    if (!(Re > 0.0)) {
+        f_out[0] = f_out[1] = f_out[2] = 0.0;
+        return;
+    }
+    double t = 0.63 + 4.8 / sqrt(Re);
+    double Cd = t * t;                                    /* Eq. 9 */
+    double lr = 1.5 - log10(Re);
+    double chi = 3.7 - 0.65 * exp(-(lr * lr) / 2.0);      /* Eq. 10 */
+    double pre = 1.0 / 8.0 * Cd * rho_f * M_PI * d * d * wm * pow(n, -chi); /* Eq. 8 */
+    f_out[0] = pre * w[0];
+    f_out[1] = pre * w[1];
+    f_out[2] = pre * w[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* void fraction (porosity n of Eq. 6), fixed-point quanta             */
+/* ------------------------------------------------------------------ */
+
+static void add_voidfrac(const ora_params* p, const double x[3], double R, uint64_t* sums) {
+    double inv_q = 1099511627776.0 / p->V_cell; /* 2^40 / V_cell */
+    if (p->vf_mode == 0) {
+        double V = sphere_volume(R);
+        sums[fluid_cell(p, x)] += (uint64_t)llrint(V * inv_q);
+        return;
+    }
+    /* equal-volume cube spread over the cells it overlaps */
+    double side = 2.0 * R * ORA_CUBE_SIDE;
+    int a0[3], a1[3];
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = x[k] - 0.5 * side;
+        hi[k] = x[k] + 0.5 * side;
+        a0[k] = (int)floor((lo[k] - p->f_lo[k]) * p->inv_hf[k]);
+        a1[k] = (int)floor((hi[k] - p->f_lo[k]) * p->inv_hf[k]);
+    }
+    for (int az = a0[2]; az <= a1[2]; ++az)
+        for (int ay = a0[1]; ay <= a1[1]; ++ay)
+            for (int ax = a0[0]; ax <= a1[0]; ++ax) {
+                int a[3] = {ax, ay, az};
+                double vol = 1.0;
+                int c[3];
+                for (int k = 0; k < 3; ++k) {
+                    double b0 = p->f_lo[k] + (double)a[k] * p->hf[k];
+                    double b1 = p->f_lo[k] + (double)(a[k] + 1) * p->hf[k];
+                    double o = fmin(hi[k], b1) - fmax(lo[k], b0);
+                    if (o < 0.0) o = 0.0;
+                    vol *= o;
+                    int ck = a[k];
+                    if (p->kind == 0) {
+                        ck %= p->nf[k];
+                        if (ck < 0) ck += p->nf[k];
+                    } else {
+                        if (ck < 0) ck = 0;
+                        if (ck > p->nf[k] - 1) ck = p->nf[k] - 1;
+                    }
+                    c[k] = ck;
+                }
+                if (vol <= 0.0) continue;
+                int64_t cell = ((int64_t)c[2] * p->nf[1] + c[1]) * p->nf[0] + c[0];
+                sums[cell] += (uint64_t)llrint(vol * inv_q);
+            }
+}
+
+static double porosity(uint64_t S, double n_min) {
+    /* n = 1 - q S / V_cell with q = V_cell 2^-40 */
+    double n = 1.0 - (double)S * ORA_TWO_M40;
+    if (n < n_min) n = n_min;
+    if (n > 1.0) n = 1.0;
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* simulation                                                          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t i, j;
+    int32_t bonded;
+    int32_t pad;
+    double xi[3];
+} ora_rec;
+
+struct ora_sim {
+    ora_params p;
+    int64_t n;
+    double *x, *v, *w, *F, *T, *R, *m, *I;
+    uint8_t* active;
+    int64_t* removed_step;
+    double* wall_xi; /* n * 3 walls * 3 */
+    ora_rec* rec;
+    int64_t nrec;
+    uint64_t* vf;
+    double* Us;
+    int64_t ncell_f;
+    int64_t step;
+    double produced;
+};
+
+static int rec_cmp(const void* a, const void* b) {
+    const ora_rec* x = (const ora_rec*)a;
+    const ora_rec* y = (const ora_rec*)b;
+    if (x->i != y->i) return x->i < y->i ? -1 : 1;
+    if (x->j != y->j) return x->j < y->j ? -1 : 1;
+    return 0;
+}
+
+ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const double* v,
+                    const double* w, const double* R, const double* Us) {
+    if (!p || n < 0) return NULL;
+    ora_sim* s = (ora_sim*)calloc(1, sizeof(ora_sim));
+    s->p = *p;
+    s->n = n;
+    size_t n3 = (size_t)(n > 0 ? n : 1) * 3;
+    s->x = (double*)calloc(n3, sizeof(double));
+    s->v = (double*)calloc(n3, sizeof(double));
+    s->w = (double*)calloc(n3, sizeof(double));
+    s->F = (double*)calloc(n3, sizeof(double));
+    s->T = (double*)calloc(n3, sizeof(double));
+    s->R = (double*)calloc(n3, sizeof(double));
+    s->m = (double*)calloc(n3, sizeof(double));
+    s->I = (double*)calloc(n3, sizeof(double));
+    s->active = (uint8_t*)calloc(n3, 1);
+    s->removed_step = (int64_t*)calloc(n3, sizeof(int64_t));
+    s->wall_xi = (double*)calloc(n3 * 3, sizeof(double));
+    if (n > 0) {
+        memcpy(s->x, x, sizeof(double) * 3 * n);
+        memcpy(s->v, v, sizeof(double) * 3 * n);
+        memcpy(s->w, w, sizeof(double) * 3 * n);
+        memcpy(s->R, R, sizeof(double) * n);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        s->m[i] = p->rho * sphere_volume(R[i]);  /* Eq. 17-20: m = rho V */
+        s->I[i] = 0.4 * s->m[i] * R[i] * R[i];   /* solid sphere */
+        s->active[i] = 1;
+        s->removed_step[i] = -1;
+    }
+    s->ncell_f = (int64_t)p->nf[0] * p->nf[1] * p->nf[2];
+    s->vf = (uint64_t*)calloc((size_t)s->ncell_f + 1, sizeof(uint64_t));
+    s->Us = (double*)calloc((size_t)s->ncell_f * 3 + 3, sizeof(double));
+    if (Us) memcpy(s->Us, Us, sizeof(double) * 3 * s->ncell_f);
+    return s;
+}
+
+void ora_destroy(ora_sim* s) {
+    if (!s) return;
+    free(s->x); free(s->v); free(s->w); free(s->F); free(s->T);
+    free(s->R); free(s->m); free(s->I); free(s->active); free(s->removed_step);
+    free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us);
+    free(s);
+}
+
+/* ---- touching-pair search: linked cells (or all pairs when the grid is tiny) ---- */
+typedef struct {
+    int32_t* pi;
+    int32_t* pj;
+    int64_t n, cap;
+} pairlist;
+
+static void pl_push(pairlist* l, int32_t i, int32_t j) {
+    if (l->n == l->cap) {
+        l->cap = l->cap ? 2 * l->cap : 1024;
+        l->pi = (int32_t*)realloc(l->pi, sizeof(int32_t) * l->cap);
+        l->pj = (int32_t*)realloc(l->pj, sizeof(int32_t) * l->cap);
+    }
+    l->pi[l->n] = i;
+    l->pj[l->n] = j;
+    l->n++;
+}
+
+/* all pairs (i<j, both active) with d^2 < (Ri+Rj+skin)^2 */
+static void find_pairs(const ora_params* p, int64_t n, const double* x, const double* R,
+                       const uint8_t* active, double skin, pairlist* out) {
+    double Rmax = 0.0;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < n; ++i) {
+        if (active && !active[i]) continue;
+        if (R[i] > Rmax) Rmax = R[i];
+        for (int k = 0; k < 3; ++k) {
+            if (x[3 * i + k] < lo[k]) lo[k] = x[3 * i + k];
+            if (x[3 * i + k] > hi[k]) hi[k] = x[3 * i + k];
+        }
+    }
+    double h = 2.0 * Rmax + skin;
+    int nc[3];
+    int brute = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (p->kind == 0) {
+            lo[k] = 0.0;
+            hi[k] = p->L[k];
+            nc[k] = (int)floor(p->L[k] / h);
+            if (nc[k] < 3) brute = 1;
+        } else {
+            nc[k] = (int)floor((hi[k] - lo[k]) / h);
+            if (nc[k] < 1 || !(hi[k] > lo[k])) {
+                nc[k] = 1;
+                hi[k] = lo[k] + 1.0;
+            }
+        }
+        if (nc[k] > 1024) nc[k] = 1024;
+    }
+    if (n < 64) brute = 1;
+    if (brute) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (active && !active[i]) continue;
+            for (int64_t j = i + 1; j < n; ++j) {
+                if (active && !active[j]) continue;
+                double d[3];
+                for (int k = 0; k < 3; ++k) {
+                    d[k] = x[3 * j + k] - x[3 * i + k];
+                    if (p->kind == 0) d[k] = min_image(d[k], p->L[k]);
+                }
+                double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double S = R[i] + R[j] + skin;
+                if (d2 < S * S) pl_push(out, (int32_t)i, (int32_t)j);
+            }
+        }
+        return;
+    }
+    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int64_t* head = (int64_t*)malloc(sizeof(int64_t) * ncell);
+    int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int* cidx = (int*)malloc(sizeof(int) * 3 * (n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        if (active && !active[i]) continue;
+        for (int k = 0; k < 3; ++k) {
+            double t = floor((x[3 * i + k] - lo[k]) / (hi[k] - lo[k]) * nc[k]);
+            if (t < 0) t = 0;
+            if (t > nc[k] - 1) t = nc[k] - 1;
+            cidx[3 * i + k] = (int)t;
+        }
+        int64_t c = ((int64_t)cidx[3 * i + 2] * nc[1] + cidx[3 * i + 1]) * nc[0] + cidx[3 * i];
+        next[i] = head[c];
+        head[c] = i;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (active && !active[i]) continue;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int c3[3] = {cidx[3 * i] + dx, cidx[3 * i + 1] + dy, cidx[3 * i + 2] + dz};
+                    int skip = 0;
+                    for (int k = 0; k < 3; ++k) {
+                        if (p->kind == 0) {
+                            c3[k] = (c3[k] + nc[k]) % nc[k];
+                        } else if (c3[k] < 0 || c3[k] >= nc[k]) {
+                            skip = 1;
+                        }
+                    }
+                    if (skip) continue;
+                    int64_t c = ((int64_t)c3[2] * nc[1] + c3[1]) * nc[0] + c3[0];
+                    for (int64_t j = head[c]; j >= 0; j = next[j]) {
+                        if (j <= i) continue;
+                        double d[3];
+                        for (int k = 0; k < 3; ++k) {
+                            d[k] = x[3 * j + k] - x[3 * i + k];
+                            if (p->kind == 0) d[k] = min_image(d[k], p->L[k]);
+                        }
+                        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        double S = R[i] + R[j] + skin;
+                        if (d2 < S * S) pl_push(out, (int32_t)i, (int32_t)j);
+                    }
+                }
+    }
+    free(head);
+    free(next);
+    free(cidx);
+}
+
+int64_t ora_pairs_bruteforce(const ora_params* p, int64_t n, const double* x, const double* R,
+                             double skin, int32_t* pi, int32_t* pj, int64_t cap) {
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double d[3];
+            for (int k = 0; k < 3; ++k) {
+                d[k] = x[3 * j + k] - x[3 * i + k];
+                if (p->kind == 0) d[k] = min_image(d[k], p->L[k]);
+            }
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double S = R[i] + R[j] + skin;
+            if (d2 < S * S) {
+                if (cnt < cap) {
+                    pi[cnt] = (int32_t)i;
+                    pj[cnt] = (int32_t)j;
+                }
+                cnt++;
+            }
+        }
+    return cnt;
+}
+
+int ora_bond_touching(ora_sim* s) {
+    /* every touching pair (d^2 < (Ri+Rj)^2) becomes a bonded record */
+    pairlist l = {0};
+    find_pairs(&s->p, s->n, s->x, s->R, s->active, 0.0, &l);
+    free(s->rec);
+    s->rec = (ora_rec*)calloc((size_t)(l.n > 0 ? l.n : 1), sizeof(ora_rec));
+    s->nrec = 0;
+    for (int64_t k = 0; k < l.n; ++k) {
+        ora_rec r = {l.pi[k], l.pj[k], 1, 0, {0, 0, 0}};
+        s->rec[s->nrec++] = r;
+    }
+    qsort(s->rec, (size_t)s->nrec, sizeof(ora_rec), rec_cmp);
+    free(l.pi);
+    free(l.pj);
+    return 0;
+}
+
+int ora_couple_fluid(ora_sim* s) {
+    memset(s->vf, 0, sizeof(uint64_t) * (size_t)s->ncell_f);
+    for (int64_t i = 0; i < s->n; ++i) {
+        if (!s->active[i]) continue;
+        add_voidfrac(&s->p, &s->x[3 * i], s->R[i], s->vf);
+    }
+    return 0;
+}
+
+int ora_voidfrac(const ora_params* p, int64_t n, const double* x, const double* R,
+                 uint64_t* cell_sums) {
+    int64_t nc = (int64_t)p->nf[0] * p->nf[1] * p->nf[2];
+    memset(cell_sums, 0, sizeof(uint64_t) * (size_t)nc);
+    for (int64_t i = 0; i < n; ++i) add_voidfrac(p, &x[3 * i], R[i], cell_sums);
+    return 0;
+}
+
+static const ora_rec* find_rec(const ora_rec* rec, int64_t nrec, int32_t i, int32_t j) {
+    ora_rec key;
+    key.i = i;
+    key.j = j;
+    return (const ora_rec*)bsearch(&key, rec, (size_t)nrec, sizeof(ora_rec), rec_cmp);
+}
+
+static int pair_cmp(const void* a, const void* b) {
+    const int32_t* x = (const int32_t*)a;
+    const int32_t* y = (const int32_t*)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1;
+    return 0;
+}
+
+/* wall contacts of one particle (cylinder domain), Hertz without cohesion */
+static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
+    const ora_params* p = &s->p;
+    const double* x = &s->x[3 * i];
+    double R = s->R[i];
+    double r = sqrt(x[0] * x[0] + x[1] * x[1]);
+    for (int wall = 0; wall < 3; ++wall) {
+        double n[3] = {0, 0, 0};
+        double delta = -1.0;
+        if (wall == 0) { /* side wall r = Rc */
+            if (r > 0.0) {
+                delta = (r + R) - p->Rc;
+                n[0] = x[0] / r;
+                n[1] = x[1] / r;
+            }
+        } else if (wall == 1) { /* bottom plane z = 0, open over the outlet r < r_out */
+            if (r >= p->r_out) {
+                delta = R - x[2];
+                n[2] = -1.0;
+            }
+        } else { /* top plane z = H */
+            delta = (x[2] + R) - p->H;
+            n[2] = 1.0;
+        }
+        double* h = &s->wall_xi[9 * i + 3 * wall];
+        if (!(delta > 0.0)) {
+            h[0] = h[1] = h[2] = 0.0;
+            continue;
+        }
+        const double* v = &s->v[3 * i];
+        const double* w = &s->w[3 * i];
+        double vrel[3] = {-v[0], -v[1], -v[2]};
+        double rw[3] = {R * w[0], R * w[1], R * w[2]};
+        double rwn[3];
+        cross(rw, n, rwn);
+        double vc[3] = {vrel[0] - rwn[0], vrel[1] - rwn[1], vrel[2] - rwn[2]};
+        int bonded = 0;
+        double F[3], Ft[3];
+        if (!contact_law(p, delta, 1, n, vrel, vc, R, s->m[i], 0.0, h, &bonded, F, Ft, NULL, NULL))
+            continue;
+        double nFt[3];
+        cross(n, Ft, nFt);
+        for (int k = 0; k < 3; ++k) {
+            Fi[k] += F[k];
+            Ti[k] += R * nFt[k];
+        }
+    }
+}
+
+int ora_compute_forces(ora_sim* s) {
+    const ora_params* p = &s->p;
+    int64_t n = s->n;
+    memset(s->F, 0, sizeof(double) * 3 * (size_t)n);
+    memset(s->T, 0, sizeof(double) * 3 * (size_t)n);
+
+    /* candidates: touching pairs plus surviving bonded records */
+    pairlist l = {0};
+    find_pairs(p, n, s->x, s->R, s->active, 0.0, &l);
+    for (int64_t k = 0; k < s->nrec; ++k) {
+        if (s->rec[k].bonded && s->active[s->rec[k].i] && s->active[s->rec[k].j])
+            pl_push(&l, s->rec[k].i, s->rec[k].j);
+    }
+    int32_t* pr = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)(l.n > 0 ? l.n : 1));
+    for (int64_t k = 0; k < l.n; ++k) {
+        pr[2 * k] = l.pi[k];
+        pr[2 * k + 1] = l.pj[k];
+    }
+    qsort(pr, (size_t)l.n, 2 * sizeof(int32_t), pair_cmp);
+    ora_rec* nrec = (ora_rec*)calloc((size_t)(l.n > 0 ? l.n : 1), sizeof(ora_rec));
+    int64_t nn = 0;
+    for (int64_t k = 0; k < l.n; ++k) {
+        if (k > 0 && pr[2 * k] == pr[2 * k - 2] && pr[2 * k + 1] == pr[2 * k - 1]) continue;
+        int32_t i = pr[2 * k], j = pr[2 * k + 1];
+        const ora_rec* old = find_rec(s->rec, s->nrec, i, j);
+        ora_rec r = {i, j, old ? old->bonded : 0, 0, {0, 0, 0}};
+        if (old) memcpy(r.xi, old->xi, sizeof(r.xi));
+        double Fi[3], Ti[3], Tj[3];
+        int act = pair_eval(p, &s->x[3 * i], &s->v[3 * i], &s->w[3 * i], s->R[i], s->m[i],
+                            &s->x[3 * j], &s->v[3 * j], &s->w[3 * j], s->R[j], s->m[j], r.xi,
+                            &r.bonded, Fi, Ti, Tj, NULL, NULL, NULL);
+        if (!act) continue;
+        for (int c = 0; c < 3; ++c) {
+            s->F[3 * i + c] += Fi[c];
+            s->F[3 * j + c] -= Fi[c];
+            s->T[3 * i + c] += Ti[c];
+            s->T[3 * j + c] += Tj[c];
+        }
+        nrec[nn++] = r;
+    }
+    free(pr);
+    free(l.pi);
+    free(l.pj);
+    free(s->rec);
+    s->rec = nrec;
+    s->nrec = nn;
+
+    /* walls, body forces and drag */
+    for (int64_t i = 0; i < n; ++i) {
+        if (!s->active[i]) continue;
+        double* F = &s->F[3 * i];
+        double* T = &s->T[3 * i];
+        if (p->kind == 1) wall_forces(s, i, F, T);
+        double V = sphere_volume(s->R[i]);
+        for (int c = 0; c < 3; ++c) {
+            F[c] += s->m[i] * p->g[c];                        /* F_g */
+            if (p->use_buoyancy) F[c] += -p->rho_f * V * p->g[c]; /* F_b */
+        }
+        if (p->use_drag) {
+            int64_t cell = fluid_cell(p, &s->x[3 * i]);
+            double nc = porosity(s->vf[cell], p->n_min);
+            double u[3] = {s->Us[3 * cell] / nc, s->Us[3 * cell + 1] / nc, s->Us[3 * cell + 2] / nc};
+            double fd[3];
+            ora_drag(p->rho_f, p->mu_f, 2.0 * s->R[i], u, &s->v[3 * i], nc, fd);
+            for (int c = 0; c < 3; ++c) F[c] += fd[c];
+        }
+    }
+    return 0;
+}
+
+int ora_set_forces(ora_sim* s, const double* F, const double* T) {
+    memcpy(s->F, F, sizeof(double) * 3 * (size_t)s->n);
+    memcpy(s->T, T, sizeof(double) * 3 * (size_t)s->n);
+    return 0;
+}
+
+static void half_kick(ora_sim* s) {
+    double h = 0.5 * s->p.dt;
+    for (int64_t i = 0; i < s->n; ++i) {
+        if (!s->active[i]) continue;
+        for (int c = 0; c < 3; ++c) {
+            s->v[3 * i + c] += h * s->F[3 * i + c] / s->m[i]; /* Eq. 1 */
+            s->w[3 * i + c] += h * s->T[3 * i + c] / s->I[i]; /* Eq. 2 */
+        }
+    }
+}
+
+int ora_step(ora_sim* s, int64_t nsteps) {
+    const ora_params* p = &s->p;
+    for (int64_t st = 0; st < nsteps; ++st) {
+        half_kick(s);
+        for (int64_t i = 0; i < s->n; ++i) {
+            if (!s->active[i]) continue;
+            for (int c = 0; c < 3; ++c) {
+                double xc = s->x[3 * i + c] + p->dt * s->v[3 * i + c];
+                if (p->kind == 0) {
+                    if (xc >= p->L[c]) xc -= p->L[c];
+                    else if (xc < 0.0) xc += p->L[c];
+                }
+                s->x[3 * i + c] = xc;
+            }
+        }
+        int ce = p->couple_every > 0 ? p->couple_every : 1;
+        if (s->step % ce == 0) ora_couple_fluid(s);
+        ora_compute_forces(s);
+        half_kick(s);
+        s->step++;
+        if (p->kind == 1) {
+            for (int64_t i = 0; i < s->n; ++i) {
+                if (!s->active[i]) continue;
+                if (s->x[3 * i + 2] < -2.0 * s->R[i]) { /* outlet: produced sand, Eq. 40 */
+                    s->active[i] = 0;
+                    s->removed_step[i] = s->step;
+                    s->produced += s->m[i];
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+int ora_get_state(const ora_sim* s, double* x, double* v, double* w, double* F, double* T) {
+    size_t b = sizeof(double) * 3 * (size_t)s->n;
+    if (x) memcpy(x, s->x, b);
+    if (v) memcpy(v, s->v, b);
+    if (w) memcpy(w, s->w, b);
+    if (F) memcpy(F, s->F, b);
+    if (T) memcpy(T, s->T, b);
+    return 0;
+}
+
+int64_t ora_num_contacts(const ora_sim* s) { return s->nrec; }
+
+int ora_get_contacts(const ora_sim* s, int32_t* id_i, int32_t* id_j, uint8_t* bonded,
+                     double* xi, int64_t cap) {
+    if (cap < s->nrec) return -1;
+    for (int64_t k = 0; k < s->nrec; ++k) {
+        if (id_i) id_i[k] = s->rec[k].i;
+        if (id_j) id_j[k] = s->rec[k].j;
+        if (bonded) bonded[k] = (uint8_t)s->rec[k].bonded;
+        if (xi) memcpy(&xi[3 * k], s->rec[k].xi, 3 * sizeof(double));
+    }
+    return 0;
+}
+
+int ora_get_voidfrac(const ora_sim* s, uint64_t* cell_sums) {
+    memcpy(cell_sums, s->vf, sizeof(uint64_t) * (size_t)s->ncell_f);
+    return 0;
+}
+
+int ora_get_diagnostics(const ora_sim* s, double out[8]) {
+    double ke = 0, kr = 0, P[3] = {0, 0, 0}, na = 0, nb = 0;
+    for (int64_t i = 0; i < s->n; ++i) {
+        if (!s->active[i]) continue;
+        const double* v = &s->v[3 * i];
+        const double* w = &s->w[3 * i];
+        ke += 0.5 * s->m[i] * dot(v, v);
+        kr += 0.5 * s->I[i] * dot(w, w);
+        for (int c = 0; c < 3; ++c) P[c] += s->m[i] * v[c];
+        na += 1;
+    }
+    for (int64_t k = 0; k < s->nrec; ++k) nb += s->rec[k].bonded ? 1 : 0;
+    out[0] = ke; out[1] = kr; out[2] = P[0]; out[3] = P[1]; out[4] = P[2];
+    out[5] = s->produced; out[6] = na; out[7] = nb;
+    return 0;
+}
+
+int ora_get_removed_step(const ora_sim* s, int64_t* removed_step) {
+    memcpy(removed_step, s->removed_step, sizeof(int64_t) * (size_t)s->n);
+    return 0;
+}

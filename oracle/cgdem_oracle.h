@@ -1,0 +1,116 @@
+/*
+ * cgdem_oracle.h -- FP64 CPU oracle for the coarse-grained CFD-DEM step of
+ * Kazidenov, Khamitov & Amanbek, "Coarse-graining of CFD-DEM for simulation
+ * of sand production in the modified cohesive contact model" (arXiv
+ * 2211.06142).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is a plain, slow, single-threaded
+ * restatement of the paper's equations.  It exists so that tests and the
+ * benchmark's CPU baseline can check the CUDA library against something
+ * written independently from the paper.  It shares no code, header, table or
+ * constant generator with the CUDA path and must never be linked into it.
+ *
+ * Units are SI.  Every function returns 0 on success and a negative value on
+ * a bad argument.
+ */
+#ifndef CGDEM_ORACLE_H
+#define CGDEM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Problem description for ONE sample, at grain level (after coarse-graining). */
+typedef struct {
+    /* material (Table 3; E*, G*, beta derived inside) */
+    double rho, E, nu, e, mu, gamma;
+    /* fluid (Table 4) */
+    double rho_f, mu_f;
+    int use_drag;       /* 1: Di Felice drag, Eq. 8-11 */
+    int use_buoyancy;   /* 1: Archimedes force -rho_f V g */
+    /* domain: 0 periodic box [0,L0)x[0,L1)x[0,L2); 1 cylinder axis z through
+       the origin, radius Rc, bottom plane z=0 open for r<r_out, top z=H */
+    int kind;
+    double L[3];
+    double Rc, H, r_out;
+    double g[3];
+    double dt;
+    int coulomb_mode;   /* 0: F_lim = F_ne + 2 F_C if bonded else F_ne; 1: |F_ne| */
+    /* fluid grid: cell of x is floor((x - f_lo) * inv_hf) clamped to [0,nf-1] */
+    int nf[3];
+    double f_lo[3], hf[3], inv_hf[3];
+    double V_cell;      /* cell volume used for the void-fraction quanta */
+    double n_min;       /* lower clamp of the porosity */
+    int vf_mode;        /* 0 centroid, 1 equal-volume cube overlap */
+    int couple_every;   /* recompute the void fraction every k-th step */
+} ora_params;
+
+/* ---- closed forms and single-contact laws (pins and unit tests) ---- */
+/* E* for one material (Eq. 12 definitions with E1=E2, nu1=nu2). */
+double ora_estar(double E, double nu);
+/* beta from the restitution coefficient (Eq. 33, squared log restored). */
+double ora_beta(double e);
+/* contact radius a on the stable branch a >= a_C solving Eq. 13 by bisection. */
+double ora_jkr_contact_radius(double delta, double Rs, double Es, double gamma);
+/* Eq. 12 */
+double ora_jkr_force(double a, double Rs, double Es, double gamma);
+/* Eq. 13 */
+double ora_jkr_overlap(double a, double Rs, double Es, double gamma);
+/* Table 1 point C overlap, delta_C (negative). */
+double ora_delta_c(double Rs, double Es, double gamma);
+/* modified-JKR break test: 1 when delta < delta_C (evaluated as documented). */
+int ora_bond_breaks(double delta, double Rs, double Es, double gamma);
+/* Rayleigh time step Eq. 37-38 with G = E/(2(1+nu)). */
+double ora_rayleigh_dt(double Rbar, double rho, double E, double nu);
+
+/* One particle-particle contact evaluated in isolation.
+ * xi_inout: tangential spring (force-on-i convention), updated in place.
+ * bonded_inout: bond state, cleared on break.
+ * out: F_i[3], T_i[3], T_j[3], then Fn_elastic, a, delta (12 doubles).
+ * Returns 1 if the contact is active (force applied), 0 if not. */
+int ora_pair_contact(const ora_params* p,
+                     const double xi_pos[3], const double vi[3], const double wi[3], double Ri, double mi,
+                     const double xj_pos[3], const double vj[3], const double wj[3], double Rj, double mj,
+                     double xi_inout[3], int* bonded_inout, double out[12]);
+
+/* Di Felice drag on one particle, Eq. 8-11.  u = interstitial fluid velocity. */
+void ora_drag(double rho_f, double mu_f, double d, const double u[3], const double v[3],
+              double n, double f_out[3]);
+
+/* ---- whole-sample simulation ---- */
+typedef struct ora_sim ora_sim;
+
+ora_sim* ora_create(const ora_params* p, int64_t n,
+                    const double* x, const double* v, const double* w,
+                    const double* R, const double* Us /* [nf0*nf1*nf2*3] superficial velocity */);
+void ora_destroy(ora_sim* s);
+/* Bond every pair with delta >= 0 (Sec. 3.1 perforation stage reading). */
+int ora_bond_touching(ora_sim* s);
+/* Cell sums of the void-fraction quanta at the current positions. */
+int ora_couple_fluid(ora_sim* s);
+/* Forces and torques at the current state; advances tangential history by dt. */
+int ora_compute_forces(ora_sim* s);
+/* nsteps of velocity Verlet (half kick, drift, contacts, fluid, forces, half kick, outlet). */
+int ora_step(ora_sim* s, int64_t nsteps);
+int ora_get_state(const ora_sim* s, double* x, double* v, double* w, double* F, double* T);
+int ora_set_forces(ora_sim* s, const double* F, const double* T);
+int64_t ora_num_contacts(const ora_sim* s);
+/* Active particle contacts sorted by (id_i < id_j). xi has 3 entries per contact. */
+int ora_get_contacts(const ora_sim* s, int32_t* id_i, int32_t* id_j, uint8_t* bonded,
+                     double* xi, int64_t cap);
+int ora_get_voidfrac(const ora_sim* s, uint64_t* cell_sums);
+/* KE_trans, KE_rot, Px, Py, Pz, produced mass, n_active, n_bonds */
+int ora_get_diagnostics(const ora_sim* s, double out[8]);
+int ora_get_removed_step(const ora_sim* s, int64_t* removed_step);
+/* Brute force O(N^2) list of pairs with d^2 < (Ri+Rj+skin)^2 (minimum image). */
+int64_t ora_pairs_bruteforce(const ora_params* p, int64_t n, const double* x, const double* R,
+                             double skin, int32_t* pi, int32_t* pj, int64_t cap);
+/* Void-fraction quanta of one sample at given positions (no simulation). */
+int ora_voidfrac(const ora_params* p, int64_t n, const double* x, const double* R,
+                 uint64_t* cell_sums);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

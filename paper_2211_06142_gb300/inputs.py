@@ -1,0 +1,284 @@
+"""Seeded synthetic inputs for the coarse-grained CFD-DEM step.
+
+This module only draws inputs: particle size distributions, packed
+positions, initial velocities and the prescribed superficial fluid-velocity
+field, plus the workload descriptions they belong to.  It holds none of the
+method's arithmetic (no contact law, no coarse-graining rule, no time-step
+rule), so both the CUDA library and the CPU oracle can be fed from it.
+
+Workloads stand in for the paper's reservoir-sand sample (Sec. 3.1, Table 2);
+there is no public dataset, so every array here is drawn from a seed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# fluid properties of Table 4 (water)
+WATER_RHO = 998.2
+WATER_MU = 1.0e-3
+
+# Table 2: mass fraction per diameter class of the original particles [mm]
+TABLE2_MASS_FRACTION = np.array([0.058, 0.075, 0.088, 0.1216, 0.2264, 0.1705, 0.121, 0.1395])
+TABLE2_DIAMETER_MM = np.array([0.15, 0.18, 0.2, 0.22, 0.25, 0.275, 0.3, 0.355])
+
+
+def lognormal_diameters(n: int, d50: float, sigma_ln: float, dmin: float, dmax: float,
+                        rng: np.random.Generator) -> np.ndarray:
+    """Diameters with a log-normal distribution truncated to [dmin, dmax].
+
+    d50 is read as the MASS median (sieve analyses such as Table 2 are by
+    mass); the number median of a log-normal with log-standard deviation
+    sigma is then d50 * exp(-3 sigma^2).
+    """
+    mu = math.log(d50) - 3.0 * sigma_ln ** 2
+    out = np.empty(0)
+    while out.size < n:
+        d = np.exp(rng.normal(mu, sigma_ln, size=2 * (n - out.size) + 16))
+        d = d[(d >= dmin) & (d <= dmax)]
+        out = np.concatenate([out, d])
+    return out[:n].copy()
+
+
+def table2_diameters(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Diameters drawn from the 8 classes of Table 2 (by mass) [m]."""
+    d = TABLE2_DIAMETER_MM * 1e-3
+    w = TABLE2_MASS_FRACTION / d ** 3
+    idx = rng.choice(len(d), size=n, p=w / w.sum())
+    return d[idx]
+
+
+# ---------------------------------------------------------------------------
+# packing: random placement, then overlap removal (geometry only)
+# ---------------------------------------------------------------------------
+
+_PACKER = None
+
+
+def _packer():
+    """Load (compiling on first use) the C overlap-removal packer."""
+    global _PACKER
+    if _PACKER is None:
+        import ctypes
+        import os
+        import subprocess
+
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "gen", "packer.c")
+        out_dir = os.path.join(here, "_build")
+        lib = os.path.join(out_dir, "libcgdem_packer.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            os.makedirs(out_dir, exist_ok=True)
+            tmp = lib + ".tmp.%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        pd = ctypes.POINTER(ctypes.c_double)
+        L.gen_pack.restype = ctypes.c_int
+        L.gen_pack.argtypes = [ctypes.c_int64, pd, pd, ctypes.c_int, pd, ctypes.c_int, ctypes.c_double]
+        _PACKER = L
+    return _PACKER
+
+
+def _pack(x, R, kind, geo, iters, tol):
+    import ctypes
+
+    pd = ctypes.POINTER(ctypes.c_double)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    g = np.ascontiguousarray(geo, dtype=np.float64)
+    _packer().gen_pack(len(R), x.ctypes.data_as(pd), R.ctypes.data_as(pd), kind,
+                       g.ctypes.data_as(pd), iters, tol)
+    return x
+
+
+def pack_periodic(R: np.ndarray, L: float, rng: np.random.Generator, iters: int = 2000,
+                  tol: float = 0.01, squeeze: float = 0.005) -> np.ndarray:
+    """Positions of spheres of radii R in the periodic cube [0, L)^3.
+
+    The spheres are packed with radii R (1 - squeeze) and returned at full
+    size, so that neighbours closer than squeeze (Ri + Rj) overlap slightly,
+    as in a compressed sample.
+    """
+    x = rng.uniform(0.0, L, size=(len(R), 3))
+    x = _pack(x, np.asarray(R) * (1.0 - squeeze), 0, [L], iters, tol)
+    return np.mod(x, L)
+
+
+def pack_cylinder(R: np.ndarray, Rc: float, r_out: float, h_bed: float, rng: np.random.Generator,
+                  iters: int = 2000, tol: float = 0.01, squeeze: float = 0.005) -> np.ndarray:
+    """Positions of spheres inside the annulus r_out < r < Rc, 0 < z < h_bed.
+
+    The central cavity r < r_out (left by the perforation stage) is empty.
+    Packed at radii R (1 - squeeze) as in pack_periodic.
+    """
+    n = len(R)
+    u = rng.uniform(0, 1, n)
+    rr = np.sqrt(r_out ** 2 + u * (Rc ** 2 - r_out ** 2))
+    th = rng.uniform(0, 2 * math.pi, n)
+    z = rng.uniform(0, h_bed, n)
+    x = np.stack([rr * np.cos(th), rr * np.sin(th), z], 1)
+    return _pack(x, np.asarray(R) * (1.0 - squeeze), 1, [Rc, r_out, h_bed], iters, tol)
+
+
+# ---------------------------------------------------------------------------
+# prescribed superficial fluid velocity on a Cartesian grid
+# ---------------------------------------------------------------------------
+
+@dataclass
+class FluidGrid:
+    nf: tuple
+    lo: tuple
+    h: tuple
+
+    @property
+    def inv_h(self):
+        return tuple(1.0 / v for v in self.h)
+
+    @property
+    def V_cell(self):
+        return self.h[0] * self.h[1] * self.h[2]
+
+    @property
+    def ncell(self):
+        return self.nf[0] * self.nf[1] * self.nf[2]
+
+    def centres(self):
+        idx = np.indices(self.nf[::-1]).reshape(3, -1)[::-1].T  # x fastest
+        return np.asarray(self.lo) + (idx + 0.5) * np.asarray(self.h)
+
+
+def uniform_field(grid: FluidGrid, U) -> np.ndarray:
+    return np.tile(np.asarray(U, dtype=np.float64), (grid.ncell, 1))
+
+
+def radial_inflow_field(grid: FluidGrid, U_in: float, Rc: float, r_out: float,
+                        h_bed: float) -> np.ndarray:
+    """Superficial velocity of a radial inflow towards a central perforation.
+
+    Outside the cavity: U_s = -U_in (Rc / r) e_r (volume flux through every
+    cylinder r = const is the same).  Inside the cavity (r < r_out) the
+    collected flux leaves downwards through the outlet: u_z grows linearly
+    with depth below the bed top, u_z = -2 Rc U_in (h_bed - z) / r_out^2.
+    """
+    c = grid.centres()
+    r = np.sqrt(c[:, 0] ** 2 + c[:, 1] ** 2)
+    U = np.zeros_like(c)
+    out = r >= r_out
+    s = -U_in * Rc / np.maximum(r[out], 1e-300)
+    U[out, 0] = s * c[out, 0] / np.maximum(r[out], 1e-300)
+    U[out, 1] = s * c[out, 1] / np.maximum(r[out], 1e-300)
+    cav = ~out
+    depth = np.clip(h_bed - c[cav, 2], 0.0, h_bed)
+    U[cav, 2] = -2.0 * Rc * U_in * depth / r_out ** 2
+    return U
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Sample:
+    """One packed sample, grain level, plus the description of its setting."""
+    name: str
+    x: np.ndarray          # [N,3] m
+    v: np.ndarray          # [N,3] m/s
+    w: np.ndarray          # [N,3] rad/s
+    R: np.ndarray          # [N] m
+    material: dict         # rho, E, nu, e, mu, gamma (grain level)
+    domain: dict           # kind, L, Rc, H, r_out
+    grid: FluidGrid
+    Us: np.ndarray         # [ncell,3] superficial fluid velocity
+    fluid: dict = field(default_factory=lambda: dict(rho_f=WATER_RHO, mu_f=WATER_MU))
+    g: tuple = (0.0, 0.0, -9.81)
+    extra: dict = field(default_factory=dict)
+
+
+def fine_diameters(n: int, seed: int, d50: float = 0.25e-3, sigma_ln: float = 0.4,
+                   dmin: float = 0.1e-3, dmax: float = 0.6e-3) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return lognormal_diameters(n, d50, sigma_ln, dmin, dmax, rng)
+
+
+def periodic_sample(d: np.ndarray, phi: float, seed: int, nf: int = 8, U=(0.0, 0.0, 0.01),
+                    material=None, name="periodic", vel_scale=0.0) -> Sample:
+    """Spheres of diameters d packed to solid fraction phi in a periodic cube."""
+    rng = np.random.default_rng(seed + 1000)
+    R = 0.5 * np.asarray(d, dtype=np.float64)
+    Vs = float((4.0 / 3.0 * math.pi * R ** 3).sum())
+    L = (Vs / phi) ** (1.0 / 3.0)
+    x = pack_periodic(R, L, rng)
+    v = rng.normal(0.0, 1.0, size=x.shape) * vel_scale
+    w = np.zeros_like(x)
+    h = L / nf
+    grid = FluidGrid((nf, nf, nf), (0.0, 0.0, 0.0), (h, h, h))
+    mat = material or dict(rho=2650.0, E=1e8, nu=0.3, e=0.5, mu=0.5, gamma=0.5)
+    dom = dict(kind=0, L=(L, L, L), Rc=0.0, H=0.0, r_out=0.0)
+    return Sample(name, x, v, w, R, dict(mat), dom, grid, uniform_field(grid, U))
+
+
+def cylinder_sample(d: np.ndarray, seed: int, d50: float = 0.25e-3, scale: float = 1.0,
+                    phi: float = 0.55, U_in: float = 0.01, nf=(40, 40, 20), material=None,
+                    name="cylinder") -> Sample:
+    """Sand-production sample: cylinder Rc = 40 d50, H = 30 d50 (x scale),
+    central perforation outlet r_out = 3 d50 on the lower face, bed packed from
+    z = 0 to the height that holds the spheres at solid fraction phi."""
+    rng = np.random.default_rng(seed + 2000)
+    R = 0.5 * np.asarray(d, dtype=np.float64)
+    Rc = 40.0 * d50 * scale
+    H = 30.0 * d50 * scale
+    r_out = 3.0 * d50
+    Vs = float((4.0 / 3.0 * math.pi * R ** 3).sum())
+    h_bed = min(Vs / (phi * math.pi * (Rc ** 2 - r_out ** 2)), H)
+    x = pack_cylinder(R, Rc, r_out, h_bed, rng)
+    v = np.zeros_like(x)
+    w = np.zeros_like(x)
+    h = (2 * Rc / nf[0], 2 * Rc / nf[1], H / nf[2])
+    grid = FluidGrid(tuple(nf), (-Rc, -Rc, 0.0), h)
+    mat = material or dict(rho=2650.0, E=1e8, nu=0.3, e=0.5, mu=0.5, gamma=0.5)
+    dom = dict(kind=1, L=(2 * Rc, 2 * Rc, H), Rc=Rc, H=H, r_out=r_out)
+    return Sample(name, x, v, w, R, dict(mat), dom, grid,
+                  radial_inflow_field(grid, U_in, Rc, r_out, h_bed), extra=dict(h_bed=h_bed))
+
+
+def cached(fn, *args, **kw) -> Sample:
+    """Call a workload constructor, memoising its result on disk.
+
+    The cache lives in $CGDEM_CACHE (default ~/.cache/cgdem) and is keyed by
+    the constructor name and its arguments; delete it to regenerate.
+    """
+    import hashlib
+    import os
+    import pickle
+
+    root = os.environ.get("CGDEM_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cgdem"))
+    key = hashlib.sha1(repr((fn.__name__, args, sorted(kw.items()), 2)).encode()).hexdigest()[:16]
+    path = os.path.join(root, f"{fn.__name__}-{key}.pkl")
+    if os.path.exists(path):
+        with open(path, "rb") as f:
+            return pickle.load(f)
+    s = fn(*args, **kw)
+    try:
+        os.makedirs(root, exist_ok=True)
+        tmp = path + ".tmp.%d" % os.getpid()
+        with open(tmp, "wb") as f:
+            pickle.dump(s, f)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return s
+
+
+def small_periodic(n: int = 2000, seed: int = 0) -> Sample:
+    """2,000 log-normal spheres (mass-median 0.25 mm, sigma_ln 0.4, 0.1-0.6 mm)
+    at solid fraction 0.55 in a periodic cube, 8^3 fluid grid, uniform
+    superficial velocity 0.01 m/s."""
+    return periodic_sample(fine_diameters(n, seed), 0.55, seed, name="periodic-2k")
+
+
+def fine_cylinder(n: int = 200_000, seed: int = 1) -> Sample:
+    """200,000 spheres, same PSD, in the 40x40x20-cell sand-production cylinder."""
+    return cylinder_sample(fine_diameters(n, seed), seed, name="cylinder-200k")
