@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: particle-steps/s of the coarse-grained CFD-DEM step on GB300.
+
+Workload (default): the fine-scale sand-production cylinder -- 200,000
+log-normal spheres (mass-median 0.25 mm, sigma_ln 0.4, 0.1-0.6 mm), radius
+40 d50, height 30 d50, central outlet of radius 3 d50 in the lower face,
+radial inflow of water on a 40x40x20 grid, modified-JKR cohesion, mixed
+FP32-force / FP64-state precision.  The FP64 form runs too and is reported
+beside it.  Inputs are seeded and synthetic (see paper_2211_06142_gb300/inputs.py).
+
+One "step" is one full DEM step of the whole path (candidate-list upkeep,
+porosity scatter, contact/wall/body/drag forces, velocity Verlet, outlet).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (different
+seed); value = all ranks' particle-steps / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-steps/s on 1 GB300 (FP64 vs mixed/batched); sand-mass error vs fine"
+UNIT = "particle-steps/s"
+WORKLOAD = "sand-production cylinder, 200k spheres, 40x40x20 fluid grid"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(n, seed):
+    from paper_2211_06142_gb300 import inputs as I
+    return I.cached(I.fine_cylinder, n, seed)
+
+
+def step_params(s):
+    """dt = 0.2 x Rayleigh step (Eq. 37-38) of the volume-mean radius; skin 2 % of d_max."""
+    from paper_2211_06142_gb300 import cgdem
+    m = s.material
+    Rbar = float(np.mean(s.R ** 3)) ** (1 / 3)
+    dt = 0.2 * cgdem.cgdem_rayleigh_dt(Rbar, m["rho"], m["E"], m["nu"])
+    skin = 0.02 * 2 * float(s.R.max())
+    return dt, skin
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(kernel_file, kernel):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source
+    has not changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, "paper_2211_06142_gb300", "csrc", kernel_file), "rb") as f:
+            h = hashlib.sha1(f.read()).hexdigest()
+        e = t.get(kernel)
+        if e and e.get("source_sha1") == h:
+            return e
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def build_context(s, precision, dt, skin, device, max_neighbors=48):
+    from paper_2211_06142_gb300 import cgdem
+    p = cgdem.sample_params(s, dt, skin)
+    ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=max_neighbors,
+                        block_size=128, steps_per_graph=32, device=device)
+    ctx.set_fluid_velocity(s.Us)
+    ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
+    ctx.compute_forces()
+    return ctx
+
+
+def time_steps(ctx, torch, K, barrier):
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def oracle_baseline(s, dt, budget_s=15.0, n_sub=20000):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the n_sub spheres nearest to a point in the bed (a coherent block of the
+    same packing, walls and outlet included), timed for ~budget_s."""
+    import oracle as O
+    centre = np.array([0.0, 0.0, 0.5 * float(s.extra.get("h_bed", s.domain["H"]))])
+    d2 = ((s.x - centre) ** 2).sum(1)
+    idx = np.sort(np.argsort(d2)[:min(n_sub, len(s.R))])
+    m = s.material
+    d = s.domain
+    p = O.make_params(rho=m["rho"], E=m["E"], nu=m["nu"], e=m["e"], mu=m["mu"], gamma=m["gamma"],
+                      rho_f=s.fluid["rho_f"], mu_f=s.fluid["mu_f"], use_drag=1, use_buoyancy=1,
+                      kind=d["kind"], L=d["L"], Rc=d["Rc"], H=d["H"], r_out=d["r_out"], g=s.g,
+                      dt=dt, nf=s.grid.nf, f_lo=s.grid.lo, hf=s.grid.h, inv_hf=s.grid.inv_h,
+                      V_cell=s.grid.V_cell, n_min=0.2)
+    sim = O.Sim(p, s.x[idx], s.v[idx], s.w[idx], s.R[idx], s.Us)
+    sim.bond_touching()
+    sim.couple_fluid()
+    sim.compute_forces()
+    sim.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        sim.step(1)
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": len(idx) * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(idx)} spheres nearest the bed centre of the same packed cylinder, "
+                      f"{steps} FP64 oracle steps in {el:.1f} s, single thread"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    s = make_workload(200_000, 1)
+    dt, _ = step_params(s)
+    K, W = max(1, args.steps), max(0, args.warmup)
+    # bounded sample per step so that the whole K + W run ends in about a minute
+    n_sub = int(min(len(s.R), max(1000, 8.0e6 / (K + W))))
+    import oracle as O
+    centre = np.array([0.0, 0.0, 0.5 * float(s.extra.get("h_bed", s.domain["H"]))])
+    idx = np.sort(np.argsort(((s.x - centre) ** 2).sum(1))[:n_sub])
+    m, d = s.material, s.domain
+    p = O.make_params(rho=m["rho"], E=m["E"], nu=m["nu"], e=m["e"], mu=m["mu"], gamma=m["gamma"],
+                      rho_f=s.fluid["rho_f"], mu_f=s.fluid["mu_f"], use_drag=1, use_buoyancy=1,
+                      kind=d["kind"], L=d["L"], Rc=d["Rc"], H=d["H"], r_out=d["r_out"], g=s.g,
+                      dt=dt, nf=s.grid.nf, f_lo=s.grid.lo, hf=s.grid.h, inv_hf=s.grid.inv_h,
+                      V_cell=s.grid.V_cell, n_min=0.2)
+    sim = O.Sim(p, s.x[idx], s.v[idx], s.w[idx], s.R[idx], s.Us)
+    sim.bond_touching()
+    sim.couple_fluid()
+    sim.compute_forces()
+    if W:
+        sim.step(W)
+    t0 = time.perf_counter()
+    sim.step(K)
+    el = time.perf_counter() - t0
+    val = n_sub * K / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (FP64 CPU oracle on a bounded block)",
+                       "sample_spheres": n_sub},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sub} spheres nearest the bed centre, {K} timed steps"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2211_06142_gb300 import cgdem
+
+    rank, world, local = dist_env()
+    device = f"cuda:{local}"
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(device))
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+
+    from paper_2211_06142_gb300 import build as B
+    B.build()
+    K, W = max(1, args.steps), max(3, args.warmup)
+    s = make_workload(args.n, 1 + rank)
+    N = len(s.R)
+    dt, skin = step_params(s)
+
+    # ---- mixed precision (headline) ----
+    ctx = build_context(s, cgdem.MIXED, dt, skin, device)
+    ctx.step(W)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    el = time_steps(ctx, torch, K, barrier)
+    clocks = clk.stop()
+    if world > 1:
+        t = torch.tensor([el], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    value = N * K * world / el
+    cnt = ctx.counters()
+    gi, _, gb = ctx.get_contacts()
+    diag = ctx.get_diagnostics()[0]
+    n_act = max(diag["n_active"], 1)
+    Zbar = 2.0 * len(gi) / n_act
+    Cbar = cnt["total_candidates"] / n_act
+    prof = ctx.profile_step(200)
+    # algorithmic bytes per particle-step of the fused force/integrate kernel:
+    # FP64 state (x,R | v,1/m | w,1/I) read + written = 192 B, contact history
+    # of every active contact read + written once per pair (16 B record per
+    # contact per particle), candidate-list entries read (4 B each)
+    alg_bytes = 192.0 + 16.0 * Zbar + 4.0 * Cbar
+    peaks, src = measured_peaks()
+    achieved = alg_bytes * n_act / (prof["force_ms"] * 1e-3) / 1e9
+    tr = kernel_traffic("k_forces.cu", "k_forces_mixed_mid")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": tr["bytes_per_launch"] if tr else None,
+                "peak_source": src, "kernel": "k_forces<mixed, fused step>",
+                "alg_bytes_per_particle_step": alg_bytes, "Zbar": Zbar, "candidates_per_particle": Cbar,
+                "force_kernel_ms": prof["force_ms"],
+                "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1)}
+    launches_per_step = 1 + 9  # fused kernel + the rebuild sequence (early exit unless due)
+    ctx.close()
+    del ctx
+
+    # ---- FP64 form ----
+    ctx64 = build_context(s, cgdem.FP64, dt, skin, device)
+    ctx64.step(W)
+    K64 = max(1, K // 8)
+    el64 = time_steps(ctx64, torch, K64, barrier)
+    fp64 = {"value": N * K64 * world / el64, "unit": UNIT, "steps": K64,
+            "ms_per_step": 1e3 * el64 / K64}
+    ctx64.close()
+    del ctx64
+
+    # ---- end to end through the public API with pinned host buffers ----
+    Ke = min(K, 1000)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    hx, hv, hw, hR = pin(s.x), pin(s.v), pin(s.w), pin(s.R)
+    p = cgdem.sample_params(s, dt, skin)
+    ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device)
+    ctx.set_fluid_velocity(s.Us)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.init_particles(hx, hv, hw, hR, bond_touching=True)
+    ctx.compute_forces()
+    ctx.step(Ke)
+    st = ctx.get_state()
+    t1 = time.perf_counter()
+    barrier()
+    e2e_val = N * Ke * world / (t1 - t0)
+    h2d = (hx.nbytes + hv.nbytes + hw.nbytes + hR.nbytes) / Ke
+    d2h = sum(a.nbytes for a in st.values()) / Ke
+    ctx.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(s, dt)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "spheres_per_gpu": N, "precision": "mixed",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "touched bytes per step exceed half the 129 MB L2; no flush"},
+            "fp64": fp64,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": Ke},
+            "gpu_launches": launches_per_step * K + 2,
+            "clocks": clocks,
+            "rebuilds": cnt["rebuilds"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * cgdem.h -- C ABI of the GB300 (sm_103a) library for the per-timestep
+ * DEM contact and fluid-coupling step of the coarse-grained CFD-DEM method of
+ * Kazidenov, Khamitov & Amanbek, "Coarse-graining of CFD-DEM for simulation
+ * of sand production in the modified cohesive contact model" (arXiv
+ * 2211.06142).
+ *
+ * What one step computes (Sec. 2.1-2.3):
+ *   - Newton-Euler motion of spheres (Eq. 1-2), integrated by velocity Verlet
+ *     with positions, velocities and the integrator update in FP64;
+ *   - contact forces: the modified JKR law (Eq. 12-13, Table 1, Sec. 2.3:
+ *     bonds break at point C and never reform; new contacts are Hertz),
+ *     normal damping (Eq. 32-33), tangential spring-dashpot with per-contact
+ *     history and Coulomb limit (Eq. 4, 35), contact torque (Eq. 5);
+ *     Hertz walls of a cylindrical sample (Sec. 3.1 particle-wall contacts);
+ *   - porosity n per fluid cell from a fixed-point particle-volume scatter
+ *     (n of Eq. 6) and the Di Felice drag gathered back (Eq. 8-11),
+ *     gravity and buoyancy (Eq. 1);
+ *   - coarse-grained parameters by the SSW / SSP rules (Sec. 2.4, Eq. 14-35,
+ *     Table 3): only the surface energy changes, gamma_g = k gamma_p.
+ *
+ * Conventions.
+ *   - Units are SI.  Every function returns a cgdem_status (0 = OK, < 0 =
+ *     error) unless stated.  Errors are also described by cgdem_last_error.
+ *   - Particles are numbered by their position in the arrays passed to
+ *     cgdem_init_particles (the "id"); samples are consecutive id ranges.
+ *     Every host array that this library reads or writes is in id order.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is enqueued on that stream; calls
+ *     that copy to or from host memory synchronise it before returning.
+ *   - Device memory belongs to the caller: the library carves one workspace
+ *     (size from cgdem_workspace_size) and never calls cudaMalloc/cudaFree.
+ *     The context object itself is host memory owned by the library.
+ *   - A context is not thread-safe; calls on one context must not overlap.
+ *   - Device-side errors (contact-list capacity exceeded, a bond that left
+ *     the candidate list, a non-finite force) are latched in a status word on
+ *     the device and returned by the next cgdem_status_sync or cgdem_get_*.
+ */
+#ifndef CGDEM_H
+#define CGDEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CGDEM_OK = 0,
+    CGDEM_E_INVALID = -1,   /* bad argument; nothing was enqueued */
+    CGDEM_E_CAPACITY = -2,  /* a particle has more candidate neighbours than max_neighbors */
+    CGDEM_E_CUDA = -3,      /* a CUDA runtime call failed */
+    CGDEM_E_NONFINITE = -4, /* a force or position became NaN/Inf */
+    CGDEM_E_STATE = -6      /* call out of order, or a bonded pair left the candidate list */
+} cgdem_status;
+
+typedef enum { CGDEM_FP64 = 0, CGDEM_MIXED = 1 } cgdem_precision;
+typedef enum { CGDEM_PERIODIC_BOX = 0, CGDEM_CYLINDER = 1 } cgdem_domain_kind;
+typedef enum { CGDEM_CG_NONE = 0, CGDEM_CG_SSW = 1, CGDEM_CG_SSP = 2 } cgdem_cg_scheme;
+
+/*
+ * Description of one sample, given at the FINE scale for the material:
+ * the library applies the coarse-graining rules itself (gamma_g = k gamma,
+ * Eq. 24; rho, E, nu, e, mu unchanged, Eq. 19, 28, 34, 35).  Radii passed to
+ * cgdem_init_particles are grain radii (see cgdem_cg_scale_diameters).
+ */
+typedef struct {
+    /* material, fine scale (Table 3) */
+    double rho, E, nu, e, mu, gamma;
+    /* coarse graining (Eq. 14-16): factor k >= 1 and scheme */
+    double k_cg;
+    int cg_scheme;          /* cgdem_cg_scheme */
+    /* fluid (Table 4) */
+    double rho_f, mu_f;
+    int use_drag;           /* Di Felice drag Eq. 8-11 on/off */
+    int use_buoyancy;       /* -rho_f V g on/off */
+    /* domain: periodic cube [0,L)^3 (L[0]==L[1]==L[2] required in mixed
+       precision), or a cylinder of radius Rc about the z axis, bottom plane
+       z = 0 open over r < r_out (the outlet), top plane z = H */
+    int kind;               /* cgdem_domain_kind */
+    double L[3];
+    double Rc, H, r_out;
+    double g[3];
+    double dt;              /* time step [s]; > 0 */
+    int coulomb_mode;       /* 0: F_lim = F_ne + 2 F_C on bonds, F_ne otherwise; 1: |F_ne| */
+    /* fluid grid: cell of x is floor((x - f_lo) * inv_hf) clamped per axis;
+       cells numbered x fastest.  V_cell is the cell volume of Eq. 7. */
+    int nf[3];
+    double f_lo[3], hf[3], inv_hf[3];
+    double V_cell;
+    double n_min;           /* lower clamp of the porosity */
+    int vf_mode;            /* 0 centroid, 1 equal-volume cube spread over cells */
+    int couple_every;       /* recompute the porosity every k-th step (>= 1, equal in all samples) */
+    double skin;            /* candidate-list skin [m]; > 2 |delta_C| required */
+    double r_max;           /* largest grain radius the sample holds [m] (sizes the search grid) */
+} cgdem_sample_params;
+
+typedef struct {
+    int precision;          /* cgdem_precision */
+    int n_samples;          /* >= 1 */
+    int max_neighbors;      /* candidate-list width per particle (ELL columns) */
+    int block_size;         /* threads per block of the force kernel (64..1024, multiple of 32) */
+    double cell_scale;      /* search cell edge = cell_scale * (2 R_max + skin), >= 1 */
+    int steps_per_graph;    /* steps captured in one CUDA graph by cgdem_step (>= 1) */
+} cgdem_config;
+
+typedef struct cgdem_ctx cgdem_ctx;
+
+/* ---------------------------------------------------------------------
+ * Host-only helpers (no GPU needed).
+ * ------------------------------------------------------------------- */
+
+/* Rayleigh critical time step, Eq. 37-38, with G = E / (2 (1 + nu)). */
+double cgdem_rayleigh_dt(double Rbar, double rho, double E, double nu);
+
+/* Coarse-grained diameters from n_fine fine diameters (Sec. 2.4, Fig. 3):
+ *   SSW: d_g = k d_p for the first floor(n_fine / k^3) fine particles;
+ *   SSP: every grain has d_g = k (mean d_p^3)^(1/3), floor(n_fine / k^3) grains;
+ *   NONE or k == 1: a copy.
+ * d_out needs room for n_fine entries; *n_out receives the grain count. */
+int cgdem_cg_scale_diameters(const double* d_fine, int64_t n_fine, double k, int scheme,
+                             double* d_out, int64_t* n_out);
+
+/* Device bytes needed for the given samples; counts[s] = grains of sample s. */
+int cgdem_workspace_size(const cgdem_config* cfg, const cgdem_sample_params* sp,
+                         const int64_t* counts, size_t* bytes);
+
+/* ---------------------------------------------------------------------
+ * Context.
+ * ------------------------------------------------------------------- */
+
+/* Create a context over a caller-owned device workspace of `bytes` bytes
+ * (256-byte aligned, at least cgdem_workspace_size).  The workspace must
+ * outlive the context.  sp has cfg->n_samples entries. */
+int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const int64_t* counts,
+                 void* workspace, size_t bytes, cgdem_ctx** out);
+void cgdem_destroy(cgdem_ctx* ctx);
+const char* cgdem_last_error(const cgdem_ctx* ctx);
+/* Returns the latched device status (and clears nothing). Synchronises stream. */
+int cgdem_status_sync(cgdem_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------------
+ * The method (Sec. 2), one verb per step of the path.
+ * ------------------------------------------------------------------- */
+
+/* Copy the initial state from HOST arrays in id order: x, v, w [N,3] and
+ * grain radii R [N] (N = sum of counts).  Forces, torques and all contact
+ * history are reset to zero.  If bond_touching != 0, every pair with
+ * d^2 < (Ri+Rj)^2 starts bonded (modified JKR, Sec. 2.3).  The porosity is
+ * computed and the contact list built.  Synchronises stream. */
+int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const double* w,
+                         const double* R, int bond_touching, void* stream);
+
+/* Prescribed superficial fluid velocity U_s per fluid cell (HOST array
+ * [Cf,3], all samples' cells in sample order, cells x fastest).  The drag
+ * (Eq. 8) uses the interstitial velocity U_s / n of the particle's cell.
+ * The simple locally averaged fluid of the coupled model stands in for the
+ * Navier-Stokes solve of Eq. 6.  Synchronises stream. */
+int cgdem_set_fluid_velocity(cgdem_ctx* ctx, const double* Us, void* stream);
+
+/* Re-sort particles by cell and rebuild the candidate list (pairs with
+ * d < Ri + Rj + skin), carrying tangential history and bond state by id pair. */
+int cgdem_build_contacts(cgdem_ctx* ctx, void* stream);
+
+/* Porosity: scatter the fixed-point volume quanta round(V_i 2^40 / V_cell)
+ * of every active particle into its fluid cell (Eq. 6-7 porosity n);
+ * n = clamp(1 - S 2^-40, n_min, 1).  Integer atomics: bit-reproducible. */
+int cgdem_couple_fluid(cgdem_ctx* ctx, void* stream);
+
+/* Forces and torques at the current state (contacts, walls, gravity,
+ * buoyancy, drag); advances the tangential history by dt and breaks bonds
+ * (Eq. 1-5, 8-13, 32-35).  Uses the candidate list of the last build. */
+int cgdem_compute_forces(cgdem_ctx* ctx, void* stream);
+
+/* Velocity Verlet halves: half = 0: v += dt/2 F/m, w += dt/2 T/I, x += dt v
+ * (wrapped into a periodic box); half = 1: v += dt/2 F/m, w += dt/2 T/I,
+ * then particles below z < -2R in a cylinder leave through the outlet. */
+int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream);
+
+/* nsteps full steps (half kick, drift, porosity every couple_every steps,
+ * candidate-list rebuild when the skin may be exceeded, forces, half kick,
+ * outlet), enqueued as CUDA graphs with no host round trip.  Needs forces
+ * consistent with the state (after init or compute_forces). */
+int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Readback (HOST arrays, id order).  Synchronise stream.
+ * ------------------------------------------------------------------- */
+
+/* Any pointer may be NULL.  Arrays are [N,3]. */
+int cgdem_get_state(cgdem_ctx* ctx, double* x, double* v, double* w, double* F, double* T,
+                    void* stream);
+
+/* Active particle contacts (those that applied a force at the last force
+ * evaluation), as id pairs id_i < id_j sorted lexicographically, with the
+ * bond flag.  *count receives the number; at most cap are written. */
+int cgdem_get_contacts(cgdem_ctx* ctx, int32_t* id_i, int32_t* id_j, uint8_t* bonded,
+                       int64_t cap, int64_t* count, void* stream);
+
+/* Porosity cell sums S (uint64 quanta) of all samples' fluid cells, sample
+ * after sample; cap = room in cell_sums. */
+int cgdem_get_voidfrac(cgdem_ctx* ctx, uint64_t* cell_sums, int64_t cap, void* stream);
+
+/* Per sample, 8 doubles: translational KE, rotational KE, momentum x,y,z,
+ * produced (outlet) mass, active particles, bonded contacts. */
+int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream);
+
+/* Step at which each particle left through the outlet (-1 if it did not). */
+int cgdem_get_removed_step(cgdem_ctx* ctx, int32_t* removed_step, void* stream);
+
+/* Steps completed, candidate-list rebuilds done, the largest number of
+ * candidates any particle had at the last rebuild, and the total number of
+ * candidate entries at the last rebuild. */
+int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_t* max_candidates,
+                       int64_t* total_candidates, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Instrumentation.
+ * ------------------------------------------------------------------- */
+
+/* Same work as cgdem_step(ctx, nsteps, stream) but launched kernel by kernel
+ * with CUDA events around the fused force/integrate kernel and around the
+ * candidate-list rebuild sequence of every step.  out (5 doubles):
+ * mean force-kernel time per step [ms], total rebuild-sequence time [ms],
+ * rebuilds done, total time [ms], steps timed.  Synchronises stream. */
+int cgdem_profile_step(cgdem_ctx* ctx, int64_t nsteps, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGDEM_H */

@@ -412,6 +412,7 @@ struct ora_sim {
     int64_t nrec;
     uint64_t* vf;
     double* Us;
+    double* Fscale; /* per particle: sum of the magnitudes of every force term */
     int64_t ncell_f;
     int64_t step;
     double produced;
@@ -443,6 +444,7 @@ ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const doubl
     s->active = (uint8_t*)calloc(n3, 1);
     s->removed_step = (int64_t*)calloc(n3, sizeof(int64_t));
     s->wall_xi = (double*)calloc(n3 * 3, sizeof(double));
+    s->Fscale = (double*)calloc(n3, sizeof(double));
     if (n > 0) {
         memcpy(s->x, x, sizeof(double) * 3 * n);
         memcpy(s->v, v, sizeof(double) * 3 * n);
@@ -466,7 +468,7 @@ void ora_destroy(ora_sim* s) {
     if (!s) return;
     free(s->x); free(s->v); free(s->w); free(s->F); free(s->T);
     free(s->R); free(s->m); free(s->I); free(s->active); free(s->removed_step);
-    free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us);
+    free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us); free(s->Fscale);
     free(s);
 }
 
@@ -714,6 +716,7 @@ int ora_compute_forces(ora_sim* s) {
     int64_t n = s->n;
     memset(s->F, 0, sizeof(double) * 3 * (size_t)n);
     memset(s->T, 0, sizeof(double) * 3 * (size_t)n);
+    memset(s->Fscale, 0, sizeof(double) * (size_t)n);
 
     /* candidates: touching pairs plus surviving bonded records */
     pairlist l = {0};
@@ -747,6 +750,8 @@ int ora_compute_forces(ora_sim* s) {
             s->T[3 * i + c] += Ti[c];
             s->T[3 * j + c] += Tj[c];
         }
+        s->Fscale[i] += sqrt(dot(Fi, Fi));
+        s->Fscale[j] += sqrt(dot(Fi, Fi));
         nrec[nn++] = r;
     }
     free(pr);
@@ -761,7 +766,13 @@ int ora_compute_forces(ora_sim* s) {
         if (!s->active[i]) continue;
         double* F = &s->F[3 * i];
         double* T = &s->T[3 * i];
-        if (p->kind == 1) wall_forces(s, i, F, T);
+        if (p->kind == 1) {
+            double Fw[3] = {0, 0, 0};
+            wall_forces(s, i, Fw, T);
+            for (int c = 0; c < 3; ++c) F[c] += Fw[c];
+            s->Fscale[i] += sqrt(dot(Fw, Fw));
+        }
+        s->Fscale[i] += s->m[i] * sqrt(dot(p->g, p->g));
         double V = sphere_volume(s->R[i]);
         for (int c = 0; c < 3; ++c) {
             F[c] += s->m[i] * p->g[c];                        /* F_g */
@@ -774,8 +785,14 @@ int ora_compute_forces(ora_sim* s) {
             double fd[3];
             ora_drag(p->rho_f, p->mu_f, 2.0 * s->R[i], u, &s->v[3 * i], nc, fd);
             for (int c = 0; c < 3; ++c) F[c] += fd[c];
+            s->Fscale[i] += sqrt(dot(fd, fd));
         }
     }
+    return 0;
+}
+
+int ora_get_force_scale(const ora_sim* s, double* scale) {
+    memcpy(scale, s->Fscale, sizeof(double) * (size_t)s->n);
     return 0;
 }
 

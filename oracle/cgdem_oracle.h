@@ -103,6 +103,9 @@ int ora_get_voidfrac(const ora_sim* s, uint64_t* cell_sums);
 /* KE_trans, KE_rot, Px, Py, Pz, produced mass, n_active, n_bonds */
 int ora_get_diagnostics(const ora_sim* s, double out[8]);
 int ora_get_removed_step(const ora_sim* s, int64_t* removed_step);
+/* Per particle, the sum of the magnitudes of all force terms of the last
+ * force evaluation (scale for normwise comparisons). */
+int ora_get_force_scale(const ora_sim* s, double* scale);
 /* Brute force O(N^2) list of pairs with d^2 < (Ri+Rj+skin)^2 (minimum image). */
 int64_t ora_pairs_bruteforce(const ora_params* p, int64_t n, const double* x, const double* R,
                              double skin, int32_t* pi, int32_t* pj, int64_t cap);

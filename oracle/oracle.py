@@ -61,6 +61,7 @@ def lib():
             ("ora_get_voidfrac", i, [vp, vp]),
             ("ora_get_diagnostics", i, [vp, pd]),
             ("ora_get_removed_step", i, [vp, vp]),
+            ("ora_get_force_scale", i, [vp, vp]),
             ("ora_pairs_bruteforce", i64, [vp, i64, pd, pd, d, vp, vp, i64]),
             ("ora_voidfrac", i, [vp, i64, pd, pd, vp]),
         ]:
@@ -234,6 +235,11 @@ class Sim:
         out = np.zeros(8)
         lib().ora_get_diagnostics(self.h, _pd(out))
         return dict(zip(["ke", "ke_rot", "px", "py", "pz", "produced_mass", "n_active", "n_bonds"], out))
+
+    def force_scale(self):
+        out = np.zeros(self.n)
+        lib().ora_get_force_scale(self.h, out.ctypes.data)
+        return out
 
     def removed_step(self):
         out = np.zeros(self.n, np.int64)

@@ -1,0 +1,313 @@
+"""Python binding of the C ABI in include/cgdem.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/libcgdem.so``;
+this module only converts arguments.  PyTorch supplies the device workspace
+and the stream.  There is no CPU fallback: if the library is missing or no
+GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcgdem.so")
+
+CGDEM_OK = 0
+CGDEM_E_INVALID = -1
+CGDEM_E_CAPACITY = -2
+CGDEM_E_CUDA = -3
+CGDEM_E_NONFINITE = -4
+CGDEM_E_STATE = -6
+FP64, MIXED = 0, 1
+PERIODIC_BOX, CYLINDER = 0, 1
+CG_NONE, CG_SSW, CG_SSP = 0, 1, 2
+
+# every symbol that include/cgdem.h declares
+EXPORTS = [
+    "cgdem_rayleigh_dt", "cgdem_cg_scale_diameters", "cgdem_workspace_size", "cgdem_create",
+    "cgdem_destroy", "cgdem_last_error", "cgdem_status_sync", "cgdem_init_particles",
+    "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
+    "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
+    "cgdem_get_contacts", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
+    "cgdem_get_counters", "cgdem_profile_step",
+]
+
+
+class CgdemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cgdem error {code}: {msg}")
+        self.code = code
+
+
+class SampleParams(C.Structure):
+    _fields_ = [
+        ("rho", C.c_double), ("E", C.c_double), ("nu", C.c_double), ("e", C.c_double),
+        ("mu", C.c_double), ("gamma", C.c_double),
+        ("k_cg", C.c_double), ("cg_scheme", C.c_int),
+        ("rho_f", C.c_double), ("mu_f", C.c_double),
+        ("use_drag", C.c_int), ("use_buoyancy", C.c_int),
+        ("kind", C.c_int), ("L", C.c_double * 3), ("Rc", C.c_double), ("H", C.c_double),
+        ("r_out", C.c_double), ("g", C.c_double * 3), ("dt", C.c_double),
+        ("coulomb_mode", C.c_int),
+        ("nf", C.c_int * 3), ("f_lo", C.c_double * 3), ("hf", C.c_double * 3),
+        ("inv_hf", C.c_double * 3), ("V_cell", C.c_double), ("n_min", C.c_double),
+        ("vf_mode", C.c_int), ("couple_every", C.c_int), ("skin", C.c_double),
+        ("r_max", C.c_double),
+    ]
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int), ("n_samples", C.c_int), ("max_neighbors", C.c_int),
+        ("block_size", C.c_int), ("cell_scale", C.c_double), ("steps_per_graph", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcgdem.so (build it first with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, i, i64, d = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "cgdem_rayleigh_dt": (d, [d, d, d, d]),
+            "cgdem_cg_scale_diameters": (i, [vp, i64, d, i, vp, vp]),
+            "cgdem_workspace_size": (i, [vp, vp, vp, vp]),
+            "cgdem_create": (i, [vp, vp, vp, vp, C.c_size_t, vp]),
+            "cgdem_destroy": (None, [vp]),
+            "cgdem_last_error": (C.c_char_p, [vp]),
+            "cgdem_status_sync": (i, [vp, vp]),
+            "cgdem_init_particles": (i, [vp, vp, vp, vp, vp, i, vp]),
+            "cgdem_set_fluid_velocity": (i, [vp, vp, vp]),
+            "cgdem_build_contacts": (i, [vp, vp]),
+            "cgdem_couple_fluid": (i, [vp, vp]),
+            "cgdem_compute_forces": (i, [vp, vp]),
+            "cgdem_integrate": (i, [vp, i, vp]),
+            "cgdem_step": (i, [vp, i64, vp]),
+            "cgdem_get_state": (i, [vp, vp, vp, vp, vp, vp, vp]),
+            "cgdem_get_contacts": (i, [vp, vp, vp, vp, i64, vp, vp]),
+            "cgdem_get_voidfrac": (i, [vp, vp, i64, vp]),
+            "cgdem_get_diagnostics": (i, [vp, vp, i64, vp]),
+            "cgdem_get_removed_step": (i, [vp, vp, vp]),
+            "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
+            "cgdem_profile_step": (i, [vp, i64, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data if a is not None else None
+
+
+# ---- host-only helpers ----
+
+def cgdem_rayleigh_dt(Rbar, rho, E, nu):
+    return lib().cgdem_rayleigh_dt(Rbar, rho, E, nu)
+
+
+def cgdem_cg_scale_diameters(d_fine, k, scheme):
+    d_fine = np.ascontiguousarray(d_fine, dtype=np.float64)
+    out = np.zeros(max(len(d_fine), 1))
+    n = C.c_int64(0)
+    r = lib().cgdem_cg_scale_diameters(_ptr(d_fine), len(d_fine), float(k), int(scheme), _ptr(out),
+                                       C.byref(n))
+    if r:
+        raise CgdemError(r, "cg_scale_diameters")
+    return out[: n.value].copy()
+
+
+@dataclass
+class Sample:
+    """One sample handed to the library: grain-level radii and positions,
+    fine-scale material, coarse-graining factor and scheme."""
+    x: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    R: np.ndarray
+    params: SampleParams
+    Us: np.ndarray
+
+
+def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1,
+                  coulomb_mode=0, vf_mode=0, couple_every=1, n_min=0.2, r_max=None,
+                  gamma_fine=None) -> SampleParams:
+    """SampleParams from an inputs.Sample-like object (material at fine scale)."""
+    p = SampleParams()
+    m = s.material
+    p.rho, p.E, p.nu, p.e, p.mu = m["rho"], m["E"], m["nu"], m["e"], m["mu"]
+    p.gamma = m["gamma"] if gamma_fine is None else gamma_fine
+    p.k_cg, p.cg_scheme = float(k), int(scheme)
+    p.rho_f, p.mu_f = s.fluid["rho_f"], s.fluid["mu_f"]
+    p.use_drag, p.use_buoyancy = int(use_drag), int(use_buoyancy)
+    dom = s.domain
+    p.kind = int(dom["kind"])
+    for i in range(3):
+        p.L[i] = dom["L"][i]
+        p.g[i] = s.g[i]
+        p.nf[i] = s.grid.nf[i]
+        p.f_lo[i] = s.grid.lo[i]
+        p.hf[i] = s.grid.h[i]
+        p.inv_hf[i] = s.grid.inv_h[i]
+    p.Rc, p.H, p.r_out = dom["Rc"], dom["H"], dom["r_out"]
+    p.dt = float(dt)
+    p.coulomb_mode = int(coulomb_mode)
+    p.V_cell = s.grid.V_cell
+    p.n_min = n_min
+    p.vf_mode = int(vf_mode)
+    p.couple_every = int(couple_every)
+    p.skin = float(skin)
+    p.r_max = float(r_max if r_max is not None else np.max(s.R))
+    return p
+
+
+class Context:
+    """A library context over one or more samples on one GPU."""
+
+    def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
+                 cell_scale=1.0, steps_per_graph=32, device="cuda:0", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("cgdem needs a CUDA GPU")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n_samples = len(params)
+        self._params = (SampleParams * self.n_samples)(*params)
+        self.counts = np.ascontiguousarray(counts, dtype=np.int64)
+        self.N = int(self.counts.sum())
+        self.cfg = Config(precision, self.n_samples, max_neighbors, block_size, cell_scale,
+                          steps_per_graph)
+        nbytes = C.c_size_t(0)
+        r = lib().cgdem_workspace_size(C.byref(self.cfg), self._params, _ptr(self.counts),
+                                       C.byref(nbytes))
+        if r:
+            raise CgdemError(r, "workspace_size: invalid configuration")
+        self.workspace_bytes = nbytes.value
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
+                                         device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        h = C.c_void_p()
+        r = lib().cgdem_create(C.byref(self.cfg), self._params, _ptr(self.counts),
+                               C.c_void_p(aligned), self.workspace_bytes, C.byref(h))
+        if r:
+            raise CgdemError(r, "create failed")
+        self.h = h
+        self.stream = stream
+
+    def _s(self):
+        if self.stream is not None:
+            return C.c_void_p(self.stream)
+        return C.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check(self, r, what):
+        if r != CGDEM_OK:
+            msg = lib().cgdem_last_error(self.h)
+            raise CgdemError(r, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cgdem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- verbs ----
+    def init_particles(self, x, v, w, R, bond_touching=True):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)
+        R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
+        if len(R) != self.N:
+            raise ValueError("particle count mismatch")
+        self._check(lib().cgdem_init_particles(self.h, _ptr(x), _ptr(v), _ptr(w), _ptr(R),
+                                               int(bond_touching), self._s()), "init_particles")
+
+    def set_fluid_velocity(self, Us):
+        Us = np.ascontiguousarray(Us, dtype=np.float64).reshape(-1, 3)
+        self._check(lib().cgdem_set_fluid_velocity(self.h, _ptr(Us), self._s()), "set_fluid_velocity")
+
+    def build_contacts(self):
+        self._check(lib().cgdem_build_contacts(self.h, self._s()), "build_contacts")
+
+    def couple_fluid(self):
+        self._check(lib().cgdem_couple_fluid(self.h, self._s()), "couple_fluid")
+
+    def compute_forces(self):
+        self._check(lib().cgdem_compute_forces(self.h, self._s()), "compute_forces")
+
+    def integrate(self, half):
+        self._check(lib().cgdem_integrate(self.h, int(half), self._s()), "integrate")
+
+    def step(self, n=1):
+        self._check(lib().cgdem_step(self.h, int(n), self._s()), "step")
+
+    # ---- readback ----
+    def get_state(self):
+        out = [np.zeros((self.N, 3)) for _ in range(5)]
+        self._check(lib().cgdem_get_state(self.h, *[_ptr(a) for a in out], self._s()), "get_state")
+        return dict(zip(["x", "v", "w", "F", "T"], out))
+
+    def get_contacts(self):
+        n = C.c_int64(0)
+        self._check(lib().cgdem_get_contacts(self.h, None, None, None, 0, C.byref(n), self._s()),
+                    "get_contacts")
+        cap = max(n.value, 1)
+        i = np.zeros(cap, np.int32)
+        j = np.zeros(cap, np.int32)
+        b = np.zeros(cap, np.uint8)
+        self._check(lib().cgdem_get_contacts(self.h, _ptr(i), _ptr(j), _ptr(b), cap, C.byref(n),
+                                             self._s()), "get_contacts")
+        k = n.value
+        return i[:k], j[:k], b[:k]
+
+    def get_voidfrac(self, ncell):
+        out = np.zeros(ncell, np.uint64)
+        self._check(lib().cgdem_get_voidfrac(self.h, _ptr(out), ncell, self._s()), "get_voidfrac")
+        return out
+
+    def get_diagnostics(self):
+        out = np.zeros((self.n_samples, 8))
+        self._check(lib().cgdem_get_diagnostics(self.h, _ptr(out), out.size, self._s()),
+                    "get_diagnostics")
+        keys = ["ke", "ke_rot", "px", "py", "pz", "produced_mass", "n_active", "n_bonds"]
+        return [dict(zip(keys, row)) for row in out]
+
+    def get_removed_step(self):
+        out = np.zeros(self.N, np.int32)
+        self._check(lib().cgdem_get_removed_step(self.h, _ptr(out), self._s()), "get_removed_step")
+        return out
+
+    def counters(self):
+        s, r, m, t = C.c_int64(0), C.c_int64(0), C.c_int32(0), C.c_int64(0)
+        self._check(lib().cgdem_get_counters(self.h, C.byref(s), C.byref(r), C.byref(m), C.byref(t),
+                                             self._s()), "get_counters")
+        return dict(steps=s.value, rebuilds=r.value, max_candidates=m.value, total_candidates=t.value)
+
+    def profile_step(self, n):
+        out = np.zeros(5)
+        self._check(lib().cgdem_profile_step(self.h, int(n), _ptr(out), self._s()), "profile_step")
+        return dict(force_ms=out[0], rebuild_ms_total=out[1], rebuilds=int(out[2]), total_ms=out[3],
+                    steps=int(out[4]))
+
+    def status(self):
+        return lib().cgdem_status_sync(self.h, self._s())

@@ -1,0 +1,722 @@
+// api.cu -- host side of the C ABI declared in include/cgdem.h: parameter
+// derivation (coarse-graining rules, Sec. 2.4), workspace layout, the verbs
+// of the step and their CUDA-graph schedule.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cgdem_internal.cuh"
+
+namespace cgdem {
+void launch_forces(const Dev& d, int mode, int block, cudaStream_t s);
+void launch_rebuild(const Dev& d, cudaStream_t s);
+void launch_set_rebuild(const Dev& d, cudaStream_t s);
+void launch_bond_touching(const Dev& d, cudaStream_t s);
+void launch_couple(const Dev& d, cudaStream_t s);
+void launch_kick_drift(const Dev& d, int couple, cudaStream_t s);
+void launch_kick_final(const Dev& d, cudaStream_t s);
+void launch_cube_after_mid(const Dev& d, cudaStream_t s);
+void launch_init(const Dev& d, cudaStream_t s);
+void launch_gather_state(const Dev& d, cudaStream_t s);
+void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
+void launch_diag(const Dev& d, double* part, cudaStream_t s);
+}  // namespace cgdem
+
+using namespace cgdem;
+
+struct cgdem_ctx {
+  cgdem_config cfg;
+  std::vector<cgdem_sample_params> sp;
+  std::vector<SampleDev> sd;
+  std::vector<int64_t> counts;
+  Dev d;
+  double* diag_part = nullptr;
+  size_t contact_cap = 0;  // pairs that fit the collection buffer
+  bool any_cube = false;
+  bool initialised = false;
+  std::string err;
+  // CUDA graphs of steps_per_graph fused steps, keyed by stream
+  std::map<cudaStream_t, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr int DIAG_BLOCKS = 128;
+
+int fail(cgdem_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(cgdem_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, CGDEM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call); \
+  } while (0)
+
+// Layout of the workspace: a bump allocator with 256-byte alignment.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Derive the device constants of one sample (grain level).
+int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params& p,
+                  int64_t first, int64_t count, int cell_off, int fcell_off, SampleDev* out,
+                  int* ncells, int* nfcells) {
+  SampleDev s;
+  memset(&s, 0, sizeof s);
+  if (!(p.dt > 0) || !(p.E > 0) || !(p.rho > 0) || !(p.nu > -1 && p.nu < 0.5) ||
+      !(p.e > 0 && p.e <= 1) || !(p.mu >= 0) || !(p.gamma >= 0) || !(p.r_max > 0) ||
+      !(p.skin > 0) || p.couple_every < 1 || !(p.V_cell > 0) || !(p.n_min > 0 && p.n_min <= 1))
+    return fail(ctx, CGDEM_E_INVALID, "sample %lld: a material, time-step or grid parameter is out of range",
+                (long long)first);
+  for (int k = 0; k < 3; ++k)
+    if (p.nf[k] < 1 || !(p.inv_hf[k] > 0) || !(p.hf[k] > 0))
+      return fail(ctx, CGDEM_E_INVALID, "fluid grid dimensions must be positive");
+  double k_cg = (p.cg_scheme == CGDEM_CG_NONE) ? 1.0 : p.k_cg;
+  if (!(k_cg >= 1.0)) return fail(ctx, CGDEM_E_INVALID, "coarse-grain factor k must be >= 1");
+  // Eq. 24: gamma_g = k gamma_p; Eq. 19, 28, 34, 35: the rest unchanged.
+  s.gamma = k_cg * p.gamma;
+  s.rho = p.rho;
+  s.Es = p.E / (2.0 * (1.0 - p.nu * p.nu));  // Eq. 12 definitions, equal materials
+  {
+    double G = p.E / (2.0 * (1.0 + p.nu));
+    s.Gs = G / (2.0 * (2.0 - p.nu));  // Mindlin
+  }
+  {
+    double l = std::log(p.e);
+    s.beta = -l / std::sqrt(l * l + PI * PI);  // Eq. 33 with ln^2 e
+  }
+  s.mu = p.mu;
+  s.dt = p.dt;
+  s.half_dt = 0.5 * p.dt;
+  for (int k = 0; k < 3; ++k) s.g[k] = p.g[k];
+  s.rho_f = p.rho_f;
+  s.mu_f = p.mu_f;
+  s.use_drag = p.use_drag;
+  s.use_buoyancy = p.use_buoyancy;
+  s.kind = p.kind;
+  s.coulomb_mode = p.coulomb_mode;
+  for (int k = 0; k < 3; ++k) s.L[k] = p.L[k];
+  s.Rc = p.Rc;
+  s.H = p.H;
+  s.r_out = p.r_out;
+  const double reach = 2.0 * p.r_max + p.skin;  // largest candidate distance
+  // bonded pairs must stay candidates: |delta_C| of the largest pair < skin / 2
+  {
+    const double Rs = 0.5 * p.r_max;
+    const double dC = 0.5723571212766659 *
+                      std::cbrt(PI * PI * s.gamma * s.gamma * Rs / (s.Es * s.Es));
+    if (!(2.0 * dC < p.skin))
+      return fail(ctx, CGDEM_E_INVALID, "skin %.3g must exceed twice the bond-break separation %.3g",
+                  p.skin, dC);
+  }
+  if (p.kind == CGDEM_PERIODIC_BOX) {
+    if (!(p.L[0] > 0) || p.L[0] != p.L[1] || p.L[0] != p.L[2])
+      return fail(ctx, CGDEM_E_INVALID, "periodic samples must be cubes");
+    if (!(reach < 0.5 * p.L[0]))
+      return fail(ctx, CGDEM_E_INVALID, "periodic box too small for 2 r_max + skin");
+    s.dq = p.L[0] / 4294967296.0;  // 2^32 steps per period: wrap-around is the minimum image
+  } else if (p.kind == CGDEM_CYLINDER) {
+    if (!(p.Rc > 0) || !(p.H > 0) || !(p.r_out >= 0))
+      return fail(ctx, CGDEM_E_INVALID, "cylinder needs Rc > 0, H > 0, r_out >= 0");
+    int e = (int)std::ceil(std::log2(reach / 1073741824.0));  // reach < 2^30 steps
+    s.dq = std::ldexp(1.0, e);
+  } else {
+    return fail(ctx, CGDEM_E_INVALID, "unknown domain kind %d", p.kind);
+  }
+  s.inv_dq = 1.0 / s.dq;
+  s.skin_q = (int32_t)std::ceil(p.skin * s.inv_dq) + 8;
+  // search grid: cell edge >= reach
+  const double h = std::max(1.0, cfg->cell_scale) * reach;
+  double lo[3], ext[3];
+  if (p.kind == CGDEM_PERIODIC_BOX) {
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = 0.0;
+      ext[k] = p.L[k];
+    }
+  } else {
+    lo[0] = lo[1] = -p.Rc;
+    ext[0] = ext[1] = 2.0 * p.Rc;
+    lo[2] = -4.0 * p.r_max;
+    ext[2] = p.H + 4.0 * p.r_max;
+  }
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    int n = (int)std::floor(ext[k] / h);
+    if (n < 1) n = 1;
+    if (n > 1024) n = 1024;
+    s.nc[k] = n;
+    s.c_lo[k] = lo[k];
+    s.c_inv_h[k] = n / ext[k];
+    ncell *= n;
+  }
+  if (ncell > (1ll << 28)) return fail(ctx, CGDEM_E_INVALID, "search grid too large");
+  s.cell_off = cell_off;
+  *ncells = (int)ncell;
+  for (int k = 0; k < 3; ++k) {
+    s.nf[k] = p.nf[k];
+    s.f_lo[k] = p.f_lo[k];
+    s.inv_hf[k] = p.inv_hf[k];
+    s.hf[k] = p.hf[k];
+  }
+  s.fcell_off = fcell_off;
+  *nfcells = p.nf[0] * p.nf[1] * p.nf[2];
+  s.inv_q = 1099511627776.0 / p.V_cell;  // 2^40 / V_cell
+  s.n_min = p.n_min;
+  s.vf_mode = p.vf_mode;
+  s.couple_every = p.couple_every;
+  s.skin = p.skin;
+  s.rebuild_disp = p.skin - 16.0 * s.dq;
+  s.first = first;
+  s.count = count;
+  s.Es_f = (float)s.Es;
+  s.Gs_f = (float)s.Gs;
+  s.beta_f = (float)s.beta;
+  s.mu_f32 = (float)s.mu;
+  s.gamma_f = (float)s.gamma;
+  s.dt_f = (float)s.dt;
+  s.dq_f = (float)s.dq;
+  s.rho_f32 = (float)s.rho_f;
+  s.muf_f32 = (float)s.mu_f;
+  s.n_min_f = (float)s.n_min;
+  for (int k = 0; k < 3; ++k) s.g_f[k] = (float)s.g[k];
+  s.rho_s_f = (float)s.rho;
+  *out = s;
+  return CGDEM_OK;
+}
+
+// Compute (and, with a base pointer, assign) the workspace layout.
+int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* sp,
+           const int64_t* counts, char* base, size_t* bytes, std::vector<SampleDev>* sd, Dev* dv,
+           double** diag_part, size_t* contact_cap, bool* any_cube) {
+  if (!cfg || !sp || !counts || cfg->n_samples < 1)
+    return fail(ctx, CGDEM_E_INVALID, "null argument or n_samples < 1");
+  if (cfg->precision != CGDEM_FP64 && cfg->precision != CGDEM_MIXED)
+    return fail(ctx, CGDEM_E_INVALID, "unknown precision");
+  const int S = cfg->n_samples;
+  int64_t N = 0;
+  int C = 0, Cf = 0;
+  bool cyl = false, cube = false;
+  sd->resize(S);
+  for (int s = 0; s < S; ++s) {
+    if (counts[s] < 0) return fail(ctx, CGDEM_E_INVALID, "negative particle count");
+    if (sp[s].couple_every != sp[0].couple_every)
+      return fail(ctx, CGDEM_E_INVALID, "couple_every must be equal in all samples");
+    int nc = 0, nfc = 0;
+    int r = derive_sample(ctx, cfg, sp[s], N, counts[s], C, Cf, &(*sd)[s], &nc, &nfc);
+    if (r) return r;
+    N += counts[s];
+    C += nc;
+    Cf += nfc;
+    cyl |= sp[s].kind == CGDEM_CYLINDER;
+    cube |= sp[s].vf_mode == 1;
+  }
+  if (N >= (1ll << 30)) return fail(ctx, CGDEM_E_INVALID, "too many particles");
+  const int cap = cfg->max_neighbors > 0 ? cfg->max_neighbors : 64;
+  const int Npad = (int)(((N + 63) / 64) * 64 + 64);
+  const bool mixed = cfg->precision == CGDEM_MIXED;
+  Carver cv{base};
+  Dev d;
+  memset(&d, 0, sizeof d);
+  for (int b = 0; b < 2; ++b) {
+    d.pos[b] = cv.take<double4>(Npad);
+    d.vel[b] = cv.take<double4>(Npad);
+    d.omg[b] = cv.take<double4>(Npad);
+    d.posq[b] = cv.take<int4>(Npad);
+    d.velf[b] = cv.take<float4>(Npad);
+    d.omgf[b] = cv.take<float4>(Npad);
+    d.id[b] = cv.take<int>(Npad);
+    d.sample[b] = cv.take<int>(Npad);
+    d.fcell[b] = cv.take<int>(Npad);
+    d.vq[b] = cv.take<unsigned long long>(Npad);
+    if (cyl) {
+      if (mixed) d.wallhf[b] = cv.take<float4>(3 * (size_t)Npad);
+      else d.wallh[b] = cv.take<double4>(3 * (size_t)Npad);
+    }
+    d.rec[b] = mixed ? (void*)cv.take<RecF>((size_t)cap * Npad) : (void*)cv.take<RecD>((size_t)cap * Npad);
+    d.cnt[b] = cv.take<uint32_t>(Npad);
+  }
+  d.F = cv.take<double4>(Npad);
+  d.T = cv.take<double4>(Npad);
+  d.cell_count = cv.take<uint32_t>((size_t)C + 2);
+  d.cell_start = cv.take<uint32_t>((size_t)C + 2);
+  d.pcell = cv.take<uint32_t>(Npad);
+  d.pslot = cv.take<uint32_t>(Npad);
+  d.perm_tmp = cv.take<uint32_t>(Npad);
+  d.perm = cv.take<uint32_t>(Npad);
+  d.inv_perm = cv.take<uint32_t>(Npad);
+  for (int b = 0; b < 3; ++b) d.vf[b] = cv.take<unsigned long long>((size_t)Cf + 1);
+  d.Us = cv.take<double4>((size_t)Cf + 1);
+  d.Usf = cv.take<float4>((size_t)Cf + 1);
+  d.removed_step = cv.take<int>(Npad);
+  d.disp = cv.take<double>(S);
+  d.vmax2 = cv.take<unsigned long long>(S);
+  d.diag = cv.take<double>(8 * (size_t)S);
+  d.staging = cv.take<double>(16 * (size_t)Npad);
+  d.contact_n = cv.take<unsigned long long>(1);
+  d.sp = cv.take<SampleDev>(S);
+  d.ctl = cv.take<Ctl>(1);
+  *diag_part = cv.take<double>((size_t)DIAG_BLOCKS * 8 * S);
+  // collected contacts reuse the spare record buffer
+  const size_t rec_bytes = (size_t)cap * Npad * (mixed ? sizeof(RecF) : sizeof(RecD));
+  *contact_cap = rec_bytes / 8;
+  d.N = (int)N;
+  d.Npad = Npad;
+  d.cap = cap;
+  d.n_samples = S;
+  d.C_total = C;
+  d.Cf_total = Cf;
+  d.mixed = mixed ? 1 : 0;
+  *bytes = cv.off + 256;
+  *dv = d;
+  *any_cube = cube;
+  return CGDEM_OK;
+}
+
+cudaStream_t st(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_status(cgdem_ctx* ctx, cudaStream_t s) {
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, ctx->d.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c.status & ST_CAPACITY)
+    return fail(ctx, CGDEM_E_CAPACITY, "a particle had %d candidates; max_neighbors is %d", c.max_cand,
+                ctx->d.cap);
+  if (c.status & ST_BOND_LOST)
+    return fail(ctx, CGDEM_E_STATE, "a bonded pair left the candidate list (skin too small)");
+  if (c.status & ST_NONFINITE) return fail(ctx, CGDEM_E_NONFINITE, "a force became NaN or Inf");
+  return CGDEM_OK;
+}
+
+int ready(cgdem_ctx* ctx) {
+  if (!ctx) return CGDEM_E_INVALID;
+  if (!ctx->initialised) return fail(ctx, CGDEM_E_STATE, "cgdem_init_particles has not been called");
+  return CGDEM_OK;
+}
+
+// One fused step (rebuild-if-flagged, forces, kick, drift, porosity).
+void enqueue_mid_step(cgdem_ctx* ctx, cudaStream_t s) {
+  launch_rebuild(ctx->d, s);
+  launch_forces(ctx->d, 1, ctx->cfg.block_size, s);
+  if (ctx->any_cube) launch_cube_after_mid(ctx->d, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+double cgdem_rayleigh_dt(double Rbar, double rho, double E, double nu) {
+  // Eq. 37-38, shear modulus G = E / (2 (1 + nu))
+  const double G = E / (2.0 * (1.0 + nu));
+  const double beta = 0.8766 + 0.163 * nu;
+  return PI * Rbar / beta * std::sqrt(rho / G);
+}
+
+int cgdem_cg_scale_diameters(const double* d_fine, int64_t n_fine, double k, int scheme,
+                             double* d_out, int64_t* n_out) {
+  if (!d_fine || !d_out || !n_out || n_fine < 0 || !(k >= 1.0)) return CGDEM_E_INVALID;
+  if (scheme == CGDEM_CG_NONE || k == 1.0) {
+    std::memcpy(d_out, d_fine, sizeof(double) * (size_t)n_fine);
+    *n_out = n_fine;
+    return CGDEM_OK;
+  }
+  // Eq. 15-16: n_CG = k^3 fine particles per grain
+  const int64_t ng = (int64_t)std::floor((double)n_fine / (k * k * k) + 1e-9);
+  if (scheme == CGDEM_CG_SSW) {  // Eq. 14 per particle: PSD shape kept
+    for (int64_t i = 0; i < ng; ++i) d_out[i] = k * d_fine[i];
+  } else if (scheme == CGDEM_CG_SSP) {  // one size: k times the volume-mean diameter
+    long double acc = 0;
+    for (int64_t i = 0; i < n_fine; ++i) acc += (long double)d_fine[i] * d_fine[i] * d_fine[i];
+    const double dbar = std::cbrt((double)(acc / (long double)n_fine));
+    for (int64_t i = 0; i < ng; ++i) d_out[i] = k * dbar;
+  } else {
+    return CGDEM_E_INVALID;
+  }
+  *n_out = ng;
+  return CGDEM_OK;
+}
+
+int cgdem_workspace_size(const cgdem_config* cfg, const cgdem_sample_params* sp,
+                         const int64_t* counts, size_t* bytes) {
+  if (!bytes) return CGDEM_E_INVALID;
+  std::vector<SampleDev> sd;
+  Dev d;
+  double* dp;
+  size_t cc;
+  bool cube;
+  return layout(nullptr, cfg, sp, counts, nullptr, bytes, &sd, &d, &dp, &cc, &cube);
+}
+
+int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const int64_t* counts,
+                 void* workspace, size_t bytes, cgdem_ctx** out) {
+  if (!out) return CGDEM_E_INVALID;
+  *out = nullptr;
+  cgdem_ctx* ctx = new cgdem_ctx();
+  size_t need = 0;
+  int r = layout(ctx, cfg, sp, counts, nullptr, &need, &ctx->sd, &ctx->d, &ctx->diag_part,
+                 &ctx->contact_cap, &ctx->any_cube);
+  if (r) {
+    // keep the message: callers read it through a temporary context
+    static thread_local std::string last;
+    last = ctx->err;
+    delete ctx;
+    fprintf(stderr, "cgdem_create: %s\n", last.c_str());
+    return r;
+  }
+  if (!workspace || bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+    fprintf(stderr, "cgdem_create: workspace must be 256-byte aligned and >= %zu bytes\n", need);
+    delete ctx;
+    return CGDEM_E_INVALID;
+  }
+  layout(ctx, cfg, sp, counts, reinterpret_cast<char*>(workspace), &need, &ctx->sd, &ctx->d,
+         &ctx->diag_part, &ctx->contact_cap, &ctx->any_cube);
+  ctx->cfg = *cfg;
+  if (ctx->cfg.block_size <= 0) ctx->cfg.block_size = 128;
+  if (ctx->cfg.block_size > 256 || ctx->cfg.block_size % 32) {
+    delete ctx;
+    return CGDEM_E_INVALID;
+  }
+  if (ctx->cfg.steps_per_graph <= 0) ctx->cfg.steps_per_graph = 32;
+  ctx->sp.assign(sp, sp + cfg->n_samples);
+  ctx->counts.assign(counts, counts + cfg->n_samples);
+  cudaError_t e = cudaMemcpy(ctx->d.sp, ctx->sd.data(), sizeof(SampleDev) * ctx->sd.size(),
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "cgdem_create: %s\n", cudaGetErrorString(e));
+    delete ctx;
+    return CGDEM_E_CUDA;
+  }
+  // fluid velocity starts at zero
+  cudaMemset(ctx->d.Us, 0, sizeof(double4) * ((size_t)ctx->d.Cf_total + 1));
+  cudaMemset(ctx->d.Usf, 0, sizeof(float4) * ((size_t)ctx->d.Cf_total + 1));
+  *out = ctx;
+  return CGDEM_OK;
+}
+
+void cgdem_destroy(cgdem_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  delete ctx;
+}
+
+const char* cgdem_last_error(const cgdem_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int cgdem_status_sync(cgdem_ctx* ctx, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  return check_status(ctx, st(stream));
+}
+
+int cgdem_set_fluid_velocity(cgdem_ctx* ctx, const double* Us, void* stream) {
+  if (!ctx || !Us) return CGDEM_E_INVALID;
+  const int Cf = ctx->d.Cf_total;
+  std::vector<double4> a((size_t)Cf + 1);
+  std::vector<float4> b((size_t)Cf + 1);
+  for (int c = 0; c < Cf; ++c) {
+    a[c] = make_double4(Us[3 * c], Us[3 * c + 1], Us[3 * c + 2], 0.0);
+    b[c] = make_float4((float)Us[3 * c], (float)Us[3 * c + 1], (float)Us[3 * c + 2], 0.f);
+  }
+  a[Cf] = make_double4(0, 0, 0, 0);
+  b[Cf] = make_float4(0, 0, 0, 0);
+  cudaStream_t s = st(stream);
+  CK(cudaMemcpyAsync(ctx->d.Us, a.data(), sizeof(double4) * a.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d.Usf, b.data(), sizeof(float4) * b.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return CGDEM_OK;
+}
+
+int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const double* w,
+                         const double* R, int bond_touching, void* stream) {
+  if (!ctx || (!x && ctx->d.N) || (!v && ctx->d.N) || (!w && ctx->d.N) || (!R && ctx->d.N))
+    return CGDEM_E_INVALID;
+  const size_t N = ctx->d.N;
+  for (int s = 0; s < ctx->d.n_samples; ++s) {
+    const SampleDev& S = ctx->sd[s];
+    for (int64_t i = S.first; i < S.first + S.count; ++i) {
+      if (!(R[i] > 0) || !(R[i] <= ctx->sp[s].r_max))
+        return fail(ctx, CGDEM_E_INVALID, "radius of particle %lld outside (0, r_max]", (long long)i);
+      if (!std::isfinite(x[3 * i] + x[3 * i + 1] + x[3 * i + 2] + v[3 * i] + v[3 * i + 1] +
+                         v[3 * i + 2] + w[3 * i] + w[3 * i + 1] + w[3 * i + 2]))
+        return fail(ctx, CGDEM_E_NONFINITE, "non-finite state of particle %lld", (long long)i);
+    }
+  }
+  cudaStream_t s = st(stream);
+  double* stg = ctx->d.staging;
+  if (N) {
+    CK(cudaMemcpyAsync(stg, x, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(stg + 3 * N, v, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(stg + 6 * N, w, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(stg + 9 * N, R, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  }
+  launch_init(ctx->d, s);
+  for (int b = 0; b < 3; ++b)
+    CK(cudaMemsetAsync(ctx->d.vf[b], 0, sizeof(unsigned long long) * ((size_t)ctx->d.Cf_total + 1), s));
+  CK(cudaMemsetAsync(ctx->d.cell_count, 0, sizeof(uint32_t) * ((size_t)ctx->d.C_total + 2), s));
+  launch_set_rebuild(ctx->d, s);
+  launch_rebuild(ctx->d, s);
+  if (bond_touching) launch_bond_touching(ctx->d, s);
+  launch_couple(ctx->d, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  ctx->initialised = true;
+  return check_status(ctx, s);
+}
+
+int cgdem_build_contacts(cgdem_ctx* ctx, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  cudaStream_t s = st(stream);
+  launch_set_rebuild(ctx->d, s);
+  launch_rebuild(ctx->d, s);
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_couple_fluid(cgdem_ctx* ctx, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  launch_couple(ctx->d, st(stream));
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_compute_forces(cgdem_ctx* ctx, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  launch_forces(ctx->d, 0, ctx->cfg.block_size, st(stream));
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (half == 0) launch_kick_drift(ctx->d, 0, st(stream));
+  else if (half == 1) launch_kick_final(ctx->d, st(stream));
+  else return fail(ctx, CGDEM_E_INVALID, "half must be 0 or 1");
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (nsteps < 0) return fail(ctx, CGDEM_E_INVALID, "nsteps < 0");
+  if (nsteps == 0 || ctx->d.N == 0) return CGDEM_OK;
+  cudaStream_t s = st(stream);
+  // half kick + drift from the full-step state, porosity of the new positions
+  launch_kick_drift(ctx->d, 1, s);
+  int64_t body = nsteps - 1;
+  const int U = ctx->cfg.steps_per_graph;
+  if (body >= U && U > 1) {
+    auto it = ctx->graphs.find(s);
+    cudaGraphExec_t exec = nullptr;
+    if (it == ctx->graphs.end()) {
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      for (int i = 0; i < U; ++i) enqueue_mid_step(ctx, cs);
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(ctx, e, "graph capture");
+      }
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+      ctx->graphs[s] = exec;
+    } else {
+      exec = it->second;
+    }
+    while (body >= U) {
+      CK(cudaGraphLaunch(exec, s));
+      body -= U;
+    }
+  }
+  for (int64_t i = 0; i < body; ++i) enqueue_mid_step(ctx, s);
+  // last step ends on the full-step state (forces, v(n), w(n))
+  launch_rebuild(ctx->d, s);
+  launch_forces(ctx->d, 2, ctx->cfg.block_size, s);
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_get_state(cgdem_ctx* ctx, double* x, double* v, double* w, double* F, double* T,
+                    void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  cudaStream_t s = st(stream);
+  const size_t N = ctx->d.N;
+  launch_gather_state(ctx->d, s);
+  double* outs[5] = {x, v, w, F, T};
+  for (int k = 0; k < 5; ++k)
+    if (outs[k] && N)
+      CK(cudaMemcpyAsync(outs[k], ctx->d.staging + 3 * N * k, sizeof(double) * 3 * N,
+                         cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
+}
+
+int cgdem_get_contacts(cgdem_ctx* ctx, int32_t* id_i, int32_t* id_j, uint8_t* bonded, int64_t cap,
+                       int64_t* count, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!count) return CGDEM_E_INVALID;
+  cudaStream_t s = st(stream);
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, ctx->d.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  uint32_t* buf = reinterpret_cast<uint32_t*>(ctx->d.rec[c.rec_cur ^ 1]);
+  launch_collect_contacts(ctx->d, buf, ctx->contact_cap, s);
+  unsigned long long n = 0;
+  CK(cudaMemcpyAsync(&n, ctx->d.contact_n, sizeof n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n > ctx->contact_cap) return fail(ctx, CGDEM_E_CAPACITY, "too many contacts to collect");
+  std::vector<uint32_t> h(2 * n);
+  if (n) CK(cudaMemcpyAsync(h.data(), buf, sizeof(uint32_t) * 2 * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<uint64_t> key(n);
+  for (size_t i = 0; i < n; ++i)
+    key[i] = ((uint64_t)h[2 * i] << 32) | (uint64_t)h[2 * i + 1];
+  std::sort(key.begin(), key.end(), [](uint64_t a, uint64_t b) {
+    uint64_t ka = (a & 0xffffffff00000000ull) | (a & 0x7fffffffull);
+    uint64_t kb = (b & 0xffffffff00000000ull) | (b & 0x7fffffffull);
+    return ka < kb;
+  });
+  *count = (int64_t)n;
+  const size_t m = std::min<size_t>(n, cap > 0 ? (size_t)cap : 0);
+  for (size_t i = 0; i < m; ++i) {
+    if (id_i) id_i[i] = (int32_t)(key[i] >> 32);
+    if (id_j) id_j[i] = (int32_t)(key[i] & 0x7fffffffull);
+    if (bonded) bonded[i] = (key[i] & 0x80000000ull) ? 1 : 0;
+  }
+  return check_status(ctx, s);
+}
+
+int cgdem_get_voidfrac(cgdem_ctx* ctx, uint64_t* cell_sums, int64_t cap, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!cell_sums || cap < ctx->d.Cf_total) return CGDEM_E_INVALID;
+  cudaStream_t s = st(stream);
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, ctx->d.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpyAsync(cell_sums, ctx->d.vf[c.vf_cur], sizeof(uint64_t) * ctx->d.Cf_total,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
+}
+
+int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!out || cap < 8 * ctx->d.n_samples) return CGDEM_E_INVALID;
+  cudaStream_t s = st(stream);
+  launch_diag(ctx->d, ctx->diag_part, s);
+  CK(cudaMemcpyAsync(out, ctx->d.diag, sizeof(double) * 8 * ctx->d.n_samples,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
+}
+
+int cgdem_get_removed_step(cgdem_ctx* ctx, int32_t* removed_step, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!removed_step) return CGDEM_E_INVALID;
+  cudaStream_t s = st(stream);
+  if (ctx->d.N)
+    CK(cudaMemcpyAsync(removed_step, ctx->d.removed_step, sizeof(int) * ctx->d.N,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
+}
+
+int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_t* max_candidates,
+                       int64_t* total_candidates, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  cudaStream_t s = st(stream);
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, ctx->d.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (steps) *steps = c.step;
+  if (rebuilds) *rebuilds = c.rebuilds;
+  if (max_candidates) *max_candidates = c.max_cand;
+  if (total_candidates) *total_candidates = c.cand_total;
+  return CGDEM_OK;
+}
+
+int cgdem_profile_step(cgdem_ctx* ctx, int64_t nsteps, double* out, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!out || nsteps < 2) return fail(ctx, CGDEM_E_INVALID, "profile needs nsteps >= 2 and out");
+  cudaStream_t s = st(stream);
+  Ctl c0;
+  CK(cudaMemcpyAsync(&c0, ctx->d.ctl, sizeof c0, cudaMemcpyDeviceToHost, s));
+  const int64_t body = nsteps - 1;
+  std::vector<cudaEvent_t> ev(3 * body + 2);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], s));
+  launch_kick_drift(ctx->d, 1, s);
+  for (int64_t i = 0; i < body; ++i) {
+    CK(cudaEventRecord(ev[1 + 3 * i], s));
+    launch_rebuild(ctx->d, s);
+    CK(cudaEventRecord(ev[2 + 3 * i], s));
+    launch_forces(ctx->d, 1, ctx->cfg.block_size, s);
+    CK(cudaEventRecord(ev[3 + 3 * i], s));
+    if (ctx->any_cube) launch_cube_after_mid(ctx->d, s);
+  }
+  launch_rebuild(ctx->d, s);
+  launch_forces(ctx->d, 2, ctx->cfg.block_size, s);
+  CK(cudaEventRecord(ev[3 * body + 1], s));
+  CK(cudaStreamSynchronize(s));
+  double force = 0, rebuild = 0;
+  for (int64_t i = 0; i < body; ++i) {
+    float a = 0, b = 0;
+    CK(cudaEventElapsedTime(&a, ev[1 + 3 * i], ev[2 + 3 * i]));
+    CK(cudaEventElapsedTime(&b, ev[2 + 3 * i], ev[3 + 3 * i]));
+    rebuild += a;
+    force += b;
+  }
+  float tot = 0;
+  CK(cudaEventElapsedTime(&tot, ev[0], ev[3 * body + 1]));
+  for (auto& e : ev) cudaEventDestroy(e);
+  Ctl c1;
+  CK(cudaMemcpy(&c1, ctx->d.ctl, sizeof c1, cudaMemcpyDeviceToHost));
+  out[0] = force / (double)body;
+  out[1] = rebuild;
+  out[2] = (double)(c1.rebuilds - c0.rebuilds);
+  out[3] = tot;
+  out[4] = (double)body;
+  return check_status(ctx, s);
+}
+
+}  // extern "C"

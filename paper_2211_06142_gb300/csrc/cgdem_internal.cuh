@@ -1,0 +1,239 @@
+// cgdem_internal.cuh -- device-side data layout and helpers of the GB300
+// CFD-DEM step (arXiv 2211.06142).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cgdem.h"
+
+namespace cgdem {
+
+// ---------------------------------------------------------------------------
+// contact record flags (bits of the first word of a record)
+// ---------------------------------------------------------------------------
+constexpr uint32_t REC_BOND = 0x80000000u;    // bonded pair (modified JKR, Sec. 2.3)
+constexpr uint32_t REC_ACTIVE = 0x40000000u;  // applied a force at the last evaluation
+constexpr uint32_t REC_IDX = 0x3fffffffu;     // partner index (current order)
+
+// latched device status bits
+constexpr unsigned ST_CAPACITY = 1u;
+constexpr unsigned ST_BOND_LOST = 2u;
+constexpr unsigned ST_NONFINITE = 4u;
+
+// FP64 record: partner/flags + tangential spring (32 bytes)
+struct __align__(16) RecD {
+  uint32_t pf, pad;
+  double x, y, z;
+};
+// mixed record: partner/flags + tangential spring in FP32 (16 bytes)
+struct __align__(16) RecF {
+  uint32_t pf;
+  float x, y, z;
+};
+
+// Per-sample constants, derived on the host (grain level).
+struct SampleDev {
+  // material (Table 3 after Eq. 24 scaling) and derived moduli
+  double Es, Gs, beta, mu, gamma, rho;
+  double dt, half_dt;
+  double g[3];
+  double rho_f, mu_f;
+  int use_drag, use_buoyancy, kind, coulomb_mode;
+  double L[3], Rc, H, r_out;
+  // fixed-point shadow: q = round(x / dq) (low 32 bits)
+  double inv_dq, dq;
+  int32_t skin_q;
+  // search grid
+  double c_lo[3], c_inv_h[3];
+  int nc[3];
+  int cell_off;
+  // fluid grid
+  int nf[3];
+  int fcell_off;
+  double f_lo[3], inv_hf[3];
+  double inv_q, n_min;
+  int vf_mode, couple_every;
+  double hf[3];
+  double skin, rebuild_disp;  // rebuild when 2 * displacement bound > rebuild_disp
+  int64_t first, count;
+  // FP32 copies
+  float Es_f, Gs_f, beta_f, mu_f32, gamma_f, dt_f, dq_f, rho_f32, muf_f32, n_min_f;
+  float g_f[3];
+  float rho_s_f;  // particle density
+};
+
+// Device control block (one per context).
+struct Ctl {
+  int cur;           // buffer of the dynamic state (pos/vel/omg and shadows); flips every step
+  int pcur;          // buffer of per-particle data permuted only at rebuilds (id, sample, ...)
+  int rec_cur;       // contact-record buffer holding the current list
+  int vf_cur;        // porosity buffer read by the next force evaluation
+  int rebuild;       // 1: rebuild the candidate list before the next force evaluation
+  long long step;    // completed steps
+  long long rebuilds;
+  unsigned status;   // latched error bits
+  unsigned block_counter;
+  int max_cand;
+  unsigned coupled;
+  long long cand_total;  // candidate entries summed over particles at the last rebuild
+  int max_cand_next;     // accumulated by the running rebuild
+  long long cand_total_next;  // set when the running step scattered porosity quanta
+};
+
+// All device pointers of a context (passed by value to kernels).
+struct Dev {
+  // particle state, double-buffered: (x,y,z,R), (vx,vy,vz,1/m), (wx,wy,wz,1/I)
+  double4* pos[2];
+  double4* vel[2];
+  double4* omg[2];
+  // mixed-precision shadows: fixed-point position + radius, FP32 v|R, w|m
+  int4* posq[2];
+  float4* velf[2];
+  float4* omgf[2];
+  double4* F;  // force (w unused)
+  double4* T;  // torque
+  int* id[2];
+  int* sample[2];
+  int* fcell[2];                  // fluid cell (global index) of the current position
+  unsigned long long* vq[2];      // volume quantum round(V 2^40 / V_cell)
+  double4* wallh[2];              // wall spring history [3][Npad] (FP64 mode)
+  float4* wallhf[2];              // wall spring history [3][Npad] (mixed)
+  void* rec[2];                   // ELL contact records [cap][Npad]
+  uint32_t* cnt[2];               // candidates per particle
+  // rebuild scratch
+  uint32_t* cell_count;           // [C+1]
+  uint32_t* cell_start;           // [C+2]
+  uint32_t* pcell;                // [N]
+  uint32_t* pslot;                // [N]
+  uint32_t* perm_tmp;             // [N]
+  uint32_t* perm;                 // new -> old
+  uint32_t* inv_perm;             // old -> new
+  // fluid
+  unsigned long long* vf[3];      // porosity cell sums, rotating
+  double4* Us;                    // superficial velocity per fluid cell
+  float4* Usf;
+  int* removed_step;              // by id
+  double* disp;                   // per-sample displacement bound since last rebuild
+  unsigned long long* vmax2;      // per-sample max (|v| dt)^2 of the last drift (double bits)
+  double* diag;                   // per-sample diagnostics [S][8]
+  double* staging;                // [N * 16] host-transfer staging
+  uint32_t* contact_out;          // [2 * cap_out] (i, j | bond << 31)
+  unsigned long long* contact_n;
+  SampleDev* sp;
+  Ctl* ctl;
+  int N, Npad, cap, n_samples, C_total, Cf_total;
+  int mixed;
+};
+
+// ---------------------------------------------------------------------------
+// small math helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ V3<T> v3(T a, T b, T c) {
+  return V3<T>{a, b, c};
+}
+template <typename T>
+__device__ __forceinline__ T dot3(V3<T> a, V3<T> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename T>
+__device__ __forceinline__ V3<T> cross3(V3<T> a, V3<T> b) {
+  return v3<T>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float sqrtT(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqrtT(double a) { return sqrt(a); }
+__device__ __forceinline__ float cbrtT(float a) { return cbrtf(a); }
+__device__ __forceinline__ double cbrtT(double a) { return cbrt(a); }
+__device__ __forceinline__ float expT(float a) { return expf(a); }
+__device__ __forceinline__ double expT(double a) { return exp(a); }
+__device__ __forceinline__ float log10T(float a) { return log10f(a); }
+__device__ __forceinline__ double log10T(double a) { return log10(a); }
+__device__ __forceinline__ float powT(float a, float b) { return powf(a, b); }
+__device__ __forceinline__ double powT(double a, double b) { return pow(a, b); }
+
+// Minimum image in IEEE double without contraction (same rounding as the
+// plain definition d > L/2 ? d - L : d < -L/2 ? d + L : d).
+__device__ __forceinline__ double min_image(double d, double L) {
+  double h = 0.5 * L;
+  if (d > h) return __dsub_rn(d, L);
+  if (d < -h) return __dadd_rn(d, L);
+  return d;
+}
+
+// Fluid cell of a position: floor((x - lo) * inv_h) clamped, per axis.
+__device__ __forceinline__ int fluid_cell_of(const SampleDev& s, double x, double y, double z) {
+  double p[3] = {x, y, z};
+  int c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = floor(__dmul_rn(__dsub_rn(p[k], s.f_lo[k]), s.inv_hf[k]));
+    if (t < 0.0) t = 0.0;
+    double hi = (double)(s.nf[k] - 1);
+    if (t > hi) t = hi;
+    c[k] = (int)t;
+  }
+  return s.fcell_off + (c[2] * s.nf[1] + c[1]) * s.nf[0] + c[0];
+}
+
+// Volume quantum of a sphere: round(((4/3 pi) R) R R * inv_q), left to right.
+__device__ __forceinline__ unsigned long long volume_quantum(double R, double inv_q) {
+  const double c = 4.1887902047863905;  // fl(fl(4/3) * fl(pi))
+  double V = __dmul_rn(__dmul_rn(__dmul_rn(c, R), R), R);
+  return (unsigned long long)__double2ll_rn(__dmul_rn(V, inv_q));
+}
+
+// Fixed-point shadow of a position (low 32 bits of round(x / dq)).
+__device__ __forceinline__ int32_t to_q(double x, double inv_dq) {
+  long long t = __double2ll_rn(x * inv_dq);
+  return (int32_t)(uint32_t)(unsigned long long)t;
+}
+
+// Search-grid cell of a position (global index).
+__device__ __forceinline__ int search_cell_of(const SampleDev& s, double x, double y, double z,
+                                              int* cxyz) {
+  double p[3] = {x, y, z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = floor((p[k] - s.c_lo[k]) * s.c_inv_h[k]);
+    if (t < 0.0) t = 0.0;
+    double hi = (double)(s.nc[k] - 1);
+    if (t > hi) t = hi;
+    cxyz[k] = (int)t;
+  }
+  return s.cell_off + (cxyz[2] * s.nc[1] + cxyz[1]) * s.nc[0] + cxyz[0];
+}
+
+// Modified-JKR break test in IEEE double: delta < delta_C, evaluated as
+// delta^3 Es^2 < C_C^3 pi^2 gamma^2 Rs (cubing keeps the order; Table 1 C).
+__device__ __forceinline__ bool bond_breaks_exact(double delta, double Rs, double Es,
+                                                  double gamma) {
+  const double KC = -1.8505508252042548;  // ((81/16)^(1/3) - 12^(1/3))^3 pi^2
+  if (!(delta < 0.0)) return false;
+  double lhs = __dmul_rn(__dmul_rn(__dmul_rn(delta, delta), delta), __dmul_rn(Es, Es));
+  double rhs = __dmul_rn(__dmul_rn(KC, __dmul_rn(gamma, gamma)), Rs);
+  return lhs < rhs;
+}
+
+// Touching test of two spheres in IEEE double: d^2 < (Ri + Rj)^2 with the
+// squared distance summed x, y, z without contraction.
+__device__ __forceinline__ void exact_geometry(const SampleDev& s, double4 a, double4 b,
+                                               double* d2_out, double* S_out) {
+  double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y), dz = __dsub_rn(b.z, a.z);
+  if (s.kind == CGDEM_PERIODIC_BOX) {
+    dx = min_image(dx, s.L[0]);
+    dy = min_image(dy, s.L[1]);
+    dz = min_image(dz, s.L[2]);
+  }
+  *d2_out = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  *S_out = __dadd_rn(fabs(a.w), fabs(b.w));
+}
+
+__device__ __forceinline__ void latch(Ctl* ctl, unsigned bits) { atomicOr(&ctl->status, bits); }
+
+}  // namespace cgdem

@@ -1,0 +1,755 @@
+// k_other.cu -- candidate-list rebuild (cell binning, deterministic counting
+// sort, permutation, neighbour-cell scan with history carry), porosity
+// scatter, velocity-Verlet halves, initial state and readback kernels.
+#include "cgdem_internal.cuh"
+
+namespace cgdem {
+
+// ---------------------------------------------------------------------------
+// rebuild: bin -> scan -> scatter -> rank -> permute -> search -> finish
+// Every kernel returns at once unless ctl->rebuild is set, so the sequence
+// can sit in a CUDA graph and only costs launches on steps without rebuild.
+// ---------------------------------------------------------------------------
+
+__global__ void k_rb_bin(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int cur = d.ctl->cur, pc = d.ctl->pcur;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  double4 P = d.pos[cur][p];
+  uint32_t c;
+  if (P.w > 0.0) {
+    int cxyz[3];
+    c = (uint32_t)search_cell_of(d.sp[d.sample[pc][p]], P.x, P.y, P.z, cxyz);
+  } else {
+    c = (uint32_t)d.C_total;  // particles that left: one bin after all cells
+  }
+  d.pcell[p] = c;
+  d.pslot[p] = atomicAdd(&d.cell_count[c], 1u);
+}
+
+// Exclusive scan of cell_count[0..C] into cell_start[0..C+1]; clears counts.
+// One block of 1024 threads walks the array in tiles, carrying the total.
+__global__ void __launch_bounds__(1024) k_rb_scan(Dev d) {
+  if (!d.ctl->rebuild) return;
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry;
+  const int n = d.C_total + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024 * 4) {
+    uint32_t v[4];
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int i = base + threadIdx.x * 4 + j;
+      v[j] = i < n ? d.cell_count[i] : 0u;
+      if (i < n) d.cell_count[i] = 0u;
+      local += v[j];
+    }
+    // inclusive scan of per-thread totals within the warp
+    uint32_t x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + (x - local);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int i = base + threadIdx.x * 4 + j;
+      if (i < n) d.cell_start[i] = excl;
+      excl += v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.cell_start[n] = carry;
+}
+
+__global__ void k_rb_scatter(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  d.perm_tmp[d.cell_start[d.pcell[p]] + d.pslot[p]] = (uint32_t)p;
+}
+
+// Deterministic order inside each cell: rank by particle id.
+__global__ void k_rb_rank(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int pc = d.ctl->pcur;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= d.N) return;
+  const uint32_t i = d.perm_tmp[q];
+  const uint32_t c = d.pcell[i];
+  const uint32_t s0 = d.cell_start[c], s1 = d.cell_start[c + 1];
+  if (c == (uint32_t)d.C_total) {  // particles that left: order is irrelevant
+    d.perm[q] = i;
+    return;
+  }
+  const int myid = d.id[pc][i];
+  uint32_t rank = 0;
+  for (uint32_t j = s0; j < s1; ++j) rank += d.id[pc][d.perm_tmp[j]] < myid ? 1u : 0u;
+  d.perm[s0 + rank] = i;
+}
+
+// Gather every per-particle array into the other buffer in the new order.
+__global__ void k_rb_permute(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int cur = d.ctl->cur, nxt = cur ^ 1;
+  const int pc = d.ctl->pcur, pn = pc ^ 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const uint32_t o = d.perm[p];
+  d.inv_perm[o] = (uint32_t)p;
+  double4 P = d.pos[cur][o];
+  d.pos[nxt][p] = P;
+  d.vel[nxt][p] = d.vel[cur][o];
+  d.omg[nxt][p] = d.omg[cur][o];
+  const int s = d.sample[pc][o];
+  const SampleDev& S = d.sp[s];
+  int4 q;
+  q.x = to_q(P.x, S.inv_dq);
+  q.y = to_q(P.y, S.inv_dq);
+  q.z = to_q(P.z, S.inv_dq);
+  q.w = P.w > 0.0 ? d.posq[cur][o].w : 0;
+  d.posq[nxt][p] = q;
+  d.velf[nxt][p] = d.velf[cur][o];
+  d.omgf[nxt][p] = d.omgf[cur][o];
+  d.id[pn][p] = d.id[pc][o];
+  d.sample[pn][p] = s;
+  d.fcell[pn][p] = d.fcell[pc][o];
+  d.vq[pn][p] = d.vq[pc][o];
+  if (d.mixed && d.wallhf[0]) {
+    for (int w = 0; w < 3; ++w)
+      d.wallhf[pn][(size_t)w * d.Npad + p] = d.wallhf[pc][(size_t)w * d.Npad + o];
+  } else if (!d.mixed && d.wallh[0]) {
+    for (int w = 0; w < 3; ++w)
+      d.wallh[pn][(size_t)w * d.Npad + p] = d.wallh[pc][(size_t)w * d.Npad + o];
+  }
+}
+
+// Permute the single-buffered force and torque through staging memory.
+__global__ void k_rb_ft_gather(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const uint32_t o = d.perm[p];
+  double4* st = reinterpret_cast<double4*>(d.staging);
+  st[p] = d.F[o];
+  st[d.Npad + p] = d.T[o];
+}
+__global__ void k_rb_ft_store(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const double4* st = reinterpret_cast<const double4*>(d.staging);
+  d.F[p] = st[p];
+  d.T[p] = st[d.Npad + p];
+}
+
+// Neighbour-cell scan in the new order and carry of contact history.
+// Candidates: d^2 < (Ri + Rj + skin)^2 in fixed point (exact integer test).
+template <bool MIXED>
+__global__ void k_rb_search(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int cur = d.ctl->cur, nxt = cur ^ 1;
+  const int pn = d.ctl->pcur ^ 1;
+  const int rc = d.ctl->rec_cur, rn = rc ^ 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const int Npad = d.Npad, cap = d.cap;
+  const int4 pq = d.posq[nxt][p];
+  uint32_t count = 0;
+  if (pq.w > 0) {
+    const int s = d.sample[pn][p];
+    const SampleDev& S = d.sp[s];
+    const uint32_t o = d.perm[p];
+    const int lc = (int)d.pcell[o] - S.cell_off;
+    const int cx = lc % S.nc[0], cy = (lc / S.nc[0]) % S.nc[1], cz = lc / (S.nc[0] * S.nc[1]);
+    const bool per = S.kind == CGDEM_PERIODIC_BOX;
+    int lists[3][3], nl[3];
+    const int cc[3] = {cx, cy, cz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      nl[k] = 0;
+      const int ncs = S.nc[k];
+      if (per && ncs < 3) {
+        for (int a = 0; a < ncs; ++a) lists[k][nl[k]++] = a;
+      } else {
+        for (int off = -1; off <= 1; ++off) {
+          int a = cc[k] + off;
+          if (per) a = (a + ncs) % ncs;
+          else if (a < 0 || a >= ncs) continue;
+          lists[k][nl[k]++] = a;
+        }
+      }
+    }
+    for (int iz = 0; iz < nl[2]; ++iz)
+      for (int iy = 0; iy < nl[1]; ++iy)
+        for (int ix = 0; ix < nl[0]; ++ix) {
+          const int c = S.cell_off + (lists[2][iz] * S.nc[1] + lists[1][iy]) * S.nc[0] + lists[0][ix];
+          const uint32_t j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+          for (uint32_t q = j0; q < j1; ++q) {
+            if ((int)q == p) continue;
+            const int4 qq = d.posq[nxt][q];
+            if (qq.w <= 0) continue;
+            const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
+            const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
+            const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
+            const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                          (unsigned long long)((long long)dy * dy) +
+                                          (unsigned long long)((long long)dz * dz);
+            const unsigned long long Sq =
+                (unsigned long long)(unsigned)pq.w + (unsigned)qq.w + (unsigned)S.skin_q;
+            if (d2 < Sq * Sq) {
+              if (count < (uint32_t)cap) {
+                const size_t idx = (size_t)count * Npad + p;
+                if (MIXED)
+                  reinterpret_cast<uint4*>(d.rec[rn])[idx] = make_uint4(q, 0u, 0u, 0u);
+                else {
+                  RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + idx;
+                  *reinterpret_cast<int4*>(rr) = make_int4((int)q, 0, 0, 0);
+                  *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
+                }
+              }
+              ++count;
+            }
+          }
+        }
+    if (count > (uint32_t)cap) {
+      latch(d.ctl, ST_CAPACITY);
+    }
+    atomicMax(&d.ctl->max_cand_next, (int)count);
+    atomicAdd((unsigned long long*)&d.ctl->cand_total_next, (unsigned long long)count);
+    const uint32_t nnew = count < (uint32_t)cap ? count : (uint32_t)cap;
+    // carry history: old records of this particle with any state
+    const uint32_t nold = d.cnt[rc][o];
+    for (uint32_t k = 0; k < nold; ++k) {
+      const size_t oidx = (size_t)k * Npad + o;
+      uint32_t pf;
+      bool nz;
+      uint4 rf;
+      int4 h0;
+      double2 h1;
+      if (MIXED) {
+        rf = reinterpret_cast<const uint4*>(d.rec[rc])[oidx];
+        pf = rf.x;
+        nz = (rf.y | rf.z | rf.w) != 0u;
+      } else {
+        const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + oidx;
+        h0 = *reinterpret_cast<const int4*>(rr);
+        h1 = *(reinterpret_cast<const double2*>(rr) + 1);
+        pf = (uint32_t)h0.x;
+        nz = (h0.z | h0.w) != 0 || h1.x != 0.0 || h1.y != 0.0;
+      }
+      if (!(pf & (REC_BOND | REC_ACTIVE)) && !nz) continue;
+      const uint32_t qn = d.inv_perm[pf & REC_IDX];
+      bool found = false;
+      for (uint32_t j = 0; j < nnew; ++j) {
+        const size_t nidx = (size_t)j * Npad + p;
+        uint32_t partner = MIXED ? reinterpret_cast<const uint4*>(d.rec[rn])[nidx].x
+                                 : reinterpret_cast<const RecD*>(d.rec[rn])[nidx].pf;
+        if (partner == qn) {
+          const uint32_t npf = qn | (pf & (REC_BOND | REC_ACTIVE));
+          if (MIXED) {
+            reinterpret_cast<uint4*>(d.rec[rn])[nidx] = make_uint4(npf, rf.y, rf.z, rf.w);
+          } else {
+            RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + nidx;
+            *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, h0.z, h0.w);
+            *(reinterpret_cast<double2*>(rr) + 1) = h1;
+          }
+          found = true;
+          break;
+        }
+      }
+      if (!found && (pf & REC_BOND)) latch(d.ctl, ST_BOND_LOST);
+    }
+    count = nnew;
+  }
+  d.cnt[rn][p] = count;
+}
+
+__global__ void k_rb_finish(Dev d) {
+  Ctl* c = d.ctl;
+  if (!c->rebuild) return;
+  c->cur ^= 1;
+  c->pcur ^= 1;
+  c->rec_cur ^= 1;
+  c->rebuild = 0;
+  c->max_cand = c->max_cand_next;
+  c->cand_total = c->cand_total_next;
+  c->max_cand_next = 0;
+  c->cand_total_next = 0;
+  c->rebuilds += 1;
+  for (int s = 0; s < d.n_samples; ++s) {
+    d.disp[s] = 0.0;
+    d.vmax2[s] = 0ull;
+  }
+}
+
+__global__ void k_set_rebuild(Dev d) {
+  d.ctl->rebuild = 1;
+}
+
+// Bond every candidate pair that touches (d^2 < (Ri+Rj)^2 in IEEE double).
+__global__ void k_bond_touching(Dev d) {
+  const int cur = d.ctl->cur, pc = d.ctl->pcur, rc = d.ctl->rec_cur;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const double4 P = d.pos[cur][p];
+  if (!(P.w > 0.0)) return;
+  const SampleDev& S = d.sp[d.sample[pc][p]];
+  const uint32_t n = d.cnt[rc][p];
+  for (uint32_t k = 0; k < n; ++k) {
+    const size_t idx = (size_t)k * d.Npad + p;
+    uint32_t* pfp = d.mixed ? &reinterpret_cast<uint4*>(d.rec[rc])[idx].x
+                            : &reinterpret_cast<RecD*>(d.rec[rc])[idx].pf;
+    const uint32_t q = *pfp & REC_IDX;
+    const double4 Q = d.pos[cur][q];
+    if (!(Q.w > 0.0)) continue;
+    double d2, Sd;
+    exact_geometry(S, P, Q, &d2, &Sd);
+    if (d2 < __dmul_rn(Sd, Sd)) *pfp |= REC_BOND;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// porosity (void-fraction) scatter, fixed point
+// ---------------------------------------------------------------------------
+
+__global__ void k_vf_zero(Dev d, int which_offset) {
+  const int b = (d.ctl->vf_cur + which_offset) % 3;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.Cf_total; c += gridDim.x * blockDim.x)
+    d.vf[b][c] = 0ull;
+}
+
+// Equal-volume cube (side (pi/6)^(1/3) d) spread over the cells it overlaps.
+__device__ void scatter_cube(const SampleDev& S, double4 P, unsigned long long* out) {
+  const double side = __dmul_rn(__dmul_rn(2.0, fabs(P.w)), 0.8059959770082348);
+  const double p3[3] = {P.x, P.y, P.z};
+  double lo[3], hi[3];
+  int a0[3], a1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = __dsub_rn(p3[k], __dmul_rn(0.5, side));
+    hi[k] = __dadd_rn(p3[k], __dmul_rn(0.5, side));
+    a0[k] = (int)floor(__dmul_rn(__dsub_rn(lo[k], S.f_lo[k]), S.inv_hf[k]));
+    a1[k] = (int)floor(__dmul_rn(__dsub_rn(hi[k], S.f_lo[k]), S.inv_hf[k]));
+  }
+  for (int az = a0[2]; az <= a1[2]; ++az)
+    for (int ay = a0[1]; ay <= a1[1]; ++ay)
+      for (int ax = a0[0]; ax <= a1[0]; ++ax) {
+        const int a[3] = {ax, ay, az};
+        double vol = 1.0;
+        int c[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double b0 = __dadd_rn(S.f_lo[k], __dmul_rn((double)a[k], S.hf[k]));
+          const double b1 = __dadd_rn(S.f_lo[k], __dmul_rn((double)(a[k] + 1), S.hf[k]));
+          double ov = __dsub_rn(fmin(hi[k], b1), fmax(lo[k], b0));
+          if (ov < 0.0) ov = 0.0;
+          vol = __dmul_rn(vol, ov);
+          int ck = a[k];
+          if (S.kind == CGDEM_PERIODIC_BOX) {
+            ck %= S.nf[k];
+            if (ck < 0) ck += S.nf[k];
+          } else {
+            if (ck < 0) ck = 0;
+            if (ck > S.nf[k] - 1) ck = S.nf[k] - 1;
+          }
+          c[k] = ck;
+        }
+        if (vol <= 0.0) continue;
+        const int cell = S.fcell_off + (c[2] * S.nf[1] + c[1]) * S.nf[0] + c[0];
+        atomicAdd(&out[cell], (unsigned long long)__double2ll_rn(__dmul_rn(vol, S.inv_q)));
+      }
+}
+
+// Scatter the quanta of all active particles into buffer (vf_cur + offset).
+// Centroid mode uses the stored fluid cell; cube mode recomputes the parts.
+__global__ void k_vf_scatter(Dev d, int which_offset) {
+  const int cur = d.ctl->cur, pc = d.ctl->pcur;
+  const int b = (d.ctl->vf_cur + which_offset) % 3;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const double4 P = d.pos[cur][p];
+  if (!(P.w > 0.0)) return;
+  const SampleDev& S = d.sp[d.sample[pc][p]];
+  if (S.vf_mode == 0)
+    atomicAdd(&d.vf[b][d.fcell[pc][p]], d.vq[pc][p]);
+  else
+    scatter_cube(S, P, d.vf[b]);
+}
+
+// Cube-mode scatter for the fused step (positions already drifted into the
+// other buffer by the force kernel; runs after it, before its bookkeeping).
+__global__ void k_vf_scatter_cube_next(Dev d) {
+  const int cur = d.ctl->cur;  // the state written by the last force kernel
+  const int pc = d.ctl->pcur;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const double4 P = d.pos[cur][p];
+  if (!(P.w > 0.0)) return;
+  const SampleDev& S = d.sp[d.sample[pc][p]];
+  if (S.vf_mode == 1 && (d.ctl->step % S.couple_every) == 0) scatter_cube(S, P, d.vf[d.ctl->vf_cur]);
+}
+
+__global__ void k_vf_rotate(Dev d) { d.ctl->vf_cur = (d.ctl->vf_cur + 1) % 3; }
+
+// ---------------------------------------------------------------------------
+// velocity Verlet halves (API verbs)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void write_shadows(Dev& d, int buf, int p, const SampleDev& S, double4 P,
+                                              double4 V, double4 W) {
+  int4 q = d.posq[buf][p];
+  q.x = to_q(P.x, S.inv_dq);
+  q.y = to_q(P.y, S.inv_dq);
+  q.z = to_q(P.z, S.inv_dq);
+  if (!(P.w > 0.0)) q.w = 0;
+  d.posq[buf][p] = q;
+  d.velf[buf][p] = make_float4((float)V.x, (float)V.y, (float)V.z, (float)fabs(P.w));
+  d.omgf[buf][p] = make_float4((float)W.x, (float)W.y, (float)W.z, (float)(1.0 / V.w));
+}
+
+// half kick + drift (in place); optionally scatter quanta into vf_cur+1.
+__global__ void k_kick_drift(Dev d, int couple) {
+  const int cur = d.ctl->cur, pc = d.ctl->pcur;
+  const int b = (d.ctl->vf_cur + 1) % 3;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < d.N) {
+    double4 P = d.pos[cur][p];
+    if (P.w > 0.0) {
+      const int s = d.sample[pc][p];
+      const SampleDev& S = d.sp[s];
+      double4 V = d.vel[cur][p], W = d.omg[cur][p];
+      const double4 F = d.F[p], Tq = d.T[p];
+      const double h = S.half_dt;
+      V.x += h * (F.x * V.w);
+      V.y += h * (F.y * V.w);
+      V.z += h * (F.z * V.w);
+      W.x += h * (Tq.x * W.w);
+      W.y += h * (Tq.y * W.w);
+      W.z += h * (Tq.z * W.w);
+      double x = P.x + S.dt * V.x, y = P.y + S.dt * V.y, z = P.z + S.dt * V.z;
+      if (S.kind == CGDEM_PERIODIC_BOX) {
+        if (x >= S.L[0]) x -= S.L[0]; else if (x < 0.0) x += S.L[0];
+        if (y >= S.L[1]) y -= S.L[1]; else if (y < 0.0) y += S.L[1];
+        if (z >= S.L[2]) z -= S.L[2]; else if (z < 0.0) z += S.L[2];
+      }
+      P.x = x;
+      P.y = y;
+      P.z = z;
+      d.pos[cur][p] = P;
+      d.vel[cur][p] = V;
+      d.omg[cur][p] = W;
+      write_shadows(d, cur, p, S, P, V, W);
+      const int fc = fluid_cell_of(S, x, y, z);
+      d.fcell[pc][p] = fc;
+      const double dx = S.dt * V.x, dy = S.dt * V.y, dz = S.dt * V.z;
+      atomicMax(&d.vmax2[s], (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
+      if (couple && (d.ctl->step % S.couple_every) == 0) {
+        if (S.vf_mode == 0) atomicAdd(&d.vf[b][fc], d.vq[pc][p]);
+        else scatter_cube(S, P, d.vf[b]);
+      }
+    }
+  }
+}
+
+// After a drift: displacement bound, rebuild flag, porosity rotation.
+__global__ void k_after_drift(Dev d, int couple) {
+  Ctl* c = d.ctl;
+  bool any = false;
+  for (int s = 0; s < d.n_samples; ++s) {
+    unsigned long long b = d.vmax2[s];
+    d.vmax2[s] = 0ull;
+    double dd = d.disp[s] + sqrt(__longlong_as_double((long long)b));
+    d.disp[s] = dd;
+    if (2.0 * dd > d.sp[s].rebuild_disp) c->rebuild = 1;
+    if ((c->step % d.sp[s].couple_every) == 0) any = true;
+  }
+  if (couple && any) c->vf_cur = (c->vf_cur + 1) % 3;
+}
+
+// final half kick + outlet (in place), completes a step.
+__global__ void k_kick_final(Dev d) {
+  const int cur = d.ctl->cur, pc = d.ctl->pcur;
+  const long long m = d.ctl->step + 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  double4 P = d.pos[cur][p];
+  if (!(P.w > 0.0)) return;
+  const SampleDev& S = d.sp[d.sample[pc][p]];
+  double4 V = d.vel[cur][p], W = d.omg[cur][p];
+  const double4 F = d.F[p], Tq = d.T[p];
+  const double h = S.half_dt;
+  V.x += h * (F.x * V.w);
+  V.y += h * (F.y * V.w);
+  V.z += h * (F.z * V.w);
+  W.x += h * (Tq.x * W.w);
+  W.y += h * (Tq.y * W.w);
+  W.z += h * (Tq.z * W.w);
+  if (S.kind == CGDEM_CYLINDER && P.z < -2.0 * P.w) {
+    d.removed_step[d.id[pc][p]] = (int)m;
+    P.w = -P.w;
+    d.pos[cur][p] = P;
+  }
+  d.vel[cur][p] = V;
+  d.omg[cur][p] = W;
+  write_shadows(d, cur, p, S, P, V, W);
+}
+
+__global__ void k_step_inc(Dev d) { d.ctl->step += 1; }
+
+// ---------------------------------------------------------------------------
+// initial state and readback
+// ---------------------------------------------------------------------------
+
+// staging layout (doubles): x[3N] v[3N] w[3N] R[N]
+__global__ void k_init_state(Dev d) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const double* st = d.staging;
+  const int N = d.N;
+  int s = 0;
+  while (s + 1 < d.n_samples && p >= d.sp[s + 1].first) ++s;
+  const SampleDev& S = d.sp[s];
+  const double R = st[9 * (size_t)N + p];
+  const double c = 4.1887902047863905;
+  const double m = S.rho * (c * R * R * R);
+  const double I = 0.4 * m * R * R;
+  double4 P = make_double4(st[3 * p], st[3 * p + 1], st[3 * p + 2], R);
+  double4 V = make_double4(st[3 * N + 3 * p], st[3 * N + 3 * p + 1], st[3 * N + 3 * p + 2], 1.0 / m);
+  double4 W = make_double4(st[6 * N + 3 * p], st[6 * N + 3 * p + 1], st[6 * N + 3 * p + 2], 1.0 / I);
+  if (S.kind == CGDEM_PERIODIC_BOX) {
+    // bring positions into [0, L)
+    double* xs[3] = {&P.x, &P.y, &P.z};
+    for (int k = 0; k < 3; ++k) {
+      double v = *xs[k];
+      if (v >= S.L[k] || v < 0.0) {
+        v = fmod(v, S.L[k]);
+        if (v < 0.0) v += S.L[k];
+        if (v >= S.L[k]) v -= S.L[k];
+      }
+      *xs[k] = v;
+    }
+  }
+  const int cur = 0;
+  d.pos[cur][p] = P;
+  d.vel[cur][p] = V;
+  d.omg[cur][p] = W;
+  d.posq[cur][p] = make_int4(0, 0, 0, (int)llrint(R * S.inv_dq));
+  write_shadows(d, cur, p, S, P, V, W);
+  d.F[p] = make_double4(0, 0, 0, 0);
+  d.T[p] = make_double4(0, 0, 0, 0);
+  d.id[cur][p] = p;
+  d.sample[cur][p] = s;
+  d.fcell[cur][p] = fluid_cell_of(S, P.x, P.y, P.z);
+  d.vq[cur][p] = volume_quantum(R, S.inv_q);
+  d.removed_step[p] = -1;
+  d.cnt[0][p] = 0;
+  d.cnt[1][p] = 0;
+  for (int w = 0; w < 3; ++w) {
+    if (d.mixed && d.wallhf[cur]) d.wallhf[cur][(size_t)w * d.Npad + p] = make_float4(0, 0, 0, 0);
+    if (!d.mixed && d.wallh[cur]) d.wallh[cur][(size_t)w * d.Npad + p] = make_double4(0, 0, 0, 0);
+  }
+}
+
+__global__ void k_init_ctl(Dev d) {
+  Ctl* c = d.ctl;
+  c->cur = 0;
+  c->pcur = 0;
+  c->rec_cur = 0;
+  c->vf_cur = 0;
+  c->rebuild = 1;
+  c->step = 0;
+  c->rebuilds = 0;
+  c->status = 0;
+  c->block_counter = 0;
+  c->max_cand = 0;
+  c->max_cand_next = 0;
+  c->cand_total = 0;
+  c->cand_total_next = 0;
+  c->coupled = 0;
+  for (int s = 0; s < d.n_samples; ++s) {
+    d.disp[s] = 0.0;
+    d.vmax2[s] = 0ull;
+  }
+}
+
+// staging layout (doubles): x[3N] v[3N] w[3N] F[3N] T[3N], id order
+__global__ void k_gather_state(Dev d) {
+  const int cur = d.ctl->cur, pc = d.ctl->pcur;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const int i = d.id[pc][p];
+  const size_t N = d.N;
+  double* st = d.staging;
+  const double4 P = d.pos[cur][p], V = d.vel[cur][p], W = d.omg[cur][p], F = d.F[p], T = d.T[p];
+  st[3 * i] = P.x; st[3 * i + 1] = P.y; st[3 * i + 2] = P.z;
+  st[3 * N + 3 * i] = V.x; st[3 * N + 3 * i + 1] = V.y; st[3 * N + 3 * i + 2] = V.z;
+  st[6 * N + 3 * i] = W.x; st[6 * N + 3 * i + 1] = W.y; st[6 * N + 3 * i + 2] = W.z;
+  st[9 * N + 3 * i] = F.x; st[9 * N + 3 * i + 1] = F.y; st[9 * N + 3 * i + 2] = F.z;
+  st[12 * N + 3 * i] = T.x; st[12 * N + 3 * i + 1] = T.y; st[12 * N + 3 * i + 2] = T.z;
+}
+
+// Active contacts as (id_i, id_j | bond << 31) with id_i < id_j.
+__global__ void k_collect_contacts(Dev d, uint32_t* out, unsigned long long cap) {
+  const int pc = d.ctl->pcur, rc = d.ctl->rec_cur;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const uint32_t n = d.cnt[rc][p];
+  const int ip = d.id[pc][p];
+  for (uint32_t k = 0; k < n; ++k) {
+    const size_t idx = (size_t)k * d.Npad + p;
+    const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
+                                : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
+    if (!(pf & REC_ACTIVE)) continue;
+    const int iq = d.id[pc][pf & REC_IDX];
+    if (ip >= iq) continue;
+    const unsigned long long slot = atomicAdd(d.contact_n, 1ull);
+    if (slot < cap) {
+      out[2 * slot] = (uint32_t)ip;
+      out[2 * slot + 1] = (uint32_t)iq | ((pf & REC_BOND) ? 0x80000000u : 0u);
+    }
+  }
+}
+
+// Per-sample diagnostics: partial sums per block (fixed order), then reduce.
+constexpr int DIAG_BLOCKS = 128;
+__global__ void k_diag_partial(Dev d, double* part) {
+  extern __shared__ double sh[];  // [n_samples * 8]
+  const int cur = d.ctl->cur, pc = d.ctl->pcur, rc = d.ctl->rec_cur;
+  const int S8 = d.n_samples * 8;
+  for (int i = threadIdx.x; i < S8; i += blockDim.x) sh[i] = 0.0;
+  __syncthreads();
+  const int per = (d.N + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * per, b1 = min(d.N, b0 + per);
+  // one thread walks the chunk in order: deterministic sums
+  if (threadIdx.x == 0) {
+    for (int p = b0; p < b1; ++p) {
+      const double4 P = d.pos[cur][p], V = d.vel[cur][p], W = d.omg[cur][p];
+      const int s = d.sample[pc][p];
+      double* o = sh + 8 * s;
+      const double m = 1.0 / V.w, I = 1.0 / W.w;
+      if (P.w > 0.0) {
+        o[0] += 0.5 * m * (V.x * V.x + V.y * V.y + V.z * V.z);
+        o[1] += 0.5 * I * (W.x * W.x + W.y * W.y + W.z * W.z);
+        o[2] += m * V.x;
+        o[3] += m * V.y;
+        o[4] += m * V.z;
+        o[6] += 1.0;
+        const uint32_t n = d.cnt[rc][p];
+        const int ip = d.id[pc][p];
+        for (uint32_t k = 0; k < n; ++k) {
+          const size_t idx = (size_t)k * d.Npad + p;
+          const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
+                                      : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
+          if ((pf & REC_BOND) && (pf & REC_ACTIVE) && ip < d.id[pc][pf & REC_IDX]) o[7] += 1.0;
+        }
+      } else {
+        o[5] += m;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < S8; i += blockDim.x) part[(size_t)blockIdx.x * S8 + i] = sh[i];
+}
+
+__global__ void k_diag_reduce(Dev d, const double* part, int nblocks) {
+  const int S8 = d.n_samples * 8;
+  for (int i = threadIdx.x; i < S8; i += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) acc += part[(size_t)b * S8 + i];
+    d.diag[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+void launch_rebuild(const Dev& d, cudaStream_t s) {
+  const int B = 256, G = nblk(d.N, B);
+  if (G == 0) return;
+  k_rb_bin<<<G, B, 0, s>>>(d);
+  k_rb_scan<<<1, 1024, 0, s>>>(d);
+  k_rb_scatter<<<G, B, 0, s>>>(d);
+  k_rb_rank<<<G, B, 0, s>>>(d);
+  k_rb_permute<<<G, B, 0, s>>>(d);
+  k_rb_ft_gather<<<G, B, 0, s>>>(d);
+  k_rb_ft_store<<<G, B, 0, s>>>(d);
+  if (d.mixed) k_rb_search<true><<<G, B, 0, s>>>(d);
+  else k_rb_search<false><<<G, B, 0, s>>>(d);
+  k_rb_finish<<<1, 1, 0, s>>>(d);
+}
+
+void launch_set_rebuild(const Dev& d, cudaStream_t s) { k_set_rebuild<<<1, 1, 0, s>>>(d); }
+
+void launch_bond_touching(const Dev& d, cudaStream_t s) {
+  if (d.N) k_bond_touching<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_couple(const Dev& d, cudaStream_t s) {
+  const int Gc = nblk(d.Cf_total, 256);
+  if (Gc) {
+    k_vf_zero<<<Gc, 256, 0, s>>>(d, 0);
+    k_vf_zero<<<Gc, 256, 0, s>>>(d, 1);
+  }
+  if (d.N) k_vf_scatter<<<nblk(d.N, 256), 256, 0, s>>>(d, 0);
+}
+
+void launch_kick_drift(const Dev& d, int couple, cudaStream_t s) {
+  if (d.N) k_kick_drift<<<nblk(d.N, 256), 256, 0, s>>>(d, couple);
+  k_after_drift<<<1, 1, 0, s>>>(d, couple);
+  // the buffer after the (possibly rotated) current one must be zero
+  const int Gc = nblk(d.Cf_total, 256);
+  if (couple && Gc) k_vf_zero<<<Gc, 256, 0, s>>>(d, 1);
+}
+
+void launch_kick_final(const Dev& d, cudaStream_t s) {
+  if (d.N) k_kick_final<<<nblk(d.N, 256), 256, 0, s>>>(d);
+  k_step_inc<<<1, 1, 0, s>>>(d);
+}
+
+void launch_cube_after_mid(const Dev& d, cudaStream_t s) {
+  if (d.N) k_vf_scatter_cube_next<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_init(const Dev& d, cudaStream_t s) {
+  k_init_ctl<<<1, 1, 0, s>>>(d);
+  if (d.N) k_init_state<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_gather_state(const Dev& d, cudaStream_t s) {
+  if (d.N) k_gather_state<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s) {
+  cudaMemsetAsync(d.contact_n, 0, sizeof(unsigned long long), s);
+  if (d.N) k_collect_contacts<<<nblk(d.N, 256), 256, 0, s>>>(d, out, cap);
+}
+
+void launch_diag(const Dev& d, double* part, cudaStream_t s) {
+  const size_t sh = sizeof(double) * 8 * d.n_samples;
+  k_diag_partial<<<DIAG_BLOCKS, 32, sh, s>>>(d, part);
+  k_diag_reduce<<<1, 256, 0, s>>>(d, part, DIAG_BLOCKS);
+}
+
+}  // namespace cgdem
