@@ -289,7 +289,7 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": tr["bytes_per_launch"] if tr else None,
                 "peak_source": src, "kernel": "k_forces<mixed, fused step>",
                 "alg_bytes_per_particle_step": alg_bytes, "Zbar": Zbar, "candidates_per_particle": Cbar,
-                "force_kernel_ms": prof["force_ms"],
+                "force_kernel_ms": prof["force_ms"], "max_candidates": cnt["max_candidates"],
                 "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1)}
     launches_per_step = 1 + 9  # fused kernel + the rebuild sequence (early exit unless due)
     ctx.close()

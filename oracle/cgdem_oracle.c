@@ -172,7 +172,7 @@ static int contact_law(const ora_params* p, double delta, int touching, const do
                        const double vrel[3], const double vrel_c[3],
                        double Rs, double ms, double gamma,
                        double xi[3], int* bonded, double Fi[3], double Ft_out[3],
-                       double* Fne_out, double* a_out) {
+                       double* Fne_out, double* a_out, double* scale_out) {
     double Es = ora_estar(p->E, p->nu);
     double Gs = ora_gstar(p->E, p->nu);
     double beta = ora_beta(p->e);
@@ -243,6 +243,13 @@ static int contact_law(const ora_params* p, double delta, int touching, const do
     Fi[0] = -Fn * n[0] + Ft[0];
     Fi[1] = -Fn * n[1] + Ft[1];
     Fi[2] = -Fn * n[2] + Ft[2];
+    if (scale_out) {
+        /* magnitudes of the separate terms: Eq. 12 repulsion and adhesion,
+           Eq. 32 damping, tangential force */
+        double rep = 4.0 * Es * a * a * a / (3.0 * Rs);
+        double adh = *bonded ? sqrt(16.0 * M_PI * gamma * Es * a * a * a) : 0.0;
+        *scale_out = rep + adh + fabs(gn * vn) + sqrt(dot(Ft, Ft));
+    }
     Ft_out[0] = Ft[0];
     Ft_out[1] = Ft[1];
     Ft_out[2] = Ft[2];
@@ -255,7 +262,8 @@ static int contact_law(const ora_params* p, double delta, int touching, const do
 static int pair_eval(const ora_params* p, const double* xi_p, const double* vi, const double* wi,
                      double Ri, double mi, const double* xj_p, const double* vj, const double* wj,
                      double Rj, double mj, double hist[3], int* bonded, double Fi[3],
-                     double Ti[3], double Tj[3], double* Fne, double* a_out, double* delta_out) {
+                     double Ti[3], double Tj[3], double* Fne, double* a_out, double* delta_out,
+                     double* scale_out) {
     double d[3];
     for (int k = 0; k < 3; ++k) {
         d[k] = xj_p[k] - xi_p[k];
@@ -281,7 +289,7 @@ static int pair_eval(const ora_params* p, const double* xi_p, const double* vi, 
     double vc[3] = {vrel[0] - rwn[0], vrel[1] - rwn[1], vrel[2] - rwn[2]};
     double Ft[3];
     int act = contact_law(p, delta, d2 < S * S, n, vrel, vc, Rs, ms, p->gamma, hist, bonded, Fi, Ft,
-                          Fne, a_out);
+                          Fne, a_out, scale_out);
     if (!act) return 0;
     double nFt[3];
     cross(n, Ft, nFt);
@@ -298,7 +306,7 @@ int ora_pair_contact(const ora_params* p, const double xi_pos[3], const double v
                      double xi_inout[3], int* bonded_inout, double out[12]) {
     double Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0}, Tj[3] = {0, 0, 0}, Fne = 0, a = 0, delta = 0;
     int act = pair_eval(p, xi_pos, vi, wi, Ri, mi, xj_pos, vj, wj, Rj, mj, xi_inout,
-                        bonded_inout, Fi, Ti, Tj, &Fne, &a, &delta);
+                        bonded_inout, Fi, Ti, Tj, &Fne, &a, &delta, NULL);
     for (int k = 0; k < 3; ++k) {
         out[k] = act ? Fi[k] : 0.0;
         out[3 + k] = act ? Ti[k] : 0.0;
@@ -699,9 +707,11 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
         cross(rw, n, rwn);
         double vc[3] = {vrel[0] - rwn[0], vrel[1] - rwn[1], vrel[2] - rwn[2]};
         int bonded = 0;
-        double F[3], Ft[3];
-        if (!contact_law(p, delta, 1, n, vrel, vc, R, s->m[i], 0.0, h, &bonded, F, Ft, NULL, NULL))
+        double F[3], Ft[3], sc = 0.0;
+        if (!contact_law(p, delta, 1, n, vrel, vc, R, s->m[i], 0.0, h, &bonded, F, Ft, NULL, NULL,
+                         &sc))
             continue;
+        s->Fscale[i] += sc;
         double nFt[3];
         cross(n, Ft, nFt);
         for (int k = 0; k < 3; ++k) {
@@ -739,10 +749,10 @@ int ora_compute_forces(ora_sim* s) {
         const ora_rec* old = find_rec(s->rec, s->nrec, i, j);
         ora_rec r = {i, j, old ? old->bonded : 0, 0, {0, 0, 0}};
         if (old) memcpy(r.xi, old->xi, sizeof(r.xi));
-        double Fi[3], Ti[3], Tj[3];
+        double Fi[3], Ti[3], Tj[3], sc = 0.0;
         int act = pair_eval(p, &s->x[3 * i], &s->v[3 * i], &s->w[3 * i], s->R[i], s->m[i],
                             &s->x[3 * j], &s->v[3 * j], &s->w[3 * j], s->R[j], s->m[j], r.xi,
-                            &r.bonded, Fi, Ti, Tj, NULL, NULL, NULL);
+                            &r.bonded, Fi, Ti, Tj, NULL, NULL, NULL, &sc);
         if (!act) continue;
         for (int c = 0; c < 3; ++c) {
             s->F[3 * i + c] += Fi[c];
@@ -750,8 +760,8 @@ int ora_compute_forces(ora_sim* s) {
             s->T[3 * i + c] += Ti[c];
             s->T[3 * j + c] += Tj[c];
         }
-        s->Fscale[i] += sqrt(dot(Fi, Fi));
-        s->Fscale[j] += sqrt(dot(Fi, Fi));
+        s->Fscale[i] += sc;
+        s->Fscale[j] += sc;
         nrec[nn++] = r;
     }
     free(pr);
@@ -770,10 +780,10 @@ int ora_compute_forces(ora_sim* s) {
             double Fw[3] = {0, 0, 0};
             wall_forces(s, i, Fw, T);
             for (int c = 0; c < 3; ++c) F[c] += Fw[c];
-            s->Fscale[i] += sqrt(dot(Fw, Fw));
         }
-        s->Fscale[i] += s->m[i] * sqrt(dot(p->g, p->g));
         double V = sphere_volume(s->R[i]);
+        s->Fscale[i] += s->m[i] * sqrt(dot(p->g, p->g));
+        if (p->use_buoyancy) s->Fscale[i] += p->rho_f * V * sqrt(dot(p->g, p->g));
         for (int c = 0; c < 3; ++c) {
             F[c] += s->m[i] * p->g[c];                        /* F_g */
             if (p->use_buoyancy) F[c] += -p->rho_f * V * p->g[c]; /* F_b */

@@ -104,7 +104,9 @@ int ora_get_voidfrac(const ora_sim* s, uint64_t* cell_sums);
 int ora_get_diagnostics(const ora_sim* s, double out[8]);
 int ora_get_removed_step(const ora_sim* s, int64_t* removed_step);
 /* Per particle, the sum of the magnitudes of all force terms of the last
- * force evaluation (scale for normwise comparisons). */
+ * force evaluation -- Eq. 12 repulsion and adhesion counted separately, plus
+ * damping, tangential, wall, gravity, buoyancy and drag terms -- the scale
+ * for normwise comparisons. */
 int ora_get_force_scale(const ora_sim* s, double* scale);
 /* Brute force O(N^2) list of pairs with d^2 < (Ri+Rj+skin)^2 (minimum image). */
 int64_t ora_pairs_bruteforce(const ora_params* p, int64_t n, const double* x, const double* R,

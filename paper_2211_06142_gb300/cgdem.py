@@ -178,7 +178,7 @@ class Context:
     """A library context over one or more samples on one GPU."""
 
     def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
-                 cell_scale=1.0, steps_per_graph=32, device="cuda:0", stream=None):
+                 cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None):
         import torch
 
         if not torch.cuda.is_available():

@@ -25,6 +25,7 @@ void launch_init(const Dev& d, cudaStream_t s);
 void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
 void launch_diag(const Dev& d, double* part, cudaStream_t s);
+void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
 }  // namespace cgdem
 
 using namespace cgdem;
@@ -42,6 +43,7 @@ struct cgdem_ctx {
   std::string err;
   // CUDA graphs of steps_per_graph fused steps, keyed by stream
   std::map<cudaStream_t, cudaGraphExec_t> graphs;
+  bool conditional_graphs = false;
 };
 
 namespace {
@@ -152,8 +154,10 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   }
   s.inv_dq = 1.0 / s.dq;
   s.skin_q = (int32_t)std::ceil(p.skin * s.inv_dq) + 8;
-  // search grid: cell edge >= reach
-  const double h = std::max(1.0, cfg->cell_scale) * reach;
+  // search grid: each pair is searched from its larger sphere over a stencil
+  // of ceil((2R + skin) / h) cells, so h can follow the typical sphere
+  const double cs = cfg->cell_scale > 0 ? std::min(1.0, std::max(0.05, cfg->cell_scale)) : 0.35;
+  const double h = cs * reach;
   double lo[3], ext[3];
   if (p.kind == CGDEM_PERIODIC_BOX) {
     for (int k = 0; k < 3; ++k) {
@@ -174,6 +178,7 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
     s.nc[k] = n;
     s.c_lo[k] = lo[k];
     s.c_inv_h[k] = n / ext[k];
+    s.c_inv_h_f[k] = (float)s.c_inv_h[k];
     ncell *= n;
   }
   if (ncell > (1ll << 28)) return fail(ctx, CGDEM_E_INVALID, "search grid too large");
@@ -192,7 +197,20 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   s.vf_mode = p.vf_mode;
   s.couple_every = p.couple_every;
   s.skin = p.skin;
+  s.skin_f = (float)p.skin;
   s.rebuild_disp = p.skin - 16.0 * s.dq;
+  {
+    const double half = 0.5 * (p.skin - 16.0 * s.dq) / s.dq;  // displacement limit, fixed units
+    s.rebuild_q2 = (float)(half * half);
+  }
+  for (int k = 0; k < 3; ++k) {
+    s.f_lo_f[k] = (float)p.f_lo[k];
+    s.inv_hf_f[k] = (float)p.inv_hf[k];
+    s.L_f[k] = (float)p.L[k];
+  }
+  s.Rc_f = (float)p.Rc;
+  s.H_f = (float)p.H;
+  s.r_out_f = (float)p.r_out;
   s.first = first;
   s.count = count;
   s.Es_f = (float)s.Es;
@@ -238,8 +256,11 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     cube |= sp[s].vf_mode == 1;
   }
   if (N >= (1ll << 30)) return fail(ctx, CGDEM_E_INVALID, "too many particles");
-  const int cap = cfg->max_neighbors > 0 ? cfg->max_neighbors : 64;
-  const int Npad = (int)(((N + 63) / 64) * 64 + 64);
+  const int cap = cfg->max_neighbors > 0 ? cfg->max_neighbors : 48;
+  if (cap > CGDEM_MAX_NEIGHBORS)
+    return fail(ctx, CGDEM_E_INVALID, "max_neighbors must be <= %d", CGDEM_MAX_NEIGHBORS);
+  // a multiple of every block size used, so grids over Npad never run past it
+  const int Npad = (int)(((N + 255) / 256) * 256 + 256);
   const bool mixed = cfg->precision == CGDEM_MIXED;
   Carver cv{base};
   Dev d;
@@ -261,7 +282,13 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     }
     d.rec[b] = mixed ? (void*)cv.take<RecF>((size_t)cap * Npad) : (void*)cv.take<RecD>((size_t)cap * Npad);
     d.cnt[b] = cv.take<uint32_t>(Npad);
+    d.roff[b] = cv.take<uint32_t>(Npad);
   }
+  d.posq_ref = cv.take<int4>(Npad);
+  d.cand_tmp = cv.take<uint32_t>((size_t)cap * Npad);
+  d.cand_n = cv.take<uint32_t>(Npad);
+  d.tile_sums = cv.take<uint32_t>((size_t)(C + 2) / 2048 + 2);
+  d.dmax2 = cv.take<unsigned>(S);
   d.F = cv.take<double4>(Npad);
   d.T = cv.take<double4>(Npad);
   d.cell_count = cv.take<uint32_t>((size_t)C + 2);
@@ -325,6 +352,68 @@ void enqueue_mid_step(cgdem_ctx* ctx, cudaStream_t s) {
   launch_rebuild(ctx->d, s);
   launch_forces(ctx->d, 1, ctx->cfg.block_size, s);
   if (ctx->any_cube) launch_cube_after_mid(ctx->d, s);
+}
+
+// Capture U fused steps into one graph.  Each step's rebuild sequence sits in
+// the body of a conditional (IF) node whose condition a one-thread kernel
+// sets from the device-side rebuild flag, so steps without a rebuild launch
+// two kernels.  Falls back to a plain capture (rebuild kernels that return at
+// once) if conditional nodes are unavailable.
+cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec_t* out) {
+  cudaStream_t cs, bs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return e;
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  for (int i = 0; i < U && e == cudaSuccess; ++i) {
+    if (!conditional) {
+      enqueue_mid_step(ctx, cs);
+      continue;
+    }
+    cudaStreamCaptureStatus stt;
+    cudaGraph_t cg;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
+    if (e != cudaSuccess) break;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0);
+    if (e != cudaSuccess) break;
+    launch_rebuild_cond(ctx->d, h, cs);
+    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    launch_rebuild(ctx->d, bs);
+    e = cudaStreamEndCapture(bs, &body);
+    if (e != cudaSuccess) break;
+    e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) break;
+    launch_forces(ctx->d, 1, ctx->cfg.block_size, cs);
+    if (ctx->any_cube) launch_cube_after_mid(ctx->d, cs);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  cudaStreamDestroy(bs);
+  cudaGetLastError();  // a failed attempt must not leave a sticky launch error behind
+  return e;
 }
 
 }  // namespace
@@ -538,20 +627,14 @@ int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {
     auto it = ctx->graphs.find(s);
     cudaGraphExec_t exec = nullptr;
     if (it == ctx->graphs.end()) {
-      cudaStream_t cs;
-      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-      cudaGraph_t g;
-      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      for (int i = 0; i < U; ++i) enqueue_mid_step(ctx, cs);
-      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      cudaError_t e = capture_steps(ctx, U, true, &exec);
       if (e != cudaSuccess) {
-        cudaStreamDestroy(cs);
-        return cuda_fail(ctx, e, "graph capture");
+        ctx->conditional_graphs = false;
+        e = capture_steps(ctx, U, false, &exec);
+      } else {
+        ctx->conditional_graphs = true;
       }
-      e = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      cudaStreamDestroy(cs);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
       ctx->graphs[s] = exec;
     } else {
       exec = it->second;

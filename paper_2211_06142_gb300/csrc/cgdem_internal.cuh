@@ -16,6 +16,9 @@ constexpr uint32_t REC_BOND = 0x80000000u;    // bonded pair (modified JKR, Sec.
 constexpr uint32_t REC_ACTIVE = 0x40000000u;  // applied a force at the last evaluation
 constexpr uint32_t REC_IDX = 0x3fffffffu;     // partner index (current order)
 
+// largest candidate list per particle (max_neighbors)
+#define CGDEM_MAX_NEIGHBORS 96
+
 // latched device status bits
 constexpr unsigned ST_CAPACITY = 1u;
 constexpr unsigned ST_BOND_LOST = 2u;
@@ -61,6 +64,10 @@ struct SampleDev {
   float Es_f, Gs_f, beta_f, mu_f32, gamma_f, dt_f, dq_f, rho_f32, muf_f32, n_min_f;
   float g_f[3];
   float rho_s_f;  // particle density
+  float f_lo_f[3], inv_hf_f[3];
+  float L_f[3], Rc_f, H_f, r_out_f;
+  float rebuild_q2;  // rebuild when (max displacement in fixed units)^2 exceeds this
+  float c_inv_h_f[3], skin_f;
 };
 
 // Device control block (one per context).
@@ -99,8 +106,14 @@ struct Dev {
   unsigned long long* vq[2];      // volume quantum round(V 2^40 / V_cell)
   double4* wallh[2];              // wall spring history [3][Npad] (FP64 mode)
   float4* wallhf[2];              // wall spring history [3][Npad] (mixed)
-  void* rec[2];                   // ELL contact records [cap][Npad]
+  void* rec[2];                   // contact records, one segment of 32*cap per warp of particles
   uint32_t* cnt[2];               // candidates per particle
+  uint32_t* roff[2];              // index of a particle's first record
+  int4* posq_ref;                 // fixed-point positions at the last rebuild
+  uint32_t* cand_tmp;             // rebuild scratch: candidate partners [cap][Npad]
+  uint32_t* cand_n;               // rebuild scratch: candidates found per particle
+  uint32_t* tile_sums;            // rebuild scratch: cell-scan tile sums
+  unsigned* dmax2;                // per-sample max squared displacement since rebuild (float bits, fixed units)
   // rebuild scratch
   uint32_t* cell_count;           // [C+1]
   uint32_t* cell_start;           // [C+2]
@@ -235,5 +248,34 @@ __device__ __forceinline__ void exact_geometry(const SampleDev& s, double4 a, do
 }
 
 __device__ __forceinline__ void latch(Ctl* ctl, unsigned bits) { atomicOr(&ctl->status, bits); }
+
+// IEEE double -> float, round to nearest even, by bit manipulation on the
+// integer pipe (GB300 runs FP64 and its conversions at ~1/60 of the FP32
+// rate).  Results below the float normal range flush to signed zero; the
+// caller never passes NaN or Inf (checked earlier).
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int fe = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned f = sign | ((unsigned)fe << 23) | m;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) f += 1u;
+  return __uint_as_float(f);
+}
+
+// float -> double (exact), by bit manipulation; float subnormals flush to zero.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned m = u & 0x7fffffu;
+  const unsigned hi = sign | ((e - 127u + 1023u) << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
 
 }  // namespace cgdem

@@ -1,29 +1,40 @@
 // k_forces.cu -- contact, wall, body and drag forces of one DEM step fused
 // with the velocity-Verlet update (arXiv 2211.06142, Sec. 2.1-2.3).
 //
-// One thread per particle walks its candidate list (ELL, column-major) and
-// sums its own contacts in list order; every pair is evaluated from both
-// sides with bit-identical magnitudes, so no float atomics are needed and
-// the result is deterministic.
+// Work decomposition.  Particles are grouped by warp (32 consecutive
+// particles in cell order).  A warp's candidate records are stored
+// contiguously (particle after particle), so the warp walks them in rounds of
+// 32 entries: every lane evaluates one pair per round whatever the
+// candidate counts of the 32 particles are (the size ratio of the sand is 6,
+// so counts vary several-fold within a warp).  Each pair is evaluated from
+// both sides with bit-identical magnitudes; a particle sums its own pair
+// forces in list order through shared memory, so the result is deterministic
+// and needs no floating-point atomics.
 //
 // Two precisions:
 //   FP64  -- geometry and contact physics in double.
 //   MIXED -- positions, integrator and accumulators stay FP64, the contact
-//            geometry comes from a per-step 32-bit fixed-point shadow of the
-//            positions (exact integer differences, so the overlap
-//            delta = Ri + Rj - d suffers no cancellation), and the contact
-//            physics and tangential history run in FP32.  Every integer
-//            decision (touching, bond break) is taken in IEEE double from the
-//            FP64 positions whenever the fixed-point value lies within its
-//            error band of the threshold, so it always equals the FP64
-//            decision.  GB300 runs FP64 at ~1/60 of the FP32 rate, so the
-//            common path holds no FP64 arithmetic per contact.
+//            geometry comes from a 32-bit fixed-point shadow of the positions
+//            (exact integer differences, so delta = Ri + Rj - d suffers no
+//            cancellation), and contact physics and tangential history run in
+//            FP32.  Every integer decision (touching, bond break) is taken in
+//            IEEE double from the FP64 positions whenever the fixed-point value
+//            lies within its error band of the threshold, so it always equals
+//            the FP64 decision.  GB300 runs FP64 at ~1/60 of the FP32 rate, so
+//            the contact path holds no FP64 arithmetic and the per-particle
+//            update keeps only the FP64 additions of the integrator.
 #include "cgdem_internal.cuh"
 
 namespace cgdem {
 
 constexpr double PI_D = 3.14159265358979323846;
 constexpr float PI_F = 3.14159265358979323846f;
+#ifndef CGDEM_FORCE_MINB
+#define CGDEM_FORCE_MINB 6  // resident blocks per SM the register budget must allow
+#endif
+constexpr int FORCE_BLOCK = 128;
+constexpr int WPB = FORCE_BLOCK / 32;
+constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
 struct Consts;
@@ -40,6 +51,26 @@ struct Consts<double> {
   static constexpr int newton_iters = 6;
 };
 
+// Elementary functions of the contact law.  Double: IEEE-accurate.  Float
+// (the mixed mode, toleranced at 1e-4 against the FP64 oracle and with every
+// integer decision taken in FP64): hardware approximations of a few ulp --
+// reciprocal square root, base-2 logarithm and exponential, fast divide --
+// which cost one to three instructions instead of an IEEE sequence.
+__device__ __forceinline__ double m_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ double m_cbrt(double a) { return cbrt(a); }
+__device__ __forceinline__ double m_exp(double a) { return exp(a); }
+__device__ __forceinline__ double m_log10(double a) { return log10(a); }
+__device__ __forceinline__ double m_pow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float m_sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float m_cbrt(float a) {
+  return a > 0.f ? exp2f(__log2f(a) * (1.0f / 3.0f)) : 0.f;
+}
+__device__ __forceinline__ float m_exp(float a) { return __expf(a); }
+__device__ __forceinline__ float m_log10(float a) { return __log10f(a); }
+__device__ __forceinline__ float m_pow(float a, float b) { return exp2f(b * __log2f(a)); }
+
 // Contact radius and elastic normal force on the stable JKR branch
 // (Eq. 12-13), solved in reduced units: with a_A^3 = 4 pi gamma R*^2 / E*
 // (Table 1, point A) and u^2 = a / a_A, Eq. 13 reads u^4 - u = delta / d_A
@@ -49,14 +80,14 @@ struct Consts<double> {
 template <typename T>
 __device__ __forceinline__ void jkr_solve(T delta, T Rs, T Es, T gamma, T* a_out, T* F_out) {
   const T pi = Consts<T>::pi();
-  T aA = cbrtT(T(4) * pi * gamma * Rs * Rs / Es);
-  T dA = aA * aA / Rs;
-  T D = delta / dA;
-  T u = D >= T(0) ? sqrtT(sqrtT(D + T(1))) + T(0.05) : T(1);
+  T aA = m_cbrt(m_div(T(4) * pi * gamma * Rs * Rs, Es));
+  T dA = m_div(aA * aA, Rs);
+  T D = m_div(delta, dA);
+  T u = D >= T(0) ? m_sqrt(m_sqrt(D + T(1))) + T(0.05) : T(1);
 #pragma unroll
   for (int it = 0; it < Consts<T>::newton_iters; ++it) {
     T u3 = u * u * u;
-    u -= (u3 * u - u - D) / (T(4) * u3 - T(1));
+    u -= m_div(u3 * u - u - D, T(4) * u3 - T(1));
   }
   const T uC = T(0.90856029641606983);  // (3/4)^(1/3)
   if (u < uC) u = uC;
@@ -76,24 +107,24 @@ __device__ __forceinline__ void contact_law(T delta, V3<T> n, V3<T> vrel, V3<T> 
   if (bonded && gamma > T(0)) {
     jkr_solve<T>(delta, Rs, Es, gamma, &a, &Fne);
   } else {
-    a = delta > T(0) ? sqrtT(Rs * delta) : T(0);
-    Fne = T(4) * Es * a * a * a / (T(3) * Rs);
+    a = delta > T(0) ? m_sqrt(Rs * delta) : T(0);
+    Fne = m_div(T(4) * Es * a * a * a, T(3) * Rs);
   }
   const T cd = Consts<T>::damp();
-  T gn = cd * beta * sqrtT(T(2) * Es * a * ms);  // Eq. 32
+  T gn = cd * beta * m_sqrt(T(2) * Es * a * ms);  // Eq. 32
   T vn = dot3(vrel, n);
   T Fn = Fne - gn * vn;
   // tangential spring rotated into the tangent plane, Eq. 4
   T vcn = dot3(vc, n);
   V3<T> vt = v3<T>(vc.x - vcn * n.x, vc.y - vcn * n.y, vc.z - vcn * n.z);
-  T old = sqrtT(dot3(xi, xi));
+  T old = m_sqrt(dot3(xi, xi));
   T xn = dot3(xi, n);
   xi.x -= xn * n.x;
   xi.y -= xn * n.y;
   xi.z -= xn * n.z;
-  T nw = sqrtT(dot3(xi, xi));
+  T nw = m_sqrt(dot3(xi, xi));
   if (nw > T(0)) {
-    T sc = old / nw;
+    T sc = m_div(old, nw);
     xi.x *= sc;
     xi.y *= sc;
     xi.z *= sc;
@@ -104,22 +135,23 @@ __device__ __forceinline__ void contact_law(T delta, V3<T> n, V3<T> vrel, V3<T> 
   xi.y += vt.y * dt;
   xi.z += vt.z * dt;
   T kt = T(8) * Gs * a;
-  T gt = cd * beta * sqrtT(kt * ms);
+  T gt = cd * beta * m_sqrt(kt * ms);
   Ft = v3<T>(kt * xi.x + gt * vt.x, kt * xi.y + gt * vt.y, kt * xi.z + gt * vt.z);
   T FC = T(3) * Consts<T>::pi() * gamma * Rs;  // Table 1
   T Flim = coulomb_mode == 1 ? fabs(Fne) : (bonded ? Fne + T(2) * FC : Fne);
   if (Flim < T(0)) Flim = T(0);
-  T ftm = sqrtT(dot3(Ft, Ft));
+  T ftm = m_sqrt(dot3(Ft, Ft));
   T cap = mu * Flim;  // Eq. 35
   if (ftm > cap) {
-    T sc = ftm > T(0) ? cap / ftm : T(0);
+    T sc = ftm > T(0) ? m_div(cap, ftm) : T(0);
     Ft.x *= sc;
     Ft.y *= sc;
     Ft.z *= sc;
     if (kt > T(0)) {
-      xi.x = (Ft.x - gt * vt.x) / kt;
-      xi.y = (Ft.y - gt * vt.y) / kt;
-      xi.z = (Ft.z - gt * vt.z) / kt;
+      const T ik = m_div(T(1), kt);
+      xi.x = (Ft.x - gt * vt.x) * ik;
+      xi.y = (Ft.y - gt * vt.y) * ik;
+      xi.z = (Ft.z - gt * vt.z) * ik;
     }
   }
   Fi = v3<T>(-Fn * n.x + Ft.x, -Fn * n.y + Ft.y, -Fn * n.z + Ft.z);
@@ -130,51 +162,65 @@ __device__ __forceinline__ void contact_law(T delta, V3<T> n, V3<T> vrel, V3<T> 
 // finite as Re -> 0.
 template <typename T>
 __device__ __forceinline__ V3<T> drag_force(T rho_f, T mu_f, T dp, V3<T> w, T n) {
-  T wm = sqrtT(dot3(w, w));
+  T wm = m_sqrt(dot3(w, w));
   if (!(wm > T(0))) return v3<T>(0, 0, 0);
-  T Re = rho_f * dp * wm / mu_f;
-  T lr = T(1.5) - log10T(Re);
-  T chi = T(3.7) - T(0.65) * expT(-(lr * lr) * T(0.5));
-  T t = T(0.63) * sqrtT(rho_f * wm) + T(4.8) * sqrtT(mu_f / dp);
-  T pre = Consts<T>::pi() * dp * dp / T(8) * t * t * powT(n, -chi);
+  T Re = m_div(rho_f * dp * wm, mu_f);
+  T lr = T(1.5) - m_log10(Re);
+  T chi = T(3.7) - T(0.65) * m_exp(-(lr * lr) * T(0.5));
+  T t = T(0.63) * m_sqrt(rho_f * wm) + T(4.8) * m_sqrt(m_div(mu_f, dp));
+  T pre = Consts<T>::pi() * dp * dp * T(0.125) * t * t * m_pow(n, -chi);
   return v3<T>(pre * w.x, pre * w.y, pre * w.z);
 }
 
-__device__ __forceinline__ float ll2f(long long v) { return __ll2float_rn(v); }
-__device__ __forceinline__ float ull2f(unsigned long long v) { return __ull2float_rn(v); }
-
 enum { MODE_FORCES = 0, MODE_MID = 1, MODE_CANON = 2 };
 
-// Per-sample atomic maximum of a non-negative double (as ordered bits).
-__device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double v) {
-  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+// 64-bit integers to float through 32-bit halves (both non-negative, so the
+// sum has no cancellation): relative error below 2^-23, no 64-bit conversion.
+__device__ __forceinline__ float u64_to_f(unsigned long long v) {
+  return fmaf((float)(unsigned)(v >> 32), 4294967296.0f, (float)(unsigned)v);
+}
+__device__ __forceinline__ float s64_to_f(long long v) {
+  const float m = u64_to_f((unsigned long long)(v < 0 ? -v : v));
+  return v < 0 ? -m : m;
 }
 
-// Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law).
+// Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law).  The
+// overlaps are computed in FP64 only for particles near a wall; a float
+// filter (margin 1e-4 of the radius, far above float rounding) rejects the rest.
 template <typename T>
-__device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, V3<T> v, V3<T> w,
-                                              T R, T m, T Es, T Gs, T beta, T mu, T dt,
-                                              V3<T>* hist, V3<T>& F, V3<T>& Tq, bool* changed) {
-  const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
+__device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, float xf, float yf,
+                                              float zf, V3<T> v, V3<T> w, T R, T m, T Es, T Gs,
+                                              T beta, T mu, T dt, V3<T>* hist, V3<T>& F,
+                                              V3<T>& Tq, bool* changed) {
+  const float Rf = (float)R;
+  const float r2f = xf * xf + yf * yf;
+  const float marg = 1e-4f * Rf;
   for (int wall = 0; wall < 3; ++wall) {
     double delta = -1.0;
     V3<T> n = v3<T>(0, 0, 0);
     if (wall == 0) {
-      double lim = s.Rc - fabs(P.w);
-      if (lim < 0) lim = 0;
-      if (r2 > lim * lim * (1.0 - 1e-6) && r2 > 0.0) {
-        double r = sqrt(r2);
-        delta = (r + fabs(P.w)) - s.Rc;
-        n = v3<T>(T(P.x / r), T(P.y / r), T(0));
+      const float lim = s.Rc_f - Rf - marg;
+      if (lim <= 0.f || r2f > lim * lim) {
+        const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
+        if (r2 > 0.0) {
+          const double r = sqrt(r2);
+          delta = (r + fabs(P.w)) - s.Rc;
+          n = v3<T>(T(P.x / r), T(P.y / r), T(0));
+        }
       }
     } else if (wall == 1) {
-      if (P.z < fabs(P.w) && sqrt(r2) >= s.r_out) {
-        delta = fabs(P.w) - P.z;
-        n = v3<T>(0, 0, -1);
+      if (zf < Rf + marg) {
+        const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
+        if (P.z < fabs(P.w) && sqrt(r2) >= s.r_out) {
+          delta = fabs(P.w) - P.z;
+          n = v3<T>(0, 0, -1);
+        }
       }
     } else {
-      delta = (P.z + fabs(P.w)) - s.H;
-      n = v3<T>(0, 0, 1);
+      if (zf + Rf > s.H_f - marg) {
+        delta = (P.z + fabs(P.w)) - s.H;
+        n = v3<T>(0, 0, 1);
+      }
     }
     if (!(delta > 0.0)) {
       if (hist[wall].x != T(0) || hist[wall].y != T(0) || hist[wall].z != T(0)) {
@@ -201,8 +247,44 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, V3<
   }
 }
 
+// Fluid cell of a position with a float pre-check: the FP64 evaluation of
+// floor((x - lo) * inv_h) is needed only within 1e-4 cell of a cell face.
+__device__ __forceinline__ int fluid_cell_fast(const SampleDev& S, double x, double y, double z,
+                                               float xf, float yf, float zf) {
+  const float pf[3] = {xf, yf, zf};
+  int c[3];
+  bool exact = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float t = (pf[k] - S.f_lo_f[k]) * S.inv_hf_f[k];
+    const float fl = floorf(t);
+    const float fr = t - fl;
+    if (fr < 1e-4f || fr > 1.f - 1e-4f) exact = true;
+    int ck = (int)fl;
+    if (ck < 0) ck = 0;
+    if (ck > S.nf[k] - 1) ck = S.nf[k] - 1;
+    c[k] = ck;
+  }
+  if (exact) return fluid_cell_of(S, x, y, z);
+  return S.fcell_off + (c[2] * S.nf[1] + c[1]) * S.nf[0] + c[0];
+}
+
+// Data of the particle that owns a record, broadcast to the lane evaluating it.
+template <bool MIXED>
+struct Owner;
+template <>
+struct Owner<true> {
+  int4 pq;    // fixed-point position, fixed-point radius
+  float4 va;  // v, R
+  float4 wa;  // w, m
+};
+template <>
+struct Owner<false> {
+  double4 P, V, W;  // x,R | v,1/m | w,1/I
+};
+
 template <bool MIXED, int MODE>
-__global__ void __launch_bounds__(256) k_forces(Dev d) {
+__global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d) {
   using T = typename std::conditional<MIXED, float, double>::type;
   Ctl* ctl = d.ctl;
   const int cur = ctl->cur;
@@ -211,36 +293,298 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
   const int rc = ctl->rec_cur;
   const int vfc = ctl->vf_cur;
   const long long m_step = ctl->step + 1;  // step completed by this evaluation
-  const int Npad = d.Npad;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  // porosity recomputed for the next positions (couple_every is equal in all samples)
+  const int ce = d.sp[0].couple_every;
+  const bool couple_next = ce == 1 || (unsigned)(m_step % ce) == 0u;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad (multiple of 32)
+  const int wbase = p - lane;
+  const bool valid = p < d.N;
+  if (wbase >= d.Npad) return;  // whole warps only (Npad is a multiple of 256)
 
-  __shared__ int s_uniform_sample;
-  __shared__ unsigned long long s_vmax;
-  __shared__ int s_couple_any;
-  if (threadIdx.x == 0) {
-    s_uniform_sample = -2;
-    s_vmax = 0ull;
-    s_couple_any = 0;
+  __shared__ T sh[WPB][6][32];
+
+  // ---- own particle, contact phase ----
+  Owner<MIXED> me;
+  int si = 0;
+  if (valid) si = d.sample[pc][p];
+  if constexpr (MIXED) {
+    if (valid) {
+      me.pq = d.posq[cur][p];
+      me.va = d.velf[cur][p];
+      me.wa = d.omgf[cur][p];
+    } else {
+      me.pq = make_int4(0, 0, 0, 0);
+      me.va = make_float4(0, 0, 0, 0);
+      me.wa = make_float4(0, 0, 0, 0);
+    }
+  } else {
+    if (valid) {
+      me.P = d.pos[cur][p];
+      me.V = d.vel[cur][p];
+      me.W = d.omg[cur][p];
+    } else {
+      me.P = make_double4(0, 0, 0, 0);
+      me.V = make_double4(0, 0, 0, 1);
+      me.W = make_double4(0, 0, 0, 1);
+    }
   }
-  __syncthreads();
+  const uint32_t ncnt = d.cnt[rc][p];
+  const uint32_t seg = (uint32_t)wbase * (uint32_t)d.cap;
+  const uint32_t lo = d.roff[rc][p] - seg;
+  const uint32_t total = __shfl_sync(FULL, lo + ncnt, 31);
+  V3<T> F = v3<T>(0, 0, 0), Tq = v3<T>(0, 0, 0);
 
-  int my_sample = -1;
-  double my_disp2 = -1.0;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t e = base + lane;
+    const bool has = e < total;
+    // owner lane: the last lane whose first entry is <= e
+    int own = 0;
+#pragma unroll
+    for (int sft = 16; sft >= 1; sft >>= 1) {
+      const int c = own + sft;
+      const uint32_t loc = __shfl_sync(FULL, lo, c & 31);
+      if (c < 32 && loc <= e) own = c;
+    }
+    const int os = __shfl_sync(FULL, si, own);
+    Owner<MIXED> o;
+    if constexpr (MIXED) {
+      o.pq.x = __shfl_sync(FULL, me.pq.x, own);
+      o.pq.y = __shfl_sync(FULL, me.pq.y, own);
+      o.pq.z = __shfl_sync(FULL, me.pq.z, own);
+      o.pq.w = __shfl_sync(FULL, me.pq.w, own);
+      o.va.x = __shfl_sync(FULL, me.va.x, own);
+      o.va.y = __shfl_sync(FULL, me.va.y, own);
+      o.va.z = __shfl_sync(FULL, me.va.z, own);
+      o.va.w = __shfl_sync(FULL, me.va.w, own);
+      o.wa.x = __shfl_sync(FULL, me.wa.x, own);
+      o.wa.y = __shfl_sync(FULL, me.wa.y, own);
+      o.wa.z = __shfl_sync(FULL, me.wa.z, own);
+      o.wa.w = __shfl_sync(FULL, me.wa.w, own);
+    } else {
+      o.P.x = __shfl_sync(FULL, me.P.x, own);
+      o.P.y = __shfl_sync(FULL, me.P.y, own);
+      o.P.z = __shfl_sync(FULL, me.P.z, own);
+      o.P.w = __shfl_sync(FULL, me.P.w, own);
+      o.V.x = __shfl_sync(FULL, me.V.x, own);
+      o.V.y = __shfl_sync(FULL, me.V.y, own);
+      o.V.z = __shfl_sync(FULL, me.V.z, own);
+      o.V.w = __shfl_sync(FULL, me.V.w, own);
+      o.W.x = __shfl_sync(FULL, me.W.x, own);
+      o.W.y = __shfl_sync(FULL, me.W.y, own);
+      o.W.z = __shfl_sync(FULL, me.W.z, own);
+    }
+    V3<T> Fc = v3<T>(0, 0, 0), Tc = v3<T>(0, 0, 0);
+    if (has) {
+      const SampleDev& S = d.sp[os];
+      const size_t idx = (size_t)seg + e;
+      const int owner_p = wbase + own;
+      uint32_t pf;
+      V3<T> xi;
+      if constexpr (MIXED) {
+        const uint4 r = reinterpret_cast<const uint4*>(d.rec[rc])[idx];
+        pf = r.x;
+        xi = v3<T>(__uint_as_float(r.y), __uint_as_float(r.z), __uint_as_float(r.w));
+      } else {
+        const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + idx;
+        const int4 h0 = *reinterpret_cast<const int4*>(rr);
+        const double2 h1 = *(reinterpret_cast<const double2*>(rr) + 1);
+        pf = (uint32_t)h0.x;
+        xi = v3<T>(__hiloint2double(h0.w, h0.z), h1.x, h1.y);
+      }
+      const int q = (int)(pf & REC_IDX);
+      bool bonded = (pf & REC_BOND) != 0u;
+      const bool had_state = (pf & (REC_BOND | REC_ACTIVE)) != 0u || xi.x != T(0) ||
+                             xi.y != T(0) || xi.z != T(0);
+      bool act = false;
+      if constexpr (MIXED) {
+        const int4 qq = d.posq[cur][q];
+        if (qq.w > 0 && o.pq.w > 0) {
+          const int dx = (int)((uint32_t)qq.x - (uint32_t)o.pq.x);
+          const int dy = (int)((uint32_t)qq.y - (uint32_t)o.pq.y);
+          const int dz = (int)((uint32_t)qq.z - (uint32_t)o.pq.z);
+          const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                        (unsigned long long)((long long)dy * dy) +
+                                        (unsigned long long)((long long)dz * dz);
+          const unsigned Sq = (unsigned)o.pq.w + (unsigned)qq.w;
+          const unsigned long long S2 = (unsigned long long)Sq * Sq;
+          const unsigned long long band = 16ull * Sq + 256ull;
+          bool touching = false, need_exact = false;
+          if (d2 > S2 + band) touching = false;
+          else if (d2 + band < S2) touching = true;
+          else need_exact = true;
+          if (bonded || touching || need_exact) {
+            const float d2f = u64_to_f(d2);
+            const float invd = rsqrtf(d2f);
+            const float dn = d2f * invd;
+            float du;
+            if (d2 < (1ull << 62))
+              du = __fdividef(s64_to_f((long long)S2 - (long long)d2), (float)Sq + dn);
+            else
+              du = (float)Sq - dn;
+            const float delta = du * S.dq_f;
+            const V3<float> n = v3<float>(dx * invd, dy * invd, dz * invd);
+            const float4 qa = d.velf[cur][q];
+            const float4 qb = d.omgf[cur][q];
+            const float Ri = o.va.w, Rj = qa.w, mi = o.wa.w, mj = qb.w;
+            const float Rs = __fdividef(Ri * Rj, Ri + Rj);
+            double d2e = 0.0, Se = 0.0;
+            bool have_exact = false;
+            if (need_exact) {
+              exact_geometry(S, d.pos[cur][owner_p], d.pos[cur][q], &d2e, &Se);
+              have_exact = true;
+              touching = d2e < __dmul_rn(Se, Se);
+            }
+            if (bonded) {
+              bool broken;
+              float dC = 0.0f, bandf = 4.0f * S.dq_f;
+              if (S.gamma_f > 0.f) {
+                const float xs = m_cbrt(__fdividef(PI_F * PI_F * S.gamma_f * S.gamma_f * Rs, S.Es_f * S.Es_f));
+                dC = -0.57235712127666594f * xs;
+                bandf += 2e-5f * fabsf(dC);
+              }
+              if (delta < dC - bandf) {
+                broken = true;
+              } else if (delta > dC + bandf) {
+                broken = false;
+              } else {
+                const double4 A = d.pos[cur][owner_p], B = d.pos[cur][q];
+                if (!have_exact) {
+                  exact_geometry(S, A, B, &d2e, &Se);
+                  have_exact = true;
+                  touching = d2e < __dmul_rn(Se, Se);
+                }
+                const double Rid = fabs(A.w), Rjd = fabs(B.w);
+                const double Rsd = __dmul_rn(Rid, Rjd) / __dadd_rn(Rid, Rjd);
+                broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, S.gamma);
+              }
+              if (broken) bonded = false;
+            }
+            act = bonded || touching;
+            if (act) {
+              const float ms = __fdividef(mi * mj, mi + mj);
+              const V3<float> vi = v3<float>(o.va.x, o.va.y, o.va.z);
+              const V3<float> wi = v3<float>(o.wa.x, o.wa.y, o.wa.z);
+              const V3<float> vrel = v3<float>(qa.x - vi.x, qa.y - vi.y, qa.z - vi.z);
+              const V3<float> rw = v3<float>(Ri * wi.x + Rj * qb.x, Ri * wi.y + Rj * qb.y,
+                                             Ri * wi.z + Rj * qb.z);
+              const V3<float> rwn = cross3(rw, n);
+              const V3<float> vc = v3<float>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
+              V3<float> Fi, Ft;
+              V3<float> xif = v3<float>((float)xi.x, (float)xi.y, (float)xi.z);
+              contact_law<float>(delta, n, vrel, vc, Rs, ms, S.gamma_f, bonded, S.Es_f, S.Gs_f,
+                                 S.beta_f, S.mu_f32, S.dt_f, S.coulomb_mode, xif, Fi, Ft);
+              xi = v3<T>(xif.x, xif.y, xif.z);
+              const V3<float> nFt = cross3(n, Ft);
+              Fc = v3<T>(Fi.x, Fi.y, Fi.z);
+              Tc = v3<T>(Ri * nFt.x, Ri * nFt.y, Ri * nFt.z);
+            }
+          }
+        }
+      } else {
+        const double4 Q = d.pos[cur][q];
+        if (Q.w > 0.0 && o.P.w > 0.0) {
+          double dx = __dsub_rn(Q.x, o.P.x), dy = __dsub_rn(Q.y, o.P.y), dz = __dsub_rn(Q.z, o.P.z);
+          if (S.kind == CGDEM_PERIODIC_BOX) {
+            dx = min_image(dx, S.L[0]);
+            dy = min_image(dy, S.L[1]);
+            dz = min_image(dz, S.L[2]);
+          }
+          const double d2 =
+              __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+          const double Sd = __dadd_rn(o.P.w, Q.w);
+          const bool touching = d2 < __dmul_rn(Sd, Sd);
+          if (bonded || touching) {
+            const double dist = sqrt(d2);
+            const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
+            const double delta = __dsub_rn(Sd, dist);
+            if (bonded && bond_breaks_exact(delta, Rs, S.Es, S.gamma)) bonded = false;
+            act = bonded || touching;
+            if (act && dist > 0.0) {
+              const double4 QV = d.vel[cur][q];
+              const double4 QW = d.omg[cur][q];
+              const double Ri = o.P.w, Rj = Q.w;
+              const double mi = 1.0 / o.V.w, mj = 1.0 / QV.w;
+              const V3<double> n = v3<double>(dx / dist, dy / dist, dz / dist);
+              const double ms = mi * mj / (mi + mj);
+              const V3<double> vrel = v3<double>(QV.x - o.V.x, QV.y - o.V.y, QV.z - o.V.z);
+              const V3<double> rw = v3<double>(Ri * o.W.x + Rj * QW.x, Ri * o.W.y + Rj * QW.y,
+                                               Ri * o.W.z + Rj * QW.z);
+              const V3<double> rwn = cross3(rw, n);
+              const V3<double> vc = v3<double>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
+              V3<double> Fi, Ft;
+              V3<double> xid = v3<double>((double)xi.x, (double)xi.y, (double)xi.z);
+              contact_law<double>(delta, n, vrel, vc, Rs, ms, S.gamma, bonded, S.Es, S.Gs, S.beta,
+                                  S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft);
+              xi = v3<T>(xid.x, xid.y, xid.z);
+              const V3<double> nFt = cross3(n, Ft);
+              Fc = v3<T>(Fi.x, Fi.y, Fi.z);
+              Tc = v3<T>(Ri * nFt.x, Ri * nFt.y, Ri * nFt.z);
+            } else if (act) {
+              act = false;  // coincident centres: no normal defined
+            }
+          }
+        }
+      }
+      // write the record back when its state changed
+      if (act) {
+        const uint32_t npf = (uint32_t)q | REC_ACTIVE | (bonded ? REC_BOND : 0u);
+        if constexpr (MIXED) {
+          reinterpret_cast<uint4*>(d.rec[rc])[idx] =
+              make_uint4(npf, __float_as_uint((float)xi.x), __float_as_uint((float)xi.y),
+                         __float_as_uint((float)xi.z));
+        } else {
+          RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
+          const double xx = (double)xi.x;
+          *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, __double2loint(xx), __double2hiint(xx));
+          *(reinterpret_cast<double2*>(rr) + 1) = make_double2((double)xi.y, (double)xi.z);
+        }
+      } else if (had_state) {
+        if constexpr (MIXED) {
+          reinterpret_cast<uint4*>(d.rec[rc])[idx] = make_uint4((uint32_t)q, 0u, 0u, 0u);
+        } else {
+          RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
+          *reinterpret_cast<int4*>(rr) = make_int4(q, 0, 0, 0);
+          *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
+        }
+      }
+    }
+    // contributions of this round to their owners, summed in list order
+    sh[wib][0][lane] = Fc.x;
+    sh[wib][1][lane] = Fc.y;
+    sh[wib][2][lane] = Fc.z;
+    sh[wib][3][lane] = Tc.x;
+    sh[wib][4][lane] = Tc.y;
+    sh[wib][5][lane] = Tc.z;
+    __syncwarp();
+    const int a = (int)max(lo, base) - (int)base;
+    const int b = (int)min(lo + ncnt, base + 32u) - (int)base;
+    for (int j = a; j < b; ++j) {
+      F.x += sh[wib][0][j];
+      F.y += sh[wib][1][j];
+      F.z += sh[wib][2][j];
+      Tq.x += sh[wib][3][j];
+      Tq.y += sh[wib][4][j];
+      Tq.z += sh[wib][5][j];
+    }
+    __syncwarp();
+  }
+
+  // ---- per-particle epilogue: walls, body forces, drag, integration ----
+  float my_disp2 = -1.f;
   bool coupled = false;
-
-  if (p < d.N) {
-    double4 P = d.pos[cur][p];
-    double4 Vd = d.vel[cur][p];
-    double4 Wd = d.omg[cur][p];
-    const int si = d.sample[pc][p];
-    my_sample = si;
+  if (valid) {
     const SampleDev& S = d.sp[si];
+    double4 P;
+    if constexpr (MIXED) P = d.pos[cur][p];
+    else P = me.P;
     const bool active = P.w > 0.0;
     if (!active) {
       if (MODE != MODE_FORCES) {
         d.pos[nxt][p] = P;
-        d.vel[nxt][p] = Vd;
-        d.omg[nxt][p] = Wd;
+        d.vel[nxt][p] = d.vel[cur][p];
+        d.omg[nxt][p] = d.omg[cur][p];
         d.posq[nxt][p] = d.posq[cur][p];
         d.velf[nxt][p] = d.velf[cur][p];
         d.omgf[nxt][p] = d.omgf[cur][p];
@@ -250,379 +594,213 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
         d.T[p] = make_double4(0, 0, 0, 0);
       }
     } else {
-      const T Es = T(S.Es), Gs = T(S.Gs), beta = T(S.beta), mu = T(S.mu), gam = T(S.gamma);
-      const T dt = T(S.dt);
-      V3<T> F = v3<T>(0, 0, 0), Tq = v3<T>(0, 0, 0);
-      // own particle in working precision
+      double4 Vd, Wd;
       T Ri, mi;
       V3<T> vi, wi;
-      int4 pq;
-      if (MIXED) {
-        pq = d.posq[cur][p];
-        float4 a = d.velf[cur][p];
-        float4 b = d.omgf[cur][p];
-        vi = v3<T>(a.x, a.y, a.z);
-        Ri = a.w;
-        wi = v3<T>(b.x, b.y, b.z);
-        mi = b.w;
+      if constexpr (MIXED) {
+        Vd = d.vel[cur][p];
+        Wd = d.omg[cur][p];
+        vi = v3<T>(me.va.x, me.va.y, me.va.z);
+        wi = v3<T>(me.wa.x, me.wa.y, me.wa.z);
+        Ri = me.va.w;
+        mi = me.wa.w;
       } else {
+        Vd = me.V;
+        Wd = me.W;
         vi = v3<T>(Vd.x, Vd.y, Vd.z);
         wi = v3<T>(Wd.x, Wd.y, Wd.z);
         Ri = P.w;
         mi = 1.0 / Vd.w;
       }
-      const uint32_t ncand = d.cnt[rc][p];
-      for (uint32_t k = 0; k < ncand; ++k) {
-        const size_t idx = (size_t)k * Npad + p;
-        uint32_t pf;
-        V3<T> xi;
-        if (MIXED) {
-          uint4 r = reinterpret_cast<const uint4*>(d.rec[rc])[idx];
-          pf = r.x;
-          xi = v3<T>(__uint_as_float(r.y), __uint_as_float(r.z), __uint_as_float(r.w));
-        } else {
-          const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + idx;
-          int4 h0 = *reinterpret_cast<const int4*>(rr);
-          double2 h1 = *(reinterpret_cast<const double2*>(rr) + 1);
-          pf = (uint32_t)h0.x;
-          xi = v3<T>(__hiloint2double(h0.w, h0.z), h1.x, h1.y);
-        }
-        const int q = (int)(pf & REC_IDX);
-        bool bonded = (pf & REC_BOND) != 0u;
-        const bool had_state = (pf & (REC_BOND | REC_ACTIVE)) != 0u || xi.x != T(0) ||
-                               xi.y != T(0) || xi.z != T(0);
-        bool touching = false, act = false;
-        T delta = 0, Rj = 0, mj = 0;
-        V3<T> n = v3<T>(0, 0, 0), vj = v3<T>(0, 0, 0), wj = v3<T>(0, 0, 0);
-        double4 Q;
-        bool q_active;
-        if (MIXED) {
-          int4 qq = d.posq[cur][q];
-          q_active = qq.w > 0;
-          if (q_active) {
-            const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
-            const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
-            const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
-            const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
-                                          (unsigned long long)((long long)dy * dy) +
-                                          (unsigned long long)((long long)dz * dz);
-            const unsigned Sq = (unsigned)pq.w + (unsigned)qq.w;
-            const unsigned long long S2 = (unsigned long long)Sq * Sq;
-            const unsigned long long band = 16ull * Sq + 256ull;
-            bool need_exact = false;
-            if (d2 > S2 + band) {
-              touching = false;
-            } else if (d2 + band < S2) {
-              touching = true;
-            } else {
-              need_exact = true;
-            }
-            if (!bonded && !touching && !need_exact) {
-              act = false;
-            } else {
-              const float dn = sqrtf(ull2f(d2));
-              float du;
-              if (d2 < (1ull << 62))
-                du = ll2f((long long)S2 - (long long)d2) / ((float)Sq + dn);
-              else
-                du = (float)Sq - dn;
-              delta = du * S.dq_f;
-              const float invd = 1.0f / dn;
-              n = v3<T>(dx * invd, dy * invd, dz * invd);
-              float4 qa = d.velf[cur][q];
-              float4 qb = d.omgf[cur][q];
-              vj = v3<T>(qa.x, qa.y, qa.z);
-              Rj = qa.w;
-              wj = v3<T>(qb.x, qb.y, qb.z);
-              mj = qb.w;
-              const T Rs = Ri * Rj / (Ri + Rj);
-              double d2e = 0.0, Se = 0.0;
-              bool have_exact = false;
-              if (need_exact) {
-                exact_geometry(S, P, d.pos[cur][q], &d2e, &Se);
-                have_exact = true;
-                touching = d2e < __dmul_rn(Se, Se);
-              }
-              if (bonded) {
-                bool broken;
-                float dC = 0.0f, bandf;
-                if (gam > T(0)) {
-                  float xs = cbrtf(PI_F * PI_F * gam * gam * Rs / (Es * Es));
-                  dC = -0.57235712127666594f * xs;
-                  bandf = 4.0f * S.dq_f + 2e-5f * fabsf(dC);
-                } else {
-                  bandf = 4.0f * S.dq_f;
-                }
-                if (delta < dC - bandf) {
-                  broken = true;
-                } else if (delta > dC + bandf) {
-                  broken = false;
-                } else {
-                  if (!have_exact) {
-                    exact_geometry(S, P, d.pos[cur][q], &d2e, &Se);
-                    have_exact = true;
-                    touching = d2e < __dmul_rn(Se, Se);
-                  }
-                  const double Rid = fabs(P.w), Rjd = fabs(d.pos[cur][q].w);
-                  const double Rsd = __dmul_rn(Rid, Rjd) / __dadd_rn(Rid, Rjd);
-                  broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, S.gamma);
-                }
-                if (broken) bonded = false;
-              }
-              act = bonded || touching;
-              if (act) {
-                const T ms = mi * mj / (mi + mj);
-                V3<T> vrel = v3<T>(vj.x - vi.x, vj.y - vi.y, vj.z - vi.z);
-                V3<T> rw = v3<T>(Ri * wi.x + Rj * wj.x, Ri * wi.y + Rj * wj.y, Ri * wi.z + Rj * wj.z);
-                V3<T> rwn = cross3(rw, n);
-                V3<T> vc = v3<T>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
-                V3<T> Fi, Ft;
-                contact_law<T>(delta, n, vrel, vc, Rs, ms, gam, bonded, Es, Gs, beta, mu, dt,
-                               S.coulomb_mode, xi, Fi, Ft);
-                V3<T> nFt = cross3(n, Ft);
-                F.x += Fi.x;
-                F.y += Fi.y;
-                F.z += Fi.z;
-                Tq.x += Ri * nFt.x;
-                Tq.y += Ri * nFt.y;
-                Tq.z += Ri * nFt.z;
-              }
-            }
-          }
-        } else {
-          Q = d.pos[cur][q];
-          q_active = Q.w > 0.0;
-          if (q_active) {
-            double dx = __dsub_rn(Q.x, P.x), dy = __dsub_rn(Q.y, P.y), dz = __dsub_rn(Q.z, P.z);
-            if (S.kind == CGDEM_PERIODIC_BOX) {
-              dx = min_image(dx, S.L[0]);
-              dy = min_image(dy, S.L[1]);
-              dz = min_image(dz, S.L[2]);
-            }
-            const double d2 =
-                __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            const double Sd = __dadd_rn(P.w, Q.w);
-            touching = d2 < __dmul_rn(Sd, Sd);
-            if (bonded || touching) {
-              const double dist = sqrt(d2);
-              const double Rs = __dmul_rn(P.w, Q.w) / __dadd_rn(P.w, Q.w);
-              delta = __dsub_rn(Sd, dist);
-              if (bonded && bond_breaks_exact(delta, Rs, S.Es, S.gamma)) bonded = false;
-              act = bonded || touching;
-              if (act && dist > 0.0) {
-                double4 QV = d.vel[cur][q];
-                double4 QW = d.omg[cur][q];
-                Rj = Q.w;
-                mj = 1.0 / QV.w;
-                n = v3<T>(dx / dist, dy / dist, dz / dist);
-                vj = v3<T>(QV.x, QV.y, QV.z);
-                wj = v3<T>(QW.x, QW.y, QW.z);
-                const T ms = mi * mj / (mi + mj);
-                V3<T> vrel = v3<T>(vj.x - vi.x, vj.y - vi.y, vj.z - vi.z);
-                V3<T> rw = v3<T>(Ri * wi.x + Rj * wj.x, Ri * wi.y + Rj * wj.y, Ri * wi.z + Rj * wj.z);
-                V3<T> rwn = cross3(rw, n);
-                V3<T> vc = v3<T>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
-                V3<T> Fi, Ft;
-                contact_law<T>(delta, n, vrel, vc, Rs, ms, gam, bonded, Es, Gs, beta, mu, dt,
-                               S.coulomb_mode, xi, Fi, Ft);
-                V3<T> nFt = cross3(n, Ft);
-                F.x += Fi.x;
-                F.y += Fi.y;
-                F.z += Fi.z;
-                Tq.x += Ri * nFt.x;
-                Tq.y += Ri * nFt.y;
-                Tq.z += Ri * nFt.z;
-              } else if (act) {
-                act = false;  // coincident centres: no normal defined
-              }
-            }
-          }
-        }
-        // write the record back when its state changed
-        if (act) {
-          uint32_t npf = (uint32_t)q | REC_ACTIVE | (bonded ? REC_BOND : 0u);
-          if (MIXED) {
-            reinterpret_cast<uint4*>(d.rec[rc])[idx] =
-                make_uint4(npf, __float_as_uint((float)xi.x), __float_as_uint((float)xi.y),
-                           __float_as_uint((float)xi.z));
-          } else {
-            RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
-            double xx = (double)xi.x;
-            *reinterpret_cast<int4*>(rr) =
-                make_int4((int)npf, 0, __double2loint(xx), __double2hiint(xx));
-            *(reinterpret_cast<double2*>(rr) + 1) = make_double2((double)xi.y, (double)xi.z);
-          }
-        } else if (had_state) {
-          if (MIXED) {
-            reinterpret_cast<uint4*>(d.rec[rc])[idx] = make_uint4((uint32_t)q, 0u, 0u, 0u);
-          } else {
-            RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
-            *reinterpret_cast<int4*>(rr) = make_int4(q, 0, 0, 0);
-            *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
-          }
-        }
+      const float xf = d2f_bits(P.x), yf = d2f_bits(P.y), zf = d2f_bits(P.z);
+      T Es, Gs, beta, mu, dt;
+      if constexpr (MIXED) {
+        Es = S.Es_f; Gs = S.Gs_f; beta = S.beta_f; mu = S.mu_f32; dt = S.dt_f;
+      } else {
+        Es = S.Es; Gs = S.Gs; beta = S.beta; mu = S.mu; dt = S.dt;
       }
-
-      // walls of the cylindrical sample
       if (S.kind == CGDEM_CYLINDER) {
         V3<T> hist[3];
         bool changed[3] = {false, false, false};
-        if (MIXED) {
 #pragma unroll
-          for (int w = 0; w < 3; ++w) {
-            float4 h = d.wallhf[pc][(size_t)w * Npad + p];
+        for (int w = 0; w < 3; ++w) {
+          if constexpr (MIXED) {
+            const float4 h = d.wallhf[pc][(size_t)w * d.Npad + p];
             hist[w] = v3<T>(h.x, h.y, h.z);
-          }
-        } else {
-#pragma unroll
-          for (int w = 0; w < 3; ++w) {
-            double4 h = d.wallh[pc][(size_t)w * Npad + p];
+          } else {
+            const double4 h = d.wallh[pc][(size_t)w * d.Npad + p];
             hist[w] = v3<T>(h.x, h.y, h.z);
           }
         }
-        wall_contacts<T>(S, P, vi, wi, Ri, mi, Es, Gs, beta, mu, dt, hist, F, Tq, changed);
+        wall_contacts<T>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt, hist, F, Tq, changed);
 #pragma unroll
         for (int w = 0; w < 3; ++w) {
           if (!changed[w]) continue;
-          if (MIXED)
-            d.wallhf[pc][(size_t)w * Npad + p] =
+          if constexpr (MIXED)
+            d.wallhf[pc][(size_t)w * d.Npad + p] =
                 make_float4((float)hist[w].x, (float)hist[w].y, (float)hist[w].z, 0.f);
           else
-            d.wallh[pc][(size_t)w * Npad + p] =
+            d.wallh[pc][(size_t)w * d.Npad + p] =
                 make_double4((double)hist[w].x, (double)hist[w].y, (double)hist[w].z, 0.0);
         }
       }
-
       // gravity, buoyancy (Eq. 1) and drag (Eq. 8-11)
       {
-        const T rho_s = T(S.rho);
+        T rho_s, rf, g0, g1, g2, nmin, muf;
+        if constexpr (MIXED) {
+          rho_s = S.rho_s_f; rf = S.rho_f32; g0 = S.g_f[0]; g1 = S.g_f[1]; g2 = S.g_f[2];
+          nmin = S.n_min_f; muf = S.muf_f32;
+        } else {
+          rho_s = S.rho; rf = S.rho_f; g0 = S.g[0]; g1 = S.g[1]; g2 = S.g[2];
+          nmin = S.n_min; muf = S.mu_f;
+        }
         const T Vp = mi / rho_s;
-        const T rf = T(S.rho_f);
-        F.x += mi * T(S.g[0]);
-        F.y += mi * T(S.g[1]);
-        F.z += mi * T(S.g[2]);
+        F.x += mi * g0;
+        F.y += mi * g1;
+        F.z += mi * g2;
         if (S.use_buoyancy) {
-          F.x -= rf * Vp * T(S.g[0]);
-          F.y -= rf * Vp * T(S.g[1]);
-          F.z -= rf * Vp * T(S.g[2]);
+          F.x -= rf * Vp * g0;
+          F.y -= rf * Vp * g1;
+          F.z -= rf * Vp * g2;
         }
         if (S.use_drag) {
           const int fc = d.fcell[pc][p];
           const unsigned long long Sc = d.vf[vfc][fc];
-          T nc = T(1) - (MIXED ? T(ull2f(Sc)) : T((double)Sc)) * T(9.094947017729282379150390625e-13);
-          if (nc < T(S.n_min)) nc = T(S.n_min);
+          T scount;
+          if constexpr (MIXED) scount = u64_to_f(Sc);
+          else scount = (double)Sc;
+          T nc = T(1) - scount * T(9.094947017729282379150390625e-13);  // 2^-40
+          if (nc < nmin) nc = nmin;
           if (nc > T(1)) nc = T(1);
           V3<T> U;
-          if (MIXED) {
-            float4 u = d.Usf[fc];
+          if constexpr (MIXED) {
+            const float4 u = d.Usf[fc];
             U = v3<T>(u.x, u.y, u.z);
           } else {
-            double4 u = d.Us[fc];
+            const double4 u = d.Us[fc];
             U = v3<T>(u.x, u.y, u.z);
           }
-          V3<T> w = v3<T>(U.x / nc - vi.x, U.y / nc - vi.y, U.z / nc - vi.z);
-          V3<T> fd = drag_force<T>(rf, T(S.mu_f), T(2) * Ri, w, nc);
+          const V3<T> w = v3<T>(U.x / nc - vi.x, U.y / nc - vi.y, U.z / nc - vi.z);
+          const V3<T> fd = drag_force<T>(rf, muf, T(2) * Ri, w, nc);
           F.x += fd.x;
           F.y += fd.y;
           F.z += fd.z;
         }
       }
-
-      const double Fx = (double)F.x, Fy = (double)F.y, Fz = (double)F.z;
-      const double Tx = (double)Tq.x, Ty = (double)Tq.y, Tz = (double)Tq.z;
-      if (!isfinite(Fx + Fy + Fz + Tx + Ty + Tz)) latch(ctl, ST_NONFINITE);
+      if (!isfinite(F.x + F.y + F.z + Tq.x + Tq.y + Tq.z)) latch(ctl, ST_NONFINITE);
 
       if (MODE == MODE_FORCES) {
-        d.F[p] = make_double4(Fx, Fy, Fz, 0.0);
-        d.T[p] = make_double4(Tx, Ty, Tz, 0.0);
+        d.F[p] = make_double4((double)F.x, (double)F.y, (double)F.z, 0.0);
+        d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
       } else {
-        // velocity Verlet: complete this step's kick, then (MODE_MID) the
-        // next step's half kick and drift.
-        const double h = S.half_dt;
-        const double im = Vd.w, iI = Wd.w;
+        // outlet (produced sand, Eq. 40): float filter, FP64 decision
+        const bool removed = S.kind == CGDEM_CYLINDER && zf < -1.999f * d2f_bits(P.w) &&
+                             P.z < -2.0 * P.w;
+        if (removed) d.removed_step[d.id[pc][p]] = (int)m_step;
         double vx, vy, vz, wx, wy, wz;
-        bool removed = false;
-        if (MODE == MODE_CANON || !MIXED) {
-          vx = Vd.x + h * (Fx * im);
-          vy = Vd.y + h * (Fy * im);
-          vz = Vd.z + h * (Fz * im);
-          wx = Wd.x + h * (Tx * iI);
-          wy = Wd.y + h * (Ty * iI);
-          wz = Wd.z + h * (Tz * iI);
-        }
-        if (S.kind == CGDEM_CYLINDER && P.z < -2.0 * P.w) {  // outlet (Eq. 40 produced sand)
-          removed = true;
-          d.removed_step[d.id[pc][p]] = (int)m_step;
+        if constexpr (MIXED) {
+          // FP32 force increments added to the FP64 state
+          const float im = 1.0f / me.wa.w;
+          const float iI = d2f_bits(Wd.w);
+          const float c = (MODE == MODE_MID ? S.dt_f : 0.5f * S.dt_f);
+          vx = Vd.x + f2d_bits(c * im * (float)F.x);
+          vy = Vd.y + f2d_bits(c * im * (float)F.y);
+          vz = Vd.z + f2d_bits(c * im * (float)F.z);
+          wx = Wd.x + f2d_bits(c * iI * (float)Tq.x);
+          wy = Wd.y + f2d_bits(c * iI * (float)Tq.y);
+          wz = Wd.z + f2d_bits(c * iI * (float)Tq.z);
+        } else {
+          const double h = S.half_dt, im = Vd.w, iI = Wd.w;
+          vx = Vd.x + h * (F.x * im);
+          vy = Vd.y + h * (F.y * im);
+          vz = Vd.z + h * (F.z * im);
+          wx = Wd.x + h * (Tq.x * iI);
+          wy = Wd.y + h * (Tq.y * iI);
+          wz = Wd.z + h * (Tq.z * iI);
+          if (MODE == MODE_MID) {
+            vx += h * (F.x * im);
+            vy += h * (F.y * im);
+            vz += h * (F.z * im);
+            wx += h * (Tq.x * iI);
+            wy += h * (Tq.y * iI);
+            wz += h * (Tq.z * iI);
+          }
         }
         if (MODE == MODE_CANON) {
-          d.F[p] = make_double4(Fx, Fy, Fz, 0.0);
-          d.T[p] = make_double4(Tx, Ty, Tz, 0.0);
+          d.F[p] = make_double4((double)F.x, (double)F.y, (double)F.z, 0.0);
+          d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
           double4 Pn = P;
-          if (removed) Pn.w = -P.w;
+          int4 pqn = d.posq[cur][p];
+          if (removed) {
+            Pn.w = -P.w;
+            pqn.w = 0;
+          }
           d.pos[nxt][p] = Pn;
           d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
           d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
-          int4 pqn = d.posq[cur][p];
-          if (removed) pqn.w = 0;
           d.posq[nxt][p] = pqn;
-          d.velf[nxt][p] = make_float4((float)vx, (float)vy, (float)vz, (float)P.w);
-          d.omgf[nxt][p] = make_float4((float)wx, (float)wy, (float)wz, (float)(1.0 / Vd.w));
+          const float4 va = d.velf[cur][p], wa = d.omgf[cur][p];
+          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), va.w);
+          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), wa.w);
+        } else if (removed) {
+          double4 Pn = P;
+          Pn.w = -P.w;
+          d.pos[nxt][p] = Pn;
+          d.vel[nxt][p] = Vd;
+          d.omg[nxt][p] = Wd;
+          int4 pqn = d.posq[cur][p];
+          pqn.w = 0;
+          d.posq[nxt][p] = pqn;
+          d.velf[nxt][p] = d.velf[cur][p];
+          d.omgf[nxt][p] = d.omgf[cur][p];
         } else {
-          if (MIXED) {
-            // both half kicks at once: v(n+1/2) = v(n-1/2) + dt F / m
-            const double c = S.dt * im, cI = S.dt * iI;
-            vx = Vd.x + c * Fx;
-            vy = Vd.y + c * Fy;
-            vz = Vd.z + c * Fz;
-            wx = Wd.x + cI * Tx;
-            wy = Wd.y + cI * Ty;
-            wz = Wd.z + cI * Tz;
-          } else {
-            vx += h * (Fx * im);
-            vy += h * (Fy * im);
-            vz += h * (Fz * im);
-            wx += h * (Tx * iI);
-            wy += h * (Ty * iI);
-            wz += h * (Tz * iI);
-          }
-          if (removed) {
-            double4 Pn = P;
-            Pn.w = -P.w;
-            d.pos[nxt][p] = Pn;
-            d.vel[nxt][p] = Vd;
-            d.omg[nxt][p] = Wd;
-            int4 pqn = d.posq[cur][p];
-            pqn.w = 0;
-            d.posq[nxt][p] = pqn;
-            d.velf[nxt][p] = d.velf[cur][p];
-            d.omgf[nxt][p] = d.omgf[cur][p];
-          } else {
-            double x = P.x + S.dt * vx, y = P.y + S.dt * vy, z = P.z + S.dt * vz;
-            if (S.kind == CGDEM_PERIODIC_BOX) {
+          double x = P.x + S.dt * vx, y = P.y + S.dt * vy, z = P.z + S.dt * vz;
+          float nxf = d2f_bits(x), nyf = d2f_bits(y), nzf = d2f_bits(z);
+          if (S.kind == CGDEM_PERIODIC_BOX) {
+            const float Lf = S.L_f[0], eps = 1e-4f * Lf;
+            if (nxf < eps || nxf > Lf - eps) {
               if (x >= S.L[0]) x -= S.L[0]; else if (x < 0.0) x += S.L[0];
+              nxf = d2f_bits(x);
+            }
+            if (nyf < eps || nyf > Lf - eps) {
               if (y >= S.L[1]) y -= S.L[1]; else if (y < 0.0) y += S.L[1];
+              nyf = d2f_bits(y);
+            }
+            if (nzf < eps || nzf > Lf - eps) {
               if (z >= S.L[2]) z -= S.L[2]; else if (z < 0.0) z += S.L[2];
+              nzf = d2f_bits(z);
             }
-            d.pos[nxt][p] = make_double4(x, y, z, P.w);
-            d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
-            d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
-            int4 pqn = d.posq[cur][p];
-            pqn.x = to_q(x, S.inv_dq);
-            pqn.y = to_q(y, S.inv_dq);
-            pqn.z = to_q(z, S.inv_dq);
-            d.posq[nxt][p] = pqn;
-            d.velf[nxt][p] = make_float4((float)vx, (float)vy, (float)vz, (float)P.w);
-            d.omgf[nxt][p] = make_float4((float)wx, (float)wy, (float)wz, (float)(1.0 / Vd.w));
-            const double ddx = S.dt * vx, ddy = S.dt * vy, ddz = S.dt * vz;
-            my_disp2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            const int fc = fluid_cell_of(S, x, y, z);
-            d.fcell[pc][p] = fc;
-            if (m_step % S.couple_every == 0) {
-              coupled = true;
-              if (S.vf_mode == 0) {
-                atomicAdd(&d.vf[(vfc + 1) % 3][fc], d.vq[pc][p]);
-              }
-            }
+          }
+          d.pos[nxt][p] = make_double4(x, y, z, P.w);
+          d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
+          d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
+          int4 pqn;
+          pqn.x = to_q(x, S.inv_dq);
+          pqn.y = to_q(y, S.inv_dq);
+          pqn.z = to_q(z, S.inv_dq);
+          float Rf, mf;
+          if constexpr (MIXED) {
+            pqn.w = me.pq.w;
+            Rf = me.va.w;
+            mf = me.wa.w;
+          } else {
+            pqn.w = d.posq[cur][p].w;
+            Rf = d.velf[cur][p].w;
+            mf = d.omgf[cur][p].w;
+          }
+          d.posq[nxt][p] = pqn;
+          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), Rf);
+          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), mf);
+          const int4 ref = d.posq_ref[p];
+          const float ex = (float)(int)((uint32_t)pqn.x - (uint32_t)ref.x);
+          const float ey = (float)(int)((uint32_t)pqn.y - (uint32_t)ref.y);
+          const float ez = (float)(int)((uint32_t)pqn.z - (uint32_t)ref.z);
+          my_disp2 = ex * ex + ey * ey + ez * ez;
+          const int fc = fluid_cell_fast(S, x, y, z, nxf, nyf, nzf);
+          d.fcell[pc][p] = fc;
+          if (couple_next) {
+            coupled = true;
+            if (S.vf_mode == 0) atomicAdd(&d.vf[(vfc + 1) % 3][fc], d.vq[pc][p]);
           }
         }
       }
@@ -631,38 +809,33 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
 
   if (MODE != MODE_MID) return;
 
-  // ---- per-sample displacement bound, porosity rotation, step bookkeeping
-  // zero the porosity buffer that the step after next will fill
+  // ---- bookkeeping: displacement since rebuild, porosity rotation, step ----
   {
     unsigned long long* z = d.vf[(vfc + 2) % 3];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.Cf_total; c += gridDim.x * blockDim.x)
       z[c] = 0ull;
   }
-  if (coupled) s_couple_any = 1;
-  // block-uniform sample: one atomic per block
-  if (my_sample >= 0) atomicCAS(&s_uniform_sample, -2, my_sample);
-  __syncthreads();
-  const int us = s_uniform_sample;
-  bool uniform = __syncthreads_and(my_sample < 0 || my_sample == us);
-  if (my_disp2 >= 0.0) {
-    if (uniform)
-      atomicMax(&s_vmax, (unsigned long long)__double_as_longlong(my_disp2));
-    else
-      atomic_max_pos(&d.vmax2[my_sample], my_disp2);
+  const int s0 = __shfl_sync(FULL, si, 0);
+  const bool uniform = __all_sync(FULL, !valid || si == s0);
+  float md = my_disp2;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
+  if (uniform) {
+    if (lane == 0 && md >= 0.f) atomicMax(&d.dmax2[s0], __float_as_uint(md));
+  } else if (my_disp2 >= 0.f) {
+    atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (uniform && us >= 0 && s_vmax != 0ull) atomicMax(&d.vmax2[us], s_vmax);
-    if (s_couple_any) atomicOr(&ctl->coupled, 1u);
+  const bool any_coupled = __any_sync(FULL, coupled);
+  if (lane == 0) {
+    if (any_coupled) atomicOr(&ctl->coupled, 1u);
     __threadfence();
-    unsigned t = atomicAdd(&ctl->block_counter, 1u);
-    if (t == gridDim.x - 1) {
+    const unsigned total_warps = (unsigned)(d.Npad >> 5);
+    const unsigned t = atomicAdd(&ctl->block_counter, 1u);
+    if (t == total_warps - 1) {
       __threadfence();
       for (int s = 0; s < d.n_samples; ++s) {
-        unsigned long long b = atomicExch(&d.vmax2[s], 0ull);
-        double dd = d.disp[s] + sqrt(__longlong_as_double((long long)b));
-        d.disp[s] = dd;
-        if (2.0 * dd > d.sp[s].rebuild_disp) ctl->rebuild = 1;
+        const unsigned b = atomicAdd(&d.dmax2[s], 0u);
+        if (__uint_as_float(b) > d.sp[s].rebuild_q2) ctl->rebuild = 1;
       }
       if (atomicExch(&ctl->coupled, 0u)) ctl->vf_cur = (vfc + 1) % 3;
       ctl->cur = nxt;
@@ -673,7 +846,7 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
   }
 }
 
-// MODE_CANON / MODE_FORCES bookkeeping kernel (single thread).
+// MODE_CANON bookkeeping kernel (single thread).
 __global__ void k_after_canon(Dev d) {
   Ctl* ctl = d.ctl;
   ctl->cur ^= 1;
@@ -681,16 +854,17 @@ __global__ void k_after_canon(Dev d) {
 }
 
 void launch_forces(const Dev& d, int mode, int block, cudaStream_t s) {
-  const int grid = (d.N + block - 1) / block;
-  if (grid == 0) return;
+  (void)block;
+  const int grid = (d.Npad + FORCE_BLOCK - 1) / FORCE_BLOCK;
+  if (d.N == 0) return;
   if (d.mixed) {
-    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES><<<grid, block, 0, s>>>(d);
-    else if (mode == MODE_MID) k_forces<true, MODE_MID><<<grid, block, 0, s>>>(d);
-    else k_forces<true, MODE_CANON><<<grid, block, 0, s>>>(d);
+    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES><<<grid, FORCE_BLOCK, 0, s>>>(d);
+    else if (mode == MODE_MID) k_forces<true, MODE_MID><<<grid, FORCE_BLOCK, 0, s>>>(d);
+    else k_forces<true, MODE_CANON><<<grid, FORCE_BLOCK, 0, s>>>(d);
   } else {
-    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES><<<grid, block, 0, s>>>(d);
-    else if (mode == MODE_MID) k_forces<false, MODE_MID><<<grid, block, 0, s>>>(d);
-    else k_forces<false, MODE_CANON><<<grid, block, 0, s>>>(d);
+    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES><<<grid, FORCE_BLOCK, 0, s>>>(d);
+    else if (mode == MODE_MID) k_forces<false, MODE_MID><<<grid, FORCE_BLOCK, 0, s>>>(d);
+    else k_forces<false, MODE_CANON><<<grid, FORCE_BLOCK, 0, s>>>(d);
   }
   if (mode == MODE_CANON) k_after_canon<<<1, 1, 0, s>>>(d);
 }

@@ -28,57 +28,91 @@ __global__ void k_rb_bin(Dev d) {
   d.pslot[p] = atomicAdd(&d.cell_count[c], 1u);
 }
 
-// Exclusive scan of cell_count[0..C] into cell_start[0..C+1]; clears counts.
-// One block of 1024 threads walks the array in tiles, carrying the total.
-__global__ void __launch_bounds__(1024) k_rb_scan(Dev d) {
-  if (!d.ctl->rebuild) return;
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  const int n = d.C_total + 1;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < n; base += 1024 * 4) {
-    uint32_t v[4];
-    uint32_t local = 0;
+// Exclusive scan of cell_count[0..C] into cell_start[0..C+1] in three passes
+// (tile sums, scan of the tile sums, tile scans), clearing the counts.
+constexpr int SCAN_T = 256, SCAN_V = 8, SCAN_TILE = SCAN_T * SCAN_V;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_sums,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = x;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int i = base + threadIdx.x * 4 + j;
-      v[j] = i < n ? d.cell_count[i] : 0u;
-      if (i < n) d.cell_count[i] = 0u;
-      local += v[j];
-    }
-    // inclusive scan of per-thread totals within the warp
-    uint32_t x = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < nw ? warp_sums[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      uint32_t w = warp_sums[lane];
+    if (lane < nw) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t before = wid > 0 ? warp_sums[wid - 1] : 0u;
+  *total = warp_sums[nw - 1];
+  __syncthreads();
+  return before + incl - x;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_rb_scan_tiles(Dev d, uint32_t* tile_sums) {
+  if (!d.ctl->rebuild) return;
+  __shared__ uint32_t ws[32];
+  const int n = d.C_total + 1;
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+  uint32_t s = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      warp_sums[lane] = w;
-    }
+  for (int j = 0; j < SCAN_V; ++j) s += base + j < n ? d.cell_count[base + j] : 0u;
+  uint32_t tot;
+  block_exclusive_scan(s, ws, &tot);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_rb_scan_sums(Dev d, uint32_t* tile_sums, int ntiles) {
+  if (!d.ctl->rebuild) return;
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+    const int i = b0 + threadIdx.x;
+    const uint32_t v = i < ntiles ? tile_sums[i] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(v, ws, &tot);
+    if (i < ntiles) tile_sums[i] = carry + ex;
     __syncthreads();
-    uint32_t excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + (x - local);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int i = base + threadIdx.x * 4 + j;
-      if (i < n) d.cell_start[i] = excl;
-      excl += v[j];
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = excl;
+    if (threadIdx.x == 0) carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) d.cell_start[n] = carry;
+  if (threadIdx.x == 0) d.cell_start[d.C_total + 1] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_rb_scan_apply(Dev d, const uint32_t* tile_sums) {
+  if (!d.ctl->rebuild) return;
+  __shared__ uint32_t ws[32];
+  const int n = d.C_total + 1;
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+  uint32_t v[SCAN_V];
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_V; ++j) {
+    v[j] = base + j < n ? d.cell_count[base + j] : 0u;
+    s += v[j];
+  }
+  uint32_t tot;
+  uint32_t ex = block_exclusive_scan(s, ws, &tot) + tile_sums[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < SCAN_V; ++j) {
+    if (base + j < n) {
+      d.cell_start[base + j] = ex;
+      d.cell_count[base + j] = 0u;
+    }
+    ex += v[j];
+  }
 }
 
 __global__ void k_rb_scatter(Dev d) {
@@ -116,6 +150,7 @@ __global__ void k_rb_permute(Dev d) {
   if (p >= d.N) return;
   const uint32_t o = d.perm[p];
   d.inv_perm[o] = (uint32_t)p;
+  d.cand_n[p] = 0u;
   double4 P = d.pos[cur][o];
   d.pos[nxt][p] = P;
   d.vel[nxt][p] = d.vel[cur][o];
@@ -162,126 +197,181 @@ __global__ void k_rb_ft_store(Dev d) {
   d.T[p] = st[d.Npad + p];
 }
 
-// Neighbour-cell scan in the new order and carry of contact history.
-// Candidates: d^2 < (Ri + Rj + skin)^2 in fixed point (exact integer test).
-template <bool MIXED>
-__global__ void k_rb_search(Dev d) {
+// Candidate pairs: d^2 < (Ri + Rj + skin)^2 in fixed point (exact integer
+// test).  Each pair is found once, from its larger sphere (ties: higher
+// index), whose stencil (2 R + skin) covers the pair whatever the partner's
+// size; the cell edge can then follow the typical rather than the largest
+// sphere.  The pair goes into both spheres' lists (atomic slots); the lists
+// are sorted by partner afterwards, so the result does not depend on the
+// order of the atomics.
+__global__ void k_rb_pairs(Dev d) {
   if (!d.ctl->rebuild) return;
-  const int cur = d.ctl->cur, nxt = cur ^ 1;
+  const int nxt = d.ctl->cur ^ 1;
   const int pn = d.ctl->pcur ^ 1;
-  const int rc = d.ctl->rec_cur, rn = rc ^ 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= d.N) return;
-  const int Npad = d.Npad, cap = d.cap;
   const int4 pq = d.posq[nxt][p];
-  uint32_t count = 0;
-  if (pq.w > 0) {
-    const int s = d.sample[pn][p];
-    const SampleDev& S = d.sp[s];
-    const uint32_t o = d.perm[p];
-    const int lc = (int)d.pcell[o] - S.cell_off;
-    const int cx = lc % S.nc[0], cy = (lc / S.nc[0]) % S.nc[1], cz = lc / (S.nc[0] * S.nc[1]);
-    const bool per = S.kind == CGDEM_PERIODIC_BOX;
-    int lists[3][3], nl[3];
-    const int cc[3] = {cx, cy, cz};
+  if (pq.w <= 0) return;
+  const int Npad = d.Npad, cap = d.cap;
+  const int s = d.sample[pn][p];
+  const SampleDev& S = d.sp[s];
+  const uint32_t o = d.perm[p];
+  const int lc = (int)d.pcell[o] - S.cell_off;
+  const int cc[3] = {lc % S.nc[0], (lc / S.nc[0]) % S.nc[1], lc / (S.nc[0] * S.nc[1])};
+  const bool per = S.kind == CGDEM_PERIODIC_BOX;
+  const float reach = 2.0f * (float)pq.w * S.dq_f + S.skin_f;
+  int lo[3], hi[3];
+  bool all[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      nl[k] = 0;
-      const int ncs = S.nc[k];
-      if (per && ncs < 3) {
-        for (int a = 0; a < ncs; ++a) lists[k][nl[k]++] = a;
-      } else {
-        for (int off = -1; off <= 1; ++off) {
-          int a = cc[k] + off;
-          if (per) a = (a + ncs) % ncs;
-          else if (a < 0 || a >= ncs) continue;
-          lists[k][nl[k]++] = a;
-        }
-      }
+  for (int k = 0; k < 3; ++k) {
+    const int r = (int)ceilf(reach * S.c_inv_h_f[k] * 1.000001f);
+    all[k] = per && 2 * r + 1 >= S.nc[k];
+    lo[k] = all[k] ? 0 : cc[k] - r;
+    hi[k] = all[k] ? S.nc[k] - 1 : cc[k] + r;
+    if (!per) {
+      lo[k] = max(lo[k], 0);
+      hi[k] = min(hi[k], S.nc[k] - 1);
     }
-    for (int iz = 0; iz < nl[2]; ++iz)
-      for (int iy = 0; iy < nl[1]; ++iy)
-        for (int ix = 0; ix < nl[0]; ++ix) {
-          const int c = S.cell_off + (lists[2][iz] * S.nc[1] + lists[1][iy]) * S.nc[0] + lists[0][ix];
-          const uint32_t j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
-          for (uint32_t q = j0; q < j1; ++q) {
-            if ((int)q == p) continue;
-            const int4 qq = d.posq[nxt][q];
-            if (qq.w <= 0) continue;
-            const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
-            const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
-            const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
-            const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
-                                          (unsigned long long)((long long)dy * dy) +
-                                          (unsigned long long)((long long)dz * dz);
-            const unsigned long long Sq =
-                (unsigned long long)(unsigned)pq.w + (unsigned)qq.w + (unsigned)S.skin_q;
-            if (d2 < Sq * Sq) {
-              if (count < (uint32_t)cap) {
-                const size_t idx = (size_t)count * Npad + p;
-                if (MIXED)
-                  reinterpret_cast<uint4*>(d.rec[rn])[idx] = make_uint4(q, 0u, 0u, 0u);
-                else {
-                  RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + idx;
-                  *reinterpret_cast<int4*>(rr) = make_int4((int)q, 0, 0, 0);
-                  *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
-                }
-              }
-              ++count;
-            }
-          }
-        }
-    if (count > (uint32_t)cap) {
-      latch(d.ctl, ST_CAPACITY);
-    }
-    atomicMax(&d.ctl->max_cand_next, (int)count);
-    atomicAdd((unsigned long long*)&d.ctl->cand_total_next, (unsigned long long)count);
-    const uint32_t nnew = count < (uint32_t)cap ? count : (uint32_t)cap;
-    // carry history: old records of this particle with any state
-    const uint32_t nold = d.cnt[rc][o];
-    for (uint32_t k = 0; k < nold; ++k) {
-      const size_t oidx = (size_t)k * Npad + o;
-      uint32_t pf;
-      bool nz;
-      uint4 rf;
-      int4 h0;
-      double2 h1;
-      if (MIXED) {
-        rf = reinterpret_cast<const uint4*>(d.rec[rc])[oidx];
-        pf = rf.x;
-        nz = (rf.y | rf.z | rf.w) != 0u;
-      } else {
-        const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + oidx;
-        h0 = *reinterpret_cast<const int4*>(rr);
-        h1 = *(reinterpret_cast<const double2*>(rr) + 1);
-        pf = (uint32_t)h0.x;
-        nz = (h0.z | h0.w) != 0 || h1.x != 0.0 || h1.y != 0.0;
-      }
-      if (!(pf & (REC_BOND | REC_ACTIVE)) && !nz) continue;
-      const uint32_t qn = d.inv_perm[pf & REC_IDX];
-      bool found = false;
-      for (uint32_t j = 0; j < nnew; ++j) {
-        const size_t nidx = (size_t)j * Npad + p;
-        uint32_t partner = MIXED ? reinterpret_cast<const uint4*>(d.rec[rn])[nidx].x
-                                 : reinterpret_cast<const RecD*>(d.rec[rn])[nidx].pf;
-        if (partner == qn) {
-          const uint32_t npf = qn | (pf & (REC_BOND | REC_ACTIVE));
-          if (MIXED) {
-            reinterpret_cast<uint4*>(d.rec[rn])[nidx] = make_uint4(npf, rf.y, rf.z, rf.w);
-          } else {
-            RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + nidx;
-            *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, h0.z, h0.w);
-            *(reinterpret_cast<double2*>(rr) + 1) = h1;
-          }
-          found = true;
-          break;
-        }
-      }
-      if (!found && (pf & REC_BOND)) latch(d.ctl, ST_BOND_LOST);
-    }
-    count = nnew;
   }
-  d.cnt[rn][p] = count;
+  const unsigned long long skin_q = (unsigned)S.skin_q;
+  for (int az = lo[2]; az <= hi[2]; ++az) {
+    const int z = per && !all[2] ? (az + S.nc[2]) % S.nc[2] : az;
+    for (int ay = lo[1]; ay <= hi[1]; ++ay) {
+      const int y = per && !all[1] ? (ay + S.nc[1]) % S.nc[1] : ay;
+      for (int ax = lo[0]; ax <= hi[0]; ++ax) {
+        const int x = per && !all[0] ? (ax + S.nc[0]) % S.nc[0] : ax;
+        const int c = S.cell_off + (z * S.nc[1] + y) * S.nc[0] + x;
+        const uint32_t j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+        for (uint32_t q = j0; q < j1; ++q) {
+          const int4 qq = d.posq[nxt][q];
+          if (qq.w <= 0) continue;
+          if (qq.w > pq.w || (qq.w == pq.w && (int)q <= p)) continue;  // found by the larger one
+          const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
+          const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
+          const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
+          const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                        (unsigned long long)((long long)dy * dy) +
+                                        (unsigned long long)((long long)dz * dz);
+          const unsigned long long Sq = (unsigned long long)(unsigned)pq.w + (unsigned)qq.w + skin_q;
+          if (d2 < Sq * Sq) {
+            const uint32_t a = atomicAdd(&d.cand_n[p], 1u);
+            if (a < (uint32_t)cap) d.cand_tmp[(size_t)a * Npad + p] = q;
+            const uint32_t b = atomicAdd(&d.cand_n[q], 1u);
+            if (b < (uint32_t)cap) d.cand_tmp[(size_t)b * Npad + q] = (uint32_t)p;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Sort each list by partner, pack the records of a warp contiguously and
+// carry the contact history of the old records by particle pair.
+template <bool MIXED>
+__global__ void k_rb_lists(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int nxt = d.ctl->cur ^ 1;
+  const int rc = d.ctl->rec_cur, rn = rc ^ 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad exactly
+  const int lane = threadIdx.x & 31;
+  const int Npad = d.Npad, cap = d.cap;
+  if (p - lane >= Npad) return;  // whole warps only (Npad is a multiple of 256)
+  const bool valid = p < d.N;
+  uint32_t count = valid ? d.cand_n[p] : 0u;
+  if (count > (uint32_t)cap) latch(d.ctl, ST_CAPACITY);
+  unsigned mx = count, sum = count;
+#pragma unroll
+  for (int k = 16; k >= 1; k >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, k));
+    sum += __shfl_xor_sync(0xffffffffu, sum, k);
+  }
+  if (lane == 0 && sum) {
+    atomicMax(&d.ctl->max_cand_next, (int)mx);
+    atomicAdd((unsigned long long*)&d.ctl->cand_total_next, (unsigned long long)sum);
+  }
+  const uint32_t n = count < (uint32_t)cap ? count : (uint32_t)cap;
+  uint32_t incl = n;
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, k);
+    if (lane >= k) incl += y;
+  }
+  const uint32_t seg = (uint32_t)(p - lane) * (uint32_t)cap;
+  const uint32_t first = seg + incl - n;
+  d.roff[rn][p] = first;
+  d.cnt[rn][p] = n;
+  if (!valid) return;
+  const int4 pq = d.posq[nxt][p];
+  d.posq_ref[p] = pq;
+  // insertion sort by partner index (lists are short; sizes vary with the PSD)
+  uint32_t lst[CGDEM_MAX_NEIGHBORS];
+  for (uint32_t j = 0; j < n; ++j) {
+    const uint32_t v = d.cand_tmp[(size_t)j * Npad + p];
+    uint32_t i = j;
+    while (i > 0 && lst[i - 1] > v) {
+      lst[i] = lst[i - 1];
+      --i;
+    }
+    lst[i] = v;
+  }
+  for (uint32_t j = 0; j < n; ++j) {
+    if (MIXED) {
+      reinterpret_cast<uint4*>(d.rec[rn])[first + j] = make_uint4(lst[j], 0u, 0u, 0u);
+    } else {
+      RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + first + j;
+      *reinterpret_cast<int4*>(rr) = make_int4((int)lst[j], 0, 0, 0);
+      *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
+    }
+  }
+  if (pq.w <= 0) return;
+  // carry history: old records of this particle with any state
+  const uint32_t o = d.perm[p];
+  const uint32_t nold = d.cnt[rc][o];
+  const uint32_t oldfirst = d.roff[rc][o];
+  for (uint32_t k = 0; k < nold; ++k) {
+    const size_t oidx = (size_t)oldfirst + k;
+    uint32_t pf;
+    bool nz;
+    uint4 rf = make_uint4(0, 0, 0, 0);
+    int4 h0 = make_int4(0, 0, 0, 0);
+    double2 h1 = make_double2(0, 0);
+    if (MIXED) {
+      rf = reinterpret_cast<const uint4*>(d.rec[rc])[oidx];
+      pf = rf.x;
+      nz = (rf.y | rf.z | rf.w) != 0u;
+    } else {
+      const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + oidx;
+      h0 = *reinterpret_cast<const int4*>(rr);
+      h1 = *(reinterpret_cast<const double2*>(rr) + 1);
+      pf = (uint32_t)h0.x;
+      nz = (h0.z | h0.w) != 0 || h1.x != 0.0 || h1.y != 0.0;
+    }
+    if (!(pf & (REC_BOND | REC_ACTIVE)) && !nz) continue;
+    const uint32_t qn = d.inv_perm[pf & REC_IDX];
+    // binary search in the sorted list
+    int a = 0, b = (int)n - 1, hit = -1;
+    while (a <= b) {
+      const int m = (a + b) >> 1;
+      if (lst[m] == qn) {
+        hit = m;
+        break;
+      }
+      if (lst[m] < qn) a = m + 1;
+      else b = m - 1;
+    }
+    if (hit >= 0) {
+      const uint32_t npf = qn | (pf & (REC_BOND | REC_ACTIVE));
+      if (MIXED) {
+        reinterpret_cast<uint4*>(d.rec[rn])[first + hit] = make_uint4(npf, rf.y, rf.z, rf.w);
+      } else {
+        RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + first + hit;
+        *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, h0.z, h0.w);
+        *(reinterpret_cast<double2*>(rr) + 1) = h1;
+      }
+    } else if (pf & REC_BOND) {
+      latch(d.ctl, ST_BOND_LOST);
+    }
+  }
 }
 
 __global__ void k_rb_finish(Dev d) {
@@ -296,10 +386,7 @@ __global__ void k_rb_finish(Dev d) {
   c->max_cand_next = 0;
   c->cand_total_next = 0;
   c->rebuilds += 1;
-  for (int s = 0; s < d.n_samples; ++s) {
-    d.disp[s] = 0.0;
-    d.vmax2[s] = 0ull;
-  }
+  for (int s = 0; s < d.n_samples; ++s) d.dmax2[s] = 0u;
 }
 
 __global__ void k_set_rebuild(Dev d) {
@@ -316,7 +403,7 @@ __global__ void k_bond_touching(Dev d) {
   const SampleDev& S = d.sp[d.sample[pc][p]];
   const uint32_t n = d.cnt[rc][p];
   for (uint32_t k = 0; k < n; ++k) {
-    const size_t idx = (size_t)k * d.Npad + p;
+    const size_t idx = (size_t)d.roff[rc][p] + k;
     uint32_t* pfp = d.mixed ? &reinterpret_cast<uint4*>(d.rec[rc])[idx].x
                             : &reinterpret_cast<RecD*>(d.rec[rc])[idx].pf;
     const uint32_t q = *pfp & REC_IDX;
@@ -461,8 +548,12 @@ __global__ void k_kick_drift(Dev d, int couple) {
       write_shadows(d, cur, p, S, P, V, W);
       const int fc = fluid_cell_of(S, x, y, z);
       d.fcell[pc][p] = fc;
-      const double dx = S.dt * V.x, dy = S.dt * V.y, dz = S.dt * V.z;
-      atomicMax(&d.vmax2[s], (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
+      const int4 qn = d.posq[cur][p];
+      const int4 ref = d.posq_ref[p];
+      const float ex = (float)(int)((uint32_t)qn.x - (uint32_t)ref.x);
+      const float ey = (float)(int)((uint32_t)qn.y - (uint32_t)ref.y);
+      const float ez = (float)(int)((uint32_t)qn.z - (uint32_t)ref.z);
+      atomicMax(&d.dmax2[s], __float_as_uint(ex * ex + ey * ey + ez * ez));
       if (couple && (d.ctl->step % S.couple_every) == 0) {
         if (S.vf_mode == 0) atomicAdd(&d.vf[b][fc], d.vq[pc][p]);
         else scatter_cube(S, P, d.vf[b]);
@@ -476,11 +567,7 @@ __global__ void k_after_drift(Dev d, int couple) {
   Ctl* c = d.ctl;
   bool any = false;
   for (int s = 0; s < d.n_samples; ++s) {
-    unsigned long long b = d.vmax2[s];
-    d.vmax2[s] = 0ull;
-    double dd = d.disp[s] + sqrt(__longlong_as_double((long long)b));
-    d.disp[s] = dd;
-    if (2.0 * dd > d.sp[s].rebuild_disp) c->rebuild = 1;
+    if (__uint_as_float(d.dmax2[s]) > d.sp[s].rebuild_q2) c->rebuild = 1;
     if ((c->step % d.sp[s].couple_every) == 0) any = true;
   }
   if (couple && any) c->vf_cur = (c->vf_cur + 1) % 3;
@@ -586,10 +673,7 @@ __global__ void k_init_ctl(Dev d) {
   c->cand_total = 0;
   c->cand_total_next = 0;
   c->coupled = 0;
-  for (int s = 0; s < d.n_samples; ++s) {
-    d.disp[s] = 0.0;
-    d.vmax2[s] = 0ull;
-  }
+  for (int s = 0; s < d.n_samples; ++s) d.dmax2[s] = 0u;
 }
 
 // staging layout (doubles): x[3N] v[3N] w[3N] F[3N] T[3N], id order
@@ -616,7 +700,7 @@ __global__ void k_collect_contacts(Dev d, uint32_t* out, unsigned long long cap)
   const uint32_t n = d.cnt[rc][p];
   const int ip = d.id[pc][p];
   for (uint32_t k = 0; k < n; ++k) {
-    const size_t idx = (size_t)k * d.Npad + p;
+    const size_t idx = (size_t)d.roff[rc][p] + k;
     const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
                                 : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
     if (!(pf & REC_ACTIVE)) continue;
@@ -657,7 +741,7 @@ __global__ void k_diag_partial(Dev d, double* part) {
         const uint32_t n = d.cnt[rc][p];
         const int ip = d.id[pc][p];
         for (uint32_t k = 0; k < n; ++k) {
-          const size_t idx = (size_t)k * d.Npad + p;
+          const size_t idx = (size_t)d.roff[rc][p] + k;
           const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
                                       : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
           if ((pf & REC_BOND) && (pf & REC_ACTIVE) && ip < d.id[pc][pf & REC_IDX]) o[7] += 1.0;
@@ -689,18 +773,31 @@ void launch_rebuild(const Dev& d, cudaStream_t s) {
   const int B = 256, G = nblk(d.N, B);
   if (G == 0) return;
   k_rb_bin<<<G, B, 0, s>>>(d);
-  k_rb_scan<<<1, 1024, 0, s>>>(d);
+  const int ntiles = (d.C_total + 1 + SCAN_TILE - 1) / SCAN_TILE;
+  k_rb_scan_tiles<<<ntiles, SCAN_T, 0, s>>>(d, d.tile_sums);
+  k_rb_scan_sums<<<1, 1024, 0, s>>>(d, d.tile_sums, ntiles);
+  k_rb_scan_apply<<<ntiles, SCAN_T, 0, s>>>(d, d.tile_sums);
   k_rb_scatter<<<G, B, 0, s>>>(d);
   k_rb_rank<<<G, B, 0, s>>>(d);
   k_rb_permute<<<G, B, 0, s>>>(d);
   k_rb_ft_gather<<<G, B, 0, s>>>(d);
   k_rb_ft_store<<<G, B, 0, s>>>(d);
-  if (d.mixed) k_rb_search<true><<<G, B, 0, s>>>(d);
-  else k_rb_search<false><<<G, B, 0, s>>>(d);
+  k_rb_pairs<<<G, B, 0, s>>>(d);
+  const int Gp = nblk(d.Npad, B);
+  if (d.mixed) k_rb_lists<true><<<Gp, B, 0, s>>>(d);
+  else k_rb_lists<false><<<Gp, B, 0, s>>>(d);
   k_rb_finish<<<1, 1, 0, s>>>(d);
 }
 
 void launch_set_rebuild(const Dev& d, cudaStream_t s) { k_set_rebuild<<<1, 1, 0, s>>>(d); }
+
+// Graph-side decision: run the conditional rebuild body only when flagged.
+__global__ void k_rebuild_cond(Dev d, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, d.ctl->rebuild ? 1u : 0u);
+}
+void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_rebuild_cond<<<1, 1, 0, s>>>(d, h);
+}
 
 void launch_bond_touching(const Dev& d, cudaStream_t s) {
   if (d.N) k_bond_touching<<<nblk(d.N, 256), 256, 0, s>>>(d);

@@ -255,7 +255,7 @@ def cached(fn, *args, **kw) -> Sample:
     import pickle
 
     root = os.environ.get("CGDEM_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cgdem"))
-    key = hashlib.sha1(repr((fn.__name__, args, sorted(kw.items()), 2)).encode()).hexdigest()[:16]
+    key = hashlib.sha1(repr((fn.__name__, args, sorted(kw.items()), 3)).encode()).hexdigest()[:16]
     path = os.path.join(root, f"{fn.__name__}-{key}.pkl")
     if os.path.exists(path):
         with open(path, "rb") as f:
@@ -279,6 +279,7 @@ def small_periodic(n: int = 2000, seed: int = 0) -> Sample:
     return periodic_sample(fine_diameters(n, seed), 0.55, seed, name="periodic-2k")
 
 
-def fine_cylinder(n: int = 200_000, seed: int = 1) -> Sample:
-    """200,000 spheres, same PSD, in the 40x40x20-cell sand-production cylinder."""
-    return cylinder_sample(fine_diameters(n, seed), seed, name="cylinder-200k")
+def fine_cylinder(n: int = 200_000, seed: int = 1, U_in: float = 1e-4) -> Sample:
+    """200,000 spheres, same PSD, in the 40x40x20-cell sand-production cylinder,
+    with the paper's injection velocity of 1e-4 m/s (Sec. 3.1)."""
+    return cylinder_sample(fine_diameters(n, seed), seed, U_in=U_in, name="cylinder-200k")
