@@ -216,6 +216,43 @@ int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_
                        int64_t* total_candidates, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Pair search without device allocation.
+ * ------------------------------------------------------------------- */
+
+/* Fixed limits of the scratch memory of cgdem_touching_pairs_noalloc. */
+#define CGDEM_NOALLOC_MAX_SPHERES 262144
+#define CGDEM_NOALLOC_MAX_CELLS 262144
+
+/* The paper has no counterpart of this call; it is a convenience of this
+ * library.  It finds every pair i < j of spheres with
+ *     d^2 < (Ri + Rj + skin)^2
+ * (d^2 summed x, y, z in IEEE double, minimum image when periodic != 0) --
+ * with skin = 0 exactly the touching test of the contact list -- and it
+ * allocates no device memory.  It is meant for callers that cannot call
+ * cudaMalloc: a host whose device memory is one pool fixed at start-up,
+ * or a loop that must not stall on the device synchronisation an
+ * allocation can cause.  Its working memory is a fixed array of about 5 MB
+ * inside the library that each GPU using the call keeps until the process
+ * exits; the first call on a device looks up that array's address (make
+ * that first call before any stream capture), and every later call reuses
+ * the array, so calls whose GPU work overlaps race with each other.
+ *   x [n,3], R [n]: DEVICE arrays of centres and radii (n <= 262144).
+ *   box_lo, box_hi: HOST arrays of 3 doubles bounding the centres (the
+ *     periodic cell when periodic != 0); the search grid has cells of edge
+ *     >= 2 r_max + skin and at most 262144 of them.
+ *   r_max: the largest radius; skin >= 0.
+ *   pairs [cap,2]: DEVICE output, (i, j) with i < j, in no particular order.
+ *   count: DEVICE unsigned long long receiving the number of pairs found
+ *     (pairs beyond cap are counted but not written).
+ * Returns CGDEM_E_CAPACITY (nothing enqueued) if n or the cell count exceeds
+ * the limits, CGDEM_E_INVALID for bad arguments; otherwise enqueues the work
+ * on stream and returns without synchronising. */
+int cgdem_touching_pairs_noalloc(const double* x, const double* R, int64_t n,
+                                 const double* box_lo, const double* box_hi, int periodic,
+                                 double r_max, double skin, int32_t* pairs, int64_t cap,
+                                 unsigned long long* count, void* stream);
+
+/* ---------------------------------------------------------------------
  * Instrumentation.
  * ------------------------------------------------------------------- */
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
     "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
     "cgdem_get_contacts", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
-    "cgdem_get_counters", "cgdem_profile_step",
+    "cgdem_get_counters", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
 ]
 
 
@@ -100,6 +100,7 @@ def lib():
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
             "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
             "cgdem_profile_step": (i, [vp, i64, vp, vp]),
+            "cgdem_touching_pairs_noalloc": (i, [vp, vp, i64, vp, vp, i, d, d, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -128,6 +129,19 @@ def cgdem_cg_scale_diameters(d_fine, k, scheme):
     if r:
         raise CgdemError(r, "cg_scale_diameters")
     return out[: n.value].copy()
+
+
+def cgdem_touching_pairs_noalloc(x_dev, R_dev, n, box_lo, box_hi, periodic, r_max, skin,
+                                 pairs_dev, cap, count_dev, stream=None):
+    """Pair search that allocates no device memory (device pointers in and out)."""
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(box_hi, dtype=np.float64)
+    r = lib().cgdem_touching_pairs_noalloc(C.c_void_p(x_dev), C.c_void_p(R_dev), int(n), _ptr(lo),
+                                           _ptr(hi), int(periodic), float(r_max), float(skin),
+                                           C.c_void_p(pairs_dev), int(cap), C.c_void_p(count_dev),
+                                           C.c_void_p(stream))
+    if r:
+        raise CgdemError(r, "touching_pairs_noalloc")
 
 
 @dataclass
