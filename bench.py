@@ -36,6 +36,24 @@ UNIT = "particle-steps/s"
 WORKLOAD = "sand-production cylinder, 200k spheres, 40x40x20 fluid grid"
 
 
+def shard_samples(costs, world):
+    """Greedy partition of independent samples over ranks by cost (largest
+    first onto the least-loaded rank); returns the sample indices per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[r].append(i)
+        load[r] += costs[i]
+    return [sorted(v) for v in out]
+
+
+def aggregate(units_per_rank, elapsed_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return sum(units_per_rank) / max(elapsed_per_rank)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
