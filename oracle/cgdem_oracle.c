@@ -359,8 +359,14 @@ static void add_voidfrac(const ora_params* p, const double x[3], double R, uint6
     for (int k = 0; k < 3; ++k) {
         lo[k] = x[k] - 0.5 * side;
         hi[k] = x[k] + 0.5 * side;
-        a0[k] = (int)floor((lo[k] - p->f_lo[k]) * p->inv_hf[k]);
-        a1[k] = (int)floor((hi[k] - p->f_lo[k]) * p->inv_hf[k]);
+        double t0 = floor((lo[k] - p->f_lo[k]) * p->inv_hf[k]);
+        double t1 = floor((hi[k] - p->f_lo[k]) * p->inv_hf[k]);
+        /* a sphere far outside the grid (or at a non-finite position) adds nothing */
+        double lim = 4.0 * p->nf[k] + 4.0;
+        if (!(t0 >= -lim && t0 <= lim) || !(t1 >= -lim && t1 <= lim) || t1 - t0 > p->nf[k] + 2.0)
+            return;
+        a0[k] = (int)t0;
+        a1[k] = (int)t1;
     }
     for (int az = a0[2]; az <= a1[2]; ++az)
         for (int ay = a0[1]; ay <= a1[1]; ++ay)

@@ -186,9 +186,9 @@ __device__ __forceinline__ int fluid_cell_of(const SampleDev& s, double x, doubl
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double t = floor(__dmul_rn(__dsub_rn(p[k], s.f_lo[k]), s.inv_hf[k]));
-    if (t < 0.0) t = 0.0;
-    double hi = (double)(s.nf[k] - 1);
-    if (t > hi) t = hi;
+    const double hi = (double)(s.nf[k] - 1);
+    if (!(t >= 0.0)) t = 0.0;  // also catches NaN: a diverged state must not index out of range
+    if (!(t <= hi)) t = hi;
     c[k] = (int)t;
   }
   return s.fcell_off + (c[2] * s.nf[1] + c[1]) * s.nf[0] + c[0];
@@ -214,9 +214,9 @@ __device__ __forceinline__ int search_cell_of(const SampleDev& s, double x, doub
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double t = floor((p[k] - s.c_lo[k]) * s.c_inv_h[k]);
-    if (t < 0.0) t = 0.0;
-    double hi = (double)(s.nc[k] - 1);
-    if (t > hi) t = hi;
+    const double hi = (double)(s.nc[k] - 1);
+    if (!(t >= 0.0)) t = 0.0;  // also catches NaN
+    if (!(t <= hi)) t = hi;
     cxyz[k] = (int)t;
   }
   return s.cell_off + (cxyz[2] * s.nc[1] + cxyz[1]) * s.nc[0] + cxyz[0];

@@ -174,6 +174,11 @@ __device__ __forceinline__ V3<T> drag_force(T rho_f, T mu_f, T dp, V3<T> w, T n)
 
 enum { MODE_FORCES = 0, MODE_MID = 1, MODE_CANON = 2 };
 
+// Bring a line into L1 ahead of use (no register is held meanwhile).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // 64-bit integers to float through 32-bit halves (both non-negative, so the
 // sum has no cancellation): relative error below 2^-23, no 64-bit conversion.
 __device__ __forceinline__ float u64_to_f(unsigned long long v) {
@@ -184,48 +189,50 @@ __device__ __forceinline__ float s64_to_f(long long v) {
   return v < 0 ? -m : m;
 }
 
-// Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law).  The
-// overlaps are computed in FP64 only for particles near a wall; a float
-// filter (margin 1e-4 of the radius, far above float rounding) rejects the rest.
-template <typename T>
+// Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law).  A
+// float pre-check selects the walls within 5 % of the radius; only those load
+// their spring history and compute the overlap in FP64.  A sphere cannot move
+// 5 % of its radius in one step, so every wall with a non-zero history is
+// among them (and gets its history cleared when the contact ends).
+template <typename T, typename H>
 __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, float xf, float yf,
                                               float zf, V3<T> v, V3<T> w, T R, T m, T Es, T Gs,
-                                              T beta, T mu, T dt, V3<T>* hist, V3<T>& F,
-                                              V3<T>& Tq, bool* changed) {
+                                              T beta, T mu, T dt, H* hist_base, size_t stride,
+                                              V3<T>& F, V3<T>& Tq) {
   const float Rf = (float)R;
-  const float r2f = xf * xf + yf * yf;
-  const float marg = 1e-4f * Rf;
+  const float rf = sqrtf(xf * xf + yf * yf);
+  const float near = -0.05f * Rf;
   for (int wall = 0; wall < 3; ++wall) {
+    float df;
+    if (wall == 0) df = rf + Rf - s.Rc_f;
+    else if (wall == 1) df = rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f;
+    else df = zf + Rf - s.H_f;
+    if (!(df > near)) continue;
+    const H h = hist_base[(size_t)wall * stride];
+    V3<T> hist = v3<T>(h.x, h.y, h.z);
     double delta = -1.0;
     V3<T> n = v3<T>(0, 0, 0);
+    const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
     if (wall == 0) {
-      const float lim = s.Rc_f - Rf - marg;
-      if (lim <= 0.f || r2f > lim * lim) {
-        const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
-        if (r2 > 0.0) {
-          const double r = sqrt(r2);
-          delta = (r + fabs(P.w)) - s.Rc;
-          n = v3<T>(T(P.x / r), T(P.y / r), T(0));
-        }
+      if (r2 > 0.0) {
+        const double r = sqrt(r2);
+        delta = (r + fabs(P.w)) - s.Rc;
+        n = v3<T>(T(P.x / r), T(P.y / r), T(0));
       }
     } else if (wall == 1) {
-      if (zf < Rf + marg) {
-        const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
-        if (P.z < fabs(P.w) && sqrt(r2) >= s.r_out) {
-          delta = fabs(P.w) - P.z;
-          n = v3<T>(0, 0, -1);
-        }
+      if (P.z < fabs(P.w) && sqrt(r2) >= s.r_out) {
+        delta = fabs(P.w) - P.z;
+        n = v3<T>(0, 0, -1);
       }
     } else {
-      if (zf + Rf > s.H_f - marg) {
-        delta = (P.z + fabs(P.w)) - s.H;
-        n = v3<T>(0, 0, 1);
-      }
+      delta = (P.z + fabs(P.w)) - s.H;
+      n = v3<T>(0, 0, 1);
     }
     if (!(delta > 0.0)) {
-      if (hist[wall].x != T(0) || hist[wall].y != T(0) || hist[wall].z != T(0)) {
-        hist[wall] = v3<T>(0, 0, 0);
-        changed[wall] = true;
+      if (hist.x != T(0) || hist.y != T(0) || hist.z != T(0)) {
+        H z;
+        z.x = 0; z.y = 0; z.z = 0; z.w = 0;
+        hist_base[(size_t)wall * stride] = z;
       }
       continue;
     }
@@ -235,8 +242,10 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, flo
     V3<T> vc = v3<T>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
     V3<T> Fi, Ft;
     contact_law<T>(T(delta), n, vrel, vc, R, m, T(0), false, Es, Gs, beta, mu, dt, s.coulomb_mode,
-                   hist[wall], Fi, Ft);
-    changed[wall] = true;
+                   hist, Fi, Ft);
+    H hn;
+    hn.x = hist.x; hn.y = hist.y; hn.z = hist.z; hn.w = 0;
+    hist_base[(size_t)wall * stride] = hn;
     V3<T> nFt = cross3(n, Ft);
     F.x += Fi.x;
     F.y += Fi.y;
@@ -259,7 +268,7 @@ __device__ __forceinline__ int fluid_cell_fast(const SampleDev& S, double x, dou
     const float t = (pf[k] - S.f_lo_f[k]) * S.inv_hf_f[k];
     const float fl = floorf(t);
     const float fr = t - fl;
-    if (fr < 1e-4f || fr > 1.f - 1e-4f) exact = true;
+    if (!(fr >= 1e-4f && fr <= 1.f - 1e-4f)) exact = true;  // near a face, or not finite
     int ck = (int)fl;
     if (ck < 0) ck = 0;
     if (ck > S.nf[k] - 1) ck = S.nf[k] - 1;
@@ -303,8 +312,6 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
   const bool valid = p < d.N;
   if (wbase >= d.Npad) return;  // whole warps only (Npad is a multiple of 256)
 
-  __shared__ T sh[WPB][6][32];
-
   // ---- own particle, contact phase ----
   Owner<MIXED> me;
   int si = 0;
@@ -330,15 +337,30 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
       me.W = make_double4(0, 0, 0, 1);
     }
   }
+  if (MIXED && valid) {
+    // the epilogue's per-sphere data: its latency overlaps the contact rounds
+    prefetch_l1(&d.pos[cur][p]);
+    prefetch_l1(&d.vel[cur][p]);
+    prefetch_l1(&d.omg[cur][p]);
+    prefetch_l1(&d.posq_ref[p]);
+    prefetch_l1(&d.fcell[pc][p]);
+    prefetch_l1(&d.vq[pc][p]);
+  }
   const uint32_t ncnt = d.cnt[rc][p];
   const uint32_t seg = (uint32_t)wbase * (uint32_t)d.cap;
   const uint32_t lo = d.roff[rc][p] - seg;
   const uint32_t total = __shfl_sync(FULL, lo + ncnt, 31);
   V3<T> F = v3<T>(0, 0, 0), Tq = v3<T>(0, 0, 0);
+  // mixed: each lane's record for the next round is loaded one round ahead
+  uint4 rnext = make_uint4(0u, 0u, 0u, 0u);
+  if (MIXED && lane < (int)total) rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + lane];
 
   for (uint32_t base = 0; base < total; base += 32) {
     const uint32_t e = base + lane;
     const bool has = e < total;
+    uint4 rcur = rnext;
+    if (MIXED && e + 32u < total)
+      rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + e + 32u];
     // owner lane: the last lane whose first entry is <= e
     int own = 0;
 #pragma unroll
@@ -383,9 +405,8 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
       uint32_t pf;
       V3<T> xi;
       if constexpr (MIXED) {
-        const uint4 r = reinterpret_cast<const uint4*>(d.rec[rc])[idx];
-        pf = r.x;
-        xi = v3<T>(__uint_as_float(r.y), __uint_as_float(r.z), __uint_as_float(r.w));
+        pf = rcur.x;
+        xi = v3<T>(__uint_as_float(rcur.y), __uint_as_float(rcur.z), __uint_as_float(rcur.w));
       } else {
         const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + idx;
         const int4 h0 = *reinterpret_cast<const int4*>(rr);
@@ -400,6 +421,8 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
       bool act = false;
       if constexpr (MIXED) {
         const int4 qq = d.posq[cur][q];
+        const float4 qa = d.velf[cur][q];
+        const float4 qb = d.omgf[cur][q];
         if (qq.w > 0 && o.pq.w > 0) {
           const int dx = (int)((uint32_t)qq.x - (uint32_t)o.pq.x);
           const int dy = (int)((uint32_t)qq.y - (uint32_t)o.pq.y);
@@ -418,6 +441,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
             const float d2f = u64_to_f(d2);
             const float invd = rsqrtf(d2f);
             const float dn = d2f * invd;
+            (void)0;
             float du;
             if (d2 < (1ull << 62))
               du = __fdividef(s64_to_f((long long)S2 - (long long)d2), (float)Sq + dn);
@@ -425,8 +449,6 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
               du = (float)Sq - dn;
             const float delta = du * S.dq_f;
             const V3<float> n = v3<float>(dx * invd, dy * invd, dz * invd);
-            const float4 qa = d.velf[cur][q];
-            const float4 qb = d.omgf[cur][q];
             const float Ri = o.va.w, Rj = qa.w, mi = o.wa.w, mj = qb.w;
             const float Rs = __fdividef(Ri * Rj, Ri + Rj);
             double d2e = 0.0, Se = 0.0;
@@ -550,25 +572,49 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
         }
       }
     }
-    // contributions of this round to their owners, summed in list order
-    sh[wib][0][lane] = Fc.x;
-    sh[wib][1][lane] = Fc.y;
-    sh[wib][2][lane] = Fc.z;
-    sh[wib][3][lane] = Tc.x;
-    sh[wib][4][lane] = Tc.y;
-    sh[wib][5][lane] = Tc.z;
-    __syncwarp();
-    const int a = (int)max(lo, base) - (int)base;
-    const int b = (int)min(lo + ncnt, base + 32u) - (int)base;
-    for (int j = a; j < b; ++j) {
-      F.x += sh[wib][0][j];
-      F.y += sh[wib][1][j];
-      F.z += sh[wib][2][j];
-      Tq.x += sh[wib][3][j];
-      Tq.y += sh[wib][4][j];
-      Tq.z += sh[wib][5][j];
+    // contributions of this round to their owners: a segmented inclusive
+    // scan over the lanes (entries of one owner are contiguous), then each
+    // owner takes the value at the last lane of its run.  The tree order of
+    // the sums is fixed by the list, so the result is deterministic.
+    {
+      const int key = has ? own : 32 + lane;
+      T c0 = Fc.x, c1 = Fc.y, c2 = Fc.z, c3 = Tc.x, c4 = Tc.y, c5 = Tc.z;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int ku = __shfl_up_sync(FULL, key, off);
+        const T u0 = __shfl_up_sync(FULL, c0, off);
+        const T u1 = __shfl_up_sync(FULL, c1, off);
+        const T u2 = __shfl_up_sync(FULL, c2, off);
+        const T u3 = __shfl_up_sync(FULL, c3, off);
+        const T u4 = __shfl_up_sync(FULL, c4, off);
+        const T u5 = __shfl_up_sync(FULL, c5, off);
+        if (lane >= off && ku == key) {
+          c0 += u0;
+          c1 += u1;
+          c2 += u2;
+          c3 += u3;
+          c4 += u4;
+          c5 += u5;
+        }
+      }
+      const int a = (int)max(lo, base) - (int)base;
+      const int b = (int)min(lo + ncnt, base + 32u) - (int)base;
+      const int src = b > a ? b - 1 : 0;
+      const T s0 = __shfl_sync(FULL, c0, src);
+      const T s1 = __shfl_sync(FULL, c1, src);
+      const T s2 = __shfl_sync(FULL, c2, src);
+      const T s3 = __shfl_sync(FULL, c3, src);
+      const T s4 = __shfl_sync(FULL, c4, src);
+      const T s5 = __shfl_sync(FULL, c5, src);
+      if (b > a) {
+        F.x += s0;
+        F.y += s1;
+        F.z += s2;
+        Tq.x += s3;
+        Tq.y += s4;
+        Tq.z += s5;
+      }
     }
-    __syncwarp();
   }
 
   // ---- per-particle epilogue: walls, body forces, drag, integration ----
@@ -579,6 +625,11 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
     double4 P;
     if constexpr (MIXED) P = d.pos[cur][p];
     else P = me.P;
+    const int fc0 = d.fcell[pc][p];
+    if (S.use_drag) {
+      prefetch_l1(&d.vf[vfc][fc0]);
+      prefetch_l1(MIXED ? (const void*)&d.Usf[fc0] : (const void*)&d.Us[fc0]);
+    }
     const bool active = P.w > 0.0;
     if (!active) {
       if (MODE != MODE_FORCES) {
@@ -620,29 +671,12 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
         Es = S.Es; Gs = S.Gs; beta = S.beta; mu = S.mu; dt = S.dt;
       }
       if (S.kind == CGDEM_CYLINDER) {
-        V3<T> hist[3];
-        bool changed[3] = {false, false, false};
-#pragma unroll
-        for (int w = 0; w < 3; ++w) {
-          if constexpr (MIXED) {
-            const float4 h = d.wallhf[pc][(size_t)w * d.Npad + p];
-            hist[w] = v3<T>(h.x, h.y, h.z);
-          } else {
-            const double4 h = d.wallh[pc][(size_t)w * d.Npad + p];
-            hist[w] = v3<T>(h.x, h.y, h.z);
-          }
-        }
-        wall_contacts<T>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt, hist, F, Tq, changed);
-#pragma unroll
-        for (int w = 0; w < 3; ++w) {
-          if (!changed[w]) continue;
-          if constexpr (MIXED)
-            d.wallhf[pc][(size_t)w * d.Npad + p] =
-                make_float4((float)hist[w].x, (float)hist[w].y, (float)hist[w].z, 0.f);
-          else
-            d.wallh[pc][(size_t)w * d.Npad + p] =
-                make_double4((double)hist[w].x, (double)hist[w].y, (double)hist[w].z, 0.0);
-        }
+        if constexpr (MIXED)
+          wall_contacts<T, float4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+                                   d.wallhf[pc] + p, (size_t)d.Npad, F, Tq);
+        else
+          wall_contacts<T, double4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+                                    d.wallh[pc] + p, (size_t)d.Npad, F, Tq);
       }
       // gravity, buoyancy (Eq. 1) and drag (Eq. 8-11)
       {
@@ -664,7 +698,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
           F.z -= rf * Vp * g2;
         }
         if (S.use_drag) {
-          const int fc = d.fcell[pc][p];
+          const int fc = fc0;
           const unsigned long long Sc = d.vf[vfc][fc];
           T scount;
           if constexpr (MIXED) scount = u64_to_f(Sc);

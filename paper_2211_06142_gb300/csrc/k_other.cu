@@ -435,8 +435,14 @@ __device__ void scatter_cube(const SampleDev& S, double4 P, unsigned long long* 
   for (int k = 0; k < 3; ++k) {
     lo[k] = __dsub_rn(p3[k], __dmul_rn(0.5, side));
     hi[k] = __dadd_rn(p3[k], __dmul_rn(0.5, side));
-    a0[k] = (int)floor(__dmul_rn(__dsub_rn(lo[k], S.f_lo[k]), S.inv_hf[k]));
-    a1[k] = (int)floor(__dmul_rn(__dsub_rn(hi[k], S.f_lo[k]), S.inv_hf[k]));
+    double t0 = floor(__dmul_rn(__dsub_rn(lo[k], S.f_lo[k]), S.inv_hf[k]));
+    double t1 = floor(__dmul_rn(__dsub_rn(hi[k], S.f_lo[k]), S.inv_hf[k]));
+    // a diverged (non-finite or far-away) position must not drive the loops
+    const double lim = 4.0 * (double)S.nf[k] + 4.0;
+    if (!(t0 >= -lim && t0 <= lim) || !(t1 >= -lim && t1 <= lim) || t1 - t0 > (double)S.nf[k] + 2.0)
+      return;
+    a0[k] = (int)t0;
+    a1[k] = (int)t1;
   }
   for (int az = a0[2]; az <= a1[2]; ++az)
     for (int ay = a0[1]; ay <= a1[1]; ++ay)

@@ -37,8 +37,8 @@ __device__ __forceinline__ int na_cell(const Grid& g, const double* x, int* c3) 
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double t = floor((x[k] - g.lo[k]) * g.inv_h[k]);
-    if (t < 0.0) t = 0.0;
-    if (t > (double)(g.nc[k] - 1)) t = (double)(g.nc[k] - 1);
+    if (!(t >= 0.0)) t = 0.0;  // also catches NaN
+    if (!(t <= (double)(g.nc[k] - 1))) t = (double)(g.nc[k] - 1);
     c3[k] = (int)t;
   }
   return (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
@@ -189,9 +189,10 @@ extern "C" int cgdem_touching_pairs_noalloc(const double* x, const double* R, in
       fprintf(stderr, "cgdem_touching_pairs_noalloc: empty box\n");
       return CGDEM_E_INVALID;
     }
-    int nc = (int)(g.L[k] / h);
-    if (nc < 1) nc = 1;
-    if (nc > NA_MAX_CELLS) nc = NA_MAX_CELLS;
+    double nd = floor(g.L[k] / h);
+    if (!(nd >= 1.0)) nd = 1.0;
+    if (nd > (double)NA_MAX_CELLS) nd = (double)NA_MAX_CELLS;
+    const int nc = (int)nd;
     g.nc[k] = nc;
     g.inv_h[k] = nc / g.L[k];
     ncells *= nc;
