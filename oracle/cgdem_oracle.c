@@ -259,11 +259,11 @@ static int contact_law(const ora_params* p, double delta, int touching, const do
 }
 
 /* pair geometry and law; returns 1 if active */
-static int pair_eval(const ora_params* p, const double* xi_p, const double* vi, const double* wi,
-                     double Ri, double mi, const double* xj_p, const double* vj, const double* wj,
-                     double Rj, double mj, double hist[3], int* bonded, double Fi[3],
-                     double Ti[3], double Tj[3], double* Fne, double* a_out, double* delta_out,
-                     double* scale_out) {
+static int pair_eval(const ora_params* p, double gamma, const double* xi_p, const double* vi,
+                     const double* wi, double Ri, double mi, const double* xj_p, const double* vj,
+                     const double* wj, double Rj, double mj, double hist[3], int* bonded,
+                     double Fi[3], double Ti[3], double Tj[3], double* Fne, double* a_out,
+                     double* delta_out, double* scale_out) {
     double d[3];
     for (int k = 0; k < 3; ++k) {
         d[k] = xj_p[k] - xi_p[k];
@@ -288,7 +288,7 @@ static int pair_eval(const ora_params* p, const double* xi_p, const double* vi, 
     cross(rw, n, rwn);
     double vc[3] = {vrel[0] - rwn[0], vrel[1] - rwn[1], vrel[2] - rwn[2]};
     double Ft[3];
-    int act = contact_law(p, delta, d2 < S * S, n, vrel, vc, Rs, ms, p->gamma, hist, bonded, Fi, Ft,
+    int act = contact_law(p, delta, d2 < S * S, n, vrel, vc, Rs, ms, gamma, hist, bonded, Fi, Ft,
                           Fne, a_out, scale_out);
     if (!act) return 0;
     double nFt[3];
@@ -305,7 +305,7 @@ int ora_pair_contact(const ora_params* p, const double xi_pos[3], const double v
                      const double vj[3], const double wj[3], double Rj, double mj,
                      double xi_inout[3], int* bonded_inout, double out[12]) {
     double Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0}, Tj[3] = {0, 0, 0}, Fne = 0, a = 0, delta = 0;
-    int act = pair_eval(p, xi_pos, vi, wi, Ri, mi, xj_pos, vj, wj, Rj, mj, xi_inout,
+    int act = pair_eval(p, p->gamma, xi_pos, vi, wi, Ri, mi, xj_pos, vj, wj, Rj, mj, xi_inout,
                         bonded_inout, Fi, Ti, Tj, &Fne, &a, &delta, NULL);
     for (int k = 0; k < 3; ++k) {
         out[k] = act ? Fi[k] : 0.0;
@@ -430,6 +430,12 @@ struct ora_sim {
     int64_t ncell_f;
     int64_t step;
     double produced;
+    /* learned-closure hooks: per-particle corrections of drag (c_d) and
+       surface energy (c_g), and what each force evaluation measured */
+    int closure;
+    double k_feat;
+    double *cd, *cg;
+    double* cdata; /* n x ORA_CL_COLS, see ora_get_closure_data */
 };
 
 static int rec_cmp(const void* a, const void* b) {
@@ -459,6 +465,9 @@ ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const doubl
     s->removed_step = (int64_t*)calloc(n3, sizeof(int64_t));
     s->wall_xi = (double*)calloc(n3 * 3, sizeof(double));
     s->Fscale = (double*)calloc(n3, sizeof(double));
+    s->cd = (double*)calloc(n3, sizeof(double));
+    s->cg = (double*)calloc(n3, sizeof(double));
+    s->cdata = (double*)calloc(n3 * ORA_CL_COLS, sizeof(double));
     if (n > 0) {
         memcpy(s->x, x, sizeof(double) * 3 * n);
         memcpy(s->v, v, sizeof(double) * 3 * n);
@@ -470,6 +479,8 @@ ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const doubl
         s->I[i] = 0.4 * s->m[i] * R[i] * R[i];   /* solid sphere */
         s->active[i] = 1;
         s->removed_step[i] = -1;
+        s->cd[i] = 1.0;
+        s->cg[i] = 1.0;
     }
     s->ncell_f = (int64_t)p->nf[0] * p->nf[1] * p->nf[2];
     s->vf = (uint64_t*)calloc((size_t)s->ncell_f + 1, sizeof(uint64_t));
@@ -483,6 +494,7 @@ void ora_destroy(ora_sim* s) {
     free(s->x); free(s->v); free(s->w); free(s->F); free(s->T);
     free(s->R); free(s->m); free(s->I); free(s->active); free(s->removed_step);
     free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us); free(s->Fscale);
+    free(s->cd); free(s->cg); free(s->cdata);
     free(s);
 }
 
@@ -733,6 +745,7 @@ int ora_compute_forces(ora_sim* s) {
     memset(s->F, 0, sizeof(double) * 3 * (size_t)n);
     memset(s->T, 0, sizeof(double) * 3 * (size_t)n);
     memset(s->Fscale, 0, sizeof(double) * (size_t)n);
+    memset(s->cdata, 0, sizeof(double) * ORA_CL_COLS * (size_t)n);
 
     /* candidates: touching pairs plus surviving bonded records */
     pairlist l = {0};
@@ -755,11 +768,25 @@ int ora_compute_forces(ora_sim* s) {
         const ora_rec* old = find_rec(s->rec, s->nrec, i, j);
         ora_rec r = {i, j, old ? old->bonded : 0, 0, {0, 0, 0}};
         if (old) memcpy(r.xi, old->xi, sizeof(r.xi));
-        double Fi[3], Ti[3], Tj[3], sc = 0.0;
-        int act = pair_eval(p, &s->x[3 * i], &s->v[3 * i], &s->w[3 * i], s->R[i], s->m[i],
+        double Fi[3], Ti[3], Tj[3], sc = 0.0, delta = 0.0;
+        /* surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure */
+        double gamma = s->closure ? p->gamma * sqrt(s->cg[i] * s->cg[j]) : p->gamma;
+        int act = pair_eval(p, gamma, &s->x[3 * i], &s->v[3 * i], &s->w[3 * i], s->R[i], s->m[i],
                             &s->x[3 * j], &s->v[3 * j], &s->w[3 * j], s->R[j], s->m[j], r.xi,
-                            &r.bonded, Fi, Ti, Tj, NULL, NULL, NULL, &sc);
+                            &r.bonded, Fi, Ti, Tj, NULL, NULL, &delta, &sc);
         if (!act) continue;
+        /* what the closure measures: coordination, summed overlap, bond capacity */
+        double* ci = &s->cdata[ORA_CL_COLS * i];
+        double* cj = &s->cdata[ORA_CL_COLS * j];
+        ci[3] += 1.0;
+        cj[3] += 1.0;
+        ci[4] += delta;
+        cj[4] += delta;
+        if (r.bonded) {
+            double half_cap = 0.5 * 3.0 * M_PI * gamma * (s->R[i] * s->R[j] / (s->R[i] + s->R[j]));
+            ci[8] += half_cap;
+            cj[8] += half_cap;
+        }
         for (int c = 0; c < 3; ++c) {
             s->F[3 * i + c] += Fi[c];
             s->F[3 * j + c] -= Fi[c];
@@ -794,16 +821,53 @@ int ora_compute_forces(ora_sim* s) {
             F[c] += s->m[i] * p->g[c];                        /* F_g */
             if (p->use_buoyancy) F[c] += -p->rho_f * V * p->g[c]; /* F_b */
         }
+        int64_t cell = fluid_cell(p, &s->x[3 * i]);
+        double nc = porosity(s->vf[cell], p->n_min);
+        double u[3] = {s->Us[3 * cell] / nc, s->Us[3 * cell + 1] / nc, s->Us[3 * cell + 2] / nc};
+        double* cl = &s->cdata[ORA_CL_COLS * i];
         if (p->use_drag) {
-            int64_t cell = fluid_cell(p, &s->x[3 * i]);
-            double nc = porosity(s->vf[cell], p->n_min);
-            double u[3] = {s->Us[3 * cell] / nc, s->Us[3 * cell + 1] / nc, s->Us[3 * cell + 2] / nc};
             double fd[3];
             ora_drag(p->rho_f, p->mu_f, 2.0 * s->R[i], u, &s->v[3 * i], nc, fd);
-            for (int c = 0; c < 3; ++c) F[c] += fd[c];
+            if (s->closure) {
+                for (int c = 0; c < 3; ++c) fd[c] *= s->cd[i];
+            }
+            for (int c = 0; c < 3; ++c) {
+                F[c] += fd[c];
+                cl[5 + c] = fd[c];
+            }
             s->Fscale[i] += sqrt(dot(fd, fd));
         }
+        /* closure inputs: solid fraction, slip speed, k, coordination, mean overlap / d */
+        double slip[3] = {u[0] - s->v[3 * i], u[1] - s->v[3 * i + 1], u[2] - s->v[3 * i + 2]};
+        cl[0] = 1.0 - nc;
+        cl[1] = sqrt(dot(slip, slip));
+        cl[2] = s->k_feat;
+        cl[4] = cl[3] > 0.0 ? cl[4] / (cl[3] * 2.0 * s->R[i]) : 0.0;
+        cl[9] = (double)cell;
+        cl[10] = s->cd[i];
+        cl[11] = s->cg[i];
     }
+    return 0;
+}
+
+int ora_set_closure(ora_sim* s, int enable, double k_feat) {
+    s->closure = enable ? 1 : 0;
+    s->k_feat = k_feat;
+    for (int64_t i = 0; i < s->n; ++i) {
+        s->cd[i] = 1.0;
+        s->cg[i] = 1.0;
+    }
+    return 0;
+}
+
+int ora_set_corrections(ora_sim* s, const double* cd, const double* cg) {
+    memcpy(s->cd, cd, sizeof(double) * (size_t)s->n);
+    memcpy(s->cg, cg, sizeof(double) * (size_t)s->n);
+    return 0;
+}
+
+int ora_get_closure_data(const ora_sim* s, double* out) {
+    memcpy(out, s->cdata, sizeof(double) * ORA_CL_COLS * (size_t)s->n);
     return 0;
 }
 

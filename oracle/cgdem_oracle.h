@@ -108,6 +108,21 @@ int ora_get_removed_step(const ora_sim* s, int64_t* removed_step);
  * damping, tangential, wall, gravity, buoyancy and drag terms -- the scale
  * for normwise comparisons. */
 int ora_get_force_scale(const ora_sim* s, double* scale);
+
+/* Learned-closure hooks (the closure is not part of the paper).  With the
+ * closure enabled, the drag of particle i (Eq. 8) is multiplied by c_d,i and
+ * each pair uses the surface energy gamma sqrt(c_g,i c_g,j) in Eq. 12-13 and
+ * in F_C = 3 pi gamma R* (Table 1).  Corrections start at 1. */
+#define ORA_CL_COLS 12
+int ora_set_closure(ora_sim* s, int enable, double k_feat);
+int ora_set_corrections(ora_sim* s, const double* cd, const double* cg);
+/* Per particle, from the last force evaluation (ORA_CL_COLS doubles each):
+ * 0 solid fraction 1 - n of its fluid cell (Eq. 6-7), 1 slip speed
+ * |U_s / n - v| (Eq. 8-11), 2 the feature k given to ora_set_closure,
+ * 3 active pair contacts, 4 mean overlap of those contacts / (2 R),
+ * 5-7 drag force as applied, 8 half the summed F_C of its bonded contacts,
+ * 9 fluid cell, 10-11 the corrections c_d, c_g used. */
+int ora_get_closure_data(const ora_sim* s, double* out);
 /* Brute force O(N^2) list of pairs with d^2 < (Ri+Rj+skin)^2 (minimum image). */
 int64_t ora_pairs_bruteforce(const ora_params* p, int64_t n, const double* x, const double* R,
                              double skin, int32_t* pi, int32_t* pj, int64_t cap);

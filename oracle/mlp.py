@@ -28,11 +28,13 @@ L = 1/(2B) sum_b sum_k m_bk (o_bk - y_bk)^2, minimised by Adam (Kingma and
 Ba, 2015: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, step
 lr * m_hat / (sqrt(v_hat) + eps) with bias-corrected m_hat, v_hat).
 
-With ``bf16=True`` every operand of a matrix product is rounded to bfloat16
+With ``bf16_ops=True`` every operand of a matrix product is rounded to bfloat16
 (round to nearest, ties to even) where the tensor-core kernels round it: the
 layer inputs (x_hat, h_1, h_2, h_3), the weights, and the back-propagated
 pre-activation gradients dZ_l that enter the products dW_l = dZ_l^T a_(l-1)
-and dA_(l-1) = dZ_l W_l; biases, activations and sums stay exact here.
+and dA_(l-1) = dZ_l W_l, and into the bias gradients of the hidden layers
+(which the kernels form as the product of dZ_l with a column of ones);
+activations, sums and the output layer's bias gradient stay exact here.
 """
 from __future__ import annotations
 
@@ -136,7 +138,10 @@ def loss_and_grad(theta, X, Y, M, bf16_ops=False):
         W, _ = layers[li]
         a_prev = acts[li]
         dzq = q(dz)
-        grads[li] = (dzq.T @ q(a_prev), dz.sum(0))
+        # hidden-layer bias gradients are the product of the rounded dZ with a
+        # column of ones; the output layer's is summed from the exact dZ
+        db = dz.sum(0) if li == len(layers) - 1 else dzq.sum(0)
+        grads[li] = (dzq.T @ q(a_prev), db)
         if li > 0:
             da = dzq @ q(W)
             dz = da * dsilu(zs[li - 1])

@@ -64,6 +64,9 @@ def lib():
             ("ora_get_force_scale", i, [vp, vp]),
             ("ora_pairs_bruteforce", i64, [vp, i64, pd, pd, d, vp, vp, i64]),
             ("ora_voidfrac", i, [vp, i64, pd, pd, vp]),
+            ("ora_set_closure", i, [vp, i, d]),
+            ("ora_set_corrections", i, [vp, pd, pd]),
+            ("ora_get_closure_data", i, [vp, pd]),
         ]:
             f = getattr(L, name)
             f.restype = res
@@ -241,10 +244,54 @@ class Sim:
         lib().ora_get_force_scale(self.h, out.ctypes.data)
         return out
 
+    # ---- learned-closure hooks ----
+    def set_closure(self, enable, k_feat):
+        lib().ora_set_closure(self.h, int(enable), float(k_feat))
+
+    def set_corrections(self, cd, cg):
+        cd = _f64(cd)
+        cg = _f64(cg)
+        assert cd.shape == (self.n,) and cg.shape == (self.n,)
+        lib().ora_set_corrections(self.h, _pd(cd), _pd(cg))
+
+    def closure_data(self):
+        """[n, 12] per particle from the last force evaluation: features
+        (solid fraction, slip speed, k, coordination, mean overlap / d), drag
+        force (3), half the summed bond capacity, fluid cell, c_d, c_g."""
+        out = np.zeros((self.n, CL_COLS))
+        lib().ora_get_closure_data(self.h, _pd(out))
+        return out
+
+    def step_closure(self, theta, nsteps, lo, hi, cd_max, cg_max):
+        """Steps with the learned closure: each step's force evaluation uses
+        the corrections from the previous one; after it the network (in the
+        kernels' bfloat16 rounding) maps the features it measured to the
+        corrections of the next step.  A particle whose features leave the
+        box [lo, hi] gets c_d = c_g = 1 (plain coarse-graining)."""
+        for _ in range(nsteps):
+            self.step(1)
+            cd, cg = closure_corrections(theta, self.closure_data(), lo, hi, cd_max, cg_max)
+            self.set_corrections(cd, cg)
+
     def removed_step(self):
         out = np.zeros(self.n, np.int64)
         lib().ora_get_removed_step(self.h, out.ctypes.data)
         return out
+
+
+CL_COLS = 12
+
+
+def closure_corrections(theta, data, lo, hi, cd_max, cg_max):
+    """(c_d, c_g) per particle from closure data rows (see Sim.closure_data)."""
+    from . import mlp
+    X = data[:, :5]
+    o, _ = mlp.forward(theta, X, bf16_ops=True)
+    cd, cg = mlp.corrections(o, cd_max, cg_max)
+    inside = np.all((X >= np.asarray(lo)) & (X <= np.asarray(hi)), axis=1)
+    cd = np.where(inside, cd, 1.0)
+    cg = np.where(inside, cg, 1.0)
+    return cd, cg
 
 
 # ---- coarse-graining rules (Sec. 2.4, Eq. 14-35, Table 3) ----
