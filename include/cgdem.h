@@ -52,6 +52,7 @@ typedef enum {
     CGDEM_E_CAPACITY = -2,  /* a particle has more candidate neighbours than max_neighbors */
     CGDEM_E_CUDA = -3,      /* a CUDA runtime call failed */
     CGDEM_E_NONFINITE = -4, /* a force or position became NaN/Inf */
+    CGDEM_E_TIMEOUT = -5,   /* a bounded device-side wait expired (the kernel gave up and returned) */
     CGDEM_E_STATE = -6      /* call out of order, or a bonded pair left the candidate list */
 } cgdem_status;
 
@@ -100,9 +101,12 @@ typedef struct {
     int precision;          /* cgdem_precision */
     int n_samples;          /* >= 1 */
     int max_neighbors;      /* candidate-list width per particle (ELL columns) */
-    int block_size;         /* threads per block of the force kernel (64..1024, multiple of 32) */
-    double cell_scale;      /* search cell edge = cell_scale * (2 R_max + skin), >= 1 */
+    int block_size;         /* threads per block of the fused force kernel: 64, 128 or 256 */
+    double cell_scale;      /* search cell edge = cell_scale * (2 R_max + skin), in [0.05, 1];
+                               <= 0 selects 0.35 (pairs are searched from the larger sphere) */
     int steps_per_graph;    /* steps captured in one CUDA graph by cgdem_step (>= 1) */
+    int closure;            /* 1: the context carries the learned closure (cgdem_set_closure);
+                               its force kernel runs blocks of 128 (block_size 0 or 128) */
 } cgdem_config;
 
 typedef struct cgdem_ctx cgdem_ctx;
@@ -262,6 +266,89 @@ int cgdem_touching_pairs_noalloc(const double* x, const double* R, int64_t n,
  * mean force-kernel time per step [ms], total rebuild-sequence time [ms],
  * rebuilds done, total time [ms], steps timed.  Synchronises stream. */
 int cgdem_profile_step(cgdem_ctx* ctx, int64_t nsteps, double* out, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Learned closure network (not part of the paper): a correction of the
+ * coarse parcels' drag (Eq. 8) and surface energy (Eq. 13) per parcel,
+ * c_d = exp(o_1) and c_g = exp(o_2), from a 5 -> 64 -> 64 -> 64 -> 2 SiLU
+ * network of the inputs (local solid fraction 1 - n of Eq. 6-7, slip speed
+ * |u - v| of Eq. 8-11, coarse-graining ratio k of Eq. 14, coordination
+ * number, mean overlap / diameter).
+ *
+ * Parameters: CGDEM_MLP_NPARAMS floats, device memory, caller-owned:
+ * mu[5], inv_sigma[5] (inputs are standardised as (x - mu) * inv_sigma),
+ * then for each layer W[out][in] row by row and b[out].  The tensor-core
+ * kernels round the inputs of every matrix product (standardised inputs,
+ * hidden activations, weights, back-propagated gradients) to bfloat16 and
+ * accumulate in FP32.
+ * ------------------------------------------------------------------- */
+#define CGDEM_MLP_NPARAMS 8844
+
+/* Bytes of device workspace the training and inference calls need.  The
+ * workspace is caller-owned and must be zero-filled before its first use. */
+int cgdem_mlp_workspace_size(size_t* bytes);
+
+/* Network outputs o[n][2] (device) of inputs X[n][5] (device, row-major).
+ * Asynchronous on `stream`.  CGDEM_E_INVALID for bad arguments or
+ * n > 2^28.  A device-side wait that expires is reported by
+ * cgdem_mlp_status. */
+int cgdem_mlp_forward(const float* theta, const float* X, int64_t n, float* out, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* One full-batch training step on samples X[n][5], targets Y[n][2] and a
+ * 0/1 mask M[n][2] (all device, row-major) of the loss
+ * L = 1/(2n) sum_b sum_k M_bk (o_bk - Y_bk)^2.  Writes the gradient
+ * (CGDEM_MLP_NPARAMS floats, zero for mu and inv_sigma) to grad_out and L
+ * to loss_out when they are non-NULL (device pointers).  When adam_m and
+ * adam_v (device, CGDEM_MLP_NPARAMS floats each, zero before step t = 1)
+ * are non-NULL, applies Adam step t (>= 1) with learning rate lr,
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8 to theta in place (mu and
+ * inv_sigma unchanged).  The gradient sum over the batch is deterministic.
+ * Asynchronous on `stream`. */
+int cgdem_mlp_train_step(float* theta, float* adam_m, float* adam_v, int64_t t, double lr,
+                         const float* X, const float* Y, const float* M, int64_t n, float* grad_out,
+                         float* loss_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Synchronises `stream` and returns CGDEM_E_TIMEOUT (clearing the flag) if
+ * a network kernel gave up a bounded wait since the last call. */
+int cgdem_mlp_status(void* workspace, void* stream);
+
+/* The closure inside the step (contexts created with cfg.closure = 1).
+ * Every force evaluation of cgdem_step uses per-particle corrections
+ * (c_d, c_g): the drag of Eq. 8 is multiplied by c_d,i and a bonded pair
+ * uses the surface energy gamma_g sqrt(c_g,i c_g,j) in Eq. 12-13, in its
+ * bond-break separation (Table 1, point C) and in F_C.  After the forces,
+ * the same kernel evaluates the network on the inputs it measured in that
+ * evaluation (tensor cores, one M = 128 tile per block) and stores the
+ * corrections of the next evaluation: c = exp(clamp(o, -log_max, log_max)),
+ * or c_d = c_g = 1 for a particle with an input outside [lo, hi] (plain
+ * coarse-graining).  The compute_forces verb uses the corrections and
+ * leaves them unchanged.  Corrections start at 1. */
+typedef struct {
+    float lo[5], hi[5];     /* range of the inputs the network was trained on */
+    float cd_log_max;       /* |ln c_d| <= cd_log_max, in [0, 20] */
+    float cg_log_max;       /* |ln c_g| <= cg_log_max, in [0, 20] */
+} cgdem_closure_params;
+
+/* Enable (theta: device pointer to CGDEM_MLP_NPARAMS floats, copied into
+ * the context's BF16 form before the call returns on `stream`; cp: host) or
+ * disable (enable = 0; theta and cp may be NULL) the closure; resets every
+ * correction to 1.  CGDEM_E_INVALID if the skin does not exceed twice the
+ * bond-break separation at the largest surface-energy correction;
+ * CGDEM_E_STATE for a context without closure support. */
+int cgdem_set_closure(cgdem_ctx* ctx, const float* theta, const cgdem_closure_params* cp, int enable,
+                      void* stream);
+
+/* While enabled, every force evaluation records per particle 12 floats:
+ * the 5 closure inputs (solid fraction 1 - n, slip speed, k, active
+ * contacts, mean overlap / diameter), the drag force as applied (3), half
+ * the summed F_C of its bonded contacts, its fluid cell within its sample,
+ * and the corrections c_d, c_g it used.  Inactive particles record zeros. */
+int cgdem_closure_record(cgdem_ctx* ctx, int enable, void* stream);
+
+/* Copies the rows recorded by the last force evaluation, in particle order
+ * (out: host, rows >= particle count). */
+int cgdem_get_closure_data(cgdem_ctx* ctx, float* out, int64_t rows, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,131 @@
+"""Project-written autotuner for the step: search-cell size, threads per
+block of the fused force kernel, and the candidate-list skin.
+
+Coordinate search (each knob in turn, the others held at the best so far),
+each trial timing a short run of ``cgdem_step`` with CUDA events after a
+warm-up.  Results are cached in JSON keyed by a signature of the workload
+(sphere counts, domain kinds, largest radii, precision), so a workload is
+tuned once per machine.  Every trial computes the same physics: the skin and
+the cells only change which candidate pairs are listed, never which pairs
+touch.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+from . import cgdem
+
+CELL_SCALES = (0.25, 0.35, 0.5, 0.75)
+BLOCKS = (64, 128, 256)
+SKIN_FRACS = (0.01, 0.02, 0.04)
+
+
+def _cache_path():
+    root = os.environ.get("CGDEM_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cgdem"))
+    return os.path.join(root, "autotune.json")
+
+
+def signature(params, counts, precision):
+    h = hashlib.sha1()
+    h.update(repr((list(map(int, counts)), int(precision))).encode())
+    for p in params:
+        h.update(repr((p.kind, round(p.r_max, 12), p.nf[0], p.nf[1], p.nf[2])).encode())
+    return h.hexdigest()[:16]
+
+
+def _with_skin(params, frac):
+    out = []
+    for p in params:
+        q = cgdem.SampleParams()
+        C = type(p)
+        for name, _ in C._fields_:
+            v = getattr(p, name)
+            if hasattr(v, "__len__"):
+                for i in range(len(v)):
+                    getattr(q, name)[i] = v[i]
+            else:
+                setattr(q, name, v)
+        q.skin = frac * 2 * p.r_max
+        out.append(q)
+    return out
+
+
+def trial(params, counts, state, Us, precision, cell_scale, block, steps=150, warm=30,
+          device="cuda:0", max_neighbors=48):
+    import torch
+    ctx = cgdem.Context(params, counts, precision=precision, max_neighbors=max_neighbors,
+                        block_size=block, cell_scale=cell_scale, device=device)
+    try:
+        ctx.set_fluid_velocity(Us)
+        ctx.init_particles(*state, bond_touching=True)
+        ctx.compute_forces()
+        ctx.step(warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.status()
+        return e0.elapsed_time(e1) / steps
+    finally:
+        ctx.close()
+
+
+def autotune(params, counts, state, Us, precision=cgdem.MIXED, device="cuda:0", use_cache=True,
+             steps=150, log=None):
+    """Return {"cell_scale", "block", "skin_frac", "ms_per_step", "trials"} for the workload."""
+    key = signature(params, counts, precision)
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return dict(cache[key], cached=True)
+    best = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02}
+    trials = []
+
+    def run(cs, b, sf):
+        try:
+            ms = trial(_with_skin(params, sf), counts, state, Us, precision, cs, b, steps=steps,
+                       device=device)
+        except cgdem.CgdemError as e:  # e.g. a skin below the bond-break separation
+            ms = float("inf")
+            if log:
+                log(f"trial cs={cs} block={b} skin={sf}: {e}")
+        trials.append({"cell_scale": cs, "block": b, "skin_frac": sf, "ms_per_step": ms})
+        return ms
+
+    best_ms = run(best["cell_scale"], best["block"], best["skin_frac"])
+    for knob, values in (("cell_scale", CELL_SCALES), ("block", BLOCKS), ("skin_frac", SKIN_FRACS)):
+        for v in values:
+            if v == best[knob]:
+                continue
+            cand = dict(best, **{knob: v})
+            ms = run(cand["cell_scale"], cand["block"], cand["skin_frac"])
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    res = dict(best, ms_per_step=best_ms, trials=trials)
+    if use_cache:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            cache[key] = res
+            tmp = path + ".tmp.%d" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return dict(res, cached=False)
+
+
+def tuned_params(params, result):
+    return _with_skin(params, result["skin_frac"])

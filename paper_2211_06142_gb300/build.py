@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcgdem.so")
-SOURCES = ["k_forces.cu", "k_other.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["k_forces.cu", "k_other.cu", "api.cu", "noalloc.cu", "k_mlp.cu"]
 HEADERS = [os.path.join(CSRC, "cgdem_internal.cuh"), os.path.join(ROOT, "include", "cgdem.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",

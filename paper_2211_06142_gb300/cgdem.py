@@ -21,7 +21,9 @@ CGDEM_E_INVALID = -1
 CGDEM_E_CAPACITY = -2
 CGDEM_E_CUDA = -3
 CGDEM_E_NONFINITE = -4
+CGDEM_E_TIMEOUT = -5
 CGDEM_E_STATE = -6
+MLP_NPARAMS = 8844
 FP64, MIXED = 0, 1
 PERIODIC_BOX, CYLINDER = 0, 1
 CG_NONE, CG_SSW, CG_SSP = 0, 1, 2
@@ -34,6 +36,8 @@ EXPORTS = [
     "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
     "cgdem_get_contacts", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
     "cgdem_get_counters", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
+    "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
+    "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
 ]
 
 
@@ -64,7 +68,16 @@ class Config(C.Structure):
     _fields_ = [
         ("precision", C.c_int), ("n_samples", C.c_int), ("max_neighbors", C.c_int),
         ("block_size", C.c_int), ("cell_scale", C.c_double), ("steps_per_graph", C.c_int),
+        ("closure", C.c_int),
     ]
+
+
+class ClosureParams(C.Structure):
+    _fields_ = [("lo", C.c_float * 5), ("hi", C.c_float * 5), ("cd_log_max", C.c_float),
+                ("cg_log_max", C.c_float)]
+
+
+CL_COLS = 12
 
 
 _lib = None
@@ -101,6 +114,14 @@ def lib():
             "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
             "cgdem_profile_step": (i, [vp, i64, vp, vp]),
             "cgdem_touching_pairs_noalloc": (i, [vp, vp, i64, vp, vp, i, d, d, vp, i64, vp, vp]),
+            "cgdem_mlp_workspace_size": (i, [vp]),
+            "cgdem_mlp_forward": (i, [vp, vp, i64, vp, vp, C.c_size_t, vp]),
+            "cgdem_mlp_train_step": (i, [vp, vp, vp, i64, d, vp, vp, vp, i64, vp, vp, vp, C.c_size_t,
+                                         vp]),
+            "cgdem_mlp_status": (i, [vp, vp]),
+            "cgdem_set_closure": (i, [vp, vp, vp, i, vp]),
+            "cgdem_closure_record": (i, [vp, i, vp]),
+            "cgdem_get_closure_data": (i, [vp, vp, i64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -142,6 +163,105 @@ def cgdem_touching_pairs_noalloc(x_dev, R_dev, n, box_lo, box_hi, periodic, r_ma
                                            C.c_void_p(stream))
     if r:
         raise CgdemError(r, "touching_pairs_noalloc")
+
+
+def cgdem_mlp_workspace_size():
+    n = C.c_size_t(0)
+    r = lib().cgdem_mlp_workspace_size(C.byref(n))
+    if r:
+        raise CgdemError(r, "mlp_workspace_size")
+    return n.value
+
+
+def cgdem_mlp_forward(theta_dev, X_dev, n, out_dev, ws_dev, ws_bytes, stream=None):
+    r = lib().cgdem_mlp_forward(C.c_void_p(theta_dev), C.c_void_p(X_dev), int(n), C.c_void_p(out_dev),
+                                C.c_void_p(ws_dev), int(ws_bytes), C.c_void_p(stream))
+    if r:
+        raise CgdemError(r, "mlp_forward")
+
+
+def cgdem_mlp_train_step(theta_dev, m_dev, v_dev, t, lr, X_dev, Y_dev, M_dev, n, grad_dev, loss_dev,
+                         ws_dev, ws_bytes, stream=None):
+    r = lib().cgdem_mlp_train_step(C.c_void_p(theta_dev), C.c_void_p(m_dev), C.c_void_p(v_dev), int(t),
+                                   float(lr), C.c_void_p(X_dev), C.c_void_p(Y_dev), C.c_void_p(M_dev),
+                                   int(n), C.c_void_p(grad_dev), C.c_void_p(loss_dev), C.c_void_p(ws_dev),
+                                   int(ws_bytes), C.c_void_p(stream))
+    if r:
+        raise CgdemError(r, "mlp_train_step")
+
+
+def cgdem_mlp_status(ws_dev, stream=None):
+    r = lib().cgdem_mlp_status(C.c_void_p(ws_dev), C.c_void_p(stream))
+    if r:
+        raise CgdemError(r, "mlp kernel")
+
+
+class Closure:
+    """The closure network on one GPU: FP32 parameters, Adam moments and the
+    kernels' workspace as torch tensors; every computation runs in the
+    library's tensor-core kernels."""
+
+    def __init__(self, theta, device="cuda:0"):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("cgdem needs a CUDA GPU")
+        self.torch = torch
+        self.device = torch.device(device)
+        theta = np.asarray(theta, dtype=np.float32)
+        if theta.shape != (MLP_NPARAMS,):
+            raise ValueError("theta must hold %d floats" % MLP_NPARAMS)
+        self.theta = torch.tensor(theta, device=self.device)
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.t = 0
+        self.ws_bytes = cgdem_mlp_workspace_size()
+        self.ws = torch.zeros(self.ws_bytes // 4 + 1, dtype=torch.float32, device=self.device)
+        self.grad = torch.zeros_like(self.theta)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def _dev(self, a, cols):
+        t = self.torch
+        if isinstance(a, t.Tensor):
+            a = a.to(device=self.device, dtype=t.float32).contiguous()
+        else:
+            a = t.tensor(np.ascontiguousarray(a, dtype=np.float32), device=self.device)
+        return a.reshape(-1, cols)
+
+    def forward(self, X):
+        X = self._dev(X, 5)
+        out = self.torch.empty((len(X), 2), dtype=self.torch.float32, device=self.device)
+        cgdem_mlp_forward(self.theta.data_ptr(), X.data_ptr(), len(X), out.data_ptr(), self.ws.data_ptr(),
+                          self.ws_bytes, self._stream())
+        cgdem_mlp_status(self.ws.data_ptr(), self._stream())
+        return out
+
+    def gradient(self, X, Y, M):
+        X, Y, M = self._dev(X, 5), self._dev(Y, 2), self._dev(M, 2)
+        cgdem_mlp_train_step(self.theta.data_ptr(), None, None, 0, 0.0, X.data_ptr(), Y.data_ptr(),
+                             M.data_ptr(), len(X), self.grad.data_ptr(), self.loss.data_ptr(),
+                             self.ws.data_ptr(), self.ws_bytes, self._stream())
+        cgdem_mlp_status(self.ws.data_ptr(), self._stream())
+        return float(self.loss.item()), self.grad.clone()
+
+    def train(self, X, Y, M, steps, lr, check_every=50):
+        """`steps` full-batch Adam steps; returns the loss before each step."""
+        X, Y, M = self._dev(X, 5), self._dev(Y, 2), self._dev(M, 2)
+        hist = self.torch.zeros(steps, dtype=self.torch.float32, device=self.device)
+        for k in range(steps):
+            self.t += 1
+            cgdem_mlp_train_step(self.theta.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.t, lr,
+                                 X.data_ptr(), Y.data_ptr(), M.data_ptr(), len(X), None,
+                                 hist[k:].data_ptr(), self.ws.data_ptr(), self.ws_bytes, self._stream())
+            if (k + 1) % check_every == 0 or k + 1 == steps:
+                cgdem_mlp_status(self.ws.data_ptr(), self._stream())
+        return hist.cpu().numpy()
+
+    def params(self):
+        return self.theta.cpu().numpy()
 
 
 @dataclass
@@ -192,7 +312,7 @@ class Context:
     """A library context over one or more samples on one GPU."""
 
     def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
-                 cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None):
+                 cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None, closure=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -204,7 +324,7 @@ class Context:
         self.counts = np.ascontiguousarray(counts, dtype=np.int64)
         self.N = int(self.counts.sum())
         self.cfg = Config(precision, self.n_samples, max_neighbors, block_size, cell_scale,
-                          steps_per_graph)
+                          steps_per_graph, int(bool(closure)))
         nbytes = C.c_size_t(0)
         r = lib().cgdem_workspace_size(C.byref(self.cfg), self._params, _ptr(self.counts),
                                        C.byref(nbytes))
@@ -316,6 +436,34 @@ class Context:
         self._check(lib().cgdem_get_counters(self.h, C.byref(s), C.byref(r), C.byref(m), C.byref(t),
                                              self._s()), "get_counters")
         return dict(steps=s.value, rebuilds=r.value, max_candidates=m.value, total_candidates=t.value)
+
+    # ---- learned closure ----
+    def set_closure(self, theta=None, lo=None, hi=None, cd_log_max=3.0, cg_log_max=1.386,
+                    enable=True):
+        """Enable the closure with parameters theta (array or tensor of
+        MLP_NPARAMS floats) and input range [lo, hi], or disable it."""
+        t = self.torch
+        if enable:
+            th = t.as_tensor(np.asarray(theta, dtype=np.float32) if not isinstance(theta, t.Tensor)
+                             else theta, dtype=t.float32, device=self.device).contiguous()
+            if th.numel() != MLP_NPARAMS:
+                raise ValueError("theta must hold %d floats" % MLP_NPARAMS)
+            self._closure_theta = th  # kept alive until the copy on the stream has run
+            cp = ClosureParams((C.c_float * 5)(*lo), (C.c_float * 5)(*hi), cd_log_max, cg_log_max)
+            self._check(lib().cgdem_set_closure(self.h, C.c_void_p(th.data_ptr()), C.byref(cp), 1,
+                                                self._s()), "set_closure")
+        else:
+            self._check(lib().cgdem_set_closure(self.h, None, None, 0, self._s()), "set_closure")
+
+    def closure_record(self, enable=True):
+        self._check(lib().cgdem_closure_record(self.h, int(bool(enable)), self._s()), "closure_record")
+
+    def closure_data(self):
+        """[N, 12] rows recorded by the last force evaluation (see include/cgdem.h)."""
+        out = np.zeros((self.N, CL_COLS), np.float32)
+        self._check(lib().cgdem_get_closure_data(self.h, _ptr(out), self.N, self._s()),
+                    "get_closure_data")
+        return out
 
     def profile_step(self, n):
         out = np.zeros(5)

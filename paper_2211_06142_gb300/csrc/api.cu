@@ -26,6 +26,10 @@ void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
 void launch_diag(const Dev& d, double* part, cudaStream_t s);
 void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s);
+void launch_closure_gather(const Dev& d, cudaStream_t s);
+void launch_closure_pack(const float* theta, const float* lo, const float* hi, float cd_max, float cg_max,
+                         uint8_t* blob, cudaStream_t s);
 }  // namespace cgdem
 
 using namespace cgdem;
@@ -225,6 +229,7 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   s.n_min_f = (float)s.n_min;
   for (int k = 0; k < 3; ++k) s.g_f[k] = (float)s.g[k];
   s.rho_s_f = (float)s.rho;
+  s.k_feat_f = (float)k_cg;
   *out = s;
   return CGDEM_OK;
 }
@@ -237,6 +242,9 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     return fail(ctx, CGDEM_E_INVALID, "null argument or n_samples < 1");
   if (cfg->precision != CGDEM_FP64 && cfg->precision != CGDEM_MIXED)
     return fail(ctx, CGDEM_E_INVALID, "unknown precision");
+  if (cfg->closure != 0 && cfg->closure != 1) return fail(ctx, CGDEM_E_INVALID, "closure must be 0 or 1");
+  if (cfg->closure && cfg->block_size != 128 && cfg->block_size > 0)
+    return fail(ctx, CGDEM_E_INVALID, "a context with the learned closure runs blocks of 128 threads");
   const int S = cfg->n_samples;
   int64_t N = 0;
   int C = 0, Cf = 0;
@@ -287,6 +295,8 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.posq_ref = cv.take<int4>(Npad);
   d.cand_tmp = cv.take<uint32_t>((size_t)cap * Npad);
   d.cand_n = cv.take<uint32_t>(Npad);
+  d.big_list = cv.take<uint32_t>(Npad);
+  d.big_n = cv.take<uint32_t>(1);
   d.tile_sums = cv.take<uint32_t>((size_t)(C + 2) / 2048 + 2);
   d.dmax2 = cv.take<unsigned>(S);
   d.F = cv.take<double4>(Npad);
@@ -307,6 +317,12 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.diag = cv.take<double>(8 * (size_t)S);
   d.staging = cv.take<double>(16 * (size_t)Npad);
   d.contact_n = cv.take<unsigned long long>(1);
+  if (cfg->closure) {
+    d.clc[0] = cv.take<float2>(Npad);
+    d.clc[1] = cv.take<float2>(Npad);
+    d.clrec = cv.take<float>((size_t)CL_COLS * Npad);
+    d.clblob = cv.take<uint8_t>(CL_BLOB);
+  }
   d.sp = cv.take<SampleDev>(S);
   d.ctl = cv.take<Ctl>(1);
   *diag_part = cv.take<double>((size_t)DIAG_BLOCKS * 8 * S);
@@ -336,8 +352,13 @@ int check_status(cgdem_ctx* ctx, cudaStream_t s) {
     return fail(ctx, CGDEM_E_CAPACITY, "a particle had %d candidates; max_neighbors is %d", c.max_cand,
                 ctx->d.cap);
   if (c.status & ST_BOND_LOST)
-    return fail(ctx, CGDEM_E_STATE, "a bonded pair left the candidate list (skin too small)");
+    return fail(ctx, CGDEM_E_STATE,
+                "a bonded pair left the candidate list (skin too small): particles %d and %d, squared "
+                "distance %llu vs squared reach %llu (fixed-point units)",
+                c.lost_i, c.lost_j, c.lost_d2, c.lost_S2);
   if (c.status & ST_NONFINITE) return fail(ctx, CGDEM_E_NONFINITE, "a force became NaN or Inf");
+  if (c.status & ST_TIMEOUT)
+    return fail(ctx, CGDEM_E_TIMEOUT, "a bounded wait of the closure network expired (corrections reset to 1)");
   return CGDEM_OK;
 }
 
@@ -487,7 +508,7 @@ int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const i
          &ctx->diag_part, &ctx->contact_cap, &ctx->any_cube);
   ctx->cfg = *cfg;
   if (ctx->cfg.block_size <= 0) ctx->cfg.block_size = 128;
-  if (ctx->cfg.block_size > 256 || ctx->cfg.block_size % 32) {
+  if (ctx->cfg.block_size != 64 && ctx->cfg.block_size != 128 && ctx->cfg.block_size != 256) {
     delete ctx;
     return CGDEM_E_INVALID;
   }
@@ -650,6 +671,59 @@ int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {
   launch_forces(ctx->d, 2, ctx->cfg.block_size, s);
   CK(cudaGetLastError());
   return CGDEM_OK;
+}
+
+int cgdem_set_closure(cgdem_ctx* ctx, const float* theta, const cgdem_closure_params* cp, int enable,
+                      void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!ctx->d.clblob) return fail(ctx, CGDEM_E_STATE, "the context was created without closure support");
+  cudaStream_t s = st(stream);
+  if (enable) {
+    if (!theta || !cp) return fail(ctx, CGDEM_E_INVALID, "enabling the closure needs theta and its parameters");
+    if (!(cp->cd_log_max >= 0.f) || !(cp->cg_log_max >= 0.f) || !(cp->cd_log_max <= 20.f) ||
+        !(cp->cg_log_max <= 20.f))
+      return fail(ctx, CGDEM_E_INVALID, "correction bounds must lie in [0, 20]");
+    // bonded pairs must stay candidates at the largest corrected surface energy
+    const double cmax = std::exp((double)cp->cg_log_max);
+    for (size_t i = 0; i < ctx->sd.size(); ++i) {
+      const SampleDev& S = ctx->sd[i];
+      const double Rs = 0.5 * ctx->sp[i].r_max, g = S.gamma * cmax;
+      const double dC = 0.5723571212766659 * std::cbrt(PI * PI * g * g * Rs / (S.Es * S.Es));
+      if (!(2.0 * dC < ctx->sp[i].skin))
+        return fail(ctx, CGDEM_E_INVALID,
+                    "sample %zu: skin %.3g must exceed twice the bond-break separation %.3g at "
+                    "the largest surface-energy correction", i, ctx->sp[i].skin, dC);
+    }
+    launch_closure_pack(theta, cp->lo, cp->hi, cp->cd_log_max, cp->cg_log_max, ctx->d.clblob, s);
+  }
+  launch_closure_set(ctx->d, enable ? 1 : 0, -1, s);
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_closure_record(cgdem_ctx* ctx, int enable, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!ctx->d.clblob) return fail(ctx, CGDEM_E_STATE, "the context was created without closure support");
+  cudaStream_t s = st(stream);
+  launch_closure_set(ctx->d, -1, enable ? 1 : 0, s);
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
+int cgdem_get_closure_data(cgdem_ctx* ctx, float* out, int64_t rows, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!ctx->d.clblob) return fail(ctx, CGDEM_E_STATE, "the context was created without closure support");
+  if (!out || rows < ctx->d.N) return fail(ctx, CGDEM_E_INVALID, "output must hold one row per particle");
+  cudaStream_t s = st(stream);
+  launch_closure_gather(ctx->d, s);
+  if (ctx->d.N)
+    CK(cudaMemcpyAsync(out, ctx->d.staging, sizeof(float) * CL_COLS * (size_t)ctx->d.N,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
 }
 
 int cgdem_get_state(cgdem_ctx* ctx, double* x, double* v, double* w, double* F, double* T,

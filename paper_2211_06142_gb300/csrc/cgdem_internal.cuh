@@ -23,6 +23,7 @@ constexpr uint32_t REC_IDX = 0x3fffffffu;     // partner index (current order)
 constexpr unsigned ST_CAPACITY = 1u;
 constexpr unsigned ST_BOND_LOST = 2u;
 constexpr unsigned ST_NONFINITE = 4u;
+constexpr unsigned ST_TIMEOUT = 8u;  // a bounded device-side wait expired
 
 // FP64 record: partner/flags + tangential spring (32 bytes)
 struct __align__(16) RecD {
@@ -68,7 +69,22 @@ struct SampleDev {
   float L_f[3], Rc_f, H_f, r_out_f;
   float rebuild_q2;  // rebuild when (max displacement in fixed units)^2 exceeds this
   float c_inv_h_f[3], skin_f;
+  float k_feat_f;  // coarse-graining ratio k as a closure input
 };
+
+// Learned closure (not part of the paper): per-particle corrections
+// (c_d, c_g) of drag and surface energy from a 5-64-64-64-2 SiLU network
+// evaluated on the tensor cores in the epilogue of each step's force kernel.
+// The network's BF16 weight tiles and FP32 constants form one blob that each
+// block copies into shared memory with a bulk copy.
+constexpr int CL_COLS = 12;               // recorded floats per particle
+constexpr uint32_t CL_TILES = 20480;      // W1 [64x16] | W2 [64x64] | W3 [64x64] | W4 [16x64]
+constexpr uint32_t CL_P_B1 = 0, CL_P_B2 = 64, CL_P_B3 = 128, CL_P_B4 = 192, CL_P_MU = 196,
+                   CL_P_ISG = 204, CL_P_LO = 212, CL_P_HI = 220, CL_P_CMAX = 228;  // floats after the tiles
+constexpr uint32_t CL_BLOB = CL_TILES + 232 * 4;  // 21408 bytes
+constexpr uint32_t CL_SM_A0 = 22528;        // x_hat tile [128 x 16]
+constexpr uint32_t CL_SM_AH = 26624;        // hidden tile [128 x 64]
+constexpr uint32_t CL_SMEM = 43008 + 1024;  // dynamic shared memory of the force kernel (+ alignment)
 
 // Device control block (one per context).
 struct Ctl {
@@ -86,6 +102,12 @@ struct Ctl {
   long long cand_total;  // candidate entries summed over particles at the last rebuild
   int max_cand_next;     // accumulated by the running rebuild
   long long cand_total_next;  // set when the running step scattered porosity quanta
+  int closure;            // 1: corrections applied and the network evaluated every step
+  int record;             // 1: every force evaluation records per-particle closure data
+  // first bonded pair found missing from a rebuilt list: ids, and its squared
+  // distance and squared reach (fixed-point units) at the rebuild
+  int lost_i, lost_j;
+  unsigned long long lost_d2, lost_S2;
 };
 
 // All device pointers of a context (passed by value to kernels).
@@ -112,6 +134,8 @@ struct Dev {
   int4* posq_ref;                 // fixed-point positions at the last rebuild
   uint32_t* cand_tmp;             // rebuild scratch: candidate partners [cap][Npad]
   uint32_t* cand_n;               // rebuild scratch: candidates found per particle
+  uint32_t* big_list;             // rebuild scratch: spheres whose stencil a warp walks
+  uint32_t* big_n;
   uint32_t* tile_sums;            // rebuild scratch: cell-scan tile sums
   unsigned* dmax2;                // per-sample max squared displacement since rebuild (float bits, fixed units)
   // rebuild scratch
@@ -133,6 +157,10 @@ struct Dev {
   double* staging;                // [N * 16] host-transfer staging
   uint32_t* contact_out;          // [2 * cap_out] (i, j | bond << 31)
   unsigned long long* contact_n;
+  // learned closure (allocated when the context supports it)
+  float2* clc[2];                 // (c_d, c_g) per particle, double-buffered like the state
+  float* clrec;                   // [Npad][CL_COLS] data recorded by the last evaluation
+  uint8_t* clblob;                // network blob (CL_BLOB bytes)
   SampleDev* sp;
   Ctl* ctl;
   int N, Npad, cap, n_samples, C_total, Cf_total;

@@ -24,16 +24,16 @@
 //            the contact path holds no FP64 arithmetic and the per-particle
 //            update keeps only the FP64 additions of the integrator.
 #include "cgdem_internal.cuh"
+#include "tc05.cuh"
 
 namespace cgdem {
 
 constexpr double PI_D = 3.14159265358979323846;
 constexpr float PI_F = 3.14159265358979323846f;
 #ifndef CGDEM_FORCE_MINB
-#define CGDEM_FORCE_MINB 6  // resident blocks per SM the register budget must allow
+#define CGDEM_FORCE_MINB 3  // resident 256-thread blocks per SM the register budget must allow
 #endif
-constexpr int FORCE_BLOCK = 128;
-constexpr int WPB = FORCE_BLOCK / 32;
+constexpr int FORCE_BLOCK_MAX = 256;  // launches use 64, 128 or 256 threads (autotuned)
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
@@ -278,6 +278,85 @@ __device__ __forceinline__ int fluid_cell_fast(const SampleDev& S, double x, dou
   return S.fcell_off + (c[2] * S.nf[1] + c[1]) * S.nf[0] + c[0];
 }
 
+// ---- learned closure: the network's forward pass on the tensor cores ----
+
+// all threads wait for the MMA group committed on bar; false on timeout
+__device__ __forceinline__ bool cl_wait(uint64_t* bar, uint32_t& phase) {
+  const bool ok = tc05::mbar_wait(bar, phase);
+  phase ^= 1u;
+  const int bad = __syncthreads_or(!ok);
+  tc05::fence_after_sync();
+  return bad == 0;
+}
+__device__ __forceinline__ void cl_publish() {
+  tc05::fence_smem_to_async();
+  tc05::fence_before_sync();
+  __syncthreads();
+  tc05::fence_after_sync();
+}
+
+// One forward pass over the block's 128 rows (thread t = row t, M = 128):
+// x_hat = (f - mu) inv_sigma, three SiLU layers of 64 and the 2 outputs,
+// BF16 operands from shared memory, FP32 accumulators in 64 TMEM columns.
+// sm holds the network blob (bulk copy completing on bar[0]); bar[1] tracks
+// the MMAs.  False (in every thread) if a bounded wait expired.
+__device__ bool closure_infer(const float (&f)[5], uint8_t* sm, uint64_t* bar, uint32_t tb, float& o0,
+                              float& o1) {
+  using namespace tc05;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t s0 = smem_u32(sm);
+  const bool got = mbar_wait(&bar[0], 0);
+  if (__syncthreads_or(!got)) return false;
+  const float* P = reinterpret_cast<const float*>(sm + CL_TILES);
+  float xh[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) xh[k] = (f[k] - P[CL_P_MU + k]) * P[CL_P_ISG + k];
+  *reinterpret_cast<uint4*>(sm + CL_SM_A0 + tile_off(tid, 0, 16)) =
+      make_uint4(pack_bf16x2(xh[0], xh[1]), pack_bf16x2(xh[2], xh[3]), pack_bf16x2(xh[4], 0.0f), 0u);
+  *reinterpret_cast<uint4*>(sm + CL_SM_A0 + tile_off(tid, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+  cl_publish();
+  uint32_t ph = 0;
+  const uint32_t ID64 = idesc_bf16(128, 64), ID16 = idesc_bf16(128, 16);
+  if (tid == 0) {
+    mma_bf16(tb, kdesc(s0 + CL_SM_A0, 16, 0), kdesc(s0, 16, 0), ID64, 0u);
+    mma_commit(&bar[1]);
+  }
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    if (!cl_wait(&bar[1], ph)) return false;
+    const float* bias = P + CL_P_B1 + 64 * l;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float z[16];
+      tmem_ld16(taddr(tb, 32u * warp, 16u * c), z);
+      float h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float zz = z[j] + bias[16 * c + j];
+        h[j] = zz / (1.0f + __expf(-zz));
+      }
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf)
+        *reinterpret_cast<uint4*>(sm + CL_SM_AH + tile_off(tid, 16 * c + 8 * hf, 64)) =
+            make_uint4(pack_bf16x2(h[8 * hf + 0], h[8 * hf + 1]), pack_bf16x2(h[8 * hf + 2], h[8 * hf + 3]),
+                       pack_bf16x2(h[8 * hf + 4], h[8 * hf + 5]), pack_bf16x2(h[8 * hf + 6], h[8 * hf + 7]));
+    }
+    cl_publish();
+    if (tid == 0) {
+      const uint32_t w = l == 0 ? 2048u : (l == 1 ? 10240u : 18432u);
+      for (uint32_t s = 0; s < 4; ++s)
+        mma_bf16(tb, kdesc(s0 + CL_SM_AH, 64, s), kdesc(s0 + w, 64, s), l < 2 ? ID64 : ID16, s > 0);
+      mma_commit(&bar[1]);
+    }
+  }
+  if (!cl_wait(&bar[1], ph)) return false;
+  float v[16];
+  tmem_ld16(taddr(tb, 32u * warp, 0u), v);
+  o0 = v[0] + P[CL_P_B4];
+  o1 = v[1] + P[CL_P_B4 + 1];
+  return true;
+}
+
 // Data of the particle that owns a record, broadcast to the lane evaluating it.
 template <bool MIXED>
 struct Owner;
@@ -292,8 +371,10 @@ struct Owner<false> {
   double4 P, V, W;  // x,R | v,1/m | w,1/I
 };
 
-template <bool MIXED, int MODE>
-__global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d) {
+// CL: the context carries the learned closure (blocks of 128 threads; more
+// registers per thread for the closure data and the network epilogue).
+template <bool MIXED, int MODE, bool CL>
+__global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB) k_forces(Dev d) {
   using T = typename std::conditional<MIXED, float, double>::type;
   Ctl* ctl = d.ctl;
   const int cur = ctl->cur;
@@ -306,11 +387,42 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
   const int ce = d.sp[0].couple_every;
   const bool couple_next = ce == 1 || (unsigned)(m_step % ce) == 0u;
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad (multiple of 32)
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad exactly
   const int wbase = p - lane;
   const bool valid = p < d.N;
-  if (wbase >= d.Npad) return;  // whole warps only (Npad is a multiple of 256)
+
+  // learned closure: corrections in use, network evaluated after the
+  // forces (blocks of 128), per-particle data recorded
+  const bool use_c = CL && ctl->closure != 0;
+  const bool net = use_c && MODE != MODE_FORCES;
+  const bool rec = CL && ctl->record != 0;
+  const bool feat = net || rec;
+  __shared__ __align__(8) uint64_t cl_bar[2];
+  __shared__ uint32_t cl_tmem;
+  extern __shared__ uint8_t cl_raw[];
+  uint8_t* cl_sm = nullptr;
+  if (net) {
+    const uint32_t a = tc05::smem_u32(cl_raw);
+    cl_sm = cl_raw + (((a + 1023u) & ~1023u) - a);
+    if (threadIdx.x == 0) {
+      tc05::mbar_init(&cl_bar[0], 1);
+      tc05::mbar_init(&cl_bar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the weights arrive while the contacts are evaluated
+      tc05::mbar_expect_tx(&cl_bar[0], CL_BLOB);
+      tc05::bulk_g2s(cl_sm, d.clblob, CL_BLOB, &cl_bar[0]);
+    }
+    if (threadIdx.x < 32) {
+      tc05::tmem_alloc(&cl_tmem, 64);
+      tc05::tmem_relinquish();
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+  }
+  float2 my_c = make_float2(1.0f, 1.0f);
+  if (use_c && valid) my_c = d.clc[cur][p];
 
   // ---- own particle, contact phase ----
   Owner<MIXED> me;
@@ -351,6 +463,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
   const uint32_t lo = d.roff[rc][p] - seg;
   const uint32_t total = __shfl_sync(FULL, lo + ncnt, 31);
   V3<T> F = v3<T>(0, 0, 0), Tq = v3<T>(0, 0, 0);
+  T Zacc = 0, Dacc = 0, Cacc = 0;  // closure data: active contacts, summed overlap, bond capacity
   // mixed: each lane's record for the next round is loaded one round ahead
   uint4 rnext = make_uint4(0u, 0u, 0u, 0u);
   if (MIXED && lane < (int)total) rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + lane];
@@ -370,6 +483,8 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
       if (c < 32 && loc <= e) own = c;
     }
     const int os = __shfl_sync(FULL, si, own);
+    const float o_cg = use_c ? __shfl_sync(FULL, my_c.y, own) : 1.0f;
+    T e_z = 0, e_d = 0, e_c = 0;
     Owner<MIXED> o;
     if constexpr (MIXED) {
       o.pq.x = __shfl_sync(FULL, me.pq.x, own);
@@ -451,6 +566,14 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
             const V3<float> n = v3<float>(dx * invd, dy * invd, dz * invd);
             const float Ri = o.va.w, Rj = qa.w, mi = o.wa.w, mj = qb.w;
             const float Rs = __fdividef(Ri * Rj, Ri + Rj);
+            // surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure
+            float gam_f = S.gamma_f;
+            double gam_d = S.gamma;
+            if (use_c && bonded) {
+              const float qcg = d.clc[cur][q].y;
+              gam_f = S.gamma_f * sqrtf(o_cg * qcg);
+              gam_d = S.gamma * sqrt((double)o_cg * (double)qcg);
+            }
             double d2e = 0.0, Se = 0.0;
             bool have_exact = false;
             if (need_exact) {
@@ -461,8 +584,8 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
             if (bonded) {
               bool broken;
               float dC = 0.0f, bandf = 4.0f * S.dq_f;
-              if (S.gamma_f > 0.f) {
-                const float xs = m_cbrt(__fdividef(PI_F * PI_F * S.gamma_f * S.gamma_f * Rs, S.Es_f * S.Es_f));
+              if (gam_f > 0.f) {
+                const float xs = m_cbrt(__fdividef(PI_F * PI_F * gam_f * gam_f * Rs, S.Es_f * S.Es_f));
                 dC = -0.57235712127666594f * xs;
                 bandf += 2e-5f * fabsf(dC);
               }
@@ -479,7 +602,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
                 }
                 const double Rid = fabs(A.w), Rjd = fabs(B.w);
                 const double Rsd = __dmul_rn(Rid, Rjd) / __dadd_rn(Rid, Rjd);
-                broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, S.gamma);
+                broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, gam_d);
               }
               if (broken) bonded = false;
             }
@@ -495,12 +618,17 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
               const V3<float> vc = v3<float>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
               V3<float> Fi, Ft;
               V3<float> xif = v3<float>((float)xi.x, (float)xi.y, (float)xi.z);
-              contact_law<float>(delta, n, vrel, vc, Rs, ms, S.gamma_f, bonded, S.Es_f, S.Gs_f,
+              contact_law<float>(delta, n, vrel, vc, Rs, ms, gam_f, bonded, S.Es_f, S.Gs_f,
                                  S.beta_f, S.mu_f32, S.dt_f, S.coulomb_mode, xif, Fi, Ft);
               xi = v3<T>(xif.x, xif.y, xif.z);
               const V3<float> nFt = cross3(n, Ft);
               Fc = v3<T>(Fi.x, Fi.y, Fi.z);
               Tc = v3<T>(Ri * nFt.x, Ri * nFt.y, Ri * nFt.z);
+              if (feat) {
+                e_z = 1;
+                e_d = delta;
+                e_c = bonded ? 0.5f * 3.0f * PI_F * gam_f * Rs : 0.0f;
+              }
             }
           }
         }
@@ -521,7 +649,9 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
             const double dist = sqrt(d2);
             const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
             const double delta = __dsub_rn(Sd, dist);
-            if (bonded && bond_breaks_exact(delta, Rs, S.Es, S.gamma)) bonded = false;
+            double gam_d = S.gamma;  // gamma sqrt(c_g,i c_g,j) under the closure
+            if (use_c && bonded) gam_d = S.gamma * sqrt((double)o_cg * (double)d.clc[cur][q].y);
+            if (bonded && bond_breaks_exact(delta, Rs, S.Es, gam_d)) bonded = false;
             act = bonded || touching;
             if (act && dist > 0.0) {
               const double4 QV = d.vel[cur][q];
@@ -537,12 +667,17 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
               const V3<double> vc = v3<double>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
               V3<double> Fi, Ft;
               V3<double> xid = v3<double>((double)xi.x, (double)xi.y, (double)xi.z);
-              contact_law<double>(delta, n, vrel, vc, Rs, ms, S.gamma, bonded, S.Es, S.Gs, S.beta,
+              contact_law<double>(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S.Es, S.Gs, S.beta,
                                   S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft);
               xi = v3<T>(xid.x, xid.y, xid.z);
               const V3<double> nFt = cross3(n, Ft);
               Fc = v3<T>(Fi.x, Fi.y, Fi.z);
               Tc = v3<T>(Ri * nFt.x, Ri * nFt.y, Ri * nFt.z);
+              if (feat) {
+                e_z = 1;
+                e_d = delta;
+                e_c = bonded ? 0.5 * 3.0 * PI_D * gam_d * Rs : 0.0;
+              }
             } else if (act) {
               act = false;  // coincident centres: no normal defined
             }
@@ -614,12 +749,43 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
         Tq.y += s4;
         Tq.z += s5;
       }
+      if (feat) {  // the closure data, same segments
+        T c6 = e_z, c7 = e_d, c8 = e_c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int ku = __shfl_up_sync(FULL, key, off);
+          const T u6 = __shfl_up_sync(FULL, c6, off);
+          const T u7 = __shfl_up_sync(FULL, c7, off);
+          const T u8 = __shfl_up_sync(FULL, c8, off);
+          if (lane >= off && ku == key) {
+            c6 += u6;
+            c7 += u7;
+            c8 += u8;
+          }
+        }
+        const T s6 = __shfl_sync(FULL, c6, src);
+        const T s7 = __shfl_sync(FULL, c7, src);
+        const T s8 = __shfl_sync(FULL, c8, src);
+        if (b > a) {
+          Zacc += s6;
+          Dacc += s7;
+          Cacc += s8;
+        }
+      }
     }
   }
 
   // ---- per-particle epilogue: walls, body forces, drag, integration ----
   float my_disp2 = -1.f;
   bool coupled = false;
+  float ft[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // closure inputs of this particle
+  bool net_row = false;
+  if (rec && valid) {  // inactive particles record zeros
+    float4* r4 = reinterpret_cast<float4*>(d.clrec + (size_t)p * CL_COLS);
+    r4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   if (valid) {
     const SampleDev& S = d.sp[si];
     double4 P;
@@ -697,7 +863,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
           F.y -= rf * Vp * g1;
           F.z -= rf * Vp * g2;
         }
-        if (S.use_drag) {
+        if (S.use_drag || feat) {
           const int fc = fc0;
           const unsigned long long Sc = d.vf[vfc][fc];
           T scount;
@@ -715,10 +881,32 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
             U = v3<T>(u.x, u.y, u.z);
           }
           const V3<T> w = v3<T>(U.x / nc - vi.x, U.y / nc - vi.y, U.z / nc - vi.z);
-          const V3<T> fd = drag_force<T>(rf, muf, T(2) * Ri, w, nc);
-          F.x += fd.x;
-          F.y += fd.y;
-          F.z += fd.z;
+          V3<T> fd = v3<T>(0, 0, 0);
+          if (S.use_drag) {
+            fd = drag_force<T>(rf, muf, T(2) * Ri, w, nc);
+            if (use_c) {  // drag correction of the closure
+              fd.x *= (T)my_c.x;
+              fd.y *= (T)my_c.x;
+              fd.z *= (T)my_c.x;
+            }
+            F.x += fd.x;
+            F.y += fd.y;
+            F.z += fd.z;
+          }
+          if (feat) {
+            net_row = true;
+            ft[0] = (float)(T(1) - nc);
+            ft[1] = (float)m_sqrt(dot3(w, w));
+            ft[2] = S.k_feat_f;
+            ft[3] = (float)Zacc;
+            ft[4] = Zacc > T(0) ? (float)(Dacc / (Zacc * T(2) * Ri)) : 0.f;
+            if (rec) {
+              float4* r4 = reinterpret_cast<float4*>(d.clrec + (size_t)p * CL_COLS);
+              r4[0] = make_float4(ft[0], ft[1], ft[2], ft[3]);
+              r4[1] = make_float4(ft[4], (float)fd.x, (float)fd.y, (float)fd.z);
+              r4[2] = make_float4((float)Cacc, (float)(fc - S.fcell_off), my_c.x, my_c.y);
+            }
+          }
         }
       }
       if (!isfinite(F.x + F.y + F.z + Tq.x + Tq.y + Tq.z)) latch(ctl, ST_NONFINITE);
@@ -841,6 +1029,31 @@ __global__ void __launch_bounds__(FORCE_BLOCK, CGDEM_FORCE_MINB) k_forces(Dev d)
     }
   }
 
+  // ---- learned closure: corrections for the next evaluation ----
+  if (net) {
+    float o0 = 0.f, o1 = 0.f;
+    const bool ok = closure_infer(ft, cl_sm, cl_bar, cl_tmem, o0, o1);
+    if (valid) {
+      float2 c = make_float2(1.0f, 1.0f);  // plain coarse-graining outside the training range
+      if (ok && net_row) {
+        const float* P = reinterpret_cast<const float*>(cl_sm + CL_TILES);
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) inside = inside && ft[k] >= P[CL_P_LO + k] && ft[k] <= P[CL_P_HI + k];
+        if (inside) {
+          const float cdm = P[CL_P_CMAX], cgm = P[CL_P_CMAX + 1];
+          c.x = expf(fminf(fmaxf(o0, -cdm), cdm));
+          c.y = expf(fminf(fmaxf(o1, -cgm), cgm));
+        }
+      }
+      d.clc[nxt][p] = c;
+    }
+    if (!ok && threadIdx.x == 0) latch(ctl, ST_TIMEOUT);
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc05::tmem_dealloc(cl_tmem, 64);
+  }
+
   if (MODE != MODE_MID) return;
 
   // ---- bookkeeping: displacement since rebuild, porosity rotation, step ----
@@ -888,17 +1101,30 @@ __global__ void k_after_canon(Dev d) {
 }
 
 void launch_forces(const Dev& d, int mode, int block, cudaStream_t s) {
-  (void)block;
-  const int grid = (d.Npad + FORCE_BLOCK - 1) / FORCE_BLOCK;
+  // Npad is a multiple of 256, so every block size divides it exactly
+  // (a context with the learned closure runs blocks of 128: one M = 128 tile)
+  const int B = d.clblob ? 128 : ((block == 64 || block == 256) ? block : 128);
+  const int grid = d.Npad / B;
+  const size_t sm = d.clblob ? CL_SMEM : 0;
   if (d.N == 0) return;
-  if (d.mixed) {
-    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES><<<grid, FORCE_BLOCK, 0, s>>>(d);
-    else if (mode == MODE_MID) k_forces<true, MODE_MID><<<grid, FORCE_BLOCK, 0, s>>>(d);
-    else k_forces<true, MODE_CANON><<<grid, FORCE_BLOCK, 0, s>>>(d);
+  if (d.clblob) {
+    if (d.mixed) {
+      if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, true><<<grid, B, sm, s>>>(d);
+      else if (mode == MODE_MID) k_forces<true, MODE_MID, true><<<grid, B, sm, s>>>(d);
+      else k_forces<true, MODE_CANON, true><<<grid, B, sm, s>>>(d);
+    } else {
+      if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, true><<<grid, B, sm, s>>>(d);
+      else if (mode == MODE_MID) k_forces<false, MODE_MID, true><<<grid, B, sm, s>>>(d);
+      else k_forces<false, MODE_CANON, true><<<grid, B, sm, s>>>(d);
+    }
+  } else if (d.mixed) {
+    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, false><<<grid, B, 0, s>>>(d);
+    else if (mode == MODE_MID) k_forces<true, MODE_MID, false><<<grid, B, 0, s>>>(d);
+    else k_forces<true, MODE_CANON, false><<<grid, B, 0, s>>>(d);
   } else {
-    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES><<<grid, FORCE_BLOCK, 0, s>>>(d);
-    else if (mode == MODE_MID) k_forces<false, MODE_MID><<<grid, FORCE_BLOCK, 0, s>>>(d);
-    else k_forces<false, MODE_CANON><<<grid, FORCE_BLOCK, 0, s>>>(d);
+    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, false><<<grid, B, 0, s>>>(d);
+    else if (mode == MODE_MID) k_forces<false, MODE_MID, false><<<grid, B, 0, s>>>(d);
+    else k_forces<false, MODE_CANON, false><<<grid, B, 0, s>>>(d);
   }
   if (mode == MODE_CANON) k_after_canon<<<1, 1, 0, s>>>(d);
 }

@@ -151,6 +151,7 @@ __global__ void k_rb_permute(Dev d) {
   const uint32_t o = d.perm[p];
   d.inv_perm[o] = (uint32_t)p;
   d.cand_n[p] = 0u;
+  if (p == 0) *d.big_n = 0u;
   double4 P = d.pos[cur][o];
   d.pos[nxt][p] = P;
   d.vel[nxt][p] = d.vel[cur][o];
@@ -169,6 +170,7 @@ __global__ void k_rb_permute(Dev d) {
   d.sample[pn][p] = s;
   d.fcell[pn][p] = d.fcell[pc][o];
   d.vq[pn][p] = d.vq[pc][o];
+  if (d.clc[0]) d.clc[nxt][p] = d.clc[cur][o];
   if (d.mixed && d.wallhf[0]) {
     for (int w = 0; w < 3; ++w)
       d.wallhf[pn][(size_t)w * d.Npad + p] = d.wallhf[pc][(size_t)w * d.Npad + o];
@@ -196,6 +198,8 @@ __global__ void k_rb_ft_store(Dev d) {
   d.F[p] = st[p];
   d.T[p] = st[d.Npad + p];
 }
+
+constexpr int BIG_STENCIL = 27;  // stencils of more than 3^3 cells are walked by a warp
 
 // Candidate pairs: d^2 < (Ri + Rj + skin)^2 in fixed point (exact integer
 // test).  Each pair is found once, from its larger sphere (ties: higher
@@ -234,6 +238,13 @@ __global__ void k_rb_pairs(Dev d) {
     }
   }
   const unsigned long long skin_q = (unsigned)S.skin_q;
+  // a large sphere's stencil is walked by a whole warp in k_rb_pairs_big:
+  // its cells are serial dependent loads, and one thread would set the
+  // kernel's time
+  if ((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) > BIG_STENCIL) {
+    d.big_list[atomicAdd(d.big_n, 1u)] = (uint32_t)p;
+    return;
+  }
   for (int az = lo[2]; az <= hi[2]; ++az) {
     const int z = per && !all[2] ? (az + S.nc[2]) % S.nc[2] : az;
     for (int ay = lo[1]; ay <= hi[1]; ++ay) {
@@ -265,12 +276,81 @@ __global__ void k_rb_pairs(Dev d) {
   }
 }
 
+// Candidate pairs of the large spheres deferred by k_rb_pairs: one warp per
+// sphere, the lanes sharing its stencil cells.
+__global__ void k_rb_pairs_big(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int nxt = d.ctl->cur ^ 1;
+  const int pn = d.ctl->pcur ^ 1;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nbig = (int)*d.big_n;
+  const int Npad = d.Npad, cap = d.cap;
+  for (int b = gw; b < nbig; b += nw) {
+    const int p = (int)d.big_list[b];
+    const int4 pq = d.posq[nxt][p];
+    const SampleDev& S = d.sp[d.sample[pn][p]];
+    const uint32_t o = d.perm[p];
+    const int lc = (int)d.pcell[o] - S.cell_off;
+    const int cc[3] = {lc % S.nc[0], (lc / S.nc[0]) % S.nc[1], lc / (S.nc[0] * S.nc[1])};
+    const bool per = S.kind == CGDEM_PERIODIC_BOX;
+    const float reach = 2.0f * (float)pq.w * S.dq_f + S.skin_f;
+    int lo[3], ext[3];
+    bool all[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int r = (int)ceilf(reach * S.c_inv_h_f[k] * 1.000001f);
+      all[k] = per && 2 * r + 1 >= S.nc[k];
+      int l = all[k] ? 0 : cc[k] - r;
+      int h = all[k] ? S.nc[k] - 1 : cc[k] + r;
+      if (!per) {
+        l = max(l, 0);
+        h = min(h, S.nc[k] - 1);
+      }
+      lo[k] = l;
+      ext[k] = h - l + 1;
+    }
+    const unsigned long long skin_q = (unsigned)S.skin_q;
+    const int total = ext[0] * ext[1] * ext[2];
+    for (int t = lane; t < total; t += 32) {
+      const int ax = lo[0] + t % ext[0];
+      const int ay = lo[1] + (t / ext[0]) % ext[1];
+      const int az = lo[2] + t / (ext[0] * ext[1]);
+      const int x = per && !all[0] ? (ax + S.nc[0]) % S.nc[0] : ax;
+      const int y = per && !all[1] ? (ay + S.nc[1]) % S.nc[1] : ay;
+      const int z = per && !all[2] ? (az + S.nc[2]) % S.nc[2] : az;
+      const int c = S.cell_off + (z * S.nc[1] + y) * S.nc[0] + x;
+      const uint32_t j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+      for (uint32_t q = j0; q < j1; ++q) {
+        const int4 qq = d.posq[nxt][q];
+        if (qq.w <= 0) continue;
+        if (qq.w > pq.w || (qq.w == pq.w && (int)q <= p)) continue;
+        const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
+        const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
+        const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
+        const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                      (unsigned long long)((long long)dy * dy) +
+                                      (unsigned long long)((long long)dz * dz);
+        const unsigned long long Sq = (unsigned long long)(unsigned)pq.w + (unsigned)qq.w + skin_q;
+        if (d2 < Sq * Sq) {
+          const uint32_t a = atomicAdd(&d.cand_n[p], 1u);
+          if (a < (uint32_t)cap) d.cand_tmp[(size_t)a * Npad + p] = q;
+          const uint32_t bq = atomicAdd(&d.cand_n[q], 1u);
+          if (bq < (uint32_t)cap) d.cand_tmp[(size_t)bq * Npad + q] = (uint32_t)p;
+        }
+      }
+    }
+  }
+}
+
 // Sort each list by partner, pack the records of a warp contiguously and
 // carry the contact history of the old records by particle pair.
 template <bool MIXED>
 __global__ void k_rb_lists(Dev d) {
   if (!d.ctl->rebuild) return;
   const int nxt = d.ctl->cur ^ 1;
+  const int pn = d.ctl->pcur ^ 1;
   const int rc = d.ctl->rec_cur, rn = rc ^ 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad exactly
   const int lane = threadIdx.x & 31;
@@ -368,7 +448,20 @@ __global__ void k_rb_lists(Dev d) {
         *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, h0.z, h0.w);
         *(reinterpret_cast<double2*>(rr) + 1) = h1;
       }
-    } else if (pf & REC_BOND) {
+    } else if ((pf & REC_BOND) && d.posq[nxt][qn].w > 0) {
+      // a bond may leave the list only with a partner that left the domain
+      if (atomicCAS(&d.ctl->lost_i, -1, d.id[pn][p]) == -1) {
+        const int4 qq = d.posq[nxt][qn];
+        const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
+        const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
+        const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
+        d.ctl->lost_j = d.id[pn][qn];
+        d.ctl->lost_d2 = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+                         (unsigned long long)((long long)dz * dz);
+        const unsigned long long S = (unsigned long long)(unsigned)pq.w + (unsigned)qq.w +
+                                     (unsigned)d.sp[d.sample[pn][p]].skin_q;
+        d.ctl->lost_S2 = S * S;
+      }
       latch(d.ctl, ST_BOND_LOST);
     }
   }
@@ -657,6 +750,10 @@ __global__ void k_init_state(Dev d) {
   d.removed_step[p] = -1;
   d.cnt[0][p] = 0;
   d.cnt[1][p] = 0;
+  if (d.clc[0]) {
+    d.clc[0][p] = make_float2(1.0f, 1.0f);
+    d.clc[1][p] = make_float2(1.0f, 1.0f);
+  }
   for (int w = 0; w < 3; ++w) {
     if (d.mixed && d.wallhf[cur]) d.wallhf[cur][(size_t)w * d.Npad + p] = make_float4(0, 0, 0, 0);
     if (!d.mixed && d.wallh[cur]) d.wallh[cur][(size_t)w * d.Npad + p] = make_double4(0, 0, 0, 0);
@@ -679,6 +776,12 @@ __global__ void k_init_ctl(Dev d) {
   c->cand_total = 0;
   c->cand_total_next = 0;
   c->coupled = 0;
+  c->closure = 0;
+  c->record = 0;
+  c->lost_i = -1;
+  c->lost_j = -1;
+  c->lost_d2 = 0;
+  c->lost_S2 = 0;
   for (int s = 0; s < d.n_samples; ++s) d.dmax2[s] = 0u;
 }
 
@@ -789,6 +892,7 @@ void launch_rebuild(const Dev& d, cudaStream_t s) {
   k_rb_ft_gather<<<G, B, 0, s>>>(d);
   k_rb_ft_store<<<G, B, 0, s>>>(d);
   k_rb_pairs<<<G, B, 0, s>>>(d);
+  k_rb_pairs_big<<<4 * 152, 256, 0, s>>>(d);
   const int Gp = nblk(d.Npad, B);
   if (d.mixed) k_rb_lists<true><<<Gp, B, 0, s>>>(d);
   else k_rb_lists<false><<<Gp, B, 0, s>>>(d);
@@ -833,6 +937,42 @@ void launch_kick_final(const Dev& d, cudaStream_t s) {
 
 void launch_cube_after_mid(const Dev& d, cudaStream_t s) {
   if (d.N) k_vf_scatter_cube_next<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+// ---------------------------------------------------------------------------
+// learned closure: switch, reset of the corrections, recorded data by id
+// ---------------------------------------------------------------------------
+
+__global__ void k_closure_set(Dev d, int enable, int record) {
+  if (enable >= 0) d.ctl->closure = enable;
+  if (record >= 0) d.ctl->record = record;
+}
+
+__global__ void k_closure_reset(Dev d) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  d.clc[0][p] = make_float2(1.0f, 1.0f);
+  d.clc[1][p] = make_float2(1.0f, 1.0f);
+}
+
+// recorded rows in particle-id order, into the staging buffer (floats)
+__global__ void k_closure_gather(Dev d) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const int i = d.id[d.ctl->pcur][p];
+  float* out = reinterpret_cast<float*>(d.staging);
+  const float* in = d.clrec + (size_t)p * CL_COLS;
+#pragma unroll
+  for (int k = 0; k < CL_COLS; ++k) out[(size_t)i * CL_COLS + k] = in[k];
+}
+
+void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s) {
+  k_closure_set<<<1, 1, 0, s>>>(d, enable, record);
+  if (enable >= 0 && d.N) k_closure_reset<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_closure_gather(const Dev& d, cudaStream_t s) {
+  if (d.N) k_closure_gather<<<nblk(d.N, 256), 256, 0, s>>>(d);
 }
 
 void launch_init(const Dev& d, cudaStream_t s) {

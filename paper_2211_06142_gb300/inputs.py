@@ -232,7 +232,10 @@ def cylinder_sample(d: np.ndarray, seed: int, d50: float = 0.25e-3, scale: float
     H = 30.0 * d50 * scale
     r_out = 3.0 * d50
     Vs = float((4.0 / 3.0 * math.pi * R ** 3).sum())
-    h_bed = min(Vs / (phi * math.pi * (Rc ** 2 - r_out ** 2)), H)
+    h_bed = Vs / (phi * math.pi * (Rc ** 2 - r_out ** 2))
+    if not h_bed <= H:
+        raise ValueError(f"{name}: the cylinder (Rc {Rc:.3g}, H {H:.3g}, cavity {r_out:.3g}) cannot hold "
+                         f"the grains at solid fraction {phi}")
     x = pack_cylinder(R, Rc, r_out, h_bed, rng)
     v = np.zeros_like(x)
     w = np.zeros_like(x)
@@ -255,7 +258,7 @@ def cached(fn, *args, **kw) -> Sample:
     import pickle
 
     root = os.environ.get("CGDEM_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cgdem"))
-    key = hashlib.sha1(repr((fn.__name__, args, sorted(kw.items()), 3)).encode()).hexdigest()[:16]
+    key = hashlib.sha1(repr((fn.__name__, args, sorted(kw.items()), 5)).encode()).hexdigest()[:16]
     path = os.path.join(root, f"{fn.__name__}-{key}.pkl")
     if os.path.exists(path):
         with open(path, "rb") as f:
@@ -283,3 +286,91 @@ def fine_cylinder(n: int = 200_000, seed: int = 1, U_in: float = 1e-4) -> Sample
     """200,000 spheres, same PSD, in the 40x40x20-cell sand-production cylinder,
     with the paper's injection velocity of 1e-4 m/s (Sec. 3.1)."""
     return cylinder_sample(fine_diameters(n, seed), seed, U_in=U_in, name="cylinder-200k")
+
+
+# ---------------------------------------------------------------------------
+# batched ensemble (a calibration sweep): many independent samples
+# ---------------------------------------------------------------------------
+
+@dataclass
+class SampleSpec:
+    """Description of one ensemble member before coarse-graining."""
+    index: int
+    n_grains: int
+    d50: float
+    gamma: float         # fine-scale surface energy [J/m^2]
+    k: int               # coarse-graining ratio
+    kind: int            # 0 periodic cube, 1 cylinder
+    seed: int
+    d_fine: np.ndarray   # n_grains * k^3 fine diameters (a PSD realisation)
+
+
+def ensemble_specs(n_samples: int = 64, seed: int = 3, n_lo: int = 5000, n_hi: int = 50000,
+                   d50_lo: float = 0.15e-3, d50_hi: float = 0.35e-3, g_lo: float = 0.1,
+                   g_hi: float = 2.0, ks=(1, 2, 3)):
+    """Seeded draws of the ensemble: grain count uniform in [n_lo, n_hi], d50
+    uniform, surface energy uniform, ratio k from ks, half periodic and half
+    cylindrical.  Each member carries n_grains * k^3 fine diameters, from
+    which the coarse-graining rule makes n_grains grains."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_samples):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        d50 = float(rng.uniform(d50_lo, d50_hi))
+        g = float(rng.uniform(g_lo, g_hi))
+        k = int(ks[int(rng.integers(0, len(ks)))])
+        kind = i % 2
+        r2 = np.random.default_rng(seed * 1000 + i)
+        d = lognormal_diameters(n * k ** 3, d50, 0.4, 0.4 * d50, 2.4 * d50, r2)
+        out.append(SampleSpec(i, n, d50, g, k, kind, seed * 1000 + i, d))
+    return out
+
+
+def pack_member(spec: SampleSpec, d_grain: np.ndarray, U: float = 0.01) -> Sample:
+    """Pack one ensemble member with the given grain diameters.  Periodic
+    members: cube at solid fraction 0.55, 8 fluid cells per side.  Cylinder
+    members: a cylinder of height 0.75 Rc whose bed (0.7 of the height,
+    around the central cavity) holds the grains at solid fraction 0.55,
+    outlet 3 grain d50, fluid cells of two grain d50 (the grain d50 is k
+    times the fine d50)."""
+    mat = dict(rho=2650.0, E=1e8, nu=0.3, e=0.5, mu=0.5, gamma=spec.gamma)
+    if spec.kind == 0:
+        return periodic_sample(d_grain, 0.55, spec.seed, nf=8, U=(0.0, 0.0, U), material=mat,
+                               name=f"ens{spec.index}-periodic")
+    R = 0.5 * np.asarray(d_grain)
+    Vs = float((4.0 / 3.0 * math.pi * R ** 3).sum())
+    d50 = spec.d50 * spec.k
+    r_out = 3.0 * d50
+    # cylinder of aspect H = 0.75 Rc whose bed (0.7 H, outside the central
+    # cavity of radius r_out) holds Vs at solid fraction 0.55:
+    # Vs = 0.55 pi (Rc^2 - r_out^2) 0.525 Rc, solved by bisection
+    a, b = r_out, r_out + (Vs / (0.55 * math.pi * 0.525)) ** (1.0 / 3.0) + r_out
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        if 0.55 * math.pi * (m * m - r_out * r_out) * 0.525 * m < Vs:
+            a = m
+        else:
+            b = m
+    Rc = 0.5 * (a + b)
+    scale = Rc / (40.0 * d50)
+    nf = (max(4, int(round(40 * scale))), max(4, int(round(40 * scale))), max(2, int(round(20 * scale))))
+    return cylinder_sample(d_grain, spec.seed, d50=d50, scale=scale, nf=nf, U_in=U, material=mat,
+                           name=f"ens{spec.index}-cylinder")
+
+
+def _pack_job(args):
+    spec, d_grain, U = args
+    return pack_member(spec, d_grain, U)
+
+
+def pack_ensemble(specs, grain_diameters, U: float = 0.01, workers: int = 0):
+    """Pack every member (in parallel worker processes started with spawn)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    jobs = [(s, d, U) for s, d in zip(specs, grain_diameters)]
+    w = workers or min(len(jobs), os.cpu_count() or 1)
+    if w <= 1:
+        return [_pack_job(j) for j in jobs]
+    with cf.ProcessPoolExecutor(max_workers=w, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_pack_job, jobs))

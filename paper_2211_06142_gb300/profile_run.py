@@ -1,0 +1,82 @@
+"""Short runs of the library's kernels for a profiler (ncu) to capture.
+
+    python -m paper_2211_06142_gb300.profile_run step [mixed|fp64] [steps]
+        the fused step on the 200,000-sphere sand-production cylinder
+    python -m paper_2211_06142_gb300.profile_run closure [steps]
+        the step with the learned closure on the same cylinder at SSW k = 2
+    python -m paper_2211_06142_gb300.profile_run mlp [n] [iters]
+        full-batch training steps of the closure network on n samples
+
+Each prints its counters and "ok" when it ends without an error.
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+
+def _cylinder_ctx(precision, closure=False, k=1):
+    from . import cgdem
+    from . import inputs as I
+    from . import workloads as W
+    s = I.cached(I.fine_cylinder) if k == 1 else W.coarse_cylinder(k=k)
+    m = s.material
+    Rbar = float(np.mean(s.R ** 3)) ** (1 / 3)
+    dt = 0.2 * cgdem.cgdem_rayleigh_dt(Rbar, m["rho"], m["E"], m["nu"])
+    skin = (0.06 if closure else 0.02) * 2 * float(s.R.max())
+    p = cgdem.sample_params(s, dt, skin, k=k, scheme=cgdem.CG_SSW if k > 1 else cgdem.CG_NONE)
+    ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=64 if closure else 48,
+                        closure=closure)
+    ctx.set_fluid_velocity(s.Us)
+    ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
+    ctx.compute_forces()
+    return ctx
+
+
+def main(argv):
+    import torch
+
+    from . import build as B
+    from . import cgdem
+    B.build()
+    what = argv[0] if argv else "step"
+    if what == "step":
+        prec = cgdem.FP64 if len(argv) > 1 and argv[1] == "fp64" else cgdem.MIXED
+        steps = int(argv[2]) if len(argv) > 2 else 12
+        ctx = _cylinder_ctx(prec)
+        ctx.step(steps)
+        torch.cuda.synchronize()
+        print("counters", ctx.counters())
+        ctx.status()
+    elif what == "closure":
+        steps = int(argv[1]) if len(argv) > 1 else 12
+        ctx = _cylinder_ctx(cgdem.MIXED, closure=True, k=2)
+        rng = np.random.default_rng(0)
+        theta = np.zeros(cgdem.MLP_NPARAMS, np.float32)
+        theta[5:10] = 1.0
+        theta[10:] = rng.normal(0, 0.1, cgdem.MLP_NPARAMS - 10)
+        ctx.set_closure(theta, [-1e9] * 5, [1e9] * 5, 3.0, 0.5)
+        ctx.step(steps)
+        torch.cuda.synchronize()
+        print("counters", ctx.counters())
+        ctx.status()
+    elif what == "mlp":
+        n = int(argv[1]) if len(argv) > 1 else 65536
+        iters = int(argv[2]) if len(argv) > 2 else 3
+        rng = np.random.default_rng(0)
+        theta = np.zeros(cgdem.MLP_NPARAMS, np.float32)
+        theta[5:10] = 1.0
+        theta[10:] = rng.normal(0, 0.1, cgdem.MLP_NPARAMS - 10)
+        net = cgdem.Closure(theta)
+        X = rng.normal(size=(n, 5)).astype(np.float32)
+        Y = rng.normal(size=(n, 2)).astype(np.float32)
+        hist = net.train(X, Y, np.ones_like(Y), iters, 1e-3)
+        print("loss", hist.tolist())
+    else:
+        raise SystemExit(__doc__)
+    print("ok")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
