@@ -146,11 +146,11 @@ def kernel_traffic(kernel_file, kernel):
     return None
 
 
-def build_context(s, precision, dt, skin, device, max_neighbors=48):
+def build_context(s, precision, dt, skin, device, max_neighbors=48, block=128, cell_scale=0.0):
     from paper_2211_06142_gb300 import cgdem
     p = cgdem.sample_params(s, dt, skin)
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=max_neighbors,
-                        block_size=128, steps_per_graph=32, device=device)
+                        block_size=block, cell_scale=cell_scale, steps_per_graph=32, device=device)
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     ctx.compute_forces()
@@ -345,9 +345,19 @@ def main():
     s = make_workload(args.n, 1 + rank)
     N = len(s.R)
     dt, skin = step_params(s)
+    # search cells, force-kernel block and skin from the autotuner (cached per workload)
+    tune = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "cached": False, "trials": []}
+    if not args.no_tune:
+        from paper_2211_06142_gb300 import autotune as A
+        t0 = time.perf_counter()
+        tune = A.autotune([cgdem.sample_params(s, dt, skin)], [N], (s.x, s.v, s.w, s.R), s.Us,
+                          cgdem.MIXED, device=device)
+        tune["seconds"] = time.perf_counter() - t0
+    skin = tune["skin_frac"] * 2 * float(s.R.max())
+    knobs = dict(block=tune["block"], cell_scale=tune["cell_scale"])
 
     # ---- mixed precision (headline) ----
-    ctx = build_context(s, cgdem.MIXED, dt, skin, device)
+    ctx = build_context(s, cgdem.MIXED, dt, skin, device, **knobs)
     ctx.step(W)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
@@ -384,7 +394,7 @@ def main():
     del ctx
 
     # ---- FP64 form ----
-    ctx64 = build_context(s, cgdem.FP64, dt, skin, device)
+    ctx64 = build_context(s, cgdem.FP64, dt, skin, device, **knobs)
     ctx64.step(W)
     K64 = max(1, K // 8)
     el64 = time_steps(ctx64, torch, K64, barrier)
@@ -398,7 +408,8 @@ def main():
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
     hx, hv, hw, hR = pin(s.x), pin(s.v), pin(s.w), pin(s.R)
     p = cgdem.sample_params(s, dt, skin)
-    ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device)
+    ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device,
+                        block_size=knobs["block"], cell_scale=knobs["cell_scale"])
     ctx.set_fluid_velocity(s.Us)
     barrier()
     torch.cuda.synchronize()
@@ -432,7 +443,10 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "spheres_per_gpu": N, "precision": "mixed",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "touched bytes per step exceed half the 129 MB L2; no flush"},
+                       "l2": "touched bytes per step exceed half the 129 MB L2; no flush",
+                       "autotune": {k: tune[k] for k in ("cell_scale", "block", "skin_frac")} |
+                                   {"cached": tune.get("cached", False),
+                                    "trials": len(tune.get("trials", []))}},
             "fp64": fp64,
             "batched": batched,
             "roofline": roofline,

@@ -262,9 +262,12 @@ int cgdem_touching_pairs_noalloc(const double* x, const double* R, int64_t n,
 
 /* Same work as cgdem_step(ctx, nsteps, stream) but launched kernel by kernel
  * with CUDA events around the fused force/integrate kernel and around the
- * candidate-list rebuild sequence of every step.  out (5 doubles):
- * mean force-kernel time per step [ms], total rebuild-sequence time [ms],
- * rebuilds done, total time [ms], steps timed.  Synchronises stream. */
+ * candidate-list rebuild sequence of every step.  out (6 doubles):
+ * mean force-kernel time per step [ms], rebuild work [ms] (the per-step
+ * rebuild-sequence times summed, less the shortest one on each step: the
+ * cost of the early-returning launches, which a CUDA graph's conditional
+ * node does not run), rebuilds done, total time [ms], steps timed, the
+ * shortest per-step rebuild-sequence time [ms].  Synchronises stream. */
 int cgdem_profile_step(cgdem_ctx* ctx, int64_t nsteps, double* out, void* stream);
 
 /* ---------------------------------------------------------------------

@@ -19,9 +19,9 @@ import numpy as np
 
 from . import cgdem
 
-CELL_SCALES = (0.25, 0.35, 0.5, 0.75)
+CELL_SCALES = (0.25, 0.35, 0.5, 0.75, 1.0)
 BLOCKS = (64, 128, 256)
-SKIN_FRACS = (0.01, 0.02, 0.04)
+SKIN_FRACS = (0.01, 0.02, 0.04, 0.06, 0.09)
 
 
 def _cache_path():

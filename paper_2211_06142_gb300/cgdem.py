@@ -466,10 +466,10 @@ class Context:
         return out
 
     def profile_step(self, n):
-        out = np.zeros(5)
+        out = np.zeros(6)
         self._check(lib().cgdem_profile_step(self.h, int(n), _ptr(out), self._s()), "profile_step")
         return dict(force_ms=out[0], rebuild_ms_total=out[1], rebuilds=int(out[2]), total_ms=out[3],
-                    steps=int(out[4]))
+                    steps=int(out[4]), rebuild_floor_ms=out[5])
 
     def status(self):
         return lib().cgdem_status_sync(self.h, self._s())

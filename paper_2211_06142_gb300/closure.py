@@ -37,16 +37,17 @@ COL_CELL = 9
 
 @dataclass
 class Run:
-    """Recorded rows (one [N, 12] array per time) and the produced mass."""
+    """Recorded rows (one [N, 12] array per time), the produced mass and
+    the fluid grid's dimensions."""
     data: list
     times: list
     produced: list
-    ncell: int
+    nf: tuple
 
 
 def make_context(s, dt, skin, k, precision=cgdem.MIXED, max_neighbors=64, scheme=cgdem.CG_SSW,
-                 device="cuda:0"):
-    p = cgdem.sample_params(s, dt, skin, k=k, scheme=scheme if k > 1 else cgdem.CG_NONE)
+                 device="cuda:0", **sample_kw):
+    p = cgdem.sample_params(s, dt, skin, k=k, scheme=scheme if k > 1 else cgdem.CG_NONE, **sample_kw)
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=max_neighbors,
                         closure=True, device=device)
     ctx.set_fluid_velocity(s.Us)
@@ -71,36 +72,50 @@ def record_run(ctx, s, dt, times, closure=None):
             done += n
         data.append(ctx.closure_data().copy())
         produced.append(ctx.get_diagnostics()[0]["produced_mass"])
-    return Run(data, list(times), produced, s.grid.ncell)
+    return Run(data, list(times), produced, tuple(int(v) for v in s.grid.nf))
 
 
-def cell_sums(rows, ncell):
-    """(D [ncell], B [ncell], parcels per cell) from one recorded array."""
+def _region(cell, nf, merge):
+    """Index of the block of merge^3 fluid cells holding each cell."""
+    nx, ny, _ = nf
+    x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+    mx, my = -(-nx // merge), -(-ny // merge)
+    return ((z // merge) * my + y // merge) * mx + x // merge
+
+
+def _nregion(nf, merge):
+    return int(np.prod([-(-n // merge) for n in nf]))
+
+
+def cell_sums(rows, nf, merge=1):
+    """(D, B, parcels) per block of merge^3 fluid cells from one recorded
+    array: D = |sum of drag forces|, B = sum of bond capacities."""
     act = rows[:, 2] > 0  # the k input is positive on every active particle
-    cell = rows[act, COL_CELL].astype(np.int64)
-    D = np.zeros((ncell, 3))
-    np.add.at(D, cell, rows[act][:, COL_DRAG].astype(np.float64))
-    B = np.bincount(cell, weights=rows[act, COL_CAP].astype(np.float64), minlength=ncell)
-    n = np.bincount(cell, minlength=ncell)
+    reg = _region(rows[act, COL_CELL].astype(np.int64), nf, merge)
+    nr = _nregion(nf, merge)
+    D = np.zeros((nr, 3))
+    np.add.at(D, reg, rows[act][:, COL_DRAG].astype(np.float64))
+    B = np.bincount(reg, weights=rows[act, COL_CAP].astype(np.float64), minlength=nr)
+    n = np.bincount(reg, minlength=nr)
     return np.linalg.norm(D, axis=1), B, n
 
 
-def targets(fine: Run, coarse: Run, min_parcels=2):
+def targets(fine: Run, coarse: Run, min_parcels=2, merge=1):
     """Inputs X, targets Y and mask M of every active coarse parcel at every
-    recorded time."""
+    recorded time (ratios over blocks of merge^3 fluid cells)."""
     Xs, Ys, Ms = [], [], []
     for rf, rc in zip(fine.data, coarse.data):
-        Df, Bf, _ = cell_sums(rf, fine.ncell)
-        Dc, Bc, nc = cell_sums(rc, coarse.ncell)
+        Df, Bf, _ = cell_sums(rf, fine.nf, merge)
+        Dc, Bc, nc = cell_sums(rc, coarse.nf, merge)
         okd = (Df > 0) & (Dc > 0) & (nc >= min_parcels)
         okb = (Bf > 0) & (Bc > 0) & (nc >= min_parcels)
         y1 = np.where(okd, np.log(np.where(okd, Df, 1.0) / np.where(okd, Dc, 1.0)), 0.0)
         y2 = np.where(okb, np.log(np.where(okb, Bf, 1.0) / np.where(okb, Bc, 1.0)), 0.0)
         act = rc[:, 2] > 0
-        cell = rc[act, COL_CELL].astype(np.int64)
+        reg = _region(rc[act, COL_CELL].astype(np.int64), coarse.nf, merge)
         Xs.append(rc[act][:, COL_FEAT].astype(np.float64))
-        Ys.append(np.stack([y1[cell], y2[cell]], 1))
-        Ms.append(np.stack([okd[cell], okb[cell]], 1).astype(np.float64))
+        Ys.append(np.stack([y1[reg], y2[reg]], 1))
+        Ms.append(np.stack([okd[reg], okb[reg]], 1).astype(np.float64))
     return np.concatenate(Xs), np.concatenate(Ys), np.concatenate(Ms)
 
 
@@ -139,23 +154,34 @@ def fit(X, Y, M, steps=1000, lr=3e-3, seed=0, device="cuda:0"):
     return net.params(), hist
 
 
-def cell_drag_error(fine: Run, coarse: Run, min_parcels=2):
-    """Mean over cells and times of |ln D_coarse / D_fine| (cells holding at
-    least min_parcels parcels and drag on both sides)."""
+def cell_drag_error(fine: Run, coarse: Run, min_parcels=2, merge=1):
+    """Mean over blocks of merge^3 cells and times of |ln D_coarse / D_fine|
+    (blocks holding at least min_parcels parcels and drag on both sides)."""
     errs = []
     for rf, rc in zip(fine.data, coarse.data):
-        Df, _, _ = cell_sums(rf, fine.ncell)
-        Dc, _, nc = cell_sums(rc, coarse.ncell)
+        Df, _, _ = cell_sums(rf, fine.nf, merge)
+        Dc, _, nc = cell_sums(rc, coarse.nf, merge)
         ok = (Df > 0) & (Dc > 0) & (nc >= min_parcels)
         errs.append(np.abs(np.log(Dc[ok] / Df[ok])))
     return float(np.mean(np.concatenate(errs)))
 
 
-def cell_bond_error(fine: Run, coarse: Run, min_parcels=2):
+def total_drag_error(fine: Run, coarse: Run):
+    """Mean over times of |ln sum_cells D_coarse / sum_cells D_fine| (the
+    drag magnitude the fluid sees from the whole bed)."""
     errs = []
     for rf, rc in zip(fine.data, coarse.data):
-        _, Bf, _ = cell_sums(rf, fine.ncell)
-        _, Bc, nc = cell_sums(rc, coarse.ncell)
+        Df, _, _ = cell_sums(rf, fine.nf)
+        Dc, _, _ = cell_sums(rc, coarse.nf)
+        errs.append(abs(np.log(Dc.sum() / Df.sum())))
+    return float(np.mean(errs))
+
+
+def cell_bond_error(fine: Run, coarse: Run, min_parcels=2, merge=1):
+    errs = []
+    for rf, rc in zip(fine.data, coarse.data):
+        _, Bf, _ = cell_sums(rf, fine.nf, merge)
+        _, Bc, nc = cell_sums(rc, coarse.nf, merge)
         ok = (Bf > 0) & (Bc > 0) & (nc >= min_parcels)
         errs.append(np.abs(np.log(Bc[ok] / Bf[ok])))
     return float(np.mean(np.concatenate(errs)))

@@ -202,12 +202,13 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, flo
   const float Rf = (float)R;
   const float rf = sqrtf(xf * xf + yf * yf);
   const float near = -0.05f * Rf;
+  const float dw[3] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f, zf + Rf - s.H_f};
+  // most spheres are far from every wall: leave before any FP64 work (the
+  // compiler would otherwise hoist the loop-invariant radius and its square
+  // root out of the wall loop and run them for every sphere)
+  if (!(dw[0] > near) && !(dw[1] > near) && !(dw[2] > near)) return;
   for (int wall = 0; wall < 3; ++wall) {
-    float df;
-    if (wall == 0) df = rf + Rf - s.Rc_f;
-    else if (wall == 1) df = rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f;
-    else df = zf + Rf - s.H_f;
-    if (!(df > near)) continue;
+    if (!(dw[wall] > near)) continue;
     const H h = hist_base[(size_t)wall * stride];
     V3<T> hist = v3<T>(h.x, h.y, h.z);
     double delta = -1.0;

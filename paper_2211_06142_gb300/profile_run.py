@@ -1,7 +1,12 @@
 """Short runs of the library's kernels for a profiler (ncu) to capture.
 
-    python -m paper_2211_06142_gb300.profile_run step [mixed|fp64] [steps]
+    python -m paper_2211_06142_gb300.profile_run step [mixed|fp64] [steps] [eager]
         the fused step on the 200,000-sphere sand-production cylinder
+        ("eager": every kernel launched from the host, no CUDA graph, so
+        that a profiler sees each launch)
+    python -m paper_2211_06142_gb300.profile_run rebuild [mixed|fp64] [count]
+        the candidate-list rebuild sequence, forced before each of `count`
+        steps on the same cylinder (kernels launched from the host)
     python -m paper_2211_06142_gb300.profile_run closure [steps]
         the step with the learned closure on the same cylinder at SSW k = 2
     python -m paper_2211_06142_gb300.profile_run mlp [n] [iters]
@@ -16,7 +21,7 @@ import sys
 import numpy as np
 
 
-def _cylinder_ctx(precision, closure=False, k=1):
+def _cylinder_ctx(precision, closure=False, k=1, steps_per_graph=32):
     from . import cgdem
     from . import inputs as I
     from . import workloads as W
@@ -27,7 +32,7 @@ def _cylinder_ctx(precision, closure=False, k=1):
     skin = (0.06 if closure else 0.02) * 2 * float(s.R.max())
     p = cgdem.sample_params(s, dt, skin, k=k, scheme=cgdem.CG_SSW if k > 1 else cgdem.CG_NONE)
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=64 if closure else 48,
-                        closure=closure)
+                        closure=closure, steps_per_graph=steps_per_graph)
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     ctx.compute_forces()
@@ -44,8 +49,18 @@ def main(argv):
     if what == "step":
         prec = cgdem.FP64 if len(argv) > 1 and argv[1] == "fp64" else cgdem.MIXED
         steps = int(argv[2]) if len(argv) > 2 else 12
-        ctx = _cylinder_ctx(prec)
+        ctx = _cylinder_ctx(prec, steps_per_graph=1 if "eager" in argv[3:] else 32)
         ctx.step(steps)
+        torch.cuda.synchronize()
+        print("counters", ctx.counters())
+        ctx.status()
+    elif what == "rebuild":
+        prec = cgdem.FP64 if len(argv) > 1 and argv[1] == "fp64" else cgdem.MIXED
+        count = int(argv[2]) if len(argv) > 2 else 4
+        ctx = _cylinder_ctx(prec, steps_per_graph=1)
+        for _ in range(count):
+            ctx.build_contacts()
+            ctx.step(1)
         torch.cuda.synchronize()
         print("counters", ctx.counters())
         ctx.status()
