@@ -708,6 +708,13 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
         }
       }
     }
+    if (MIXED && e + 32u < total) {
+      // the next round's partner, into L1 while this round's sums run
+      const uint32_t qn = rnext.x & REC_IDX;
+      prefetch_l1(&d.posq[cur][qn]);
+      prefetch_l1(&d.velf[cur][qn]);
+      prefetch_l1(&d.omgf[cur][qn]);
+    }
     // contributions of this round to their owners: a segmented inclusive
     // scan over the lanes (entries of one owner are contiguous), then each
     // owner takes the value at the last lane of its run.  The tree order of
@@ -1068,18 +1075,30 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   float md = my_disp2;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
+  // one fence and one arrival per block: thread 0 publishes the maxima of
+  // the block's single-sample warps itself; a warp that straddles samples
+  // publishes per lane and fences
+  __shared__ int bk_s[FORCE_BLOCK_MAX / 32];
+  __shared__ float bk_m[FORCE_BLOCK_MAX / 32];
+  const int wib = threadIdx.x >> 5;
   if (uniform) {
-    if (lane == 0 && md >= 0.f) atomicMax(&d.dmax2[s0], __float_as_uint(md));
-  } else if (my_disp2 >= 0.f) {
-    atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
+    if (lane == 0) {
+      bk_s[wib] = s0;
+      bk_m[wib] = md;
+    }
+  } else {
+    if (my_disp2 >= 0.f) atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
+    __threadfence();
+    if (lane == 0) bk_m[wib] = -1.f;
   }
-  const bool any_coupled = __any_sync(FULL, coupled);
-  if (lane == 0) {
+  const int any_coupled = __syncthreads_or(coupled);
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (bk_m[w] >= 0.f) atomicMax(&d.dmax2[bk_s[w]], __float_as_uint(bk_m[w]));
     if (any_coupled) atomicOr(&ctl->coupled, 1u);
     __threadfence();
-    const unsigned total_warps = (unsigned)(d.Npad >> 5);
     const unsigned t = atomicAdd(&ctl->block_counter, 1u);
-    if (t == total_warps - 1) {
+    if (t == gridDim.x - 1) {
       __threadfence();
       for (int s = 0; s < d.n_samples; ++s) {
         const unsigned b = atomicAdd(&d.dmax2[s], 0u);

@@ -618,10 +618,12 @@ __global__ void k_kick_drift(Dev d, int couple) {
   const int cur = d.ctl->cur, pc = d.ctl->pcur;
   const int b = (d.ctl->vf_cur + 1) % 3;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  float disp2 = -1.f;  // squared displacement since the rebuild (fixed units)
+  int s = 0;
   if (p < d.N) {
     double4 P = d.pos[cur][p];
+    s = d.sample[pc][p];
     if (P.w > 0.0) {
-      const int s = d.sample[pc][p];
       const SampleDev& S = d.sp[s];
       double4 V = d.vel[cur][p], W = d.omg[cur][p];
       const double4 F = d.F[p], Tq = d.T[p];
@@ -652,12 +654,23 @@ __global__ void k_kick_drift(Dev d, int couple) {
       const float ex = (float)(int)((uint32_t)qn.x - (uint32_t)ref.x);
       const float ey = (float)(int)((uint32_t)qn.y - (uint32_t)ref.y);
       const float ez = (float)(int)((uint32_t)qn.z - (uint32_t)ref.z);
-      atomicMax(&d.dmax2[s], __float_as_uint(ex * ex + ey * ey + ez * ez));
+      disp2 = ex * ex + ey * ey + ez * ez;
       if (couple && (d.ctl->step % S.couple_every) == 0) {
         if (S.vf_mode == 0) atomicAdd(&d.vf[b][fc], d.vq[pc][p]);
         else scatter_cube(S, P, d.vf[b]);
       }
     }
+  }
+  // per-sample maximum: one atomic per warp when the warp holds one sample
+  const unsigned FULLM = 0xffffffffu;
+  const int s0 = __shfl_sync(FULLM, s, 0);
+  if (__all_sync(FULLM, p >= d.N || s == s0)) {
+    float md = disp2;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULLM, md, o));
+    if ((threadIdx.x & 31) == 0 && md >= 0.f) atomicMax(&d.dmax2[s0], __float_as_uint(md));
+  } else if (disp2 >= 0.f) {
+    atomicMax(&d.dmax2[s], __float_as_uint(disp2));
   }
 }
 
