@@ -225,6 +225,46 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
             "Zbar": Zbar, "candidates_per_particle": Cbar}
 
 
+def run_sand(T=0.004, n_times=20):
+    """Produced sand (Eq. 40) of the coarse-grained models against the fine
+    200k-sphere cylinder over the same physical time T: RMSRE (Eq. 41) and
+    the relative error at T for SSW and SSP at k = 2 and 3, and for SSW at
+    k = 3 with the learned closure trained on this very pair of runs."""
+    import math
+    from paper_2211_06142_gb300 import cgdem
+    from paper_2211_06142_gb300 import closure as CL
+    from paper_2211_06142_gb300 import inputs as I
+    from paper_2211_06142_gb300 import sand as SD
+    from paper_2211_06142_gb300 import workloads as Wl
+    t0 = time.perf_counter()
+    fine = I.cached(I.fine_cylinder)
+    ref = SD.run(fine, T=T, n_times=n_times, record=True)
+    out = {"T_s": T, "times": n_times, "U_in_m_s": SD.U_SAND, "dt_over_rayleigh": SD.DT_FRAC,
+           "fine_mass_mg": float(ref.mass[-1] * 1e6), "fine_steps": ref.steps, "models": {}}
+    ssw3 = None
+    for scheme, k in (("ssw", 2), ("ssw", 3), ("ssp", 2), ("ssp", 3)):
+        s = Wl.coarse_cylinder(k=k, scheme=scheme)
+        rec = scheme == "ssw" and k == 3
+        r = SD.run(s, k=k, scheme=Wl.SCHEME[scheme], T=T, n_times=n_times, record=rec)
+        out["models"][f"{scheme}{k}"] = {"parcels": len(s.R), "mass_mg": float(r.mass[-1] * 1e6),
+                                         "rmsre_pct": SD.rmsre(ref, r), "rmsre_late_pct": SD.rmsre_late(ref, r),
+                                         "final_rel_err": SD.final_error(ref, r)}
+        if rec:
+            ssw3 = (s, r)
+    s3, r3 = ssw3
+    X, Y, M = CL.targets(ref, r3, merge=2)
+    theta, hist = CL.fit(X, Y, M, steps=1000, lr=3e-3)
+    lo, hi = CL.input_range(X)
+    rc = SD.run(s3, k=3, scheme=cgdem.CG_SSW, T=T, n_times=n_times,
+                closure=(theta, lo, hi, 3.0, math.log(4.0)))
+    out["models"]["ssw3+closure"] = {"parcels": len(s3.R), "mass_mg": float(rc.mass[-1] * 1e6),
+                                     "rmsre_pct": SD.rmsre(ref, rc), "rmsre_late_pct": SD.rmsre_late(ref, rc),
+                                     "final_rel_err": SD.final_error(ref, rc),
+                                     "train_samples": int(len(X)), "loss": [float(hist[0]), float(hist[-1])]}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
 def time_steps(ctx, torch, K, barrier):
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -318,6 +358,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-sand", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -432,6 +473,10 @@ def main():
         peaks_b = peaks["hbm_gbs"]
         batched["roofline_frac"] = batched["force_kernel_gbs"] / peaks_b
 
+    sand = None
+    if rank == 0 and not args.no_sand:
+        sand = run_sand()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_baseline(s, dt)
@@ -449,6 +494,7 @@ def main():
                                     "trials": len(tune.get("trials", []))}},
             "fp64": fp64,
             "batched": batched,
+            "sand": sand,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,

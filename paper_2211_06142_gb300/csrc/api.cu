@@ -148,11 +148,13 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
     if (!(reach < 0.5 * p.L[0]))
       return fail(ctx, CGDEM_E_INVALID, "periodic box too small for 2 r_max + skin");
     s.dq = p.L[0] / 4294967296.0;  // 2^32 steps per period: wrap-around is the minimum image
+    s.q_exp = 0x7fffffff;
   } else if (p.kind == CGDEM_CYLINDER) {
     if (!(p.Rc > 0) || !(p.H > 0) || !(p.r_out >= 0))
       return fail(ctx, CGDEM_E_INVALID, "cylinder needs Rc > 0, H > 0, r_out >= 0");
     int e = (int)std::ceil(std::log2(reach / 1073741824.0));  // reach < 2^30 steps
     s.dq = std::ldexp(1.0, e);
+    s.q_exp = e;
   } else {
     return fail(ctx, CGDEM_E_INVALID, "unknown domain kind %d", p.kind);
   }

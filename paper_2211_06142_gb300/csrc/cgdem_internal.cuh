@@ -47,6 +47,7 @@ struct SampleDev {
   double L[3], Rc, H, r_out;
   // fixed-point shadow: q = round(x / dq) (low 32 bits)
   double inv_dq, dq;
+  int q_exp;  // dq = 2^q_exp (cylinders); 0x7fffffff when dq is not a power of two
   int32_t skin_q;
   // search grid
   double c_lo[3], c_inv_h[3];
@@ -233,6 +234,31 @@ __device__ __forceinline__ unsigned long long volume_quantum(double R, double in
 __device__ __forceinline__ int32_t to_q(double x, double inv_dq) {
   long long t = __double2ll_rn(x * inv_dq);
   return (int32_t)(uint32_t)(unsigned long long)t;
+}
+
+// to_q for dq = 2^e by integer operations on the IEEE representation:
+// round to nearest, ties to even, low 32 bits -- the value to_q gives -- with
+// no FP64 instruction (GB300 issues two FP64 operations per SM per clock).
+__device__ __forceinline__ int32_t to_q_pow2(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  if (ex == 0) return 0;  // zero or subnormal
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);  // x = m 2^(ex - 1075)
+  const int sh = ex - 1075 - e;
+  unsigned long long q;
+  if (sh >= 0) {
+    q = sh < 64 ? (m << sh) : 0ull;  // exact; only the low bits are kept
+  } else if (-sh > 54) {
+    q = 0ull;
+  } else {
+    const int r = -sh;
+    const unsigned long long half = 1ull << (r - 1);
+    const unsigned long long rem = m & ((1ull << r) - 1ull);
+    q = m >> r;
+    if (rem > half || (rem == half && (q & 1ull))) q += 1ull;
+  }
+  if (b >> 63) q = 0ull - q;
+  return (int32_t)(uint32_t)q;
 }
 
 // Search-grid cell of a position (global index).

@@ -424,6 +424,15 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   }
   float2 my_c = make_float2(1.0f, 1.0f);
   if (use_c && valid) my_c = d.clc[cur][p];
+  // per-block bookkeeping of the fused step (see the end of the kernel)
+  __shared__ int bk_s[FORCE_BLOCK_MAX / 32];
+  __shared__ float bk_m[FORCE_BLOCK_MAX / 32];
+  __shared__ unsigned bk_c[FORCE_BLOCK_MAX / 32];
+  __shared__ unsigned bk_n;
+  if (MODE == MODE_MID) {
+    if (threadIdx.x == 0) bk_n = 0u;
+    __syncthreads();
+  }
 
   // ---- own particle, contact phase ----
   Owner<MIXED> me;
@@ -1005,9 +1014,15 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
           d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
           int4 pqn;
-          pqn.x = to_q(x, S.inv_dq);
-          pqn.y = to_q(y, S.inv_dq);
-          pqn.z = to_q(z, S.inv_dq);
+          if (S.q_exp != 0x7fffffff) {
+            pqn.x = to_q_pow2(x, S.q_exp);
+            pqn.y = to_q_pow2(y, S.q_exp);
+            pqn.z = to_q_pow2(z, S.q_exp);
+          } else {
+            pqn.x = to_q(x, S.inv_dq);
+            pqn.y = to_q(y, S.inv_dq);
+            pqn.z = to_q(z, S.inv_dq);
+          }
           float Rf, mf;
           if constexpr (MIXED) {
             pqn.w = me.pq.w;
@@ -1075,27 +1090,31 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   float md = my_disp2;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
-  // one fence and one arrival per block: thread 0 publishes the maxima of
-  // the block's single-sample warps itself; a warp that straddles samples
-  // publishes per lane and fences
-  __shared__ int bk_s[FORCE_BLOCK_MAX / 32];
-  __shared__ float bk_m[FORCE_BLOCK_MAX / 32];
+  // one fence and one arrival per block, without a block barrier: each warp
+  // leaves its maximum in shared memory, and the block's last warp publishes
+  // them (a warp that straddles samples publishes per lane and fences)
   const int wib = threadIdx.x >> 5;
-  if (uniform) {
-    if (lane == 0) {
-      bk_s[wib] = s0;
-      bk_m[wib] = md;
-    }
-  } else {
+  const unsigned wcoupled = __any_sync(FULL, coupled) ? 1u : 0u;
+  if (!uniform) {
     if (my_disp2 >= 0.f) atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
     __threadfence();
-    if (lane == 0) bk_m[wib] = -1.f;
   }
-  const int any_coupled = __syncthreads_or(coupled);
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      if (bk_m[w] >= 0.f) atomicMax(&d.dmax2[bk_s[w]], __float_as_uint(bk_m[w]));
-    if (any_coupled) atomicOr(&ctl->coupled, 1u);
+  if (lane != 0) return;
+  bk_s[wib] = s0;
+  bk_m[wib] = uniform ? md : -1.f;
+  bk_c[wib] = wcoupled;
+  __threadfence_block();
+  const unsigned nw = blockDim.x >> 5;
+  if (atomicAdd(&bk_n, 1u) != nw - 1u) return;
+  __threadfence_block();
+  {
+    unsigned any = 0u;
+    for (unsigned w = 0; w < nw; ++w) {
+      const float mw = *((volatile float*)&bk_m[w]);
+      if (mw >= 0.f) atomicMax(&d.dmax2[*((volatile int*)&bk_s[w])], __float_as_uint(mw));
+      any |= *((volatile unsigned*)&bk_c[w]);
+    }
+    if (any) atomicOr(&ctl->coupled, 1u);
     __threadfence();
     const unsigned t = atomicAdd(&ctl->block_counter, 1u);
     if (t == gridDim.x - 1) {
