@@ -13,7 +13,7 @@
 #include "cgdem_internal.cuh"
 
 namespace cgdem {
-void launch_forces(const Dev& d, int mode, int block, cudaStream_t s);
+void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next);
 void launch_rebuild(const Dev& d, cudaStream_t s);
 void launch_set_rebuild(const Dev& d, cudaStream_t s);
 void launch_bond_touching(const Dev& d, cudaStream_t s);
@@ -25,7 +25,6 @@ void launch_init(const Dev& d, cudaStream_t s);
 void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
 void launch_diag(const Dev& d, double* part, cudaStream_t s);
-void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s);
 void launch_closure_gather(const Dev& d, cudaStream_t s);
 void launch_closure_pack(const float* theta, const float* lo, const float* hi, float cd_max, float cg_max,
@@ -373,7 +372,7 @@ int ready(cgdem_ctx* ctx) {
 // One fused step (rebuild-if-flagged, forces, kick, drift, porosity).
 void enqueue_mid_step(cgdem_ctx* ctx, cudaStream_t s) {
   launch_rebuild(ctx->d, s);
-  launch_forces(ctx->d, 1, ctx->cfg.block_size, s);
+  launch_forces(ctx->d, 1, ctx->cfg.block_size, s, 0);
   if (ctx->any_cube) launch_cube_after_mid(ctx->d, s);
 }
 
@@ -393,6 +392,17 @@ cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec
   }
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  // one handle per step: the first runs the (self-checking) rebuild body at
+  // every launch of the graph; step i's force kernel sets step i + 1's
+  std::vector<cudaGraphConditionalHandle> hs;
+  if (conditional && e == cudaSuccess) {
+    cudaStreamCaptureStatus stt;
+    cudaGraph_t cg;
+    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, nullptr, nullptr, nullptr);
+    hs.resize(U);
+    for (int i = 0; i < U && e == cudaSuccess; ++i)
+      e = cudaGraphConditionalHandleCreate(&hs[i], cg, i == 0 ? 1u : 0u, i == 0 ? cudaGraphCondAssignDefault : 0u);
+  }
   for (int i = 0; i < U && e == cudaSuccess; ++i) {
     if (!conditional) {
       enqueue_mid_step(ctx, cs);
@@ -404,15 +414,9 @@ cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec
     size_t nd = 0;
     e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
     if (e != cudaSuccess) break;
-    cudaGraphConditionalHandle h;
-    e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0);
-    if (e != cudaSuccess) break;
-    launch_rebuild_cond(ctx->d, h, cs);
-    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
-    if (e != cudaSuccess) break;
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
+    cp.conditional.handle = hs[i];
     cp.conditional.type = cudaGraphCondTypeIf;
     cp.conditional.size = 1;
     cudaGraphNode_t cn;
@@ -426,7 +430,7 @@ cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec
     if (e != cudaSuccess) break;
     e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
     if (e != cudaSuccess) break;
-    launch_forces(ctx->d, 1, ctx->cfg.block_size, cs);
+    launch_forces(ctx->d, 1, ctx->cfg.block_size, cs, i + 1 < U ? hs[i + 1] : 0);
     if (ctx->any_cube) launch_cube_after_mid(ctx->d, cs);
   }
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -621,7 +625,7 @@ int cgdem_couple_fluid(cgdem_ctx* ctx, void* stream) {
 int cgdem_compute_forces(cgdem_ctx* ctx, void* stream) {
   int r = ready(ctx);
   if (r) return r;
-  launch_forces(ctx->d, 0, ctx->cfg.block_size, st(stream));
+  launch_forces(ctx->d, 0, ctx->cfg.block_size, st(stream), 0);
   CK(cudaGetLastError());
   return CGDEM_OK;
 }
@@ -670,7 +674,7 @@ int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {
   for (int64_t i = 0; i < body; ++i) enqueue_mid_step(ctx, s);
   // last step ends on the full-step state (forces, v(n), w(n))
   launch_rebuild(ctx->d, s);
-  launch_forces(ctx->d, 2, ctx->cfg.block_size, s);
+  launch_forces(ctx->d, 2, ctx->cfg.block_size, s, 0);
   CK(cudaGetLastError());
   return CGDEM_OK;
 }
@@ -849,12 +853,12 @@ int cgdem_profile_step(cgdem_ctx* ctx, int64_t nsteps, double* out, void* stream
     CK(cudaEventRecord(ev[1 + 3 * i], s));
     launch_rebuild(ctx->d, s);
     CK(cudaEventRecord(ev[2 + 3 * i], s));
-    launch_forces(ctx->d, 1, ctx->cfg.block_size, s);
+    launch_forces(ctx->d, 1, ctx->cfg.block_size, s, 0);
     CK(cudaEventRecord(ev[3 + 3 * i], s));
     if (ctx->any_cube) launch_cube_after_mid(ctx->d, s);
   }
   launch_rebuild(ctx->d, s);
-  launch_forces(ctx->d, 2, ctx->cfg.block_size, s);
+  launch_forces(ctx->d, 2, ctx->cfg.block_size, s, 0);
   CK(cudaEventRecord(ev[3 * body + 1], s));
   CK(cudaStreamSynchronize(s));
   double force = 0, rebuild = 0, floor_ms = 1e30;

@@ -374,8 +374,11 @@ struct Owner<false> {
 
 // CL: the context carries the learned closure (blocks of 128 threads; more
 // registers per thread for the closure data and the network epilogue).
+// h_next: conditional handle of the next step's rebuild node when the launch
+// sits in a CUDA graph (0 otherwise); the step's last warp sets it.
 template <bool MIXED, int MODE, bool CL>
-__global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB) k_forces(Dev d) {
+__global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
+    k_forces(Dev d, cudaGraphConditionalHandle h_next) {
   using T = typename std::conditional<MIXED, float, double>::type;
   Ctl* ctl = d.ctl;
   const int cur = ctl->cur;
@@ -1128,6 +1131,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
       ctl->step = m_step;
       ctl->block_counter = 0u;
       __threadfence();
+      if (h_next) cudaGraphSetConditional(h_next, ctl->rebuild ? 1u : 0u);
     }
   }
 }
@@ -1139,7 +1143,7 @@ __global__ void k_after_canon(Dev d) {
   ctl->step += 1;
 }
 
-void launch_forces(const Dev& d, int mode, int block, cudaStream_t s) {
+void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next) {
   // Npad is a multiple of 256, so every block size divides it exactly
   // (a context with the learned closure runs blocks of 128: one M = 128 tile)
   const int B = d.clblob ? 128 : ((block == 64 || block == 256) ? block : 128);
@@ -1148,22 +1152,22 @@ void launch_forces(const Dev& d, int mode, int block, cudaStream_t s) {
   if (d.N == 0) return;
   if (d.clblob) {
     if (d.mixed) {
-      if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, true><<<grid, B, sm, s>>>(d);
-      else if (mode == MODE_MID) k_forces<true, MODE_MID, true><<<grid, B, sm, s>>>(d);
-      else k_forces<true, MODE_CANON, true><<<grid, B, sm, s>>>(d);
+      if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
+      else if (mode == MODE_MID) k_forces<true, MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
+      else k_forces<true, MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
     } else {
-      if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, true><<<grid, B, sm, s>>>(d);
-      else if (mode == MODE_MID) k_forces<false, MODE_MID, true><<<grid, B, sm, s>>>(d);
-      else k_forces<false, MODE_CANON, true><<<grid, B, sm, s>>>(d);
+      if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
+      else if (mode == MODE_MID) k_forces<false, MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
+      else k_forces<false, MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
     }
   } else if (d.mixed) {
-    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, false><<<grid, B, 0, s>>>(d);
-    else if (mode == MODE_MID) k_forces<true, MODE_MID, false><<<grid, B, 0, s>>>(d);
-    else k_forces<true, MODE_CANON, false><<<grid, B, 0, s>>>(d);
+    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
+    else if (mode == MODE_MID) k_forces<true, MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
+    else k_forces<true, MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
   } else {
-    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, false><<<grid, B, 0, s>>>(d);
-    else if (mode == MODE_MID) k_forces<false, MODE_MID, false><<<grid, B, 0, s>>>(d);
-    else k_forces<false, MODE_CANON, false><<<grid, B, 0, s>>>(d);
+    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
+    else if (mode == MODE_MID) k_forces<false, MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
+    else k_forces<false, MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
   }
   if (mode == MODE_CANON) k_after_canon<<<1, 1, 0, s>>>(d);
 }
