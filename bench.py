@@ -238,30 +238,74 @@ def run_sand(T=0.004, n_times=20):
     from paper_2211_06142_gb300 import workloads as Wl
     t0 = time.perf_counter()
     fine = I.cached(I.fine_cylinder)
+    # time to simulate T (plain runs, no recording), the coarse-graining speedup
+    tf = time.perf_counter()
+    SD.run(fine, T=T, n_times=1)
+    t_fine = time.perf_counter() - tf
     ref = SD.run(fine, T=T, n_times=n_times, record=True)
     out = {"T_s": T, "times": n_times, "U_in_m_s": SD.U_SAND, "dt_over_rayleigh": SD.DT_FRAC,
-           "fine_mass_mg": float(ref.mass[-1] * 1e6), "fine_steps": ref.steps, "models": {}}
+           "fine_mass_mg": float(ref.mass[-1] * 1e6), "fine_steps": ref.steps, "fine_wall_s": t_fine,
+           "models": {}}
     ssw3 = None
     for scheme, k in (("ssw", 2), ("ssw", 3), ("ssp", 2), ("ssp", 3)):
         s = Wl.coarse_cylinder(k=k, scheme=scheme)
         rec = scheme == "ssw" and k == 3
+        tc = time.perf_counter()
+        SD.run(s, k=k, scheme=Wl.SCHEME[scheme], T=T, n_times=1)
+        t_c = time.perf_counter() - tc
         r = SD.run(s, k=k, scheme=Wl.SCHEME[scheme], T=T, n_times=n_times, record=rec)
         out["models"][f"{scheme}{k}"] = {"parcels": len(s.R), "mass_mg": float(r.mass[-1] * 1e6),
+                                         "wall_s": t_c, "speedup_vs_fine": t_fine / t_c,
                                          "rmsre_pct": SD.rmsre(ref, r), "rmsre_late_pct": SD.rmsre_late(ref, r),
                                          "final_rel_err": SD.final_error(ref, r)}
         if rec:
             ssw3 = (s, r)
     s3, r3 = ssw3
     X, Y, M = CL.targets(ref, r3, merge=2)
-    theta, hist = CL.fit(X, Y, M, steps=1000, lr=3e-3)
     lo, hi = CL.input_range(X)
-    rc = SD.run(s3, k=3, scheme=cgdem.CG_SSW, T=T, n_times=n_times,
-                closure=(theta, lo, hi, 3.0, math.log(4.0)))
-    out["models"]["ssw3+closure"] = {"parcels": len(s3.R), "mass_mg": float(rc.mass[-1] * 1e6),
-                                     "rmsre_pct": SD.rmsre(ref, rc), "rmsre_late_pct": SD.rmsre_late(ref, rc),
-                                     "final_rel_err": SD.final_error(ref, rc),
-                                     "train_samples": int(len(X)), "loss": [float(hist[0]), float(hist[-1])]}
+    # the full closure (drag and cohesion), and one that corrects drag only
+    # (the cohesion target masked out: c_g stays at 1)
+    Md = M.copy()
+    Md[:, 1] = 0.0
+    for name, mask in (("ssw3+closure", M), ("ssw3+drag_closure", Md)):
+        theta, hist = CL.fit(X, Y, mask, steps=1000, lr=3e-3)
+        rc = SD.run(s3, k=3, scheme=cgdem.CG_SSW, T=T, n_times=n_times,
+                    closure=(theta, lo, hi, 3.0, math.log(4.0)))
+        out["models"][name] = {"parcels": len(s3.R), "mass_mg": float(rc.mass[-1] * 1e6),
+                               "rmsre_pct": SD.rmsre(ref, rc), "rmsre_late_pct": SD.rmsre_late(ref, rc),
+                               "final_rel_err": SD.final_error(ref, rc),
+                               "train_samples": int(len(X)), "loss": [float(hist[0]), float(hist[-1])]}
     out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def run_closure_cost(torch, device, barrier, K=2000):
+    """Cost of the fused closure inference: the SSW k = 2 coarse cylinder
+    (25,000 parcels, mixed) stepped by a plain context, by a closure-capable
+    context with the closure off, and with the network evaluated every step."""
+    from paper_2211_06142_gb300 import cgdem
+    from paper_2211_06142_gb300 import closure as CL
+    from paper_2211_06142_gb300 import workloads as Wl
+    s = Wl.coarse_cylinder(k=2, scheme="ssw")
+    m = s.material
+    dt = 0.2 * cgdem.cgdem_rayleigh_dt(float(np.mean(s.R ** 3)) ** (1 / 3), m["rho"], m["E"], m["nu"])
+    skin = 0.06 * 2 * float(s.R.max())
+    theta = CL.init_theta(np.array([0.4, 0.01, 2.0, 3.0, 0.0]), np.array([5.0, 50.0, 1.0, 0.5, 500.0]), 0)
+    out = {"workload": "SSW k = 2 cylinder", "parcels": len(s.R)}
+    for name, closure, on in (("plain", False, False), ("closure_off", True, False), ("closure_on", True, True)):
+        p = cgdem.sample_params(s, dt, skin, k=2, scheme=cgdem.CG_SSW)
+        ctx = cgdem.Context([p], [len(s.R)], precision=cgdem.MIXED, max_neighbors=64, closure=closure,
+                            device=device)
+        ctx.set_fluid_velocity(s.Us)
+        ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
+        if on:
+            ctx.set_closure(theta, [-1e9] * 5, [1e9] * 5, 3.0, 0.5)
+        ctx.compute_forces()
+        ctx.step(50)
+        el = time_steps(ctx, torch, K, barrier)
+        out[name] = {"value": len(s.R) * K / el, "ms_per_step": 1e3 * el / K}
+        ctx.close()
+    out["inference_us_per_step"] = 1e3 * (out["closure_on"]["ms_per_step"] - out["closure_off"]["ms_per_step"])
     return out
 
 
@@ -473,6 +517,7 @@ def main():
         peaks_b = peaks["hbm_gbs"]
         batched["roofline_frac"] = batched["force_kernel_gbs"] / peaks_b
 
+    closure_cost = run_closure_cost(torch, device, barrier, min(K, 2000))
     sand = None
     if rank == 0 and not args.no_sand:
         sand = run_sand()
@@ -494,6 +539,7 @@ def main():
                                     "trials": len(tune.get("trials", []))}},
             "fp64": fp64,
             "batched": batched,
+            "closure": closure_cost,
             "sand": sand,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -9,7 +9,6 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -262,18 +261,6 @@ class Closure:
 
     def params(self):
         return self.theta.cpu().numpy()
-
-
-@dataclass
-class Sample:
-    """One sample handed to the library: grain-level radii and positions,
-    fine-scale material, coarse-graining factor and scheme."""
-    x: np.ndarray
-    v: np.ndarray
-    w: np.ndarray
-    R: np.ndarray
-    params: SampleParams
-    Us: np.ndarray
 
 
 def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1,

@@ -705,6 +705,11 @@ int cgdem_set_closure(cgdem_ctx* ctx, const float* theta, const cgdem_closure_pa
   }
   launch_closure_set(ctx->d, enable ? 1 : 0, -1, s);
   CK(cudaGetLastError());
+  // the force launches change shape: captured step graphs are rebuilt
+  ctx->d.cl_smem = enable ? 1 : 0;
+  CK(cudaStreamSynchronize(s));
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
   return CGDEM_OK;
 }
 

@@ -162,6 +162,7 @@ struct Dev {
   float2* clc[2];                 // (c_d, c_g) per particle, double-buffered like the state
   float* clrec;                   // [Npad][CL_COLS] data recorded by the last evaluation
   uint8_t* clblob;                // network blob (CL_BLOB bytes)
+  int cl_smem;                    // 1: force launches carry the network's shared memory (closure on)
   SampleDev* sp;
   Ctl* ctl;
   int N, Npad, cap, n_samples, C_total, Cf_total;

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   // learned closure: corrections in use, network evaluated after the
   // forces (blocks of 128), per-particle data recorded
   const bool use_c = CL && ctl->closure != 0;
-  const bool net = use_c && MODE != MODE_FORCES;
+  const bool net = use_c && MODE != MODE_FORCES && d.cl_smem;
   const bool rec = CL && ctl->record != 0;
   const bool feat = net || rec;
   __shared__ __align__(8) uint64_t cl_bar[2];
@@ -1148,7 +1148,9 @@ void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphC
   // (a context with the learned closure runs blocks of 128: one M = 128 tile)
   const int B = d.clblob ? 128 : ((block == 64 || block == 256) ? block : 128);
   const int grid = d.Npad / B;
-  const size_t sm = d.clblob ? CL_SMEM : 0;
+  // the network's tiles only while the closure is on: the shared memory
+  // they take shrinks the L1 cache the neighbour gathers hit
+  const size_t sm = (d.clblob && d.cl_smem) ? CL_SMEM : 0;
   if (d.N == 0) return;
   if (d.clblob) {
     if (d.mixed) {

@@ -186,3 +186,47 @@ def test_batched_member_removal_isolated(ensemble):
         assert (ro[0] >= 0) == (s.domain["kind"] == 1)
         off += n
     ctx.close()
+
+
+def test_empty_and_single_sphere_members(ensemble):
+    """Degenerate members beside a normal one: a member with no grains and a
+    member with one grain (no contact; gravity, buoyancy and drag only).
+    Every member matches the oracle run on it alone."""
+    specs, samples = ensemble
+    s = samples[2]
+    one = copy.deepcopy(s)
+    keep = np.array([0])
+    one.x, one.v, one.w, one.R = s.x[keep], s.v[keep], s.w[keep], s.R[keep]
+    none = copy.deepcopy(s)
+    none.x, none.v, none.w, none.R = (np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 3)),
+                                      np.zeros(0))
+    members = [none, one, s]
+    # the degenerate members take the time step, skin and largest radius of s
+    params = [cgdem.sample_params(m, default_dt(s), skin(s), k=specs[2].k,
+                                  scheme=SSW if specs[2].k > 1 else 0, r_max=float(s.R.max()))
+              for m in members]
+    ctx = cgdem.Context(params, [len(m.R) for m in members], precision=cgdem.FP64, max_neighbors=64)
+    ctx.set_fluid_velocity(np.concatenate([m.Us for m in members]))
+    ctx.init_particles(*(np.concatenate([getattr(m, a) for m in members]) for a in "xvwR"),
+                       bond_touching=True)
+    ctx.compute_forces()
+    ctx.step(7)
+    g = ctx.get_state()
+    diag = ctx.get_diagnostics()
+    assert diag[0]["n_active"] == 0 and diag[0]["ke"] == 0.0
+    assert diag[1]["n_active"] == 1 and diag[1]["n_bonds"] == 0
+    off = 0
+    for m in members:
+        n = len(m.R)
+        if n:
+            p = oracle_params(m, default_dt(s), k=specs[2].k, scheme=SSW if specs[2].k > 1 else 0)
+            sim = O.Sim(p, m.x, m.v, m.w, m.R, m.Us)
+            sim.bond_touching()
+            sim.couple_fluid()
+            sim.compute_forces()
+            sim.step(7)
+            o = sim.state()
+            assert np.allclose(g["x"][off:off + n], o["x"], rtol=0, atol=1e-15 + 1e-12 * np.abs(o["x"]).max())
+            assert normwise_error(g["F"][off:off + n], o["F"], sim.force_scale()) <= 1e-10
+        off += n
+    ctx.close()

@@ -234,3 +234,38 @@ def test_capacity_error_is_reported(periodic):
     with pytest.raises(cgdem.CgdemError) as e:
         gpu_context([s], cgdem.MIXED, max_neighbors=2)
     assert e.value.code == cgdem.CGDEM_E_CAPACITY
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_cube_porosity_coarse_grains(prec):
+    """Grains as large as a fluid cell (SSW k = 2 of the small cylinder) with
+    the equal-volume cube spread of the porosity (vf_mode 1): cell sums
+    bit-exact, contacts exact (FP64) and forces within the tolerance, before
+    and after 10 steps, with couple_every = 2 so the rotating porosity
+    buffers are exercised."""
+    import oracle as O
+    d = I.fine_diameters(6000, 23)
+    dg, _ = O.cg_scale(d, 2, "ssw", 0.5)
+    s = with_velocities(I.cylinder_sample(dg, 23, scale=0.3, nf=(12, 12, 6), U_in=0.05, name="cyl-k2"),
+                        1e-3)
+    dt = default_dt(s)
+    kw = dict(k=2, scheme=1, vf_mode=1, couple_every=2)
+    ctx = gpu_context([s], prec, dt=dt, **kw)
+    ctx.compute_forces()
+    sim = run_oracle(s, dt, **kw)
+    assert np.array_equal(ctx.get_voidfrac(s.grid.ncell), sim.voidfrac())
+    check_contacts(ctx, sim)
+    g, o = ctx.get_state(), sim.state()
+    assert normwise_error(g["F"], o["F"], sim.force_scale()) <= TOL[prec]
+    rel = 1e-15 if prec == cgdem.FP64 else 1e-7
+    ref = run_oracle(perturbed(s, rel), dt, **kw)
+    ctx.step(10)
+    sim.step(10)
+    ref.step(10)
+    g, o, r = ctx.get_state(), sim.state(), ref.state()
+    scale = sim.force_scale()
+    spread = normwise_error(r["F"], o["F"], scale)
+    assert normwise_error(g["F"], o["F"], scale) <= max(TOL[prec], 10 * spread)
+    if prec == cgdem.FP64:
+        check_contacts(ctx, sim)
+        assert np.array_equal(ctx.get_voidfrac(s.grid.ncell), sim.voidfrac())
