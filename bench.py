@@ -129,9 +129,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_traffic(kernel_file, kernel):
+def kernel_traffic(kernel_file, kernel, knobs):
     """DRAM bytes per launch from a committed ncu summary, if the kernel source
-    has not changed since the counters were taken."""
+    has not changed since the counters were taken and the counters were taken
+    in the same launch configuration (search cells, skin, block, spheres per
+    warp)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -139,18 +141,23 @@ def kernel_traffic(kernel_file, kernel):
         with open(os.path.join(ROOT, "paper_2211_06142_gb300", "csrc", kernel_file), "rb") as f:
             h = hashlib.sha1(f.read()).hexdigest()
         e = t.get(kernel)
-        if e and e.get("source_sha1") == h:
-            return e
-    except (OSError, ValueError):
+        if not e or e.get("source_sha1") != h:
+            return None
+        for c in e.get("configs", []):
+            if all(abs(float(c[k]) - float(knobs[k])) < 1e-9 for k in ("cell_scale", "skin_frac", "block", "ppw")):
+                return c
+    except (OSError, ValueError, KeyError):
         pass
     return None
 
 
-def build_context(s, precision, dt, skin, device, max_neighbors=48, block=128, cell_scale=0.0):
+def build_context(s, precision, dt, skin, device, max_neighbors=48, block=128, cell_scale=0.0,
+                  ppw=32):
     from paper_2211_06142_gb300 import cgdem
     p = cgdem.sample_params(s, dt, skin)
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=max_neighbors,
-                        block_size=block, cell_scale=cell_scale, steps_per_graph=32, device=device)
+                        block_size=block, cell_scale=cell_scale, steps_per_graph=32, device=device,
+                        particles_per_warp=ppw)
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     ctx.compute_forces()
@@ -176,13 +183,15 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
     N = int(sum(counts))
     t0 = time.perf_counter()
     best = (A.autotune(params, counts, state, Us, cgdem.MIXED, device=device) if tune else
-            {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "cached": False, "trials": []})
+            {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32, "cached": False,
+             "trials": []})
     tune_s = time.perf_counter() - t0
     params = A.tuned_params(params, best)
 
     def make(prec):
         ctx = cgdem.Context(params, counts, precision=prec, max_neighbors=48,
-                            block_size=best["block"], cell_scale=best["cell_scale"], device=device)
+                            block_size=best["block"], cell_scale=best["cell_scale"], device=device,
+                            particles_per_warp=best["ppw"])
         ctx.set_fluid_velocity(Us)
         ctx.init_particles(*state, bond_touching=True)
         ctx.compute_forces()
@@ -216,7 +225,7 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
     return {"value": N_all * K / el, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * el / K,
             "samples": 64, "spheres": N_all, "precision": "mixed",
             "fp64": {"value": N_all * K64 / el64, "steps": K64, "ms_per_step": 1e3 * el64 / K64},
-            "autotune": {k: best[k] for k in ("cell_scale", "block", "skin_frac")} |
+            "autotune": {k: best[k] for k in ("cell_scale", "block", "skin_frac", "ppw")} |
                         {"cached": best.get("cached", False), "trials": len(best.get("trials", [])),
                          "seconds": tune_s},
             "force_kernel_ms": prof["force_ms"], "alg_bytes_per_particle_step": alg,
@@ -282,7 +291,8 @@ def run_sand(T=0.004, n_times=20):
 def run_closure_cost(torch, device, barrier, K=2000):
     """Cost of the fused closure inference: the SSW k = 2 coarse cylinder
     (25,000 parcels, mixed) stepped by a plain context, by a closure-capable
-    context with the closure off, and with the network evaluated every step."""
+    context with the closure off, and with the network evaluated every step;
+    also the plain context at 16 spheres per warp of the force kernel."""
     from paper_2211_06142_gb300 import cgdem
     from paper_2211_06142_gb300 import closure as CL
     from paper_2211_06142_gb300 import workloads as Wl
@@ -292,10 +302,12 @@ def run_closure_cost(torch, device, barrier, K=2000):
     skin = 0.06 * 2 * float(s.R.max())
     theta = CL.init_theta(np.array([0.4, 0.01, 2.0, 3.0, 0.0]), np.array([5.0, 50.0, 1.0, 0.5, 500.0]), 0)
     out = {"workload": "SSW k = 2 cylinder", "parcels": len(s.R)}
-    for name, closure, on in (("plain", False, False), ("closure_off", True, False), ("closure_on", True, True)):
+    for name, closure, on, ppw in (("plain", False, False, 32), ("plain_16_per_warp", False, False, 16),
+                                   ("closure_off", True, False, 32), ("closure_on", True, True, 32),
+                                   ("closure_on_16_per_warp", True, True, 16)):
         p = cgdem.sample_params(s, dt, skin, k=2, scheme=cgdem.CG_SSW)
         ctx = cgdem.Context([p], [len(s.R)], precision=cgdem.MIXED, max_neighbors=64, closure=closure,
-                            device=device)
+                            device=device, particles_per_warp=ppw)
         ctx.set_fluid_velocity(s.Us)
         ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
         if on:
@@ -306,6 +318,8 @@ def run_closure_cost(torch, device, barrier, K=2000):
         out[name] = {"value": len(s.R) * K / el, "ms_per_step": 1e3 * el / K}
         ctx.close()
     out["inference_us_per_step"] = 1e3 * (out["closure_on"]["ms_per_step"] - out["closure_off"]["ms_per_step"])
+    out["inference_us_per_step_16_per_warp"] = 1e3 * (out["closure_on_16_per_warp"]["ms_per_step"] -
+                                                      out["plain_16_per_warp"]["ms_per_step"])
     return out
 
 
@@ -431,7 +445,8 @@ def main():
     N = len(s.R)
     dt, skin = step_params(s)
     # search cells, force-kernel block and skin from the autotuner (cached per workload)
-    tune = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "cached": False, "trials": []}
+    tune = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32, "cached": False,
+            "trials": []}
     if not args.no_tune:
         from paper_2211_06142_gb300 import autotune as A
         t0 = time.perf_counter()
@@ -439,7 +454,7 @@ def main():
                           cgdem.MIXED, device=device)
         tune["seconds"] = time.perf_counter() - t0
     skin = tune["skin_frac"] * 2 * float(s.R.max())
-    knobs = dict(block=tune["block"], cell_scale=tune["cell_scale"])
+    knobs = dict(block=tune["block"], cell_scale=tune["cell_scale"], ppw=tune["ppw"])
 
     # ---- mixed precision (headline) ----
     ctx = build_context(s, cgdem.MIXED, dt, skin, device, **knobs)
@@ -467,7 +482,7 @@ def main():
     alg_bytes = 192.0 + 16.0 * Zbar + 4.0 * Cbar
     peaks, src = measured_peaks()
     achieved = alg_bytes * n_act / (prof["force_ms"] * 1e-3) / 1e9
-    tr = kernel_traffic("k_forces.cu", "k_forces_mixed_mid")
+    tr = kernel_traffic("k_forces.cu", "k_forces_mixed_mid", tune)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": tr["bytes_per_launch"] if tr else None,
                 "peak_source": src, "kernel": "k_forces<mixed, fused step>",
@@ -494,7 +509,8 @@ def main():
     hx, hv, hw, hR = pin(s.x), pin(s.v), pin(s.w), pin(s.R)
     p = cgdem.sample_params(s, dt, skin)
     ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device,
-                        block_size=knobs["block"], cell_scale=knobs["cell_scale"])
+                        block_size=knobs["block"], cell_scale=knobs["cell_scale"],
+                        particles_per_warp=knobs["ppw"])
     ctx.set_fluid_velocity(s.Us)
     barrier()
     torch.cuda.synchronize()
@@ -534,7 +550,7 @@ def main():
             "config": {"workload": WORKLOAD, "spheres_per_gpu": N, "precision": "mixed",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "touched bytes per step exceed half the 129 MB L2; no flush",
-                       "autotune": {k: tune[k] for k in ("cell_scale", "block", "skin_frac")} |
+                       "autotune": {k: tune[k] for k in ("cell_scale", "block", "skin_frac", "ppw")} |
                                    {"cached": tune.get("cached", False),
                                     "trials": len(tune.get("trials", []))}},
             "fp64": fp64,

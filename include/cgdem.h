@@ -107,6 +107,8 @@ typedef struct {
     int steps_per_graph;    /* steps captured in one CUDA graph by cgdem_step (>= 1) */
     int closure;            /* 1: the context carries the learned closure (cgdem_set_closure);
                                its force kernel runs blocks of 128 (block_size 0 or 128) */
+    int particles_per_warp; /* spheres per warp of the fused force kernel: 32 (0 selects it),
+                               or 16 (twice the warps: for samples too small to fill the GPU) */
 } cgdem_config;
 
 typedef struct cgdem_ctx cgdem_ctx;

@@ -1,5 +1,6 @@
 """Project-written autotuner for the step: search-cell size, threads per
-block of the fused force kernel, and the candidate-list skin.
+block of the fused force kernel, spheres per warp of that kernel (32, or 16
+for samples too small to fill the GPU), and the candidate-list skin.
 
 Coordinate search (each knob in turn, the others held at the best so far),
 each trial timing a short run of ``cgdem_step`` with CUDA events after a
@@ -22,6 +23,7 @@ from . import cgdem
 CELL_SCALES = (0.25, 0.35, 0.5, 0.75, 1.0)
 BLOCKS = (64, 128, 256)
 SKIN_FRACS = (0.01, 0.02, 0.04, 0.06, 0.09)
+PPWS = (32, 16)
 
 
 def _cache_path():
@@ -31,7 +33,7 @@ def _cache_path():
 
 def signature(params, counts, precision):
     h = hashlib.sha1()
-    h.update(repr((list(map(int, counts)), int(precision))).encode())
+    h.update(repr((2, list(map(int, counts)), int(precision))).encode())
     for p in params:
         h.update(repr((p.kind, round(p.r_max, 12), p.nf[0], p.nf[1], p.nf[2])).encode())
     return h.hexdigest()[:16]
@@ -54,11 +56,12 @@ def _with_skin(params, frac):
     return out
 
 
-def trial(params, counts, state, Us, precision, cell_scale, block, steps=150, warm=30,
-          device="cuda:0", max_neighbors=48):
+def trial(params, counts, state, Us, precision, cell_scale, block, steps=600, warm=50,
+          device="cuda:0", max_neighbors=48, ppw=32):
     import torch
     ctx = cgdem.Context(params, counts, precision=precision, max_neighbors=max_neighbors,
-                        block_size=block, cell_scale=cell_scale, device=device)
+                        block_size=block, cell_scale=cell_scale, device=device,
+                        particles_per_warp=ppw)
     try:
         ctx.set_fluid_velocity(Us)
         ctx.init_particles(*state, bond_touching=True)
@@ -77,8 +80,9 @@ def trial(params, counts, state, Us, precision, cell_scale, block, steps=150, wa
 
 
 def autotune(params, counts, state, Us, precision=cgdem.MIXED, device="cuda:0", use_cache=True,
-             steps=150, log=None):
-    """Return {"cell_scale", "block", "skin_frac", "ms_per_step", "trials"} for the workload."""
+             steps=600, log=None):
+    """Return {"cell_scale", "block", "skin_frac", "ppw", "ms_per_step", "trials"} for the
+    workload."""
     key = signature(params, counts, precision)
     path = _cache_path()
     cache = {}
@@ -90,27 +94,28 @@ def autotune(params, counts, state, Us, precision=cgdem.MIXED, device="cuda:0", 
             cache = {}
         if key in cache:
             return dict(cache[key], cached=True)
-    best = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02}
+    best = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32}
     trials = []
 
-    def run(cs, b, sf):
+    def run(cs, b, sf, pw):
         try:
             ms = trial(_with_skin(params, sf), counts, state, Us, precision, cs, b, steps=steps,
-                       device=device)
+                       device=device, ppw=pw)
         except cgdem.CgdemError as e:  # e.g. a skin below the bond-break separation
             ms = float("inf")
             if log:
-                log(f"trial cs={cs} block={b} skin={sf}: {e}")
-        trials.append({"cell_scale": cs, "block": b, "skin_frac": sf, "ms_per_step": ms})
+                log(f"trial cs={cs} block={b} skin={sf} ppw={pw}: {e}")
+        trials.append({"cell_scale": cs, "block": b, "skin_frac": sf, "ppw": pw, "ms_per_step": ms})
         return ms
 
-    best_ms = run(best["cell_scale"], best["block"], best["skin_frac"])
-    for knob, values in (("cell_scale", CELL_SCALES), ("block", BLOCKS), ("skin_frac", SKIN_FRACS)):
+    best_ms = run(best["cell_scale"], best["block"], best["skin_frac"], best["ppw"])
+    for knob, values in (("cell_scale", CELL_SCALES), ("block", BLOCKS), ("skin_frac", SKIN_FRACS),
+                         ("ppw", PPWS)):
         for v in values:
             if v == best[knob]:
                 continue
             cand = dict(best, **{knob: v})
-            ms = run(cand["cell_scale"], cand["block"], cand["skin_frac"])
+            ms = run(cand["cell_scale"], cand["block"], cand["skin_frac"], cand["ppw"])
             if ms < best_ms:
                 best, best_ms = cand, ms
     res = dict(best, ms_per_step=best_ms, trials=trials)

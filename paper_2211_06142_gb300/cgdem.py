@@ -67,7 +67,7 @@ class Config(C.Structure):
     _fields_ = [
         ("precision", C.c_int), ("n_samples", C.c_int), ("max_neighbors", C.c_int),
         ("block_size", C.c_int), ("cell_scale", C.c_double), ("steps_per_graph", C.c_int),
-        ("closure", C.c_int),
+        ("closure", C.c_int), ("particles_per_warp", C.c_int),
     ]
 
 
@@ -299,7 +299,8 @@ class Context:
     """A library context over one or more samples on one GPU."""
 
     def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
-                 cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None, closure=False):
+                 cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None, closure=False,
+                 particles_per_warp=32):
         import torch
 
         if not torch.cuda.is_available():
@@ -311,7 +312,7 @@ class Context:
         self.counts = np.ascontiguousarray(counts, dtype=np.int64)
         self.N = int(self.counts.sum())
         self.cfg = Config(precision, self.n_samples, max_neighbors, block_size, cell_scale,
-                          steps_per_graph, int(bool(closure)))
+                          steps_per_graph, int(bool(closure)), int(particles_per_warp))
         nbytes = C.c_size_t(0)
         r = lib().cgdem_workspace_size(C.byref(self.cfg), self._params, _ptr(self.counts),
                                        C.byref(nbytes))

@@ -244,6 +244,8 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   if (cfg->precision != CGDEM_FP64 && cfg->precision != CGDEM_MIXED)
     return fail(ctx, CGDEM_E_INVALID, "unknown precision");
   if (cfg->closure != 0 && cfg->closure != 1) return fail(ctx, CGDEM_E_INVALID, "closure must be 0 or 1");
+  if (cfg->particles_per_warp != 0 && cfg->particles_per_warp != 16 && cfg->particles_per_warp != 32)
+    return fail(ctx, CGDEM_E_INVALID, "particles_per_warp must be 0, 16 or 32");
   if (cfg->closure && cfg->block_size != 128 && cfg->block_size > 0)
     return fail(ctx, CGDEM_E_INVALID, "a context with the learned closure runs blocks of 128 threads");
   const int S = cfg->n_samples;
@@ -337,6 +339,7 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.C_total = C;
   d.Cf_total = Cf;
   d.mixed = mixed ? 1 : 0;
+  d.ppw = cfg->particles_per_warp == 16 ? 16 : 32;
   *bytes = cv.off + 256;
   *dv = d;
   *any_cube = cube;
@@ -720,6 +723,12 @@ int cgdem_closure_record(cgdem_ctx* ctx, int enable, void* stream) {
   cudaStream_t s = st(stream);
   launch_closure_set(ctx->d, -1, enable ? 1 : 0, s);
   CK(cudaGetLastError());
+  if (ctx->d.cl_rec != (enable ? 1 : 0)) {  // the force kernel variant changes
+    ctx->d.cl_rec = enable ? 1 : 0;
+    CK(cudaStreamSynchronize(s));
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+  }
   return CGDEM_OK;
 }
 

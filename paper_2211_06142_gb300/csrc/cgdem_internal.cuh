@@ -163,9 +163,11 @@ struct Dev {
   float* clrec;                   // [Npad][CL_COLS] data recorded by the last evaluation
   uint8_t* clblob;                // network blob (CL_BLOB bytes)
   int cl_smem;                    // 1: force launches carry the network's shared memory (closure on)
+  int cl_rec;                     // 1: closure data recorded (host mirror of Ctl::record)
   SampleDev* sp;
   Ctl* ctl;
   int N, Npad, cap, n_samples, C_total, Cf_total;
+  int ppw;  // spheres per warp of the force kernel (32 or 16); a record segment holds ppw spheres
   int mixed;
 };
 

@@ -391,9 +391,14 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   const int ce = d.sp[0].couple_every;
   const bool couple_next = ce == 1 || (unsigned)(m_step % ce) == 0u;
   const int lane = threadIdx.x & 31;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad exactly
-  const int wbase = p - lane;
-  const bool valid = p < d.N;
+  // P spheres per warp (32; 16 for small samples, twice the warps to hide
+  // latency); lanes >= P own no sphere but evaluate entries.  The grid
+  // covers Npad / P warps exactly.
+  const int P = d.ppw;
+  const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * P;
+  const bool owner_lane = lane < P;
+  const int p = owner_lane ? wbase + lane : wbase;
+  const bool valid = owner_lane && p < d.N;
 
   // learned closure: corrections in use, network evaluated after the
   // forces (blocks of 128), per-particle data recorded
@@ -471,10 +476,12 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     prefetch_l1(&d.fcell[pc][p]);
     prefetch_l1(&d.vq[pc][p]);
   }
-  const uint32_t ncnt = d.cnt[rc][p];
+  const uint32_t ncnt = owner_lane ? d.cnt[rc][p] : 0u;
   const uint32_t seg = (uint32_t)wbase * (uint32_t)d.cap;
-  const uint32_t lo = d.roff[rc][p] - seg;
-  const uint32_t total = __shfl_sync(FULL, lo + ncnt, 31);
+  const uint32_t lo0 = owner_lane ? d.roff[rc][p] - seg : 0u;
+  const uint32_t total = __shfl_sync(FULL, lo0 + ncnt, P - 1);
+  // a lane without a sphere starts its (empty) run at the end: never an owner
+  const uint32_t lo = owner_lane ? lo0 : total;
   V3<T> F = v3<T>(0, 0, 0), Tq = v3<T>(0, 0, 0);
   T Zacc = 0, Dacc = 0, Cacc = 0;  // closure data: active contacts, summed overlap, bond capacity
   // mixed: each lane's record for the next round is loaded one round ahead
@@ -1146,13 +1153,16 @@ __global__ void k_after_canon(Dev d) {
 void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next) {
   // Npad is a multiple of 256, so every block size divides it exactly
   // (a context with the learned closure runs blocks of 128: one M = 128 tile)
-  const int B = d.clblob ? 128 : ((block == 64 || block == 256) ? block : 128);
-  const int grid = d.Npad / B;
-  // the network's tiles only while the closure is on: the shared memory
-  // they take shrinks the L1 cache the neighbour gathers hit
-  const size_t sm = (d.clblob && d.cl_smem) ? CL_SMEM : 0;
+  // The closure variant only while the closure is on or recording: its
+  // tiles' shared memory shrinks the L1 cache the neighbour gathers hit,
+  // and its registers the occupancy.  With both off the plain kernel
+  // computes the same step (corrections 1).
+  const bool cl = d.clblob && (d.cl_smem || d.cl_rec);
+  const int B = cl ? 128 : ((block == 64 || block == 256) ? block : 128);
+  const int grid = d.Npad * (32 / d.ppw) / B;
+  const size_t sm = (cl && d.cl_smem) ? CL_SMEM : 0;
   if (d.N == 0) return;
-  if (d.clblob) {
+  if (cl) {
     if (d.mixed) {
       if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
       else if (mode == MODE_MID) k_forces<true, MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);

@@ -370,13 +370,15 @@ __global__ void k_rb_lists(Dev d) {
     atomicAdd((unsigned long long*)&d.ctl->cand_total_next, (unsigned long long)sum);
   }
   const uint32_t n = count < (uint32_t)cap ? count : (uint32_t)cap;
+  // records of a segment of P consecutive spheres are contiguous (P spheres per warp of the force kernel)
+  const int P = d.ppw, sub = lane & (P - 1);
   uint32_t incl = n;
 #pragma unroll
   for (int k = 1; k < 32; k <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, k);
-    if (lane >= k) incl += y;
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, k, P);
+    if (k < P && sub >= k) incl += y;
   }
-  const uint32_t seg = (uint32_t)(p - lane) * (uint32_t)cap;
+  const uint32_t seg = (uint32_t)(p - sub) * (uint32_t)cap;
   const uint32_t first = seg + incl - n;
   d.roff[rn][p] = first;
   d.cnt[rn][p] = n;

@@ -12,6 +12,11 @@
     python -m paper_2211_06142_gb300.profile_run mlp [n] [iters]
         full-batch training steps of the closure network on n samples
 
+Options (before or after the mode's arguments): --cell S (search-cell
+scale), --skin F (skin / largest grain diameter), --block B (threads per
+block of the force kernel), --ppw P (spheres per warp of that kernel), for
+capturing the launch configuration the autotuner chose.
+
 Each prints its counters and "ok" when it ends without an error.
 """
 from __future__ import annotations
@@ -19,6 +24,9 @@ from __future__ import annotations
 import sys
 
 import numpy as np
+
+
+KNOBS = {"cell": 0.0, "skin": None, "block": 128, "ppw": 32}
 
 
 def _cylinder_ctx(precision, closure=False, k=1, steps_per_graph=32):
@@ -29,10 +37,12 @@ def _cylinder_ctx(precision, closure=False, k=1, steps_per_graph=32):
     m = s.material
     Rbar = float(np.mean(s.R ** 3)) ** (1 / 3)
     dt = 0.2 * cgdem.cgdem_rayleigh_dt(Rbar, m["rho"], m["E"], m["nu"])
-    skin = (0.06 if closure else 0.02) * 2 * float(s.R.max())
+    skin_frac = KNOBS["skin"] if KNOBS["skin"] is not None else (0.06 if closure else 0.02)
+    skin = skin_frac * 2 * float(s.R.max())
     p = cgdem.sample_params(s, dt, skin, k=k, scheme=cgdem.CG_SSW if k > 1 else cgdem.CG_NONE)
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=64 if closure else 48,
-                        closure=closure, steps_per_graph=steps_per_graph)
+                        closure=closure, steps_per_graph=steps_per_graph, cell_scale=KNOBS["cell"],
+                        block_size=128 if closure else KNOBS["block"], particles_per_warp=KNOBS["ppw"])
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     ctx.compute_forces()
@@ -45,6 +55,13 @@ def main(argv):
     from . import build as B
     from . import cgdem
     B.build()
+    argv = list(argv)
+    for flag, key, conv in (("--cell", "cell", float), ("--skin", "skin", float),
+                            ("--block", "block", int), ("--ppw", "ppw", int)):
+        if flag in argv:
+            i = argv.index(flag)
+            KNOBS[key] = conv(argv[i + 1])
+            del argv[i:i + 2]
     what = argv[0] if argv else "step"
     if what == "step":
         prec = cgdem.FP64 if len(argv) > 1 and argv[1] == "fp64" else cgdem.MIXED

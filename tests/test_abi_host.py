@@ -80,6 +80,10 @@ def test_workspace_size_and_invalid_arguments(lib):
     # too many neighbours per sphere
     cfg2 = cgdem.Config(cgdem.MIXED, 1, 4096, 128, 0.0, 32)
     assert lib.cgdem_workspace_size(C.byref(cfg2), arr, counts.ctypes.data, C.byref(nb)) == cgdem.CGDEM_E_INVALID
+    # spheres per warp of the force kernel: 0, 16 or 32
+    for ppw, rc in ((16, 0), (32, 0), (0, 0), (8, cgdem.CGDEM_E_INVALID)):
+        cfg3 = cgdem.Config(cgdem.MIXED, 1, 48, 128, 0.0, 32, 0, ppw)
+        assert lib.cgdem_workspace_size(C.byref(cfg3), arr, counts.ctypes.data, C.byref(nb)) == rc
 
 
 def test_noalloc_rejects_oversize_without_gpu(lib):

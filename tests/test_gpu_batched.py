@@ -53,11 +53,12 @@ def skin(s):
     return 0.05 * 2 * float(s.R.max())
 
 
-def batched_context(specs, samples, prec):
+def batched_context(specs, samples, prec, ppw=32):
     params = [cgdem.sample_params(s, default_dt(s), skin(s), k=sp.k,
                                   scheme=SSW if sp.k > 1 else 0)
               for sp, s in zip(specs, samples)]
-    ctx = cgdem.Context(params, [len(s.R) for s in samples], precision=prec, max_neighbors=64)
+    ctx = cgdem.Context(params, [len(s.R) for s in samples], precision=prec, max_neighbors=64,
+                        particles_per_warp=ppw)
     ctx.set_fluid_velocity(np.concatenate([s.Us for s in samples]))
     ctx.init_particles(*(np.concatenate([getattr(s, a) for s in samples]) for a in "xvwR"),
                        bond_touching=True)
@@ -116,10 +117,12 @@ def near_threshold(s, x, pairs, eps, k):
     return (np.minimum(np.abs(dl), np.abs(dl - dC)) <= eps * S).all()
 
 
-@pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
-def test_batched_members_match_oracle(ensemble, prec):
+@pytest.mark.parametrize("prec,ppw", [(cgdem.FP64, 32), (cgdem.MIXED, 32), (cgdem.FP64, 16)])
+def test_batched_members_match_oracle(ensemble, prec, ppw):
+    """Members against their own oracle runs (at 16 spheres per warp, record
+    segments also straddle members)."""
     specs, samples = ensemble
-    ctx = batched_context(specs, samples, prec)
+    ctx = batched_context(specs, samples, prec, ppw)
     ctx.compute_forces()
     sims = [member_oracle(sp, s) for sp, s in zip(specs, samples)]
     rel = 1e-15 if prec == cgdem.FP64 else 1e-7

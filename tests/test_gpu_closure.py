@@ -56,10 +56,11 @@ def random_theta(seed):
     return M.pack(mu, isg, layers).astype(np.float32).astype(np.float64)
 
 
-def gpu_run(s, prec, theta, steps):
+def gpu_run(s, prec, theta, steps, ppw=32):
     skin = 3 * default_skin(s)  # room for the largest surface-energy correction
     p = cgdem.sample_params(s, default_dt(s), skin)
-    ctx = cgdem.Context([p], [len(s.R)], precision=prec, max_neighbors=96, closure=True)
+    ctx = cgdem.Context([p], [len(s.R)], precision=prec, max_neighbors=96, closure=True,
+                        particles_per_warp=ppw)
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     ctx.set_closure(theta, LO, HI, CD, CG)
@@ -126,10 +127,13 @@ def dlog_c(gd, od):
 
 
 @pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
-def test_constant_network_corrections(cyl, prec):
+@pytest.mark.parametrize("ppw", [32, 16])
+def test_constant_network_corrections(cyl, prec, ppw):
+    """At 16 spheres per warp half of each block's 128 network rows are
+    empty; the corrections and records must not change."""
     s = cyl
     theta = const_theta(2.0, 0.5)
-    ctx = gpu_run(s, prec, theta, 6)
+    ctx = gpu_run(s, prec, theta, 6, ppw)
     sim = oracle_run(s, theta, 6)
     g, o = ctx.get_state(), sim.state()
     gd, od = ctx.closure_data(), sim.closure_data()

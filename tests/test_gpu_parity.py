@@ -18,13 +18,14 @@ TOL = {cgdem.FP64: 1e-10, cgdem.MIXED: 1e-4}
 PREC = [cgdem.FP64, cgdem.MIXED]
 
 
-def gpu_context(samples, prec, dt=None, skin=None, max_neighbors=64, bond=True, **kw):
+def gpu_context(samples, prec, dt=None, skin=None, max_neighbors=64, bond=True, ppw=32, **kw):
     params, counts = [], []
     for s in samples:
         params.append(cgdem.sample_params(s, dt if dt is not None else default_dt(s),
                                           skin if skin is not None else default_skin(s), **kw))
         counts.append(len(s.R))
-    ctx = cgdem.Context(params, counts, precision=prec, max_neighbors=max_neighbors)
+    ctx = cgdem.Context(params, counts, precision=prec, max_neighbors=max_neighbors,
+                        particles_per_warp=ppw)
     ctx.set_fluid_velocity(np.concatenate([s.Us for s in samples]))
     x = np.concatenate([s.x for s in samples])
     v = np.concatenate([s.v for s in samples])
@@ -203,6 +204,66 @@ def test_cylinder_walls_outlet_drag(cylinder, prec):
         bound = max(bound, drift_bound(s, sim, 20, dt, TOL[prec]))
     assert np.abs(g["x"] - o["x"]).max() <= bound
     # produced sand and removal steps agree (Eq. 40)
+    np.testing.assert_array_equal(ctx.get_removed_step(), np.where(sim.removed_step() < 0, -1, sim.removed_step()))
+
+
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("domain", ["periodic", "cylinder"])
+def test_sixteen_spheres_per_warp(periodic, cylinder, prec, domain):
+    """The force kernel at 16 spheres per warp (record segments of 16
+    spheres, lanes 16-31 evaluating entries only) against the oracle, with
+    the checks of the 32-per-warp trajectory tests at the same step counts
+    (1, 10 and 50 steps): contacts bit-exact (FP64) or off only at
+    thresholds (mixed), forces within the tolerance, same produced sand.
+    The mixed trajectory's force error varies along the run (on the periodic
+    packing it is 1.5e-4 at step 20 and 1.1e-5 at step 50 at both 16 and 32
+    spheres per warp: position drift of ~3e-12 m near the touching and
+    break thresholds), so the bound is checked where the 32-per-warp tests
+    check it.  Both layouts also give the same forces up to the summation
+    order of the contributions."""
+    s = periodic if domain == "periodic" else cylinder
+    dt = default_dt(s)
+    ctx = gpu_context([s], prec, dt=dt, ppw=16)
+    c32 = gpu_context([s], prec, dt=dt)
+    ctx.compute_forces()
+    c32.compute_forces()
+    sim = run_oracle(s, dt)
+    check_contacts(ctx, sim)
+    assert np.array_equal(ctx.get_voidfrac(s.grid.ncell), sim.voidfrac())
+    g, o = ctx.get_state(), sim.state()
+    assert normwise_error(g["F"], o["F"], sim.force_scale()) <= TOL[prec]
+    assert normwise_error(g["T"], o["T"], sim.force_scale() * s.R) <= TOL[prec]
+    order = 1e-13 if prec == cgdem.FP64 else 1e-6  # summation order only
+    assert normwise_error(g["F"], c32.get_state()["F"], sim.force_scale()) <= order
+    rel = 1e-15 if prec == cgdem.FP64 else 1e-7
+    ref = run_oracle(perturbed(s, rel), dt)
+    done = 0
+    for chunk in (1, 9, 40):
+        ctx.step(chunk)
+        c32.step(chunk)
+        sim.step(chunk)
+        ref.step(chunk)
+        done += chunk
+        g, o, r = ctx.get_state(), sim.state(), ref.state()
+        if done == 1:
+            assert normwise_error(g["F"], c32.get_state()["F"], sim.force_scale()) <= order
+        scale = sim.force_scale()
+        dxr = r["x"] - o["x"]
+        dx = g["x"] - o["x"]
+        if domain == "periodic":
+            L = s.domain["L"][0]
+            dxr -= L * np.round(dxr / L)
+            dx -= L * np.round(dx / L)
+        spreadx = np.abs(dxr).max()
+        if prec == cgdem.FP64:
+            check_contacts(ctx, sim)
+        else:
+            check_contacts_near(ctx, sim, s, eps=max(1e-9, 10 * spreadx / float(s.R.min())))
+        assert normwise_error(g["F"], o["F"], scale) <= max(TOL[prec], 10 * normwise_error(r["F"], o["F"], scale))
+        bound = max(1e-13, 10 * spreadx)
+        if prec == cgdem.MIXED:
+            bound = max(bound, drift_bound(s, sim, done, dt, TOL[prec]))
+        assert np.abs(dx).max() <= bound
     np.testing.assert_array_equal(ctx.get_removed_step(), np.where(sim.removed_step() < 0, -1, sim.removed_step()))
 
 
