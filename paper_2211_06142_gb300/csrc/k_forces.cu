@@ -2,14 +2,15 @@
 // with the velocity-Verlet update (arXiv 2211.06142, Sec. 2.1-2.3).
 //
 // Work decomposition.  Particles are grouped by warp (32 consecutive
-// particles in cell order).  A warp's candidate records are stored
-// contiguously (particle after particle), so the warp walks them in rounds of
-// 32 entries: every lane evaluates one pair per round whatever the
-// candidate counts of the 32 particles are (the size ratio of the sand is 6,
-// so counts vary several-fold within a warp).  Each pair is evaluated from
-// both sides with bit-identical magnitudes; a particle sums its own pair
-// forces in list order through shared memory, so the result is deterministic
-// and needs no floating-point atomics.
+// particles in cell order, or 16 for samples too small to fill the GPU).  A
+// warp's candidate records are stored contiguously (particle after
+// particle), so the warp walks them in rounds of 32 entries: every lane
+// evaluates one pair per round whatever the candidate counts of the
+// particles are (the size ratio of the sand is 6, so counts vary several-fold
+// within a warp).  Each pair is evaluated from both sides with bit-identical
+// magnitudes; a particle sums its own pair forces in list order by a
+// segmented warp scan, so the result is deterministic and needs no
+// floating-point atomics.
 //
 // Two precisions:
 //   FP64  -- geometry and contact physics in double.
