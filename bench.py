@@ -475,10 +475,11 @@ def main():
     Zbar = 2.0 * len(gi) / n_act
     Cbar = cnt["total_candidates"] / n_act
     prof = ctx.profile_step(200)
-    # algorithmic bytes per particle-step of the fused force/integrate kernel:
-    # FP64 state (x,R | v,1/m | w,1/I) read + written = 192 B, contact history
-    # of every active contact read + written once per pair (16 B record per
-    # contact per particle), candidate-list entries read (4 B each)
+    # algorithmic bytes per particle-step of the fused step kernel: FP64
+    # state (x,R | v,1/m | w,1/I) read + written = 192 B, the record of every
+    # active pair read + written once (16 B per contact per particle), each
+    # sphere's list entries read once (4 B per candidate: the owner reads the
+    # pair's index, the partner its incoming index)
     alg_bytes = 192.0 + 16.0 * Zbar + 4.0 * Cbar
     peaks, src = measured_peaks()
     achieved = alg_bytes * n_act / (prof["force_ms"] * 1e-3) / 1e9

@@ -296,6 +296,15 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     d.roff[b] = cv.take<uint32_t>(Npad);
   }
   d.posq_ref = cv.take<int4>(Npad);
+  if (!mixed) {  // pairs listed once
+    d.inc = cv.take<uint32_t>((size_t)cap * Npad);
+    d.inc_n = cv.take<uint32_t>(Npad);
+    d.rslot = cv.take<uint32_t>((size_t)cap * Npad);
+    d.inbox = cv.take<double4>(2 * (size_t)cap * Npad);
+    d.seg_flag = cv.take<uint32_t>(Npad / 16);
+    d.seg_wait = cv.take<uint32_t>(Npad / 16);
+    if (cfg->closure) d.inbox_cl = cv.take<float4>((size_t)cap * Npad);
+  }
   d.cand_tmp = cv.take<uint32_t>((size_t)cap * Npad);
   d.cand_n = cv.take<uint32_t>(Npad);
   d.big_list = cv.take<uint32_t>(Npad);
@@ -597,6 +606,8 @@ int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const
   for (int b = 0; b < 3; ++b)
     CK(cudaMemsetAsync(ctx->d.vf[b], 0, sizeof(unsigned long long) * ((size_t)ctx->d.Cf_total + 1), s));
   CK(cudaMemsetAsync(ctx->d.cell_count, 0, sizeof(uint32_t) * ((size_t)ctx->d.C_total + 2), s));
+  if (ctx->d.seg_flag)
+    CK(cudaMemsetAsync(ctx->d.seg_flag, 0, sizeof(uint32_t) * (size_t)(ctx->d.Npad / 16), s));
   launch_set_rebuild(ctx->d, s);
   launch_rebuild(ctx->d, s);
   if (bond_touching) launch_bond_touching(ctx->d, s);

@@ -98,6 +98,8 @@ struct Ctl {
   long long rebuilds;
   unsigned status;   // latched error bits
   unsigned block_counter;
+  int blk_next;      // next block of the running force launch (blocks take segments in start order)
+  uint32_t epoch;    // force launches completed (segment flags of the running launch reach epoch + 1)
   int max_cand;
   unsigned coupled;
   long long cand_total;  // candidate entries summed over particles at the last rebuild
@@ -129,9 +131,20 @@ struct Dev {
   unsigned long long* vq[2];      // volume quantum round(V 2^40 / V_cell)
   double4* wallh[2];              // wall spring history [3][Npad] (FP64 mode)
   float4* wallhf[2];              // wall spring history [3][Npad] (mixed)
-  void* rec[2];                   // contact records, one segment of 32*cap per warp of particles
-  uint32_t* cnt[2];               // candidates per particle
+  // Candidate lists.  Mixed: every sphere lists all its candidates (a pair
+  // is evaluated from both sides).  FP64: a pair is listed once, by its
+  // lower-index sphere (the owner); the partner receives the result in its
+  // inbox.
+  void* rec[2];                   // contact records, one segment of ppw*cap per warp of the force kernel
+  uint32_t* cnt[2];               // records of a particle
   uint32_t* roff[2];              // index of a particle's first record
+  uint32_t* inc;                  // FP64, rebuild scratch [cap][Npad]: lower-index partners
+  uint32_t* inc_n;                // FP64: pairs a particle's lower-index partners own
+  uint32_t* rslot;                // FP64, per record: slot k of the pair in the partner's inbox
+  double4* inbox;                 // FP64 [cap][Npad] x 2: force on the owner and n x F_t of a pair
+  float4* inbox_cl;               // FP64 [cap][Npad]: closure data of a pair (contact, overlap, bond capacity)
+  uint32_t* seg_flag;             // FP64, per warp segment: launch epoch once its pairs are evaluated
+  uint32_t* seg_wait;             // FP64, per warp segment: lowest segment owning a pair of its spheres
   int4* posq_ref;                 // fixed-point positions at the last rebuild
   uint32_t* cand_tmp;             // rebuild scratch: candidate partners [cap][Npad]
   uint32_t* cand_n;               // rebuild scratch: candidates found per particle

@@ -1,16 +1,29 @@
 // k_forces.cu -- contact, wall, body and drag forces of one DEM step fused
 // with the velocity-Verlet update (arXiv 2211.06142, Sec. 2.1-2.3).
 //
-// Work decomposition.  Particles are grouped by warp (32 consecutive
-// particles in cell order, or 16 for samples too small to fill the GPU).  A
-// warp's candidate records are stored contiguously (particle after
-// particle), so the warp walks them in rounds of 32 entries: every lane
-// evaluates one pair per round whatever the candidate counts of the
-// particles are (the size ratio of the sand is 6, so counts vary several-fold
-// within a warp).  Each pair is evaluated from both sides with bit-identical
-// magnitudes; a particle sums its own pair forces in list order by a
-// segmented warp scan, so the result is deterministic and needs no
-// floating-point atomics.
+// Work decomposition.  Spheres are grouped by warp (32 consecutive spheres
+// in cell order, or 16 for samples too small to fill the GPU); a warp's
+// candidate records are stored contiguously (sphere after sphere), so the
+// warp walks them in rounds of 32 entries: every lane evaluates one pair per
+// round whatever the list lengths are (the size ratio of the sand is 6, so
+// they vary several-fold within a warp).  The spheres' sums come from a
+// segmented warp scan in list order, then each lane that owns a sphere runs
+// its epilogue: walls, gravity, buoyancy, drag, integration, porosity
+// scatter, closure network, bookkeeping.
+//
+// Mixed precision lists every pair from both sides and evaluates it twice
+// (bit-identical magnitudes).  The step is bound by the latency of the
+// rounds, not by arithmetic: listing each pair once and passing its result
+// to the partner through memory measured slower (the exchange and the wait
+// for it cost more than the halved rounds save).  FP64 is bound by the FP64
+// pipe, so there each pair is listed once, by its lower-index sphere (the
+// owner): the owner's warp writes the pair's result (the force on the owner
+// and n x F_t) into the partner's inbox slot, publishes that its segment is
+// done, waits until the segments owning its spheres' lower-index partners
+// have published (blocks take segments in the order they start, from a
+// counter, so every warp waited on is running and publishes before it waits
+// itself) and adds its inbox in slot order.  Every sum runs in a fixed
+// order, so the step is deterministic and needs no floating-point atomics.
 //
 // Two precisions:
 //   FP64  -- geometry and contact physics in double.
@@ -174,6 +187,23 @@ __device__ __forceinline__ V3<T> drag_force(T rho_f, T mu_f, T dp, V3<T> w, T n)
 }
 
 enum { MODE_FORCES = 0, MODE_MID = 1, MODE_CANON = 2 };
+
+// Flags and data that other blocks of the same launch write: the flag with
+// acquire / release semantics at GPU scope, the data from L2 (not L1).
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* a) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* a, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ double4 ldcg_d4(const double4* a) {
+  const double2* b = reinterpret_cast<const double2*>(a);
+  const double2 u = __ldcg(b), w = __ldcg(b + 1);
+  return make_double4(u.x, u.y, w.x, w.y);
+}
+constexpr int WAIT_LIMIT = 1 << 22;  // polls of a segment flag before the step reports a timeout
 
 // Bring a line into L1 ahead of use (no register is held meanwhile).
 __device__ __forceinline__ void prefetch_l1(const void* p) {
@@ -392,11 +422,23 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   const int ce = d.sp[0].couple_every;
   const bool couple_next = ce == 1 || (unsigned)(m_step % ce) == 0u;
   const int lane = threadIdx.x & 31;
+  // FP64: blocks take their segments in the order they start (a counter),
+  // so a warp only ever waits for warps that are already running
+  constexpr bool HALF = !MIXED;  // FP64: every pair listed once (see the file comment)
+  const uint32_t epoch = ctl->epoch + 1u;  // value of a segment flag once its pairs are done
+  __shared__ int blk_s;
+  __shared__ unsigned bk_n;
+  if (threadIdx.x == 0) {
+    blk_s = HALF ? atomicAdd(&ctl->blk_next, 1) : (int)blockIdx.x;
+    bk_n = 0u;
+  }
+  __syncthreads();
   // P spheres per warp (32; 16 for small samples, twice the warps to hide
   // latency); lanes >= P own no sphere but evaluate entries.  The grid
   // covers Npad / P warps exactly.
   const int P = d.ppw;
-  const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * P;
+  const int sg = (blk_s * (int)blockDim.x + (int)threadIdx.x) >> 5;  // segment of this warp
+  const int wbase = sg * P;
   const bool owner_lane = lane < P;
   const int p = owner_lane ? wbase + lane : wbase;
   const bool valid = owner_lane && p < d.N;
@@ -437,11 +479,6 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   __shared__ int bk_s[FORCE_BLOCK_MAX / 32];
   __shared__ float bk_m[FORCE_BLOCK_MAX / 32];
   __shared__ unsigned bk_c[FORCE_BLOCK_MAX / 32];
-  __shared__ unsigned bk_n;
-  if (MODE == MODE_MID) {
-    if (threadIdx.x == 0) bk_n = 0u;
-    __syncthreads();
-  }
 
   // ---- own particle, contact phase ----
   Owner<MIXED> me;
@@ -537,6 +574,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     if (has) {
       const SampleDev& S = d.sp[os];
       const size_t idx = (size_t)seg + e;
+      const uint32_t slot = HALF ? d.rslot[idx] : 0xffffffffu;  // the pair's slot in the partner's inbox
       const int owner_p = wbase + own;
       uint32_t pf;
       V3<T> xi;
@@ -693,7 +731,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
               xi = v3<T>(xid.x, xid.y, xid.z);
               const V3<double> nFt = cross3(n, Ft);
               Fc = v3<T>(Fi.x, Fi.y, Fi.z);
-              Tc = v3<T>(Ri * nFt.x, Ri * nFt.y, Ri * nFt.z);
+              Tc = v3<T>(nFt.x, nFt.y, nFt.z);
               if (feat) {
                 e_z = 1;
                 e_d = delta;
@@ -725,6 +763,18 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
           *reinterpret_cast<int4*>(rr) = make_int4(q, 0, 0, 0);
           *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
+        }
+      }
+      // FP64: the pair's result for the partner (zeros when inactive), into
+      // its slot of the partner's inbox: the force on the owner and n x F_t
+      // (the torque on either sphere divided by its radius)
+      if constexpr (HALF) {
+        if (slot < (uint32_t)d.cap) {
+          const size_t ib = (size_t)slot * d.Npad + q;
+          double4* o4 = d.inbox + 2 * ib;
+          o4[0] = make_double4(Fc.x, Fc.y, Fc.z, Tc.x);
+          o4[1] = make_double4(Tc.y, Tc.z, 0.0, 0.0);
+          if (feat) d.inbox_cl[ib] = make_float4((float)e_z, (float)e_d, (float)e_c, 0.f);
         }
       }
     }
@@ -800,6 +850,57 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           Cacc += s8;
         }
       }
+    }
+  }
+
+  // ---- FP64: the pairs owned by lower-index partners ----
+  // publish this segment, then wait for the segments owning the lowest
+  // partners of its spheres (bounded: a wait that runs out reports a timeout)
+  if constexpr (HALF) {
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_u32(&d.seg_flag[sg], epoch);
+    const int w0 = (int)d.seg_wait[sg];
+    bool ok = true;
+    for (int t0 = w0; t0 < sg && ok; t0 += 32) {
+      const int t = t0 + lane;
+      for (int it = 0;; ++it) {
+        const bool done = t >= sg || (int)(ld_acquire_u32(&d.seg_flag[t]) - epoch) >= 0;
+        if (__all_sync(FULL, done)) break;
+        if (it >= WAIT_LIMIT) {
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (!ok && lane == 0) latch(ctl, ST_TIMEOUT);
+    __threadfence();
+    if (valid) {
+      // inbox in slot order: force on the owner negated, n x F_t as it is
+      const uint32_t nin = d.inc_n[p];
+#pragma unroll 4
+      for (uint32_t k = 0; k < nin; ++k) {
+        const double4* o4 = d.inbox + 2 * ((size_t)k * d.Npad + p);
+        const double4 b0 = ldcg_d4(o4), b1 = ldcg_d4(o4 + 1);
+        F.x -= b0.x;
+        F.y -= b0.y;
+        F.z -= b0.z;
+        Tq.x += b0.w;
+        Tq.y += b1.x;
+        Tq.z += b1.y;
+      }
+      if (feat) {
+        for (uint32_t k = 0; k < nin; ++k) {
+          const float4 c = __ldcg(d.inbox_cl + (size_t)k * d.Npad + p);
+          Zacc += c.x;
+          Dacc += c.y;
+          Cacc += c.z;
+        }
+      }
+      // the torque arm R_i multiplies the summed n x F_t
+      const T Ri = me.P.w;
+      Tq = v3<T>(Ri * Tq.x, Ri * Tq.y, Ri * Tq.z);
     }
   }
 
@@ -1088,58 +1189,67 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     if (threadIdx.x < 32) tc05::tmem_dealloc(cl_tmem, 64);
   }
 
-  if (MODE != MODE_MID) return;
-
   // ---- bookkeeping: displacement since rebuild, porosity rotation, step ----
-  {
+  const int wib = threadIdx.x >> 5;
+  if (MODE == MODE_MID) {
     unsigned long long* z = d.vf[(vfc + 2) % 3];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.Cf_total; c += gridDim.x * blockDim.x)
       z[c] = 0ull;
-  }
-  const int s0 = __shfl_sync(FULL, si, 0);
-  const bool uniform = __all_sync(FULL, !valid || si == s0);
-  float md = my_disp2;
+    const int s0 = __shfl_sync(FULL, si, 0);
+    const bool uniform = __all_sync(FULL, !valid || si == s0);
+    float md = my_disp2;
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
-  // one fence and one arrival per block, without a block barrier: each warp
-  // leaves its maximum in shared memory, and the block's last warp publishes
-  // them (a warp that straddles samples publishes per lane and fences)
-  const int wib = threadIdx.x >> 5;
-  const unsigned wcoupled = __any_sync(FULL, coupled) ? 1u : 0u;
-  if (!uniform) {
-    if (my_disp2 >= 0.f) atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
-    __threadfence();
+    for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
+    // one fence and one arrival per block, without a block barrier: each
+    // warp leaves its maximum in shared memory, and the block's last warp
+    // publishes them (a warp that straddles samples publishes per lane and
+    // fences)
+    const unsigned wcoupled = __any_sync(FULL, coupled) ? 1u : 0u;
+    if (!uniform) {
+      if (my_disp2 >= 0.f) atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
+      __threadfence();
+    }
+    if (lane == 0) {
+      bk_s[wib] = s0;
+      bk_m[wib] = uniform ? md : -1.f;
+      bk_c[wib] = wcoupled;
+    }
   }
   if (lane != 0) return;
-  bk_s[wib] = s0;
-  bk_m[wib] = uniform ? md : -1.f;
-  bk_c[wib] = wcoupled;
   __threadfence_block();
   const unsigned nw = blockDim.x >> 5;
   if (atomicAdd(&bk_n, 1u) != nw - 1u) return;
   __threadfence_block();
   {
-    unsigned any = 0u;
-    for (unsigned w = 0; w < nw; ++w) {
-      const float mw = *((volatile float*)&bk_m[w]);
-      if (mw >= 0.f) atomicMax(&d.dmax2[*((volatile int*)&bk_s[w])], __float_as_uint(mw));
-      any |= *((volatile unsigned*)&bk_c[w]);
+    if (MODE == MODE_MID) {
+      unsigned any = 0u;
+      for (unsigned w = 0; w < nw; ++w) {
+        const float mw = *((volatile float*)&bk_m[w]);
+        if (mw >= 0.f) atomicMax(&d.dmax2[*((volatile int*)&bk_s[w])], __float_as_uint(mw));
+        any |= *((volatile unsigned*)&bk_c[w]);
+      }
+      if (any) atomicOr(&ctl->coupled, 1u);
     }
-    if (any) atomicOr(&ctl->coupled, 1u);
     __threadfence();
     const unsigned t = atomicAdd(&ctl->block_counter, 1u);
     if (t == gridDim.x - 1) {
+      // every block has started and finished: the segment order and the
+      // flags' epoch move on for the next launch
       __threadfence();
-      for (int s = 0; s < d.n_samples; ++s) {
-        const unsigned b = atomicAdd(&d.dmax2[s], 0u);
-        if (__uint_as_float(b) > d.sp[s].rebuild_q2) ctl->rebuild = 1;
+      if (MODE == MODE_MID) {
+        for (int s = 0; s < d.n_samples; ++s) {
+          const unsigned b = atomicAdd(&d.dmax2[s], 0u);
+          if (__uint_as_float(b) > d.sp[s].rebuild_q2) ctl->rebuild = 1;
+        }
+        if (atomicExch(&ctl->coupled, 0u)) ctl->vf_cur = (vfc + 1) % 3;
+        ctl->cur = nxt;
+        ctl->step = m_step;
       }
-      if (atomicExch(&ctl->coupled, 0u)) ctl->vf_cur = (vfc + 1) % 3;
-      ctl->cur = nxt;
-      ctl->step = m_step;
+      ctl->epoch = epoch;
+      ctl->blk_next = 0;
       ctl->block_counter = 0u;
       __threadfence();
-      if (h_next) cudaGraphSetConditional(h_next, ctl->rebuild ? 1u : 0u);
+      if (MODE == MODE_MID && h_next) cudaGraphSetConditional(h_next, ctl->rebuild ? 1u : 0u);
     }
   }
 }

@@ -344,10 +344,11 @@ __global__ void k_rb_pairs_big(Dev d) {
   }
 }
 
-// Sort each list by partner, pack the records of a warp contiguously and
-// carry the contact history of the old records by particle pair.
+// Mixed: every sphere lists all its candidates.  Sort each list by partner,
+// pack the records of a warp contiguously and carry the contact history of
+// the old records by particle pair.
 template <bool MIXED>
-__global__ void k_rb_lists(Dev d) {
+__global__ void k_rb_lists_full(Dev d) {
   if (!d.ctl->rebuild) return;
   const int nxt = d.ctl->cur ^ 1;
   const int pn = d.ctl->pcur ^ 1;
@@ -449,6 +450,192 @@ __global__ void k_rb_lists(Dev d) {
         RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + first + hit;
         *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, h0.z, h0.w);
         *(reinterpret_cast<double2*>(rr) + 1) = h1;
+      }
+    } else if ((pf & REC_BOND) && d.posq[nxt][qn].w > 0) {
+      // a bond may leave the list only with a partner that left the domain
+      if (atomicCAS(&d.ctl->lost_i, -1, d.id[pn][p]) == -1) {
+        const int4 qq = d.posq[nxt][qn];
+        const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
+        const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
+        const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
+        d.ctl->lost_j = d.id[pn][qn];
+        d.ctl->lost_d2 = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+                         (unsigned long long)((long long)dz * dz);
+        const unsigned long long S = (unsigned long long)(unsigned)pq.w + (unsigned)qq.w +
+                                     (unsigned)d.sp[d.sample[pn][p]].skin_q;
+        d.ctl->lost_S2 = S * S;
+      }
+      latch(d.ctl, ST_BOND_LOST);
+    }
+  }
+}
+
+// FP64: sort each candidate list by partner.  A sphere owns the pairs with
+// its higher-index partners: their records (zero history) are packed so that
+// the records of a segment of ppw consecutive spheres (one warp of the force
+// kernel) are contiguous.  Its lower-index partners are kept for k_rb_carry.
+template <bool MIXED>
+__global__ void k_rb_lists_half(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int nxt = d.ctl->cur ^ 1;
+  const int rn = d.ctl->rec_cur ^ 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad exactly
+  const int lane = threadIdx.x & 31;
+  const int Npad = d.Npad, cap = d.cap;
+  if (p - lane >= Npad) return;  // whole warps only (Npad is a multiple of 256)
+  const bool valid = p < d.N;
+  uint32_t count = valid ? d.cand_n[p] : 0u;
+  if (count > (uint32_t)cap) latch(d.ctl, ST_CAPACITY);
+  unsigned mx = count, sum = count;
+#pragma unroll
+  for (int k = 16; k >= 1; k >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, k));
+    sum += __shfl_xor_sync(0xffffffffu, sum, k);
+  }
+  if (lane == 0 && sum) {
+    atomicMax(&d.ctl->max_cand_next, (int)mx);
+    atomicAdd((unsigned long long*)&d.ctl->cand_total_next, (unsigned long long)sum);
+  }
+  const uint32_t n = count < (uint32_t)cap ? count : (uint32_t)cap;
+  // insertion sort by partner index (lists are short; sizes vary with the PSD)
+  uint32_t lst[CGDEM_MAX_NEIGHBORS];
+  uint32_t nl = 0;  // lower-index partners come first
+  if (valid) {
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t v = d.cand_tmp[(size_t)j * Npad + p];
+      uint32_t i = j;
+      while (i > 0 && lst[i - 1] > v) {
+        lst[i] = lst[i - 1];
+        --i;
+      }
+      lst[i] = v;
+    }
+    while (nl < n && lst[nl] < (uint32_t)p) ++nl;
+  }
+  const uint32_t nu = n - nl;
+  const int P = d.ppw, sub = lane & (P - 1);
+  uint32_t incl = nu;
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, k, P);
+    if (k < P && sub >= k) incl += y;
+  }
+  const uint32_t seg = (uint32_t)(p - sub) * (uint32_t)cap;
+  const uint32_t first = seg + incl - nu;
+  d.roff[rn][p] = first;
+  d.cnt[rn][p] = nu;
+  d.inc_n[p] = nl;
+  if (sub == 0) d.seg_wait[p / P] = (uint32_t)(p / P);  // lowered by k_rb_carry
+  if (!valid) return;
+  d.posq_ref[p] = d.posq[nxt][p];
+  for (uint32_t j = 0; j < nu; ++j) {
+    if (MIXED) {
+      reinterpret_cast<uint4*>(d.rec[rn])[first + j] = make_uint4(lst[nl + j], 0u, 0u, 0u);
+    } else {
+      RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + first + j;
+      *reinterpret_cast<int4*>(rr) = make_int4((int)lst[nl + j], 0, 0, 0);
+      *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
+    }
+    d.rslot[first + j] = 0xffffffffu;  // set by k_rb_carry from the partner's side
+  }
+  for (uint32_t k = 0; k < nl; ++k) d.inc[(size_t)k * Npad + p] = lst[k];
+}
+
+// Record index of the pair (owner, partner) in list buffer b, or UINT_MAX.
+// Lists are sorted by partner; only the partner bits of the first word are
+// read (another thread may be rewriting the flags of the same word).
+__device__ __forceinline__ uint32_t find_record(const Dev& d, int b, uint32_t owner, uint32_t partner) {
+  const uint32_t base = d.roff[b][owner];
+  int lo = 0, hi = (int)d.cnt[b][owner] - 1;
+  while (lo <= hi) {
+    const int m = (lo + hi) >> 1;
+    const size_t idx = (size_t)base + m;
+    const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[b])[idx].x
+                                : reinterpret_cast<const RecD*>(d.rec[b])[idx].pf;
+    const uint32_t q = pf & REC_IDX;
+    if (q == partner) return (uint32_t)idx;
+    if (q < partner) lo = m + 1;
+    else hi = m - 1;
+  }
+  return 0xffffffffu;
+}
+
+// FP64, after k_rb_lists_half: (1) the record of each pair a lower-index partner owns
+// learns its slot in this sphere's inbox; (2) the contact history of the old
+// lists moves to the pair's record in the new lists, negated when the
+// pair's owner changed (the other sphere's tangential spring is the
+// opposite vector, Eq. 4).
+template <bool MIXED>
+__global__ void k_rb_carry(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int nxt = d.ctl->cur ^ 1;
+  const int pn = d.ctl->pcur ^ 1;
+  const int rc = d.ctl->rec_cur, rn = rc ^ 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const size_t Npad = (size_t)d.Npad;
+  const uint32_t nl = d.inc_n[p];
+  // the force kernel's warp of this sphere waits for the warp owning its
+  // lowest partner (the list is sorted)
+  if (nl) atomicMin(&d.seg_wait[p / d.ppw], d.inc[p] / (uint32_t)d.ppw);
+  for (uint32_t k = 0; k < nl; ++k) {
+    const uint32_t q = d.inc[k * Npad + p];
+    const uint32_t e = find_record(d, rn, q, (uint32_t)p);
+    if (e == 0xffffffffu) {  // the candidate relation lost its symmetry: a list overflowed
+      latch(d.ctl, ST_CAPACITY);
+      d.inc_n[p] = k;
+      break;
+    }
+    d.rslot[e] = k;
+  }
+  const int4 pq = d.posq[nxt][p];
+  if (pq.w <= 0) return;  // a sphere that left the domain drops its pairs
+  const uint32_t o = d.perm[p];
+  const uint32_t nold = d.cnt[rc][o];
+  const uint32_t oldfirst = d.roff[rc][o];
+  for (uint32_t k = 0; k < nold; ++k) {
+    const size_t oidx = (size_t)oldfirst + k;
+    uint32_t pf;
+    bool nz;
+    uint4 rf = make_uint4(0, 0, 0, 0);
+    int4 h0 = make_int4(0, 0, 0, 0);
+    double2 h1 = make_double2(0, 0);
+    if (MIXED) {
+      rf = reinterpret_cast<const uint4*>(d.rec[rc])[oidx];
+      pf = rf.x;
+      nz = (rf.y | rf.z | rf.w) != 0u;
+    } else {
+      const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + oidx;
+      h0 = *reinterpret_cast<const int4*>(rr);
+      h1 = *(reinterpret_cast<const double2*>(rr) + 1);
+      pf = (uint32_t)h0.x;
+      nz = (h0.z | h0.w) != 0 || h1.x != 0.0 || h1.y != 0.0;
+    }
+    if (!(pf & (REC_BOND | REC_ACTIVE)) && !nz) continue;
+    const uint32_t qn = d.inv_perm[pf & REC_IDX];
+    const bool mine = (uint32_t)p < qn;
+    const uint32_t owner = mine ? (uint32_t)p : qn, partner = mine ? qn : (uint32_t)p;
+    const uint32_t e = find_record(d, rn, owner, partner);
+    if (e != 0xffffffffu) {
+      const uint32_t npf = partner | (pf & (REC_BOND | REC_ACTIVE));
+      if (MIXED) {
+        uint4 w = make_uint4(npf, rf.y, rf.z, rf.w);
+        if (!mine) {
+          w.y = __float_as_uint(-__uint_as_float(rf.y));
+          w.z = __float_as_uint(-__uint_as_float(rf.z));
+          w.w = __float_as_uint(-__uint_as_float(rf.w));
+        }
+        reinterpret_cast<uint4*>(d.rec[rn])[e] = w;
+      } else {
+        double hx = __hiloint2double(h0.w, h0.z);
+        double2 hyz = h1;
+        if (!mine) {
+          hx = -hx;
+          hyz = make_double2(-h1.x, -h1.y);
+        }
+        RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + e;
+        *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, __double2loint(hx), __double2hiint(hx));
+        *(reinterpret_cast<double2*>(rr) + 1) = hyz;
       }
     } else if ((pf & REC_BOND) && d.posq[nxt][qn].w > 0) {
       // a bond may leave the list only with a partner that left the domain
@@ -786,6 +973,8 @@ __global__ void k_init_ctl(Dev d) {
   c->rebuilds = 0;
   c->status = 0;
   c->block_counter = 0;
+  c->blk_next = 0;
+  c->epoch = 0;
   c->max_cand = 0;
   c->max_cand_next = 0;
   c->cand_total = 0;
@@ -829,11 +1018,11 @@ __global__ void k_collect_contacts(Dev d, uint32_t* out, unsigned long long cap)
                                 : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
     if (!(pf & REC_ACTIVE)) continue;
     const int iq = d.id[pc][pf & REC_IDX];
-    if (ip >= iq) continue;
+    if (d.mixed && ip >= iq) continue;  // mixed lists hold each pair twice, FP64 lists once
     const unsigned long long slot = atomicAdd(d.contact_n, 1ull);
     if (slot < cap) {
-      out[2 * slot] = (uint32_t)ip;
-      out[2 * slot + 1] = (uint32_t)iq | ((pf & REC_BOND) ? 0x80000000u : 0u);
+      out[2 * slot] = (uint32_t)min(ip, iq);
+      out[2 * slot + 1] = (uint32_t)max(ip, iq) | ((pf & REC_BOND) ? 0x80000000u : 0u);
     }
   }
 }
@@ -868,7 +1057,8 @@ __global__ void k_diag_partial(Dev d, double* part) {
           const size_t idx = (size_t)d.roff[rc][p] + k;
           const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
                                       : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
-          if ((pf & REC_BOND) && (pf & REC_ACTIVE) && ip < d.id[pc][pf & REC_IDX]) o[7] += 1.0;
+          if ((pf & REC_BOND) && (pf & REC_ACTIVE) && (!d.mixed || ip < d.id[pc][pf & REC_IDX]))
+            o[7] += 1.0;  // mixed lists hold each pair twice
         }
       } else {
         o[5] += m;
@@ -909,8 +1099,12 @@ void launch_rebuild(const Dev& d, cudaStream_t s) {
   k_rb_pairs<<<G, B, 0, s>>>(d);
   k_rb_pairs_big<<<4 * 152, 256, 0, s>>>(d);
   const int Gp = nblk(d.Npad, B);
-  if (d.mixed) k_rb_lists<true><<<Gp, B, 0, s>>>(d);
-  else k_rb_lists<false><<<Gp, B, 0, s>>>(d);
+  if (d.mixed) {
+    k_rb_lists_full<true><<<Gp, B, 0, s>>>(d);
+  } else {
+    k_rb_lists_half<false><<<Gp, B, 0, s>>>(d);
+    k_rb_carry<false><<<G, B, 0, s>>>(d);
+  }
   k_rb_finish<<<1, 1, 0, s>>>(d);
 }
 
