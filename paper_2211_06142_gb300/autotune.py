@@ -4,8 +4,9 @@ for samples too small to fill the GPU), and the candidate-list skin.
 
 Coordinate search (each knob in turn, the others held at the best so far),
 each trial timing a short run of ``cgdem_step`` with CUDA events after a
-warm-up.  Results are cached in JSON keyed by a signature of the workload
-(sphere counts, domain kinds, largest radii, precision), so a workload is
+warm-up; the two fastest settings are then timed again with longer runs.
+Results are cached in JSON keyed by a signature of the workload (sphere
+counts, domain kinds, largest radii, precision), so a workload is
 tuned once per machine.  Every trial computes the same physics: the skin and
 the cells only change which candidate pairs are listed, never which pairs
 touch.
@@ -97,9 +98,9 @@ def autotune(params, counts, state, Us, precision=cgdem.MIXED, device="cuda:0", 
     best = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32}
     trials = []
 
-    def run(cs, b, sf, pw):
+    def run(cs, b, sf, pw, n=steps):
         try:
-            ms = trial(_with_skin(params, sf), counts, state, Us, precision, cs, b, steps=steps,
+            ms = trial(_with_skin(params, sf), counts, state, Us, precision, cs, b, steps=n,
                        device=device, ppw=pw)
         except cgdem.CgdemError as e:  # e.g. a skin below the bond-break separation
             ms = float("inf")
@@ -118,6 +119,22 @@ def autotune(params, counts, state, Us, precision=cgdem.MIXED, device="cuda:0", 
             ms = run(cand["cell_scale"], cand["block"], cand["skin_frac"], cand["ppw"])
             if ms < best_ms:
                 best, best_ms = cand, ms
+    # the short trials carry a few per cent of noise: the two fastest distinct
+    # settings are timed again, twice each with runs twice as long
+    keys = ("cell_scale", "block", "skin_frac", "ppw")
+    ranked, seen = [], set()
+    for t in sorted(trials, key=lambda t: t["ms_per_step"]):
+        k = tuple(t[x] for x in keys)
+        if k not in seen and t["ms_per_step"] < float("inf"):
+            seen.add(k)
+            ranked.append(dict(zip(keys, k)))
+    if len(ranked) > 1:
+        mean = {}
+        for c in ranked[:2]:
+            mean[tuple(c[x] for x in keys)] = sum(
+                run(c["cell_scale"], c["block"], c["skin_frac"], c["ppw"], 2 * steps) for _ in range(2)) / 2
+        k = min(mean, key=mean.get)
+        best, best_ms = dict(zip(keys, k)), mean[k]
     res = dict(best, ms_per_step=best_ms, trials=trials)
     if use_cache:
         try:

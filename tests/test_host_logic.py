@@ -82,3 +82,31 @@ def test_autotune_skin_copy_keeps_the_rest():
     assert q.L[0] == 3e-3 and q.nf[1] == 7 and p.skin == 1e-6
     assert A.signature([p], [10], 1) == A.signature([q], [10], 1)
     assert A.signature([p], [10], 1) != A.signature([p], [11], 1)
+
+
+def test_autotune_search_and_confirmation(monkeypatch, tmp_path):
+    """Coordinate search over the knobs with a fake timing: the best setting
+    wins, a noisy short trial is corrected by the longer confirmation runs,
+    and the result is cached by workload signature."""
+    monkeypatch.setenv("CGDEM_CACHE", str(tmp_path))
+    calls = []
+
+    def fake_trial(params, counts, state, Us, precision, cs, block, steps=600, device=None, ppw=32, **kw):
+        calls.append((cs, block, round(params[0].skin / (2 * params[0].r_max), 6), ppw, steps))
+        ms = 1.0 + abs(cs - 0.5) + 0.1 * abs(block - 128) / 128 + abs(params[0].skin / (2 * params[0].r_max) - 0.04)
+        ms += 0.01 * (ppw == 16)
+        if steps == 600 and (cs, block, ppw) == (0.75, 128, 32) and abs(params[0].skin - 0.02 * 2e-4) < 1e-12:
+            ms -= 0.3  # one short trial that happened to run fast
+        return ms
+
+    monkeypatch.setattr(A, "trial", fake_trial)
+    p = cgdem.SampleParams()
+    p.r_max = 1e-4
+    res = A.autotune([p], [100], None, None, cgdem.MIXED)
+    # the noisy trial misleads the cell sweep (0.75 kept, so the skin sweep
+    # runs there); the confirmation runs put the runner-up (0.5) back
+    assert (res["cell_scale"], res["block"], res["skin_frac"], res["ppw"]) == (0.5, 128, 0.02, 32)
+    assert not res["cached"] and any(c[4] == 1200 for c in calls)
+    n = len(calls)
+    again = A.autotune([p], [100], None, None, cgdem.MIXED)
+    assert again["cached"] and len(calls) == n and again["cell_scale"] == 0.5
