@@ -365,7 +365,7 @@ __device__ bool closure_infer(const float (&f)[5], uint8_t* sm, uint64_t* bar, u
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float zz = z[j] + bias[16 * c + j];
-        h[j] = zz / (1.0f + __expf(-zz));
+        h[j] = __fdividef(zz, 1.0f + __expf(-zz));  // SiLU; 0 where the exponential overflows
       }
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf)

@@ -55,7 +55,10 @@ constexpr uint32_t S_END = S_DZT + 32768;
 constexpr uint32_t C_Z1 = 0, C_Z2 = 64, C_Z3 = 128, C_O = 192, C_DA = 192;
 constexpr uint32_t C_DW4 = 256, C_DW2 = 320, C_DW3 = 416, C_DW1 = 496;
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+// logistic function with the hardware exponential and reciprocal (a few ulp
+// in FP32, far below the BF16 rounding of the activations; 0 where the
+// exponential overflows)
+__device__ __forceinline__ float sigm(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ void st_bf16(uint8_t* sm, uint32_t off, float v) {
   *reinterpret_cast<unsigned short*>(sm + off) = bf16_bits(v);
