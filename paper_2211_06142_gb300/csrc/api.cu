@@ -389,10 +389,10 @@ void enqueue_mid_step(cgdem_ctx* ctx, cudaStream_t s) {
 }
 
 // Capture U fused steps into one graph.  Each step's rebuild sequence sits in
-// the body of a conditional (IF) node whose condition a one-thread kernel
-// sets from the device-side rebuild flag, so steps without a rebuild launch
-// two kernels.  Falls back to a plain capture (rebuild kernels that return at
-// once) if conditional nodes are unavailable.
+// the body of a conditional (IF) node whose condition the previous step's
+// force kernel sets from the device-side rebuild flag, so a step without a
+// rebuild launches one kernel.  Falls back to a plain capture (rebuild
+// kernels that return at once) if conditional nodes are unavailable.
 cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec_t* out) {
   cudaStream_t cs, bs;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);

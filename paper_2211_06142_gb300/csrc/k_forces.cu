@@ -62,7 +62,7 @@ template <>
 struct Consts<double> {
   static __device__ __forceinline__ double damp() { return 1.8257418583505538; }
   static __device__ __forceinline__ double pi() { return PI_D; }
-  static constexpr int newton_iters = 6;
+  static constexpr int newton_iters = 5;  // from within ~5 % of the root: 1 ulp after 5 steps
 };
 
 // Elementary functions of the contact law.  Double: IEEE-accurate.  Float
@@ -717,7 +717,8 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
               const double4 QW = d.omg[cur][q];
               const double Ri = o.P.w, Rj = Q.w;
               const double mi = 1.0 / o.V.w, mj = 1.0 / QV.w;
-              const V3<double> n = v3<double>(dx / dist, dy / dist, dz / dist);
+              const double idist = 1.0 / dist;  // one FP64 division instead of three
+              const V3<double> n = v3<double>(dx * idist, dy * idist, dz * idist);
               const double ms = mi * mj / (mi + mj);
               const V3<double> vrel = v3<double>(QV.x - o.V.x, QV.y - o.V.y, QV.z - o.V.z);
               const V3<double> rw = v3<double>(Ri * o.W.x + Rj * QW.x, Ri * o.W.y + Rj * QW.y,
