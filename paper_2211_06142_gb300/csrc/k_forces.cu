@@ -65,7 +65,8 @@ struct Consts<double> {
   static constexpr int newton_iters = 5;  // from within ~5 % of the root: 1 ulp after 5 steps
 };
 
-// Elementary functions of the contact law.  Double: IEEE-accurate.  Float
+// Elementary functions of the contact law.  Double: correctly rounded or
+// within a few 1e-16 (the FP64 tolerance against the oracle is 1e-10).  Float
 // (the mixed mode, toleranced at 1e-4 against the FP64 oracle and with every
 // integer decision taken in FP64): hardware approximations of a few ulp --
 // reciprocal square root, base-2 logarithm and exponential, fast divide --
@@ -75,7 +76,10 @@ __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ double m_cbrt(double a) { return cbrt(a); }
 __device__ __forceinline__ double m_exp(double a) { return exp(a); }
 __device__ __forceinline__ double m_log10(double a) { return log10(a); }
-__device__ __forceinline__ double m_pow(double a, double b) { return pow(a, b); }
+// a^b for a > 0 as 2^(b log2 a): the exponent's rounding error (|b log2 a| < 10
+// here) moves the result by a few 1e-16 relative, and the general pow's
+// extra-precision path costs several times more FP64 work
+__device__ __forceinline__ double m_pow(double a, double b) { return exp2(b * log2(a)); }
 __device__ __forceinline__ float m_sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
 __device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ float m_cbrt(float a) {
