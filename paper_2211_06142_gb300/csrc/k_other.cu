@@ -245,14 +245,27 @@ __global__ void k_rb_pairs(Dev d) {
     d.big_list[atomicAdd(d.big_n, 1u)] = (uint32_t)p;
     return;
   }
+  // The cells of a stencil row (fixed y, z) are consecutive in the cell
+  // order, so their spheres are one index range (two where a periodic row
+  // wraps): one pair of cell_start loads per row instead of per cell.
+  int xs[2], xe[2], nseg = 1;
+  xs[0] = lo[0];
+  xe[0] = hi[0];
+  if (per && !all[0]) {
+    if (lo[0] < 0) {
+      xs[0] = lo[0] + S.nc[0], xe[0] = S.nc[0] - 1, xs[1] = 0, xe[1] = hi[0], nseg = 2;
+    } else if (hi[0] >= S.nc[0]) {
+      xs[0] = lo[0], xe[0] = S.nc[0] - 1, xs[1] = 0, xe[1] = hi[0] - S.nc[0], nseg = 2;
+    }
+  }
   for (int az = lo[2]; az <= hi[2]; ++az) {
     const int z = per && !all[2] ? (az + S.nc[2]) % S.nc[2] : az;
     for (int ay = lo[1]; ay <= hi[1]; ++ay) {
       const int y = per && !all[1] ? (ay + S.nc[1]) % S.nc[1] : ay;
-      for (int ax = lo[0]; ax <= hi[0]; ++ax) {
-        const int x = per && !all[0] ? (ax + S.nc[0]) % S.nc[0] : ax;
-        const int c = S.cell_off + (z * S.nc[1] + y) * S.nc[0] + x;
-        const uint32_t j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+      const int row = S.cell_off + (z * S.nc[1] + y) * S.nc[0];
+      for (int sgm = 0; sgm < nseg; ++sgm) {
+        const uint32_t j0 = d.cell_start[row + xs[sgm]], j1 = d.cell_start[row + xe[sgm] + 1];
+#pragma unroll 4
         for (uint32_t q = j0; q < j1; ++q) {
           const int4 qq = d.posq[nxt][q];
           if (qq.w <= 0) continue;
