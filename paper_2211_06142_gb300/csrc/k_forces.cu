@@ -529,11 +529,24 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   // mixed: each lane's record for the next round is loaded one round ahead
   uint4 rnext = make_uint4(0u, 0u, 0u, 0u);
   if (MIXED && lane < (int)total) rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + lane];
+  // mixed: and the partner's shadows one round ahead, in registers (the
+  // closure variant, short of registers, brings them into L1 instead)
+  constexpr bool RPF = MIXED && !CL;
+  int4 pq_nx = make_int4(0, 0, 0, 0);
+  float4 pa_nx = make_float4(0.f, 0.f, 0.f, 0.f), pb_nx = pa_nx;
+  if (RPF && lane < (int)total) {
+    const uint32_t q0 = rnext.x & REC_IDX;
+    pq_nx = d.posq[cur][q0];
+    pa_nx = d.velf[cur][q0];
+    pb_nx = d.omgf[cur][q0];
+  }
 
   for (uint32_t base = 0; base < total; base += 32) {
     const uint32_t e = base + lane;
     const bool has = e < total;
     uint4 rcur = rnext;
+    const int4 qq_c = pq_nx;
+    const float4 qa_c = pa_nx, qb_c = pb_nx;
     if (MIXED && e + 32u < total)
       rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + e + 32u];
     // owner lane: the last lane whose first entry is <= e
@@ -598,9 +611,9 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
                              xi.y != T(0) || xi.z != T(0);
       bool act = false;
       if constexpr (MIXED) {
-        const int4 qq = d.posq[cur][q];
-        const float4 qa = d.velf[cur][q];
-        const float4 qb = d.omgf[cur][q];
+        const int4 qq = RPF ? qq_c : d.posq[cur][q];
+        const float4 qa = RPF ? qa_c : d.velf[cur][q];
+        const float4 qb = RPF ? qb_c : d.omgf[cur][q];
         if (qq.w > 0 && o.pq.w > 0) {
           const int dx = (int)((uint32_t)qq.x - (uint32_t)o.pq.x);
           const int dy = (int)((uint32_t)qq.y - (uint32_t)o.pq.y);
@@ -784,11 +797,17 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
       }
     }
     if (MIXED && e + 32u < total) {
-      // the next round's partner, into L1 while this round's sums run
+      // the next round's partner, loaded while this round's sums run
       const uint32_t qn = rnext.x & REC_IDX;
-      prefetch_l1(&d.posq[cur][qn]);
-      prefetch_l1(&d.velf[cur][qn]);
-      prefetch_l1(&d.omgf[cur][qn]);
+      if constexpr (RPF) {
+        pq_nx = d.posq[cur][qn];
+        pa_nx = d.velf[cur][qn];
+        pb_nx = d.omgf[cur][qn];
+      } else {
+        prefetch_l1(&d.posq[cur][qn]);
+        prefetch_l1(&d.velf[cur][qn]);
+        prefetch_l1(&d.omgf[cur][qn]);
+      }
     }
     // contributions of this round to their owners: a segmented inclusive
     // scan over the lanes (entries of one owner are contiguous), then each
