@@ -325,16 +325,28 @@ __global__ void k_rb_pairs_big(Dev d) {
       ext[k] = h - l + 1;
     }
     const unsigned long long skin_q = (unsigned)S.skin_q;
-    const int total = ext[0] * ext[1] * ext[2];
+    // lanes take the stencil's rows of cells (fixed y, z), each one index
+    // range of the cell-sorted spheres (two where a periodic row wraps)
+    int xs[2], xe[2], nseg = 1;
+    xs[0] = lo[0];
+    xe[0] = lo[0] + ext[0] - 1;
+    if (per && !all[0]) {
+      if (xs[0] < 0) {
+        xs[1] = 0, xe[1] = xe[0], xs[0] += S.nc[0], xe[0] = S.nc[0] - 1, nseg = 2;
+      } else if (xe[0] >= S.nc[0]) {
+        xs[1] = 0, xe[1] = xe[0] - S.nc[0], xe[0] = S.nc[0] - 1, nseg = 2;
+      }
+    }
+    const int total = ext[1] * ext[2] * nseg;
     for (int t = lane; t < total; t += 32) {
-      const int ax = lo[0] + t % ext[0];
-      const int ay = lo[1] + (t / ext[0]) % ext[1];
-      const int az = lo[2] + t / (ext[0] * ext[1]);
-      const int x = per && !all[0] ? (ax + S.nc[0]) % S.nc[0] : ax;
+      const int sgm = t % nseg, r = t / nseg;
+      const int ay = lo[1] + r % ext[1];
+      const int az = lo[2] + r / ext[1];
       const int y = per && !all[1] ? (ay + S.nc[1]) % S.nc[1] : ay;
       const int z = per && !all[2] ? (az + S.nc[2]) % S.nc[2] : az;
-      const int c = S.cell_off + (z * S.nc[1] + y) * S.nc[0] + x;
-      const uint32_t j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+      const int row = S.cell_off + (z * S.nc[1] + y) * S.nc[0];
+      const uint32_t j0 = d.cell_start[row + xs[sgm]], j1 = d.cell_start[row + xe[sgm] + 1];
+#pragma unroll 4
       for (uint32_t q = j0; q < j1; ++q) {
         const int4 qq = d.posq[nxt][q];
         if (qq.w <= 0) continue;
