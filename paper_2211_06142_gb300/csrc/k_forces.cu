@@ -733,10 +733,10 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
               const double4 QV = d.vel[cur][q];
               const double4 QW = d.omg[cur][q];
               const double Ri = o.P.w, Rj = Q.w;
-              const double mi = 1.0 / o.V.w, mj = 1.0 / QV.w;
               const double idist = 1.0 / dist;  // one FP64 division instead of three
               const V3<double> n = v3<double>(dx * idist, dy * idist, dz * idist);
-              const double ms = mi * mj / (mi + mj);
+              // m* = m_i m_j / (m_i + m_j) = 1 / (1/m_i + 1/m_j), from the stored 1/m
+              const double ms = 1.0 / (o.V.w + QV.w);
               const V3<double> vrel = v3<double>(QV.x - o.V.x, QV.y - o.V.y, QV.z - o.V.z);
               const V3<double> rw = v3<double>(Ri * o.W.x + Rj * QW.x, Ri * o.W.y + Rj * QW.y,
                                                Ri * o.W.z + Rj * QW.z);

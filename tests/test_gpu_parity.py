@@ -267,6 +267,43 @@ def test_sixteen_spheres_per_warp(periodic, cylinder, prec, domain):
     np.testing.assert_array_equal(ctx.get_removed_step(), np.where(sim.removed_step() < 0, -1, sim.removed_step()))
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_rebuild_every_step_carries_history(periodic, prec):
+    """A candidate-list rebuild forced before each of 50 steps: the sphere
+    order is re-sorted every step, so pair records (and, in FP64, the
+    sphere that owns a pair and its inbox slots) change hands all the time;
+    the tangential springs and bonds carried across must give the oracle's
+    trajectory (contacts bit-exact in FP64, forces within the tolerance),
+    checked after 10 and 50 steps as in the trajectory tests."""
+    s = periodic
+    dt = default_dt(s)
+    ctx = gpu_context([s], prec, dt=dt)
+    ctx.compute_forces()
+    sim = run_oracle(s, dt)
+    rel = 1e-15 if prec == cgdem.FP64 else 1e-7
+    ref = run_oracle(perturbed(s, rel), dt)
+    L = s.domain["L"][0]
+    for chunk in (10, 40):
+        for _ in range(chunk):
+            ctx.build_contacts()
+            ctx.step(1)
+        sim.step(chunk)
+        ref.step(chunk)
+        g, o, r = ctx.get_state(), sim.state(), ref.state()
+        scale = sim.force_scale()
+        dxr = r["x"] - o["x"]
+        dxr -= L * np.round(dxr / L)
+        spreadx = np.abs(dxr).max()
+        if prec == cgdem.FP64:
+            check_contacts(ctx, sim)
+        else:
+            check_contacts_near(ctx, sim, s, eps=max(1e-9, 10 * spreadx / float(s.R.min())))
+        assert normwise_error(g["F"], o["F"], scale) <= max(TOL[prec], 10 * normwise_error(r["F"], o["F"], scale))
+        tsc = scale * s.R
+        assert normwise_error(g["T"], o["T"], tsc) <= max(TOL[prec], 10 * normwise_error(r["T"], o["T"], tsc))
+    assert ctx.counters()["rebuilds"] >= 51
+
+
 def test_fp64_fused_step_equals_verbs(periodic):
     """step(n) and the verbs (integrate 0, couple, forces, integrate 1) give
     the same FP64 state, up to FMA-contraction rounding, when no rebuild
