@@ -168,8 +168,9 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
     """The calibration-sweep ensemble: 64 independent periodic and cylinder
     samples (5k-50k grains, d50 0.15-0.35 mm, gamma 0.1-2 J/m^2, k in
     {1, 2, 3} under SSW) in one context, mixed precision, graph-captured
-    steps, search cells / block size / skin from the autotuner.  Under
-    torchrun the members are shared out over ranks by grain count."""
+    steps, search cells / block size / skin from the autotuner, per-member
+    skins balanced by drift rate when that is faster.  Under torchrun the
+    members are shared out over ranks by grain count."""
     from paper_2211_06142_gb300 import autotune as A
     from paper_2211_06142_gb300 import workloads as Wl
     specs, samples = Wl.ensemble(64, 3)
@@ -187,6 +188,23 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
              "trials": []})
     tune_s = time.perf_counter() - t0
     params = A.tuned_params(params, best)
+    # members that drift fastest get larger skins, so that one of them does
+    # not set the rebuild pace of the whole ensemble; kept only if faster
+    knobs = dict(cell_scale=best["cell_scale"], block=best["block"], ppw=best["ppw"], device=device)
+    balance = {"used": False}
+    if tune:
+        try:
+            bal, fac = A.balance_skins(params, counts, state, Us, cgdem.MIXED, **knobs)
+            ms0 = A.trial(params, counts, state, Us, cgdem.MIXED, best["cell_scale"], best["block"],
+                          steps=1200, device=device, ppw=best["ppw"])
+            ms1 = A.trial(bal, counts, state, Us, cgdem.MIXED, best["cell_scale"], best["block"],
+                          steps=1200, device=device, ppw=best["ppw"])
+            balance = {"used": bool(ms1 < ms0), "members_scaled": int((fac > 1.0).sum()),
+                       "max_factor": float(fac.max()), "ms_per_step": [ms0, ms1]}
+            if ms1 < ms0:
+                params = bal
+        except cgdem.CgdemError as e:  # e.g. a list over capacity at the larger skins
+            balance = {"used": False, "error": str(e)[:120]}
 
     def make(prec):
         ctx = cgdem.Context(params, counts, precision=prec, max_neighbors=48,
@@ -199,7 +217,9 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
         return ctx
 
     ctx = make(cgdem.MIXED)
+    c0 = ctx.counters()["rebuilds"]
     el = time_steps(ctx, torch, K, barrier)
+    rebuilds = ctx.counters()["rebuilds"] - c0
     prof = ctx.profile_step(100)
     cnt = ctx.counters()
     gi, _, _ = ctx.get_contacts()
@@ -231,6 +251,7 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
             "force_kernel_ms": prof["force_ms"], "alg_bytes_per_particle_step": alg,
             "force_kernel_gbs": alg * n_act / (prof["force_ms"] * 1e-3) / 1e9,
             "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1),
+            "rebuilds_in_timed_steps": rebuilds, "skin_balance": balance,
             "Zbar": Zbar, "candidates_per_particle": Cbar}
 
 

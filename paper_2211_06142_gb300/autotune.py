@@ -151,3 +151,46 @@ def autotune(params, counts, state, Us, precision=cgdem.MIXED, device="cuda:0", 
 
 def tuned_params(params, result):
     return _with_skin(params, result["skin_frac"])
+
+
+def skin_factors(rates, quantile=0.75, max_factor=2.5):
+    """Per-sample skin multipliers from each sample's drift rate (largest
+    speed x dt / skin): a rebuild of the ensemble is due when any member has
+    moved half its skin, so members that drift faster than the given
+    quantile of the ensemble get a proportionally larger skin (at most
+    max_factor), and the ensemble rebuilds at the pace of the bulk of its
+    members instead of its fastest one."""
+    rates = np.asarray(rates, float)
+    ref = float(np.quantile(rates, quantile)) if len(rates) else 0.0
+    if not ref > 0.0:
+        return np.ones(len(rates))
+    return np.clip(rates / ref, 1.0, max_factor)
+
+
+def balance_skins(params, counts, state, Us, precision=cgdem.MIXED, cell_scale=0.0, block=128, ppw=32,
+                  steps=300, device="cuda:0", max_neighbors=48, **kw):
+    """Run the ensemble for `steps` steps, measure each member's drift rate
+    and return its parameters with skins scaled by `skin_factors` (and the
+    factors)."""
+    ctx = cgdem.Context(params, counts, precision=precision, max_neighbors=max_neighbors,
+                        block_size=block, cell_scale=cell_scale, device=device, particles_per_warp=ppw)
+    try:
+        ctx.set_fluid_velocity(Us)
+        ctx.init_particles(*state, bond_touching=True)
+        ctx.compute_forces()
+        ctx.step(steps)
+        v = ctx.get_state()["v"]
+    finally:
+        ctx.close()
+    rates, off = [], 0
+    for p, n in zip(params, counts):
+        vm = float(np.sqrt((v[off:off + n] ** 2).sum(1)).max()) if n else 0.0
+        off += n
+        rates.append(vm * p.dt / p.skin if p.skin > 0 else 0.0)
+    f = skin_factors(rates, **kw)
+    out = []
+    for p, fk in zip(params, f):
+        q = _with_skin([p], p.skin / (2 * p.r_max))[0]
+        q.skin = p.skin * float(fk)
+        out.append(q)
+    return out, f

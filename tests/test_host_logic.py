@@ -110,3 +110,16 @@ def test_autotune_search_and_confirmation(monkeypatch, tmp_path):
     n = len(calls)
     again = A.autotune([p], [100], None, None, cgdem.MIXED)
     assert again["cached"] and len(calls) == n and again["cell_scale"] == 0.5
+
+
+def test_skin_factors_follow_drift_rates():
+    """Members drifting faster than the ensemble's upper quartile get a skin
+    scaled by their rate over it, capped; the rest keep theirs."""
+    rates = [1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 2.0, 3.0, 10.0]
+    f = A.skin_factors(rates, quantile=0.75, max_factor=2.5)
+    ref = float(np.quantile(rates, 0.75))
+    assert f[:7].tolist() == [1.0] * 7
+    assert f[7] == pytest.approx(max(1.0, 2.0 / ref)) and f[8] == pytest.approx(min(2.5, 3.0 / ref))
+    assert f[9] == 2.5
+    assert A.skin_factors([0.0, 0.0]).tolist() == [1.0, 1.0]
+    assert len(A.skin_factors([])) == 0
