@@ -263,6 +263,17 @@ class Closure:
         return self.theta.cpu().numpy()
 
 
+def spheres_per_warp_for(n, device="cuda:0"):
+    """Spheres per warp of the force kernel for a context of n spheres run
+    without the autotuner: 16 when 32 per warp would leave the GPU with fewer
+    than two blocks of 128 threads per SM (the step is then bound by one
+    warp's chain of rounds; on the 25,000-parcel coarse cylinder 16 per warp
+    is 16 % faster), else 32."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    return 16 if n < 2 * 128 * sms else 32
+
+
 def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1,
                   coulomb_mode=0, vf_mode=0, couple_every=1, n_min=0.2, r_max=None,
                   gamma_fine=None) -> SampleParams:

@@ -57,7 +57,7 @@ def run(s, k=1, scheme=cgdem.CG_NONE, U_ref=1e-4, T=0.004, n_times=20, precision
     p = cgdem.sample_params(s, dt, skin, k=k, scheme=scheme if k > 1 else cgdem.CG_NONE, vf_mode=vf_mode)
     use_cl = closure is not None or record
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=64, closure=use_cl,
-                        device=device)
+                        device=device, particles_per_warp=cgdem.spheres_per_warp_for(len(s.R), device))
     try:
         ctx.set_fluid_velocity(s.Us * (U_SAND / U_ref))
         ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
