@@ -49,8 +49,7 @@ def make_context(s, dt, skin, k, precision=cgdem.MIXED, max_neighbors=64, scheme
                  device="cuda:0", **sample_kw):
     p = cgdem.sample_params(s, dt, skin, k=k, scheme=scheme if k > 1 else cgdem.CG_NONE, **sample_kw)
     ctx = cgdem.Context([p], [len(s.R)], precision=precision, max_neighbors=max_neighbors,
-                        closure=True, device=device,
-                        particles_per_warp=cgdem.spheres_per_warp_for(len(s.R), device))
+                        closure=True, device=device)
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     return ctx
