@@ -482,8 +482,10 @@ def main():
     ctx.step(W)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
+    rb0 = ctx.counters()["rebuilds"]
     el = time_steps(ctx, torch, K, barrier)
     clocks = clk.stop()
+    rebuilds_timed = ctx.counters()["rebuilds"] - rb0
     if world > 1:
         t = torch.tensor([el], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -511,7 +513,14 @@ def main():
                 "alg_bytes_per_particle_step": alg_bytes, "Zbar": Zbar, "candidates_per_particle": Cbar,
                 "force_kernel_ms": prof["force_ms"], "max_candidates": cnt["max_candidates"],
                 "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1)}
-    launches_per_step = 1 + 9  # fused kernel + the rebuild sequence (early exit unless due)
+    # kernels launched by the timed cgdem_step(K): the half kick (3 kernels),
+    # one fused kernel per step, the final step's extra bookkeeping kernel,
+    # and the 13-kernel rebuild sequence in the final step, in the first step
+    # of every captured block of 32 steps (it runs by default there and
+    # returns early unless due) and in each rebuild that fell due (counted
+    # whether or not it fell in such a first step, so this bounds from above)
+    U = 32
+    gpu_launches = 3 + K + 1 + 13 * (1 + (K - 1) // U + rebuilds_timed)
     ctx.close()
     del ctx
 
@@ -583,9 +592,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": Ke},
-            "gpu_launches": launches_per_step * K + 2,
+            "gpu_launches": gpu_launches,
             "clocks": clocks,
-            "rebuilds": cnt["rebuilds"],
+            "rebuilds": cnt["rebuilds"], "rebuilds_in_timed_steps": rebuilds_timed,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
