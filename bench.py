@@ -515,12 +515,11 @@ def main():
                 "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1)}
     # kernels launched by the timed cgdem_step(K): the half kick (3 kernels),
     # one fused kernel per step, the final step's extra bookkeeping kernel,
-    # and the 13-kernel rebuild sequence in the final step, in the first step
-    # of every captured block of 32 steps (it runs by default there and
-    # returns early unless due) and in each rebuild that fell due (counted
-    # whether or not it fell in such a first step, so this bounds from above)
+    # one condition kernel at the start of every captured block of 32 steps,
+    # and the 13-kernel rebuild sequence in the final step (it returns early
+    # unless due) and in each rebuild that fell due
     U = 32
-    gpu_launches = 3 + K + 1 + 13 * (1 + (K - 1) // U + rebuilds_timed)
+    gpu_launches = 3 + K + 1 + (K - 1) // U + 13 * (1 + rebuilds_timed)
     ctx.close()
     del ctx
 

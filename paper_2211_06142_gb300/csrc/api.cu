@@ -16,6 +16,7 @@ namespace cgdem {
 void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next);
 void launch_rebuild(const Dev& d, cudaStream_t s);
 void launch_set_rebuild(const Dev& d, cudaStream_t s);
+void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_bond_touching(const Dev& d, cudaStream_t s);
 void launch_couple(const Dev& d, cudaStream_t s);
 void launch_kick_drift(const Dev& d, int couple, cudaStream_t s);
@@ -390,8 +391,9 @@ void enqueue_mid_step(cgdem_ctx* ctx, cudaStream_t s) {
 
 // Capture U fused steps into one graph.  Each step's rebuild sequence sits in
 // the body of a conditional (IF) node whose condition the previous step's
-// force kernel sets from the device-side rebuild flag, so a step without a
-// rebuild launches one kernel.  Falls back to a plain capture (rebuild
+// force kernel sets from the device-side rebuild flag (the first step's, a
+// one-thread kernel at the graph's start), so a step without a rebuild
+// launches one kernel.  Falls back to a plain capture (rebuild
 // kernels that return at once) if conditional nodes are unavailable.
 cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec_t* out) {
   cudaStream_t cs, bs;
@@ -404,8 +406,8 @@ cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec
   }
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  // one handle per step: the first runs the (self-checking) rebuild body at
-  // every launch of the graph; step i's force kernel sets step i + 1's
+  // one handle per step: a one-thread kernel sets the first from the device
+  // flag at every launch of the graph; step i's force kernel sets step i + 1's
   std::vector<cudaGraphConditionalHandle> hs;
   if (conditional && e == cudaSuccess) {
     cudaStreamCaptureStatus stt;
@@ -420,6 +422,7 @@ cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec
       enqueue_mid_step(ctx, cs);
       continue;
     }
+    if (i == 0) launch_rebuild_cond(ctx->d, hs[0], cs);
     cudaStreamCaptureStatus stt;
     cudaGraph_t cg;
     const cudaGraphNode_t* deps = nullptr;

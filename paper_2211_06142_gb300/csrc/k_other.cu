@@ -1135,6 +1135,16 @@ void launch_rebuild(const Dev& d, cudaStream_t s) {
 
 void launch_set_rebuild(const Dev& d, cudaStream_t s) { k_set_rebuild<<<1, 1, 0, s>>>(d); }
 
+// First step of a captured block of steps: its rebuild node's condition from
+// the device flag (the later steps' conditions are set by the force kernel
+// of the step before).
+__global__ void k_rebuild_cond(Dev d, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, d.ctl->rebuild ? 1u : 0u);
+}
+void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_rebuild_cond<<<1, 1, 0, s>>>(d, h);
+}
+
 
 void launch_bond_touching(const Dev& d, cudaStream_t s) {
   if (d.N) k_bond_touching<<<nblk(d.N, 256), 256, 0, s>>>(d);
