@@ -187,7 +187,11 @@ int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream);
 /* nsteps full steps (half kick, drift, porosity every couple_every steps,
  * candidate-list rebuild when the skin may be exceeded, forces, half kick,
  * outlet), enqueued as CUDA graphs with no host round trip.  Needs forces
- * consistent with the state (after init or compute_forces). */
+ * consistent with the state (after init or compute_forces).  In FP64 each
+ * candidate pair is evaluated once and its result passed between warps of
+ * the force kernel in a fixed order; a warp's wait for another is bounded,
+ * and one that runs out (never expected) latches CGDEM_E_TIMEOUT, returned
+ * by the next readback or cgdem_status_sync. */
 int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream);
 
 /* ---------------------------------------------------------------------
