@@ -86,7 +86,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -479,9 +479,12 @@ def main():
 
     # ---- mixed precision (headline) ----
     ctx = build_context(s, cgdem.MIXED, dt, skin, device, **knobs)
+    # the sampler starts before the warm-up so that it is polling when the
+    # timed steps begin (nvidia-smi takes a while to start)
+    clk = ClockSampler(local)
     ctx.step(W)
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
+    time.sleep(0.3)
     rb0 = ctx.counters()["rebuilds"]
     el = time_steps(ctx, torch, K, barrier)
     clocks = clk.stop()
