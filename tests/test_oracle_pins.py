@@ -426,3 +426,80 @@ def test_gravity_buoyancy_free_fall():
     sim.step(100)
     v = sim.state()["v"][0, 2]
     assert v == pytest.approx(-9.81 * (1 - 998.2 / 2650.0) * 1e-3, rel=1e-12)
+
+
+# ------------------------------------------- tangential law, walls, outlet
+
+def _pair_at(overlap, R=1e-4, hist=None, p=None):
+    """Two equal unbonded spheres at rest along x with the given overlap."""
+    p = p or base_params(gamma=0.0)
+    m = 2650.0 * 4 / 3 * math.pi * R ** 3
+    return O.pair_contact(p, [0, 0, 0], [0, 0, 0], [0, 0, 0], R, m,
+                          [2 * R - overlap, 0, 0], [0, 0, 0], [0, 0, 0], R, m, hist=hist)
+
+
+def test_tangential_to_normal_stiffness_is_mindlin_ratio():
+    """For two identical elastic spheres the tangential contact stiffness
+    over the normal one is 2 (1 - nu) / (2 - nu) (Mindlin), whatever the
+    overlap: the normal stiffness by central differences of F_ne(delta),
+    the tangential one from a spring set in the tangent plane at rest."""
+    for delta in (1e-8, 1e-7, 1e-6):
+        h = 1e-4 * delta
+        kn = (_pair_at(delta + h)[4] - _pair_at(delta - h)[4]) / (2 * h)
+        s = 1e-12  # far below the Coulomb limit
+        Fi = _pair_at(delta, hist=[0.0, s, 0.0])[1]
+        kt = Fi[1] / s
+        assert kt / kn == pytest.approx(2 * (1 - NU) / (2 - NU), rel=1e-6)
+
+
+def test_coulomb_cap_saturates_at_mu_times_normal_force():
+    """A stretched spring beyond the Coulomb limit gives |F_t| = mu F_ne
+    exactly, along the spring, and the stored spring shrinks to F_t / k_t
+    (Eq. 35, R4)."""
+    p = base_params(gamma=0.0, mu=0.3)
+    delta = 1e-7
+    act, Fi, _, _, Fne, _, _, hist, _ = _pair_at(delta, hist=[0.0, 0.0, 1e-6], p=p)
+    assert act and Fne > 0
+    assert abs(Fi[2]) == pytest.approx(0.3 * Fne, rel=1e-12) and Fi[2] > 0 and Fi[1] == 0.0
+    # at rest the spring force is k_t xi: the shrunk spring reproduces the capped force
+    Fi2 = _pair_at(delta, hist=list(hist), p=p)[1]
+    assert Fi2[2] == pytest.approx(Fi[2], rel=1e-12)
+
+
+def test_sphere_resting_on_the_bottom_plane_has_the_hertz_overlap():
+    """One sphere on the bottom plane of the cylinder under gravity and
+    buoyancy comes to rest (damping, e = 0.5) at the overlap where the Hertz
+    force of a sphere on a flat, (4/3) E* sqrt(R) delta^(3/2), carries its
+    apparent weight m g (1 - rho_f / rho)."""
+    R, rho, rho_f, g = 1e-4, 2650.0, 998.2, 9.81
+    p = base_params(kind=1, Rc=1.0, H=1.0, r_out=1e-3, g=(0, 0, -g), dt=1e-6, use_buoyancy=1,
+                    gamma=0.0)
+    sim = O.Sim(p, [[0.5, 0.0, R]], [[0, 0, 0]], [[0, 0, 0]], [R])
+    sim.compute_forces()
+    sim.step(60000)
+    st = sim.state()
+    m = rho * 4 / 3 * math.pi * R ** 3
+    W = m * g * (1 - rho_f / rho)
+    delta = (3 * W / (4 * ES * math.sqrt(R))) ** (2 / 3)
+    assert R - st["x"][0, 2] == pytest.approx(delta, rel=1e-6)
+    assert abs(st["v"][0, 2]) < 1e-9 * math.sqrt(g * R)
+
+
+def test_outlet_removes_a_falling_sphere_on_time():
+    """A sphere released above the outlet hole falls freely (velocity
+    Verlet is exact under a constant force) and leaves at the first step
+    whose position is below -2R (Eq. 40), adding its mass to the produced
+    sand."""
+    R, rho, rho_f, g, dt = 1e-4, 2650.0, 998.2, 9.81, 1e-5
+    z0 = 3e-3
+    p = base_params(kind=1, Rc=1.0, H=1.0, r_out=2e-3, g=(0, 0, -g), dt=dt, use_buoyancy=1,
+                    gamma=0.0)
+    sim = O.Sim(p, [[0.0, 0.0, z0]], [[0, 0, 0]], [[0, 0, 0]], [R])
+    sim.compute_forces()
+    a = g * (1 - rho_f / rho)
+    n = 1
+    while z0 - 0.5 * a * (n * dt) ** 2 >= -2 * R:
+        n += 1
+    sim.step(n + 5)
+    assert sim.removed_step()[0] == n
+    assert sim.diagnostics()["produced_mass"] == pytest.approx(rho * 4 / 3 * math.pi * R ** 3, rel=1e-14)
