@@ -21,6 +21,14 @@
  *   - Bonds break at Table 1 point C (delta < delta_C) and never reform.
  *   - Drag: Eq. 8-11 with u the interstitial velocity U_s / n.
  *   - Rayleigh step Eq. 37-38 with G = E / (2 (1 + nu)).
+ *
+ * Parity unpinned (no value the paper prints or the mathematics fixes checks
+ * these parts; the GPU is compared against them as written): the tangential
+ * damping and spring rotation (the tangential stiffness is pinned by
+ * Mindlin's ratio), the Coulomb limit under cohesion F_ne + 2 F_C (the cap
+ * itself is pinned without cohesion), the drag of a coarse grain, the cube
+ * porosity spread, the side and top walls of the cylinder, and the closure
+ * hooks (not part of the paper).
  */
 #include "cgdem_oracle.h"
 
