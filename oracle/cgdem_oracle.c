@@ -27,8 +27,8 @@
  * damping and spring rotation (the tangential stiffness is pinned by
  * Mindlin's ratio), the Coulomb limit under cohesion F_ne + 2 F_C (the cap
  * itself is pinned without cohesion), the drag of a coarse grain, the cube
- * porosity spread, the side and top walls of the cylinder, and the closure
- * hooks (not part of the paper).
+ * porosity spread, the walls' tangential contact (their normal Hertz law is
+ * pinned), and the closure hooks (not part of the paper).
  */
 #include "cgdem_oracle.h"
 

@@ -466,23 +466,36 @@ def test_coulomb_cap_saturates_at_mu_times_normal_force():
     assert Fi2[2] == pytest.approx(Fi[2], rel=1e-12)
 
 
-def test_sphere_resting_on_the_bottom_plane_has_the_hertz_overlap():
-    """One sphere on the bottom plane of the cylinder under gravity and
-    buoyancy comes to rest (damping, e = 0.5) at the overlap where the Hertz
-    force of a sphere on a flat, (4/3) E* sqrt(R) delta^(3/2), carries its
-    apparent weight m g (1 - rho_f / rho)."""
+@pytest.mark.parametrize("wall", ["bottom", "side", "top"])
+def test_sphere_resting_on_a_wall_has_the_hertz_overlap(wall):
+    """One sphere pushed onto a wall of the cylinder by gravity (pointing at
+    that wall) and buoyancy comes to rest (damping, e = 0.5) at the overlap
+    where the Hertz force of a sphere on a flat, (4/3) E* sqrt(R)
+    delta^(3/2), carries its apparent weight m g (1 - rho_f / rho)."""
     R, rho, rho_f, g = 1e-4, 2650.0, 998.2, 9.81
-    p = base_params(kind=1, Rc=1.0, H=1.0, r_out=1e-3, g=(0, 0, -g), dt=1e-6, use_buoyancy=1,
-                    gamma=0.0)
-    sim = O.Sim(p, [[0.5, 0.0, R]], [[0, 0, 0]], [[0, 0, 0]], [R])
+    Rc, H = 0.1, 0.1
+    if wall == "bottom":
+        gv, x0, k = (0, 0, -g), [0.05, 0.0, R], 2
+    elif wall == "side":
+        gv, x0, k = (g, 0, 0), [Rc - R, 0.0, 0.05], 0
+    else:
+        gv, x0, k = (0, 0, g), [0.05, 0.0, H - R], 2
+    p = base_params(kind=1, Rc=Rc, H=H, r_out=1e-3, g=gv, dt=1e-6, use_buoyancy=1, gamma=0.0)
+    sim = O.Sim(p, [x0], [[0, 0, 0]], [[0, 0, 0]], [R])
     sim.compute_forces()
     sim.step(60000)
     st = sim.state()
     m = rho * 4 / 3 * math.pi * R ** 3
     W = m * g * (1 - rho_f / rho)
     delta = (3 * W / (4 * ES * math.sqrt(R))) ** (2 / 3)
-    assert R - st["x"][0, 2] == pytest.approx(delta, rel=1e-6)
-    assert abs(st["v"][0, 2]) < 1e-9 * math.sqrt(g * R)
+    if wall == "bottom":
+        ov = R - st["x"][0, 2]
+    elif wall == "side":
+        ov = math.hypot(st["x"][0, 0], st["x"][0, 1]) + R - Rc
+    else:
+        ov = st["x"][0, 2] + R - H
+    assert ov == pytest.approx(delta, rel=1e-6)
+    assert abs(st["v"][0, k]) < 1e-9 * math.sqrt(g * R)
 
 
 def test_outlet_removes_a_falling_sphere_on_time():
