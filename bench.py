@@ -513,6 +513,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": tr["bytes_per_launch"] if tr else None,
                 "peak_source": src, "kernel": "k_forces<mixed, fused step>",
+                "limiter": "latency and issue (half the issue slots used; DRAM traffic ~1.1x the algorithmic bytes)",
                 "alg_bytes_per_particle_step": alg_bytes, "Zbar": Zbar, "candidates_per_particle": Cbar,
                 "force_kernel_ms": prof["force_ms"], "max_candidates": cnt["max_candidates"],
                 "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1)}
