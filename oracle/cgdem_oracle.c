@@ -25,8 +25,9 @@
  * Parity unpinned (no value the paper prints or the mathematics fixes checks
  * these parts; the GPU is compared against them as written): the tangential
  * damping and spring rotation (the tangential stiffness is pinned by
- * Mindlin's ratio), the Coulomb limit under cohesion F_ne + 2 F_C (the cap
- * itself is pinned without cohesion), the drag of a coarse grain, the cube
+ * Mindlin's ratio), the choice of F_ne + 2 F_C as the Coulomb limit under
+ * cohesion (its positivity on the JKR branch is pinned), the drag of a
+ * coarse grain, the cube
  * porosity spread, the walls' tangential contact (their normal Hertz law is
  * pinned), and the closure hooks (not part of the paper).
  */

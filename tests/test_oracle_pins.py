@@ -516,3 +516,26 @@ def test_outlet_removes_a_falling_sphere_on_time():
     sim.step(n + 5)
     assert sim.removed_step()[0] == n
     assert sim.diagnostics()["produced_mass"] == pytest.approx(rho * 4 / 3 * math.pi * R ** 3, rel=1e-14)
+
+
+def test_cohesive_coulomb_limit_stays_positive_on_the_jkr_branch():
+    """Under cohesion the Coulomb limit is F_ne + 2 F_C (R5).  JKR theory
+    puts the smallest normal force of the stable branch at -F_C (the
+    pull-off force 3 pi gamma R*, Table 1), so the limit never drops below
+    F_C even where the bond pulls; a stretched spring saturates at mu times
+    it."""
+    R, g, mu = 1e-4, 0.5, 0.3
+    p = base_params(gamma=g, mu=mu, e=1.0)
+    m = 2650.0 * 4 / 3 * math.pi * R ** 3
+    Rs = R / 2
+    FC = 3 * math.pi * g * Rs
+    dC = O.delta_c(Rs, ES, g)
+    z = np.zeros(3)
+    for frac in (0.999, 0.5, 0.0, -0.5):  # from just above break to compression
+        d = frac * dC if frac > 0 else -frac * abs(dC)
+        act, Fi, _, _, Fne, _, _, _, bonded = O.pair_contact(
+            p, z, z, z, R, m, np.array([2 * R - d, 0, 0]), z, z, R, m, [0.0, 0.0, 1e-5], True)
+        assert act and bonded
+        assert Fne >= -FC * (1 + 1e-9)
+        assert abs(Fi[2]) == pytest.approx(mu * (Fne + 2 * FC), rel=1e-12)
+        assert abs(Fi[2]) >= mu * FC * (1 - 1e-9)
