@@ -27,9 +27,9 @@
  * damping and spring rotation (the tangential stiffness is pinned by
  * Mindlin's ratio), the choice of F_ne + 2 F_C as the Coulomb limit under
  * cohesion (its positivity on the JKR branch is pinned), the drag of a
- * coarse grain, the cube
- * porosity spread, the walls' tangential contact (their normal Hertz law is
- * pinned), and the closure hooks (not part of the paper).
+ * coarse grain, the cube porosity spread (its volume conservation is
+ * pinned), the walls' tangential contact (their normal Hertz law is pinned),
+ * and the closure hooks (not part of the paper).
  */
 #include "cgdem_oracle.h"
 
