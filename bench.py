@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark: particle-steps/s of the coarse-grained CFD-DEM step on GB300.
 
-Workload (default): the fine-scale sand-production cylinder -- 200,000
-log-normal spheres (mass-median 0.25 mm, sigma_ln 0.4, 0.1-0.6 mm), radius
-40 d50, height 30 d50, central outlet of radius 3 d50 in the lower face,
-radial inflow of water on a 40x40x20 grid, modified-JKR cohesion, mixed
-FP32-force / FP64-state precision.  The FP64 form runs too and is reported
-beside it.  Inputs are seeded and synthetic (see paper_2211_06142_gb300/inputs.py).
+Workload (headline): the largest single-GPU sample -- the sand-production
+cylinder scaled by 2.15 in radius and height (radius 21.5 mm, outlet of
+radius 3 d50 in the lower face), 1.97M log-normal spheres (mass-median
+0.25 mm, sigma_ln 0.4, 0.1-0.6 mm) at solid fraction 0.55, radial inflow of
+water on an 86x86x43 grid, modified-JKR cohesion, mixed FP32-force /
+FP64-state precision.  The FP64 form runs beside it.  Extra keys: the
+200k-sphere cylinder, the 64-member batched ensemble, the closure's cost
+and the produced-sand comparison of the coarse-grained models.  Inputs are
+seeded and synthetic (see paper_2211_06142_gb300/inputs.py).
 
 One "step" is one full DEM step of the whole path (candidate-list upkeep,
 porosity scatter, contact/wall/body/drag forces, velocity Verlet, outlet).
@@ -33,7 +36,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "particle-steps/s on 1 GB300 (FP64 vs mixed/batched); sand-mass error vs fine"
 UNIT = "particle-steps/s"
-WORKLOAD = "sand-production cylinder, 200k spheres, 40x40x20 fluid grid"
+WORKLOAD = ("sand-production cylinder scaled x2.15 (radius 21.5 mm, bed 11.3 mm, outlet 0.75 mm), "
+            "1.97M log-normal spheres, 86x86x43 fluid grid, radial inflow")
 
 
 def shard_samples(costs, world):
@@ -61,9 +65,17 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(n, seed):
+def make_workload(seed):
+    """The largest single-GPU sample: the sand-production cylinder scaled by
+    2.15 in radius and height, about 2.0M spheres (a packed periodic block
+    tiled through the bed)."""
     from paper_2211_06142_gb300 import inputs as I
-    return I.cached(I.fine_cylinder, n, seed)
+    return I.cached(I.tiled_cylinder, 2_000_000, 2.15, 3 + seed)
+
+
+def make_workload_200k(seed):
+    from paper_2211_06142_gb300 import inputs as I
+    return I.cached(I.fine_cylinder, 200_000, seed)
 
 
 def step_params(s):
@@ -144,6 +156,8 @@ def kernel_traffic(kernel_file, kernel, knobs):
         if not e or e.get("source_sha1") != h:
             return None
         for c in e.get("configs", []):
+            if "n" in c and int(c["n"]) != int(knobs.get("n", -1)):
+                continue
             if all(abs(float(c[k]) - float(knobs[k])) < 1e-9 for k in ("cell_scale", "skin_frac", "block", "ppw")):
                 return c
     except (OSError, ValueError, KeyError):
@@ -392,7 +406,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    s = make_workload(200_000, 1)
+    s = make_workload(1)
     dt, _ = step_params(s)
     K, W = max(1, args.steps), max(0, args.warmup)
     # bounded sample per step so that the whole K + W run ends in about a minute
@@ -427,17 +441,145 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=True, fp64=True):
+    """Headline-style measurement of one workload: autotuned knobs, the mixed
+    step timed over exactly K steps (CUDA events on the launching stream,
+    clocks sampled meanwhile), the FP64 step beside it, the fused kernel's
+    roofline, the kernels launched in the timed steps, and the candidate-list
+    rebuilds.  The rebuild is part of every step of the method but falls due
+    only every few tens of steps (when a sphere may have moved half the
+    skin), so a short timed window holds more or fewer rebuilds than its
+    share: the window's time is also reported with its rebuilds replaced by
+    the natural rate measured over a longer stretch (`amortised`)."""
+    N = len(s.R)
+    dt, skin = step_params(s)
+    tune = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32, "cached": False,
+            "trials": []}
+    if tune_on:
+        from paper_2211_06142_gb300 import autotune as A
+        t0 = time.perf_counter()
+        tune = A.autotune([cgdem.sample_params(s, dt, skin)], [N], (s.x, s.v, s.w, s.R), s.Us,
+                          cgdem.MIXED, device=device)
+        tune["seconds"] = time.perf_counter() - t0
+    skin = tune["skin_frac"] * 2 * float(s.R.max())
+    knobs = dict(block=tune["block"], cell_scale=tune["cell_scale"], ppw=tune["ppw"])
+
+    ctx = build_context(s, cgdem.MIXED, dt, skin, device, **knobs)
+    # the sampler starts before the warm-up so that it is polling when the
+    # timed steps begin (nvidia-smi takes a while to start)
+    clk = ClockSampler(local)
+    ctx.step(W)
+    torch.cuda.synchronize()
+    time.sleep(0.3)
+    rb0 = ctx.counters()["rebuilds"]
+    ks0, body = ctx.launch_counts()
+    el = time_steps(ctx, torch, K, barrier)
+    clocks = clk.stop()
+    rebuilds_timed = ctx.counters()["rebuilds"] - rb0
+    ks1, body = ctx.launch_counts()
+    gpu_launches = (ks1 - ks0) + body * rebuilds_timed
+    # natural rebuild rate over a longer stretch, and the cost of a rebuild
+    cal = max(400, 4 * K) if K < 400 else 0
+    rb1 = ctx.counters()["rebuilds"]
+    if cal:
+        ctx.step(cal)
+    rate = (ctx.counters()["rebuilds"] - rb1 + rebuilds_timed) / float(cal + K)
+    prof = ctx.profile_step(200)
+    rb_ms = prof["rebuild_ms_total"] / prof["rebuilds"] if prof["rebuilds"] else 0.0
+    el_am = el + (rate * K - rebuilds_timed) * rb_ms * 1e-3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([el, el_am], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el, el_am = (float(v) for v in t.tolist())
+    cnt = ctx.counters()
+    gi, _, _ = ctx.get_contacts()
+    diag = ctx.get_diagnostics()[0]
+    n_act = max(diag["n_active"], 1)
+    Zbar = 2.0 * len(gi) / n_act
+    Cbar = cnt["total_candidates"] / n_act
+    # algorithmic bytes per particle-step of the fused step kernel: FP64
+    # state (x,R | v,1/m | w,1/I) read + written = 192 B, the record of every
+    # active pair read + written once (16 B per contact per particle), each
+    # sphere's list entries read once (4 B per candidate: the owner reads the
+    # pair's index, the partner its incoming index)
+    alg_bytes = 192.0 + 16.0 * Zbar + 4.0 * Cbar
+    peaks, src = measured_peaks()
+    achieved = alg_bytes * n_act / (prof["force_ms"] * 1e-3) / 1e9
+    tr = kernel_traffic("k_forces.cu", "k_forces_mixed_mid", dict(tune, n=N))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "peak_source": src, "kernel": "k_forces<mixed, fused step>",
+                "alg_bytes_per_particle_step": alg_bytes, "units_per_launch": n_act,
+                "Zbar": Zbar, "candidates_per_particle": Cbar,
+                "force_kernel_ms": prof["force_ms"], "max_candidates": cnt["max_candidates"]}
+    ctx.close()
+    del ctx
+    out = {"spheres": N, "dt": dt, "skin": skin,
+           "value": N * K * world / el_am, "ms_per_step": 1e3 * el_am / K,
+           "raw": {"value": N * K * world / el, "ms_per_step": 1e3 * el / K,
+                   "rebuilds_in_timed_steps": rebuilds_timed},
+           "amortised": {"rebuilds_per_step": rate, "rebuild_ms": rb_ms, "stretch_steps": cal + K,
+                         "note": "timed window with its rebuilds replaced by rate x K rebuilds of "
+                                 "the measured cost"},
+           "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clocks,
+           "autotune": {k: tune[k] for k in ("cell_scale", "block", "skin_frac", "ppw")} |
+                       {"cached": tune.get("cached", False), "trials": len(tune.get("trials", []))},
+           "knobs": knobs}
+    if fp64:
+        ctx64 = build_context(s, cgdem.FP64, dt, skin, device, **knobs)
+        ctx64.step(W)
+        K64 = max(2, K // 8)
+        el64 = time_steps(ctx64, torch, K64, barrier)
+        p64 = ctx64.profile_step(20)
+        ctx64.close()
+        del ctx64
+        out["fp64"] = {"value": N * K64 * world / el64, "unit": UNIT, "steps": K64,
+                       "ms_per_step": 1e3 * el64 / K64, "force_kernel_ms": p64["force_ms"]}
+    return out
+
+
+def run_e2e(torch, cgdem, s, knobs, skin, K, device, barrier, world):
+    """The same metric end to end through the public API: pinned host
+    buffers in, initialisation (porosity, contact list, bonds), K steps, the
+    state (x, v, w, F, T) read back, all inside the timed region."""
+    N = len(s.R)
+    dt, _ = step_params(s)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    hx, hv, hw, hR = pin(s.x), pin(s.v), pin(s.w), pin(s.R)
+    p = cgdem.sample_params(s, dt, skin)
+    ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device,
+                        block_size=knobs["block"], cell_scale=knobs["cell_scale"],
+                        particles_per_warp=knobs["ppw"])
+    ctx.set_fluid_velocity(s.Us)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.init_particles(hx, hv, hw, hR, bond_touching=True)
+    ctx.compute_forces()
+    ctx.step(K)
+    st = ctx.get_state()
+    t1 = time.perf_counter()
+    barrier()
+    ctx.close()
+    h2d = (hx.nbytes + hv.nbytes + hw.nbytes + hR.nbytes) / K
+    d2h = sum(a.nbytes for a in st.values()) / K
+    return {"value": N * K * world / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": K}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-sand", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -462,143 +604,53 @@ def main():
     from paper_2211_06142_gb300 import build as B
     B.build()
     K, W = max(1, args.steps), max(3, args.warmup)
-    s = make_workload(args.n, 1 + rank)
+
+    # ---- headline: the 2.0M-sphere sand-production cylinder, mixed precision ----
+    s = make_workload(1 + rank)
     N = len(s.R)
-    dt, skin = step_params(s)
-    # search cells, force-kernel block and skin from the autotuner (cached per workload)
-    tune = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32, "cached": False,
-            "trials": []}
-    if not args.no_tune:
-        from paper_2211_06142_gb300 import autotune as A
-        t0 = time.perf_counter()
-        tune = A.autotune([cgdem.sample_params(s, dt, skin)], [N], (s.x, s.v, s.w, s.R), s.Us,
-                          cgdem.MIXED, device=device)
-        tune["seconds"] = time.perf_counter() - t0
-    skin = tune["skin_frac"] * 2 * float(s.R.max())
-    knobs = dict(block=tune["block"], cell_scale=tune["cell_scale"], ppw=tune["ppw"])
+    head = time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=not args.no_tune)
+    e2e = run_e2e(torch, cgdem, s, head["knobs"], head["skin"], min(K, 1000), device, barrier, world)
+    del s
 
-    # ---- mixed precision (headline) ----
-    ctx = build_context(s, cgdem.MIXED, dt, skin, device, **knobs)
-    # the sampler starts before the warm-up so that it is polling when the
-    # timed steps begin (nvidia-smi takes a while to start)
-    clk = ClockSampler(local)
-    ctx.step(W)
-    torch.cuda.synchronize()
-    time.sleep(0.3)
-    rb0 = ctx.counters()["rebuilds"]
-    el = time_steps(ctx, torch, K, barrier)
-    clocks = clk.stop()
-    rebuilds_timed = ctx.counters()["rebuilds"] - rb0
-    if world > 1:
-        t = torch.tensor([el], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    value = N * K * world / el
-    cnt = ctx.counters()
-    gi, _, gb = ctx.get_contacts()
-    diag = ctx.get_diagnostics()[0]
-    n_act = max(diag["n_active"], 1)
-    Zbar = 2.0 * len(gi) / n_act
-    Cbar = cnt["total_candidates"] / n_act
-    prof = ctx.profile_step(200)
-    # algorithmic bytes per particle-step of the fused step kernel: FP64
-    # state (x,R | v,1/m | w,1/I) read + written = 192 B, the record of every
-    # active pair read + written once (16 B per contact per particle), each
-    # sphere's list entries read once (4 B per candidate: the owner reads the
-    # pair's index, the partner its incoming index)
-    alg_bytes = 192.0 + 16.0 * Zbar + 4.0 * Cbar
-    peaks, src = measured_peaks()
-    achieved = alg_bytes * n_act / (prof["force_ms"] * 1e-3) / 1e9
-    tr = kernel_traffic("k_forces.cu", "k_forces_mixed_mid", tune)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": tr["bytes_per_launch"] if tr else None,
-                "peak_source": src, "kernel": "k_forces<mixed, fused step>",
-                "limiter": "latency and issue (half the issue slots used; DRAM traffic ~1.1x the algorithmic bytes)",
-                "alg_bytes_per_particle_step": alg_bytes, "Zbar": Zbar, "candidates_per_particle": Cbar,
-                "force_kernel_ms": prof["force_ms"], "max_candidates": cnt["max_candidates"],
-                "rebuild_ms_per_step": prof["rebuild_ms_total"] / max(prof["steps"], 1)}
-    # kernels launched by the timed cgdem_step(K): the half kick (3 kernels),
-    # one fused kernel per step, the final step's extra bookkeeping kernel,
-    # one condition kernel at the start of every captured block of 32 steps,
-    # and the 13-kernel rebuild sequence in the final step (it returns early
-    # unless due) and in each rebuild that fell due
-    U = 32
-    gpu_launches = 3 + K + 1 + (K - 1) // U + 13 * (1 + rebuilds_timed)
-    ctx.close()
-    del ctx
-
-    # ---- FP64 form ----
-    ctx64 = build_context(s, cgdem.FP64, dt, skin, device, **knobs)
-    ctx64.step(W)
-    K64 = max(1, K // 8)
-    el64 = time_steps(ctx64, torch, K64, barrier)
-    fp64 = {"value": N * K64 * world / el64, "unit": UNIT, "steps": K64,
-            "ms_per_step": 1e3 * el64 / K64}
-    ctx64.close()
-    del ctx64
-
-    # ---- end to end through the public API with pinned host buffers ----
-    Ke = min(K, 1000)
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-    hx, hv, hw, hR = pin(s.x), pin(s.v), pin(s.w), pin(s.R)
-    p = cgdem.sample_params(s, dt, skin)
-    ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device,
-                        block_size=knobs["block"], cell_scale=knobs["cell_scale"],
-                        particles_per_warp=knobs["ppw"])
-    ctx.set_fluid_velocity(s.Us)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.init_particles(hx, hv, hw, hR, bond_touching=True)
-    ctx.compute_forces()
-    ctx.step(Ke)
-    st = ctx.get_state()
-    t1 = time.perf_counter()
-    barrier()
-    e2e_val = N * Ke * world / (t1 - t0)
-    h2d = (hx.nbytes + hv.nbytes + hw.nbytes + hR.nbytes) / Ke
-    d2h = sum(a.nbytes for a in st.values()) / Ke
-    ctx.close()
-
-    batched = None
-    if not args.no_batched:
-        batched = run_batched(torch, cgdem, device, barrier, rank, world, min(K, 2000), W,
-                              tune=not args.no_tune)
-        peaks_b = peaks["hbm_gbs"]
-        batched["roofline_frac"] = batched["force_kernel_gbs"] / peaks_b
-
-    closure_cost = run_closure_cost(torch, device, barrier, min(K, 2000))
-    sand = None
-    if rank == 0 and not args.no_sand:
-        sand = run_sand()
+    extras = {}
+    if not args.no_extras:
+        # the 200k-sphere cylinder (the fine sand-production sample)
+        s2 = make_workload_200k(1 + rank)
+        extras["cylinder200k"] = time_workload(torch, cgdem, s2, max(K, 500), W, barrier, device, world,
+                                               local, tune_on=not args.no_tune)
+        if not args.no_batched:
+            b = run_batched(torch, cgdem, device, barrier, rank, world, min(max(K, 500), 2000), W,
+                            tune=not args.no_tune)
+            b["roofline_frac"] = b["force_kernel_gbs"] / measured_peaks()[0]["hbm_gbs"]
+            extras["batched"] = b
+        extras["closure"] = run_closure_cost(torch, device, barrier, min(max(K, 500), 2000))
+        if rank == 0 and not args.no_sand:
+            extras["sand"] = run_sand()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(s, dt)
+        cpu = oracle_baseline(make_workload(1), head["dt"])
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "spheres_per_gpu": N, "precision": "mixed",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "touched bytes per step exceed half the 129 MB L2; no flush",
-                       "autotune": {k: tune[k] for k in ("cell_scale", "block", "skin_frac", "ppw")} |
-                                   {"cached": tune.get("cached", False),
-                                    "trials": len(tune.get("trials", []))}},
-            "fp64": fp64,
-            "batched": batched,
-            "closure": closure_cost,
-            "sand": sand,
-            "roofline": roofline,
+                       "l2": "inputs larger than L2 (~0.5 GB of state and contact records touched "
+                             "per step vs the 129 MB L2); no flush",
+                       "autotune": head["autotune"]},
+            "timing": {"raw": head["raw"], "amortised": head["amortised"]},
+            "fp64": head.get("fp64"),
+            "roofline": head["roofline"],
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": Ke},
-            "gpu_launches": gpu_launches,
-            "clocks": clocks,
-            "rebuilds": cnt["rebuilds"], "rebuilds_in_timed_steps": rebuilds_timed,
+            "e2e": e2e,
+            "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"],
         }
+        for k, v in extras.items():
+            line[k] = v
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -186,7 +186,10 @@ int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream);
 
 /* nsteps full steps (half kick, drift, porosity every couple_every steps,
  * candidate-list rebuild when the skin may be exceeded, forces, half kick,
- * outlet), enqueued as CUDA graphs with no host round trip.  Needs forces
+ * outlet), enqueued as CUDA graphs with no host round trip: the opening half
+ * kick, blocks of steps_per_graph steps, blocks of the powers of two below
+ * it for the remainder, and the closing step, each captured on first use
+ * per stream.  Needs forces
  * consistent with the state (after init or compute_forces).  In FP64 each
  * candidate pair is evaluated once and its result passed between warps of
  * the force kernel in a fixed order; a warp's wait for another is bounded,
@@ -225,6 +228,17 @@ int cgdem_get_removed_step(cgdem_ctx* ctx, int32_t* removed_step, void* stream);
 int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_t* max_candidates,
                        int64_t* total_candidates, void* stream);
 
+/* Kernel launches of cgdem_step (no synchronisation; host counters):
+ * *step_kernels = kernels that cgdem_step calls on this context have
+ * launched unconditionally so far (every node of the captured graphs that
+ * runs on each replay); *rebuild_kernels = kernels of one candidate-list
+ * rebuild sequence, which a conditional graph node runs only on the steps
+ * whose rebuild falls due (0 when conditional nodes are unavailable: the
+ * rebuild kernels are then captured plainly and counted in *step_kernels).
+ * Kernels launched by a stretch of calls = the difference of step_kernels
+ * + rebuild_kernels x the rebuilds done in it (cgdem_get_counters). */
+int cgdem_get_launch_counts(cgdem_ctx* ctx, int64_t* step_kernels, int32_t* rebuild_kernels);
+
 /* ---------------------------------------------------------------------
  * Pair search without device allocation.
  * ------------------------------------------------------------------- */
@@ -245,7 +259,9 @@ int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_
  * inside the library that each GPU using the call keeps until the process
  * exits; the first call on a device looks up that array's address (make
  * that first call before any stream capture), and every later call reuses
- * the array, so calls whose GPU work overlaps race with each other.
+ * the array, so calls whose GPU work overlaps race with each other.  The
+ * address is kept for the life of the process: the call assumes that the
+ * device's primary context is never reset (cudaDeviceReset) in between.
  *   x [n,3], R [n]: DEVICE arrays of centres and radii (n <= 262144).
  *   box_lo, box_hi: HOST arrays of 3 doubles bounding the centres (the
  *     periodic cell when periodic != 0); the search grid has cells of edge

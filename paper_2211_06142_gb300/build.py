@@ -14,7 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcgdem.so")
 SOURCES = ["k_forces.cu", "k_other.cu", "api.cu", "noalloc.cu", "k_mlp.cu"]
-HEADERS = [os.path.join(CSRC, "cgdem_internal.cuh"), os.path.join(ROOT, "include", "cgdem.h")]
+# every translation unit is rebuilt when any shared header changes
+HEADERS = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))) + [
+    os.path.join(ROOT, "include", "cgdem.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]

@@ -34,7 +34,7 @@ EXPORTS = [
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
     "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
     "cgdem_get_contacts", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
-    "cgdem_get_counters", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
+    "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
     "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
 ]
@@ -111,6 +111,7 @@ def lib():
             "cgdem_get_diagnostics": (i, [vp, vp, i64, vp]),
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
             "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
+            "cgdem_get_launch_counts": (i, [vp, vp, vp]),
             "cgdem_profile_step": (i, [vp, i64, vp, vp]),
             "cgdem_touching_pairs_noalloc": (i, [vp, vp, i64, vp, vp, i, d, d, vp, i64, vp, vp]),
             "cgdem_mlp_workspace_size": (i, [vp]),
@@ -435,6 +436,13 @@ class Context:
         self._check(lib().cgdem_get_counters(self.h, C.byref(s), C.byref(r), C.byref(m), C.byref(t),
                                              self._s()), "get_counters")
         return dict(steps=s.value, rebuilds=r.value, max_candidates=m.value, total_candidates=t.value)
+
+    def launch_counts(self):
+        """(kernels cgdem_step launched unconditionally so far, kernels of one
+        conditional rebuild sequence)."""
+        k, b = C.c_int64(0), C.c_int32(0)
+        self._check(lib().cgdem_get_launch_counts(self.h, C.byref(k), C.byref(b)), "get_launch_counts")
+        return k.value, b.value
 
     # ---- learned closure ----
     def set_closure(self, theta=None, lo=None, hi=None, cd_log_max=3.0, cg_log_max=1.386,

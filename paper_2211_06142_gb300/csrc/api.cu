@@ -34,6 +34,16 @@ void launch_closure_pack(const float* theta, const float* lo, const float* hi, f
 
 using namespace cgdem;
 
+// One captured part of cgdem_step: the executable graph, the kernels it
+// launches on every replay, and the kernels of a rebuild body it holds.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+  int body_kernels = 0;
+};
+constexpr int GRAPH_HEAD = -1;
+constexpr int GRAPH_TAIL = -2;
+
 struct cgdem_ctx {
   cgdem_config cfg;
   std::vector<cgdem_sample_params> sp;
@@ -45,9 +55,15 @@ struct cgdem_ctx {
   bool any_cube = false;
   bool initialised = false;
   std::string err;
-  // CUDA graphs of steps_per_graph fused steps, keyed by stream
-  std::map<cudaStream_t, cudaGraphExec_t> graphs;
-  bool conditional_graphs = false;
+  // CUDA graphs of cgdem_step, keyed by (stream, part): part > 0 is a block
+  // of that many fused steps, GRAPH_HEAD the opening half kick and drift,
+  // GRAPH_TAIL the closing step
+  std::map<std::pair<cudaStream_t, int>, StepGraph> graphs;
+  bool conditional_graphs = true;
+  // kernels that cgdem_step calls launched unconditionally, and the kernels
+  // of one candidate-list rebuild sequence (run by a conditional graph node)
+  int64_t step_kernels = 0;
+  int rebuild_kernels = 0;
 };
 
 namespace {
@@ -382,20 +398,62 @@ int ready(cgdem_ctx* ctx) {
   return CGDEM_OK;
 }
 
-// One fused step (rebuild-if-flagged, forces, kick, drift, porosity).
-void enqueue_mid_step(cgdem_ctx* ctx, cudaStream_t s) {
-  launch_rebuild(ctx->d, s);
-  launch_forces(ctx->d, 1, ctx->cfg.block_size, s, 0);
-  if (ctx->any_cube) launch_cube_after_mid(ctx->d, s);
+// Kernel nodes of a graph (the bodies of conditional nodes are not counted).
+int count_kernels(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  int k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
 }
 
-// Capture U fused steps into one graph.  Each step's rebuild sequence sits in
-// the body of a conditional (IF) node whose condition the previous step's
-// force kernel sets from the device-side rebuild flag (the first step's, a
-// one-thread kernel at the graph's start), so a step without a rebuild
-// launches one kernel.  Falls back to a plain capture (rebuild
-// kernels that return at once) if conditional nodes are unavailable.
-cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec_t* out) {
+// Append to the capture on cs a conditional (IF) node whose body is the
+// rebuild sequence, captured on bs; its condition is handle h.
+cudaError_t add_rebuild_node(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs,
+                             cudaGraphConditionalHandle h, int* body_kernels) {
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t cg;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  launch_rebuild(ctx->d, bs);
+  e = cudaStreamEndCapture(bs, &body);
+  if (e != cudaSuccess) return e;
+  *body_kernels = count_kernels(body);
+  return cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Capture one part of cgdem_step into a graph:
+//   part = U > 0: U fused steps (rebuild if flagged, forces, kick, drift,
+//     porosity).  Each step's rebuild sequence sits in the body of a
+//     conditional (IF) node whose condition the previous step's force kernel
+//     sets from the device-side rebuild flag (the first step's, a one-thread
+//     kernel at the graph's start), so a step without a rebuild launches one
+//     kernel;
+//   GRAPH_HEAD: the half kick and drift that open a call (state at a full
+//     step -> the first mid-step state);
+//   GRAPH_TAIL: the closing step, which ends on the full-step state (forces,
+//     v(n), w(n)): conditional rebuild, then the force evaluation.
+// Without conditional nodes the rebuild kernels are captured plainly (they
+// return at once unless a rebuild is due).
+cudaError_t capture_part(cgdem_ctx* ctx, int part, bool conditional, StepGraph* out) {
   cudaStream_t cs, bs;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return e;
@@ -405,57 +463,83 @@ cudaError_t capture_steps(cgdem_ctx* ctx, int U, bool conditional, cudaGraphExec
     return e;
   }
   cudaGraph_t g = nullptr;
+  int body_kernels = 0;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  // one handle per step: a one-thread kernel sets the first from the device
-  // flag at every launch of the graph; step i's force kernel sets step i + 1's
-  std::vector<cudaGraphConditionalHandle> hs;
-  if (conditional && e == cudaSuccess) {
-    cudaStreamCaptureStatus stt;
-    cudaGraph_t cg;
-    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, nullptr, nullptr, nullptr);
-    hs.resize(U);
-    for (int i = 0; i < U && e == cudaSuccess; ++i)
-      e = cudaGraphConditionalHandleCreate(&hs[i], cg, i == 0 ? 1u : 0u, i == 0 ? cudaGraphCondAssignDefault : 0u);
-  }
-  for (int i = 0; i < U && e == cudaSuccess; ++i) {
-    if (!conditional) {
-      enqueue_mid_step(ctx, cs);
-      continue;
+  if (part == GRAPH_HEAD) {
+    if (e == cudaSuccess) launch_kick_drift(ctx->d, 1, cs);
+  } else {
+    const int U = part > 0 ? part : 1;
+    const bool tail = part == GRAPH_TAIL;
+    // one handle per step: a one-thread kernel sets the first from the device
+    // flag at every launch of the graph; step i's force kernel sets step i + 1's
+    std::vector<cudaGraphConditionalHandle> hs;
+    if (conditional && e == cudaSuccess) {
+      cudaStreamCaptureStatus stt;
+      cudaGraph_t cg;
+      e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, nullptr, nullptr, nullptr);
+      hs.resize(U);
+      for (int i = 0; i < U && e == cudaSuccess; ++i)
+        e = cudaGraphConditionalHandleCreate(&hs[i], cg, i == 0 ? 1u : 0u,
+                                             i == 0 ? cudaGraphCondAssignDefault : 0u);
     }
-    if (i == 0) launch_rebuild_cond(ctx->d, hs[0], cs);
-    cudaStreamCaptureStatus stt;
-    cudaGraph_t cg;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
-    if (e != cudaSuccess) break;
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hs[i];
-    cp.conditional.type = cudaGraphCondTypeIf;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cn;
-    e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
-    if (e != cudaSuccess) break;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
-    launch_rebuild(ctx->d, bs);
-    e = cudaStreamEndCapture(bs, &body);
-    if (e != cudaSuccess) break;
-    e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e != cudaSuccess) break;
-    launch_forces(ctx->d, 1, ctx->cfg.block_size, cs, i + 1 < U ? hs[i + 1] : 0);
-    if (ctx->any_cube) launch_cube_after_mid(ctx->d, cs);
+    for (int i = 0; i < U && e == cudaSuccess; ++i) {
+      if (conditional) {
+        if (i == 0) launch_rebuild_cond(ctx->d, hs[0], cs);
+        e = add_rebuild_node(ctx, cs, bs, hs[i], &body_kernels);
+        if (e != cudaSuccess) break;
+      } else {
+        launch_rebuild(ctx->d, cs);
+      }
+      if (tail) {
+        launch_forces(ctx->d, 2, ctx->cfg.block_size, cs, 0);
+      } else {
+        launch_forces(ctx->d, 1, ctx->cfg.block_size, cs,
+                      conditional && i + 1 < U ? hs[i + 1] : 0);
+        if (ctx->any_cube) launch_cube_after_mid(ctx->d, cs);
+      }
+    }
   }
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
   if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (e == cudaSuccess) {
+    out->kernels = count_kernels(g);
+    out->body_kernels = body_kernels;
+    e = cudaGraphInstantiate(&out->exec, g, 0);
+  }
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
   cudaStreamDestroy(bs);
   cudaGetLastError();  // a failed attempt must not leave a sticky launch error behind
   return e;
+}
+
+void drop_graphs(cgdem_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+  ctx->graphs.clear();
+}
+
+// Launch part of cgdem_step on s (capturing it on first use for this stream).
+int launch_part(cgdem_ctx* ctx, int part, cudaStream_t s) {
+  const auto key = std::make_pair(s, part);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    StepGraph g;
+    cudaError_t e = cudaErrorUnknown;
+    if (ctx->conditional_graphs) {
+      e = capture_part(ctx, part, true, &g);
+      if (e != cudaSuccess) {  // conditional nodes unavailable: plain captures from now on
+        ctx->conditional_graphs = false;
+        drop_graphs(ctx);
+      }
+    }
+    if (e != cudaSuccess) e = capture_part(ctx, part, false, &g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+    it = ctx->graphs.emplace(key, g).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, s));
+  ctx->step_kernels += it->second.kernels;
+  if (it->second.body_kernels) ctx->rebuild_kernels = it->second.body_kernels;
+  return CGDEM_OK;
 }
 
 }  // namespace
@@ -552,7 +636,7 @@ int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const i
 
 void cgdem_destroy(cgdem_ctx* ctx) {
   if (!ctx) return;
-  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  drop_graphs(ctx);
   delete ctx;
 }
 
@@ -664,36 +748,23 @@ int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {
   if (nsteps == 0 || ctx->d.N == 0) return CGDEM_OK;
   cudaStream_t s = st(stream);
   // half kick + drift from the full-step state, porosity of the new positions
-  launch_kick_drift(ctx->d, 1, s);
+  if ((r = launch_part(ctx, GRAPH_HEAD, s))) return r;
+  // the nsteps - 1 fused steps as graphs of U steps, then of the powers of
+  // two below U (each captured once per stream), so that every call runs
+  // from graphs whatever its length
   int64_t body = nsteps - 1;
   const int U = ctx->cfg.steps_per_graph;
-  if (body >= U && U > 1) {
-    auto it = ctx->graphs.find(s);
-    cudaGraphExec_t exec = nullptr;
-    if (it == ctx->graphs.end()) {
-      cudaError_t e = capture_steps(ctx, U, true, &exec);
-      if (e != cudaSuccess) {
-        ctx->conditional_graphs = false;
-        e = capture_steps(ctx, U, false, &exec);
-      } else {
-        ctx->conditional_graphs = true;
-      }
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
-      ctx->graphs[s] = exec;
-    } else {
-      exec = it->second;
-    }
-    while (body >= U) {
-      CK(cudaGraphLaunch(exec, s));
-      body -= U;
-    }
+  while (body >= U) {
+    if ((r = launch_part(ctx, U, s))) return r;
+    body -= U;
   }
-  for (int64_t i = 0; i < body; ++i) enqueue_mid_step(ctx, s);
+  for (int b = 1 << 30; b >= 1; b >>= 1) {
+    if (b >= U || body < b) continue;
+    if ((r = launch_part(ctx, b, s))) return r;
+    body -= b;
+  }
   // last step ends on the full-step state (forces, v(n), w(n))
-  launch_rebuild(ctx->d, s);
-  launch_forces(ctx->d, 2, ctx->cfg.block_size, s, 0);
-  CK(cudaGetLastError());
-  return CGDEM_OK;
+  return launch_part(ctx, GRAPH_TAIL, s);
 }
 
 int cgdem_set_closure(cgdem_ctx* ctx, const float* theta, const cgdem_closure_params* cp, int enable,
@@ -725,8 +796,7 @@ int cgdem_set_closure(cgdem_ctx* ctx, const float* theta, const cgdem_closure_pa
   // the force launches change shape: captured step graphs are rebuilt
   ctx->d.cl_smem = enable ? 1 : 0;
   CK(cudaStreamSynchronize(s));
-  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-  ctx->graphs.clear();
+  drop_graphs(ctx);
   return CGDEM_OK;
 }
 
@@ -740,8 +810,7 @@ int cgdem_closure_record(cgdem_ctx* ctx, int enable, void* stream) {
   if (ctx->d.cl_rec != (enable ? 1 : 0)) {  // the force kernel variant changes
     ctx->d.cl_rec = enable ? 1 : 0;
     CK(cudaStreamSynchronize(s));
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    drop_graphs(ctx);
   }
   return CGDEM_OK;
 }
@@ -862,6 +931,13 @@ int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_
   if (rebuilds) *rebuilds = c.rebuilds;
   if (max_candidates) *max_candidates = c.max_cand;
   if (total_candidates) *total_candidates = c.cand_total;
+  return CGDEM_OK;
+}
+
+int cgdem_get_launch_counts(cgdem_ctx* ctx, int64_t* step_kernels, int32_t* rebuild_kernels) {
+  if (!ctx) return CGDEM_E_INVALID;
+  if (step_kernels) *step_kernels = ctx->step_kernels;
+  if (rebuild_kernels) *rebuild_kernels = ctx->rebuild_kernels;
   return CGDEM_OK;
 }
 

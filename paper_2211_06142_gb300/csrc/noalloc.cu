@@ -189,7 +189,9 @@ extern "C" int cgdem_touching_pairs_noalloc(const double* x, const double* R, in
       fprintf(stderr, "cgdem_touching_pairs_noalloc: empty box\n");
       return CGDEM_E_INVALID;
     }
-    double nd = floor(g.L[k] / h);
+    // cells a little wider than h: the cell coordinate (x - lo) * inv_h is
+    // rounded, and a pair closer than h must never land two cells apart
+    double nd = floor(g.L[k] / (h * (1.0 + 1e-9)));
     if (!(nd >= 1.0)) nd = 1.0;
     if (nd > (double)NA_MAX_CELLS) nd = (double)NA_MAX_CELLS;
     const int nc = (int)nd;

@@ -275,6 +275,78 @@ def cached(fn, *args, **kw) -> Sample:
     return s
 
 
+def _tile_block(n_block: int, seed: int, phi: float = 0.55):
+    """A periodic block of n_block fine-PSD spheres packed at solid fraction
+    phi: diameters, positions in [0, L)^3 and L.  Copies of a periodic packing
+    placed side by side form a packing of the larger region with no seams
+    (every contact across a block face is a contact across the period)."""
+    rng = np.random.default_rng(seed + 3000)
+    d = fine_diameters(n_block, seed)
+    R = 0.5 * d
+    L = (float((4.0 / 3.0 * math.pi * R ** 3).sum()) / phi) ** (1.0 / 3.0)
+    x = pack_periodic(R, L, rng)
+    return R, x, L
+
+
+def tiled_cylinder(n_target: int = 2_000_000, scale: float = 2.15, seed: int = 4,
+                   n_block: int = 65_536, d50: float = 0.25e-3, U_in: float = 1e-4,
+                   nf=(86, 86, 43)) -> Sample:
+    """The sand-production cylinder scaled by `scale` in radius and height
+    (radius 40 d50 scale, height 30 d50 scale, outlet 3 d50, fluid cells of
+    the 200k-sphere cylinder's size), holding about n_target spheres of the
+    same PSD at solid fraction 0.55: copies of one packed periodic block of
+    n_block spheres tile the region, and the spheres whose centres lie in
+    the bed annulus (r_out + R <= r <= Rc - R, R <= z <= h_bed) are kept.
+    Packing n_target spheres directly takes the host packer tens of minutes;
+    the tiled bed repeats the block's arrangement every block edge."""
+    Rb, xb, Lb = _tile_block(n_block, seed)
+    Vmean = float((4.0 / 3.0 * math.pi * Rb ** 3).mean())
+    Rc = 40.0 * d50 * scale
+    H = 30.0 * d50 * scale
+    r_out = 3.0 * d50
+    h_bed = n_target * Vmean / (0.55 * math.pi * (Rc ** 2 - r_out ** 2))
+    if not h_bed <= H:
+        raise ValueError("the scaled cylinder cannot hold n_target spheres at solid fraction 0.55")
+    nxy = int(math.ceil(2 * Rc / Lb))
+    nz = int(math.ceil(h_bed / Lb))
+    xs, Rs = [], []
+    for a in range(nxy):
+        for b in range(nxy):
+            for c in range(nz):
+                q = xb + np.array([a * Lb - Rc, b * Lb - Rc, c * Lb])
+                r = np.sqrt(q[:, 0] ** 2 + q[:, 1] ** 2)
+                keep = ((r >= r_out + Rb) & (r <= Rc - Rb) & (q[:, 2] >= Rb) & (q[:, 2] <= h_bed))
+                xs.append(q[keep])
+                Rs.append(Rb[keep])
+    x = np.concatenate(xs)
+    R = np.concatenate(Rs)
+    h = (2 * Rc / nf[0], 2 * Rc / nf[1], H / nf[2])
+    grid = FluidGrid(tuple(nf), (-Rc, -Rc, 0.0), h)
+    mat = dict(rho=2650.0, E=1e8, nu=0.3, e=0.5, mu=0.5, gamma=0.5)
+    dom = dict(kind=1, L=(2 * Rc, 2 * Rc, H), Rc=Rc, H=H, r_out=r_out)
+    return Sample(f"cylinder-tiled-{len(R)}", x, np.zeros_like(x), np.zeros_like(x), R, mat, dom,
+                  grid, radial_inflow_field(grid, U_in, Rc, r_out, h_bed),
+                  extra=dict(h_bed=h_bed, block_spheres=n_block, block_edge=Lb))
+
+
+def tiled_periodic(n_block: int = 12_500, reps: int = 2, seed: int = 8, nf: int = 16,
+                   U=(0.0, 0.0, 0.01)) -> Sample:
+    """A periodic cube of reps^3 copies of one packed periodic block of
+    n_block fine-PSD spheres (solid fraction 0.55): a large periodic packing
+    at the cost of packing the block."""
+    Rb, xb, Lb = _tile_block(n_block, seed)
+    xs = [xb + Lb * np.array([a, b, c]) for a in range(reps) for b in range(reps) for c in range(reps)]
+    x = np.concatenate(xs)
+    R = np.tile(Rb, reps ** 3)
+    L = reps * Lb
+    h = L / nf
+    grid = FluidGrid((nf, nf, nf), (0.0, 0.0, 0.0), (h, h, h))
+    mat = dict(rho=2650.0, E=1e8, nu=0.3, e=0.5, mu=0.5, gamma=0.5)
+    dom = dict(kind=0, L=(L, L, L), Rc=0.0, H=0.0, r_out=0.0)
+    return Sample(f"periodic-tiled-{len(R)}", np.mod(x, L), np.zeros_like(x), np.zeros_like(x), R, mat,
+                  dom, grid, uniform_field(grid, U))
+
+
 def small_periodic(n: int = 2000, seed: int = 0) -> Sample:
     """2,000 log-normal spheres (mass-median 0.25 mm, sigma_ln 0.4, 0.1-0.6 mm)
     at solid fraction 0.55 in a periodic cube, 8^3 fluid grid, uniform

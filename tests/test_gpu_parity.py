@@ -132,7 +132,7 @@ def drift_bound(s, sim, n, dt, tau):
 
 @pytest.mark.parametrize("prec", PREC)
 def test_steps_periodic(periodic, prec):
-    """Trajectories over 50 steps.  FP64: within ten times the oracle's own
+    """Trajectories over 100 steps.  FP64: within ten times the oracle's own
     spread when its initial velocities are perturbed at rounding level (1e-15).
     Mixed: within the drift that the 1e-4 per-step force tolerance allows, or
     ten times the oracle's spread under a 1e-7 perturbation, whichever is larger."""
@@ -145,7 +145,7 @@ def test_steps_periodic(periodic, prec):
     ref = run_oracle(perturbed(s, rel), dt)
     L = s.domain["L"][0]
     done = 0
-    for chunk in [1, 9, 40]:
+    for chunk in [1, 9, 40, 50]:
         ctx.step(chunk)
         sim.step(chunk)
         ref.step(chunk)
@@ -213,7 +213,7 @@ def test_sixteen_spheres_per_warp(periodic, cylinder, prec, domain):
     """The force kernel at 16 spheres per warp (record segments of 16
     spheres, lanes 16-31 evaluating entries only) against the oracle, with
     the checks of the 32-per-warp trajectory tests at the same step counts
-    (1, 10 and 50 steps): contacts bit-exact (FP64) or off only at
+    (1, 10, 50 and 100 steps): contacts bit-exact (FP64) or off only at
     thresholds (mixed), forces within the tolerance, same produced sand.
     The mixed trajectory's force error varies along the run (on the periodic
     packing it is 1.5e-4 at step 20 and 1.1e-5 at step 50 at both 16 and 32
@@ -238,7 +238,7 @@ def test_sixteen_spheres_per_warp(periodic, cylinder, prec, domain):
     rel = 1e-15 if prec == cgdem.FP64 else 1e-7
     ref = run_oracle(perturbed(s, rel), dt)
     done = 0
-    for chunk in (1, 9, 40):
+    for chunk in (1, 9, 40, 50):
         ctx.step(chunk)
         c32.step(chunk)
         sim.step(chunk)
