@@ -156,7 +156,7 @@ def kernel_traffic(kernel_file, kernel, knobs):
         if not e or e.get("source_sha1") != h:
             return None
         for c in e.get("configs", []):
-            if "n" in c and int(c["n"]) != int(knobs.get("n", -1)):
+            if int(c.get("n", -1)) != int(knobs.get("n", -2)):
                 continue
             if all(abs(float(c[k]) - float(knobs[k])) < 1e-9 for k in ("cell_scale", "skin_frac", "block", "ppw")):
                 return c

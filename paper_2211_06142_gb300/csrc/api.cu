@@ -248,6 +248,11 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   for (int k = 0; k < 3; ++k) s.g_f[k] = (float)s.g[k];
   s.rho_s_f = (float)s.rho;
   s.k_feat_f = (float)k_cg;
+  {
+    const double cd = 2.0 * std::sqrt(5.0 / 6.0);
+    s.cdbn_f = (float)(cd * s.beta * std::sqrt(2.0 * s.Es));
+    s.cdbt_f = (float)(cd * s.beta * std::sqrt(8.0 * s.Gs));
+  }
   *out = s;
   return CGDEM_OK;
 }
@@ -313,6 +318,7 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     d.roff[b] = cv.take<uint32_t>(Npad);
   }
   d.posq_ref = cv.take<int4>(Npad);
+  if (mixed) d.sched = cv.take<uint32_t>(Npad);
   if (!mixed) {  // pairs listed once
     d.inc = cv.take<uint32_t>((size_t)cap * Npad);
     d.inc_n = cv.take<uint32_t>(Npad);
@@ -366,6 +372,7 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.Cf_total = Cf;
   d.mixed = mixed ? 1 : 0;
   d.ppw = cfg->particles_per_warp == 16 ? 16 : 32;
+  d.rstride = mixed ? d.ppw : 1;
   *bytes = cv.off + 256;
   *dv = d;
   *any_cube = cube;

@@ -71,6 +71,9 @@ struct SampleDev {
   float rebuild_q2;  // rebuild when (max displacement in fixed units)^2 exceeds this
   float c_inv_h_f[3], skin_f;
   float k_feat_f;  // coarse-graining ratio k as a closure input
+  // Eq. 32 and its tangential twin with the contact radius and reduced mass
+  // factored out: gamma_n = cdbn sqrt(a m*), gamma_t = cdbt sqrt(a m*)
+  float cdbn_f, cdbt_f;  // 2 sqrt(5/6) beta sqrt(2 E*), 2 sqrt(5/6) beta sqrt(8 G*)
 };
 
 // Learned closure (not part of the paper): per-particle corrections
@@ -137,7 +140,12 @@ struct Dev {
   // inbox.
   void* rec[2];                   // contact records, one segment of ppw*cap per warp of the force kernel
   uint32_t* cnt[2];               // records of a particle
-  uint32_t* roff[2];              // index of a particle's first record
+  uint32_t* roff[2];              // index of a particle's first record; entry k at roff + k * rstride
+  // Mixed: the force kernel's lanes take the spheres in the order sched
+  // gives (per tile of 1024 spheres in cell order, by decreasing candidate
+  // count); the records of a warp are entry-major (rstride = ppw)
+  uint32_t* sched;                // [Npad] slot -> sphere (UINT_MAX: no sphere)
+  int rstride;                    // 1 (FP64: a sphere's records are consecutive) or ppw (mixed)
   uint32_t* inc;                  // FP64, rebuild scratch [cap][Npad]: lower-index partners
   uint32_t* inc_n;                // FP64: pairs a particle's lower-index partners own
   uint32_t* rslot;                // FP64, per record: slot k of the pair in the partner's inbox

@@ -175,6 +175,86 @@ __device__ __forceinline__ void contact_law(T delta, V3<T> n, V3<T> vrel, V3<T> 
   Fi = v3<T>(-Fn * n.x + Ft.x, -Fn * n.y + Ft.y, -Fn * n.z + Ft.z);
 }
 
+// The contact law of the mixed step in FP32: the terms of contact_law in an
+// order that shares work between them.  Bonded pairs (stable JKR branch,
+// Eq. 12-13) take d_A = a_A^2 / R* = 16^(1/3) (pi^2 gamma^2 R* / E*^2)^(1/3),
+// which the caller has for the bond-break test, and start Newton's method on
+// u^4 - u = delta / d_A from (delta / d_A + 1)^(1/4) (exact at delta = 0,
+// within 4 % on the branch): three steps reach 2e-10 relative.  Unbonded
+// pairs: Hertz with a^2 = R* delta, so 4 E* a^3 / (3 R*) = (4/3) E* a delta.
+// Damping (Eq. 32) and the tangential dashpot share sqrt(a m*); the spring
+// keeps its length through one square root and one reciprocal square root;
+// the Coulomb test (Eq. 35) compares squares and takes the root only when the
+// spring slips.
+__device__ __forceinline__ void contact_law_mixed(float delta, V3<float> n, V3<float> vrel, V3<float> vc,
+                                                  float Rs, float ms, float gamma, bool bonded, float dA,
+                                                  const SampleDev& S, V3<float>& xi, V3<float>& Fi,
+                                                  V3<float>& Ft) {
+  float a, Fne;
+  if (bonded && gamma > 0.f) {
+    const float D = __fdividef(delta, dA);
+    float u = m_sqrt(m_sqrt(D + 1.f));
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const float u3 = u * u * u;
+      u -= __fdividef(u3 * u - u - D, 4.f * u3 - 1.f);
+    }
+    const float uC = 0.90856029641606983f;  // (3/4)^(1/3)
+    if (u < uC) u = uC;
+    const float u3 = u * u * u;
+    a = u * u * m_sqrt(dA * Rs);
+    Fne = PI_F * gamma * Rs * (16.f / 3.f * u3 * u3 - 8.f * u3);
+  } else {
+    a = delta > 0.f ? m_sqrt(Rs * delta) : 0.f;
+    Fne = (4.f / 3.f) * S.Es_f * a * delta;
+  }
+  const float sq = m_sqrt(a * ms);
+  const float vn = dot3(vrel, n);
+  const float Fn = Fne - S.cdbn_f * sq * vn;  // Eq. 32
+  // tangential spring rotated into the tangent plane, Eq. 4
+  const float vcn = dot3(vc, n);
+  const V3<float> vt = v3<float>(vc.x - vcn * n.x, vc.y - vcn * n.y, vc.z - vcn * n.z);
+  const float old2 = dot3(xi, xi);
+  const float xn = dot3(xi, n);
+  xi.x -= xn * n.x;
+  xi.y -= xn * n.y;
+  xi.z -= xn * n.z;
+  const float nw2 = dot3(xi, xi);
+  if (nw2 > 0.f) {
+    const float sc = m_sqrt(old2) * rsqrtf(nw2);
+    xi.x *= sc;
+    xi.y *= sc;
+    xi.z *= sc;
+  } else {
+    xi = v3<float>(0, 0, 0);
+  }
+  const float dt = S.dt_f;
+  xi.x += vt.x * dt;
+  xi.y += vt.y * dt;
+  xi.z += vt.z * dt;
+  const float kt = 8.f * S.Gs_f * a;
+  const float gt = S.cdbt_f * sq;
+  Ft = v3<float>(kt * xi.x + gt * vt.x, kt * xi.y + gt * vt.y, kt * xi.z + gt * vt.z);
+  const float FC = 3.f * PI_F * gamma * Rs;  // Table 1
+  float Flim = S.coulomb_mode == 1 ? fabsf(Fne) : (bonded ? Fne + 2.f * FC : Fne);
+  if (Flim < 0.f) Flim = 0.f;
+  const float cap = S.mu_f32 * Flim;  // Eq. 35
+  const float ft2 = dot3(Ft, Ft);
+  if (ft2 > cap * cap) {
+    const float sc = cap * rsqrtf(ft2);
+    Ft.x *= sc;
+    Ft.y *= sc;
+    Ft.z *= sc;
+    if (kt > 0.f) {
+      const float ik = __fdividef(1.f, kt);
+      xi.x = (Ft.x - gt * vt.x) * ik;
+      xi.y = (Ft.y - gt * vt.y) * ik;
+      xi.z = (Ft.z - gt * vt.z) * ik;
+    }
+  }
+  Fi = v3<float>(-Fn * n.x + Ft.x, -Fn * n.y + Ft.y, -Fn * n.z + Ft.z);
+}
+
 // Di Felice drag (Eq. 8-11) written as (pi d^2 / 8) (0.63 sqrt(rho_f |w|)
 // + 4.8 sqrt(mu_f / d))^2 w n^-chi, which equals Eq. 8 with Eq. 9 and stays
 // finite as Re -> 0.
@@ -406,6 +486,374 @@ template <>
 struct Owner<false> {
   double4 P, V, W;  // x,R | v,1/m | w,1/I
 };
+
+// The per-sphere end of a step, shared by both force kernels: walls,
+// gravity, buoyancy, drag, velocity Verlet, fixed-point shadows, porosity
+// scatter, closure network, and the step's bookkeeping (displacement since
+// the rebuild, porosity rotation, step counter, next rebuild condition).
+// valid: this thread owns sphere p (of sample si) and ends its step; F, Tq
+// and the closure sums hold its contact forces.
+template <bool MIXED, int MODE, bool CL>
+__device__ __forceinline__ void finish_step(
+    const Dev& d, Ctl* ctl, int cur, int nxt, int pc, int vfc, long long m_step, bool couple_next,
+    uint32_t epoch, int lane, bool valid, int p, int si, const Owner<MIXED>& me,
+    V3<typename std::conditional<MIXED, float, double>::type> F,
+    V3<typename std::conditional<MIXED, float, double>::type> Tq,
+    typename std::conditional<MIXED, float, double>::type Zacc,
+    typename std::conditional<MIXED, float, double>::type Dacc,
+    typename std::conditional<MIXED, float, double>::type Cacc, float2 my_c, bool use_c, bool feat,
+    bool rec, bool net, uint8_t* cl_sm, uint64_t* cl_bar, uint32_t cl_tmem, unsigned* bk_n, int* bk_s,
+    float* bk_m, unsigned* bk_c, cudaGraphConditionalHandle h_next) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  // ---- per-particle epilogue: walls, body forces, drag, integration ----
+  float my_disp2 = -1.f;
+  bool coupled = false;
+  float ft[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // closure inputs of this particle
+  bool net_row = false;
+  if (rec && valid) {  // inactive particles record zeros
+    float4* r4 = reinterpret_cast<float4*>(d.clrec + (size_t)p * CL_COLS);
+    r4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (valid) {
+    const SampleDev& S = d.sp[si];
+    double4 P;
+    if constexpr (MIXED) P = d.pos[cur][p];
+    else P = me.P;
+    const int fc0 = d.fcell[pc][p];
+    if (S.use_drag) {
+      prefetch_l1(&d.vf[vfc][fc0]);
+      prefetch_l1(MIXED ? (const void*)&d.Usf[fc0] : (const void*)&d.Us[fc0]);
+    }
+    const bool active = P.w > 0.0;
+    if (!active) {
+      if (MODE != MODE_FORCES) {
+        d.pos[nxt][p] = P;
+        d.vel[nxt][p] = d.vel[cur][p];
+        d.omg[nxt][p] = d.omg[cur][p];
+        d.posq[nxt][p] = d.posq[cur][p];
+        d.velf[nxt][p] = d.velf[cur][p];
+        d.omgf[nxt][p] = d.omgf[cur][p];
+      }
+      if (MODE != MODE_MID) {
+        d.F[p] = make_double4(0, 0, 0, 0);
+        d.T[p] = make_double4(0, 0, 0, 0);
+      }
+    } else {
+      double4 Vd, Wd;
+      T Ri, mi;
+      V3<T> vi, wi;
+      if constexpr (MIXED) {
+        Vd = d.vel[cur][p];
+        Wd = d.omg[cur][p];
+        vi = v3<T>(me.va.x, me.va.y, me.va.z);
+        wi = v3<T>(me.wa.x, me.wa.y, me.wa.z);
+        Ri = me.va.w;
+        mi = me.wa.w;
+      } else {
+        Vd = me.V;
+        Wd = me.W;
+        vi = v3<T>(Vd.x, Vd.y, Vd.z);
+        wi = v3<T>(Wd.x, Wd.y, Wd.z);
+        Ri = P.w;
+        mi = 1.0 / Vd.w;
+      }
+      const float xf = d2f_bits(P.x), yf = d2f_bits(P.y), zf = d2f_bits(P.z);
+      T Es, Gs, beta, mu, dt;
+      if constexpr (MIXED) {
+        Es = S.Es_f; Gs = S.Gs_f; beta = S.beta_f; mu = S.mu_f32; dt = S.dt_f;
+      } else {
+        Es = S.Es; Gs = S.Gs; beta = S.beta; mu = S.mu; dt = S.dt;
+      }
+      if (S.kind == CGDEM_CYLINDER) {
+        if constexpr (MIXED)
+          wall_contacts<T, float4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+                                   d.wallhf[pc] + p, (size_t)d.Npad, F, Tq);
+        else
+          wall_contacts<T, double4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+                                    d.wallh[pc] + p, (size_t)d.Npad, F, Tq);
+      }
+      // gravity, buoyancy (Eq. 1) and drag (Eq. 8-11)
+      {
+        T rho_s, rf, g0, g1, g2, nmin, muf;
+        if constexpr (MIXED) {
+          rho_s = S.rho_s_f; rf = S.rho_f32; g0 = S.g_f[0]; g1 = S.g_f[1]; g2 = S.g_f[2];
+          nmin = S.n_min_f; muf = S.muf_f32;
+        } else {
+          rho_s = S.rho; rf = S.rho_f; g0 = S.g[0]; g1 = S.g[1]; g2 = S.g[2];
+          nmin = S.n_min; muf = S.mu_f;
+        }
+        const T Vp = mi / rho_s;
+        F.x += mi * g0;
+        F.y += mi * g1;
+        F.z += mi * g2;
+        if (S.use_buoyancy) {
+          F.x -= rf * Vp * g0;
+          F.y -= rf * Vp * g1;
+          F.z -= rf * Vp * g2;
+        }
+        if (S.use_drag || feat) {
+          const int fc = fc0;
+          const unsigned long long Sc = d.vf[vfc][fc];
+          T scount;
+          if constexpr (MIXED) scount = u64_to_f(Sc);
+          else scount = (double)Sc;
+          T nc = T(1) - scount * T(9.094947017729282379150390625e-13);  // 2^-40
+          if (nc < nmin) nc = nmin;
+          if (nc > T(1)) nc = T(1);
+          V3<T> U;
+          if constexpr (MIXED) {
+            const float4 u = d.Usf[fc];
+            U = v3<T>(u.x, u.y, u.z);
+          } else {
+            const double4 u = d.Us[fc];
+            U = v3<T>(u.x, u.y, u.z);
+          }
+          const V3<T> w = v3<T>(U.x / nc - vi.x, U.y / nc - vi.y, U.z / nc - vi.z);
+          V3<T> fd = v3<T>(0, 0, 0);
+          if (S.use_drag) {
+            fd = drag_force<T>(rf, muf, T(2) * Ri, w, nc);
+            if (use_c) {  // drag correction of the closure
+              fd.x *= (T)my_c.x;
+              fd.y *= (T)my_c.x;
+              fd.z *= (T)my_c.x;
+            }
+            F.x += fd.x;
+            F.y += fd.y;
+            F.z += fd.z;
+          }
+          if (feat) {
+            net_row = true;
+            ft[0] = (float)(T(1) - nc);
+            ft[1] = (float)m_sqrt(dot3(w, w));
+            ft[2] = S.k_feat_f;
+            ft[3] = (float)Zacc;
+            ft[4] = Zacc > T(0) ? (float)(Dacc / (Zacc * T(2) * Ri)) : 0.f;
+            if (rec) {
+              float4* r4 = reinterpret_cast<float4*>(d.clrec + (size_t)p * CL_COLS);
+              r4[0] = make_float4(ft[0], ft[1], ft[2], ft[3]);
+              r4[1] = make_float4(ft[4], (float)fd.x, (float)fd.y, (float)fd.z);
+              r4[2] = make_float4((float)Cacc, (float)(fc - S.fcell_off), my_c.x, my_c.y);
+            }
+          }
+        }
+      }
+      if (!isfinite(F.x + F.y + F.z + Tq.x + Tq.y + Tq.z)) latch(ctl, ST_NONFINITE);
+
+      if (MODE == MODE_FORCES) {
+        d.F[p] = make_double4((double)F.x, (double)F.y, (double)F.z, 0.0);
+        d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
+      } else {
+        // outlet (produced sand, Eq. 40): float filter, FP64 decision
+        const bool removed = S.kind == CGDEM_CYLINDER && zf < -1.999f * d2f_bits(P.w) &&
+                             P.z < -2.0 * P.w;
+        if (removed) d.removed_step[d.id[pc][p]] = (int)m_step;
+        double vx, vy, vz, wx, wy, wz;
+        if constexpr (MIXED) {
+          // FP32 force increments added to the FP64 state
+          const float im = 1.0f / me.wa.w;
+          const float iI = d2f_bits(Wd.w);
+          const float c = (MODE == MODE_MID ? S.dt_f : 0.5f * S.dt_f);
+          vx = Vd.x + f2d_bits(c * im * (float)F.x);
+          vy = Vd.y + f2d_bits(c * im * (float)F.y);
+          vz = Vd.z + f2d_bits(c * im * (float)F.z);
+          wx = Wd.x + f2d_bits(c * iI * (float)Tq.x);
+          wy = Wd.y + f2d_bits(c * iI * (float)Tq.y);
+          wz = Wd.z + f2d_bits(c * iI * (float)Tq.z);
+        } else {
+          const double h = S.half_dt, im = Vd.w, iI = Wd.w;
+          vx = Vd.x + h * (F.x * im);
+          vy = Vd.y + h * (F.y * im);
+          vz = Vd.z + h * (F.z * im);
+          wx = Wd.x + h * (Tq.x * iI);
+          wy = Wd.y + h * (Tq.y * iI);
+          wz = Wd.z + h * (Tq.z * iI);
+          if (MODE == MODE_MID) {
+            vx += h * (F.x * im);
+            vy += h * (F.y * im);
+            vz += h * (F.z * im);
+            wx += h * (Tq.x * iI);
+            wy += h * (Tq.y * iI);
+            wz += h * (Tq.z * iI);
+          }
+        }
+        if (MODE == MODE_CANON) {
+          d.F[p] = make_double4((double)F.x, (double)F.y, (double)F.z, 0.0);
+          d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
+          double4 Pn = P;
+          int4 pqn = d.posq[cur][p];
+          if (removed) {
+            Pn.w = -P.w;
+            pqn.w = 0;
+          }
+          d.pos[nxt][p] = Pn;
+          d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
+          d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
+          d.posq[nxt][p] = pqn;
+          const float4 va = d.velf[cur][p], wa = d.omgf[cur][p];
+          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), va.w);
+          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), wa.w);
+        } else if (removed) {
+          double4 Pn = P;
+          Pn.w = -P.w;
+          d.pos[nxt][p] = Pn;
+          d.vel[nxt][p] = Vd;
+          d.omg[nxt][p] = Wd;
+          int4 pqn = d.posq[cur][p];
+          pqn.w = 0;
+          d.posq[nxt][p] = pqn;
+          d.velf[nxt][p] = d.velf[cur][p];
+          d.omgf[nxt][p] = d.omgf[cur][p];
+        } else {
+          double x = P.x + S.dt * vx, y = P.y + S.dt * vy, z = P.z + S.dt * vz;
+          float nxf = d2f_bits(x), nyf = d2f_bits(y), nzf = d2f_bits(z);
+          if (S.kind == CGDEM_PERIODIC_BOX) {
+            const float Lf = S.L_f[0], eps = 1e-4f * Lf;
+            if (nxf < eps || nxf > Lf - eps) {
+              if (x >= S.L[0]) x -= S.L[0]; else if (x < 0.0) x += S.L[0];
+              nxf = d2f_bits(x);
+            }
+            if (nyf < eps || nyf > Lf - eps) {
+              if (y >= S.L[1]) y -= S.L[1]; else if (y < 0.0) y += S.L[1];
+              nyf = d2f_bits(y);
+            }
+            if (nzf < eps || nzf > Lf - eps) {
+              if (z >= S.L[2]) z -= S.L[2]; else if (z < 0.0) z += S.L[2];
+              nzf = d2f_bits(z);
+            }
+          }
+          d.pos[nxt][p] = make_double4(x, y, z, P.w);
+          d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
+          d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
+          int4 pqn;
+          if (S.q_exp != 0x7fffffff) {
+            pqn.x = to_q_pow2(x, S.q_exp);
+            pqn.y = to_q_pow2(y, S.q_exp);
+            pqn.z = to_q_pow2(z, S.q_exp);
+          } else {
+            pqn.x = to_q(x, S.inv_dq);
+            pqn.y = to_q(y, S.inv_dq);
+            pqn.z = to_q(z, S.inv_dq);
+          }
+          float Rf, mf;
+          if constexpr (MIXED) {
+            pqn.w = me.pq.w;
+            Rf = me.va.w;
+            mf = me.wa.w;
+          } else {
+            pqn.w = d.posq[cur][p].w;
+            Rf = d.velf[cur][p].w;
+            mf = d.omgf[cur][p].w;
+          }
+          d.posq[nxt][p] = pqn;
+          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), Rf);
+          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), mf);
+          const int4 ref = d.posq_ref[p];
+          const float ex = (float)(int)((uint32_t)pqn.x - (uint32_t)ref.x);
+          const float ey = (float)(int)((uint32_t)pqn.y - (uint32_t)ref.y);
+          const float ez = (float)(int)((uint32_t)pqn.z - (uint32_t)ref.z);
+          my_disp2 = ex * ex + ey * ey + ez * ez;
+          const int fc = fluid_cell_fast(S, x, y, z, nxf, nyf, nzf);
+          d.fcell[pc][p] = fc;
+          if (couple_next) {
+            coupled = true;
+            if (S.vf_mode == 0) atomicAdd(&d.vf[(vfc + 1) % 3][fc], d.vq[pc][p]);
+          }
+        }
+      }
+    }
+  }
+
+  // ---- learned closure: corrections for the next evaluation ----
+  if (net) {
+    float o0 = 0.f, o1 = 0.f;
+    const bool ok = closure_infer(ft, cl_sm, cl_bar, cl_tmem, o0, o1);
+    if (valid) {
+      float2 c = make_float2(1.0f, 1.0f);  // plain coarse-graining outside the training range
+      if (ok && net_row) {
+        const float* P = reinterpret_cast<const float*>(cl_sm + CL_TILES);
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) inside = inside && ft[k] >= P[CL_P_LO + k] && ft[k] <= P[CL_P_HI + k];
+        if (inside) {
+          const float cdm = P[CL_P_CMAX], cgm = P[CL_P_CMAX + 1];
+          c.x = expf(fminf(fmaxf(o0, -cdm), cdm));
+          c.y = expf(fminf(fmaxf(o1, -cgm), cgm));
+        }
+      }
+      d.clc[nxt][p] = c;
+    }
+    if (!ok && threadIdx.x == 0) latch(ctl, ST_TIMEOUT);
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc05::tmem_dealloc(cl_tmem, 64);
+  }
+
+  // ---- bookkeeping: displacement since rebuild, porosity rotation, step ----
+  const int wib = threadIdx.x >> 5;
+  if (MODE == MODE_MID) {
+    unsigned long long* z = d.vf[(vfc + 2) % 3];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.Cf_total; c += gridDim.x * blockDim.x)
+      z[c] = 0ull;
+    const int s0 = __shfl_sync(FULL, si, 0);
+    const bool uniform = __all_sync(FULL, !valid || si == s0);
+    float md = my_disp2;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
+    // one fence and one arrival per block, without a block barrier: each
+    // warp leaves its maximum in shared memory, and the block's last warp
+    // publishes them (a warp that straddles samples publishes per lane and
+    // fences)
+    const unsigned wcoupled = __any_sync(FULL, coupled) ? 1u : 0u;
+    if (!uniform) {
+      if (my_disp2 >= 0.f) atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
+      __threadfence();
+    }
+    if (lane == 0) {
+      bk_s[wib] = s0;
+      bk_m[wib] = uniform ? md : -1.f;
+      bk_c[wib] = wcoupled;
+    }
+  }
+  if (lane != 0) return;
+  __threadfence_block();
+  const unsigned nw = blockDim.x >> 5;
+  if (atomicAdd(bk_n, 1u) != nw - 1u) return;
+  __threadfence_block();
+  {
+    if (MODE == MODE_MID) {
+      unsigned any = 0u;
+      for (unsigned w = 0; w < nw; ++w) {
+        const float mw = *((volatile float*)&bk_m[w]);
+        if (mw >= 0.f) atomicMax(&d.dmax2[*((volatile int*)&bk_s[w])], __float_as_uint(mw));
+        any |= *((volatile unsigned*)&bk_c[w]);
+      }
+      if (any) atomicOr(&ctl->coupled, 1u);
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->block_counter, 1u);
+    if (t == gridDim.x - 1) {
+      // every block has started and finished: the segment order and the
+      // flags' epoch move on for the next launch
+      __threadfence();
+      if (MODE == MODE_MID) {
+        for (int s = 0; s < d.n_samples; ++s) {
+          const unsigned b = atomicAdd(&d.dmax2[s], 0u);
+          if (__uint_as_float(b) > d.sp[s].rebuild_q2) ctl->rebuild = 1;
+        }
+        if (atomicExch(&ctl->coupled, 0u)) ctl->vf_cur = (vfc + 1) % 3;
+        ctl->cur = nxt;
+        ctl->step = m_step;
+      }
+      ctl->epoch = epoch;
+      ctl->blk_next = 0;
+      ctl->block_counter = 0u;
+      __threadfence();
+      if (MODE == MODE_MID && h_next) cudaGraphSetConditional(h_next, ctl->rebuild ? 1u : 0u);
+    }
+  }
+}
 
 // CL: the context carries the learned closure (blocks of 128 threads; more
 // registers per thread for the closure data and the network epilogue).
@@ -928,355 +1376,281 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     }
   }
 
-  // ---- per-particle epilogue: walls, body forces, drag, integration ----
-  float my_disp2 = -1.f;
-  bool coupled = false;
-  float ft[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // closure inputs of this particle
-  bool net_row = false;
-  if (rec && valid) {  // inactive particles record zeros
-    float4* r4 = reinterpret_cast<float4*>(d.clrec + (size_t)p * CL_COLS);
-    r4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  if (valid) {
-    const SampleDev& S = d.sp[si];
-    double4 P;
-    if constexpr (MIXED) P = d.pos[cur][p];
-    else P = me.P;
-    const int fc0 = d.fcell[pc][p];
-    if (S.use_drag) {
-      prefetch_l1(&d.vf[vfc][fc0]);
-      prefetch_l1(MIXED ? (const void*)&d.Usf[fc0] : (const void*)&d.Us[fc0]);
-    }
-    const bool active = P.w > 0.0;
-    if (!active) {
-      if (MODE != MODE_FORCES) {
-        d.pos[nxt][p] = P;
-        d.vel[nxt][p] = d.vel[cur][p];
-        d.omg[nxt][p] = d.omg[cur][p];
-        d.posq[nxt][p] = d.posq[cur][p];
-        d.velf[nxt][p] = d.velf[cur][p];
-        d.omgf[nxt][p] = d.omgf[cur][p];
-      }
-      if (MODE != MODE_MID) {
-        d.F[p] = make_double4(0, 0, 0, 0);
-        d.T[p] = make_double4(0, 0, 0, 0);
-      }
-    } else {
-      double4 Vd, Wd;
-      T Ri, mi;
-      V3<T> vi, wi;
-      if constexpr (MIXED) {
-        Vd = d.vel[cur][p];
-        Wd = d.omg[cur][p];
-        vi = v3<T>(me.va.x, me.va.y, me.va.z);
-        wi = v3<T>(me.wa.x, me.wa.y, me.wa.z);
-        Ri = me.va.w;
-        mi = me.wa.w;
-      } else {
-        Vd = me.V;
-        Wd = me.W;
-        vi = v3<T>(Vd.x, Vd.y, Vd.z);
-        wi = v3<T>(Wd.x, Wd.y, Wd.z);
-        Ri = P.w;
-        mi = 1.0 / Vd.w;
-      }
-      const float xf = d2f_bits(P.x), yf = d2f_bits(P.y), zf = d2f_bits(P.z);
-      T Es, Gs, beta, mu, dt;
-      if constexpr (MIXED) {
-        Es = S.Es_f; Gs = S.Gs_f; beta = S.beta_f; mu = S.mu_f32; dt = S.dt_f;
-      } else {
-        Es = S.Es; Gs = S.Gs; beta = S.beta; mu = S.mu; dt = S.dt;
-      }
-      if (S.kind == CGDEM_CYLINDER) {
-        if constexpr (MIXED)
-          wall_contacts<T, float4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
-                                   d.wallhf[pc] + p, (size_t)d.Npad, F, Tq);
-        else
-          wall_contacts<T, double4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
-                                    d.wallh[pc] + p, (size_t)d.Npad, F, Tq);
-      }
-      // gravity, buoyancy (Eq. 1) and drag (Eq. 8-11)
-      {
-        T rho_s, rf, g0, g1, g2, nmin, muf;
-        if constexpr (MIXED) {
-          rho_s = S.rho_s_f; rf = S.rho_f32; g0 = S.g_f[0]; g1 = S.g_f[1]; g2 = S.g_f[2];
-          nmin = S.n_min_f; muf = S.muf_f32;
-        } else {
-          rho_s = S.rho; rf = S.rho_f; g0 = S.g[0]; g1 = S.g[1]; g2 = S.g[2];
-          nmin = S.n_min; muf = S.mu_f;
-        }
-        const T Vp = mi / rho_s;
-        F.x += mi * g0;
-        F.y += mi * g1;
-        F.z += mi * g2;
-        if (S.use_buoyancy) {
-          F.x -= rf * Vp * g0;
-          F.y -= rf * Vp * g1;
-          F.z -= rf * Vp * g2;
-        }
-        if (S.use_drag || feat) {
-          const int fc = fc0;
-          const unsigned long long Sc = d.vf[vfc][fc];
-          T scount;
-          if constexpr (MIXED) scount = u64_to_f(Sc);
-          else scount = (double)Sc;
-          T nc = T(1) - scount * T(9.094947017729282379150390625e-13);  // 2^-40
-          if (nc < nmin) nc = nmin;
-          if (nc > T(1)) nc = T(1);
-          V3<T> U;
-          if constexpr (MIXED) {
-            const float4 u = d.Usf[fc];
-            U = v3<T>(u.x, u.y, u.z);
-          } else {
-            const double4 u = d.Us[fc];
-            U = v3<T>(u.x, u.y, u.z);
-          }
-          const V3<T> w = v3<T>(U.x / nc - vi.x, U.y / nc - vi.y, U.z / nc - vi.z);
-          V3<T> fd = v3<T>(0, 0, 0);
-          if (S.use_drag) {
-            fd = drag_force<T>(rf, muf, T(2) * Ri, w, nc);
-            if (use_c) {  // drag correction of the closure
-              fd.x *= (T)my_c.x;
-              fd.y *= (T)my_c.x;
-              fd.z *= (T)my_c.x;
-            }
-            F.x += fd.x;
-            F.y += fd.y;
-            F.z += fd.z;
-          }
-          if (feat) {
-            net_row = true;
-            ft[0] = (float)(T(1) - nc);
-            ft[1] = (float)m_sqrt(dot3(w, w));
-            ft[2] = S.k_feat_f;
-            ft[3] = (float)Zacc;
-            ft[4] = Zacc > T(0) ? (float)(Dacc / (Zacc * T(2) * Ri)) : 0.f;
-            if (rec) {
-              float4* r4 = reinterpret_cast<float4*>(d.clrec + (size_t)p * CL_COLS);
-              r4[0] = make_float4(ft[0], ft[1], ft[2], ft[3]);
-              r4[1] = make_float4(ft[4], (float)fd.x, (float)fd.y, (float)fd.z);
-              r4[2] = make_float4((float)Cacc, (float)(fc - S.fcell_off), my_c.x, my_c.y);
-            }
-          }
-        }
-      }
-      if (!isfinite(F.x + F.y + F.z + Tq.x + Tq.y + Tq.z)) latch(ctl, ST_NONFINITE);
+  finish_step<MIXED, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
+                               F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
+                               &bk_n, bk_s, bk_m, bk_c, h_next);
+}
 
-      if (MODE == MODE_FORCES) {
-        d.F[p] = make_double4((double)F.x, (double)F.y, (double)F.z, 0.0);
-        d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
-      } else {
-        // outlet (produced sand, Eq. 40): float filter, FP64 decision
-        const bool removed = S.kind == CGDEM_CYLINDER && zf < -1.999f * d2f_bits(P.w) &&
-                             P.z < -2.0 * P.w;
-        if (removed) d.removed_step[d.id[pc][p]] = (int)m_step;
-        double vx, vy, vz, wx, wy, wz;
-        if constexpr (MIXED) {
-          // FP32 force increments added to the FP64 state
-          const float im = 1.0f / me.wa.w;
-          const float iI = d2f_bits(Wd.w);
-          const float c = (MODE == MODE_MID ? S.dt_f : 0.5f * S.dt_f);
-          vx = Vd.x + f2d_bits(c * im * (float)F.x);
-          vy = Vd.y + f2d_bits(c * im * (float)F.y);
-          vz = Vd.z + f2d_bits(c * im * (float)F.z);
-          wx = Wd.x + f2d_bits(c * iI * (float)Tq.x);
-          wy = Wd.y + f2d_bits(c * iI * (float)Tq.y);
-          wz = Wd.z + f2d_bits(c * iI * (float)Tq.z);
-        } else {
-          const double h = S.half_dt, im = Vd.w, iI = Wd.w;
-          vx = Vd.x + h * (F.x * im);
-          vy = Vd.y + h * (F.y * im);
-          vz = Vd.z + h * (F.z * im);
-          wx = Wd.x + h * (Tq.x * iI);
-          wy = Wd.y + h * (Tq.y * iI);
-          wz = Wd.z + h * (Tq.z * iI);
-          if (MODE == MODE_MID) {
-            vx += h * (F.x * im);
-            vy += h * (F.y * im);
-            vz += h * (F.z * im);
-            wx += h * (Tq.x * iI);
-            wy += h * (Tq.y * iI);
-            wz += h * (Tq.z * iI);
-          }
-        }
-        if (MODE == MODE_CANON) {
-          d.F[p] = make_double4((double)F.x, (double)F.y, (double)F.z, 0.0);
-          d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
-          double4 Pn = P;
-          int4 pqn = d.posq[cur][p];
-          if (removed) {
-            Pn.w = -P.w;
-            pqn.w = 0;
-          }
-          d.pos[nxt][p] = Pn;
-          d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
-          d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
-          d.posq[nxt][p] = pqn;
-          const float4 va = d.velf[cur][p], wa = d.omgf[cur][p];
-          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), va.w);
-          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), wa.w);
-        } else if (removed) {
-          double4 Pn = P;
-          Pn.w = -P.w;
-          d.pos[nxt][p] = Pn;
-          d.vel[nxt][p] = Vd;
-          d.omg[nxt][p] = Wd;
-          int4 pqn = d.posq[cur][p];
-          pqn.w = 0;
-          d.posq[nxt][p] = pqn;
-          d.velf[nxt][p] = d.velf[cur][p];
-          d.omgf[nxt][p] = d.omgf[cur][p];
-        } else {
-          double x = P.x + S.dt * vx, y = P.y + S.dt * vy, z = P.z + S.dt * vz;
-          float nxf = d2f_bits(x), nyf = d2f_bits(y), nzf = d2f_bits(z);
-          if (S.kind == CGDEM_PERIODIC_BOX) {
-            const float Lf = S.L_f[0], eps = 1e-4f * Lf;
-            if (nxf < eps || nxf > Lf - eps) {
-              if (x >= S.L[0]) x -= S.L[0]; else if (x < 0.0) x += S.L[0];
-              nxf = d2f_bits(x);
-            }
-            if (nyf < eps || nyf > Lf - eps) {
-              if (y >= S.L[1]) y -= S.L[1]; else if (y < 0.0) y += S.L[1];
-              nyf = d2f_bits(y);
-            }
-            if (nzf < eps || nzf > Lf - eps) {
-              if (z >= S.L[2]) z -= S.L[2]; else if (z < 0.0) z += S.L[2];
-              nzf = d2f_bits(z);
-            }
-          }
-          d.pos[nxt][p] = make_double4(x, y, z, P.w);
-          d.vel[nxt][p] = make_double4(vx, vy, vz, Vd.w);
-          d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
-          int4 pqn;
-          if (S.q_exp != 0x7fffffff) {
-            pqn.x = to_q_pow2(x, S.q_exp);
-            pqn.y = to_q_pow2(y, S.q_exp);
-            pqn.z = to_q_pow2(z, S.q_exp);
-          } else {
-            pqn.x = to_q(x, S.inv_dq);
-            pqn.y = to_q(y, S.inv_dq);
-            pqn.z = to_q(z, S.inv_dq);
-          }
-          float Rf, mf;
-          if constexpr (MIXED) {
-            pqn.w = me.pq.w;
-            Rf = me.va.w;
-            mf = me.wa.w;
-          } else {
-            pqn.w = d.posq[cur][p].w;
-            Rf = d.velf[cur][p].w;
-            mf = d.omgf[cur][p].w;
-          }
-          d.posq[nxt][p] = pqn;
-          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), Rf);
-          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), mf);
-          const int4 ref = d.posq_ref[p];
-          const float ex = (float)(int)((uint32_t)pqn.x - (uint32_t)ref.x);
-          const float ey = (float)(int)((uint32_t)pqn.y - (uint32_t)ref.y);
-          const float ez = (float)(int)((uint32_t)pqn.z - (uint32_t)ref.z);
-          my_disp2 = ex * ex + ey * ey + ez * ez;
-          const int fc = fluid_cell_fast(S, x, y, z, nxf, nyf, nzf);
-          d.fcell[pc][p] = fc;
-          if (couple_next) {
-            coupled = true;
-            if (S.vf_mode == 0) atomicAdd(&d.vf[(vfc + 1) % 3][fc], d.vq[pc][p]);
-          }
-        }
-      }
-    }
-  }
+// Mixed precision: one lane per sphere (ppw = 32), or two lanes per sphere
+// taking alternate entries of its list (ppw = 16, for samples too small to
+// fill the GPU).  The rebuild orders the spheres of each tile of 1024
+// consecutive spheres in cell order by candidate count and stores them in
+// that order (the schedule order), so the spheres of a warp have lists of
+// about the same length and are read and written in consecutive lines; a
+// warp's records are stored entry-major (entry k of its lanes' spheres side
+// by side), so every iteration of the loop below reads one contiguous line
+// of records.  Each lane sums its own
+// sphere's pairs in list order: no search for the owner of an entry, no
+// broadcast of its data and no segmented scan, and the sums stay
+// deterministic.
+template <int MODE, bool CL>
+__global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
+    k_forces_lanes(Dev d, cudaGraphConditionalHandle h_next) {
+  Ctl* ctl = d.ctl;
+  const int cur = ctl->cur;
+  const int nxt = cur ^ 1;
+  const int pc = ctl->pcur;
+  const int rc = ctl->rec_cur;
+  const int vfc = ctl->vf_cur;
+  const long long m_step = ctl->step + 1;  // step completed by this evaluation
+  const int ce = d.sp[0].couple_every;
+  const bool couple_next = ce == 1 || (unsigned)(m_step % ce) == 0u;
+  const int lane = threadIdx.x & 31;
+  const uint32_t epoch = ctl->epoch + 1u;
+  __shared__ unsigned bk_n;
+  if (threadIdx.x == 0) bk_n = 0u;
+  __syncthreads();
+  const int P = d.ppw;                  // spheres per warp
+  const int Lp = 32 / P;                // lanes per sphere (1 or 2)
+  const int sub = lane & (P - 1);       // the warp's sphere this lane works on
+  const int half = lane / P;            // which of its entries: half, half + Lp, ...
+  const int gw = (blockIdx.x * (int)blockDim.x + (int)threadIdx.x) >> 5;
+  const int slot = gw * P + sub;        // the grid covers Npad slots exactly
+  const bool has = slot < d.N;
+  const int p = has ? slot : 0;
+  const bool valid = has && half == 0;  // the lane that ends the sphere's step
 
-  // ---- learned closure: corrections for the next evaluation ----
+  // learned closure: corrections in use, network evaluated after the
+  // forces (blocks of 128), per-particle data recorded
+  const bool use_c = CL && ctl->closure != 0;
+  const bool net = use_c && MODE != MODE_FORCES && d.cl_smem;
+  const bool rec = CL && ctl->record != 0;
+  const bool feat = net || rec;
+  __shared__ __align__(8) uint64_t cl_bar[2];
+  __shared__ uint32_t cl_tmem;
+  extern __shared__ uint8_t cl_raw[];
+  uint8_t* cl_sm = nullptr;
   if (net) {
-    float o0 = 0.f, o1 = 0.f;
-    const bool ok = closure_infer(ft, cl_sm, cl_bar, cl_tmem, o0, o1);
-    if (valid) {
-      float2 c = make_float2(1.0f, 1.0f);  // plain coarse-graining outside the training range
-      if (ok && net_row) {
-        const float* P = reinterpret_cast<const float*>(cl_sm + CL_TILES);
-        bool inside = true;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) inside = inside && ft[k] >= P[CL_P_LO + k] && ft[k] <= P[CL_P_HI + k];
-        if (inside) {
-          const float cdm = P[CL_P_CMAX], cgm = P[CL_P_CMAX + 1];
-          c.x = expf(fminf(fmaxf(o0, -cdm), cdm));
-          c.y = expf(fminf(fmaxf(o1, -cgm), cgm));
-        }
-      }
-      d.clc[nxt][p] = c;
+    const uint32_t a = tc05::smem_u32(cl_raw);
+    cl_sm = cl_raw + (((a + 1023u) & ~1023u) - a);
+    if (threadIdx.x == 0) {
+      tc05::mbar_init(&cl_bar[0], 1);
+      tc05::mbar_init(&cl_bar[1], 1);
     }
-    if (!ok && threadIdx.x == 0) latch(ctl, ST_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the weights arrive while the contacts are evaluated
+      tc05::mbar_expect_tx(&cl_bar[0], CL_BLOB);
+      tc05::bulk_g2s(cl_sm, d.clblob, CL_BLOB, &cl_bar[0]);
+    }
+    if (threadIdx.x < 32) {
+      tc05::tmem_alloc(&cl_tmem, 64);
+      tc05::tmem_relinquish();
+    }
     tc05::fence_before_sync();
     __syncthreads();
-    if (threadIdx.x < 32) tc05::tmem_dealloc(cl_tmem, 64);
+    tc05::fence_after_sync();
   }
+  float2 my_c = make_float2(1.0f, 1.0f);
+  if (use_c && has) my_c = d.clc[cur][p];
+  __shared__ int bk_s[FORCE_BLOCK_MAX / 32];
+  __shared__ float bk_m[FORCE_BLOCK_MAX / 32];
+  __shared__ unsigned bk_c[FORCE_BLOCK_MAX / 32];
 
-  // ---- bookkeeping: displacement since rebuild, porosity rotation, step ----
-  const int wib = threadIdx.x >> 5;
-  if (MODE == MODE_MID) {
-    unsigned long long* z = d.vf[(vfc + 2) % 3];
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.Cf_total; c += gridDim.x * blockDim.x)
-      z[c] = 0ull;
-    const int s0 = __shfl_sync(FULL, si, 0);
-    const bool uniform = __all_sync(FULL, !valid || si == s0);
-    float md = my_disp2;
+  // ---- own sphere ----
+  Owner<true> me;
+  int si = 0;
+  if (has) {
+    si = d.sample[pc][p];
+    me.pq = d.posq[cur][p];
+    me.va = d.velf[cur][p];
+    me.wa = d.omgf[cur][p];
+    // the end of the step's per-sphere data, and the fluid cell's porosity and
+    // velocity: their latency overlaps the contacts
+    if (valid) {
+      prefetch_l1(&d.pos[cur][p]);
+      prefetch_l1(&d.vel[cur][p]);
+      prefetch_l1(&d.omg[cur][p]);
+      prefetch_l1(&d.posq_ref[p]);
+      prefetch_l1(&d.vq[pc][p]);
+      const int fc = d.fcell[pc][p];
+      prefetch_l1(&d.vf[vfc][fc]);
+      prefetch_l1(&d.Usf[fc]);
+    }
+  } else {
+    me.pq = make_int4(0, 0, 0, 0);
+    me.va = make_float4(0, 0, 0, 0);
+    me.wa = make_float4(0, 0, 0, 0);
+  }
+  const SampleDev& S = d.sp[si];
+  // the slot's records (the schedule's layout, k_rb_sched): entry k at rbase + k P
+  const uint32_t rbase = (uint32_t)gw * (uint32_t)P * (uint32_t)d.cap + (uint32_t)sub;
+  uint4* const recs = reinterpret_cast<uint4*>(d.rec[rc]);
+  // the first two records are read while the list length arrives (entries
+  // past a list's end, inside the warp's segment, are never dereferenced)
+  uint32_t k = (uint32_t)half;
+  const uint32_t cap = (uint32_t)d.cap;
+  uint4 r1 = make_uint4(0u, 0u, 0u, 0u), r2 = r1;
+  if (k < cap) r1 = recs[rbase + k * P];
+  if (k + Lp < cap) r2 = recs[rbase + (k + Lp) * P];
+  const uint32_t n = has ? d.cnt[rc][p] : 0u;
+  uint32_t kmax = n;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) md = fmaxf(md, __shfl_xor_sync(FULL, md, o));
-    // one fence and one arrival per block, without a block barrier: each
-    // warp leaves its maximum in shared memory, and the block's last warp
-    // publishes them (a warp that straddles samples publishes per lane and
-    // fences)
-    const unsigned wcoupled = __any_sync(FULL, coupled) ? 1u : 0u;
-    if (!uniform) {
-      if (my_disp2 >= 0.f) atomicMax(&d.dmax2[si], __float_as_uint(my_disp2));
-      __threadfence();
-    }
-    if (lane == 0) {
-      bk_s[wib] = s0;
-      bk_m[wib] = uniform ? md : -1.f;
-      bk_c[wib] = wcoupled;
-    }
+  for (int o = 16; o >= 1; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+  V3<float> F = v3<float>(0, 0, 0), Tq = v3<float>(0, 0, 0);
+  float Zacc = 0.f, Dacc = 0.f, Cacc = 0.f;  // closure data: active contacts, summed overlap, bond capacity
+  // software pipeline: records are loaded two entries ahead and the next
+  // entry's partner shadows one entry ahead, so neither load waits on the
+  // other and both overlap the evaluation of the current entry
+  int4 pq_nx = make_int4(0, 0, 0, 0);
+  float4 pa_nx = make_float4(0.f, 0.f, 0.f, 0.f), pb_nx = pa_nx;
+  if (k < n) {
+    const uint32_t q0 = r1.x & REC_IDX;
+    pq_nx = d.posq[cur][q0];
+    pa_nx = d.velf[cur][q0];
+    pb_nx = d.omgf[cur][q0];
   }
-  if (lane != 0) return;
-  __threadfence_block();
-  const unsigned nw = blockDim.x >> 5;
-  if (atomicAdd(&bk_n, 1u) != nw - 1u) return;
-  __threadfence_block();
-  {
-    if (MODE == MODE_MID) {
-      unsigned any = 0u;
-      for (unsigned w = 0; w < nw; ++w) {
-        const float mw = *((volatile float*)&bk_m[w]);
-        if (mw >= 0.f) atomicMax(&d.dmax2[*((volatile int*)&bk_s[w])], __float_as_uint(mw));
-        any |= *((volatile unsigned*)&bk_c[w]);
-      }
-      if (any) atomicOr(&ctl->coupled, 1u);
+  for (; k < kmax; k += Lp) {
+    const bool live = k < n;
+    const uint4 rcur = r1;
+    const int4 qq = pq_nx;
+    const float4 qa = pa_nx, qb = pb_nx;
+    r1 = r2;
+    if (k + 2 * Lp < n) r2 = recs[rbase + (k + 2 * Lp) * P];
+    if (k + Lp < n) {
+      const uint32_t qn = r1.x & REC_IDX;
+      pq_nx = d.posq[cur][qn];
+      pa_nx = d.velf[cur][qn];
+      pb_nx = d.omgf[cur][qn];
     }
-    __threadfence();
-    const unsigned t = atomicAdd(&ctl->block_counter, 1u);
-    if (t == gridDim.x - 1) {
-      // every block has started and finished: the segment order and the
-      // flags' epoch move on for the next launch
-      __threadfence();
-      if (MODE == MODE_MID) {
-        for (int s = 0; s < d.n_samples; ++s) {
-          const unsigned b = atomicAdd(&d.dmax2[s], 0u);
-          if (__uint_as_float(b) > d.sp[s].rebuild_q2) ctl->rebuild = 1;
+    if (!live) continue;
+    const size_t idx = (size_t)rbase + (size_t)k * P;
+    const uint32_t pf = rcur.x;
+    V3<float> xi = v3<float>(__uint_as_float(rcur.y), __uint_as_float(rcur.z), __uint_as_float(rcur.w));
+    const int q = (int)(pf & REC_IDX);
+    bool bonded = (pf & REC_BOND) != 0u;
+    const bool had_state = (pf & (REC_BOND | REC_ACTIVE)) != 0u || xi.x != 0.f || xi.y != 0.f ||
+                           xi.z != 0.f;
+    bool act = false;
+    if (qq.w > 0 && me.pq.w > 0) {
+      const int dx = (int)((uint32_t)qq.x - (uint32_t)me.pq.x);
+      const int dy = (int)((uint32_t)qq.y - (uint32_t)me.pq.y);
+      const int dz = (int)((uint32_t)qq.z - (uint32_t)me.pq.z);
+      const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                    (unsigned long long)((long long)dy * dy) +
+                                    (unsigned long long)((long long)dz * dz);
+      const unsigned Sq = (unsigned)me.pq.w + (unsigned)qq.w;
+      const unsigned long long S2 = (unsigned long long)Sq * Sq;
+      const unsigned long long band = 16ull * Sq + 256ull;
+      bool touching = false, need_exact = false;
+      if (d2 > S2 + band) touching = false;
+      else if (d2 + band < S2) touching = true;
+      else need_exact = true;
+      if (bonded || touching || need_exact) {
+        const float d2f = u64_to_f(d2);
+        const float invd = rsqrtf(d2f);
+        const float dn = d2f * invd;
+        float du;
+        if (d2 < (1ull << 62))
+          du = __fdividef(s64_to_f((long long)S2 - (long long)d2), (float)Sq + dn);
+        else
+          du = (float)Sq - dn;
+        const float delta = du * S.dq_f;
+        const V3<float> nrm = v3<float>(dx * invd, dy * invd, dz * invd);
+        const float Ri = me.va.w, Rj = qa.w, mi = me.wa.w, mj = qb.w;
+        const float Rs = __fdividef(Ri * Rj, Ri + Rj);
+        // surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure
+        float gam_f = S.gamma_f;
+        double gam_d = S.gamma;
+        if (use_c && bonded) {
+          const float qcg = d.clc[cur][q].y;
+          gam_f = S.gamma_f * sqrtf(my_c.y * qcg);
+          gam_d = S.gamma * sqrt((double)my_c.y * (double)qcg);
         }
-        if (atomicExch(&ctl->coupled, 0u)) ctl->vf_cur = (vfc + 1) % 3;
-        ctl->cur = nxt;
-        ctl->step = m_step;
+        double d2e = 0.0, Se = 0.0;
+        bool have_exact = false;
+        if (need_exact) {
+          exact_geometry(S, d.pos[cur][p], d.pos[cur][q], &d2e, &Se);
+          have_exact = true;
+          touching = d2e < __dmul_rn(Se, Se);
+        }
+        float xs = 0.0f;  // (pi^2 gamma^2 R* / E*^2)^(1/3) of a bonded pair
+        if (bonded) {
+          bool broken;
+          float dC = 0.0f, bandf = 4.0f * S.dq_f;
+          if (gam_f > 0.f) {
+            xs = m_cbrt(__fdividef(PI_F * PI_F * gam_f * gam_f * Rs, S.Es_f * S.Es_f));
+            dC = -0.57235712127666594f * xs;
+            bandf += 2e-5f * fabsf(dC);
+          }
+          if (delta < dC - bandf) {
+            broken = true;
+          } else if (delta > dC + bandf) {
+            broken = false;
+          } else {
+            const double4 A = d.pos[cur][p], B = d.pos[cur][q];
+            if (!have_exact) {
+              exact_geometry(S, A, B, &d2e, &Se);
+              have_exact = true;
+              touching = d2e < __dmul_rn(Se, Se);
+            }
+            const double Rid = fabs(A.w), Rjd = fabs(B.w);
+            const double Rsd = __dmul_rn(Rid, Rjd) / __dadd_rn(Rid, Rjd);
+            broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, gam_d);
+          }
+          if (broken) bonded = false;
+        }
+        act = bonded || touching;
+        if (act) {
+          const float ms = __fdividef(mi * mj, mi + mj);
+          const V3<float> vrel = v3<float>(qa.x - me.va.x, qa.y - me.va.y, qa.z - me.va.z);
+          const V3<float> rw = v3<float>(Ri * me.wa.x + Rj * qb.x, Ri * me.wa.y + Rj * qb.y,
+                                         Ri * me.wa.z + Rj * qb.z);
+          const V3<float> rwn = cross3(rw, nrm);
+          const V3<float> vc = v3<float>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
+          V3<float> Fi, Ft;
+          contact_law_mixed(delta, nrm, vrel, vc, Rs, ms, gam_f, bonded, 2.5198420997897464f * xs, S, xi,
+                            Fi, Ft);  // d_A = 16^(1/3) xs
+          const V3<float> nFt = cross3(nrm, Ft);
+          F.x += Fi.x;
+          F.y += Fi.y;
+          F.z += Fi.z;
+          Tq.x += Ri * nFt.x;
+          Tq.y += Ri * nFt.y;
+          Tq.z += Ri * nFt.z;
+          if (feat) {
+            Zacc += 1.f;
+            Dacc += delta;
+            Cacc += bonded ? 0.5f * 3.0f * PI_F * gam_f * Rs : 0.0f;
+          }
+        }
       }
-      ctl->epoch = epoch;
-      ctl->blk_next = 0;
-      ctl->block_counter = 0u;
-      __threadfence();
-      if (MODE == MODE_MID && h_next) cudaGraphSetConditional(h_next, ctl->rebuild ? 1u : 0u);
+    }
+    // write the record back when its state changed
+    if (act) {
+      const uint32_t npf = (uint32_t)q | REC_ACTIVE | (bonded ? REC_BOND : 0u);
+      recs[idx] = make_uint4(npf, __float_as_uint(xi.x), __float_as_uint(xi.y), __float_as_uint(xi.z));
+    } else if (had_state) {
+      recs[idx] = make_uint4((uint32_t)q, 0u, 0u, 0u);
     }
   }
+  if (Lp == 2) {  // two lanes per sphere: the odd entries' sums join the even ones'
+    F.x += __shfl_down_sync(FULL, F.x, 16);
+    F.y += __shfl_down_sync(FULL, F.y, 16);
+    F.z += __shfl_down_sync(FULL, F.z, 16);
+    Tq.x += __shfl_down_sync(FULL, Tq.x, 16);
+    Tq.y += __shfl_down_sync(FULL, Tq.y, 16);
+    Tq.z += __shfl_down_sync(FULL, Tq.z, 16);
+    if (feat) {
+      Zacc += __shfl_down_sync(FULL, Zacc, 16);
+      Dacc += __shfl_down_sync(FULL, Dacc, 16);
+      Cacc += __shfl_down_sync(FULL, Cacc, 16);
+    }
+  }
+  finish_step<true, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
+                              F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
+                              &bk_n, bk_s, bk_m, bk_c, h_next);
 }
+
 
 // MODE_CANON bookkeeping kernel (single thread).
 __global__ void k_after_canon(Dev d) {
@@ -1299,18 +1673,18 @@ void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphC
   if (d.N == 0) return;
   if (cl) {
     if (d.mixed) {
-      if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
-      else if (mode == MODE_MID) k_forces<true, MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
-      else k_forces<true, MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
+      if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
+      else if (mode == MODE_MID) k_forces_lanes<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
+      else k_forces_lanes<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
     } else {
       if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
       else if (mode == MODE_MID) k_forces<false, MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
       else k_forces<false, MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
     }
   } else if (d.mixed) {
-    if (mode == MODE_FORCES) k_forces<true, MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
-    else if (mode == MODE_MID) k_forces<true, MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
-    else k_forces<true, MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
+    if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
+    else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
+    else k_forces_lanes<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
   } else {
     if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
     else if (mode == MODE_MID) k_forces<false, MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);

@@ -195,8 +195,9 @@ __global__ void k_rb_ft_store(Dev d) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= d.N) return;
   const double4* st = reinterpret_cast<const double4*>(d.staging);
-  d.F[p] = st[p];
-  d.T[p] = st[d.Npad + p];
+  const uint32_t c = d.mixed ? d.sched[p] : (uint32_t)p;  // mixed: schedule order
+  d.F[p] = st[c];
+  d.T[p] = st[d.Npad + c];
 }
 
 constexpr int BIG_STENCIL = 27;  // stencils of more than 3^3 cells are walked by a warp
@@ -369,21 +370,123 @@ __global__ void k_rb_pairs_big(Dev d) {
   }
 }
 
-// Mixed: every sphere lists all its candidates.  Sort each list by partner,
-// pack the records of a warp contiguously and carry the contact history of
-// the old records by particle pair.
-template <bool MIXED>
+// Mixed: the force kernel's schedule.  Per tile of SCHED_TILE consecutive
+// spheres (cell order, so a tile is a compact region of the sample), the
+// spheres are ordered by decreasing candidate count, spheres of equal count
+// in cell order (a stable counting sort: the slots, and so the order of
+// every list, are the same on every run), and dealt to consecutive slots;
+// slot s is lane s % ppw of the force kernel's warp s / ppw, whose records
+// are entry-major: entry k of that lane's sphere at
+// (s / ppw) ppw cap + k ppw + s % ppw.
+constexpr int SCHED_TILE = 1024;
+__global__ void __launch_bounds__(SCHED_TILE) k_rb_sched(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int rn = d.ctl->rec_cur ^ 1;
+  constexpr int NW = SCHED_TILE / 32, NK = CGDEM_MAX_NEIGHBORS + 1;
+  __shared__ uint32_t wpre[NW][NK];  // per warp and count: spheres, then the earlier warps' spheres
+  __shared__ uint32_t start[NK];     // per count: spheres, then the first slot
+  const int cap = d.cap, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < NW * NK; i += blockDim.x) (&wpre[0][0])[i] = 0u;
+  __syncthreads();
+  const int t0 = blockIdx.x * SCHED_TILE;
+  const int p = t0 + (int)threadIdx.x;
+  const bool valid = p < d.N;
+  const uint32_t n = valid ? min(d.cand_n[p], (uint32_t)cap) : 0u;
+  const uint32_t key = valid ? (uint32_t)cap - n : 0xffffffffu;  // larger lists first
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));  // earlier lanes with this count
+  if (valid && rank == 0) wpre[wid][key] = __popc(peers);
+  __syncthreads();
+  if ((int)threadIdx.x <= cap) {
+    uint32_t run = 0u;
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t c = wpre[w][threadIdx.x];
+      wpre[w][threadIdx.x] = run;
+      run += c;
+    }
+    start[threadIdx.x] = run;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the cap + 1 <= 97 counts: 4 per lane
+    uint32_t v[4], sum = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = 4 * lane + j;
+      v[j] = b <= cap ? start[b] : 0u;
+      sum += v[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = 4 * lane + j;
+      if (b <= cap) start[b] = run;
+      run += v[j];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    const uint32_t slot = (uint32_t)t0 + start[key] + wpre[wid][key] + rank;
+    d.sched[slot] = (uint32_t)p;
+    d.perm_tmp[p] = slot;  // cell-order index -> slot (free after k_rb_rank)
+  } else if (p < d.Npad) {
+    d.sched[p] = 0xffffffffu;  // the slots after the last sphere
+  }
+  if (p < d.Npad) {
+    const uint32_t P = (uint32_t)d.ppw, sl = (uint32_t)p;
+    d.roff[rn][sl] = (sl / P) * P * (uint32_t)cap + (sl & (P - 1u));
+  }
+}
+
+// Mixed: gather every per-particle array from cell order (the buffers the
+// first permutation filled) into schedule order (back into the current
+// buffers), so that the force kernel's warps read and write their spheres'
+// data in consecutive lines.  Slot s holds the sphere of cell-order index
+// sched[s].
+__global__ void k_rb_permute2(Dev d) {
+  if (!d.ctl->rebuild) return;
+  const int cur = d.ctl->cur, nxt = cur ^ 1;
+  const int pc = d.ctl->pcur, pn = pc ^ 1;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.N) return;
+  const uint32_t c = d.sched[s];
+  d.pos[cur][s] = d.pos[nxt][c];
+  d.vel[cur][s] = d.vel[nxt][c];
+  d.omg[cur][s] = d.omg[nxt][c];
+  d.posq[cur][s] = d.posq[nxt][c];
+  d.velf[cur][s] = d.velf[nxt][c];
+  d.omgf[cur][s] = d.omgf[nxt][c];
+  d.id[pc][s] = d.id[pn][c];
+  d.sample[pc][s] = d.sample[pn][c];
+  d.fcell[pc][s] = d.fcell[pn][c];
+  d.vq[pc][s] = d.vq[pn][c];
+  if (d.clc[0]) d.clc[cur][s] = d.clc[nxt][c];
+  if (d.wallhf[0])
+    for (int w = 0; w < 3; ++w)
+      d.wallhf[pc][(size_t)w * d.Npad + s] = d.wallhf[pn][(size_t)w * d.Npad + c];
+}
+
+// Mixed: every sphere lists all its candidates.  Per slot (the sphere's
+// index in schedule order), sort its list by partner (partners in schedule
+// order), write it at the slot's records (entry-major per warp) and carry the
+// contact history of the old records by particle pair.
 __global__ void k_rb_lists_full(Dev d) {
   if (!d.ctl->rebuild) return;
-  const int nxt = d.ctl->cur ^ 1;
-  const int pn = d.ctl->pcur ^ 1;
+  const int cur = d.ctl->cur;  // the new state, in schedule order (k_rb_permute2)
+  const int pc = d.ctl->pcur;
   const int rc = d.ctl->rec_cur, rn = rc ^ 1;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers Npad exactly
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // slot; the grid covers Npad exactly
   const int lane = threadIdx.x & 31;
   const int Npad = d.Npad, cap = d.cap;
   if (p - lane >= Npad) return;  // whole warps only (Npad is a multiple of 256)
   const bool valid = p < d.N;
-  uint32_t count = valid ? d.cand_n[p] : 0u;
+  const uint32_t c = valid ? d.sched[p] : 0u;  // cell-order index of the slot's sphere
+  uint32_t count = valid ? d.cand_n[c] : 0u;
   if (count > (uint32_t)cap) latch(d.ctl, ST_CAPACITY);
   unsigned mx = count, sum = count;
 #pragma unroll
@@ -396,25 +499,16 @@ __global__ void k_rb_lists_full(Dev d) {
     atomicAdd((unsigned long long*)&d.ctl->cand_total_next, (unsigned long long)sum);
   }
   const uint32_t n = count < (uint32_t)cap ? count : (uint32_t)cap;
-  // records of a segment of P consecutive spheres are contiguous (P spheres per warp of the force kernel)
-  const int P = d.ppw, sub = lane & (P - 1);
-  uint32_t incl = n;
-#pragma unroll
-  for (int k = 1; k < 32; k <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, k, P);
-    if (k < P && sub >= k) incl += y;
-  }
-  const uint32_t seg = (uint32_t)(p - sub) * (uint32_t)cap;
-  const uint32_t first = seg + incl - n;
-  d.roff[rn][p] = first;
   d.cnt[rn][p] = n;
   if (!valid) return;
-  const int4 pq = d.posq[nxt][p];
+  const size_t first = d.roff[rn][p];
+  const size_t rs = (size_t)d.rstride;
+  const int4 pq = d.posq[cur][p];
   d.posq_ref[p] = pq;
-  // insertion sort by partner index (lists are short; sizes vary with the PSD)
+  // insertion sort by partner slot (lists are short; sizes vary with the PSD)
   uint32_t lst[CGDEM_MAX_NEIGHBORS];
   for (uint32_t j = 0; j < n; ++j) {
-    const uint32_t v = d.cand_tmp[(size_t)j * Npad + p];
+    const uint32_t v = d.perm_tmp[d.cand_tmp[(size_t)j * Npad + c]];
     uint32_t i = j;
     while (i > 0 && lst[i - 1] > v) {
       lst[i] = lst[i - 1];
@@ -422,40 +516,22 @@ __global__ void k_rb_lists_full(Dev d) {
     }
     lst[i] = v;
   }
-  for (uint32_t j = 0; j < n; ++j) {
-    if (MIXED) {
-      reinterpret_cast<uint4*>(d.rec[rn])[first + j] = make_uint4(lst[j], 0u, 0u, 0u);
-    } else {
-      RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + first + j;
-      *reinterpret_cast<int4*>(rr) = make_int4((int)lst[j], 0, 0, 0);
-      *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
-    }
-  }
+  uint4* recs = reinterpret_cast<uint4*>(d.rec[rn]);
+  for (uint32_t j = 0; j < n; ++j) recs[first + j * rs] = make_uint4(lst[j], 0u, 0u, 0u);
   if (pq.w <= 0) return;
-  // carry history: old records of this particle with any state
-  const uint32_t o = d.perm[p];
+  // carry history: old records of this particle with any state; an old
+  // index maps to its cell-order index (inv_perm), then to its slot
+  uint32_t carried[(CGDEM_MAX_NEIGHBORS + 31) / 32] = {};  // entries that received a state
+  const uint32_t o = d.perm[c];
   const uint32_t nold = d.cnt[rc][o];
-  const uint32_t oldfirst = d.roff[rc][o];
+  const size_t oldfirst = d.roff[rc][o];
+  const uint4* orecs = reinterpret_cast<const uint4*>(d.rec[rc]);
   for (uint32_t k = 0; k < nold; ++k) {
-    const size_t oidx = (size_t)oldfirst + k;
-    uint32_t pf;
-    bool nz;
-    uint4 rf = make_uint4(0, 0, 0, 0);
-    int4 h0 = make_int4(0, 0, 0, 0);
-    double2 h1 = make_double2(0, 0);
-    if (MIXED) {
-      rf = reinterpret_cast<const uint4*>(d.rec[rc])[oidx];
-      pf = rf.x;
-      nz = (rf.y | rf.z | rf.w) != 0u;
-    } else {
-      const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + oidx;
-      h0 = *reinterpret_cast<const int4*>(rr);
-      h1 = *(reinterpret_cast<const double2*>(rr) + 1);
-      pf = (uint32_t)h0.x;
-      nz = (h0.z | h0.w) != 0 || h1.x != 0.0 || h1.y != 0.0;
-    }
+    const uint4 rf = orecs[oldfirst + k * rs];
+    const uint32_t pf = rf.x;
+    const bool nz = (rf.y | rf.z | rf.w) != 0u;
     if (!(pf & (REC_BOND | REC_ACTIVE)) && !nz) continue;
-    const uint32_t qn = d.inv_perm[pf & REC_IDX];
+    const uint32_t qn = d.perm_tmp[d.inv_perm[pf & REC_IDX]];
     // binary search in the sorted list
     int a = 0, b = (int)n - 1, hit = -1;
     while (a <= b) {
@@ -469,30 +545,39 @@ __global__ void k_rb_lists_full(Dev d) {
     }
     if (hit >= 0) {
       const uint32_t npf = qn | (pf & (REC_BOND | REC_ACTIVE));
-      if (MIXED) {
-        reinterpret_cast<uint4*>(d.rec[rn])[first + hit] = make_uint4(npf, rf.y, rf.z, rf.w);
-      } else {
-        RecD* rr = reinterpret_cast<RecD*>(d.rec[rn]) + first + hit;
-        *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, h0.z, h0.w);
-        *(reinterpret_cast<double2*>(rr) + 1) = h1;
-      }
-    } else if ((pf & REC_BOND) && d.posq[nxt][qn].w > 0) {
+      recs[first + hit * rs] = make_uint4(npf, rf.y, rf.z, rf.w);
+      carried[hit >> 5] |= 1u << (hit & 31);
+    } else if ((pf & REC_BOND) && d.posq[cur][qn].w > 0) {
       // a bond may leave the list only with a partner that left the domain
-      if (atomicCAS(&d.ctl->lost_i, -1, d.id[pn][p]) == -1) {
-        const int4 qq = d.posq[nxt][qn];
+      if (atomicCAS(&d.ctl->lost_i, -1, d.id[pc][p]) == -1) {
+        const int4 qq = d.posq[cur][qn];
         const int dx = (int)((uint32_t)qq.x - (uint32_t)pq.x);
         const int dy = (int)((uint32_t)qq.y - (uint32_t)pq.y);
         const int dz = (int)((uint32_t)qq.z - (uint32_t)pq.z);
-        d.ctl->lost_j = d.id[pn][qn];
+        d.ctl->lost_j = d.id[pc][qn];
         d.ctl->lost_d2 = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
                          (unsigned long long)((long long)dz * dz);
         const unsigned long long S = (unsigned long long)(unsigned)pq.w + (unsigned)qq.w +
-                                     (unsigned)d.sp[d.sample[pn][p]].skin_q;
+                                     (unsigned)d.sp[d.sample[pc][p]].skin_q;
         d.ctl->lost_S2 = S * S;
       }
       latch(d.ctl, ST_BOND_LOST);
     }
   }
+  // entries with a state (bonds, touching pairs, springs) first, in partner
+  // order, then the candidates without one: the force kernel's warps then
+  // meet the stateless entries, which need no contact law, in the same
+  // iterations (a list's order is free once the carry above has used its
+  // sort by partner)
+  uint32_t ns = 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!((carried[j >> 5] >> (j & 31)) & 1u)) continue;
+    if (ns != j) recs[first + ns * rs] = recs[first + j * rs];
+    ++ns;
+  }
+  if (ns == 0 || ns == n) return;
+  for (uint32_t j = 0; j < n; ++j)
+    if (!((carried[j >> 5] >> (j & 31)) & 1u)) recs[first + (ns++) * rs] = make_uint4(lst[j], 0u, 0u, 0u);
 }
 
 // FP64: sort each candidate list by partner.  A sphere owns the pairs with
@@ -574,7 +659,7 @@ __device__ __forceinline__ uint32_t find_record(const Dev& d, int b, uint32_t ow
   int lo = 0, hi = (int)d.cnt[b][owner] - 1;
   while (lo <= hi) {
     const int m = (lo + hi) >> 1;
-    const size_t idx = (size_t)base + m;
+    const size_t idx = (size_t)base + (size_t)m * d.rstride;
     const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[b])[idx].x
                                 : reinterpret_cast<const RecD*>(d.rec[b])[idx].pf;
     const uint32_t q = pf & REC_IDX;
@@ -619,7 +704,7 @@ __global__ void k_rb_carry(Dev d) {
   const uint32_t nold = d.cnt[rc][o];
   const uint32_t oldfirst = d.roff[rc][o];
   for (uint32_t k = 0; k < nold; ++k) {
-    const size_t oidx = (size_t)oldfirst + k;
+    const size_t oidx = (size_t)oldfirst + (size_t)k * d.rstride;
     uint32_t pf;
     bool nz;
     uint4 rf = make_uint4(0, 0, 0, 0);
@@ -684,8 +769,10 @@ __global__ void k_rb_carry(Dev d) {
 __global__ void k_rb_finish(Dev d) {
   Ctl* c = d.ctl;
   if (!c->rebuild) return;
-  c->cur ^= 1;
-  c->pcur ^= 1;
+  if (!d.mixed) {  // mixed: k_rb_permute2 wrote the state back into the current buffers
+    c->cur ^= 1;
+    c->pcur ^= 1;
+  }
   c->rec_cur ^= 1;
   c->rebuild = 0;
   c->max_cand = c->max_cand_next;
@@ -710,7 +797,7 @@ __global__ void k_bond_touching(Dev d) {
   const SampleDev& S = d.sp[d.sample[pc][p]];
   const uint32_t n = d.cnt[rc][p];
   for (uint32_t k = 0; k < n; ++k) {
-    const size_t idx = (size_t)d.roff[rc][p] + k;
+    const size_t idx = (size_t)d.roff[rc][p] + (size_t)k * d.rstride;
     uint32_t* pfp = d.mixed ? &reinterpret_cast<uint4*>(d.rec[rc])[idx].x
                             : &reinterpret_cast<RecD*>(d.rec[rc])[idx].pf;
     const uint32_t q = *pfp & REC_IDX;
@@ -1038,7 +1125,7 @@ __global__ void k_collect_contacts(Dev d, uint32_t* out, unsigned long long cap)
   const uint32_t n = d.cnt[rc][p];
   const int ip = d.id[pc][p];
   for (uint32_t k = 0; k < n; ++k) {
-    const size_t idx = (size_t)d.roff[rc][p] + k;
+    const size_t idx = (size_t)d.roff[rc][p] + (size_t)k * d.rstride;
     const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
                                 : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
     if (!(pf & REC_ACTIVE)) continue;
@@ -1079,7 +1166,7 @@ __global__ void k_diag_partial(Dev d, double* part) {
         const uint32_t n = d.cnt[rc][p];
         const int ip = d.id[pc][p];
         for (uint32_t k = 0; k < n; ++k) {
-          const size_t idx = (size_t)d.roff[rc][p] + k;
+          const size_t idx = (size_t)d.roff[rc][p] + (size_t)k * d.rstride;
           const uint32_t pf = d.mixed ? reinterpret_cast<const uint4*>(d.rec[rc])[idx].x
                                       : reinterpret_cast<const RecD*>(d.rec[rc])[idx].pf;
           if ((pf & REC_BOND) && (pf & REC_ACTIVE) && (!d.mixed || ip < d.id[pc][pf & REC_IDX]))
@@ -1120,12 +1207,15 @@ void launch_rebuild(const Dev& d, cudaStream_t s) {
   k_rb_rank<<<G, B, 0, s>>>(d);
   k_rb_permute<<<G, B, 0, s>>>(d);
   k_rb_ft_gather<<<G, B, 0, s>>>(d);
-  k_rb_ft_store<<<G, B, 0, s>>>(d);
+  if (!d.mixed) k_rb_ft_store<<<G, B, 0, s>>>(d);
   k_rb_pairs<<<G, B, 0, s>>>(d);
   k_rb_pairs_big<<<4 * 152, 256, 0, s>>>(d);
   const int Gp = nblk(d.Npad, B);
   if (d.mixed) {
-    k_rb_lists_full<true><<<Gp, B, 0, s>>>(d);
+    k_rb_sched<<<nblk(d.Npad, SCHED_TILE), SCHED_TILE, 0, s>>>(d);
+    k_rb_permute2<<<G, B, 0, s>>>(d);
+    k_rb_ft_store<<<G, B, 0, s>>>(d);
+    k_rb_lists_full<<<Gp, B, 0, s>>>(d);
   } else {
     k_rb_lists_half<false><<<Gp, B, 0, s>>>(d);
     k_rb_carry<false><<<G, B, 0, s>>>(d);

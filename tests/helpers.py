@@ -69,3 +69,154 @@ def normwise_error(Fg, Fo, scale):
     """max over particles of |F_gpu - F_oracle| / (sum of force-term magnitudes)."""
     err = np.linalg.norm(Fg - Fo, axis=1)
     return float(np.max(err / np.maximum(scale, 1e-300)))
+
+
+# ---------------------------------------------------------------------------
+# mixed precision over several steps
+# ---------------------------------------------------------------------------
+#
+# One evaluation of the mixed step on the same state is within 1e-4 of the
+# oracle (normwise, per particle).  After n steps the two trajectories sit at
+# slightly different states, so their forces also differ by what the state
+# difference changes: that part is bounded here to first order from the
+# oracle's contacts -- normal and tangential stiffness times the position
+# differences of the pair, normal and tangential damping times their
+# velocity differences (surface velocities included), the drag's slope times
+# the velocity difference, the walls likewise -- with a factor of 2 for the
+# second-order terms and the tangential history.  The mixed step also takes
+# each contact's geometry from positions and radii rounded to a fixed-point
+# quantum dq (the library's shadow of the positions), so an overlap carries
+# an error of up to (sqrt(3) + 1) dq: its stiffness times that is added (it
+# dominates for a contact that has only just formed, a few nm deep).  A
+# particle whose contact
+# set (with bond flags) differs between the two runs has crossed a touching
+# or bond-break threshold in one of them; those are checked separately (every
+# differing pair must sit at a threshold) and left out of the force check.
+
+def jkr_radius_np(delta, Rs, Es, gamma):
+    """Contact radius on the stable branch of Eq. 13, by Newton on the reduced
+    quartic (test-side, for a bound)."""
+    aA = (4 * np.pi * gamma * Rs * Rs / Es) ** (1 / 3)
+    dA = aA * aA / Rs
+    D = delta / dA
+    u = np.where(D >= 0, (np.maximum(D, 0) + 1) ** 0.25 + 0.05, 1.0)
+    for _ in range(40):
+        u = u - (u ** 4 - u - D) / (4 * u ** 3 - 1)
+    u = np.maximum(u, 0.75 ** (1 / 3))
+    return u * u * aA
+
+
+def state_diff(s, g, o):
+    dx = g["x"] - o["x"]
+    if s.domain["kind"] == 0:
+        L = s.domain["L"][0]
+        dx -= L * np.round(dx / L)
+    return (np.linalg.norm(dx, axis=1), np.linalg.norm(g["v"] - o["v"], axis=1),
+            np.linalg.norm(g["w"] - o["w"], axis=1))
+
+
+def fixed_quantum(s, skin):
+    """The fixed-point quantum of the mixed step's position shadow: L / 2^32
+    in a periodic cube, else the power of two that puts the largest
+    candidate distance 2 r_max + skin below 2^30 quanta."""
+    if s.domain["kind"] == 0:
+        return s.domain["L"][0] / 2.0 ** 32
+    reach = 2 * float(s.R.max()) + skin
+    return 2.0 ** math.ceil(math.log2(reach / 2.0 ** 30))
+
+
+def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0):
+    """Per-particle bounds on |F_gpu - F_oracle| and |T_gpu - T_oracle| after
+    several mixed steps (see above)."""
+    m = s.material
+    Es = m["E"] / (2 * (1 - m["nu"] ** 2))
+    Gs = m["E"] / (2 * (1 + m["nu"])) / (2 * (2 - m["nu"]))
+    le = np.log(m["e"])
+    beta = -le / np.sqrt(le * le + np.pi ** 2)
+    cd = 2 * np.sqrt(5 / 6) * beta
+    gamma = m["gamma"] * k
+    R = s.R
+    mass = m["rho"] * 4 / 3 * np.pi * R ** 3
+    dx, dv, dw = state_diff(s, g, o)
+    n = len(R)
+    B = np.zeros(n)
+    oi, oj, ob, _ = sim.contacts()
+    if len(oi):
+        d = o["x"][oj] - o["x"][oi]
+        if s.domain["kind"] == 0:
+            L = s.domain["L"][0]
+            d -= L * np.round(d / L)
+        dist = np.linalg.norm(d, axis=1)
+        Ri, Rj = R[oi], R[oj]
+        Rs = Ri * Rj / (Ri + Rj)
+        ms = mass[oi] * mass[oj] / (mass[oi] + mass[oj])
+        delta = Ri + Rj - dist
+        bond = ob.astype(bool) & (gamma > 0)
+        a = np.sqrt(Rs * np.maximum(delta, 0))
+        kn = 2 * Es * a
+        if bond.any():
+            ab = jkr_radius_np(delta[bond], Rs[bond], Es, gamma)
+            dFda = 4 * Es * ab ** 2 / Rs[bond] - 1.5 * np.sqrt(16 * np.pi * gamma * Es * ab)
+            ddda = 2 * ab / Rs[bond] - np.sqrt(np.pi * gamma / (Es * ab))
+            a[bond] = ab
+            kn[bond] = np.abs(dFda) / np.maximum(ddda, 1e-300)
+        kt = 8 * Gs * a
+        gn = cd * np.sqrt(2 * Es * a * ms)
+        gt = cd * np.sqrt(kt * ms)
+        t = (kn + kt) * (dx[oi] + dx[oj] + (math.sqrt(3) + 1) * dq) + \
+            (gn + gt) * (dv[oi] + dv[oj] + Ri * dw[oi] + Rj * dw[oj])
+        np.add.at(B, oi, t)
+        np.add.at(B, oj, t)
+    if s.domain["kind"] == 1:
+        x = o["x"]
+        r = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
+        dom = s.domain
+        for dw_ in (r + R - dom["Rc"], np.where(r >= dom["r_out"], R - x[:, 2], -1.0),
+                    x[:, 2] + R - dom["H"]):
+            aw = np.sqrt(R * np.maximum(dw_, 0))
+            kw = (2 * Es + 8 * Gs) * aw
+            gw = cd * (np.sqrt(2 * Es * aw * mass) + np.sqrt(8 * Gs * aw * mass))
+            B += np.where(dw_ > 0, kw * dx + gw * (dv + R * dw), 0.0)
+    cl = sim.closure_data()
+    fd = np.linalg.norm(cl[:, 5:8], axis=1)
+    slip = cl[:, 1]
+    B += np.where(slip > 0, 2 * fd / np.maximum(slip, 1e-300), 0.0) * dv
+    scale = sim.force_scale()
+    bF = tau * scale + 2 * B
+    return bF, R * bF
+
+
+def agreeing_particles(n, gc, oc):
+    """Particles whose contacts (partner and bond flag) agree between the runs.
+    gc, oc: (i, j, bonded) arrays."""
+    G = set(zip(*(a.tolist() for a in gc)))
+    Oc = set(zip(*(a.tolist() for a in oc)))
+    ok = np.ones(n, bool)
+    for i, j, _ in G ^ Oc:
+        ok[i] = ok[j] = False
+    return ok
+
+
+def check_mixed_forces(s, g, o, sim, gc, tau, k=1.0, rows=None, skin=None):
+    """Forces and torques after several mixed steps within force_bound for
+    the particles (of `rows`, default all) whose contacts agree; returns the
+    number of particles left out."""
+    oi, oj, ob, _ = sim.contacts()
+    ok = agreeing_particles(len(s.R), gc, (oi, oj, ob))
+    if rows is not None:
+        ok &= rows
+    dq = fixed_quantum(s, default_skin(s) if skin is None else skin)
+    bF, bT = force_bound(s, o, sim, g, tau, k, dq)
+    eF = np.linalg.norm(g["F"] - o["F"], axis=1)
+    eT = np.linalg.norm(g["T"] - o["T"], axis=1)
+    bad = ok & ((eF > bF) | (eT > bT))
+    if bad.any():
+        b = np.flatnonzero(bad)[:3]
+        scale = sim.force_scale()
+        info = [dict(i=int(i), eF=float(eF[i]), bF=float(bF[i]), eT=float(eT[i]), bT=float(bT[i]),
+                     scale=float(scale[i]), R=float(s.R[i]), x=o["x"][i].tolist(),
+                     Fo=o["F"][i].tolist(), Fg=g["F"][i].tolist(),
+                     contacts=int(((oi == i) | (oj == i)).sum()),
+                     bonds=int((((oi == i) | (oj == i)) & (ob > 0)).sum())) for i in b]
+        raise AssertionError(f"mixed forces beyond the bound: {info}")
+    return int((~ok).sum() if rows is None else (rows & ~ok).sum())

@@ -12,9 +12,11 @@ full sizes, against the FP64 oracle.
   earlier wave; contacts bit-exact and forces within 1e-10 over 3 steps.
 * The 2.0M-sphere cylinder of the benchmark at the autotuner's knobs (the
   same call the benchmark makes): forces and contacts of spheres well inside
-  two sub-blocks of 30,000 spheres (one mid-bed, one at the outlet and the
+  two sub-blocks of 100,000 spheres (one mid-bed, one at the outlet and the
   bottom wall) against the oracle run on each sub-block, at the first force
-  evaluation and after 3 steps, in both precisions.
+  evaluation and after 3 steps, in both precisions (mixed after 3 steps:
+  within the per-step tolerance plus the first-order change of the forces
+  that the two runs' state difference produces, tests/helpers.py).
 * The 64-member ensemble of the benchmark at its autotuned knobs, with and
   without the per-member skins balanced by drift rate: every member against
   the oracle at the first evaluation, six members after 12 steps.
@@ -27,7 +29,8 @@ import pytest
 import oracle as O
 from paper_2211_06142_gb300 import cgdem
 from paper_2211_06142_gb300 import inputs as I
-from tests.helpers import default_dt, default_skin, normwise_error, oracle_params, with_velocities
+from tests.helpers import (check_mixed_forces, default_dt, default_skin, normwise_error, oracle_params,
+                           with_velocities)
 
 pytestmark = pytest.mark.gpu
 
@@ -255,19 +258,28 @@ def test_full_size_cylinder_at_bench_knobs(big, prec):
             inner = np.linalg.norm(s.x[idx] - c, axis=1) < rad - (steps + 1) * hop - 1e-4
             assert inner.sum() > 1000
             scale = sim.force_scale()[inner]
-            spread = normwise_error(r["F"][inner], o["F"][inner], scale)
-            e = normwise_error(g["F"][idx][inner], o["F"][inner], scale)
-            assert e <= max(TOL[prec], 10 * spread), (steps, e, spread)
-            tsc = scale * s.R[idx][inner]
-            spread_t = normwise_error(r["T"][inner], o["T"][inner], tsc)
-            et = normwise_error(g["T"][idx][inner], o["T"][inner], tsc)
-            assert et <= max(TOL[prec], 10 * spread_t), (steps, et, spread_t)
+            loc = -np.ones(len(s.R), np.int64)
+            loc[idx] = np.arange(len(idx))
+            li, lj = loc[gi], loc[gj]
+            both = (li >= 0) & (lj >= 0)
+            if prec == cgdem.FP64 or steps == 0:
+                spread = normwise_error(r["F"][inner], o["F"][inner], scale)
+                e = normwise_error(g["F"][idx][inner], o["F"][inner], scale)
+                assert e <= max(TOL[prec], 10 * spread), (steps, e, spread)
+                tsc = scale * s.R[idx][inner]
+                spread_t = normwise_error(r["T"][inner], o["T"][inner], tsc)
+                et = normwise_error(g["T"][idx][inner], o["T"][inner], tsc)
+                assert et <= max(TOL[prec], 10 * spread_t), (steps, et, spread_t)
+            else:
+                sub = copy.copy(s)
+                sub.x, sub.v, sub.w, sub.R = s.x[idx], s.v[idx], s.w[idx], s.R[idx]
+                gs = {q: g[q][idx] for q in ("x", "v", "w", "F", "T")}
+                left = check_mixed_forces(sub, gs, o, sim, (li[both], lj[both], gb[both]), TOL[prec],
+                                          rows=inner, skin=skin)
+                assert left <= 0.02 * inner.sum()
             # contacts of the inner spheres, bit-exact (FP64; mixed at step 0)
             if prec == cgdem.FP64 or steps == 0:
-                loc = -np.ones(len(s.R), np.int64)
-                loc[idx] = np.arange(len(idx))
-                li, lj = loc[gi], loc[gj]
-                keep = (li >= 0) & (lj >= 0)
+                keep = both.copy()
                 keep[keep] &= inner[li[keep]] & inner[lj[keep]]
                 G = set(zip(li[keep].tolist(), lj[keep].tolist(), gb[keep].tolist()))
                 oi, oj, ob, _ = sim.contacts()
@@ -333,21 +345,18 @@ def test_ensemble_at_bench_knobs(ensemble64, skins):
         assert np.array_equal(gi[m] - offs[k], oi) and np.array_equal(gj[m] - offs[k], oj), k
         assert np.array_equal(gb[m], ob), k
         if k in stepped:
-            rng = np.random.default_rng(99)
-            ref = O.Sim(o_p, s.x, s.v * (1 + 1e-7 * rng.standard_normal(s.v.shape)), s.w, s.R, s.Us)
-            ref.bond_touching()
-            ref.couple_fluid()
-            ref.compute_forces()
-            sims[k] = (sim, ref)
+            sims[k] = sim
     ctx.step(12)
     g = ctx.get_state()
-    for k, (sim, ref) in sims.items():
+    gi, gj, gb = ctx.get_contacts()
+    for k, sim in sims.items():
         sim.step(12)
-        ref.step(12)
         sl = slice(offs[k], offs[k + 1])
-        scale = sim.force_scale()
-        spread = normwise_error(ref.state()["F"], sim.state()["F"], scale)
-        err = normwise_error(g["F"][sl], sim.state()["F"], scale)
-        assert err <= max(TOL[cgdem.MIXED], 10 * spread), (k, err, spread)
+        m = (gi >= offs[k]) & (gi < offs[k + 1])
+        gk = {q: g[q][sl] for q in ("x", "v", "w", "F", "T")}
+        left = check_mixed_forces(samples[k], gk, sim.state(), sim,
+                                  (gi[m] - offs[k], gj[m] - offs[k], gb[m]), TOL[cgdem.MIXED], k=specs[k].k,
+                                  skin=pp[k].skin)
+        assert left <= 0.02 * counts[k], (k, left)
     assert ctx.status() == 0
     ctx.close()
