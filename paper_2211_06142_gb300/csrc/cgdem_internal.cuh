@@ -327,33 +327,4 @@ __device__ __forceinline__ void exact_geometry(const SampleDev& s, double4 a, do
 
 __device__ __forceinline__ void latch(Ctl* ctl, unsigned bits) { atomicOr(&ctl->status, bits); }
 
-// IEEE double -> float, round to nearest even, by bit manipulation on the
-// integer pipe (GB300 runs FP64 and its conversions at ~1/60 of the FP32
-// rate).  Results below the float normal range flush to signed zero; the
-// caller never passes NaN or Inf (checked earlier).
-__device__ __forceinline__ float d2f_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned sign = hi & 0x80000000u;
-  const int fe = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (fe <= 0) return __uint_as_float(sign);
-  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu;
-  unsigned f = sign | ((unsigned)fe << 23) | m;
-  if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) f += 1u;
-  return __uint_as_float(f);
-}
-
-// float -> double (exact), by bit manipulation; float subnormals flush to zero.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned sign = u & 0x80000000u;
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u) return __hiloint2double((int)sign, 0);
-  const unsigned m = u & 0x7fffffu;
-  const unsigned hi = sign | ((e - 127u + 1023u) << 20) | (m >> 3);
-  return __hiloint2double((int)hi, (int)(m << 29));
-}
-
 }  // namespace cgdem

@@ -1,42 +1,34 @@
 // k_forces.cu -- contact, wall, body and drag forces of one DEM step fused
 // with the velocity-Verlet update (arXiv 2211.06142, Sec. 2.1-2.3).
 //
-// Work decomposition.  Spheres are grouped by warp (32 consecutive spheres
-// in cell order, or 16 for samples too small to fill the GPU); a warp's
-// candidate records are stored contiguously (sphere after sphere), so the
-// warp walks them in rounds of 32 entries: every lane evaluates one pair per
-// round whatever the list lengths are (the size ratio of the sand is 6, so
-// they vary several-fold within a warp).  The spheres' sums come from a
-// segmented warp scan in list order, then each lane that owns a sphere runs
-// its epilogue: walls, gravity, buoyancy, drag, integration, porosity
-// scatter, closure network, bookkeeping.
+// Two kernels, one per precision, share the per-sphere end of the step
+// (finish_step: walls, gravity, buoyancy, drag, integration, porosity
+// scatter, closure network, bookkeeping).  Every sum runs in a fixed order,
+// so the step is deterministic and needs no floating-point atomics.
 //
-// Mixed precision lists every pair from both sides and evaluates it twice
-// (bit-identical magnitudes).  The step is bound by the latency of the
-// rounds, not by arithmetic: listing each pair once and passing its result
-// to the partner through memory measured slower (the exchange and the wait
-// for it cost more than the halved rounds save).  FP64 is bound by the FP64
-// pipe, so there each pair is listed once, by its lower-index sphere (the
-// owner): the owner's warp writes the pair's result (the force on the owner
-// and n x F_t) into the partner's inbox slot, publishes that its segment is
-// done, waits until the segments owning its spheres' lower-index partners
-// have published (blocks take segments in the order they start, from a
-// counter, so every warp waited on is running and publishes before it waits
-// itself) and adds its inbox in slot order.  Every sum runs in a fixed
-// order, so the step is deterministic and needs no floating-point atomics.
+// Mixed precision (k_forces_lanes) -- positions, integrator and accumulators
+// stay FP64; the contact geometry comes from a 32-bit fixed-point shadow of
+// the positions (exact integer differences, so delta = Ri + Rj - d suffers no
+// cancellation); contact physics and tangential history run in FP32.  Every
+// integer decision (touching, bond break) is taken in IEEE double from the
+// FP64 positions whenever the fixed-point value lies within its error band of
+// the threshold, so it always equals the FP64 decision.  Every pair is listed
+// from both sides and evaluated twice (bit-identical magnitudes); one lane
+// walks one sphere's list.  The rebuild stores the spheres of each tile of
+// 1024 (in cell order) by decreasing list length, so a warp's lanes have
+// lists of about the same length, and lays the records out entry-major per
+// warp, so each step of the walk reads one contiguous line.  The kernel is
+// bound by latency (dependent chains of the contact law, the partner
+// gathers), not by arithmetic or bandwidth.
 //
-// Two precisions:
-//   FP64  -- geometry and contact physics in double.
-//   MIXED -- positions, integrator and accumulators stay FP64, the contact
-//            geometry comes from a 32-bit fixed-point shadow of the positions
-//            (exact integer differences, so delta = Ri + Rj - d suffers no
-//            cancellation), and contact physics and tangential history run in
-//            FP32.  Every integer decision (touching, bond break) is taken in
-//            IEEE double from the FP64 positions whenever the fixed-point value
-//            lies within its error band of the threshold, so it always equals
-//            the FP64 decision.  GB300 runs FP64 at ~1/60 of the FP32 rate, so
-//            the contact path holds no FP64 arithmetic and the per-particle
-//            update keeps only the FP64 additions of the integrator.
+// FP64 (k_forces_pairs) -- geometry and contact physics in double.  GB300
+// runs FP64 at two operations per SM per clock, so each pair is listed once,
+// by its lower-index sphere (the owner): the owner's warp writes the pair's
+// result (the force on the owner and n x F_t) into the partner's inbox slot,
+// publishes that its segment is done, waits until the segments owning its
+// spheres' lower-index partners have published (blocks take segments in the
+// order they start, from a counter, so every warp waited on is running and
+// publishes before it waits itself) and adds its inbox in slot order.
 #include "cgdem_internal.cuh"
 #include "tc05.cuh"
 
@@ -559,7 +551,7 @@ __device__ __forceinline__ void finish_step(
         Ri = P.w;
         mi = 1.0 / Vd.w;
       }
-      const float xf = d2f_bits(P.x), yf = d2f_bits(P.y), zf = d2f_bits(P.z);
+      const float xf = __double2float_rn(P.x), yf = __double2float_rn(P.y), zf = __double2float_rn(P.z);
       T Es, Gs, beta, mu, dt;
       if constexpr (MIXED) {
         Es = S.Es_f; Gs = S.Gs_f; beta = S.beta_f; mu = S.mu_f32; dt = S.dt_f;
@@ -646,21 +638,21 @@ __device__ __forceinline__ void finish_step(
         d.T[p] = make_double4((double)Tq.x, (double)Tq.y, (double)Tq.z, 0.0);
       } else {
         // outlet (produced sand, Eq. 40): float filter, FP64 decision
-        const bool removed = S.kind == CGDEM_CYLINDER && zf < -1.999f * d2f_bits(P.w) &&
+        const bool removed = S.kind == CGDEM_CYLINDER && zf < -1.999f * __double2float_rn(P.w) &&
                              P.z < -2.0 * P.w;
         if (removed) d.removed_step[d.id[pc][p]] = (int)m_step;
         double vx, vy, vz, wx, wy, wz;
         if constexpr (MIXED) {
           // FP32 force increments added to the FP64 state
           const float im = 1.0f / me.wa.w;
-          const float iI = d2f_bits(Wd.w);
+          const float iI = __double2float_rn(Wd.w);
           const float c = (MODE == MODE_MID ? S.dt_f : 0.5f * S.dt_f);
-          vx = Vd.x + f2d_bits(c * im * (float)F.x);
-          vy = Vd.y + f2d_bits(c * im * (float)F.y);
-          vz = Vd.z + f2d_bits(c * im * (float)F.z);
-          wx = Wd.x + f2d_bits(c * iI * (float)Tq.x);
-          wy = Wd.y + f2d_bits(c * iI * (float)Tq.y);
-          wz = Wd.z + f2d_bits(c * iI * (float)Tq.z);
+          vx = Vd.x + (double)(c * im * (float)F.x);
+          vy = Vd.y + (double)(c * im * (float)F.y);
+          vz = Vd.z + (double)(c * im * (float)F.z);
+          wx = Wd.x + (double)(c * iI * (float)Tq.x);
+          wy = Wd.y + (double)(c * iI * (float)Tq.y);
+          wz = Wd.z + (double)(c * iI * (float)Tq.z);
         } else {
           const double h = S.half_dt, im = Vd.w, iI = Wd.w;
           vx = Vd.x + h * (F.x * im);
@@ -692,8 +684,8 @@ __device__ __forceinline__ void finish_step(
           d.omg[nxt][p] = make_double4(wx, wy, wz, Wd.w);
           d.posq[nxt][p] = pqn;
           const float4 va = d.velf[cur][p], wa = d.omgf[cur][p];
-          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), va.w);
-          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), wa.w);
+          d.velf[nxt][p] = make_float4(__double2float_rn(vx), __double2float_rn(vy), __double2float_rn(vz), va.w);
+          d.omgf[nxt][p] = make_float4(__double2float_rn(wx), __double2float_rn(wy), __double2float_rn(wz), wa.w);
         } else if (removed) {
           double4 Pn = P;
           Pn.w = -P.w;
@@ -707,20 +699,20 @@ __device__ __forceinline__ void finish_step(
           d.omgf[nxt][p] = d.omgf[cur][p];
         } else {
           double x = P.x + S.dt * vx, y = P.y + S.dt * vy, z = P.z + S.dt * vz;
-          float nxf = d2f_bits(x), nyf = d2f_bits(y), nzf = d2f_bits(z);
+          float nxf = __double2float_rn(x), nyf = __double2float_rn(y), nzf = __double2float_rn(z);
           if (S.kind == CGDEM_PERIODIC_BOX) {
             const float Lf = S.L_f[0], eps = 1e-4f * Lf;
             if (nxf < eps || nxf > Lf - eps) {
               if (x >= S.L[0]) x -= S.L[0]; else if (x < 0.0) x += S.L[0];
-              nxf = d2f_bits(x);
+              nxf = __double2float_rn(x);
             }
             if (nyf < eps || nyf > Lf - eps) {
               if (y >= S.L[1]) y -= S.L[1]; else if (y < 0.0) y += S.L[1];
-              nyf = d2f_bits(y);
+              nyf = __double2float_rn(y);
             }
             if (nzf < eps || nzf > Lf - eps) {
               if (z >= S.L[2]) z -= S.L[2]; else if (z < 0.0) z += S.L[2];
-              nzf = d2f_bits(z);
+              nzf = __double2float_rn(z);
             }
           }
           d.pos[nxt][p] = make_double4(x, y, z, P.w);
@@ -747,8 +739,8 @@ __device__ __forceinline__ void finish_step(
             mf = d.omgf[cur][p].w;
           }
           d.posq[nxt][p] = pqn;
-          d.velf[nxt][p] = make_float4(d2f_bits(vx), d2f_bits(vy), d2f_bits(vz), Rf);
-          d.omgf[nxt][p] = make_float4(d2f_bits(wx), d2f_bits(wy), d2f_bits(wz), mf);
+          d.velf[nxt][p] = make_float4(__double2float_rn(vx), __double2float_rn(vy), __double2float_rn(vz), Rf);
+          d.omgf[nxt][p] = make_float4(__double2float_rn(wx), __double2float_rn(wy), __double2float_rn(wz), mf);
           const int4 ref = d.posq_ref[p];
           const float ex = (float)(int)((uint32_t)pqn.x - (uint32_t)ref.x);
           const float ey = (float)(int)((uint32_t)pqn.y - (uint32_t)ref.y);
@@ -855,14 +847,21 @@ __device__ __forceinline__ void finish_step(
   }
 }
 
-// CL: the context carries the learned closure (blocks of 128 threads; more
-// registers per thread for the closure data and the network epilogue).
+// FP64: each pair listed once, by its lower-index sphere.  Warps walk their
+// record segment in rounds of 32 entries (every lane evaluates one pair per
+// round whatever the list lengths are); each entry's owner is found by a
+// search over the lanes and its data broadcast, and a round's contributions
+// are summed per sphere by a segmented scan in list order.  The owner's warp
+// passes the pair's result to the partner through the partner's inbox (see
+// the file comment).  CL: the context carries the learned closure (blocks of
+// 128 threads; more registers per thread for the closure data and the network
+// epilogue).
 // h_next: conditional handle of the next step's rebuild node when the launch
 // sits in a CUDA graph (0 otherwise); the step's last warp sets it.
-template <bool MIXED, int MODE, bool CL>
+template <int MODE, bool CL>
 __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
-    k_forces(Dev d, cudaGraphConditionalHandle h_next) {
-  using T = typename std::conditional<MIXED, float, double>::type;
+    k_forces_pairs(Dev d, cudaGraphConditionalHandle h_next) {
+  using T = double;
   Ctl* ctl = d.ctl;
   const int cur = ctl->cur;
   const int nxt = cur ^ 1;
@@ -874,14 +873,13 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   const int ce = d.sp[0].couple_every;
   const bool couple_next = ce == 1 || (unsigned)(m_step % ce) == 0u;
   const int lane = threadIdx.x & 31;
-  // FP64: blocks take their segments in the order they start (a counter),
-  // so a warp only ever waits for warps that are already running
-  constexpr bool HALF = !MIXED;  // FP64: every pair listed once (see the file comment)
+  // blocks take their segments in the order they start (a counter), so a
+  // warp only ever waits for warps that are already running
   const uint32_t epoch = ctl->epoch + 1u;  // value of a segment flag once its pairs are done
   __shared__ int blk_s;
   __shared__ unsigned bk_n;
   if (threadIdx.x == 0) {
-    blk_s = HALF ? atomicAdd(&ctl->blk_next, 1) : (int)blockIdx.x;
+    blk_s = atomicAdd(&ctl->blk_next, 1);
     bk_n = 0u;
   }
   __syncthreads();
@@ -933,39 +931,19 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   __shared__ unsigned bk_c[FORCE_BLOCK_MAX / 32];
 
   // ---- own particle, contact phase ----
-  Owner<MIXED> me;
+  Owner<false> me;
   int si = 0;
   if (valid) si = d.sample[pc][p];
-  if constexpr (MIXED) {
-    if (valid) {
-      me.pq = d.posq[cur][p];
-      me.va = d.velf[cur][p];
-      me.wa = d.omgf[cur][p];
-    } else {
-      me.pq = make_int4(0, 0, 0, 0);
-      me.va = make_float4(0, 0, 0, 0);
-      me.wa = make_float4(0, 0, 0, 0);
-    }
+  if (valid) {
+    me.P = d.pos[cur][p];
+    me.V = d.vel[cur][p];
+    me.W = d.omg[cur][p];
   } else {
-    if (valid) {
-      me.P = d.pos[cur][p];
-      me.V = d.vel[cur][p];
-      me.W = d.omg[cur][p];
-    } else {
-      me.P = make_double4(0, 0, 0, 0);
-      me.V = make_double4(0, 0, 0, 1);
-      me.W = make_double4(0, 0, 0, 1);
-    }
+    me.P = make_double4(0, 0, 0, 0);
+    me.V = make_double4(0, 0, 0, 1);
+    me.W = make_double4(0, 0, 0, 1);
   }
-  if (MIXED && valid) {
-    // the epilogue's per-sphere data: its latency overlaps the contact rounds
-    prefetch_l1(&d.pos[cur][p]);
-    prefetch_l1(&d.vel[cur][p]);
-    prefetch_l1(&d.omg[cur][p]);
-    prefetch_l1(&d.posq_ref[p]);
-    prefetch_l1(&d.fcell[pc][p]);
-    prefetch_l1(&d.vq[pc][p]);
-  }
+
   const uint32_t ncnt = owner_lane ? d.cnt[rc][p] : 0u;
   const uint32_t seg = (uint32_t)wbase * (uint32_t)d.cap;
   const uint32_t lo0 = owner_lane ? d.roff[rc][p] - seg : 0u;
@@ -974,29 +952,10 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   const uint32_t lo = owner_lane ? lo0 : total;
   V3<T> F = v3<T>(0, 0, 0), Tq = v3<T>(0, 0, 0);
   T Zacc = 0, Dacc = 0, Cacc = 0;  // closure data: active contacts, summed overlap, bond capacity
-  // mixed: each lane's record for the next round is loaded one round ahead
-  uint4 rnext = make_uint4(0u, 0u, 0u, 0u);
-  if (MIXED && lane < (int)total) rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + lane];
-  // mixed: and the partner's shadows one round ahead, in registers (the
-  // closure variant, short of registers, brings them into L1 instead)
-  constexpr bool RPF = MIXED && !CL;
-  int4 pq_nx = make_int4(0, 0, 0, 0);
-  float4 pa_nx = make_float4(0.f, 0.f, 0.f, 0.f), pb_nx = pa_nx;
-  if (RPF && lane < (int)total) {
-    const uint32_t q0 = rnext.x & REC_IDX;
-    pq_nx = d.posq[cur][q0];
-    pa_nx = d.velf[cur][q0];
-    pb_nx = d.omgf[cur][q0];
-  }
 
   for (uint32_t base = 0; base < total; base += 32) {
     const uint32_t e = base + lane;
     const bool has = e < total;
-    uint4 rcur = rnext;
-    const int4 qq_c = pq_nx;
-    const float4 qa_c = pa_nx, qb_c = pb_nx;
-    if (MIXED && e + 32u < total)
-      rnext = reinterpret_cast<const uint4*>(d.rec[rc])[(size_t)seg + e + 32u];
     // owner lane: the last lane whose first entry is <= e
     int own = 0;
 #pragma unroll
@@ -1008,233 +967,108 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     const int os = __shfl_sync(FULL, si, own);
     const float o_cg = use_c ? __shfl_sync(FULL, my_c.y, own) : 1.0f;
     T e_z = 0, e_d = 0, e_c = 0;
-    Owner<MIXED> o;
-    if constexpr (MIXED) {
-      o.pq.x = __shfl_sync(FULL, me.pq.x, own);
-      o.pq.y = __shfl_sync(FULL, me.pq.y, own);
-      o.pq.z = __shfl_sync(FULL, me.pq.z, own);
-      o.pq.w = __shfl_sync(FULL, me.pq.w, own);
-      o.va.x = __shfl_sync(FULL, me.va.x, own);
-      o.va.y = __shfl_sync(FULL, me.va.y, own);
-      o.va.z = __shfl_sync(FULL, me.va.z, own);
-      o.va.w = __shfl_sync(FULL, me.va.w, own);
-      o.wa.x = __shfl_sync(FULL, me.wa.x, own);
-      o.wa.y = __shfl_sync(FULL, me.wa.y, own);
-      o.wa.z = __shfl_sync(FULL, me.wa.z, own);
-      o.wa.w = __shfl_sync(FULL, me.wa.w, own);
-    } else {
-      o.P.x = __shfl_sync(FULL, me.P.x, own);
-      o.P.y = __shfl_sync(FULL, me.P.y, own);
-      o.P.z = __shfl_sync(FULL, me.P.z, own);
-      o.P.w = __shfl_sync(FULL, me.P.w, own);
-      o.V.x = __shfl_sync(FULL, me.V.x, own);
-      o.V.y = __shfl_sync(FULL, me.V.y, own);
-      o.V.z = __shfl_sync(FULL, me.V.z, own);
-      o.V.w = __shfl_sync(FULL, me.V.w, own);
-      o.W.x = __shfl_sync(FULL, me.W.x, own);
-      o.W.y = __shfl_sync(FULL, me.W.y, own);
-      o.W.z = __shfl_sync(FULL, me.W.z, own);
-    }
+    Owner<false> o;
+    o.P.x = __shfl_sync(FULL, me.P.x, own);
+    o.P.y = __shfl_sync(FULL, me.P.y, own);
+    o.P.z = __shfl_sync(FULL, me.P.z, own);
+    o.P.w = __shfl_sync(FULL, me.P.w, own);
+    o.V.x = __shfl_sync(FULL, me.V.x, own);
+    o.V.y = __shfl_sync(FULL, me.V.y, own);
+    o.V.z = __shfl_sync(FULL, me.V.z, own);
+    o.V.w = __shfl_sync(FULL, me.V.w, own);
+    o.W.x = __shfl_sync(FULL, me.W.x, own);
+    o.W.y = __shfl_sync(FULL, me.W.y, own);
+    o.W.z = __shfl_sync(FULL, me.W.z, own);
+
     V3<T> Fc = v3<T>(0, 0, 0), Tc = v3<T>(0, 0, 0);
     if (has) {
       const SampleDev& S = d.sp[os];
       const size_t idx = (size_t)seg + e;
-      const uint32_t slot = HALF ? d.rslot[idx] : 0xffffffffu;  // the pair's slot in the partner's inbox
+      const uint32_t slot = d.rslot[idx];  // the pair's slot in the partner's inbox
       const int owner_p = wbase + own;
       uint32_t pf;
       V3<T> xi;
-      if constexpr (MIXED) {
-        pf = rcur.x;
-        xi = v3<T>(__uint_as_float(rcur.y), __uint_as_float(rcur.z), __uint_as_float(rcur.w));
-      } else {
-        const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + idx;
-        const int4 h0 = *reinterpret_cast<const int4*>(rr);
-        const double2 h1 = *(reinterpret_cast<const double2*>(rr) + 1);
-        pf = (uint32_t)h0.x;
-        xi = v3<T>(__hiloint2double(h0.w, h0.z), h1.x, h1.y);
-      }
+      const RecD* rr = reinterpret_cast<const RecD*>(d.rec[rc]) + idx;
+      const int4 h0 = *reinterpret_cast<const int4*>(rr);
+      const double2 h1 = *(reinterpret_cast<const double2*>(rr) + 1);
+      pf = (uint32_t)h0.x;
+      xi = v3<T>(__hiloint2double(h0.w, h0.z), h1.x, h1.y);
+
       const int q = (int)(pf & REC_IDX);
       bool bonded = (pf & REC_BOND) != 0u;
       const bool had_state = (pf & (REC_BOND | REC_ACTIVE)) != 0u || xi.x != T(0) ||
                              xi.y != T(0) || xi.z != T(0);
       bool act = false;
-      if constexpr (MIXED) {
-        const int4 qq = RPF ? qq_c : d.posq[cur][q];
-        const float4 qa = RPF ? qa_c : d.velf[cur][q];
-        const float4 qb = RPF ? qb_c : d.omgf[cur][q];
-        if (qq.w > 0 && o.pq.w > 0) {
-          const int dx = (int)((uint32_t)qq.x - (uint32_t)o.pq.x);
-          const int dy = (int)((uint32_t)qq.y - (uint32_t)o.pq.y);
-          const int dz = (int)((uint32_t)qq.z - (uint32_t)o.pq.z);
-          const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
-                                        (unsigned long long)((long long)dy * dy) +
-                                        (unsigned long long)((long long)dz * dz);
-          const unsigned Sq = (unsigned)o.pq.w + (unsigned)qq.w;
-          const unsigned long long S2 = (unsigned long long)Sq * Sq;
-          const unsigned long long band = 16ull * Sq + 256ull;
-          bool touching = false, need_exact = false;
-          if (d2 > S2 + band) touching = false;
-          else if (d2 + band < S2) touching = true;
-          else need_exact = true;
-          if (bonded || touching || need_exact) {
-            const float d2f = u64_to_f(d2);
-            const float invd = rsqrtf(d2f);
-            const float dn = d2f * invd;
-            (void)0;
-            float du;
-            if (d2 < (1ull << 62))
-              du = __fdividef(s64_to_f((long long)S2 - (long long)d2), (float)Sq + dn);
-            else
-              du = (float)Sq - dn;
-            const float delta = du * S.dq_f;
-            const V3<float> n = v3<float>(dx * invd, dy * invd, dz * invd);
-            const float Ri = o.va.w, Rj = qa.w, mi = o.wa.w, mj = qb.w;
-            const float Rs = __fdividef(Ri * Rj, Ri + Rj);
-            // surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure
-            float gam_f = S.gamma_f;
-            double gam_d = S.gamma;
-            if (use_c && bonded) {
-              const float qcg = d.clc[cur][q].y;
-              gam_f = S.gamma_f * sqrtf(o_cg * qcg);
-              gam_d = S.gamma * sqrt((double)o_cg * (double)qcg);
-            }
-            double d2e = 0.0, Se = 0.0;
-            bool have_exact = false;
-            if (need_exact) {
-              exact_geometry(S, d.pos[cur][owner_p], d.pos[cur][q], &d2e, &Se);
-              have_exact = true;
-              touching = d2e < __dmul_rn(Se, Se);
-            }
-            if (bonded) {
-              bool broken;
-              float dC = 0.0f, bandf = 4.0f * S.dq_f;
-              if (gam_f > 0.f) {
-                const float xs = m_cbrt(__fdividef(PI_F * PI_F * gam_f * gam_f * Rs, S.Es_f * S.Es_f));
-                dC = -0.57235712127666594f * xs;
-                bandf += 2e-5f * fabsf(dC);
-              }
-              if (delta < dC - bandf) {
-                broken = true;
-              } else if (delta > dC + bandf) {
-                broken = false;
-              } else {
-                const double4 A = d.pos[cur][owner_p], B = d.pos[cur][q];
-                if (!have_exact) {
-                  exact_geometry(S, A, B, &d2e, &Se);
-                  have_exact = true;
-                  touching = d2e < __dmul_rn(Se, Se);
-                }
-                const double Rid = fabs(A.w), Rjd = fabs(B.w);
-                const double Rsd = __dmul_rn(Rid, Rjd) / __dadd_rn(Rid, Rjd);
-                broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, gam_d);
-              }
-              if (broken) bonded = false;
-            }
-            act = bonded || touching;
-            if (act) {
-              const float ms = __fdividef(mi * mj, mi + mj);
-              const V3<float> vi = v3<float>(o.va.x, o.va.y, o.va.z);
-              const V3<float> wi = v3<float>(o.wa.x, o.wa.y, o.wa.z);
-              const V3<float> vrel = v3<float>(qa.x - vi.x, qa.y - vi.y, qa.z - vi.z);
-              const V3<float> rw = v3<float>(Ri * wi.x + Rj * qb.x, Ri * wi.y + Rj * qb.y,
-                                             Ri * wi.z + Rj * qb.z);
-              const V3<float> rwn = cross3(rw, n);
-              const V3<float> vc = v3<float>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
-              V3<float> Fi, Ft;
-              V3<float> xif = v3<float>((float)xi.x, (float)xi.y, (float)xi.z);
-              contact_law<float>(delta, n, vrel, vc, Rs, ms, gam_f, bonded, S.Es_f, S.Gs_f,
-                                 S.beta_f, S.mu_f32, S.dt_f, S.coulomb_mode, xif, Fi, Ft);
-              xi = v3<T>(xif.x, xif.y, xif.z);
-              const V3<float> nFt = cross3(n, Ft);
-              Fc = v3<T>(Fi.x, Fi.y, Fi.z);
-              Tc = v3<T>(Ri * nFt.x, Ri * nFt.y, Ri * nFt.z);
-              if (feat) {
-                e_z = 1;
-                e_d = delta;
-                e_c = bonded ? 0.5f * 3.0f * PI_F * gam_f * Rs : 0.0f;
-              }
-            }
-          }
+      const double4 Q = d.pos[cur][q];
+      if (Q.w > 0.0 && o.P.w > 0.0) {
+        double dx = __dsub_rn(Q.x, o.P.x), dy = __dsub_rn(Q.y, o.P.y), dz = __dsub_rn(Q.z, o.P.z);
+        if (S.kind == CGDEM_PERIODIC_BOX) {
+          dx = min_image(dx, S.L[0]);
+          dy = min_image(dy, S.L[1]);
+          dz = min_image(dz, S.L[2]);
         }
-      } else {
-        const double4 Q = d.pos[cur][q];
-        if (Q.w > 0.0 && o.P.w > 0.0) {
-          double dx = __dsub_rn(Q.x, o.P.x), dy = __dsub_rn(Q.y, o.P.y), dz = __dsub_rn(Q.z, o.P.z);
-          if (S.kind == CGDEM_PERIODIC_BOX) {
-            dx = min_image(dx, S.L[0]);
-            dy = min_image(dy, S.L[1]);
-            dz = min_image(dz, S.L[2]);
-          }
-          const double d2 =
-              __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-          const double Sd = __dadd_rn(o.P.w, Q.w);
-          const bool touching = d2 < __dmul_rn(Sd, Sd);
-          if (bonded || touching) {
-            const double dist = sqrt(d2);
-            const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
-            const double delta = __dsub_rn(Sd, dist);
-            double gam_d = S.gamma;  // gamma sqrt(c_g,i c_g,j) under the closure
-            if (use_c && bonded) gam_d = S.gamma * sqrt((double)o_cg * (double)d.clc[cur][q].y);
-            if (bonded && bond_breaks_exact(delta, Rs, S.Es, gam_d)) bonded = false;
-            act = bonded || touching;
-            if (act && dist > 0.0) {
-              const double4 QV = d.vel[cur][q];
-              const double4 QW = d.omg[cur][q];
-              const double Ri = o.P.w, Rj = Q.w;
-              const double idist = 1.0 / dist;  // one FP64 division instead of three
-              const V3<double> n = v3<double>(dx * idist, dy * idist, dz * idist);
-              // m* = m_i m_j / (m_i + m_j) = 1 / (1/m_i + 1/m_j), from the stored 1/m
-              const double ms = 1.0 / (o.V.w + QV.w);
-              const V3<double> vrel = v3<double>(QV.x - o.V.x, QV.y - o.V.y, QV.z - o.V.z);
-              const V3<double> rw = v3<double>(Ri * o.W.x + Rj * QW.x, Ri * o.W.y + Rj * QW.y,
-                                               Ri * o.W.z + Rj * QW.z);
-              const V3<double> rwn = cross3(rw, n);
-              const V3<double> vc = v3<double>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
-              V3<double> Fi, Ft;
-              V3<double> xid = v3<double>((double)xi.x, (double)xi.y, (double)xi.z);
-              contact_law<double>(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S.Es, S.Gs, S.beta,
-                                  S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft);
-              xi = v3<T>(xid.x, xid.y, xid.z);
-              const V3<double> nFt = cross3(n, Ft);
-              Fc = v3<T>(Fi.x, Fi.y, Fi.z);
-              Tc = v3<T>(nFt.x, nFt.y, nFt.z);
-              if (feat) {
-                e_z = 1;
-                e_d = delta;
-                e_c = bonded ? 0.5 * 3.0 * PI_D * gam_d * Rs : 0.0;
-              }
-            } else if (act) {
-              act = false;  // coincident centres: no normal defined
+        const double d2 =
+            __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double Sd = __dadd_rn(o.P.w, Q.w);
+        const bool touching = d2 < __dmul_rn(Sd, Sd);
+        if (bonded || touching) {
+          const double dist = sqrt(d2);
+          const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
+          const double delta = __dsub_rn(Sd, dist);
+          double gam_d = S.gamma;  // gamma sqrt(c_g,i c_g,j) under the closure
+          if (use_c && bonded) gam_d = S.gamma * sqrt((double)o_cg * (double)d.clc[cur][q].y);
+          if (bonded && bond_breaks_exact(delta, Rs, S.Es, gam_d)) bonded = false;
+          act = bonded || touching;
+          if (act && dist > 0.0) {
+            const double4 QV = d.vel[cur][q];
+            const double4 QW = d.omg[cur][q];
+            const double Ri = o.P.w, Rj = Q.w;
+            const double idist = 1.0 / dist;  // one FP64 division instead of three
+            const V3<double> n = v3<double>(dx * idist, dy * idist, dz * idist);
+            // m* = m_i m_j / (m_i + m_j) = 1 / (1/m_i + 1/m_j), from the stored 1/m
+            const double ms = 1.0 / (o.V.w + QV.w);
+            const V3<double> vrel = v3<double>(QV.x - o.V.x, QV.y - o.V.y, QV.z - o.V.z);
+            const V3<double> rw = v3<double>(Ri * o.W.x + Rj * QW.x, Ri * o.W.y + Rj * QW.y,
+                                             Ri * o.W.z + Rj * QW.z);
+            const V3<double> rwn = cross3(rw, n);
+            const V3<double> vc = v3<double>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
+            V3<double> Fi, Ft;
+            V3<double> xid = v3<double>((double)xi.x, (double)xi.y, (double)xi.z);
+            contact_law<double>(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S.Es, S.Gs, S.beta,
+                                S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft);
+            xi = v3<T>(xid.x, xid.y, xid.z);
+            const V3<double> nFt = cross3(n, Ft);
+            Fc = v3<T>(Fi.x, Fi.y, Fi.z);
+            Tc = v3<T>(nFt.x, nFt.y, nFt.z);
+            if (feat) {
+              e_z = 1;
+              e_d = delta;
+              e_c = bonded ? 0.5 * 3.0 * PI_D * gam_d * Rs : 0.0;
             }
+          } else if (act) {
+            act = false;  // coincident centres: no normal defined
           }
         }
       }
+
       // write the record back when its state changed
       if (act) {
         const uint32_t npf = (uint32_t)q | REC_ACTIVE | (bonded ? REC_BOND : 0u);
-        if constexpr (MIXED) {
-          reinterpret_cast<uint4*>(d.rec[rc])[idx] =
-              make_uint4(npf, __float_as_uint((float)xi.x), __float_as_uint((float)xi.y),
-                         __float_as_uint((float)xi.z));
-        } else {
-          RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
-          const double xx = (double)xi.x;
-          *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, __double2loint(xx), __double2hiint(xx));
-          *(reinterpret_cast<double2*>(rr) + 1) = make_double2((double)xi.y, (double)xi.z);
-        }
+        RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
+        const double xx = (double)xi.x;
+        *reinterpret_cast<int4*>(rr) = make_int4((int)npf, 0, __double2loint(xx), __double2hiint(xx));
+        *(reinterpret_cast<double2*>(rr) + 1) = make_double2((double)xi.y, (double)xi.z);
+
       } else if (had_state) {
-        if constexpr (MIXED) {
-          reinterpret_cast<uint4*>(d.rec[rc])[idx] = make_uint4((uint32_t)q, 0u, 0u, 0u);
-        } else {
-          RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
-          *reinterpret_cast<int4*>(rr) = make_int4(q, 0, 0, 0);
-          *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
-        }
+        RecD* rr = reinterpret_cast<RecD*>(d.rec[rc]) + idx;
+        *reinterpret_cast<int4*>(rr) = make_int4(q, 0, 0, 0);
+        *(reinterpret_cast<double2*>(rr) + 1) = make_double2(0.0, 0.0);
+
       }
       // FP64: the pair's result for the partner (zeros when inactive), into
       // its slot of the partner's inbox: the force on the owner and n x F_t
       // (the torque on either sphere divided by its radius)
-      if constexpr (HALF) {
+      {
         if (slot < (uint32_t)d.cap) {
           const size_t ib = (size_t)slot * d.Npad + q;
           double4* o4 = d.inbox + 2 * ib;
@@ -1242,19 +1076,6 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           o4[1] = make_double4(Tc.y, Tc.z, 0.0, 0.0);
           if (feat) d.inbox_cl[ib] = make_float4((float)e_z, (float)e_d, (float)e_c, 0.f);
         }
-      }
-    }
-    if (MIXED && e + 32u < total) {
-      // the next round's partner, loaded while this round's sums run
-      const uint32_t qn = rnext.x & REC_IDX;
-      if constexpr (RPF) {
-        pq_nx = d.posq[cur][qn];
-        pa_nx = d.velf[cur][qn];
-        pb_nx = d.omgf[cur][qn];
-      } else {
-        prefetch_l1(&d.posq[cur][qn]);
-        prefetch_l1(&d.velf[cur][qn]);
-        prefetch_l1(&d.omgf[cur][qn]);
       }
     }
     // contributions of this round to their owners: a segmented inclusive
@@ -1328,7 +1149,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   // ---- FP64: the pairs owned by lower-index partners ----
   // publish this segment, then wait for the segments owning the lowest
   // partners of its spheres (bounded: a wait that runs out reports a timeout)
-  if constexpr (HALF) {
+  {
     __threadfence();
     __syncwarp();
     if (lane == 0) st_release_u32(&d.seg_flag[sg], epoch);
@@ -1376,10 +1197,11 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     }
   }
 
-  finish_step<MIXED, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
+  finish_step<false, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
                                F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
                                &bk_n, bk_s, bk_m, bk_c, h_next);
 }
+
 
 // Mixed precision: one lane per sphere (ppw = 32), or two lanes per sphere
 // taking alternate entries of its list (ppw = 16, for samples too small to
@@ -1677,18 +1499,18 @@ void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphC
       else if (mode == MODE_MID) k_forces_lanes<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
       else k_forces_lanes<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
     } else {
-      if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
-      else if (mode == MODE_MID) k_forces<false, MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
-      else k_forces<false, MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
+      if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
+      else if (mode == MODE_MID) k_forces_pairs<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
+      else k_forces_pairs<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
     }
   } else if (d.mixed) {
     if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
     else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
     else k_forces_lanes<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
   } else {
-    if (mode == MODE_FORCES) k_forces<false, MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
-    else if (mode == MODE_MID) k_forces<false, MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
-    else k_forces<false, MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
+    if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
+    else if (mode == MODE_MID) k_forces_pairs<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
+    else k_forces_pairs<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
   }
   if (mode == MODE_CANON) k_after_canon<<<1, 1, 0, s>>>(d);
 }
