@@ -372,48 +372,14 @@ def time_steps(ctx, torch, K, barrier):
     return e0.elapsed_time(e1) / 1e3
 
 
-def oracle_baseline(s, dt, budget_s=15.0, n_sub=20000):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    the n_sub spheres nearest to a point in the bed (a coherent block of the
-    same packing, walls and outlet included), timed for ~budget_s."""
+def oracle_sample(s, n_sub, dt):
+    """The FP64 CPU oracle on the n_sub spheres nearest to a point in the bed
+    (a coherent block of the same packing, walls and outlet included)."""
     import oracle as O
     centre = np.array([0.0, 0.0, 0.5 * float(s.extra.get("h_bed", s.domain["H"]))])
-    d2 = ((s.x - centre) ** 2).sum(1)
-    idx = np.sort(np.argsort(d2)[:min(n_sub, len(s.R))])
-    m = s.material
-    d = s.domain
-    p = O.make_params(rho=m["rho"], E=m["E"], nu=m["nu"], e=m["e"], mu=m["mu"], gamma=m["gamma"],
-                      rho_f=s.fluid["rho_f"], mu_f=s.fluid["mu_f"], use_drag=1, use_buoyancy=1,
-                      kind=d["kind"], L=d["L"], Rc=d["Rc"], H=d["H"], r_out=d["r_out"], g=s.g,
-                      dt=dt, nf=s.grid.nf, f_lo=s.grid.lo, hf=s.grid.h, inv_hf=s.grid.inv_h,
-                      V_cell=s.grid.V_cell, n_min=0.2)
-    sim = O.Sim(p, s.x[idx], s.v[idx], s.w[idx], s.R[idx], s.Us)
-    sim.bond_touching()
-    sim.couple_fluid()
-    sim.compute_forces()
-    sim.step(1)
-    steps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        sim.step(1)
-        steps += 1
-    el = time.perf_counter() - t0
-    return {"value": len(idx) * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(idx)} spheres nearest the bed centre of the same packed cylinder, "
-                      f"{steps} FP64 oracle steps in {el:.1f} s, single thread"}
-
-
-def run_reference(args):
-    rank, world, local = dist_env()
-    if rank != 0:
-        return
-    s = make_workload(1)
-    dt, _ = step_params(s)
-    K, W = max(1, args.steps), max(0, args.warmup)
-    # bounded sample per step so that the whole K + W run ends in about a minute
-    n_sub = int(min(len(s.R), max(1000, 8.0e6 / (K + W))))
-    import oracle as O
-    centre = np.array([0.0, 0.0, 0.5 * float(s.extra.get("h_bed", s.domain["H"]))])
-    idx = np.sort(np.argsort(((s.x - centre) ** 2).sum(1))[:n_sub])
+    if s.domain["kind"] == 1:  # mid-bed, away from the axis and its cavity
+        centre[0] = 0.5 * s.domain["Rc"]
+    idx = np.sort(np.argsort(((s.x - centre) ** 2).sum(1))[:min(n_sub, len(s.R))])
     m, d = s.material, s.domain
     p = O.make_params(rho=m["rho"], E=m["E"], nu=m["nu"], e=m["e"], mu=m["mu"], gamma=m["gamma"],
                       rho_f=s.fluid["rho_f"], mu_f=s.fluid["mu_f"], use_drag=1, use_buoyancy=1,
@@ -424,6 +390,48 @@ def run_reference(args):
     sim.bond_touching()
     sim.couple_fluid()
     sim.compute_forces()
+    return sim, len(idx)
+
+
+def oracle_baseline(s, dt, budget_s=8.0, n_sub=20000):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload
+    (the n_sub spheres nearest a mid-bed point), timed for ~budget_s on one
+    host thread and on all of them (its pair evaluations and per-particle
+    loops are OpenMP loops; the results do not depend on the thread count)."""
+    import oracle as O
+    out = {}
+    nmax = O.set_threads(os.cpu_count() or 1)
+    for label, t in (("single_thread", 1), ("all_cores", nmax)):
+        O.set_threads(t)
+        sim, n = oracle_sample(s, n_sub, dt)
+        sim.step(1)
+        steps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            sim.step(1)
+            steps += 1
+        el = time.perf_counter() - t0
+        out[label] = {"value": n * steps / el, "threads": t, "steps": steps, "seconds": el}
+    O.set_threads(nmax)
+    return {"value": out["all_cores"]["value"], "unit": UNIT, "cores": nmax, "kind": "oracle",
+            "sample": f"{n_sub} spheres nearest a mid-bed point of the same cylinder, FP64 oracle steps "
+                      f"for ~{budget_s:.0f} s on all {nmax} host threads and on one",
+            "single_thread": out["single_thread"], "all_cores": out["all_cores"]}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on all host
+    cores, each step a bounded sample of the headline workload (the spheres
+    nearest a mid-bed point) sized so the K + W steps end in about a minute."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    s = make_workload(1)
+    dt, _ = step_params(s)
+    K, W = max(1, args.steps), max(0, args.warmup)
+    cores = O.set_threads(os.cpu_count() or 1)
+    n_sub = int(min(len(s.R), max(1000, 4.0e7 / (K + W))))
+    sim, n_sub = oracle_sample(s, n_sub, dt)
     if W:
         sim.step(W)
     t0 = time.perf_counter()
@@ -435,8 +443,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + " (FP64 CPU oracle on a bounded block)",
                        "sample_spheres": n_sub},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n_sub} spheres nearest the bed centre, {K} timed steps"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sub} spheres nearest a mid-bed point, {K} timed steps"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

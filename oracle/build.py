@@ -22,7 +22,9 @@ def build(force: bool = False) -> str:
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-D_GNU_SOURCE", "-Wall", "-o", tmp, SRC, "-lm"]
-    subprocess.check_call(cmd)
+    # host threads for the pair evaluations when the compiler has OpenMP
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+        subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
 

@@ -34,6 +34,9 @@
 #include "cgdem_oracle.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -436,6 +439,7 @@ struct ora_sim {
     uint64_t* vf;
     double* Us;
     double* Fscale; /* per particle: sum of the magnitudes of every force term */
+    double* Fnet;   /* per particle: sum of the magnitudes of its contact, wall and body force vectors */
     int64_t ncell_f;
     int64_t step;
     double produced;
@@ -474,6 +478,7 @@ ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const doubl
     s->removed_step = (int64_t*)calloc(n3, sizeof(int64_t));
     s->wall_xi = (double*)calloc(n3 * 3, sizeof(double));
     s->Fscale = (double*)calloc(n3, sizeof(double));
+    s->Fnet = (double*)calloc(n3, sizeof(double));
     s->cd = (double*)calloc(n3, sizeof(double));
     s->cg = (double*)calloc(n3, sizeof(double));
     s->cdata = (double*)calloc(n3 * ORA_CL_COLS, sizeof(double));
@@ -502,7 +507,7 @@ void ora_destroy(ora_sim* s) {
     if (!s) return;
     free(s->x); free(s->v); free(s->w); free(s->F); free(s->T);
     free(s->R); free(s->m); free(s->I); free(s->active); free(s->removed_step);
-    free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us); free(s->Fscale);
+    free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us); free(s->Fscale); free(s->Fnet);
     free(s->cd); free(s->cg); free(s->cdata);
     free(s);
 }
@@ -591,6 +596,21 @@ static void find_pairs(const ora_params* p, int64_t n, const double* x, const do
         next[i] = head[c];
         head[c] = i;
     }
+    /* each thread collects the pairs of its spheres; the lists are joined in
+       thread order (the callers sort the pairs, so the order is immaterial) */
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    pairlist* part = (pairlist*)calloc((size_t)nthr, sizeof(pairlist));
+#pragma omp parallel num_threads(nthr)
+    {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    pairlist* mine = &part[tid];
+#pragma omp for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
         if (active && !active[i]) continue;
         for (int dz = -1; dz <= 1; ++dz)
@@ -616,10 +636,17 @@ static void find_pairs(const ora_params* p, int64_t n, const double* x, const do
                         }
                         double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                         double S = R[i] + R[j] + skin;
-                        if (d2 < S * S) pl_push(out, (int32_t)i, (int32_t)j);
+                        if (d2 < S * S) pl_push(mine, (int32_t)i, (int32_t)j);
                     }
                 }
     }
+    }
+    for (int t = 0; t < nthr; ++t) {
+        for (int64_t k = 0; k < part[t].n; ++k) pl_push(out, part[t].pi[k], part[t].pj[k]);
+        free(part[t].pi);
+        free(part[t].pj);
+    }
+    free(part);
     free(head);
     free(next);
     free(cidx);
@@ -739,6 +766,7 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
                          &sc))
             continue;
         s->Fscale[i] += sc;
+        s->Fnet[i] += sqrt(dot(F, F));
         double nFt[3];
         cross(n, Ft, nFt);
         for (int k = 0; k < 3; ++k) {
@@ -748,12 +776,20 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
     }
 }
 
+/* one pair's evaluation, kept until the results are summed in pair order */
+typedef struct {
+    ora_rec r;
+    double Fi[3], Ti[3], Tj[3], sc, delta, gamma;
+    int act;
+} pair_eval_out;
+
 int ora_compute_forces(ora_sim* s) {
     const ora_params* p = &s->p;
     int64_t n = s->n;
     memset(s->F, 0, sizeof(double) * 3 * (size_t)n);
     memset(s->T, 0, sizeof(double) * 3 * (size_t)n);
     memset(s->Fscale, 0, sizeof(double) * (size_t)n);
+    memset(s->Fnet, 0, sizeof(double) * (size_t)n);
     memset(s->cdata, 0, sizeof(double) * ORA_CL_COLS * (size_t)n);
 
     /* candidates: touching pairs plus surviving bonded records */
@@ -769,43 +805,62 @@ int ora_compute_forces(ora_sim* s) {
         pr[2 * k + 1] = l.pj[k];
     }
     qsort(pr, (size_t)l.n, 2 * sizeof(int32_t), pair_cmp);
-    ora_rec* nrec = (ora_rec*)calloc((size_t)(l.n > 0 ? l.n : 1), sizeof(ora_rec));
-    int64_t nn = 0;
+    int64_t np = 0; /* distinct pairs, in order */
     for (int64_t k = 0; k < l.n; ++k) {
         if (k > 0 && pr[2 * k] == pr[2 * k - 2] && pr[2 * k + 1] == pr[2 * k - 1]) continue;
+        pr[2 * np] = pr[2 * k];
+        pr[2 * np + 1] = pr[2 * k + 1];
+        np++;
+    }
+    /* every pair on its own (each reads the state and its own old record) ... */
+    pair_eval_out* ev = (pair_eval_out*)calloc((size_t)(np > 0 ? np : 1), sizeof(pair_eval_out));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < np; ++k) {
         int32_t i = pr[2 * k], j = pr[2 * k + 1];
+        pair_eval_out* e = &ev[k];
         const ora_rec* old = find_rec(s->rec, s->nrec, i, j);
         ora_rec r = {i, j, old ? old->bonded : 0, 0, {0, 0, 0}};
         if (old) memcpy(r.xi, old->xi, sizeof(r.xi));
-        double Fi[3], Ti[3], Tj[3], sc = 0.0, delta = 0.0;
         /* surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure */
-        double gamma = s->closure ? p->gamma * sqrt(s->cg[i] * s->cg[j]) : p->gamma;
-        int act = pair_eval(p, gamma, &s->x[3 * i], &s->v[3 * i], &s->w[3 * i], s->R[i], s->m[i],
-                            &s->x[3 * j], &s->v[3 * j], &s->w[3 * j], s->R[j], s->m[j], r.xi,
-                            &r.bonded, Fi, Ti, Tj, NULL, NULL, &delta, &sc);
-        if (!act) continue;
+        e->gamma = s->closure ? p->gamma * sqrt(s->cg[i] * s->cg[j]) : p->gamma;
+        e->act = pair_eval(p, e->gamma, &s->x[3 * i], &s->v[3 * i], &s->w[3 * i], s->R[i], s->m[i],
+                           &s->x[3 * j], &s->v[3 * j], &s->w[3 * j], s->R[j], s->m[j], r.xi,
+                           &r.bonded, e->Fi, e->Ti, e->Tj, NULL, NULL, &e->delta, &e->sc);
+        e->r = r;
+    }
+    /* ... then their sums, in pair order */
+    ora_rec* nrec = (ora_rec*)calloc((size_t)(np > 0 ? np : 1), sizeof(ora_rec));
+    int64_t nn = 0;
+    for (int64_t k = 0; k < np; ++k) {
+        const pair_eval_out* e = &ev[k];
+        if (!e->act) continue;
+        int32_t i = e->r.i, j = e->r.j;
         /* what the closure measures: coordination, summed overlap, bond capacity */
         double* ci = &s->cdata[ORA_CL_COLS * i];
         double* cj = &s->cdata[ORA_CL_COLS * j];
         ci[3] += 1.0;
         cj[3] += 1.0;
-        ci[4] += delta;
-        cj[4] += delta;
-        if (r.bonded) {
-            double half_cap = 0.5 * 3.0 * M_PI * gamma * (s->R[i] * s->R[j] / (s->R[i] + s->R[j]));
+        ci[4] += e->delta;
+        cj[4] += e->delta;
+        if (e->r.bonded) {
+            double half_cap = 0.5 * 3.0 * M_PI * e->gamma * (s->R[i] * s->R[j] / (s->R[i] + s->R[j]));
             ci[8] += half_cap;
             cj[8] += half_cap;
         }
         for (int c = 0; c < 3; ++c) {
-            s->F[3 * i + c] += Fi[c];
-            s->F[3 * j + c] -= Fi[c];
-            s->T[3 * i + c] += Ti[c];
-            s->T[3 * j + c] += Tj[c];
+            s->F[3 * i + c] += e->Fi[c];
+            s->F[3 * j + c] -= e->Fi[c];
+            s->T[3 * i + c] += e->Ti[c];
+            s->T[3 * j + c] += e->Tj[c];
         }
-        s->Fscale[i] += sc;
-        s->Fscale[j] += sc;
-        nrec[nn++] = r;
+        s->Fscale[i] += e->sc;
+        s->Fscale[j] += e->sc;
+        double fm = sqrt(dot(e->Fi, e->Fi));
+        s->Fnet[i] += fm;
+        s->Fnet[j] += fm;
+        nrec[nn++] = e->r;
     }
+    free(ev);
     free(pr);
     free(l.pi);
     free(l.pj);
@@ -813,7 +868,8 @@ int ora_compute_forces(ora_sim* s) {
     s->rec = nrec;
     s->nrec = nn;
 
-    /* walls, body forces and drag */
+    /* walls, body forces and drag: each particle on its own */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (!s->active[i]) continue;
         double* F = &s->F[3 * i];
@@ -826,10 +882,13 @@ int ora_compute_forces(ora_sim* s) {
         double V = sphere_volume(s->R[i]);
         s->Fscale[i] += s->m[i] * sqrt(dot(p->g, p->g));
         if (p->use_buoyancy) s->Fscale[i] += p->rho_f * V * sqrt(dot(p->g, p->g));
+        double Fgb[3];
         for (int c = 0; c < 3; ++c) {
-            F[c] += s->m[i] * p->g[c];                        /* F_g */
-            if (p->use_buoyancy) F[c] += -p->rho_f * V * p->g[c]; /* F_b */
+            Fgb[c] = s->m[i] * p->g[c];                           /* F_g */
+            if (p->use_buoyancy) Fgb[c] += -p->rho_f * V * p->g[c]; /* F_b */
+            F[c] += Fgb[c];
         }
+        s->Fnet[i] += sqrt(dot(Fgb, Fgb));
         int64_t cell = fluid_cell(p, &s->x[3 * i]);
         double nc = porosity(s->vf[cell], p->n_min);
         double u[3] = {s->Us[3 * cell] / nc, s->Us[3 * cell + 1] / nc, s->Us[3 * cell + 2] / nc};
@@ -845,6 +904,7 @@ int ora_compute_forces(ora_sim* s) {
                 cl[5 + c] = fd[c];
             }
             s->Fscale[i] += sqrt(dot(fd, fd));
+            s->Fnet[i] += sqrt(dot(fd, fd));
         }
         /* closure inputs: solid fraction, slip speed, k, coordination, mean overlap / d */
         double slip[3] = {u[0] - s->v[3 * i], u[1] - s->v[3 * i + 1], u[2] - s->v[3 * i + 2]};
@@ -885,6 +945,21 @@ int ora_get_force_scale(const ora_sim* s, double* scale) {
     return 0;
 }
 
+int ora_get_force_scale_net(const ora_sim* s, double* scale) {
+    memcpy(scale, s->Fnet, sizeof(double) * (size_t)s->n);
+    return 0;
+}
+
+int ora_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
 int ora_set_forces(ora_sim* s, const double* F, const double* T) {
     memcpy(s->F, F, sizeof(double) * 3 * (size_t)s->n);
     memcpy(s->T, T, sizeof(double) * 3 * (size_t)s->n);
@@ -893,6 +968,7 @@ int ora_set_forces(ora_sim* s, const double* F, const double* T) {
 
 static void half_kick(ora_sim* s) {
     double h = 0.5 * s->p.dt;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < s->n; ++i) {
         if (!s->active[i]) continue;
         for (int c = 0; c < 3; ++c) {
@@ -906,6 +982,7 @@ int ora_step(ora_sim* s, int64_t nsteps) {
     const ora_params* p = &s->p;
     for (int64_t st = 0; st < nsteps; ++st) {
         half_kick(s);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < s->n; ++i) {
             if (!s->active[i]) continue;
             for (int c = 0; c < 3; ++c) {

@@ -4,8 +4,11 @@
  * of sand production in the modified cohesive contact model" (arXiv
  * 2211.06142).
  *
- * TEST INFRASTRUCTURE ONLY.  This library is a plain, slow, single-threaded
- * restatement of the paper's equations.  It exists so that tests and the
+ * TEST INFRASTRUCTURE ONLY.  This library is a plain, slow restatement of
+ * the paper's equations.  Its pair evaluations and per-particle loops may run
+ * on several host threads (OpenMP, ora_set_threads) without changing a bit
+ * of any result: each pair's evaluation is independent, and every sum is
+ * taken in the same order as with one thread.  It exists so that tests and the
  * benchmark's CPU baseline can check the CUDA library against something
  * written independently from the paper.  It shares no code, header, table or
  * constant generator with the CUDA path and must never be linked into it.
@@ -100,14 +103,18 @@ int64_t ora_num_contacts(const ora_sim* s);
 int ora_get_contacts(const ora_sim* s, int32_t* id_i, int32_t* id_j, uint8_t* bonded,
                      double* xi, int64_t cap);
 int ora_get_voidfrac(const ora_sim* s, uint64_t* cell_sums);
+/* Per particle, two scales of the last force evaluation: the sum of the
+ * magnitudes of every separate force term (Eq. 12 repulsion and adhesion,
+ * Eq. 32 damping, tangential force, gravity, buoyancy, drag), and the sum of
+ * the magnitudes of its contact, wall and body force vectors. */
+int ora_get_force_scale(const ora_sim* s, double* scale);
+int ora_get_force_scale_net(const ora_sim* s, double* scale);
+/* Host threads for the following calls (<= 0 keeps the current number);
+ * returns the number in use (1 without OpenMP). */
+int ora_set_threads(int nthreads);
 /* KE_trans, KE_rot, Px, Py, Pz, produced mass, n_active, n_bonds */
 int ora_get_diagnostics(const ora_sim* s, double out[8]);
 int ora_get_removed_step(const ora_sim* s, int64_t* removed_step);
-/* Per particle, the sum of the magnitudes of all force terms of the last
- * force evaluation -- Eq. 12 repulsion and adhesion counted separately, plus
- * damping, tangential, wall, gravity, buoyancy and drag terms -- the scale
- * for normwise comparisons. */
-int ora_get_force_scale(const ora_sim* s, double* scale);
 
 /* Learned-closure hooks (the closure is not part of the paper).  With the
  * closure enabled, the drag of particle i (Eq. 8) is multiplied by c_d,i and

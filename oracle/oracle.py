@@ -62,6 +62,8 @@ def lib():
             ("ora_get_diagnostics", i, [vp, pd]),
             ("ora_get_removed_step", i, [vp, vp]),
             ("ora_get_force_scale", i, [vp, vp]),
+            ("ora_get_force_scale_net", i, [vp, vp]),
+            ("ora_set_threads", i, [i]),
             ("ora_pairs_bruteforce", i64, [vp, i64, pd, pd, d, vp, vp, i64]),
             ("ora_voidfrac", i, [vp, i64, pd, pd, vp]),
             ("ora_set_closure", i, [vp, i, d]),
@@ -155,6 +157,12 @@ def drag(rho_f, mu_f, d, u, v, n):
     return f
 
 
+def set_threads(n):
+    """Host threads the oracle's loops use (results do not depend on it);
+    returns the number in use."""
+    return lib().ora_set_threads(int(n))
+
+
 def pairs_bruteforce(p, x, R, skin):
     x = _f64(x, (-1, 3))
     R = _f64(R)
@@ -240,8 +248,16 @@ class Sim:
         return dict(zip(["ke", "ke_rot", "px", "py", "pz", "produced_mass", "n_active", "n_bonds"], out))
 
     def force_scale(self):
+        """Per particle: the sum of the magnitudes of every force term."""
         out = np.zeros(self.n)
         lib().ora_get_force_scale(self.h, out.ctypes.data)
+        return out
+
+    def force_scale_net(self):
+        """Per particle: the sum of the magnitudes of its contact, wall and
+        body force vectors."""
+        out = np.zeros(self.n)
+        lib().ora_get_force_scale_net(self.h, out.ctypes.data)
         return out
 
     # ---- learned-closure hooks ----

@@ -539,3 +539,163 @@ def test_cohesive_coulomb_limit_stays_positive_on_the_jkr_branch():
         assert Fne >= -FC * (1 + 1e-9)
         assert abs(Fi[2]) == pytest.approx(mu * (Fne + 2 * FC), rel=1e-12)
         assert abs(Fi[2]) >= mu * FC * (1 - 1e-9)
+
+
+# ------------------------------------- tangential dynamics (walls, springs)
+
+def _resting_on_floor(R, rho=2650.0, g=9.81):
+    """Overlap of a sphere resting on a flat under its weight (Hertz, sphere on
+    a flat: (4/3) E* sqrt(R) delta^(3/2) = m g)."""
+    m = rho * 4 / 3 * math.pi * R ** 3
+    return (3 * m * g / (4 * ES * math.sqrt(R))) ** (2 / 3), m
+
+
+@pytest.mark.parametrize("mu", [0.3, 0.8])
+def test_sliding_sphere_rolls_at_five_sevenths(mu):
+    """A sphere launched along the bottom wall of the cylinder at v0 without
+    spin slides, friction at the contact spins it up, and it ends up rolling
+    at v = (5/7) v0 whatever the friction coefficient: friction acts at the
+    contact point, so the angular momentum about the contact line,
+    m R v_x + I w_y with I = (2/5) m R^2, keeps its initial value m R v0 at
+    every step; rolling (v_x = R w_y) then fixes v.  Pins the walls'
+    tangential law: its sign, its torque arm R and the contact velocity
+    v - R w x n it acts on."""
+    R, v0 = 1e-4, 1e-3
+    delta, m = _resting_on_floor(R)
+    I_ = 0.4 * m * R * R
+    p = base_params(kind=1, Rc=0.1, H=0.1, r_out=1e-3, g=(0, 0, -9.81), dt=2e-8, gamma=0.0, mu=mu)
+    sim = O.Sim(p, [[0.05, 0.0, R - delta]], [[v0, 0, 0]], [[0, 0, 0]], [R])
+    sim.compute_forces()
+    L0 = m * R * v0
+    for _ in range(60):
+        sim.step(1000)
+        st = sim.state()
+        L = m * R * st["v"][0, 0] + I_ * st["w"][0, 1]
+        assert L == pytest.approx(L0, rel=1e-11)
+    st = sim.state()
+    assert st["v"][0, 0] == pytest.approx(5 / 7 * v0, rel=1e-4)
+    assert R * st["w"][0, 1] == pytest.approx(st["v"][0, 0], rel=1e-4)
+
+
+def _rot(axis, ang):
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+
+@pytest.mark.parametrize("bonded", [False, True])
+def test_contact_law_is_frame_indifferent(bonded):
+    """A rigid rotation Q of a whole pair (positions, velocities, spins and
+    the stored spring, here not in the tangent plane) rotates the forces,
+    the torques and the updated spring by Q and changes nothing else: the
+    law may depend on the frame only through its vectors (Eq. 3-5, 12-13,
+    32-35 are written in vectors)."""
+    rng = np.random.default_rng(5)
+    R1, R2 = 1.1e-4, 0.8e-4
+    m1, m2 = (2650.0 * 4 / 3 * math.pi * r ** 3 for r in (R1, R2))
+    p = base_params(gamma=0.5 if bonded else 0.0, mu=0.5)
+    x1 = rng.normal(size=3) * 1e-4
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    x2 = x1 + n * (R1 + R2 - 2e-7)
+    v1, v2 = rng.normal(size=3) * 1e-3, rng.normal(size=3) * 1e-3
+    w1, w2 = rng.normal(size=3), rng.normal(size=3)
+    hist = rng.normal(size=3) * 2e-9
+    ref = O.pair_contact(p, x1, v1, w1, R1, m1, x2, v2, w2, R2, m2, hist=hist, bonded=bonded)
+    Q = _rot(rng.normal(size=3), 1.234)
+    rot = O.pair_contact(p, Q @ x1, Q @ v1, Q @ w1, R1, m1, Q @ x2, Q @ v2, Q @ w2, R2, m2,
+                         hist=Q @ hist, bonded=bonded)
+    assert ref[0] and rot[0] and ref[8] == rot[8] == bonded
+    for k in (1, 2, 3, 7):  # Fi, Ti, Tj, updated spring
+        scale = np.linalg.norm(ref[k])
+        np.testing.assert_allclose(rot[k], Q @ ref[k], rtol=0, atol=1e-12 * scale)
+    for k in (4, 5, 6):  # F_ne, contact radius, overlap
+        assert rot[k] == pytest.approx(ref[k], rel=1e-12)
+
+
+def test_spring_follows_the_tangent_plane_keeping_its_length():
+    """With no relative motion the stored spring only turns with the contact:
+    after one evaluation it lies in the current tangent plane, has kept its
+    length, and lies in the plane of its old direction and the normal (it is
+    turned, not twisted).  A spring turned the wrong way, or not rescaled,
+    fails one of these."""
+    R = 1e-4
+    m = 2650.0 * 4 / 3 * math.pi * R ** 3
+    p = base_params(gamma=0.0, mu=10.0)
+    z = np.zeros(3)
+    n = np.array([1.0, 0.0, 0.0])
+    for tilt in (0.0, 0.05, 0.4):
+        hist = np.array([math.sin(tilt), math.cos(tilt), 0.0]) * 3e-10  # tilted out of the plane
+        act, Fi, _, _, Fne, a, delta, h, _ = O.pair_contact(p, z, z, z, R, m, n * (2 * R - 1e-7), z, z, R, m,
+                                                            hist=hist)
+        assert act
+        assert abs(h @ n) <= 1e-15 * np.linalg.norm(h)
+        assert np.linalg.norm(h) == pytest.approx(np.linalg.norm(hist), rel=1e-14)
+        assert abs(np.cross(hist, n) @ h) <= 1e-15 * np.linalg.norm(h) * np.linalg.norm(hist)
+
+
+def test_tangential_oscillation_on_a_wall_decays_at_the_dashpot_rate():
+    """A sphere at rest on the bottom wall, its contact point given a small
+    sideways velocity (no slip: mu = 10), oscillates in the tangent plane
+    under the spring k_t = 8 G* a and the dashpot g_t = 2 sqrt(5/6) beta
+    sqrt(k_t m) (R6) of that contact.  The slip velocity u' = v_x - R w_y obeys
+    u'' + g_t u' / m_e + k_t u / m_e = 0 with 1 / m_e = 1 / m + R^2 / I (the
+    force acts on translation and, through the arm R, on spin): its zero
+    crossings come every half period pi / (w0 sqrt(1 - z^2)) and its peaks
+    shrink by exp(-z w0 t), w0^2 = k_t / m_e, z = g_t / (2 sqrt(k_t m_e))."""
+    R = 1e-4
+    delta, m = _resting_on_floor(R)
+    a = math.sqrt(R * delta)
+    G = E / (2 * (1 + NU))
+    Gs = G / (2 * (2 - NU))
+    le = math.log(0.5)
+    beta = -le / math.sqrt(le * le + math.pi ** 2)
+    kt = 8 * Gs * a
+    gt = 2 * math.sqrt(5 / 6) * beta * math.sqrt(kt * m)
+    me = 1.0 / (1.0 / m + R * R / (0.4 * m * R * R))
+    w0 = math.sqrt(kt / me)
+    zeta = gt / (2 * math.sqrt(kt * me))
+    wd = w0 * math.sqrt(1 - zeta * zeta)
+    dt = 2 * math.pi / w0 / 4000
+    p = base_params(kind=1, Rc=0.1, H=0.1, r_out=1e-3, g=(0, 0, -9.81), dt=dt, gamma=0.0, mu=10.0)
+    u0 = 1e-7  # slip velocity kick, all in translation
+    sim = O.Sim(p, [[0.05, 0.0, R - delta]], [[u0, 0, 0]], [[0, 0, 0]], [R])
+    sim.compute_forces()
+    t, u = [], []
+    for k in range(int(2.2 * 2 * math.pi / wd / dt / 10)):
+        sim.step(10)
+        st = sim.state()
+        t.append((k + 1) * 10 * dt)
+        u.append(st["v"][0, 0] - R * st["w"][0, 1])
+    t, u = np.array(t), np.array(u)
+    # zero crossings by linear interpolation
+    s = np.flatnonzero(np.sign(u[:-1]) != np.sign(u[1:]))
+    tz = t[s] - u[s] * (t[s + 1] - t[s]) / (u[s + 1] - u[s])
+    half = np.diff(tz)
+    assert len(half) >= 3
+    assert np.median(half) == pytest.approx(math.pi / wd, rel=2e-3)
+    # decay of the extrema between successive half periods
+    peaks = [np.abs(u[s[i]:s[i + 1]]).max() for i in range(len(s) - 1)]
+    ratio = np.array(peaks[1:]) / np.array(peaks[:-1])
+    assert np.median(ratio) == pytest.approx(math.exp(-zeta * w0 * math.pi / wd), rel=1e-2)
+
+
+def test_oracle_threads_change_no_bit():
+    """The oracle on one host thread and on all of them: identical states,
+    forces and contacts after 30 steps of a cylinder with walls, outlet and
+    drag (the pair evaluations run in parallel, their sums in pair order)."""
+    from tests.helpers import run_oracle, small_cylinder, default_dt, with_velocities
+    s = with_velocities(small_cylinder(), 1e-3)
+    out = []
+    nmax = O.set_threads(0)
+    for t in (1, nmax):
+        O.set_threads(t)
+        sim = run_oracle(s, default_dt(s), steps=30)
+        out.append((sim.state(), sim.contacts(), sim.force_scale(), sim.force_scale_net()))
+    O.set_threads(nmax)
+    (a, ca, fa, na), (b, cb, fb, nb) = out
+    for k in ("x", "v", "w", "F", "T"):
+        assert np.array_equal(a[k], b[k]), k
+    for u, v in zip(ca, cb):
+        assert np.array_equal(u, v)
+    assert np.array_equal(fa, fb) and np.array_equal(na, nb)
