@@ -211,6 +211,13 @@ int cgdem_get_state(cgdem_ctx* ctx, double* x, double* v, double* w, double* F, 
 int cgdem_get_contacts(cgdem_ctx* ctx, int32_t* id_i, int32_t* id_j, uint8_t* bonded,
                        int64_t cap, int64_t* count, void* stream);
 
+/* The same active contacts, sorted the same way, with the tangential spring
+ * xi of Eq. 4 of each ([count,3] doubles, SI): the spring as seen from id_i,
+ * i.e. the one whose force k_t xi acts on id_i (the mixed precision keeps it
+ * in FP32).  Any output pointer may be NULL; at most cap are written. */
+int cgdem_get_contact_springs(cgdem_ctx* ctx, int32_t* id_i, int32_t* id_j, double* xi,
+                              int64_t cap, int64_t* count, void* stream);
+
 /* Porosity cell sums S (uint64 quanta) of all samples' fluid cells, sample
  * after sample; cap = room in cell_sums. */
 int cgdem_get_voidfrac(cgdem_ctx* ctx, uint64_t* cell_sums, int64_t cap, void* stream);

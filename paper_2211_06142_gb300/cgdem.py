@@ -33,7 +33,7 @@ EXPORTS = [
     "cgdem_destroy", "cgdem_last_error", "cgdem_status_sync", "cgdem_init_particles",
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
     "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
-    "cgdem_get_contacts", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
+    "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
     "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
@@ -107,6 +107,7 @@ def lib():
             "cgdem_step": (i, [vp, i64, vp]),
             "cgdem_get_state": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "cgdem_get_contacts": (i, [vp, vp, vp, vp, i64, vp, vp]),
+            "cgdem_get_contact_springs": (i, [vp, vp, vp, vp, i64, vp, vp]),
             "cgdem_get_voidfrac": (i, [vp, vp, i64, vp]),
             "cgdem_get_diagnostics": (i, [vp, vp, i64, vp]),
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
@@ -413,6 +414,20 @@ class Context:
                                              self._s()), "get_contacts")
         k = n.value
         return i[:k], j[:k], b[:k]
+
+    def get_contact_springs(self):
+        """(id_i, id_j, xi [n,3]) of the active contacts, xi as seen from id_i."""
+        n = C.c_int64(0)
+        self._check(lib().cgdem_get_contact_springs(self.h, None, None, None, 0, C.byref(n), self._s()),
+                    "get_contact_springs")
+        cap = max(n.value, 1)
+        i = np.zeros(cap, np.int32)
+        j = np.zeros(cap, np.int32)
+        xi = np.zeros((cap, 3))
+        self._check(lib().cgdem_get_contact_springs(self.h, _ptr(i), _ptr(j), _ptr(xi), cap, C.byref(n),
+                                                    self._s()), "get_contact_springs")
+        k = n.value
+        return i[:k], j[:k], xi[:k]
 
     def get_voidfrac(self, ncell):
         out = np.zeros(ncell, np.uint64)

@@ -25,6 +25,7 @@ void launch_cube_after_mid(const Dev& d, cudaStream_t s);
 void launch_init(const Dev& d, cudaStream_t s);
 void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
+void launch_collect_springs(const Dev& d, uint32_t* out, double* xi, unsigned long long cap, cudaStream_t s);
 void launch_diag(const Dev& d, double* part, cudaStream_t s);
 void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s);
 void launch_closure_gather(const Dev& d, cudaStream_t s);
@@ -884,6 +885,49 @@ int cgdem_get_contacts(cgdem_ctx* ctx, int32_t* id_i, int32_t* id_j, uint8_t* bo
     if (id_i) id_i[i] = (int32_t)(key[i] >> 32);
     if (id_j) id_j[i] = (int32_t)(key[i] & 0x7fffffffull);
     if (bonded) bonded[i] = (key[i] & 0x80000000ull) ? 1 : 0;
+  }
+  return check_status(ctx, s);
+}
+
+int cgdem_get_contact_springs(cgdem_ctx* ctx, int32_t* id_i, int32_t* id_j, double* xi, int64_t cap,
+                              int64_t* count, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!count) return CGDEM_E_INVALID;
+  cudaStream_t s = st(stream);
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, ctx->d.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // pairs (8 bytes) and springs (24 bytes) in the spare record buffer
+  const size_t cap2 = ctx->contact_cap / 4;
+  uint32_t* buf = reinterpret_cast<uint32_t*>(ctx->d.rec[c.rec_cur ^ 1]);
+  double* xib = reinterpret_cast<double*>(buf + 2 * cap2);
+  launch_collect_springs(ctx->d, buf, xib, cap2, s);
+  unsigned long long n = 0;
+  CK(cudaMemcpyAsync(&n, ctx->d.contact_n, sizeof n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n > cap2) return fail(ctx, CGDEM_E_CAPACITY, "too many contacts to collect");
+  std::vector<uint32_t> h(2 * n);
+  std::vector<double> hx(3 * n);
+  if (n) {
+    CK(cudaMemcpyAsync(h.data(), buf, sizeof(uint32_t) * 2 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hx.data(), xib, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  std::vector<size_t> order(n);
+  for (size_t i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    if (h[2 * a] != h[2 * b]) return h[2 * a] < h[2 * b];
+    return (h[2 * a + 1] & 0x7fffffffu) < (h[2 * b + 1] & 0x7fffffffu);
+  });
+  *count = (int64_t)n;
+  const size_t m = std::min<size_t>(n, cap > 0 ? (size_t)cap : 0);
+  for (size_t i = 0; i < m; ++i) {
+    const size_t k = order[i];
+    if (id_i) id_i[i] = (int32_t)h[2 * k];
+    if (id_j) id_j[i] = (int32_t)(h[2 * k + 1] & 0x7fffffffu);
+    if (xi)
+      for (int c3 = 0; c3 < 3; ++c3) xi[3 * i + c3] = hx[3 * k + c3];
   }
   return check_status(ctx, s);
 }

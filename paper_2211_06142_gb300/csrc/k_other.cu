@@ -1139,6 +1139,49 @@ __global__ void k_collect_contacts(Dev d, uint32_t* out, unsigned long long cap)
   }
 }
 
+// Active contacts with their tangential springs: (id_i, id_j | bond << 31)
+// with id_i < id_j, and the spring as seen from id_i (the force-on-i
+// convention of Eq. 4): mixed lists hold each pair twice and the lower id's
+// record is taken; an FP64 pair is held by its lower-index sphere, whose
+// spring is negated when that sphere has the higher id.
+__global__ void k_collect_springs(Dev d, uint32_t* out, double* xi, unsigned long long cap) {
+  const int pc = d.ctl->pcur, rc = d.ctl->rec_cur;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const uint32_t n = d.cnt[rc][p];
+  const int ip = d.id[pc][p];
+  for (uint32_t k = 0; k < n; ++k) {
+    const size_t idx = (size_t)d.roff[rc][p] + (size_t)k * d.rstride;
+    uint32_t pf;
+    double sx, sy, sz;
+    if (d.mixed) {
+      const uint4 r = reinterpret_cast<const uint4*>(d.rec[rc])[idx];
+      pf = r.x;
+      sx = __uint_as_float(r.y);
+      sy = __uint_as_float(r.z);
+      sz = __uint_as_float(r.w);
+    } else {
+      const RecD& r = reinterpret_cast<const RecD*>(d.rec[rc])[idx];
+      pf = r.pf;
+      sx = r.x;
+      sy = r.y;
+      sz = r.z;
+    }
+    if (!(pf & REC_ACTIVE)) continue;
+    const int iq = d.id[pc][pf & REC_IDX];
+    if (d.mixed && ip >= iq) continue;
+    const double sg = ip < iq ? 1.0 : -1.0;
+    const unsigned long long slot = atomicAdd(d.contact_n, 1ull);
+    if (slot < cap) {
+      out[2 * slot] = (uint32_t)min(ip, iq);
+      out[2 * slot + 1] = (uint32_t)max(ip, iq) | ((pf & REC_BOND) ? 0x80000000u : 0u);
+      xi[3 * slot] = sg * sx;
+      xi[3 * slot + 1] = sg * sy;
+      xi[3 * slot + 2] = sg * sz;
+    }
+  }
+}
+
 // Per-sample diagnostics: partial sums per block (fixed order), then reduce.
 constexpr int DIAG_BLOCKS = 128;
 __global__ void k_diag_partial(Dev d, double* part) {
@@ -1309,6 +1352,11 @@ void launch_init(const Dev& d, cudaStream_t s) {
 
 void launch_gather_state(const Dev& d, cudaStream_t s) {
   if (d.N) k_gather_state<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_collect_springs(const Dev& d, uint32_t* out, double* xi, unsigned long long cap, cudaStream_t s) {
+  cudaMemsetAsync(d.contact_n, 0, sizeof(unsigned long long), s);
+  if (d.N) k_collect_springs<<<nblk(d.N, 256), 256, 0, s>>>(d, out, xi, cap);
 }
 
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s) {
