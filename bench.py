@@ -269,7 +269,7 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
             "Zbar": Zbar, "candidates_per_particle": Cbar}
 
 
-def run_sand(T=0.004, n_times=20):
+def run_sand(T=0.004, n_times=40):
     """Produced sand (Eq. 40) of the coarse-grained models against the fine
     200k-sphere cylinder over the same physical time T: RMSRE (Eq. 41) and
     the relative error at T for SSW and SSP at k = 2 and 3, and for SSW at
@@ -287,9 +287,12 @@ def run_sand(T=0.004, n_times=20):
     SD.run(fine, T=T, n_times=1)
     t_fine = time.perf_counter() - tf
     ref = SD.run(fine, T=T, n_times=n_times, record=True)
+    mg = lambda a: [[round(float(v) * 1e6, 4) for v in row] for row in a]  # noqa: E731
     out = {"T_s": T, "times": n_times, "U_in_m_s": SD.U_SAND, "dt_over_rayleigh": SD.DT_FRAC,
            "fine_mass_mg": float(ref.mass[-1] * 1e6), "fine_steps": ref.steps, "fine_wall_s": t_fine,
-           "models": {}}
+           "psd_classes_mm": [round(float(v) * 1e3, 4) for v in SD.table2_edges()],
+           "psd_window_fractions": list(SD.WINDOW_FRACTIONS),
+           "fine_psd_windows_mg": mg(SD.psd_windows(ref)), "models": {}}
     ssw3 = None
     for scheme, k in (("ssw", 2), ("ssw", 3), ("ssp", 2), ("ssp", 3)):
         s = Wl.coarse_cylinder(k=k, scheme=scheme)
@@ -301,7 +304,9 @@ def run_sand(T=0.004, n_times=20):
         out["models"][f"{scheme}{k}"] = {"parcels": len(s.R), "mass_mg": float(r.mass[-1] * 1e6),
                                          "wall_s": t_c, "speedup_vs_fine": t_fine / t_c,
                                          "rmsre_pct": SD.rmsre(ref, r), "rmsre_late_pct": SD.rmsre_late(ref, r),
-                                         "final_rel_err": SD.final_error(ref, r)}
+                                         "rmsre_normalized_pct": SD.rmsre_normalized(ref, r),
+                                         "final_rel_err": SD.final_error(ref, r),
+                                         "psd_windows_mg": mg(SD.psd_windows(r))}
         if rec:
             ssw3 = (s, r)
     s3, r3 = ssw3

@@ -226,6 +226,24 @@ int cgdem_get_voidfrac(cgdem_ctx* ctx, uint64_t* cell_sums, int64_t cap, void* s
  * produced (outlet) mass, active particles, bonded contacts. */
 int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream);
 
+/* Produced sand by size class (Sec. 3.4, Fig. 11).  edges: nclass + 1
+ * increasing fine-scale diameters [m] (HOST), 1 <= nclass <= 16, or nclass
+ * = 0 to stop recording.  A grain of radius R in a sample coarse-grained at
+ * ratio k stands for fine grains of diameter 2 R / k; it is counted in class
+ * c when edges[c] <= 2 R / k < edges[c + 1] (below edges[0]: class 0; at or
+ * above edges[nclass]: the last class).  From the call on, every grain that
+ * leaves through the outlet adds 1 to its class's count and its mass
+ * rho (4/3 pi) R^3 to its class's mass (integer quanta of 2^-40 of the
+ * sample's largest grain mass, so the sums do not depend on the order of
+ * the removals); the sums start at zero (and again at cgdem_init_particles).
+ * Applies to every sample.  Synchronises stream. */
+int cgdem_set_psd_classes(cgdem_ctx* ctx, const double* edges, int nclass, void* stream);
+
+/* The cumulative produced mass [kg] and grain count per sample and class:
+ * HOST arrays of cap >= 16 x n_samples entries, 16 per sample (classes past
+ * nclass hold 0).  Either pointer may be NULL.  Synchronises stream. */
+int cgdem_get_produced_psd(cgdem_ctx* ctx, double* mass, int64_t* count, int64_t cap, void* stream);
+
 /* Step at which each particle left through the outlet (-1 if it did not). */
 int cgdem_get_removed_step(cgdem_ctx* ctx, int32_t* removed_step, void* stream);
 

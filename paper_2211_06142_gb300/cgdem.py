@@ -23,6 +23,7 @@ CGDEM_E_NONFINITE = -4
 CGDEM_E_TIMEOUT = -5
 CGDEM_E_STATE = -6
 MLP_NPARAMS = 8844
+PSD_MAX = 16  # size classes of the produced-sand accumulators
 FP64, MIXED = 0, 1
 PERIODIC_BOX, CYLINDER = 0, 1
 CG_NONE, CG_SSW, CG_SSP = 0, 1, 2
@@ -33,7 +34,7 @@ EXPORTS = [
     "cgdem_destroy", "cgdem_last_error", "cgdem_status_sync", "cgdem_init_particles",
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
     "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
-    "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step",
+    "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step", "cgdem_set_psd_classes", "cgdem_get_produced_psd",
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
     "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
@@ -111,6 +112,8 @@ def lib():
             "cgdem_get_voidfrac": (i, [vp, vp, i64, vp]),
             "cgdem_get_diagnostics": (i, [vp, vp, i64, vp]),
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
+            "cgdem_set_psd_classes": (i, [vp, vp, i, vp]),
+            "cgdem_get_produced_psd": (i, [vp, vp, vp, i64, vp]),
             "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
             "cgdem_get_launch_counts": (i, [vp, vp, vp]),
             "cgdem_profile_step": (i, [vp, i64, vp, vp]),
@@ -445,6 +448,19 @@ class Context:
         out = np.zeros(self.N, np.int32)
         self._check(lib().cgdem_get_removed_step(self.h, _ptr(out), self._s()), "get_removed_step")
         return out
+
+    def set_psd_classes(self, edges):
+        """Record produced sand by size class (fine-scale diameter edges [m])."""
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        self._check(lib().cgdem_set_psd_classes(self.h, _ptr(e), len(e) - 1, self._s()), "set_psd_classes")
+
+    def produced_psd(self):
+        """(mass [n_samples, 16] kg, count [n_samples, 16]) produced so far."""
+        m = np.zeros((self.n_samples, PSD_MAX))
+        c = np.zeros((self.n_samples, PSD_MAX), np.int64)
+        self._check(lib().cgdem_get_produced_psd(self.h, _ptr(m), _ptr(c), m.size, self._s()),
+                    "get_produced_psd")
+        return m, c
 
     def counters(self):
         s, r, m, t = C.c_int64(0), C.c_int64(0), C.c_int32(0), C.c_int64(0)

@@ -249,6 +249,11 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   for (int k = 0; k < 3; ++k) s.g_f[k] = (float)s.g[k];
   s.rho_s_f = (float)s.rho;
   s.k_feat_f = (float)k_cg;
+  s.k_cg = k_cg;
+  s.n_psd = 0;  // no size classes until cgdem_set_psd_classes
+  // mass quantum: 2^-40 of the largest grain's mass (a grain's quanta fit
+  // 40 bits, 2^23 of the largest grains fit a class sum)
+  s.psd_mq = std::ldexp(p.rho * (4.0 / 3.0 * PI) * p.r_max * p.r_max * p.r_max, -40);
   {
     const double cd = 2.0 * std::sqrt(5.0 / 6.0);
     s.cdbn_f = (float)(cd * s.beta * std::sqrt(2.0 * s.Es));
@@ -351,6 +356,8 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.disp = cv.take<double>(S);
   d.vmax2 = cv.take<unsigned long long>(S);
   d.diag = cv.take<double>(8 * (size_t)S);
+  d.psd_count = cv.take<unsigned long long>((size_t)CGDEM_PSD_MAX * S);
+  d.psd_mass = cv.take<unsigned long long>((size_t)CGDEM_PSD_MAX * S);
   d.staging = cv.take<double>(16 * (size_t)Npad);
   d.contact_n = cv.take<unsigned long long>(1);
   if (cfg->closure) {
@@ -703,6 +710,8 @@ int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const
   CK(cudaMemsetAsync(ctx->d.cell_count, 0, sizeof(uint32_t) * ((size_t)ctx->d.C_total + 2), s));
   if (ctx->d.seg_flag)
     CK(cudaMemsetAsync(ctx->d.seg_flag, 0, sizeof(uint32_t) * (size_t)(ctx->d.Npad / 16), s));
+  CK(cudaMemsetAsync(ctx->d.psd_count, 0, sizeof(unsigned long long) * CGDEM_PSD_MAX * ctx->d.n_samples, s));
+  CK(cudaMemsetAsync(ctx->d.psd_mass, 0, sizeof(unsigned long long) * CGDEM_PSD_MAX * ctx->d.n_samples, s));
   launch_set_rebuild(ctx->d, s);
   launch_rebuild(ctx->d, s);
   if (bond_touching) launch_bond_touching(ctx->d, s);
@@ -955,6 +964,45 @@ int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream
   CK(cudaMemcpyAsync(out, ctx->d.diag, sizeof(double) * 8 * ctx->d.n_samples,
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
+}
+
+int cgdem_set_psd_classes(cgdem_ctx* ctx, const double* edges, int nclass, void* stream) {
+  if (!ctx) return CGDEM_E_INVALID;
+  if (nclass < 0 || nclass > CGDEM_PSD_MAX || (nclass > 0 && !edges))
+    return fail(ctx, CGDEM_E_INVALID, "nclass must lie in [0, %d] with nclass + 1 edges", CGDEM_PSD_MAX);
+  for (int c = 0; c < nclass; ++c)
+    if (!(edges[c] < edges[c + 1]) || !(edges[c] >= 0.0))
+      return fail(ctx, CGDEM_E_INVALID, "class edges must be non-negative and increasing");
+  for (auto& S : ctx->sd) {
+    S.n_psd = nclass;
+    for (int c = 0; c <= CGDEM_PSD_MAX; ++c) S.psd_edge[c] = c <= nclass && nclass ? edges[c] : 0.0;
+  }
+  cudaStream_t s = st(stream);
+  CK(cudaMemcpyAsync(ctx->d.sp, ctx->sd.data(), sizeof(SampleDev) * ctx->sd.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d.psd_count, 0, sizeof(unsigned long long) * CGDEM_PSD_MAX * ctx->d.n_samples, s));
+  CK(cudaMemsetAsync(ctx->d.psd_mass, 0, sizeof(unsigned long long) * CGDEM_PSD_MAX * ctx->d.n_samples, s));
+  CK(cudaStreamSynchronize(s));
+  return CGDEM_OK;
+}
+
+int cgdem_get_produced_psd(cgdem_ctx* ctx, double* mass, int64_t* count, int64_t cap, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  const int S = ctx->d.n_samples;
+  if (cap < (int64_t)CGDEM_PSD_MAX * S) return fail(ctx, CGDEM_E_INVALID, "output needs %d entries per sample",
+                                                     CGDEM_PSD_MAX);
+  cudaStream_t s = st(stream);
+  std::vector<unsigned long long> c((size_t)CGDEM_PSD_MAX * S), q((size_t)CGDEM_PSD_MAX * S);
+  CK(cudaMemcpyAsync(c.data(), ctx->d.psd_count, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(q.data(), ctx->d.psd_mass, sizeof(unsigned long long) * q.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < S; ++k)
+    for (int j = 0; j < CGDEM_PSD_MAX; ++j) {
+      const size_t i = (size_t)k * CGDEM_PSD_MAX + j;
+      if (count) count[i] = (int64_t)c[i];
+      if (mass) mass[i] = (double)q[i] * ctx->sd[k].psd_mq;
+    }
   return check_status(ctx, s);
 }
 

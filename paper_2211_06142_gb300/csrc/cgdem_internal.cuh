@@ -18,6 +18,8 @@ constexpr uint32_t REC_IDX = 0x3fffffffu;     // partner index (current order)
 
 // largest candidate list per particle (max_neighbors)
 #define CGDEM_MAX_NEIGHBORS 96
+// size classes of the produced-sand accumulators (per sample)
+#define CGDEM_PSD_MAX 16
 
 // latched device status bits
 constexpr unsigned ST_CAPACITY = 1u;
@@ -74,6 +76,14 @@ struct SampleDev {
   // Eq. 32 and its tangential twin with the contact radius and reduced mass
   // factored out: gamma_n = cdbn sqrt(a m*), gamma_t = cdbt sqrt(a m*)
   float cdbn_f, cdbt_f;  // 2 sqrt(5/6) beta sqrt(2 E*), 2 sqrt(5/6) beta sqrt(8 G*)
+  // produced sand by size class (Sec. 3.4): a grain of radius R stands for
+  // fine grains of diameter 2 R / k; class c holds psd_edge[c] <= 2 R / k <
+  // psd_edge[c + 1] (the first and last classes also take what lies below or
+  // above); masses are summed in quanta of psd_mq (0 classes: not recorded)
+  double k_cg;
+  int n_psd;
+  double psd_edge[CGDEM_PSD_MAX + 1];
+  double psd_mq;
 };
 
 // Learned closure (not part of the paper): per-particle corrections
@@ -176,6 +186,8 @@ struct Dev {
   double* disp;                   // per-sample displacement bound since last rebuild
   unsigned long long* vmax2;      // per-sample max (|v| dt)^2 of the last drift (double bits)
   double* diag;                   // per-sample diagnostics [S][8]
+  unsigned long long* psd_count;  // produced grains per sample and size class [S][CGDEM_PSD_MAX]
+  unsigned long long* psd_mass;   // their mass in quanta of the sample's psd_mq [S][CGDEM_PSD_MAX]
   double* staging;                // [N * 16] host-transfer staging
   uint32_t* contact_out;          // [2 * cap_out] (i, j | bond << 31)
   unsigned long long* contact_n;
@@ -326,5 +338,19 @@ __device__ __forceinline__ void exact_geometry(const SampleDev& s, double4 a, do
 }
 
 __device__ __forceinline__ void latch(Ctl* ctl, unsigned bits) { atomicOr(&ctl->status, bits); }
+
+// A grain of sample s and radius R left through the outlet: its size class
+// and its mass rho (4/3 pi) R^3 in fixed-point quanta (integer atomics: the
+// sums do not depend on the order of the removals).
+__device__ __forceinline__ void record_produced(const Dev& d, const SampleDev& S, int s, double R) {
+  if (S.n_psd <= 0) return;
+  const double dfine = 2.0 * R / S.k_cg;
+  int c = 0;
+  while (c + 1 < S.n_psd && !(dfine < S.psd_edge[c + 1])) ++c;
+  const double m = S.rho * (4.1887902047863905 * R * R * R);
+  const size_t k = (size_t)s * CGDEM_PSD_MAX + c;
+  atomicAdd(&d.psd_count[k], 1ull);
+  atomicAdd(&d.psd_mass[k], (unsigned long long)__double2ll_rn(m / S.psd_mq));
+}
 
 }  // namespace cgdem

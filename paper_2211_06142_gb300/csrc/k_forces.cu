@@ -640,7 +640,10 @@ __device__ __forceinline__ void finish_step(
         // outlet (produced sand, Eq. 40): float filter, FP64 decision
         const bool removed = S.kind == CGDEM_CYLINDER && zf < -1.999f * __double2float_rn(P.w) &&
                              P.z < -2.0 * P.w;
-        if (removed) d.removed_step[d.id[pc][p]] = (int)m_step;
+        if (removed) {
+          d.removed_step[d.id[pc][p]] = (int)m_step;
+          record_produced(d, S, si, P.w);
+        }
         double vx, vy, vz, wx, wy, wz;
         if constexpr (MIXED) {
           // FP32 force increments added to the FP64 state

@@ -1006,6 +1006,7 @@ __global__ void k_kick_final(Dev d) {
   W.z += h * (Tq.z * W.w);
   if (S.kind == CGDEM_CYLINDER && P.z < -2.0 * P.w) {
     d.removed_step[d.id[pc][p]] = (int)m;
+    record_produced(d, S, d.sample[pc][p], P.w);
     P.w = -P.w;
     d.pos[cur][p] = P;
   }

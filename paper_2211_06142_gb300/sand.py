@@ -27,8 +27,21 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import cgdem
+from . import inputs as I
 
 U_SAND = 0.02      # inflow velocity at the cylinder wall [m/s]
+# Sec. 3.4 reads the produced PSD over 0-0.003, 0.003-0.015 and
+# 0.015-0.04 s of a 0.04 s run: the same fractions of the run time here
+WINDOW_FRACTIONS = (0.075, 0.375, 1.0)
+
+
+def table2_edges():
+    """Size classes of the produced-sand PSD: the eight diameter classes of
+    Table 2, each taking the diameters nearer to it than to its neighbours
+    (edges at the midpoints) [m]."""
+    d = I.TABLE2_DIAMETER_MM * 1e-3
+    mid = 0.5 * (d[1:] + d[:-1])
+    return np.concatenate([[0.0], mid, [1.0]])
 DT_FRAC = 0.02     # time step / Rayleigh time of the volume-mean grain
 SKIN_FRAC = 0.04   # candidate-list skin / largest grain diameter
 
@@ -40,6 +53,7 @@ class Production:
     steps: int
     data: list = field(default_factory=list)  # recorded closure rows per time
     nf: tuple = ()
+    psd: np.ndarray = None  # [n, classes] kg, cumulative produced mass per Table 2 class
 
 
 def rayleigh_dt(s, frac=DT_FRAC):
@@ -48,7 +62,7 @@ def rayleigh_dt(s, frac=DT_FRAC):
     return frac * cgdem.cgdem_rayleigh_dt(Rbar, m["rho"], m["E"], m["nu"])
 
 
-def run(s, k=1, scheme=cgdem.CG_NONE, U_ref=1e-4, T=0.004, n_times=20, precision=cgdem.MIXED,
+def run(s, k=1, scheme=cgdem.CG_NONE, U_ref=1e-4, T=0.004, n_times=40, precision=cgdem.MIXED,
         closure=None, record=False, device="cuda:0", vf_mode=0, skin_frac=SKIN_FRAC):
     """Run sample s (its field built for an inflow of U_ref, rescaled to
     U_SAND) for time T; returns the produced mass at n_times times."""
@@ -61,6 +75,8 @@ def run(s, k=1, scheme=cgdem.CG_NONE, U_ref=1e-4, T=0.004, n_times=20, precision
     try:
         ctx.set_fluid_velocity(s.Us * (U_SAND / U_ref))
         ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
+        edges = table2_edges()
+        ctx.set_psd_classes(edges)
         if closure is not None:
             theta, lo, hi, cd_max, cg_max = closure
             ctx.set_closure(theta, lo, hi, cd_max, cg_max)
@@ -68,16 +84,18 @@ def run(s, k=1, scheme=cgdem.CG_NONE, U_ref=1e-4, T=0.004, n_times=20, precision
             ctx.closure_record(True)
         ctx.compute_forces()
         times = T * np.arange(1, n_times + 1) / n_times
-        mass, data, done = [], [], 0
+        mass, data, psd, done = [], [], [], 0
         for t in times:
             n = int(round(t / dt)) - done
             if n > 0:
                 ctx.step(n)
                 done += n
             mass.append(ctx.get_diagnostics()[0]["produced_mass"])
+            psd.append(ctx.produced_psd()[0][0, :len(edges) - 1])
             if record:
                 data.append(ctx.closure_data().copy())
-        return Production(times, np.array(mass), done, data, tuple(int(v) for v in s.grid.nf))
+        return Production(times, np.array(mass), done, data, tuple(int(v) for v in s.grid.nf),
+                          np.array(psd))
     finally:
         ctx.close()
 
@@ -107,3 +125,33 @@ def final_error(ref: Production, mod: Production):
     if not ref.mass[-1] > 0:
         return None
     return float(abs(mod.mass[-1] - ref.mass[-1]) / ref.mass[-1])
+
+
+def normalized_curve(prod: Production):
+    """Eq. 39-40: t_d = t / t_end and M_d = cumulative produced mass over its
+    value at t_end (None if nothing was produced)."""
+    if not prod.mass[-1] > 0:
+        return None
+    return prod.times / prod.times[-1], prod.mass / prod.mass[-1]
+
+
+def rmsre_normalized(ref: Production, mod: Production):
+    """Eq. 41 (square restored) on the normalised curves of Eq. 40, over the
+    read times where the reference's M_d is positive."""
+    a, b = normalized_curve(ref), normalized_curve(mod)
+    if a is None or b is None:
+        return None
+    ok = a[1] > 0
+    r = (a[1][ok] - b[1][ok]) / a[1][ok]
+    return float(100.0 * np.sqrt(np.mean(r * r)))
+
+
+def psd_windows(prod: Production, fractions=WINDOW_FRACTIONS):
+    """Produced mass per Table 2 class in each time window ending at the
+    given fractions of the run time (Sec. 3.4, Fig. 11): [windows, classes]."""
+    out, prev = [], np.zeros(prod.psd.shape[1])
+    for f in fractions:
+        i = int(np.argmin(np.abs(prod.times - f * prod.times[-1])))
+        out.append(prod.psd[i] - prev)
+        prev = prod.psd[i]
+    return np.array(out)

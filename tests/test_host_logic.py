@@ -123,3 +123,26 @@ def test_skin_factors_follow_drift_rates():
     assert f[9] == 2.5
     assert A.skin_factors([0.0, 0.0]).tolist() == [1.0, 1.0]
     assert len(A.skin_factors([])) == 0
+
+
+def test_normalised_sand_curves_and_windows():
+    """Eq. 39-41 on made-up production records: M_d ends at 1, a curve has
+    no error against itself and against a scaled copy (normalisation), and
+    the per-window class masses add up to the final cumulative ones."""
+    from paper_2211_06142_gb300 import sand as SD
+    t = np.linspace(0.1, 4.0, 40) * 1e-3
+    m = 1e-6 * (1 - np.exp(-t / 1e-3))
+    psd = np.outer(m, np.linspace(1, 2, 8)) / 12.0
+    a = SD.Production(t, m, 100, psd=psd)
+    b = SD.Production(t, 2 * m, 100, psd=2 * psd)
+    td, md = SD.normalized_curve(a)
+    assert td[-1] == 1.0 and md[-1] == 1.0 and np.all(np.diff(md) > 0)
+    assert SD.rmsre_normalized(a, a) == 0.0
+    assert SD.rmsre_normalized(a, b) == pytest.approx(0.0, abs=1e-12)
+    c = SD.Production(t, m * (1 + 0.1 * (t < 1e-3)), 100, psd=psd)
+    assert SD.rmsre_normalized(a, c) > 0
+    w = SD.psd_windows(a)
+    assert w.shape == (3, 8)
+    np.testing.assert_allclose(w.sum(0), psd[-1], rtol=1e-14)
+    e = SD.table2_edges()
+    assert len(e) == 9 and np.all(np.diff(e) > 0)
