@@ -440,6 +440,10 @@ struct ora_sim {
     double* Us;
     double* Fscale; /* per particle: sum of the magnitudes of every force term */
     double* Fnet;   /* per particle: sum of the magnitudes of its contact, wall and body force vectors */
+    double* pres;   /* fluid_mode 1: dynamic pressure per fluid cell */
+    double* gradp;  /* its gradient per cell [3] */
+    int64_t* react; /* drag reaction (Eq. 7) per cell [3], quanta of 2^-60 N */
+    int64_t fluid_iters;
     int64_t ncell_f;
     int64_t step;
     double produced;
@@ -500,6 +504,9 @@ ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const doubl
     s->vf = (uint64_t*)calloc((size_t)s->ncell_f + 1, sizeof(uint64_t));
     s->Us = (double*)calloc((size_t)s->ncell_f * 3 + 3, sizeof(double));
     if (Us) memcpy(s->Us, Us, sizeof(double) * 3 * s->ncell_f);
+    s->pres = (double*)calloc((size_t)s->ncell_f + 1, sizeof(double));
+    s->gradp = (double*)calloc((size_t)s->ncell_f * 3 + 3, sizeof(double));
+    s->react = (int64_t*)calloc((size_t)s->ncell_f * 3 + 3, sizeof(int64_t));
     return s;
 }
 
@@ -509,6 +516,7 @@ void ora_destroy(ora_sim* s) {
     free(s->R); free(s->m); free(s->I); free(s->active); free(s->removed_step);
     free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us); free(s->Fscale); free(s->Fnet);
     free(s->cd); free(s->cg); free(s->cdata);
+    free(s->pres); free(s->gradp); free(s->react);
     free(s);
 }
 
@@ -692,12 +700,16 @@ int ora_bond_touching(ora_sim* s) {
     return 0;
 }
 
+static int solve_fluid(ora_sim* s);
+
 int ora_couple_fluid(ora_sim* s) {
     memset(s->vf, 0, sizeof(uint64_t) * (size_t)s->ncell_f);
     for (int64_t i = 0; i < s->n; ++i) {
         if (!s->active[i]) continue;
         add_voidfrac(&s->p, &s->x[3 * i], s->R[i], s->vf);
     }
+    /* two-way coupling: the flow follows the new porosity */
+    if (s->p.fluid_mode == 1 && s->p.kind == 1) return solve_fluid(s);
     return 0;
 }
 
@@ -890,6 +902,15 @@ int ora_compute_forces(ora_sim* s) {
         }
         s->Fnet[i] += sqrt(dot(Fgb, Fgb));
         int64_t cell = fluid_cell(p, &s->x[3 * i]);
+        if (p->fluid_mode == 1) { /* dynamic pressure gradient on the grain's volume */
+            double Fp[3];
+            for (int c = 0; c < 3; ++c) {
+                Fp[c] = -V * s->gradp[3 * cell + c];
+                F[c] += Fp[c];
+            }
+            s->Fscale[i] += sqrt(dot(Fp, Fp));
+            s->Fnet[i] += sqrt(dot(Fp, Fp));
+        }
         double nc = porosity(s->vf[cell], p->n_min);
         double u[3] = {s->Us[3 * cell] / nc, s->Us[3 * cell + 1] / nc, s->Us[3 * cell + 2] / nc};
         double* cl = &s->cdata[ORA_CL_COLS * i];
@@ -915,6 +936,17 @@ int ora_compute_forces(ora_sim* s) {
         cl[9] = (double)cell;
         cl[10] = s->cd[i];
         cl[11] = s->cg[i];
+    }
+    /* drag reaction of Eq. 7: the particles' drag summed per cell, in
+       integer quanta (the sums do not depend on their order) */
+    if (p->fluid_mode == 1) {
+        memset(s->react, 0, sizeof(int64_t) * 3 * (size_t)s->ncell_f);
+        for (int64_t i = 0; i < n; ++i) {
+            if (!s->active[i]) continue;
+            const double* cl = &s->cdata[ORA_CL_COLS * i];
+            int64_t cell = (int64_t)cl[9];
+            for (int c = 0; c < 3; ++c) s->react[3 * cell + c] += (int64_t)llrint(cl[5 + c] * 0x1p60);
+        }
     }
     return 0;
 }
@@ -942,6 +974,208 @@ int ora_get_closure_data(const ora_sim* s, double* out) {
 
 int ora_get_force_scale(const ora_sim* s, double* scale) {
     memcpy(scale, s->Fscale, sizeof(double) * (size_t)s->n);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Darcy flow: the fluid of Eq. 6 in the slow-flow limit              */
+/* ------------------------------------------------------------------ */
+
+/* conductance of the face between cells a and b along axis k */
+static double face_cond(const double h[3], double mu, int k, double Ka, double Kb) {
+    double A = h[(k + 1) % 3] * h[(k + 2) % 3];
+    return A / (mu * h[k]) * (2.0 * Ka * Kb / (Ka + Kb));
+}
+
+static double outlet_cond(const double h[3], double mu, double K) {
+    return h[0] * h[1] / (mu * 0.5 * h[2]) * K;
+}
+
+/* out = A x on the unknown cells (x of the other cells is ignored), and,
+   with b != NULL, the right-hand side of the fixed pressures */
+static void darcy_apply(int nx, int ny, int nz, const double h[3], double mu, const double* K,
+                        const int8_t* type, const uint8_t* outlet, double p_out, const double* pfix,
+                        const double* x, double* out, double* b) {
+    int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t c = 0; c < n; ++c) {
+        out[c] = 0.0;
+        if (b) b[c] = 0.0;
+        if (type[c] != 0) continue;
+        int i = (int)(c % nx), j = (int)((c / nx) % ny), l = (int)(c / ((int64_t)nx * ny));
+        int idx[3] = {i, j, l}, dim[3] = {nx, ny, nz};
+        int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+        double acc = 0.0, rhs = 0.0;
+        for (int k = 0; k < 3; ++k)
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                int q = idx[k] + sgn;
+                if (q < 0 || q >= dim[k]) continue;
+                int64_t nb = c + sgn * stride[k];
+                if (type[nb] == 2) continue;
+                double T = face_cond(h, mu, k, K[c], K[nb]);
+                if (type[nb] == 0) {
+                    acc += T * (x[c] - x[nb]);
+                } else {
+                    acc += T * x[c];
+                    rhs += T * pfix[nb];
+                }
+            }
+        if (outlet[c]) {
+            double T = outlet_cond(h, mu, K[c]);
+            acc += T * x[c];
+            rhs += T * p_out;
+        }
+        out[c] = acc;
+        if (b) b[c] = rhs;
+    }
+}
+
+static double darcy_diag(int nx, int ny, int nz, const double h[3], double mu, const double* K,
+                         const int8_t* type, const uint8_t* outlet, int64_t c) {
+    int i = (int)(c % nx), j = (int)((c / nx) % ny), l = (int)(c / ((int64_t)nx * ny));
+    int idx[3] = {i, j, l}, dim[3] = {nx, ny, nz};
+    int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+    double dg = 0.0;
+    for (int k = 0; k < 3; ++k)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int q = idx[k] + sgn;
+            if (q < 0 || q >= dim[k]) continue;
+            int64_t nb = c + sgn * stride[k];
+            if (type[nb] == 2) continue;
+            dg += face_cond(h, mu, k, K[c], K[nb]);
+        }
+    if (outlet[c]) dg += outlet_cond(h, mu, K[c]);
+    return dg;
+}
+
+int ora_darcy_solve(int nx, int ny, int nz, const double h[3], double mu, const double* K,
+                    const int8_t* type, const uint8_t* outlet, double p_out, double* p,
+                    double tol, int max_iter) {
+    int64_t n = (int64_t)nx * ny * nz;
+    double* b = (double*)calloc((size_t)n, sizeof(double));
+    double* r = (double*)calloc((size_t)n, sizeof(double));
+    double* z = (double*)calloc((size_t)n, sizeof(double));
+    double* d = (double*)calloc((size_t)n, sizeof(double));
+    double* q = (double*)calloc((size_t)n, sizeof(double));
+    double* M = (double*)calloc((size_t)n, sizeof(double));
+    darcy_apply(nx, ny, nz, h, mu, K, type, outlet, p_out, p, p, q, b);
+    double bb = 0.0, rz = 0.0, rr = 0.0;
+    for (int64_t c = 0; c < n; ++c) {
+        if (type[c] != 0) continue;
+        M[c] = darcy_diag(nx, ny, nz, h, mu, K, type, outlet, c);
+        r[c] = b[c] - q[c];
+        z[c] = r[c] / M[c];
+        d[c] = z[c];
+        bb += b[c] * b[c];
+        rz += r[c] * z[c];
+        rr += r[c] * r[c];
+    }
+    int it = 0;
+    while (rr > tol * tol * bb && it < max_iter) {
+        darcy_apply(nx, ny, nz, h, mu, K, type, outlet, p_out, p, d, q, NULL);
+        double dq = 0.0;
+        for (int64_t c = 0; c < n; ++c)
+            if (type[c] == 0) dq += d[c] * q[c];
+        double alpha = rz / dq;
+        double rz1 = 0.0;
+        rr = 0.0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (type[c] != 0) continue;
+            p[c] += alpha * d[c];
+            r[c] -= alpha * q[c];
+            z[c] = r[c] / M[c];
+            rz1 += r[c] * z[c];
+            rr += r[c] * r[c];
+        }
+        double beta = rz1 / rz;
+        rz = rz1;
+        for (int64_t c = 0; c < n; ++c)
+            if (type[c] == 0) d[c] = z[c] + beta * d[c];
+        ++it;
+    }
+    free(b); free(r); free(z); free(d); free(q); free(M);
+    return rr > tol * tol * bb ? -1 : it;
+}
+
+int ora_darcy_velocity(int nx, int ny, int nz, const double h[3], double mu, const double* K,
+                       const int8_t* type, const uint8_t* outlet, double p_out, const double* p,
+                       double* U) {
+    int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t c = 0; c < n; ++c) {
+        U[3 * c] = U[3 * c + 1] = U[3 * c + 2] = 0.0;
+        if (type[c] != 0) continue;
+        int i = (int)(c % nx), j = (int)((c / nx) % ny), l = (int)(c / ((int64_t)nx * ny));
+        int idx[3] = {i, j, l}, dim[3] = {nx, ny, nz};
+        int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+        for (int k = 0; k < 3; ++k) {
+            double A = h[(k + 1) % 3] * h[(k + 2) % 3];
+            double u = 0.0; /* sum of the two face velocities along +k */
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                int qi = idx[k] + sgn;
+                if (qi < 0 || qi >= dim[k]) continue;
+                int64_t nb = c + sgn * stride[k];
+                if (type[nb] == 2) continue;
+                /* flux out of c through this face, along sgn * e_k */
+                double Q = face_cond(h, mu, k, K[c], K[nb]) * (p[c] - p[nb]);
+                u += sgn * Q / A;
+            }
+            if (k == 2 && outlet[c]) u += -outlet_cond(h, mu, K[c]) * (p[c] - p_out) / A;
+            U[3 * c + k] = 0.5 * u;
+        }
+    }
+    return 0;
+}
+
+/* Permeability of the cells (Kozeny-Carman) and the cells' roles: in a
+   cylinder, a cell whose centre lies outside the wall holds the injection
+   pressure; a bottom cell whose centre lies over the outlet drains to it */
+static void darcy_setup(const ora_sim* s, double* K, int8_t* type, uint8_t* outlet, double* p) {
+    const ora_params* P = &s->p;
+    int nx = P->nf[0], ny = P->nf[1], nz = P->nf[2];
+    double d2 = P->perm_d * P->perm_d / 180.0;
+    for (int64_t c = 0; c < s->ncell_f; ++c) {
+        int i = (int)(c % nx), j = (int)((c / nx) % ny), l = (int)(c / ((int64_t)nx * ny));
+        double xc = P->f_lo[0] + (i + 0.5) * P->hf[0];
+        double yc = P->f_lo[1] + (j + 0.5) * P->hf[1];
+        double rc = sqrt(xc * xc + yc * yc);
+        double n = porosity(s->vf[c], P->n_min);
+        if (n > P->n_cap) n = P->n_cap;
+        K[c] = d2 * n * n * n / ((1.0 - n) * (1.0 - n));
+        type[c] = rc >= P->Rc ? 1 : 0;
+        if (type[c] == 1) p[c] = P->p_inlet;
+        outlet[c] = (l == 0 && rc < P->r_out && type[c] == 0) ? 1 : 0;
+    }
+}
+
+/* solve the sample's flow from the current porosity; the drag then uses U / n */
+static int solve_fluid(ora_sim* s) {
+    const ora_params* P = &s->p;
+    int64_t n = s->ncell_f;
+    double* K = (double*)calloc((size_t)n, sizeof(double));
+    int8_t* type = (int8_t*)calloc((size_t)n, sizeof(int8_t));
+    uint8_t* outlet = (uint8_t*)calloc((size_t)n, sizeof(uint8_t));
+    darcy_setup(s, K, type, outlet, s->pres);
+    s->fluid_iters = ora_darcy_solve(P->nf[0], P->nf[1], P->nf[2], P->hf, P->mu_f, K, type, outlet,
+                                     0.0, s->pres, 1e-13, 100000);
+    ora_darcy_velocity(P->nf[0], P->nf[1], P->nf[2], P->hf, P->mu_f, K, type, outlet, 0.0, s->pres,
+                       s->Us);
+    for (int64_t c = 0; c < n; ++c)
+        for (int k = 0; k < 3; ++k) s->gradp[3 * c + k] = type[c] == 0 ? -P->mu_f * s->Us[3 * c + k] / K[c] : 0.0;
+    free(K);
+    free(type);
+    free(outlet);
+    return s->fluid_iters < 0 ? -1 : 0;
+}
+
+int ora_get_fluid(const ora_sim* s, double* p, double* U, double* gradp, int64_t* iters) {
+    if (p) memcpy(p, s->pres, sizeof(double) * (size_t)s->ncell_f);
+    if (U) memcpy(U, s->Us, sizeof(double) * 3 * (size_t)s->ncell_f);
+    if (gradp) memcpy(gradp, s->gradp, sizeof(double) * 3 * (size_t)s->ncell_f);
+    if (iters) *iters = s->fluid_iters;
+    return 0;
+}
+
+int ora_get_reaction(const ora_sim* s, int64_t* sums) {
+    memcpy(sums, s->react, sizeof(int64_t) * 3 * (size_t)s->ncell_f);
     return 0;
 }
 

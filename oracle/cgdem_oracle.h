@@ -47,6 +47,13 @@ typedef struct {
     double n_min;       /* lower clamp of the porosity */
     int vf_mode;        /* 0 centroid, 1 equal-volume cube overlap */
     int couple_every;   /* recompute the void fraction every k-th step */
+    /* fluid: 0 the superficial velocity given at creation; 1 (cylinder only)
+       Darcy flow from the porosity, solved at every coupling step: dynamic
+       pressure p_inlet outside the cylinder wall, 0 at the outlet */
+    int fluid_mode;
+    double p_inlet;     /* [Pa] */
+    double perm_d;      /* grain diameter of the Kozeny-Carman permeability [m] */
+    double n_cap;       /* porosity cap of the permeability (n -> 1 has none) */
 } ora_params;
 
 /* ---- closed forms and single-contact laws (pins and unit tests) ---- */
@@ -109,6 +116,33 @@ int ora_get_voidfrac(const ora_sim* s, uint64_t* cell_sums);
  * the magnitudes of its contact, wall and body force vectors. */
 int ora_get_force_scale(const ora_sim* s, double* scale);
 int ora_get_force_scale_net(const ora_sim* s, double* scale);
+/* Darcy flow on a Cartesian grid of nx x ny x nz cells (x fastest) with
+ * spacing h: K permeability per cell [m^2]; type 0 unknown, 1 pressure fixed
+ * at p[c], 2 no cell (no flux); outlet[c] != 0 joins a cell's lower z face to
+ * the pressure p_out half a cell below.  Between neighbouring cells the face
+ * conductance is A / (mu h) times the harmonic mean of their K; the outlet's
+ * is A_z K / (mu h_z / 2).  Solves the unknown pressures (p holds the first
+ * guess) by conjugate gradients with the diagonal as preconditioner until the
+ * residual is below tol times the right-hand side.  Returns the iterations,
+ * or -1 if max_iter did not reach tol. */
+int ora_darcy_solve(int nx, int ny, int nz, const double h[3], double mu, const double* K,
+                    const int8_t* type, const uint8_t* outlet, double p_out, double* p,
+                    double tol, int max_iter);
+/* Superficial velocity at cell centres from the solved pressures: per axis
+ * the mean of the face velocities -(K_f / mu) dp / h of the cell's two faces
+ * (0 through a domain edge or a cell of type 2); U[3 * c + k].  Cells of
+ * type 1 and 2 get 0. */
+int ora_darcy_velocity(int nx, int ny, int nz, const double h[3], double mu, const double* K,
+                       const int8_t* type, const uint8_t* outlet, double p_out, const double* p,
+                       double* U);
+/* The sample's fluid state (fluid_mode 1): pressure [Cf], superficial
+ * velocity [Cf,3], dynamic pressure gradient [Cf,3] = -mu U / K, the
+ * iterations of the last solve; the drag reaction of Eq. 7 per cell [Cf,3]
+ * as sums of the particles' drag forces in quanta of 2^-60 N (the cell's
+ * force density is that sum over V_cell). */
+int ora_get_fluid(const ora_sim* s, double* p, double* U, double* gradp, int64_t* iters);
+int ora_get_reaction(const ora_sim* s, int64_t* sums);
+
 /* Host threads for the following calls (<= 0 keeps the current number);
  * returns the number in use (1 without OpenMP). */
 int ora_set_threads(int nthreads);

@@ -28,6 +28,7 @@ class OraParams(C.Structure):
         ("f_lo", C.c_double * 3), ("hf", C.c_double * 3), ("inv_hf", C.c_double * 3),
         ("V_cell", C.c_double), ("n_min", C.c_double),
         ("vf_mode", C.c_int), ("couple_every", C.c_int),
+        ("fluid_mode", C.c_int), ("p_inlet", C.c_double), ("perm_d", C.c_double), ("n_cap", C.c_double),
     ]
 
 
@@ -64,6 +65,10 @@ def lib():
             ("ora_get_force_scale", i, [vp, vp]),
             ("ora_get_force_scale_net", i, [vp, vp]),
             ("ora_set_threads", i, [i]),
+            ("ora_darcy_solve", i, [i, i, i, pd, d, vp, vp, vp, d, vp, d, i]),
+            ("ora_darcy_velocity", i, [i, i, i, pd, d, vp, vp, vp, d, vp, vp]),
+            ("ora_get_fluid", i, [vp, vp, vp, vp, vp]),
+            ("ora_get_reaction", i, [vp, vp]),
             ("ora_pairs_bruteforce", i64, [vp, i64, pd, pd, d, vp, vp, i64]),
             ("ora_voidfrac", i, [vp, i64, pd, pd, vp]),
             ("ora_set_closure", i, [vp, i, d]),
@@ -100,6 +105,8 @@ def make_params(**kw) -> OraParams:
             setattr(p, k, v)
     if "couple_every" not in kw:
         p.couple_every = 1
+    if "n_cap" not in kw:
+        p.n_cap = 0.95
     return p
 
 
@@ -155,6 +162,32 @@ def drag(rho_f, mu_f, d, u, v, n):
     uu, vv = _f64(u, 3), _f64(v, 3)
     lib().ora_drag(rho_f, mu_f, d, _pd(uu), _pd(vv), n, _pd(f))
     return f
+
+
+def darcy_solve(nf, h, mu, K, ctype, outlet, p_out, p0, tol=1e-13, max_iter=100000):
+    """Pressures of a Darcy flow on a grid (see ora_darcy_solve); returns (p, iterations)."""
+    nx, ny, nz = (int(v) for v in nf)
+    hh = _f64(h, 3)
+    K = np.ascontiguousarray(K, dtype=np.float64).reshape(-1)
+    t = np.ascontiguousarray(ctype, dtype=np.int8).reshape(-1)
+    o = np.ascontiguousarray(outlet, dtype=np.uint8).reshape(-1)
+    p = np.array(p0, dtype=np.float64).reshape(-1)
+    it = lib().ora_darcy_solve(nx, ny, nz, _pd(hh), mu, K.ctypes.data, t.ctypes.data, o.ctypes.data,
+                               p_out, p.ctypes.data, tol, max_iter)
+    return p, it
+
+
+def darcy_velocity(nf, h, mu, K, ctype, outlet, p_out, p):
+    nx, ny, nz = (int(v) for v in nf)
+    hh = _f64(h, 3)
+    K = np.ascontiguousarray(K, dtype=np.float64).reshape(-1)
+    t = np.ascontiguousarray(ctype, dtype=np.int8).reshape(-1)
+    o = np.ascontiguousarray(outlet, dtype=np.uint8).reshape(-1)
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1)
+    U = np.zeros((len(p), 3))
+    lib().ora_darcy_velocity(nx, ny, nz, _pd(hh), mu, K.ctypes.data, t.ctypes.data, o.ctypes.data,
+                             p_out, p.ctypes.data, U.ctypes.data)
+    return U
 
 
 def set_threads(n):
@@ -288,6 +321,21 @@ class Sim:
             self.step(1)
             cd, cg = closure_corrections(theta, self.closure_data(), lo, hi, cd_max, cg_max)
             self.set_corrections(cd, cg)
+
+    def fluid(self):
+        """(pressure [Cf], superficial velocity [Cf,3], dynamic pressure
+        gradient [Cf,3], iterations of the last solve) of a Darcy sample."""
+        nc = self.ncell
+        p, U, g = np.zeros(nc), np.zeros((nc, 3)), np.zeros((nc, 3))
+        it = C.c_int64(0)
+        lib().ora_get_fluid(self.h, p.ctypes.data, U.ctypes.data, g.ctypes.data, C.byref(it))
+        return p, U, g, it.value
+
+    def reaction(self):
+        """Drag reaction per cell (Eq. 7) in quanta of 2^-60 N [Cf,3]."""
+        out = np.zeros((self.ncell, 3), np.int64)
+        lib().ora_get_reaction(self.h, out.ctypes.data)
+        return out
 
     def removed_step(self):
         out = np.zeros(self.n, np.int64)
