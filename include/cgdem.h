@@ -95,6 +95,21 @@ typedef struct {
     int couple_every;       /* recompute the porosity every k-th step (>= 1, equal in all samples) */
     double skin;            /* candidate-list skin [m]; > 2 |delta_C| required */
     double r_max;           /* largest grain radius the sample holds [m] (sizes the search grid) */
+    /* fluid: 0 the superficial velocity of cgdem_set_fluid_velocity;
+       1 (cylinders) two-way coupling by Darcy flow, the fluid of Eq. 6 in the
+       slow-flow limit: after every porosity update the dynamic pressure p
+       solves div(K(n) grad p) = 0 on the fluid grid with the Kozeny-Carman
+       permeability K = perm_d^2 n^3 / (180 (1 - n)^2) (n capped at 0.95),
+       p = p_inlet in the cells whose centre lies outside the cylinder wall
+       and p = 0 at the outlet (the lower face of the bottom cells whose
+       centre lies over it); the superficial velocity U = -(K / mu_f) grad p
+       (cell centre: mean of its two face velocities per axis) replaces the
+       prescribed one in the drag, every grain feels -V grad p (grad p =
+       -mu_f U / K of its cell), and the drag reaction of Eq. 7 is summed per
+       cell (cgdem_get_fluid) */
+    int fluid_mode;
+    double p_inlet;         /* injection (dynamic) pressure [Pa] */
+    double perm_d;          /* grain diameter of the Kozeny-Carman permeability [m] */
 } cgdem_sample_params;
 
 typedef struct {
@@ -109,6 +124,9 @@ typedef struct {
                                its force kernel runs blocks of 128 (block_size 0 or 128) */
     int particles_per_warp; /* spheres per warp of the fused force kernel: 32 (0 selects it),
                                or 16 (twice the warps: for samples too small to fill the GPU) */
+    int fluid_iters;        /* Darcy samples: conjugate-gradient iterations per solve at most
+                               (0 selects 2000; each solve starts from the last pressure) */
+    double fluid_tol;       /* stop when |residual| <= fluid_tol |right-hand side| (0 selects 1e-10) */
 } cgdem_config;
 
 typedef struct cgdem_ctx cgdem_ctx;
@@ -225,6 +243,18 @@ int cgdem_get_voidfrac(cgdem_ctx* ctx, uint64_t* cell_sums, int64_t cap, void* s
 /* Per sample, 8 doubles: translational KE, rotational KE, momentum x,y,z,
  * produced (outlet) mass, active particles, bonded contacts. */
 int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream);
+
+/* Fluid state of the Darcy samples (fluid_mode 1), HOST arrays over all
+ * samples' fluid cells (sample after sample, x fastest), any may be NULL:
+ * p [Cf] dynamic pressure [Pa]; U [Cf,3] superficial velocity [m/s];
+ * gradp [Cf,3] its driving gradient -mu_f U / K [Pa/m]; reaction [Cf,3] the
+ * drag forces of the grains in each cell at the last force evaluation
+ * (Eq. 7: the fluid's force density is this over V_cell) in integer quanta
+ * of 2^-60 N; *iters the iterations of the last solve (-1: it stopped at
+ * fluid_iters short of fluid_tol).  Cells of other samples hold zeros.
+ * Synchronises stream. */
+int cgdem_get_fluid(cgdem_ctx* ctx, double* p, double* U, double* gradp, int64_t* reaction,
+                    int64_t* iters, void* stream);
 
 /* Produced sand by size class (Sec. 3.4, Fig. 11).  edges: nclass + 1
  * increasing fine-scale diameters [m] (HOST), 1 <= nclass <= 16, or nclass

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcgdem.so")
-SOURCES = ["k_forces.cu", "k_other.cu", "api.cu", "noalloc.cu", "k_mlp.cu"]
+SOURCES = ["k_forces.cu", "k_other.cu", "api.cu", "noalloc.cu", "k_mlp.cu", "k_fluid.cu"]
 # every translation unit is rebuilt when any shared header changes
 HEADERS = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))) + [
     os.path.join(ROOT, "include", "cgdem.h")]

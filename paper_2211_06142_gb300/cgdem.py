@@ -34,7 +34,7 @@ EXPORTS = [
     "cgdem_destroy", "cgdem_last_error", "cgdem_status_sync", "cgdem_init_particles",
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
     "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
-    "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step", "cgdem_set_psd_classes", "cgdem_get_produced_psd",
+    "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step", "cgdem_set_psd_classes", "cgdem_get_produced_psd", "cgdem_get_fluid",
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
     "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
@@ -61,6 +61,7 @@ class SampleParams(C.Structure):
         ("inv_hf", C.c_double * 3), ("V_cell", C.c_double), ("n_min", C.c_double),
         ("vf_mode", C.c_int), ("couple_every", C.c_int), ("skin", C.c_double),
         ("r_max", C.c_double),
+        ("fluid_mode", C.c_int), ("p_inlet", C.c_double), ("perm_d", C.c_double),
     ]
 
 
@@ -69,6 +70,7 @@ class Config(C.Structure):
         ("precision", C.c_int), ("n_samples", C.c_int), ("max_neighbors", C.c_int),
         ("block_size", C.c_int), ("cell_scale", C.c_double), ("steps_per_graph", C.c_int),
         ("closure", C.c_int), ("particles_per_warp", C.c_int),
+        ("fluid_iters", C.c_int), ("fluid_tol", C.c_double),
     ]
 
 
@@ -113,6 +115,7 @@ def lib():
             "cgdem_get_diagnostics": (i, [vp, vp, i64, vp]),
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
             "cgdem_set_psd_classes": (i, [vp, vp, i, vp]),
+            "cgdem_get_fluid": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "cgdem_get_produced_psd": (i, [vp, vp, vp, i64, vp]),
             "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
             "cgdem_get_launch_counts": (i, [vp, vp, vp]),
@@ -281,7 +284,7 @@ def spheres_per_warp_for(n, device="cuda:0"):
 
 def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1,
                   coulomb_mode=0, vf_mode=0, couple_every=1, n_min=0.2, r_max=None,
-                  gamma_fine=None) -> SampleParams:
+                  gamma_fine=None, fluid_mode=0, p_inlet=0.0, perm_d=None) -> SampleParams:
     """SampleParams from an inputs.Sample-like object (material at fine scale)."""
     p = SampleParams()
     m = s.material
@@ -308,6 +311,10 @@ def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1
     p.couple_every = int(couple_every)
     p.skin = float(skin)
     p.r_max = float(r_max if r_max is not None else np.max(s.R))
+    p.fluid_mode = int(fluid_mode)
+    p.p_inlet = float(p_inlet)
+    # Kozeny-Carman diameter: the volume-mean grain diameter unless given
+    p.perm_d = float(perm_d if perm_d is not None else np.mean((2 * np.asarray(s.R)) ** 3) ** (1 / 3))
     return p
 
 
@@ -316,7 +323,7 @@ class Context:
 
     def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
                  cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None, closure=False,
-                 particles_per_warp=32):
+                 particles_per_warp=32, fluid_iters=0, fluid_tol=0.0):
         import torch
 
         if not torch.cuda.is_available():
@@ -328,7 +335,8 @@ class Context:
         self.counts = np.ascontiguousarray(counts, dtype=np.int64)
         self.N = int(self.counts.sum())
         self.cfg = Config(precision, self.n_samples, max_neighbors, block_size, cell_scale,
-                          steps_per_graph, int(bool(closure)), int(particles_per_warp))
+                          steps_per_graph, int(bool(closure)), int(particles_per_warp), int(fluid_iters),
+                          float(fluid_tol))
         nbytes = C.c_size_t(0)
         r = lib().cgdem_workspace_size(C.byref(self.cfg), self._params, _ptr(self.counts),
                                        C.byref(nbytes))
@@ -448,6 +456,17 @@ class Context:
         out = np.zeros(self.N, np.int32)
         self._check(lib().cgdem_get_removed_step(self.h, _ptr(out), self._s()), "get_removed_step")
         return out
+
+    def get_fluid(self, ncell):
+        """(pressure [Cf], superficial velocity [Cf,3], pressure gradient
+        [Cf,3], drag reaction [Cf,3] in 2^-60 N quanta, iterations of the last
+        solve) of the Darcy samples."""
+        p, U, g = np.zeros(ncell), np.zeros((ncell, 3)), np.zeros((ncell, 3))
+        r = np.zeros((ncell, 3), np.int64)
+        it = C.c_int64(0)
+        self._check(lib().cgdem_get_fluid(self.h, _ptr(p), _ptr(U), _ptr(g), _ptr(r), C.byref(it), self._s()),
+                    "get_fluid")
+        return p, U, g, r, it.value
 
     def set_psd_classes(self, edges):
         """Record produced sand by size class (fine-scale diameter edges [m])."""

@@ -25,6 +25,12 @@ void launch_cube_after_mid(const Dev& d, cudaStream_t s);
 void launch_init(const Dev& d, cudaStream_t s);
 void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
+void launch_fluid_mark(const Dev& d, cudaStream_t s);
+void launch_fluid_head(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_fluid_iteration(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_fluid_tail(const Dev& d, cudaStream_t s);
+void launch_react_clear(const Dev& d, cudaStream_t s);
+int fluid_blocks(int Cf_total);
 void launch_collect_springs(const Dev& d, uint32_t* out, double* xi, unsigned long long cap, cudaStream_t s);
 void launch_diag(const Dev& d, double* part, cudaStream_t s);
 void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s);
@@ -44,6 +50,7 @@ struct StepGraph {
 };
 constexpr int GRAPH_HEAD = -1;
 constexpr int GRAPH_TAIL = -2;
+constexpr int GRAPH_FLUID = -3;  // a Darcy solve on its own (the coupling verbs)
 
 struct cgdem_ctx {
   cgdem_config cfg;
@@ -250,6 +257,15 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   s.rho_s_f = (float)s.rho;
   s.k_feat_f = (float)k_cg;
   s.k_cg = k_cg;
+  if (p.fluid_mode != 0 && p.fluid_mode != 1)
+    return fail(ctx, CGDEM_E_INVALID, "fluid_mode must be 0 or 1");
+  if (p.fluid_mode == 1 && (p.kind != CGDEM_CYLINDER || !(p.perm_d > 0) || !std::isfinite(p.p_inlet) ||
+                            !p.use_drag))
+    return fail(ctx, CGDEM_E_INVALID, "Darcy flow (fluid_mode 1) needs a cylinder, use_drag, perm_d > 0 "
+                "and a finite p_inlet");
+  s.fluid_mode = p.fluid_mode;
+  s.p_inlet = p.p_inlet;
+  s.perm_d2 = p.perm_d * p.perm_d / 180.0;
   s.n_psd = 0;  // no size classes until cgdem_set_psd_classes
   // mass quantum: 2^-40 of the largest grain's mass (a grain's quanta fit
   // 40 bits, 2^23 of the largest grains fit a class sum)
@@ -356,6 +372,30 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.disp = cv.take<double>(S);
   d.vmax2 = cv.take<unsigned long long>(S);
   d.diag = cv.take<double>(8 * (size_t)S);
+  bool fluid = false;
+  for (int k = 0; k < S; ++k) fluid |= sp[k].fluid_mode == 1;
+  if (fluid) {
+    const size_t nc = (size_t)Cf + 1;
+    d.fl_sample = cv.take<int>(nc);
+    d.fl_type = cv.take<signed char>(nc);
+    d.fl_K = cv.take<double>(nc);
+    d.fl_p = cv.take<double>(nc);
+    d.fl_r = cv.take<double>(nc);
+    d.fl_z = cv.take<double>(nc);
+    d.fl_d = cv.take<double>(nc);
+    d.fl_q = cv.take<double>(nc);
+    d.fl_M = cv.take<double>(nc);
+    d.fl_b = cv.take<double>(nc);
+    d.fl_blocks = fluid_blocks(Cf);
+    d.fl_part = cv.take<double>(4 * (size_t)d.fl_blocks);
+    d.gradp = cv.take<double4>(nc);
+    d.gradpf = cv.take<float4>(nc);
+    d.react[0] = cv.take<unsigned long long>(3 * nc);
+    d.react[1] = cv.take<unsigned long long>(3 * nc);
+    d.any_fluid = 1;
+  }
+  d.fl_iters_max = cfg->fluid_iters > 0 ? cfg->fluid_iters : 2000;
+  d.fl_tol = cfg->fluid_tol > 0 ? cfg->fluid_tol : 1e-10;
   d.psd_count = cv.take<unsigned long long>((size_t)CGDEM_PSD_MAX * S);
   d.psd_mass = cv.take<unsigned long long>((size_t)CGDEM_PSD_MAX * S);
   d.staging = cv.take<double>(16 * (size_t)Npad);
@@ -455,6 +495,51 @@ cudaError_t add_rebuild_node(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs,
   return cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
+// Append a Darcy solve to the capture on cs (it does nothing unless a
+// porosity update is pending): the set-up kernels, then the conjugate-gradient
+// iterations as the body of a WHILE node (captured on bs) whose condition the
+// kernels set, then the velocity field.  Without conditional nodes, the
+// iterations are captured fluid_iters times (each returns at once once the
+// solve has converged).
+cudaError_t add_fluid_solve(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs, bool conditional) {
+  if (!conditional) {
+    launch_fluid_head(ctx->d, 0, cs);
+    for (int i = 0; i < ctx->d.fl_iters_max; ++i) launch_fluid_iteration(ctx->d, 0, cs);
+    launch_fluid_tail(ctx->d, cs);
+    return cudaSuccess;
+  }
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t cg;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, cg, 0u, 0u);
+  if (e != cudaSuccess) return e;
+  launch_fluid_head(ctx->d, h, cs);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  launch_fluid_iteration(ctx->d, h, bs);
+  e = cudaStreamEndCapture(bs, &body);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  launch_fluid_tail(ctx->d, cs);
+  return cudaSuccess;
+}
+
 // Capture one part of cgdem_step into a graph:
 //   part = U > 0: U fused steps (rebuild if flagged, forces, kick, drift,
 //     porosity).  Each step's rebuild sequence sits in the body of a
@@ -480,8 +565,9 @@ cudaError_t capture_part(cgdem_ctx* ctx, int part, bool conditional, StepGraph* 
   cudaGraph_t g = nullptr;
   int body_kernels = 0;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (part == GRAPH_HEAD) {
-    if (e == cudaSuccess) launch_kick_drift(ctx->d, 1, cs);
+  if (part == GRAPH_HEAD || part == GRAPH_FLUID) {
+    if (e == cudaSuccess && part == GRAPH_HEAD) launch_kick_drift(ctx->d, 1, cs);
+    if (e == cudaSuccess && ctx->d.any_fluid) e = add_fluid_solve(ctx, cs, bs, conditional);
   } else {
     const int U = part > 0 ? part : 1;
     const bool tail = part == GRAPH_TAIL;
@@ -511,6 +597,10 @@ cudaError_t capture_part(cgdem_ctx* ctx, int part, bool conditional, StepGraph* 
         launch_forces(ctx->d, 1, ctx->cfg.block_size, cs,
                       conditional && i + 1 < U ? hs[i + 1] : 0);
         if (ctx->any_cube) launch_cube_after_mid(ctx->d, cs);
+        if (ctx->d.any_fluid) {
+          e = add_fluid_solve(ctx, cs, bs, conditional);
+          if (e != cudaSuccess) break;
+        }
       }
     }
   }
@@ -552,7 +642,7 @@ int launch_part(cgdem_ctx* ctx, int part, cudaStream_t s) {
     it = ctx->graphs.emplace(key, g).first;
   }
   CK(cudaGraphLaunch(it->second.exec, s));
-  ctx->step_kernels += it->second.kernels;
+  if (part != GRAPH_FLUID) ctx->step_kernels += it->second.kernels;
   if (it->second.body_kernels) ctx->rebuild_kernels = it->second.body_kernels;
   return CGDEM_OK;
 }
@@ -645,6 +735,20 @@ int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const i
   // fluid velocity starts at zero
   cudaMemset(ctx->d.Us, 0, sizeof(double4) * ((size_t)ctx->d.Cf_total + 1));
   cudaMemset(ctx->d.Usf, 0, sizeof(float4) * ((size_t)ctx->d.Cf_total + 1));
+  if (ctx->d.any_fluid) {  // Darcy flow: each cell's sample; pressures and gradients start at zero
+    const size_t nc = (size_t)ctx->d.Cf_total + 1;
+    std::vector<int> cs(nc, 0);
+    for (size_t k = 0; k < ctx->sd.size(); ++k)
+      for (int c = 0; c < ctx->sd[k].nf[0] * ctx->sd[k].nf[1] * ctx->sd[k].nf[2]; ++c)
+        cs[(size_t)ctx->sd[k].fcell_off + c] = (int)k;
+    cudaMemcpy(ctx->d.fl_sample, cs.data(), sizeof(int) * nc, cudaMemcpyHostToDevice);
+    cudaMemset(ctx->d.fl_p, 0, sizeof(double) * nc);
+    cudaMemset(ctx->d.fl_type, 2, nc);
+    cudaMemset(ctx->d.gradp, 0, sizeof(double4) * nc);
+    cudaMemset(ctx->d.gradpf, 0, sizeof(float4) * nc);
+    cudaMemset(ctx->d.react[0], 0, sizeof(unsigned long long) * 3 * nc);
+    cudaMemset(ctx->d.react[1], 0, sizeof(unsigned long long) * 3 * nc);
+  }
   *out = ctx;
   return CGDEM_OK;
 }
@@ -716,6 +820,11 @@ int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const
   launch_rebuild(ctx->d, s);
   if (bond_touching) launch_bond_touching(ctx->d, s);
   launch_couple(ctx->d, s);
+  if (ctx->d.any_fluid) {  // the initial Darcy flow of the initial porosity
+    launch_fluid_mark(ctx->d, s);
+    int rr = launch_part(ctx, GRAPH_FLUID, s);
+    if (rr) return rr;
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   ctx->initialised = true;
@@ -736,6 +845,10 @@ int cgdem_couple_fluid(cgdem_ctx* ctx, void* stream) {
   int r = ready(ctx);
   if (r) return r;
   launch_couple(ctx->d, st(stream));
+  if (ctx->d.any_fluid) {  // two-way coupling: the Darcy flow of the new porosity
+    launch_fluid_mark(ctx->d, st(stream));
+    if ((r = launch_part(ctx, GRAPH_FLUID, st(stream)))) return r;
+  }
   CK(cudaGetLastError());
   return CGDEM_OK;
 }
@@ -743,6 +856,7 @@ int cgdem_couple_fluid(cgdem_ctx* ctx, void* stream) {
 int cgdem_compute_forces(cgdem_ctx* ctx, void* stream) {
   int r = ready(ctx);
   if (r) return r;
+  if (ctx->d.any_fluid) launch_react_clear(ctx->d, st(stream));
   launch_forces(ctx->d, 0, ctx->cfg.block_size, st(stream), 0);
   CK(cudaGetLastError());
   return CGDEM_OK;
@@ -964,6 +1078,43 @@ int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream
   CK(cudaMemcpyAsync(out, ctx->d.diag, sizeof(double) * 8 * ctx->d.n_samples,
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return check_status(ctx, s);
+}
+
+int cgdem_get_fluid(cgdem_ctx* ctx, double* p, double* U, double* gradp, int64_t* reaction,
+                    int64_t* iters, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  cudaStream_t s = st(stream);
+  const size_t nc = (size_t)ctx->d.Cf_total;
+  if (!ctx->d.any_fluid) {
+    if (p) std::fill(p, p + nc, 0.0);
+    if (U) std::fill(U, U + 3 * nc, 0.0);
+    if (gradp) std::fill(gradp, gradp + 3 * nc, 0.0);
+    if (reaction) std::fill(reaction, reaction + 3 * nc, (int64_t)0);
+    if (iters) *iters = 0;
+    return CGDEM_OK;
+  }
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, ctx->d.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+  std::vector<double4> u(nc), g(nc);
+  if (p) CK(cudaMemcpyAsync(p, ctx->d.fl_p, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(u.data(), ctx->d.Us, sizeof(double4) * nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(g.data(), ctx->d.gradp, sizeof(double4) * nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // the last force evaluation's reaction buffer
+  if (reaction)
+    CK(cudaMemcpyAsync(reaction, ctx->d.react[c.step & 1], sizeof(int64_t) * 3 * nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<signed char> t(nc);
+  CK(cudaMemcpy(t.data(), ctx->d.fl_type, nc, cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < nc; ++k) {
+    const double w = t[k] == 2 ? 0.0 : 1.0;  // cells of samples without Darcy flow hold zeros
+    if (p && t[k] == 2) p[k] = 0.0;
+    if (U) { U[3 * k] = w * u[k].x; U[3 * k + 1] = w * u[k].y; U[3 * k + 2] = w * u[k].z; }
+    if (gradp) { gradp[3 * k] = w * g[k].x; gradp[3 * k + 1] = w * g[k].y; gradp[3 * k + 2] = w * g[k].z; }
+  }
+  if (iters) *iters = c.fl_iters;
   return check_status(ctx, s);
 }
 

@@ -80,6 +80,10 @@ struct SampleDev {
   // fine grains of diameter 2 R / k; class c holds psd_edge[c] <= 2 R / k <
   // psd_edge[c + 1] (the first and last classes also take what lies below or
   // above); masses are summed in quanta of psd_mq (0 classes: not recorded)
+  // Darcy flow (fluid_mode 1): K = perm_d2 n^3 / (1 - n)^2 with perm_d2 =
+  // perm_d^2 / 180 and n <= DARCY_N_CAP
+  int fluid_mode;
+  double p_inlet, perm_d2;
   double k_cg;
   int n_psd;
   double psd_edge[CGDEM_PSD_MAX + 1];
@@ -124,7 +128,13 @@ struct Ctl {
   // distance and squared reach (fixed-point units) at the rebuild
   int lost_i, lost_j;
   unsigned long long lost_d2, lost_S2;
+  // Darcy solve: a porosity update not yet followed by a solve; the
+  // conjugate-gradient scalars of the running solve
+  int fl_pending, fl_done, fl_it;
+  long long fl_iters;  // iterations of the last solve (-1: stopped short of the tolerance)
+  double fl_rz, fl_alpha, fl_beta, fl_bb;
 };
+constexpr double DARCY_N_CAP = 0.95;  // the permeability's porosity cap
 
 // All device pointers of a context (passed by value to kernels).
 struct Dev {
@@ -186,6 +196,20 @@ struct Dev {
   double* disp;                   // per-sample displacement bound since last rebuild
   unsigned long long* vmax2;      // per-sample max (|v| dt)^2 of the last drift (double bits)
   double* diag;                   // per-sample diagnostics [S][8]
+  // Darcy flow, per fluid cell (allocated when a sample has fluid_mode 1)
+  int* fl_sample;                 // the cell's sample
+  signed char* fl_type;           // 0 unknown, 1 fixed pressure, 2 not solved, 3 unknown draining to the outlet
+  double* fl_K;                   // permeability
+  double* fl_p;                   // dynamic pressure (kept: the next solve starts from it)
+  double *fl_r, *fl_z, *fl_d, *fl_q, *fl_M, *fl_b;  // conjugate-gradient vectors, diagonal, right-hand side
+  double* fl_part;                // per-block partial sums [4][fl_blocks]
+  int fl_blocks;
+  double4* gradp;                 // grad p per cell (w unused)
+  float4* gradpf;
+  unsigned long long* react[2];   // drag reaction [Cf][3], quanta of 2^-60 N; by parity of the evaluation
+  int any_fluid;
+  int fl_iters_max;
+  double fl_tol;
   unsigned long long* psd_count;  // produced grains per sample and size class [S][CGDEM_PSD_MAX]
   unsigned long long* psd_mass;   // their mass in quanta of the sample's psd_mq [S][CGDEM_PSD_MAX]
   double* staging;                // [N * 16] host-transfer staging

@@ -615,6 +615,27 @@ __device__ __forceinline__ void finish_step(
             F.y += fd.y;
             F.z += fd.z;
           }
+          if (S.fluid_mode == 1 && d.any_fluid) {
+            // Darcy flow: the dynamic pressure gradient on the grain's volume,
+            // and the drag's reaction on the fluid (Eq. 7) summed per cell in
+            // integer quanta of 2^-60 N, into the buffer of this evaluation
+            V3<T> G;
+            if constexpr (MIXED) {
+              const float4 g = d.gradpf[fc];
+              G = v3<T>(g.x, g.y, g.z);
+            } else {
+              const double4 g = d.gradp[fc];
+              G = v3<T>(g.x, g.y, g.z);
+            }
+            F.x -= Vp * G.x;
+            F.y -= Vp * G.y;
+            F.z -= Vp * G.z;
+            const long long e = MODE == MODE_FORCES ? m_step - 1 : m_step;
+            unsigned long long* rx = d.react[e & 1] + 3 * (size_t)fc;
+            atomicAdd(rx, (unsigned long long)__double2ll_rn((double)fd.x * 1152921504606846976.0));
+            atomicAdd(rx + 1, (unsigned long long)__double2ll_rn((double)fd.y * 1152921504606846976.0));
+            atomicAdd(rx + 2, (unsigned long long)__double2ll_rn((double)fd.z * 1152921504606846976.0));
+          }
           if (feat) {
             net_row = true;
             ft[0] = (float)(T(1) - nc);
@@ -787,6 +808,12 @@ __device__ __forceinline__ void finish_step(
 
   // ---- bookkeeping: displacement since rebuild, porosity rotation, step ----
   const int wib = threadIdx.x >> 5;
+  if (d.any_fluid) {  // the next evaluation's reaction buffer starts at zero
+    const long long e = MODE == MODE_FORCES ? m_step - 1 : m_step;
+    unsigned long long* z = d.react[(e + 1) & 1];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 3 * d.Cf_total; c += gridDim.x * blockDim.x)
+      z[c] = 0ull;
+  }
   if (MODE == MODE_MID) {
     unsigned long long* z = d.vf[(vfc + 2) % 3];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.Cf_total; c += gridDim.x * blockDim.x)
@@ -837,7 +864,10 @@ __device__ __forceinline__ void finish_step(
           const unsigned b = atomicAdd(&d.dmax2[s], 0u);
           if (__uint_as_float(b) > d.sp[s].rebuild_q2) ctl->rebuild = 1;
         }
-        if (atomicExch(&ctl->coupled, 0u)) ctl->vf_cur = (vfc + 1) % 3;
+        if (atomicExch(&ctl->coupled, 0u)) {
+          ctl->vf_cur = (vfc + 1) % 3;
+          ctl->fl_pending = 1;  // the Darcy flow follows the new porosity
+        }
         ctl->cur = nxt;
         ctl->step = m_step;
       }

@@ -983,7 +983,10 @@ __global__ void k_after_drift(Dev d, int couple) {
     if (__uint_as_float(d.dmax2[s]) > d.sp[s].rebuild_q2) c->rebuild = 1;
     if ((c->step % d.sp[s].couple_every) == 0) any = true;
   }
-  if (couple && any) c->vf_cur = (c->vf_cur + 1) % 3;
+  if (couple && any) {
+    c->vf_cur = (c->vf_cur + 1) % 3;
+    c->fl_pending = 1;  // the Darcy flow follows the new porosity
+  }
 }
 
 // final half kick + outlet (in place), completes a step.
@@ -1099,6 +1102,10 @@ __global__ void k_init_ctl(Dev d) {
   c->lost_j = -1;
   c->lost_d2 = 0;
   c->lost_S2 = 0;
+  c->fl_pending = 0;
+  c->fl_done = 1;
+  c->fl_it = -1;
+  c->fl_iters = 0;
   for (int s = 0; s < d.n_samples; ++s) d.dmax2[s] = 0u;
 }
 
