@@ -50,7 +50,7 @@ def setup(prec, couple_every=5):
 def field_check(s, ctx, sim):
     gp, gU, gG, gR, it = ctx.get_fluid(s.grid.ncell)
     op, oU, oG, oit = sim.fluid()
-    assert it > 0 and oit > 0
+    assert it >= 0 and oit >= 0  # converged (0: the last pressure already solved the new porosity)
     assert np.abs(gp - op).max() <= 1e-9 * np.abs(op).max()
     assert np.abs(gU - oU).max() <= 1e-8 * np.abs(oU).max()
     assert np.abs(gG - oG).max() <= 1e-8 * np.abs(oG).max()
@@ -72,6 +72,7 @@ def force_bound(s, sim, gU, oU, tau):
 @pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
 def test_darcy_flow_and_forces_match_the_oracle(prec):
     s, ctx, sim = setup(prec)
+    assert ctx.get_fluid(s.grid.ncell)[4] > 0  # the first solve starts from zero pressure
     gU, oU, gR = field_check(s, ctx, sim)
     g, o = ctx.get_state(), sim.state()
     b = force_bound(s, sim, gU, oU, TOL[prec])
