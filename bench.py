@@ -363,6 +363,34 @@ def run_closure_cost(torch, device, barrier, K=2000):
     return out
 
 
+def run_darcy(torch, device, barrier, K=1000, couple_every=100, p_inlet=2000.0):
+    """Cost of the two-way coupling: the 200k-sphere cylinder in mixed
+    precision with the flow solved by Darcy's law after every porosity
+    update (every couple_every steps, the paper's dt_CFD = 100 dt_DEM), beside
+    the same steps with the prescribed radial inflow."""
+    from paper_2211_06142_gb300 import cgdem
+    s = make_workload_200k(1)
+    dt, skin = step_params(s)
+    out = {"workload": "200k-sphere cylinder, mixed", "couple_every": couple_every, "p_inlet_Pa": p_inlet}
+    for name, mode in (("prescribed", 0), ("darcy", 1)):
+        p = cgdem.sample_params(s, dt, skin, couple_every=couple_every, fluid_mode=mode, p_inlet=p_inlet)
+        ctx = cgdem.Context([p], [len(s.R)], precision=cgdem.MIXED, max_neighbors=48, device=device,
+                            cell_scale=0.5)
+        ctx.set_fluid_velocity(s.Us)
+        ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
+        ctx.compute_forces()
+        ctx.step(50)
+        el = time_steps(ctx, torch, K, barrier)
+        out[name] = {"value": len(s.R) * K / el, "ms_per_step": 1e3 * el / K}
+        if mode:
+            fl = ctx.get_fluid(s.grid.ncell)
+            out[name]["last_solve_iterations"] = int(fl[4])
+            out[name]["max_abs_pressure_Pa"] = float(np.abs(fl[0]).max())
+        ctx.close()
+    out["solve_ms_per_coupling"] = (out["darcy"]["ms_per_step"] - out["prescribed"]["ms_per_step"]) * couple_every
+    return out
+
+
 def time_steps(ctx, torch, K, barrier):
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -637,6 +665,7 @@ def main():
             b["roofline_frac"] = b["force_kernel_gbs"] / measured_peaks()[0]["hbm_gbs"]
             extras["batched"] = b
         extras["closure"] = run_closure_cost(torch, device, barrier, min(max(K, 500), 2000))
+        extras["two_way_coupling"] = run_darcy(torch, device, barrier, min(max(K, 500), 2000))
         if rank == 0 and not args.no_sand:
             extras["sand"] = run_sand()
 

@@ -15,7 +15,8 @@
 Options (before or after the mode's arguments): --cell S (search-cell
 scale), --skin F (skin / largest grain diameter), --block B (threads per
 block of the force kernel), --ppw P (spheres per warp of that kernel), for
-capturing the launch configuration the autotuner chose.
+capturing the launch configuration the autotuner chose; --workload
+cylinder200k | tiled500k | tiled2m (the benchmark's 2.0M-sphere cylinder).
 
 Each prints its counters and "ok" when it ends without an error.
 """
@@ -26,14 +27,23 @@ import sys
 import numpy as np
 
 
-KNOBS = {"cell": 0.0, "skin": None, "block": 128, "ppw": 32}
+KNOBS = {"cell": 0.0, "skin": None, "block": 128, "ppw": 32, "workload": "cylinder200k"}
+
+# --workload: the 200k-sphere cylinder, or the tiled cylinders of about
+# 500k spheres (radius and height x1.357) and 2.0M spheres (x2.15, the
+# benchmark's headline sample)
+WORKLOADS = {
+    "cylinder200k": lambda I: I.cached(I.fine_cylinder),
+    "tiled500k": lambda I: I.cached(I.tiled_cylinder, 500_000, 1.357, 5, nf=(54, 54, 27)),
+    "tiled2m": lambda I: I.cached(I.tiled_cylinder, 2_000_000, 2.15, 4),
+}
 
 
 def _cylinder_ctx(precision, closure=False, k=1, steps_per_graph=32):
     from . import cgdem
     from . import inputs as I
     from . import workloads as W
-    s = I.cached(I.fine_cylinder) if k == 1 else W.coarse_cylinder(k=k)
+    s = WORKLOADS[KNOBS["workload"]](I) if k == 1 else W.coarse_cylinder(k=k)
     m = s.material
     Rbar = float(np.mean(s.R ** 3)) ** (1 / 3)
     dt = 0.2 * cgdem.cgdem_rayleigh_dt(Rbar, m["rho"], m["E"], m["nu"])
@@ -57,7 +67,7 @@ def main(argv):
     B.build()
     argv = list(argv)
     for flag, key, conv in (("--cell", "cell", float), ("--skin", "skin", float),
-                            ("--block", "block", int), ("--ppw", "ppw", int)):
+                            ("--block", "block", int), ("--ppw", "ppw", int), ("--workload", "workload", str)):
         if flag in argv:
             i = argv.index(flag)
             KNOBS[key] = conv(argv[i + 1])
