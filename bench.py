@@ -155,6 +155,8 @@ def kernel_traffic(kernel_file, kernel, knobs):
         e = t.get(kernel)
         if not e or e.get("source_sha1") != h:
             return None
+        if knobs is None:  # a per-particle figure that holds for any launch configuration
+            return e
         for c in e.get("configs", []):
             if int(c.get("n", -1)) != int(knobs.get("n", -2)):
                 continue
@@ -520,13 +522,24 @@ def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=
     ks1, body = ctx.launch_counts()
     gpu_launches = (ks1 - ks0) + body * rebuilds_timed
     # natural rebuild rate over a longer stretch, and the cost of a rebuild
-    cal = max(400, 4 * K) if K < 400 else 0
-    rb1 = ctx.counters()["rebuilds"]
-    if cal:
-        ctx.step(cal)
-    rate = (ctx.counters()["rebuilds"] - rb1 + rebuilds_timed) / float(cal + K)
+    # inside the step graphs: the stretch runs as calls of 32 steps, each
+    # timed, and a least-squares fit of call time = a + b * (rebuilds in the
+    # call) gives b
+    cal_calls = max(0, -(-(2000 - K) // 32))
+    rows = []
+    for _ in range(cal_calls):
+        r0 = ctx.counters()["rebuilds"]
+        t = time_steps(ctx, torch, 32, barrier)
+        rows.append((t, ctx.counters()["rebuilds"] - r0))
+    cal = 32 * cal_calls
+    rate = (sum(r for _, r in rows) + rebuilds_timed) / float(cal + K)
     prof = ctx.profile_step(200)
-    rb_ms = prof["rebuild_ms_total"] / prof["rebuilds"] if prof["rebuilds"] else 0.0
+    rb_host_ms = prof["rebuild_ms_total"] / prof["rebuilds"] if prof["rebuilds"] else 0.0
+    rb_ms = rb_host_ms
+    if rows and len({r for _, r in rows}) > 1:
+        A = np.array([[1.0, r] for _, r in rows])
+        y = np.array([t for t, _ in rows])
+        rb_ms = float(np.linalg.lstsq(A, y, rcond=None)[0][1]) * 1e3
     el_am = el + (rate * K - rebuilds_timed) * rb_ms * 1e-3
     if world > 1:
         import torch.distributed as dist
@@ -562,8 +575,9 @@ def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=
            "raw": {"value": N * K * world / el, "ms_per_step": 1e3 * el / K,
                    "rebuilds_in_timed_steps": rebuilds_timed},
            "amortised": {"rebuilds_per_step": rate, "rebuild_ms": rb_ms, "stretch_steps": cal + K,
+                         "rebuild_ms_host_launched": rb_host_ms,
                          "note": "timed window with its rebuilds replaced by rate x K rebuilds of "
-                                 "the measured cost"},
+                                 "the cost fitted over the stretch's 32-step calls"},
            "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clocks,
            "autotune": {k: tune[k] for k in ("cell_scale", "block", "skin_frac", "ppw")} |
                        {"cached": tune.get("cached", False), "trials": len(tune.get("trials", []))},
@@ -577,8 +591,32 @@ def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=
         ctx64.close()
         del ctx64
         out["fp64"] = {"value": N * K64 * world / el64, "unit": UNIT, "steps": K64,
-                       "ms_per_step": 1e3 * el64 / K64, "force_kernel_ms": p64["force_ms"]}
+                       "ms_per_step": 1e3 * el64 / K64, "force_kernel_ms": p64["force_ms"],
+                       "roofline": fp64_roofline(n_act, p64["force_ms"])}
     return out
+
+
+# FP64 peak of the chip: 2 DFMA per SM per clock (ncu's peak_sustained of
+# sm__sass_thread_inst_executed_op_dfma_pred_on) x 152 SMs x 2.07 GHz x 2 flops
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+
+def fp64_roofline(n_act, force_ms):
+    """The FP64 step kernel against the FP64 pipe: DADD + DMUL + 2 DFMA per
+    particle-step, counted by ncu on the 200k cylinder for the current kernel
+    source (none if the source has changed since), over the kernel's event
+    time."""
+    c = kernel_traffic("k_forces.cu", "k_forces_fp64_mid", None)
+    if not c:
+        return None
+    fl = float(c["dflop_per_particle_step"])
+    ach = fl * n_act / (force_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "dflop_per_particle_step": fl,
+            "fp64_pipe_active_pct": c.get("fp64_pipe_active_pct"),
+            "peak_source": "2 DFMA per SM per clock x 152 SMs x 2.07 GHz (a DFMA-chain probe "
+                           "measured 1.257 TFLOP/s)",
+            "counted_on": c.get("workload")}
 
 
 def run_e2e(torch, cgdem, s, knobs, skin, K, device, barrier, world):

@@ -623,8 +623,9 @@ void drop_graphs(cgdem_ctx* ctx) {
   ctx->graphs.clear();
 }
 
-// Launch part of cgdem_step on s (capturing it on first use for this stream).
-int launch_part(cgdem_ctx* ctx, int part, cudaStream_t s) {
+// The captured graph of one part of cgdem_step for stream s (captured on
+// first use for this stream).
+int find_part(cgdem_ctx* ctx, int part, cudaStream_t s, StepGraph** out) {
   const auto key = std::make_pair(s, part);
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
@@ -639,12 +640,38 @@ int launch_part(cgdem_ctx* ctx, int part, cudaStream_t s) {
     }
     if (e != cudaSuccess) e = capture_part(ctx, part, false, &g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+    // upload now, so that the first replay does not pay it
+    CK(cudaGraphUpload(g.exec, s));
     it = ctx->graphs.emplace(key, g).first;
   }
-  CK(cudaGraphLaunch(it->second.exec, s));
-  if (part != GRAPH_FLUID) ctx->step_kernels += it->second.kernels;
-  if (it->second.body_kernels) ctx->rebuild_kernels = it->second.body_kernels;
+  *out = &it->second;
   return CGDEM_OK;
+}
+
+// Launch part of cgdem_step on s.
+int launch_part(cgdem_ctx* ctx, int part, cudaStream_t s) {
+  StepGraph* g = nullptr;
+  int r = find_part(ctx, part, s, &g);
+  if (r) return r;
+  CK(cudaGraphLaunch(g->exec, s));
+  if (part != GRAPH_FLUID) ctx->step_kernels += g->kernels;
+  if (g->body_kernels) ctx->rebuild_kernels = g->body_kernels;
+  return CGDEM_OK;
+}
+
+// Capture every part that cgdem_step may launch on s (the opening and
+// closing parts, U steps and each power of two below U), so that the first
+// call on a stream pays all captures and later calls of any length replay.
+int prepare_parts(cgdem_ctx* ctx, cudaStream_t s) {
+  if (ctx->graphs.count(std::make_pair(s, GRAPH_HEAD))) return CGDEM_OK;
+  StepGraph* g = nullptr;
+  int r;
+  if ((r = find_part(ctx, GRAPH_TAIL, s, &g))) return r;
+  const int U = ctx->cfg.steps_per_graph;
+  if ((r = find_part(ctx, U, s, &g))) return r;
+  for (int b = 1 << 30; b >= 1; b >>= 1)
+    if (b < U && (r = find_part(ctx, b, s, &g))) return r;
+  return find_part(ctx, GRAPH_HEAD, s, &g);
 }
 
 }  // namespace
@@ -878,6 +905,7 @@ int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {
   if (nsteps < 0) return fail(ctx, CGDEM_E_INVALID, "nsteps < 0");
   if (nsteps == 0 || ctx->d.N == 0) return CGDEM_OK;
   cudaStream_t s = st(stream);
+  if ((r = prepare_parts(ctx, s))) return r;
   // half kick + drift from the full-step state, porosity of the new positions
   if ((r = launch_part(ctx, GRAPH_HEAD, s))) return r;
   // the nsteps - 1 fused steps as graphs of U steps, then of the powers of

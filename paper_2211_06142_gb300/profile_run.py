@@ -1,9 +1,10 @@
 """Short runs of the library's kernels for a profiler (ncu) to capture.
 
     python -m paper_2211_06142_gb300.profile_run step [mixed|fp64] [steps] [eager]
-        the fused step on the 200,000-sphere sand-production cylinder
-        ("eager": every kernel launched from the host, no CUDA graph, so
-        that a profiler sees each launch)
+        the fused step on the 200,000-sphere sand-production cylinder (or
+        the --workload one); "eager": the same kernels launched from the
+        host (the library's profiling entry point), since a profiler does
+        not see the kernel nodes of graphs that hold conditional nodes
     python -m paper_2211_06142_gb300.profile_run rebuild [mixed|fp64] [count]
         the candidate-list rebuild sequence, forced before each of `count`
         steps on the same cylinder (kernels launched from the host)
@@ -76,8 +77,11 @@ def main(argv):
     if what == "step":
         prec = cgdem.FP64 if len(argv) > 1 and argv[1] == "fp64" else cgdem.MIXED
         steps = int(argv[2]) if len(argv) > 2 else 12
-        ctx = _cylinder_ctx(prec, steps_per_graph=1 if "eager" in argv[3:] else 32)
-        ctx.step(steps)
+        ctx = _cylinder_ctx(prec)
+        if "eager" in argv[3:]:
+            print("force ms", ctx.profile_step(max(steps, 2))["force_ms"])
+        else:
+            ctx.step(steps)
         torch.cuda.synchronize()
         print("counters", ctx.counters())
         ctx.status()
