@@ -10,6 +10,7 @@
         steps on the same cylinder (kernels launched from the host)
     python -m paper_2211_06142_gb300.profile_run closure [steps]
         the step with the learned closure on the same cylinder at SSW k = 2
+        (kernels launched from the host)
     python -m paper_2211_06142_gb300.profile_run mlp [n] [iters]
         full-batch training steps of the closure network on n samples
 
@@ -103,7 +104,8 @@ def main(argv):
         theta[5:10] = 1.0
         theta[10:] = rng.normal(0, 0.1, cgdem.MLP_NPARAMS - 10)
         ctx.set_closure(theta, [-1e9] * 5, [1e9] * 5, 3.0, 0.5)
-        ctx.step(steps)
+        # launched from the host, as "step ... eager"
+        print("force ms", ctx.profile_step(max(steps, 2))["force_ms"])
         torch.cuda.synchronize()
         print("counters", ctx.counters())
         ctx.status()
