@@ -127,6 +127,12 @@ typedef struct {
     int fluid_iters;        /* Darcy samples: conjugate-gradient iterations per solve at most
                                (0 selects 2000; each solve starts from the last pressure) */
     double fluid_tol;       /* stop when |residual| <= fluid_tol |right-hand side| (0 selects 1e-10) */
+    int fluid_kernels;      /* 0: the solve's iterations in one cooperative launch (all blocks
+                               resident, a grid barrier between phases, each wait bounded: a
+                               wait that expires latches CGDEM_E_TIMEOUT) where the device
+                               and graph capture allow it; 1: one kernel per phase of an
+                               iteration, looped by a CUDA-graph WHILE node.  The two forms
+                               sum in different orders, so they agree to rounding only */
 } cgdem_config;
 
 typedef struct cgdem_ctx cgdem_ctx;

@@ -70,7 +70,7 @@ class Config(C.Structure):
         ("precision", C.c_int), ("n_samples", C.c_int), ("max_neighbors", C.c_int),
         ("block_size", C.c_int), ("cell_scale", C.c_double), ("steps_per_graph", C.c_int),
         ("closure", C.c_int), ("particles_per_warp", C.c_int),
-        ("fluid_iters", C.c_int), ("fluid_tol", C.c_double),
+        ("fluid_iters", C.c_int), ("fluid_tol", C.c_double), ("fluid_kernels", C.c_int),
     ]
 
 
@@ -323,7 +323,7 @@ class Context:
 
     def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
                  cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None, closure=False,
-                 particles_per_warp=32, fluid_iters=0, fluid_tol=0.0):
+                 particles_per_warp=32, fluid_iters=0, fluid_tol=0.0, fluid_kernels=0):
         import torch
 
         if not torch.cuda.is_available():
@@ -336,7 +336,7 @@ class Context:
         self.N = int(self.counts.sum())
         self.cfg = Config(precision, self.n_samples, max_neighbors, block_size, cell_scale,
                           steps_per_graph, int(bool(closure)), int(particles_per_warp), int(fluid_iters),
-                          float(fluid_tol))
+                          float(fluid_tol), int(fluid_kernels))
         nbytes = C.c_size_t(0)
         r = lib().cgdem_workspace_size(C.byref(self.cfg), self._params, _ptr(self.counts),
                                        C.byref(nbytes))

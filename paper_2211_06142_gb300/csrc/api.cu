@@ -31,6 +31,8 @@ void launch_fluid_iteration(const Dev& d, cudaGraphConditionalHandle h, cudaStre
 void launch_fluid_tail(const Dev& d, cudaStream_t s);
 void launch_react_clear(const Dev& d, cudaStream_t s);
 int fluid_blocks(int Cf_total);
+int fluid_coop_blocks(int Cf_total);
+cudaError_t launch_fluid_solve_coop(const Dev& d, cudaStream_t s);
 void launch_collect_springs(const Dev& d, uint32_t* out, double* xi, unsigned long long cap, cudaStream_t s);
 void launch_diag(const Dev& d, double* part, cudaStream_t s);
 void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s);
@@ -290,6 +292,8 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   if (cfg->closure != 0 && cfg->closure != 1) return fail(ctx, CGDEM_E_INVALID, "closure must be 0 or 1");
   if (cfg->particles_per_warp != 0 && cfg->particles_per_warp != 16 && cfg->particles_per_warp != 32)
     return fail(ctx, CGDEM_E_INVALID, "particles_per_warp must be 0, 16 or 32");
+  if (cfg->fluid_kernels != 0 && cfg->fluid_kernels != 1)
+    return fail(ctx, CGDEM_E_INVALID, "fluid_kernels must be 0 or 1");
   if (cfg->closure && cfg->block_size != 128 && cfg->block_size > 0)
     return fail(ctx, CGDEM_E_INVALID, "a context with the learned closure runs blocks of 128 threads");
   const int S = cfg->n_samples;
@@ -386,6 +390,7 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     d.fl_q = cv.take<double>(nc);
     d.fl_M = cv.take<double>(nc);
     d.fl_b = cv.take<double>(nc);
+    d.fl_d2 = cv.take<double>(nc);
     d.fl_blocks = fluid_blocks(Cf);
     d.fl_part = cv.take<double>(4 * (size_t)d.fl_blocks);
     d.gradp = cv.take<double4>(nc);
@@ -502,6 +507,7 @@ cudaError_t add_rebuild_node(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs,
 // iterations are captured fluid_iters times (each returns at once once the
 // solve has converged).
 cudaError_t add_fluid_solve(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs, bool conditional) {
+  if (ctx->d.fl_coop_blocks > 0) return launch_fluid_solve_coop(ctx->d, cs);
   if (!conditional) {
     launch_fluid_head(ctx->d, 0, cs);
     for (int i = 0; i < ctx->d.fl_iters_max; ++i) launch_fluid_iteration(ctx->d, 0, cs);
@@ -633,6 +639,12 @@ int find_part(cgdem_ctx* ctx, int part, cudaStream_t s, StepGraph** out) {
     cudaError_t e = cudaErrorUnknown;
     if (ctx->conditional_graphs) {
       e = capture_part(ctx, part, true, &g);
+      if (e != cudaSuccess && ctx->d.fl_coop_blocks > 0) {
+        // no cooperative launch in a graph: the Darcy solve as separate kernels from now on
+        ctx->d.fl_coop_blocks = 0;
+        drop_graphs(ctx);
+        e = capture_part(ctx, part, true, &g);
+      }
       if (e != cudaSuccess) {  // conditional nodes unavailable: plain captures from now on
         ctx->conditional_graphs = false;
         drop_graphs(ctx);
@@ -775,6 +787,7 @@ int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const i
     cudaMemset(ctx->d.gradpf, 0, sizeof(float4) * nc);
     cudaMemset(ctx->d.react[0], 0, sizeof(unsigned long long) * 3 * nc);
     cudaMemset(ctx->d.react[1], 0, sizeof(unsigned long long) * 3 * nc);
+    ctx->d.fl_coop_blocks = cfg->fluid_kernels == 1 ? 0 : fluid_coop_blocks(ctx->d.Cf_total);
   }
   *out = ctx;
   return CGDEM_OK;

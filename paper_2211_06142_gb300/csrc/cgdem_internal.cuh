@@ -133,6 +133,10 @@ struct Ctl {
   int fl_pending, fl_done, fl_it;
   long long fl_iters;  // iterations of the last solve (-1: stopped short of the tolerance)
   double fl_rz, fl_alpha, fl_beta, fl_bb;
+  // grid barrier of the one-launch solve: arrivals, generation, and a flag a
+  // block sets when its wait gave up (the others then stop waiting too)
+  unsigned fl_bar_count, fl_bar_gen;
+  int fl_abort;
 };
 constexpr double DARCY_N_CAP = 0.95;  // the permeability's porosity cap
 
@@ -202,8 +206,10 @@ struct Dev {
   double* fl_K;                   // permeability
   double* fl_p;                   // dynamic pressure (kept: the next solve starts from it)
   double *fl_r, *fl_z, *fl_d, *fl_q, *fl_M, *fl_b;  // conjugate-gradient vectors, diagonal, right-hand side
+  double* fl_d2;                  // the one-launch solve's second direction buffer
   double* fl_part;                // per-block partial sums [4][fl_blocks]
   int fl_blocks;
+  int fl_coop_blocks;             // blocks of the one-launch solve (0: the WHILE-node form)
   double4* gradp;                 // grad p per cell (w unused)
   float4* gradpf;
   unsigned long long* react[2];   // drag reaction [Cf][3], quanta of 2^-60 N; by parity of the evaluation

@@ -10,11 +10,14 @@
 // solve's pressure.  Every sum is a fixed-order reduction (per-block partial
 // sums, then one block), so the solve is deterministic.
 //
-// Launch sequence of one solve: k_fl_setup, k_fl_init, k_fl_start, then the
-// iterations {k_fl_spmv, k_fl_alpha, k_fl_update, k_fl_beta, k_fl_dir} --
-// the body of a CUDA-graph WHILE node whose condition k_fl_start and
-// k_fl_beta set (or a fixed number of them that return at once once done),
-// then k_fl_finish.  Nothing runs unless a porosity update is pending.
+// Launch sequence of one solve: k_fl_setup, then the whole iteration in one
+// cooperative launch (k_fl_solve: all blocks resident, a bounded grid barrier
+// between phases), then k_fl_finish.  Where no cooperative launch can be
+// captured, the iteration runs as separate kernels: k_fl_init, k_fl_start,
+// then {k_fl_spmv, k_fl_alpha, k_fl_update, k_fl_beta, k_fl_dir} as the body
+// of a CUDA-graph WHILE node whose condition k_fl_start and k_fl_beta set (or
+// a fixed number of them that return at once once done).  Nothing runs unless
+// a porosity update is pending.
 #include "cgdem_internal.cuh"
 
 namespace cgdem {
@@ -308,6 +311,201 @@ __global__ void __launch_bounds__(FL_B) k_fl_finish(Dev d) {
   d.gradpf[c] = make_float4((float)G[0], (float)G[1], (float)G[2], 0.f);
 }
 
+// ---- the whole solve in one cooperative launch ----------------------------
+//
+// The same iteration in one launch whose blocks are all resident: each block
+// takes a fixed set of cells (grid stride), writes its partial sums, and a
+// grid barrier separates the phases; after a barrier every block forms the
+// same totals from the partials in the same order, so all blocks take the
+// same decisions and the result does not depend on timing.  Two barriers per
+// iteration: the new direction d = z + beta d_old is formed on the fly where
+// A d needs it (neighbours included), into a second buffer, so that nobody
+// overwrites a direction another block still reads.
+constexpr int FL_WAIT_LIMIT = 1 << 21;  // polls of a barrier before the solve gives up
+
+// Grid barrier: one arrival per block; the last to arrive opens the next
+// generation.  false when the wait gave up (the solve is then abandoned and
+// the step latches a timeout).
+__device__ __forceinline__ bool fl_grid_sync(Ctl* ctl, unsigned& gen) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned a = atomicAdd(&ctl->fl_bar_count, 1u);
+    if (a == gridDim.x - 1u) {
+      atomicExch(&ctl->fl_bar_count, 0u);
+      __threadfence();
+      atomicExch(&ctl->fl_bar_gen, gen + 1u);
+    } else {
+      int polls = 0;
+      while (atomicAdd(&ctl->fl_bar_gen, 0u) == gen) {
+        if (++polls > FL_WAIT_LIMIT || *((volatile int*)&ctl->fl_abort)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (!ok) {
+      atomicExch(&ctl->fl_abort, 1);
+      latch(ctl, ST_TIMEOUT);
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  gen += 1u;
+  return ok_s != 0;
+}
+
+// Direction entry i of this iteration, z_i + beta d_old,i: the owner and its
+// neighbours evaluate the same expression on the same values.
+__device__ __forceinline__ double fl_dir(const double* z, const double* dold, double beta, int i) {
+  return __fma_rn(beta, dold[i], z[i]);
+}
+
+// (A d)_c for the direction of this iteration; *dc receives d_c.
+__device__ double apply_A_dir(const Dev& d, const SampleDev& S, int c, const double* z, const double* dold,
+                              double beta, double* dc) {
+  const CellIdx ci = cell_idx(S, c);
+  const double Kc = d.fl_K[c];
+  const double xc = fl_dir(z, dold, beta, c);
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int sg = -1; sg <= 1; sg += 2) {
+      const int q = ci.ijk[k] + sg;
+      if (q < 0 || q >= ci.dim[k]) continue;
+      const int nb = c + sg * ci.stride[k];
+      const signed char tn = d.fl_type[nb];
+      if (tn == 2) continue;
+      const double T = face_cond(S, k, Kc, d.fl_K[nb]);
+      if (fl_unknown(tn))
+        acc += T * (xc - fl_dir(z, dold, beta, nb));
+      else
+        acc += T * xc;
+    }
+  if (d.fl_type[c] == 3) acc += outlet_cond(S, Kc) * xc;
+  *dc = xc;
+  return acc;
+}
+
+// Fixed-order block sums of up to three values per thread into part[k * G + blockIdx.x].
+__device__ __forceinline__ void block_partials(double a, double b, double c, int nv, double* part, int G) {
+  __shared__ double sh[3][FL_B];
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int o = FL_B / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int k = 0; k < nv; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < nv) part[threadIdx.x * G + blockIdx.x] = sh[threadIdx.x][0];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(FL_B) k_fl_solve(Dev d) {
+  Ctl* ctl = d.ctl;
+  // every block reads the flag before the first barrier; block 0 clears it after
+  const int pending = *((volatile int*)&ctl->fl_pending);
+  if (!pending) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->fl_done = 1;
+      ctl->fl_it = -1;  // no solve: k_fl_finish leaves the field as it is
+    }
+    return;
+  }
+  unsigned gen = atomicAdd(&ctl->fl_bar_gen, 0u);
+  const int G = (int)gridDim.x;
+  const int c0 = blockIdx.x * FL_B + threadIdx.x, cs = G * FL_B;
+  double* part = d.fl_part;  // slots of G partials: r.z, b.b (then r.r), r.r, d.q
+  const double tol2 = d.fl_tol * d.fl_tol;
+  // r = b - A p, z = r / M; the first direction is z (d_old = 0, beta = 0)
+  double rz = 0.0, bb = 0.0, rr = 0.0;
+  for (int c = c0; c < d.Cf_total; c += cs) {
+    if (!fl_unknown(d.fl_type[c])) continue;
+    const SampleDev& S = d.sp[d.fl_sample[c]];
+    double b, M;
+    const double Ap = apply_A(d, S, c, d.fl_p, &b, &M);
+    const double rc = b - Ap;
+    const double z = rc / M;
+    d.fl_M[c] = M;
+    d.fl_r[c] = rc;
+    d.fl_z[c] = z;
+    d.fl_d[c] = 0.0;
+    rz += rc * z;
+    bb += b * b;
+    rr += rc * rc;
+  }
+  block_partials(rz, bb, rr, 3, part, G);
+  if (!fl_grid_sync(ctl, gen)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->fl_pending = 0;
+  double rzt = block_total(part, G);
+  const double bbt = block_total(part + G, G);
+  double rrt = block_total(part + 2 * G, G);
+  int it = 0;
+  long long iters = 0;
+  bool done = rrt <= tol2 * bbt;
+  double beta = 0.0;
+  double* dold = d.fl_d;
+  double* dnew = d.fl_d2;
+  while (!done) {
+    // q = A d with d = z + beta d_old; d.q
+    double dq = 0.0;
+    for (int c = c0; c < d.Cf_total; c += cs) {
+      if (!fl_unknown(d.fl_type[c])) continue;
+      const SampleDev& S = d.sp[d.fl_sample[c]];
+      double dc;
+      const double q = apply_A_dir(d, S, c, d.fl_z, dold, beta, &dc);
+      dnew[c] = dc;
+      d.fl_q[c] = q;
+      dq += dc * q;
+    }
+    block_partials(dq, 0.0, 0.0, 1, part + 3 * G, G);
+    if (!fl_grid_sync(ctl, gen)) return;
+    const double alpha = rzt / block_total(part + 3 * G, G);
+    // p += alpha d, r -= alpha q, z = r / M; r.z and r.r
+    double rz1 = 0.0, rr1 = 0.0;
+    for (int c = c0; c < d.Cf_total; c += cs) {
+      if (!fl_unknown(d.fl_type[c])) continue;
+      d.fl_p[c] += alpha * dnew[c];
+      const double r = d.fl_r[c] - alpha * d.fl_q[c];
+      d.fl_r[c] = r;
+      const double z = r / d.fl_M[c];
+      d.fl_z[c] = z;
+      rz1 += r * z;
+      rr1 += r * r;
+    }
+    block_partials(rz1, rr1, 0.0, 2, part, G);  // slot 1 is free once b.b is summed
+    if (!fl_grid_sync(ctl, gen)) return;
+    const double rzn = block_total(part, G);
+    rrt = block_total(part + G, G);
+    ++it;
+    if (rrt <= tol2 * bbt) {
+      done = true;
+      iters = it;
+    } else if (it >= d.fl_iters_max) {
+      done = true;
+      iters = -1;  // stopped short of the tolerance
+    } else {
+      beta = rzn / rzt;
+      rzt = rzn;
+      double* t = dold;
+      dold = dnew;
+      dnew = t;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->fl_done = 1;
+    ctl->fl_it = it;
+    ctl->fl_iters = iters;
+  }
+}
+
 __global__ void k_fl_mark(Dev d) { d.ctl->fl_pending = 1; }
 
 // the drag-reaction buffer of a force evaluation at the current step
@@ -342,5 +540,41 @@ void launch_fluid_iteration(const Dev& d, cudaGraphConditionalHandle h, cudaStre
 void launch_fluid_tail(const Dev& d, cudaStream_t s) { k_fl_finish<<<fl_grid(d), FL_B, 0, s>>>(d); }
 
 int fluid_blocks(int Cf_total) { return (Cf_total + FL_B - 1) / FL_B; }
+
+// Blocks of the one-launch solve: two per SM, no more than the cells need and
+// no more than can be resident at once; 0 when no cooperative launch is
+// possible (the WHILE-node form is used then).
+int fluid_coop_blocks(int Cf_total) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fl_solve, FL_B, 0) != cudaSuccess) return 0;
+  if (per_sm < 1) return 0;
+  int G = 2 * sms;
+  if (G > per_sm * sms) G = per_sm * sms;
+  const int need = fluid_blocks(Cf_total);
+  if (G > need) G = need;
+  return G > 0 ? G : 0;
+}
+
+// One solve as three launches: setup, the cooperative solve, the velocity.
+cudaError_t launch_fluid_solve_coop(const Dev& d, cudaStream_t s) {
+  k_fl_setup<<<fl_grid(d), FL_B, 0, s>>>(d);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)d.fl_coop_blocks);
+  cfg.blockDim = dim3(FL_B);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_fl_solve, d);
+  if (e != cudaSuccess) return e;
+  k_fl_finish<<<fl_grid(d), FL_B, 0, s>>>(d);
+  return cudaGetLastError();
+}
 
 }  // namespace cgdem

@@ -1106,6 +1106,9 @@ __global__ void k_init_ctl(Dev d) {
   c->fl_done = 1;
   c->fl_it = -1;
   c->fl_iters = 0;
+  c->fl_bar_count = 0u;
+  c->fl_bar_gen = 0u;
+  c->fl_abort = 0;
   for (int s = 0; s < d.n_samples; ++s) d.dmax2[s] = 0u;
 }
 

@@ -84,6 +84,10 @@ def test_workspace_size_and_invalid_arguments(lib):
     for ppw, rc in ((16, 0), (32, 0), (0, 0), (8, cgdem.CGDEM_E_INVALID)):
         cfg3 = cgdem.Config(cgdem.MIXED, 1, 48, 128, 0.0, 32, 0, ppw)
         assert lib.cgdem_workspace_size(C.byref(cfg3), arr, counts.ctypes.data, C.byref(nb)) == rc
+    # form of the Darcy solve: 0 (one cooperative launch) or 1 (a kernel per phase)
+    for fk, rc in ((0, 0), (1, 0), (2, cgdem.CGDEM_E_INVALID)):
+        cfg4 = cgdem.Config(cgdem.MIXED, 1, 48, 128, 0.0, 32, 0, 32, 0, 0.0, fk)
+        assert lib.cgdem_workspace_size(C.byref(cfg4), arr, counts.ctypes.data, C.byref(nb)) == rc
 
 
 def test_noalloc_rejects_oversize_without_gpu(lib):

@@ -27,17 +27,24 @@ P_IN = 150.0
 TOL = {cgdem.FP64: 1e-10, cgdem.MIXED: 1e-4}
 
 
-def setup(prec, couple_every=5):
-    s = with_velocities(small_cylinder(), 1e-3)
+def gpu_context(s, prec, couple_every, fluid_kernels=0):
     dt = default_dt(s)
     perm_d = float(np.mean((2 * s.R) ** 3)) ** (1 / 3)
     p = cgdem.sample_params(s, dt, default_skin(s), couple_every=couple_every, fluid_mode=1, p_inlet=P_IN,
                             perm_d=perm_d)
     ctx = cgdem.Context([p], [len(s.R)], precision=prec, max_neighbors=64, fluid_tol=1e-14,
-                        fluid_iters=5000)
+                        fluid_iters=5000, fluid_kernels=fluid_kernels)
     ctx.set_fluid_velocity(s.Us)
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=True)
     ctx.compute_forces()
+    return ctx
+
+
+def setup(prec, couple_every=5):
+    s = with_velocities(small_cylinder(), 1e-3)
+    dt = default_dt(s)
+    perm_d = float(np.mean((2 * s.R) ** 3)) ** (1 / 3)
+    ctx = gpu_context(s, prec, couple_every)
     op = oracle_params(s, dt, couple_every=couple_every)
     op.fluid_mode, op.p_inlet, op.perm_d = 1, P_IN, perm_d
     sim = O.Sim(op, s.x, s.v, s.w, s.R, s.Us)
@@ -111,3 +118,26 @@ def test_darcy_steps_resolve_the_flow(prec):
         else:
             assert check_mixed_forces(s, g, o, sim, ctx.get_contacts(), TOL[prec]) <= 0.02 * len(s.R)
     ctx.close()
+
+
+def test_one_launch_solve_equals_the_kernel_per_phase_form():
+    """The solve in one cooperative launch and the solve as one kernel per
+    phase in a WHILE node: the same system, summed in different orders, so
+    the fields agree to the tolerance's rounding, over a first solve from
+    zero pressure and warm-started solves after 10 steps."""
+    s = with_velocities(small_cylinder(), 1e-3)
+    a = gpu_context(s, cgdem.FP64, 5, fluid_kernels=0)
+    b = gpu_context(s, cgdem.FP64, 5, fluid_kernels=1)
+    for n in (0, 10):
+        if n:
+            a.step(n)
+            b.step(n)
+        pa, Ua, Ga, Ra, ia = a.get_fluid(s.grid.ncell)
+        pb, Ub, Gb, Rb, ib = b.get_fluid(s.grid.ncell)
+        assert ia >= 0 and ib >= 0 and abs(ia - ib) <= max(2, ib // 20)
+        assert np.abs(pa - pb).max() <= 1e-11 * np.abs(pb).max()
+        assert np.abs(Ua - Ub).max() <= 1e-10 * np.abs(Ub).max()
+        fa, fb = a.get_state()["F"], b.get_state()["F"]
+        assert np.abs(fa - fb).max() <= 1e-9 * np.abs(fb).max()
+    a.close()
+    b.close()
