@@ -254,8 +254,10 @@ int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream
  * samples' fluid cells (sample after sample, x fastest), any may be NULL:
  * p [Cf] dynamic pressure [Pa]; U [Cf,3] superficial velocity [m/s];
  * gradp [Cf,3] its driving gradient -mu_f U / K [Pa/m]; reaction [Cf,3] the
- * drag forces of the grains in each cell at the last force evaluation
- * (Eq. 7: the fluid's force density is this over V_cell) in integer quanta
+ * drag forces of the grains in each cell at the last force evaluation, the
+ * one that ended the last cgdem_step or cgdem_compute_forces call (the steps
+ * inside a call sum none: nothing reads them back, and the Darcy solve
+ * does not use them) (Eq. 7: the fluid's force density is this over V_cell) in integer quanta
  * of 2^-60 N; *iters the iterations of the last solve (-1: it stopped at
  * fluid_iters short of fluid_tol).  Cells of other samples hold zeros.
  * Synchronises stream. */

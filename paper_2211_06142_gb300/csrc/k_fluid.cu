@@ -339,7 +339,7 @@ __device__ __forceinline__ bool fl_grid_sync(Ctl* ctl, unsigned& gen) {
       atomicExch(&ctl->fl_bar_gen, gen + 1u);
     } else {
       int polls = 0;
-      while (atomicAdd(&ctl->fl_bar_gen, 0u) == gen) {
+      while (*((volatile unsigned*)&ctl->fl_bar_gen) == gen) {
         if (++polls > FL_WAIT_LIMIT || *((volatile int*)&ctl->fl_abort)) {
           ok = 0;
           break;

@@ -630,11 +630,15 @@ __device__ __forceinline__ void finish_step(
             F.x -= Vp * G.x;
             F.y -= Vp * G.y;
             F.z -= Vp * G.z;
-            const long long e = MODE == MODE_FORCES ? m_step - 1 : m_step;
-            unsigned long long* rx = d.react[e & 1] + 3 * (size_t)fc;
-            atomicAdd(rx, (unsigned long long)__double2ll_rn((double)fd.x * 1152921504606846976.0));
-            atomicAdd(rx + 1, (unsigned long long)__double2ll_rn((double)fd.y * 1152921504606846976.0));
-            atomicAdd(rx + 2, (unsigned long long)__double2ll_rn((double)fd.z * 1152921504606846976.0));
+            if (MODE != MODE_MID) {
+              // only an evaluation that ends a call can be read back
+              // (cgdem_get_fluid): a step inside a call sums no reaction
+              const long long e = MODE == MODE_FORCES ? m_step - 1 : m_step;
+              unsigned long long* rx = d.react[e & 1] + 3 * (size_t)fc;
+              atomicAdd(rx, (unsigned long long)__double2ll_rn((double)fd.x * 1152921504606846976.0));
+              atomicAdd(rx + 1, (unsigned long long)__double2ll_rn((double)fd.y * 1152921504606846976.0));
+              atomicAdd(rx + 2, (unsigned long long)__double2ll_rn((double)fd.z * 1152921504606846976.0));
+            }
           }
           if (feat) {
             net_row = true;
