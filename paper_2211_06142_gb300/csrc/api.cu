@@ -13,7 +13,8 @@
 #include "cgdem_internal.cuh"
 
 namespace cgdem {
-void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next);
+void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next,
+                   cudaGraphConditionalHandle h_fluid = 0);
 void launch_rebuild(const Dev& d, cudaStream_t s);
 void launch_set_rebuild(const Dev& d, cudaStream_t s);
 void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_t s);
@@ -500,6 +501,34 @@ cudaError_t add_rebuild_node(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs,
   return cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
+// Append to the capture on cs a conditional (IF) node whose body, captured
+// on bs, is the one-launch Darcy solve; its condition is handle h, which the
+// step's force kernel sets when the step updated the porosity.
+cudaError_t add_fluid_if(cgdem_ctx* ctx, cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t cg;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  e = launch_fluid_solve_coop(ctx->d, bs);
+  cudaError_t e2 = cudaStreamEndCapture(bs, &body);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return e;
+  return cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 // Append a Darcy solve to the capture on cs (it does nothing unless a
 // porosity update is pending): the set-up kernels, then the conjugate-gradient
 // iterations as the body of a WHILE node (captured on bs) whose condition the
@@ -580,6 +609,11 @@ cudaError_t capture_part(cgdem_ctx* ctx, int part, bool conditional, StepGraph* 
     // one handle per step: a one-thread kernel sets the first from the device
     // flag at every launch of the graph; step i's force kernel sets step i + 1's
     std::vector<cudaGraphConditionalHandle> hs;
+    // with the one-launch Darcy solve, each step's solve sits in an IF node
+    // that the step's force kernel sets (nothing launches on the steps that
+    // do not update the porosity)
+    const bool fluid_if = conditional && !tail && ctx->d.any_fluid && ctx->d.fl_coop_blocks > 0;
+    std::vector<cudaGraphConditionalHandle> hf;
     if (conditional && e == cudaSuccess) {
       cudaStreamCaptureStatus stt;
       cudaGraph_t cg;
@@ -588,6 +622,11 @@ cudaError_t capture_part(cgdem_ctx* ctx, int part, bool conditional, StepGraph* 
       for (int i = 0; i < U && e == cudaSuccess; ++i)
         e = cudaGraphConditionalHandleCreate(&hs[i], cg, i == 0 ? 1u : 0u,
                                              i == 0 ? cudaGraphCondAssignDefault : 0u);
+      if (fluid_if) {
+        hf.resize(U);
+        for (int i = 0; i < U && e == cudaSuccess; ++i)
+          e = cudaGraphConditionalHandleCreate(&hf[i], cg, 0u, cudaGraphCondAssignDefault);
+      }
     }
     for (int i = 0; i < U && e == cudaSuccess; ++i) {
       if (conditional) {
@@ -601,9 +640,12 @@ cudaError_t capture_part(cgdem_ctx* ctx, int part, bool conditional, StepGraph* 
         launch_forces(ctx->d, 2, ctx->cfg.block_size, cs, 0);
       } else {
         launch_forces(ctx->d, 1, ctx->cfg.block_size, cs,
-                      conditional && i + 1 < U ? hs[i + 1] : 0);
+                      conditional && i + 1 < U ? hs[i + 1] : 0, fluid_if ? hf[i] : 0);
         if (ctx->any_cube) launch_cube_after_mid(ctx->d, cs);
-        if (ctx->d.any_fluid) {
+        if (fluid_if) {
+          e = add_fluid_if(ctx, cs, bs, hf[i]);
+          if (e != cudaSuccess) break;
+        } else if (ctx->d.any_fluid) {
           e = add_fluid_solve(ctx, cs, bs, conditional);
           if (e != cudaSuccess) break;
         }

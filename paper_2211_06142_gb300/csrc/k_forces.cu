@@ -495,7 +495,8 @@ __device__ __forceinline__ void finish_step(
     typename std::conditional<MIXED, float, double>::type Dacc,
     typename std::conditional<MIXED, float, double>::type Cacc, float2 my_c, bool use_c, bool feat,
     bool rec, bool net, uint8_t* cl_sm, uint64_t* cl_bar, uint32_t cl_tmem, unsigned* bk_n, int* bk_s,
-    float* bk_m, unsigned* bk_c, cudaGraphConditionalHandle h_next) {
+    float* bk_m, unsigned* bk_c, cudaGraphConditionalHandle h_next,
+    cudaGraphConditionalHandle h_fluid) {
   using T = typename std::conditional<MIXED, float, double>::type;
   // ---- per-particle epilogue: walls, body forces, drag, integration ----
   float my_disp2 = -1.f;
@@ -880,6 +881,8 @@ __device__ __forceinline__ void finish_step(
       ctl->block_counter = 0u;
       __threadfence();
       if (MODE == MODE_MID && h_next) cudaGraphSetConditional(h_next, ctl->rebuild ? 1u : 0u);
+      // the step's Darcy solve runs when this step updated the porosity
+      if (MODE == MODE_MID && h_fluid) cudaGraphSetConditional(h_fluid, ctl->fl_pending ? 1u : 0u);
     }
   }
 }
@@ -894,10 +897,12 @@ __device__ __forceinline__ void finish_step(
 // 128 threads; more registers per thread for the closure data and the network
 // epilogue).
 // h_next: conditional handle of the next step's rebuild node when the launch
-// sits in a CUDA graph (0 otherwise); the step's last warp sets it.
+// sits in a CUDA graph (0 otherwise); h_fluid: that of the step's Darcy-solve
+// node (0: none); the step's last warp sets both.
 template <int MODE, bool CL>
 __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
-    k_forces_pairs(Dev d, cudaGraphConditionalHandle h_next) {
+    k_forces_pairs(Dev d, cudaGraphConditionalHandle h_next,
+    cudaGraphConditionalHandle h_fluid) {
   using T = double;
   Ctl* ctl = d.ctl;
   const int cur = ctl->cur;
@@ -1236,7 +1241,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
 
   finish_step<false, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
                                F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
-                               &bk_n, bk_s, bk_m, bk_c, h_next);
+                               &bk_n, bk_s, bk_m, bk_c, h_next, h_fluid);
 }
 
 
@@ -1254,7 +1259,8 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
 // deterministic.
 template <int MODE, bool CL>
 __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
-    k_forces_lanes(Dev d, cudaGraphConditionalHandle h_next) {
+    k_forces_lanes(Dev d, cudaGraphConditionalHandle h_next,
+    cudaGraphConditionalHandle h_fluid) {
   Ctl* ctl = d.ctl;
   const int cur = ctl->cur;
   const int nxt = cur ^ 1;
@@ -1507,7 +1513,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
   }
   finish_step<true, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
                               F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
-                              &bk_n, bk_s, bk_m, bk_c, h_next);
+                              &bk_n, bk_s, bk_m, bk_c, h_next, h_fluid);
 }
 
 
@@ -1518,7 +1524,8 @@ __global__ void k_after_canon(Dev d) {
   ctl->step += 1;
 }
 
-void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next) {
+void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphConditionalHandle h_next,
+    cudaGraphConditionalHandle h_fluid) {
   // Npad is a multiple of 256, so every block size divides it exactly
   // (a context with the learned closure runs blocks of 128: one M = 128 tile)
   // The closure variant only while the closure is on or recording: its
@@ -1532,22 +1539,22 @@ void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphC
   if (d.N == 0) return;
   if (cl) {
     if (d.mixed) {
-      if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
-      else if (mode == MODE_MID) k_forces_lanes<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
-      else k_forces_lanes<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
+      if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0, 0);
+      else if (mode == MODE_MID) k_forces_lanes<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next, h_fluid);
+      else k_forces_lanes<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0, 0);
     } else {
-      if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0);
-      else if (mode == MODE_MID) k_forces_pairs<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next);
-      else k_forces_pairs<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0);
+      if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0, 0);
+      else if (mode == MODE_MID) k_forces_pairs<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next, h_fluid);
+      else k_forces_pairs<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0, 0);
     }
   } else if (d.mixed) {
-    if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
-    else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
-    else k_forces_lanes<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
+    if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0, 0);
+    else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next, h_fluid);
+    else k_forces_lanes<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0, 0);
   } else {
-    if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0);
-    else if (mode == MODE_MID) k_forces_pairs<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next);
-    else k_forces_pairs<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0);
+    if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0, 0);
+    else if (mode == MODE_MID) k_forces_pairs<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next, h_fluid);
+    else k_forces_pairs<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0, 0);
   }
   if (mode == MODE_CANON) k_after_canon<<<1, 1, 0, s>>>(d);
 }
