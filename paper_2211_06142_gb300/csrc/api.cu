@@ -392,6 +392,7 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     d.fl_M = cv.take<double>(nc);
     d.fl_b = cv.take<double>(nc);
     d.fl_d2 = cv.take<double>(nc);
+    d.fl_T = cv.take<double4>(nc);
     d.fl_blocks = fluid_blocks(Cf);
     d.fl_part = cv.take<double>(4 * (size_t)d.fl_blocks);
     d.gradp = cv.take<double4>(nc);

@@ -207,6 +207,7 @@ struct Dev {
   double* fl_p;                   // dynamic pressure (kept: the next solve starts from it)
   double *fl_r, *fl_z, *fl_d, *fl_q, *fl_M, *fl_b;  // conjugate-gradient vectors, diagonal, right-hand side
   double* fl_d2;                  // the one-launch solve's second direction buffer
+  double4* fl_T;                  // its face conductances per cell: upper x, y, z faces, outlet face
   double* fl_part;                // per-block partial sums [4][fl_blocks]
   int fl_blocks;
   int fl_coop_blocks;             // blocks of the one-launch solve (0: the WHILE-node form)

@@ -365,13 +365,36 @@ __device__ __forceinline__ double fl_dir(const double* z, const double* dold, do
   return __fma_rn(beta, dold[i], z[i]);
 }
 
-// (A d)_c for the direction of this iteration; *dc receives d_c.
-__device__ double apply_A_dir(const Dev& d, const SampleDev& S, int c, const double* z, const double* dold,
-                              double beta, double* dc) {
+// Conductances of cell c's upper faces (x, y, z) and of its outlet face,
+// from the permeabilities of k_fl_setup; 0 where the neighbour is not part
+// of the system.  face_cond is symmetric in its two permeabilities, so each
+// face gets the value either side would compute.
+__device__ double4 face_conds(const Dev& d, const SampleDev& S, int c) {
   const CellIdx ci = cell_idx(S, c);
   const double Kc = d.fl_K[c];
-  const double xc = fl_dir(z, dold, beta, c);
-  double acc = 0.0;
+  double T[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (ci.ijk[k] + 1 >= ci.dim[k]) continue;
+    const int nb = c + ci.stride[k];
+    if (d.fl_type[nb] == 2) continue;
+    T[k] = face_cond(S, k, Kc, d.fl_K[nb]);
+  }
+  const double To = d.fl_type[c] == 3 ? outlet_cond(S, Kc) : 0.0;
+  return make_double4(T[0], T[1], T[2], To);
+}
+
+// (A x)_c of an unknown cell from the stored conductances, where x_i =
+// z_i + beta d_old,i (dold == nullptr: x = z); with b and M, also the
+// right-hand side of the fixed pressures around it and the diagonal.  The
+// terms are added in the order apply_A adds them.
+__device__ double apply_A_stored(const Dev& d, const SampleDev& S, int c, const double* z, const double* dold,
+                                 double beta, double* xc_out, double* b, double* M) {
+  const CellIdx ci = cell_idx(S, c);
+  const double4 Tc = d.fl_T[c];
+  const double Tup[3] = {Tc.x, Tc.y, Tc.z};
+  const double xc = dold ? fl_dir(z, dold, beta, c) : z[c];
+  double acc = 0.0, rhs = 0.0, dg = 0.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -381,14 +404,28 @@ __device__ double apply_A_dir(const Dev& d, const SampleDev& S, int c, const dou
       const int nb = c + sg * ci.stride[k];
       const signed char tn = d.fl_type[nb];
       if (tn == 2) continue;
-      const double T = face_cond(S, k, Kc, d.fl_K[nb]);
-      if (fl_unknown(tn))
-        acc += T * (xc - fl_dir(z, dold, beta, nb));
-      else
+      double T;
+      if (sg < 0) {
+        const double4 Tn = d.fl_T[nb];
+        T = k == 0 ? Tn.x : (k == 1 ? Tn.y : Tn.z);
+      } else {
+        T = Tup[k];
+      }
+      dg += T;
+      if (fl_unknown(tn)) {
+        acc += T * (xc - (dold ? fl_dir(z, dold, beta, nb) : z[nb]));
+      } else {
         acc += T * xc;
+        rhs += T * d.fl_p[nb];
+      }
     }
-  if (d.fl_type[c] == 3) acc += outlet_cond(S, Kc) * xc;
-  *dc = xc;
+  if (d.fl_type[c] == 3) {
+    acc += Tc.w * xc;
+    dg += Tc.w;
+  }
+  if (xc_out) *xc_out = xc;
+  if (b) *b = rhs;
+  if (M) *M = dg;
   return acc;
 }
 
@@ -424,13 +461,19 @@ __global__ void __launch_bounds__(FL_B) k_fl_solve(Dev d) {
   const int c0 = blockIdx.x * FL_B + threadIdx.x, cs = G * FL_B;
   double* part = d.fl_part;  // slots of G partials: r.z, b.b (then r.r), r.r, d.q
   const double tol2 = d.fl_tol * d.fl_tol;
+  // the face conductances of this solve's permeabilities, once
+  for (int c = c0; c < d.Cf_total; c += cs) {
+    if (d.fl_type[c] == 2) continue;
+    d.fl_T[c] = face_conds(d, d.sp[d.fl_sample[c]], c);
+  }
+  if (!fl_grid_sync(ctl, gen)) return;
   // r = b - A p, z = r / M; the first direction is z (d_old = 0, beta = 0)
   double rz = 0.0, bb = 0.0, rr = 0.0;
   for (int c = c0; c < d.Cf_total; c += cs) {
     if (!fl_unknown(d.fl_type[c])) continue;
     const SampleDev& S = d.sp[d.fl_sample[c]];
     double b, M;
-    const double Ap = apply_A(d, S, c, d.fl_p, &b, &M);
+    const double Ap = apply_A_stored(d, S, c, d.fl_p, nullptr, 0.0, nullptr, &b, &M);
     const double rc = b - Ap;
     const double z = rc / M;
     d.fl_M[c] = M;
@@ -460,7 +503,7 @@ __global__ void __launch_bounds__(FL_B) k_fl_solve(Dev d) {
       if (!fl_unknown(d.fl_type[c])) continue;
       const SampleDev& S = d.sp[d.fl_sample[c]];
       double dc;
-      const double q = apply_A_dir(d, S, c, d.fl_z, dold, beta, &dc);
+      const double q = apply_A_stored(d, S, c, d.fl_z, dold, beta, &dc, nullptr, nullptr);
       dnew[c] = dc;
       d.fl_q[c] = q;
       dq += dc * q;
