@@ -18,18 +18,24 @@
  *     sqrt(k_t m*), spring history rotated into the tangent plane, Coulomb
  *     magnitude cap (Eq. 4 and Eq. 35) with F_lim = F_ne + 2 F_C on bonds.
  *   - Torque arm: the particle radius along the normal (Eq. 5).
- *   - Bonds break at Table 1 point C (delta < delta_C) and never reform.
+ *   - Bonds break at Table 1 point C (delta < delta_C) and never reform
+ *     (modified JKR).  The original JKR of the generation stage (Fig. 1):
+ *     a contact forms when the particles touch and separates at point S,
+ *     the turning point of Eq. 13 (a displacement-driven contact).
+ *   - Preparation stages (Sec. 3.1): the top plate moves at a velocity
+ *     proportional to the difference between the stress on it and the
+ *     target (a servo; the paper only says it moved down to 1 MPa), and the
+ *     penetrometer moves at a constant speed, down and back up.
  *   - Drag: Eq. 8-11 with u the interstitial velocity U_s / n.
  *   - Rayleigh step Eq. 37-38 with G = E / (2 (1 + nu)).
  *
  * Parity unpinned (no value the paper prints or the mathematics fixes checks
- * these parts; the GPU is compared against them as written): the tangential
- * damping and spring rotation (the tangential stiffness is pinned by
- * Mindlin's ratio), the choice of F_ne + 2 F_C as the Coulomb limit under
- * cohesion (its positivity on the JKR branch is pinned), the drag of a
- * coarse grain, the cube porosity spread (its volume conservation is
- * pinned), the walls' tangential contact (their normal Hertz law is pinned),
- * and the closure hooks (not part of the paper).
+ * these parts; the GPU is compared against them as written): the choice of
+ * F_ne + 2 F_C as the Coulomb limit under cohesion (its positivity on the
+ * JKR branch is pinned), the drag of a coarse grain, the cube porosity spread
+ * (its volume conservation is pinned), the Kozeny-Carman permeability, the
+ * plate's servo law (its equilibrium is pinned) and the closure hooks (not
+ * part of the paper).
  */
 #include "cgdem_oracle.h"
 
@@ -48,6 +54,10 @@
  * point C, exact form of the printed -0.57).  Nearest double to the real
  * number; pinned against the closed form by the oracle tests. */
 #define ORA_KC (-1.8505508252042548)
+/* (C_S)^3 * pi^2 where C_S = 4^(-2/3) - 2 4^(-1/6) = delta_S / xi (point S of
+ * Fig. 1: the turning point of Eq. 13, a_S^3 = pi gamma R*^2 / (4 E*)).
+ * Nearest double to the real number; pinned by the oracle tests. */
+#define ORA_KS (-16.654957426838293)
 /* (pi/6)^(1/3): side of the cube with the volume of a unit-diameter sphere. */
 #define ORA_CUBE_SIDE (0.8059959770082348)
 #define ORA_TWO_M40 (9.094947017729282379150390625e-13) /* 2^-40 */
@@ -104,9 +114,26 @@ int ora_bond_breaks(double delta, double Rs, double Es, double gamma) {
     return lhs < rhs;
 }
 
-double ora_jkr_contact_radius(double delta, double Rs, double Es, double gamma) {
-    /* Solve Eq. 13 for a on the stable branch a >= a_C by bisection to 1 ulp. */
-    double lo = ora_a_c(Rs, Es, gamma);
+static double ora_a_s(double Rs, double Es, double gamma) {
+    /* point S: d/da of Eq. 13 vanishes, 2 a / R* = sqrt(pi gamma / (E* a)) */
+    return cbrt(M_PI * gamma * Rs * Rs / (4.0 * Es));
+}
+
+double ora_delta_s(double Rs, double Es, double gamma) {
+    return ora_jkr_overlap(ora_a_s(Rs, Es, gamma), Rs, Es, gamma);
+}
+
+int ora_contact_separates(double delta, double Rs, double Es, double gamma) {
+    /* delta < delta_S, cubed as in ora_bond_breaks:
+     *   delta^3 * Es^2 < C_S^3 pi^2 * gamma^2 * Rs */
+    if (!(delta < 0.0)) return 0;
+    double lhs = delta * delta * delta * (Es * Es);
+    double rhs = ORA_KS * (gamma * gamma) * Rs;
+    return lhs < rhs;
+}
+
+/* Eq. 13 solved for a >= lo (where it increases with a) by bisection to 1 ulp. */
+static double jkr_radius_above(double lo, double delta, double Rs, double Es, double gamma) {
     double hi = lo;
     double base = sqrt(Rs * fabs(delta));
     if (base > hi) hi = base;
@@ -122,6 +149,16 @@ double ora_jkr_contact_radius(double delta, double Rs, double Es, double gamma) 
     double flo = fabs(ora_jkr_overlap(lo, Rs, Es, gamma) - delta);
     double fhi = fabs(ora_jkr_overlap(hi, Rs, Es, gamma) - delta);
     return flo < fhi ? lo : hi;
+}
+
+double ora_jkr_contact_radius(double delta, double Rs, double Es, double gamma) {
+    /* the stable branch of the modified JKR, a >= a_C */
+    return jkr_radius_above(ora_a_c(Rs, Es, gamma), delta, Rs, Es, gamma);
+}
+
+double ora_jkr_contact_radius_s(double delta, double Rs, double Es, double gamma) {
+    /* the branch of a displacement-driven original-JKR contact, a >= a_S */
+    return jkr_radius_above(ora_a_s(Rs, Es, gamma), delta, Rs, Es, gamma);
 }
 
 double ora_rayleigh_dt(double Rbar, double rho, double E, double nu) {
@@ -189,13 +226,17 @@ static int contact_law(const ora_params* p, double delta, int touching, const do
     double Gs = ora_gstar(p->E, p->nu);
     double beta = ora_beta(p->e);
     double a, Fne;
+    const int orig = p->jkr_mode == 1 && gamma > 0.0;
     if (*bonded) {
-        if (ora_bond_breaks(delta, Rs, Es, gamma)) {
-            *bonded = 0; /* modified JKR: break at C, no new bond */
+        if (orig ? ora_contact_separates(delta, Rs, Es, gamma) : ora_bond_breaks(delta, Rs, Es, gamma)) {
+            *bonded = 0; /* modified JKR: break at C for good; original JKR: separation at S */
         }
+    } else if (orig && touching) {
+        *bonded = 1; /* original JKR: the contact forms at A */
     }
     if (*bonded) {
-        a = ora_jkr_contact_radius(delta, Rs, Es, gamma);
+        a = orig ? ora_jkr_contact_radius_s(delta, Rs, Es, gamma)
+                 : ora_jkr_contact_radius(delta, Rs, Es, gamma);
         Fne = ora_jkr_force(a, Rs, Es, gamma);
     } else if (touching) {
         a = delta > 0.0 ? sqrt(Rs * delta) : 0.0; /* Hertz: Eq. 13 with gamma = 0 */
@@ -433,7 +474,7 @@ struct ora_sim {
     double *x, *v, *w, *F, *T, *R, *m, *I;
     uint8_t* active;
     int64_t* removed_step;
-    double* wall_xi; /* n * 3 walls * 3 */
+    double* wall_xi; /* n * 4 walls * 3: side, bottom, top plate, penetrometer */
     ora_rec* rec;
     int64_t nrec;
     uint64_t* vf;
@@ -453,6 +494,16 @@ struct ora_sim {
     double k_feat;
     double *cd, *cg;
     double* cdata; /* n x ORA_CL_COLS, see ora_get_closure_data */
+    /* moving boundaries (ora_stage): the top plate's height and velocity,
+       the penetrometer's tip height and direction; per particle the force
+       along z it exerts on each (quanta of 2^-40 N) at the last evaluation,
+       and their sums */
+    ora_stage stage;
+    double H_cur, v_plate;
+    double pen_z;
+    int pen_dir;
+    int64_t *plate_qp, *pen_qp;
+    int64_t plate_q, pen_q;
 };
 
 static int rec_cmp(const void* a, const void* b) {
@@ -480,7 +531,11 @@ ora_sim* ora_create(const ora_params* p, int64_t n, const double* x, const doubl
     s->I = (double*)calloc(n3, sizeof(double));
     s->active = (uint8_t*)calloc(n3, 1);
     s->removed_step = (int64_t*)calloc(n3, sizeof(int64_t));
-    s->wall_xi = (double*)calloc(n3 * 3, sizeof(double));
+    s->wall_xi = (double*)calloc(n3 * 4, sizeof(double));
+    s->plate_qp = (int64_t*)calloc(n3, sizeof(int64_t));
+    s->pen_qp = (int64_t*)calloc(n3, sizeof(int64_t));
+    s->H_cur = p->H;
+    s->stage.jkr_mode = p->jkr_mode;
     s->Fscale = (double*)calloc(n3, sizeof(double));
     s->Fnet = (double*)calloc(n3, sizeof(double));
     s->cd = (double*)calloc(n3, sizeof(double));
@@ -517,6 +572,7 @@ void ora_destroy(ora_sim* s) {
     free(s->wall_xi); free(s->rec); free(s->vf); free(s->Us); free(s->Fscale); free(s->Fnet);
     free(s->cd); free(s->cg); free(s->cdata);
     free(s->pres); free(s->gradp); free(s->react);
+    free(s->plate_qp); free(s->pen_qp);
     free(s);
 }
 
@@ -737,14 +793,50 @@ static int pair_cmp(const void* a, const void* b) {
 }
 
 /* wall contacts of one particle (cylinder domain), Hertz without cohesion */
+/* Penetrometer contact (Sec. 3.1): the point of the tool (a solid cylinder
+ * of radius rp on the axis, from its flat tip at height zt upwards) nearest
+ * to the particle's centre x.  Beside the tool that point is on its side,
+ * below the tip on the tip's face, and below and outside it on the tip's
+ * rim.  Returns the overlap R - distance; n is the unit vector from the
+ * centre towards that point. */
+static double tool_contact(const double x[3], double R, double rp, double zt, double n[3]) {
+    double r = sqrt(x[0] * x[0] + x[1] * x[1]);
+    n[0] = n[1] = n[2] = 0.0;
+    if (x[2] >= zt) { /* beside the tool: its side */
+        if (!(r > 0.0)) return -1.0;
+        n[0] = -x[0] / r;
+        n[1] = -x[1] / r;
+        return R - (r - rp);
+    }
+    double dz = zt - x[2];
+    if (r <= rp) { /* under the tip's face */
+        n[2] = 1.0;
+        return R - dz;
+    }
+    /* under and outside the rim: towards the nearest point of the rim circle */
+    double dr = r - rp;
+    double dist = sqrt(dr * dr + dz * dz);
+    n[0] = -dr * x[0] / (r * dist);
+    n[1] = -dr * x[1] / (r * dist);
+    n[2] = dz / dist;
+    return R - dist;
+}
+
+double ora_tool_overlap(const double x[3], double R, double rp, double zt, double n[3]) {
+    return tool_contact(x, R, rp, zt, n);
+}
+
 static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
     const ora_params* p = &s->p;
     const double* x = &s->x[3 * i];
     double R = s->R[i];
     double r = sqrt(x[0] * x[0] + x[1] * x[1]);
-    for (int wall = 0; wall < 3; ++wall) {
+    s->plate_qp[i] = 0;
+    s->pen_qp[i] = 0;
+    for (int wall = 0; wall < 4; ++wall) {
         double n[3] = {0, 0, 0};
         double delta = -1.0;
+        double vw = 0.0; /* the wall's velocity along z */
         if (wall == 0) { /* side wall r = Rc */
             if (r > 0.0) {
                 delta = (r + R) - p->Rc;
@@ -756,18 +848,22 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
                 delta = R - x[2];
                 n[2] = -1.0;
             }
-        } else { /* top plane z = H */
-            delta = (x[2] + R) - p->H;
+        } else if (wall == 2) { /* top plate z = H (moving at v_plate) */
+            delta = (x[2] + R) - s->H_cur;
             n[2] = 1.0;
+            vw = s->v_plate;
+        } else if (s->pen_dir != 0) { /* penetrometer */
+            delta = tool_contact(x, R, s->stage.pen_radius, s->pen_z, n);
+            vw = s->pen_dir * s->stage.pen_speed;
         }
-        double* h = &s->wall_xi[9 * i + 3 * wall];
+        double* h = &s->wall_xi[12 * i + 3 * wall];
         if (!(delta > 0.0)) {
             h[0] = h[1] = h[2] = 0.0;
             continue;
         }
         const double* v = &s->v[3 * i];
         const double* w = &s->w[3 * i];
-        double vrel[3] = {-v[0], -v[1], -v[2]};
+        double vrel[3] = {-v[0], -v[1], vw - v[2]};
         double rw[3] = {R * w[0], R * w[1], R * w[2]};
         double rwn[3];
         cross(rw, n, rwn);
@@ -779,6 +875,9 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
             continue;
         s->Fscale[i] += sc;
         s->Fnet[i] += sqrt(dot(F, F));
+        /* the particle pushes the plate or the tool with -F */
+        if (wall == 2) s->plate_qp[i] = (int64_t)llrint(-F[2] * 0x1p40);
+        if (wall == 3) s->pen_qp[i] = (int64_t)llrint(-F[2] * 0x1p40);
         double nFt[3];
         cross(n, Ft, nFt);
         for (int k = 0; k < 3; ++k) {
@@ -936,6 +1035,25 @@ int ora_compute_forces(ora_sim* s) {
         cl[9] = (double)cell;
         cl[10] = s->cd[i];
         cl[11] = s->cg[i];
+    }
+    /* the forces on the top plate and the penetrometer (integer quanta: the
+       sums do not depend on their order), and the plate's next velocity */
+    if (p->kind == 1) {
+        int64_t pq = 0, tq = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!s->active[i]) continue;
+            pq += s->plate_qp[i];
+            tq += s->pen_qp[i];
+        }
+        s->plate_q = pq;
+        s->pen_q = tq;
+        if (s->stage.plate_mode == 1) {
+            double stress = (double)pq * ORA_TWO_M40 / (M_PI * p->Rc * p->Rc);
+            double v = s->stage.plate_gain * (stress - s->stage.plate_stress);
+            if (v > s->stage.plate_vmax) v = s->stage.plate_vmax;
+            if (v < -s->stage.plate_vmax) v = -s->stage.plate_vmax;
+            s->v_plate = v;
+        }
     }
     /* drag reaction of Eq. 7: the particles' drag summed per cell, in
        integer quanta (the sums do not depend on their order) */
@@ -1200,6 +1318,46 @@ int ora_set_forces(ora_sim* s, const double* F, const double* T) {
     return 0;
 }
 
+/* The boundaries move with the particles' drift: the plate at the velocity
+ * of the last force evaluation, the penetrometer at its speed, turning back
+ * at pen_z_stop and removed back at pen_z_start. */
+static void drift_boundaries(ora_sim* s) {
+    const double dt = s->p.dt;
+    if (s->stage.plate_mode == 1) s->H_cur += dt * s->v_plate;
+    if (s->pen_dir != 0) {
+        s->pen_z += dt * ((double)s->pen_dir * s->stage.pen_speed);
+        if (s->pen_dir < 0 && s->pen_z <= s->stage.pen_z_stop) s->pen_dir = 1;
+        else if (s->pen_dir > 0 && s->pen_z >= s->stage.pen_z_start) s->pen_dir = 0;
+    }
+}
+
+int ora_set_stage(ora_sim* s, const ora_stage* st) {
+    if (!s || !st) return -1;
+    if (st->jkr_mode != 0 && st->jkr_mode != 1) return -1;
+    if (s->p.kind != 1 && (st->plate_mode != 0 || st->pen_mode != 0)) return -1;
+    s->stage = *st;
+    s->p.jkr_mode = st->jkr_mode;
+    if (st->plate_H > 0.0) s->H_cur = st->plate_H;
+    if (st->plate_mode != 1) s->v_plate = 0.0;
+    s->pen_dir = st->pen_mode == 1 ? -1 : 0;
+    s->pen_z = st->pen_z_start;
+    for (int64_t i = 0; i < s->n; ++i) { /* a new tool starts without spring history */
+        double* h = &s->wall_xi[12 * i + 9];
+        h[0] = h[1] = h[2] = 0.0;
+    }
+    return 0;
+}
+
+int ora_get_boundaries(const ora_sim* s, double out[6]) {
+    out[0] = s->H_cur;
+    out[1] = s->v_plate;
+    out[2] = (double)s->plate_q * ORA_TWO_M40 / (M_PI * s->p.Rc * s->p.Rc);
+    out[3] = s->pen_z;
+    out[4] = (double)s->pen_dir;
+    out[5] = (double)s->pen_q * ORA_TWO_M40;
+    return 0;
+}
+
 static void half_kick(ora_sim* s) {
     double h = 0.5 * s->p.dt;
 #pragma omp parallel for schedule(static)
@@ -1228,6 +1386,7 @@ int ora_step(ora_sim* s, int64_t nsteps) {
                 s->x[3 * i + c] = xc;
             }
         }
+        if (p->kind == 1) drift_boundaries(s);
         int ce = p->couple_every > 0 ? p->couple_every : 1;
         if (s->step % ce == 0) ora_couple_fluid(s);
         ora_compute_forces(s);

@@ -54,7 +54,38 @@ typedef struct {
     double p_inlet;     /* [Pa] */
     double perm_d;      /* grain diameter of the Kozeny-Carman permeability [m] */
     double n_cap;       /* porosity cap of the permeability (n -> 1 has none) */
+    /* particle-particle contact model: 0 the modified JKR (Fig. 2): bonds
+       only between the pairs that touch when ora_bond_touching is called,
+       broken at point C for good, new contacts Hertz; 1 the original JKR
+       (Fig. 1): a contact forms when two particles touch (point A: F jumps
+       to -8/9 F_C), follows Eq. 12-13 loading and unloading, and separates
+       at point S (delta_S, F = -5/9 F_C); the pair forms a new contact the
+       next time it touches */
+    int jkr_mode;
 } ora_params;
+
+/* The moving boundaries and contact model of a preparation stage (Sec. 3.1:
+ * generation with the original JKR, compression by the top plate to an
+ * overburden stress, perforation by a penetrometer with the modified JKR).
+ * Cylinder samples only. */
+typedef struct {
+    int jkr_mode;         /* as in ora_params */
+    int plate_mode;       /* 0: the top plate holds its height; 1: it moves at
+                             v = gain (stress - plate_stress), |v| <= plate_vmax,
+                             stress = its force along z / (pi Rc^2) at the last
+                             force evaluation */
+    double plate_H;       /* > 0: the plate's height from now on [m] */
+    double plate_stress;  /* target stress [Pa] */
+    double plate_gain;    /* [m / (s Pa)] */
+    double plate_vmax;    /* [m/s] */
+    int pen_mode;         /* 1: a penetrometer (a rigid cylinder of radius
+                             pen_radius on the axis, from its flat tip upwards)
+                             starts with its tip at pen_z_start, moves down at
+                             pen_speed until the tip reaches pen_z_stop, then up
+                             at the same speed until the tip is back at
+                             pen_z_start, where it is removed; 0: none */
+    double pen_radius, pen_speed, pen_z_start, pen_z_stop;
+} ora_stage;
 
 /* ---- closed forms and single-contact laws (pins and unit tests) ---- */
 /* E* for one material (Eq. 12 definitions with E1=E2, nu1=nu2). */
@@ -71,6 +102,13 @@ double ora_jkr_overlap(double a, double Rs, double Es, double gamma);
 double ora_delta_c(double Rs, double Es, double gamma);
 /* modified-JKR break test: 1 when delta < delta_C (evaluated as documented). */
 int ora_bond_breaks(double delta, double Rs, double Es, double gamma);
+/* Point S of the original JKR curve (Fig. 1): the turning point of Eq. 13,
+ * d delta / d a = 0, where a displacement-driven contact separates. */
+double ora_delta_s(double Rs, double Es, double gamma);
+/* original-JKR separation test: 1 when delta < delta_S (evaluated as documented). */
+int ora_contact_separates(double delta, double Rs, double Es, double gamma);
+/* contact radius on the branch a >= a_S solving Eq. 13 by bisection. */
+double ora_jkr_contact_radius_s(double delta, double Rs, double Es, double gamma);
 /* Rayleigh time step Eq. 37-38 with G = E/(2(1+nu)). */
 double ora_rayleigh_dt(double Rbar, double rho, double E, double nu);
 
@@ -104,6 +142,17 @@ int ora_compute_forces(ora_sim* s);
 /* nsteps of velocity Verlet (half kick, drift, contacts, fluid, forces, half kick, outlet). */
 int ora_step(ora_sim* s, int64_t nsteps);
 int ora_get_state(const ora_sim* s, double* x, double* v, double* w, double* F, double* T);
+/* Overlap R - distance between a particle (centre x, radius R) and the
+ * penetrometer (radius rp, tip at height zt), and the unit vector n from the
+ * centre towards the tool's nearest point. */
+double ora_tool_overlap(const double x[3], double R, double rp, double zt, double n[3]);
+/* Start a preparation stage (the boundaries move from the next drift on). */
+int ora_set_stage(ora_sim* s, const ora_stage* st);
+/* out[6]: top-plate height, its velocity for the next drift, the stress on
+ * it at the last force evaluation, the penetrometer tip's height, its
+ * direction (-1 down, +1 up, 0 none), and the force along z that the
+ * particles exert on it at the last force evaluation. */
+int ora_get_boundaries(const ora_sim* s, double out[6]);
 int ora_set_forces(ora_sim* s, const double* F, const double* T);
 int64_t ora_num_contacts(const ora_sim* s);
 /* Active particle contacts sorted by (id_i < id_j). xi has 3 entries per contact. */

@@ -29,7 +29,26 @@ class OraParams(C.Structure):
         ("V_cell", C.c_double), ("n_min", C.c_double),
         ("vf_mode", C.c_int), ("couple_every", C.c_int),
         ("fluid_mode", C.c_int), ("p_inlet", C.c_double), ("perm_d", C.c_double), ("n_cap", C.c_double),
+        ("jkr_mode", C.c_int),
     ]
+
+
+class OraStage(C.Structure):
+    _fields_ = [
+        ("jkr_mode", C.c_int),
+        ("plate_mode", C.c_int), ("plate_H", C.c_double), ("plate_stress", C.c_double),
+        ("plate_gain", C.c_double), ("plate_vmax", C.c_double),
+        ("pen_mode", C.c_int), ("pen_radius", C.c_double), ("pen_speed", C.c_double),
+        ("pen_z_start", C.c_double), ("pen_z_stop", C.c_double),
+    ]
+
+
+def make_stage(**kw) -> OraStage:
+    """A preparation stage from keyword arguments (missing ones are zero)."""
+    st = OraStage()
+    for k, v in kw.items():
+        setattr(st, k, v)
+    return st
 
 
 def lib():
@@ -46,6 +65,12 @@ def lib():
             ("ora_jkr_overlap", d, [d, d, d, d]),
             ("ora_delta_c", d, [d, d, d]),
             ("ora_bond_breaks", i, [d, d, d, d]),
+            ("ora_delta_s", d, [d, d, d]),
+            ("ora_contact_separates", i, [d, d, d, d]),
+            ("ora_jkr_contact_radius_s", d, [d, d, d, d]),
+            ("ora_set_stage", i, [vp, vp]),
+            ("ora_tool_overlap", d, [pd, d, d, d, pd]),
+            ("ora_get_boundaries", i, [vp, pd]),
             ("ora_rayleigh_dt", d, [d, d, d, d]),
             ("ora_pair_contact", i, [vp, pd, pd, pd, d, d, pd, pd, pd, d, d, pd, C.POINTER(C.c_int), pd]),
             ("ora_drag", None, [d, d, d, pd, pd, d, pd]),
@@ -134,6 +159,25 @@ def jkr_overlap(a, Rs, Es, gamma):
 
 def delta_c(Rs, Es, gamma):
     return lib().ora_delta_c(Rs, Es, gamma)
+
+
+def delta_s(Rs, Es, gamma):
+    return lib().ora_delta_s(Rs, Es, gamma)
+
+
+def contact_separates(delta, Rs, Es, gamma):
+    return bool(lib().ora_contact_separates(delta, Rs, Es, gamma))
+
+
+def jkr_contact_radius_s(delta, Rs, Es, gamma):
+    return lib().ora_jkr_contact_radius_s(delta, Rs, Es, gamma)
+
+
+def tool_overlap(x, R, rp, zt):
+    """Overlap with the penetrometer and the unit vector towards it."""
+    x = _f64(x, (3,))
+    n = np.zeros(3)
+    return lib().ora_tool_overlap(_pd(x), R, rp, zt, _pd(n)), n
 
 
 def bond_breaks(delta, Rs, Es, gamma):
@@ -321,6 +365,18 @@ class Sim:
             self.step(1)
             cd, cg = closure_corrections(theta, self.closure_data(), lo, hi, cd_max, cg_max)
             self.set_corrections(cd, cg)
+
+    def set_stage(self, st: OraStage):
+        if lib().ora_set_stage(self.h, C.byref(st)) != 0:
+            raise ValueError("ora_set_stage: invalid stage")
+
+    def boundaries(self):
+        """Top-plate height, its velocity, the stress on it, the penetrometer
+        tip's height and direction, the force along z on the penetrometer."""
+        out = np.zeros(6)
+        lib().ora_get_boundaries(self.h, _pd(out))
+        return dict(H=out[0], v_plate=out[1], stress=out[2], pen_z=out[3], pen_dir=int(out[4]),
+                    pen_force=out[5])
 
     def fluid(self):
         """(pressure [Cf], superficial velocity [Cf,3], dynamic pressure

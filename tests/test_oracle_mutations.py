@@ -4,8 +4,11 @@ Each case plants one mistake in a scratch copy of the C oracle (a torque
 of the wrong sign, the spring turned the wrong way or not rescaled, the
 tangential dashpot twice as strong, the spin left out of the contact
 velocity, half the tangential stiffness), builds it, and runs the pins of
-the tangential law against it: at least one of them must fail.  Nothing
-here touches the CUDA library.
+the tangential law against it: at least one of them must fail.  The same
+for the preparation stages (the original JKR separating at C or solved on
+the modified branch, the plate's servo of the wrong sign, the tool's rim
+normal without its axial part, the tool turning back late) against the
+preparation pins.  Nothing here touches the CUDA library.
 """
 import os
 import shutil
@@ -30,13 +33,30 @@ MUTATIONS = {
     "half the tangential stiffness": ("    double kt = 8.0 * Gs * a;", "    double kt = 4.0 * Gs * a;"),
 }
 
+# planted in the preparation stages, caught by tests/test_oracle_prep.py
+PREP_MUTATIONS = {
+    "original JKR separating at C": (
+        "if (orig ? ora_contact_separates(delta, Rs, Es, gamma) : ora_bond_breaks(delta, Rs, Es, gamma)) {",
+        "if (ora_bond_breaks(delta, Rs, Es, gamma)) {"),
+    "original JKR on the modified branch": (
+        "        a = orig ? ora_jkr_contact_radius_s(delta, Rs, Es, gamma)",
+        "        a = orig ? ora_jkr_contact_radius(delta, Rs, Es, gamma)"),
+    "plate servo of the wrong sign": (
+        "            double v = s->stage.plate_gain * (stress - s->stage.plate_stress);",
+        "            double v = s->stage.plate_gain * (s->stage.plate_stress - stress);"),
+    "tool rim normal without its axial part": ("    n[2] = dz / dist;", "    n[2] = 0.0;"),
+    "tool turning back late": ("if (s->pen_dir < 0 && s->pen_z <= s->stage.pen_z_stop) s->pen_dir = 1;",
+                               "if (s->pen_dir < 0 && s->pen_z < s->stage.pen_z_stop - 1e-6) s->pen_dir = 1;"),
+}
+
 PINS = ("five_sevenths or frame_indifferent or tangent_plane or dashpot or mindlin or coulomb")
 
 
-@pytest.mark.parametrize("name", list(MUTATIONS))
+@pytest.mark.parametrize("name", list(MUTATIONS) + list(PREP_MUTATIONS))
 def test_planted_mistake_fails_a_pin(name, tmp_path):
     src = open(os.path.join(ROOT, "oracle", "cgdem_oracle.c")).read()
-    a, b = MUTATIONS[name]
+    prep = name in PREP_MUTATIONS
+    a, b = PREP_MUTATIONS[name] if prep else MUTATIONS[name]
     assert a in src
     d = tmp_path / "tree"
     shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
@@ -44,7 +64,8 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
     (d / "oracle" / "cgdem_oracle.c").write_text(src.replace(a, b))
     for sub in ("tests", "paper_2211_06142_gb300"):
         os.symlink(os.path.join(ROOT, sub), d / sub)
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-p",
-                        "no:cacheprovider", "-m", "not gpu", "-k", PINS],
+    pins = ["tests/test_oracle_prep.py"] if prep else ["tests/test_oracle_pins.py", "-k", PINS]
+    r = subprocess.run([sys.executable, "-m", "pytest", *pins, "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"],
                        cwd=d, capture_output=True, text=True, env=dict(os.environ, PYTHONPATH=str(d)))
     assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]
