@@ -93,7 +93,8 @@ typedef struct {
     double n_min;           /* lower clamp of the porosity */
     int vf_mode;            /* 0 centroid, 1 equal-volume cube spread over cells */
     int couple_every;       /* recompute the porosity every k-th step (>= 1, equal in all samples) */
-    double skin;            /* candidate-list skin [m]; > 2 |delta_C| required */
+    double skin;            /* candidate-list skin [m]; > 2 |delta_C| required (2 |delta_S| with
+                               jkr_mode 1) */
     double r_max;           /* largest grain radius the sample holds [m] (sizes the search grid) */
     /* fluid: 0 the superficial velocity of cgdem_set_fluid_velocity;
        1 (cylinders) two-way coupling by Darcy flow, the fluid of Eq. 6 in the
@@ -110,7 +111,42 @@ typedef struct {
     int fluid_mode;
     double p_inlet;         /* injection (dynamic) pressure [Pa] */
     double perm_d;          /* grain diameter of the Kozeny-Carman permeability [m] */
+    /* particle-particle contact model (cgdem_set_stage changes it later):
+       0 the modified JKR (Sec. 2.3, Fig. 2): bonds only between the pairs
+       that cgdem_init_particles bonds, broken at point C (Table 1) for good,
+       new contacts Hertz; 1 the original JKR of the generation stage
+       (Sec. 3.1, Fig. 1): a contact forms when two grains touch (point A:
+       the force drops to -8/9 F_C), follows Eq. 12-13 loading and unloading,
+       and separates at point S, the turning point of Eq. 13 (delta_S =
+       -(3/4) (4 pi^2 gamma^2 R* / E*^2)^(1/3), F = -5/9 F_C); the pair forms
+       a new contact the next time it touches */
+    int jkr_mode;
 } cgdem_sample_params;
+
+/*
+ * A preparation stage of a cylinder sample (Sec. 3.1: generation with the
+ * original JKR, compression by the top plate to an overburden stress,
+ * perforation by a penetrometer with the modified JKR).  The boundaries move
+ * with the grains' drift, and their contacts are Hertz walls (Sec. 3.1) whose
+ * relative velocity includes the wall's.
+ */
+typedef struct {
+    int jkr_mode;           /* as in cgdem_sample_params */
+    int plate_mode;         /* 0: the top plate holds its height; 1: after every force
+                               evaluation its velocity becomes v = plate_gain (stress -
+                               plate_stress), |v| <= plate_vmax, where stress is the force
+                               along z the grains exert on it / (pi Rc^2) */
+    double plate_H;         /* > 0: the plate's height from now on (<= the sample's H) [m] */
+    double plate_stress;    /* target stress [Pa] (Sec. 3.1: 1 MPa) */
+    double plate_gain;      /* [m / (s Pa)] */
+    double plate_vmax;      /* [m/s] */
+    int pen_mode;           /* 1: a penetrometer, a rigid cylinder of radius pen_radius on the
+                               axis from its flat tip upwards, starts with its tip at
+                               pen_z_start, moves down at pen_speed until the tip reaches
+                               pen_z_stop, then up at the same speed until the tip is back at
+                               pen_z_start, where it is removed; 0: none */
+    double pen_radius, pen_speed, pen_z_start, pen_z_stop;
+} cgdem_stage;
 
 typedef struct {
     int precision;          /* cgdem_precision */
@@ -263,6 +299,23 @@ int cgdem_get_diagnostics(cgdem_ctx* ctx, double* out, int64_t cap, void* stream
  * Synchronises stream. */
 int cgdem_get_fluid(cgdem_ctx* ctx, double* p, double* U, double* gradp, int64_t* reaction,
                     int64_t* iters, void* stream);
+
+/* Start a preparation stage on cylinder sample `sample` (HOST struct): the
+ * contact model, the top plate and the penetrometer take effect from the
+ * next step (the boundaries move from the next drift on; a new penetrometer
+ * starts without spring history).  CGDEM_E_INVALID for a periodic sample
+ * with moving boundaries, a plate above the sample's H, non-positive speeds
+ * or radii where a boundary moves, or jkr_mode 1 with a skin below
+ * 2 |delta_S| of the largest pair.  Synchronises stream. */
+int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stage, void* stream);
+
+/* Per sample, 6 doubles (HOST, out[6 * n_samples]): the top plate's height
+ * [m], its velocity for the next drift [m/s], the stress on it at the last
+ * force evaluation [Pa], the penetrometer tip's height [m], its direction
+ * (-1 down, +1 up, 0 none), and the force along z the grains exert on it at
+ * the last force evaluation [N].  The forces are sums of integer quanta of
+ * 2^-40 N.  Synchronises stream. */
+int cgdem_get_boundaries(cgdem_ctx* ctx, double* out, int64_t cap, void* stream);
 
 /* Produced sand by size class (Sec. 3.4, Fig. 11).  edges: nclass + 1
  * increasing fine-scale diameters [m] (HOST), 1 <= nclass <= 16, or nclass

@@ -38,7 +38,27 @@ EXPORTS = [
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
     "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
+    "cgdem_set_stage", "cgdem_get_boundaries",
 ]
+
+
+class Stage(C.Structure):
+    """cgdem_stage: contact model and moving boundaries of a preparation stage."""
+    _fields_ = [
+        ("jkr_mode", C.c_int),
+        ("plate_mode", C.c_int), ("plate_H", C.c_double), ("plate_stress", C.c_double),
+        ("plate_gain", C.c_double), ("plate_vmax", C.c_double),
+        ("pen_mode", C.c_int), ("pen_radius", C.c_double), ("pen_speed", C.c_double),
+        ("pen_z_start", C.c_double), ("pen_z_stop", C.c_double),
+    ]
+
+
+def stage(**kw) -> Stage:
+    """A Stage from keyword arguments (missing ones are zero)."""
+    st = Stage()
+    for k, v in kw.items():
+        setattr(st, k, v)
+    return st
 
 
 class CgdemError(RuntimeError):
@@ -62,6 +82,7 @@ class SampleParams(C.Structure):
         ("vf_mode", C.c_int), ("couple_every", C.c_int), ("skin", C.c_double),
         ("r_max", C.c_double),
         ("fluid_mode", C.c_int), ("p_inlet", C.c_double), ("perm_d", C.c_double),
+        ("jkr_mode", C.c_int),
     ]
 
 
@@ -115,6 +136,8 @@ def lib():
             "cgdem_get_diagnostics": (i, [vp, vp, i64, vp]),
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
             "cgdem_set_psd_classes": (i, [vp, vp, i, vp]),
+            "cgdem_set_stage": (i, [vp, i, vp, vp]),
+            "cgdem_get_boundaries": (i, [vp, vp, i64, vp]),
             "cgdem_get_fluid": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "cgdem_get_produced_psd": (i, [vp, vp, vp, i64, vp]),
             "cgdem_get_counters": (i, [vp, vp, vp, vp, vp, vp]),
@@ -284,7 +307,7 @@ def spheres_per_warp_for(n, device="cuda:0"):
 
 def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1,
                   coulomb_mode=0, vf_mode=0, couple_every=1, n_min=0.2, r_max=None,
-                  gamma_fine=None, fluid_mode=0, p_inlet=0.0, perm_d=None) -> SampleParams:
+                  gamma_fine=None, fluid_mode=0, p_inlet=0.0, perm_d=None, jkr_mode=0) -> SampleParams:
     """SampleParams from an inputs.Sample-like object (material at fine scale)."""
     p = SampleParams()
     m = s.material
@@ -315,6 +338,7 @@ def sample_params(s, dt, skin, k=1.0, scheme=CG_NONE, use_drag=1, use_buoyancy=1
     p.p_inlet = float(p_inlet)
     # Kozeny-Carman diameter: the volume-mean grain diameter unless given
     p.perm_d = float(perm_d if perm_d is not None else np.mean((2 * np.asarray(s.R)) ** 3) ** (1 / 3))
+    p.jkr_mode = int(jkr_mode)
     return p
 
 
@@ -467,6 +491,18 @@ class Context:
         self._check(lib().cgdem_get_fluid(self.h, _ptr(p), _ptr(U), _ptr(g), _ptr(r), C.byref(it), self._s()),
                     "get_fluid")
         return p, U, g, r, it.value
+
+    def set_stage(self, sample, st: Stage):
+        """Start a preparation stage on one cylinder sample (cgdem_set_stage)."""
+        self._check(lib().cgdem_set_stage(self.h, int(sample), C.byref(st), self._s()), "set_stage")
+
+    def boundaries(self):
+        """Per sample: top-plate height, its velocity, the stress on it, the
+        penetrometer tip's height and direction, the force along z on it."""
+        out = np.zeros(6 * self.n_samples)
+        self._check(lib().cgdem_get_boundaries(self.h, _ptr(out), out.size, self._s()), "get_boundaries")
+        return [dict(H=o[0], v_plate=o[1], stress=o[2], pen_z=o[3], pen_dir=int(o[4]), pen_force=o[5])
+                for o in out.reshape(-1, 6)]
 
     def set_psd_classes(self, edges):
         """Record produced sand by size class (fine-scale diameter edges [m])."""

@@ -21,6 +21,7 @@ void launch_rebuild_cond(const Dev& d, cudaGraphConditionalHandle h, cudaStream_
 void launch_bond_touching(const Dev& d, cudaStream_t s);
 void launch_couple(const Dev& d, cudaStream_t s);
 void launch_kick_drift(const Dev& d, int couple, cudaStream_t s);
+void launch_clear_wall_history(const Dev& d, int sample, int wall, cudaStream_t s);
 void launch_kick_final(const Dev& d, cudaStream_t s);
 void launch_cube_after_mid(const Dev& d, cudaStream_t s);
 void launch_init(const Dev& d, cudaStream_t s);
@@ -118,6 +119,13 @@ struct Carver {
 };
 
 // Derive the device constants of one sample (grain level).
+// Separation at which a bonded pair of reduced radius Rs lets go: |delta_C|
+// (Table 1, modified JKR) or |delta_S| (point S, original JKR).
+double jkr_reach(double gamma, double Es, double Rs, int jkr_mode) {
+  const double c = jkr_mode == 1 ? 1.1905507889761495 : 0.5723571212766659;
+  return c * std::cbrt(PI * PI * gamma * gamma * Rs / (Es * Es));
+}
+
 int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params& p,
                   int64_t first, int64_t count, int cell_off, int fcell_off, SampleDev* out,
                   int* ncells, int* nfcells) {
@@ -160,11 +168,12 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   s.H = p.H;
   s.r_out = p.r_out;
   const double reach = 2.0 * p.r_max + p.skin;  // largest candidate distance
-  // bonded pairs must stay candidates: |delta_C| of the largest pair < skin / 2
+  // bonded pairs must stay candidates: |delta_C| (modified JKR) or |delta_S|
+  // (original JKR) of the largest pair < skin / 2
+  if (p.jkr_mode != 0 && p.jkr_mode != 1) return fail(ctx, CGDEM_E_INVALID, "jkr_mode must be 0 or 1");
+  s.jkr_mode = p.jkr_mode;
   {
-    const double Rs = 0.5 * p.r_max;
-    const double dC = 0.5723571212766659 *
-                      std::cbrt(PI * PI * s.gamma * s.gamma * Rs / (s.Es * s.Es));
+    const double dC = jkr_reach(s.gamma, s.Es, 0.5 * p.r_max, p.jkr_mode);
     if (!(2.0 * dC < p.skin))
       return fail(ctx, CGDEM_E_INVALID, "skin %.3g must exceed twice the bond-break separation %.3g",
                   p.skin, dC);
@@ -337,8 +346,8 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     d.fcell[b] = cv.take<int>(Npad);
     d.vq[b] = cv.take<unsigned long long>(Npad);
     if (cyl) {
-      if (mixed) d.wallhf[b] = cv.take<float4>(3 * (size_t)Npad);
-      else d.wallh[b] = cv.take<double4>(3 * (size_t)Npad);
+      if (mixed) d.wallhf[b] = cv.take<float4>(CGDEM_WALLS * (size_t)Npad);
+      else d.wallh[b] = cv.take<double4>(CGDEM_WALLS * (size_t)Npad);
     }
     d.rec[b] = mixed ? (void*)cv.take<RecF>((size_t)cap * Npad) : (void*)cv.take<RecD>((size_t)cap * Npad);
     d.cnt[b] = cv.take<uint32_t>(Npad);
@@ -377,6 +386,7 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
   d.disp = cv.take<double>(S);
   d.vmax2 = cv.take<unsigned long long>(S);
   d.diag = cv.take<double>(8 * (size_t)S);
+  d.stage = cv.take<StageDev>(S);
   bool fluid = false;
   for (int k = 0; k < S; ++k) fluid |= sp[k].fluid_mode == 1;
   if (fluid) {
@@ -832,6 +842,14 @@ int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const i
     cudaMemset(ctx->d.react[1], 0, sizeof(unsigned long long) * 3 * nc);
     ctx->d.fl_coop_blocks = cfg->fluid_kernels == 1 ? 0 : fluid_coop_blocks(ctx->d.Cf_total);
   }
+  {  // preparation stages: the top plate at the sample's H, no penetrometer
+    std::vector<StageDev> st(ctx->sd.size());
+    for (size_t k = 0; k < st.size(); ++k) {
+      st[k] = StageDev{};
+      st[k].H = ctx->sd[k].H;
+    }
+    cudaMemcpy(ctx->d.stage, st.data(), sizeof(StageDev) * st.size(), cudaMemcpyHostToDevice);
+  }
   *out = ctx;
   return CGDEM_OK;
 }
@@ -998,7 +1016,7 @@ int cgdem_set_closure(cgdem_ctx* ctx, const float* theta, const cgdem_closure_pa
     for (size_t i = 0; i < ctx->sd.size(); ++i) {
       const SampleDev& S = ctx->sd[i];
       const double Rs = 0.5 * ctx->sp[i].r_max, g = S.gamma * cmax;
-      const double dC = 0.5723571212766659 * std::cbrt(PI * PI * g * g * Rs / (S.Es * S.Es));
+      const double dC = jkr_reach(g, S.Es, Rs, S.jkr_mode);
       if (!(2.0 * dC < ctx->sp[i].skin))
         return fail(ctx, CGDEM_E_INVALID,
                     "sample %zu: skin %.3g must exceed twice the bond-break separation %.3g at "
@@ -1200,6 +1218,75 @@ int cgdem_get_fluid(cgdem_ctx* ctx, double* p, double* U, double* gradp, int64_t
   }
   if (iters) *iters = c.fl_iters;
   return check_status(ctx, s);
+}
+
+int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stg, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  if (!stg || sample < 0 || sample >= (int)ctx->sd.size()) return fail(ctx, CGDEM_E_INVALID, "bad sample or stage");
+  const cgdem_sample_params& p = ctx->sp[sample];
+  SampleDev& S = ctx->sd[sample];
+  if (stg->jkr_mode != 0 && stg->jkr_mode != 1) return fail(ctx, CGDEM_E_INVALID, "jkr_mode must be 0 or 1");
+  if (!(2.0 * jkr_reach(S.gamma, S.Es, 0.5 * p.r_max, stg->jkr_mode) < p.skin))
+    return fail(ctx, CGDEM_E_INVALID, "skin %.3g must exceed twice the separation of the contact model",
+                p.skin);
+  if ((stg->plate_mode != 0 || stg->pen_mode != 0) && S.kind != CGDEM_CYLINDER)
+    return fail(ctx, CGDEM_E_INVALID, "moving boundaries need a cylinder sample");
+  if ((stg->plate_mode != 0 && stg->plate_mode != 1) || (stg->pen_mode != 0 && stg->pen_mode != 1))
+    return fail(ctx, CGDEM_E_INVALID, "plate_mode and pen_mode must be 0 or 1");
+  if (stg->plate_H > S.H) return fail(ctx, CGDEM_E_INVALID, "plate_H above the sample's H");
+  if (stg->plate_mode == 1 && !(stg->plate_gain > 0 && stg->plate_vmax > 0 && std::isfinite(stg->plate_stress)))
+    return fail(ctx, CGDEM_E_INVALID, "a moving plate needs plate_gain > 0, plate_vmax > 0, a finite stress");
+  if (stg->pen_mode == 1 && !(stg->pen_radius > 0 && stg->pen_speed > 0 && stg->pen_z_stop < stg->pen_z_start))
+    return fail(ctx, CGDEM_E_INVALID, "a penetrometer needs pen_radius > 0, pen_speed > 0, pen_z_stop < pen_z_start");
+  cudaStream_t s = st(stream);
+  StageDev W;
+  CK(cudaMemcpyAsync(&W, ctx->d.stage + sample, sizeof W, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  W.plate_mode = stg->plate_mode;
+  W.plate_stress = stg->plate_stress;
+  W.plate_gain = stg->plate_gain;
+  W.plate_vmax = stg->plate_vmax;
+  if (stg->plate_H > 0) W.H = stg->plate_H;
+  if (stg->plate_mode != 1) W.v_plate = 0.0;
+  W.pen_radius = stg->pen_radius;
+  W.pen_speed = stg->pen_speed;
+  W.pen_z_start = stg->pen_z_start;
+  W.pen_z_stop = stg->pen_z_stop;
+  W.pen_z = stg->pen_z_start;
+  W.pen_dir = stg->pen_mode == 1 ? -1 : 0;
+  CK(cudaMemcpyAsync(ctx->d.stage + sample, &W, sizeof W, cudaMemcpyHostToDevice, s));
+  S.jkr_mode = stg->jkr_mode;
+  ctx->sp[sample].jkr_mode = stg->jkr_mode;
+  CK(cudaMemcpyAsync(&ctx->d.sp[sample].jkr_mode, &S.jkr_mode, sizeof(int), cudaMemcpyHostToDevice, s));
+  // a new penetrometer starts without spring history
+  if (S.kind == CGDEM_CYLINDER) launch_clear_wall_history(ctx->d, sample, 3, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return CGDEM_OK;
+}
+
+int cgdem_get_boundaries(cgdem_ctx* ctx, double* out, int64_t cap, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  const int S = (int)ctx->sd.size();
+  if (!out || cap < 6 * (int64_t)S) return fail(ctx, CGDEM_E_INVALID, "out needs 6 doubles per sample");
+  cudaStream_t s = st(stream);
+  std::vector<StageDev> W(S);
+  CK(cudaMemcpyAsync(W.data(), ctx->d.stage, sizeof(StageDev) * S, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < S; ++k) {
+    const double Rc = ctx->sd[k].Rc;
+    out[6 * k + 0] = W[k].H;
+    out[6 * k + 1] = W[k].v_plate;
+    out[6 * k + 2] = ctx->sd[k].kind == CGDEM_CYLINDER
+                         ? (double)W[k].plate_q_last * 9.094947017729282379150390625e-13 / (PI * Rc * Rc)
+                         : 0.0;
+    out[6 * k + 3] = W[k].pen_z;
+    out[6 * k + 4] = (double)W[k].pen_dir;
+    out[6 * k + 5] = (double)W[k].pen_q_last * 9.094947017729282379150390625e-13;
+  }
+  return CGDEM_OK;
 }
 
 int cgdem_set_psd_classes(cgdem_ctx* ctx, const double* edges, int nclass, void* stream) {

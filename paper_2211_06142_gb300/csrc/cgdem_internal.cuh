@@ -26,6 +26,8 @@ constexpr unsigned ST_CAPACITY = 1u;
 constexpr unsigned ST_BOND_LOST = 2u;
 constexpr unsigned ST_NONFINITE = 4u;
 constexpr unsigned ST_TIMEOUT = 8u;  // a bounded device-side wait expired
+// wall spring histories per sphere: cylinder side, bottom, top plate, penetrometer
+constexpr int CGDEM_WALLS = 4;
 
 // FP64 record: partner/flags + tangential spring (32 bytes)
 struct __align__(16) RecD {
@@ -88,6 +90,22 @@ struct SampleDev {
   int n_psd;
   double psd_edge[CGDEM_PSD_MAX + 1];
   double psd_mq;
+  int jkr_mode;  // 0 modified JKR, 1 original JKR (cgdem_sample_params)
+};
+
+// A preparation stage's moving boundaries of one sample (cgdem_set_stage),
+// and their state: the top plate's height and velocity, the penetrometer's
+// tip height and direction; the forces along z the grains exert on each,
+// summed in integer quanta of 2^-40 N over the running evaluation and kept
+// from the last one.
+struct StageDev {
+  int plate_mode;
+  int pen_dir;  // -1 down, +1 up, 0 no penetrometer
+  double plate_stress, plate_gain, plate_vmax;
+  double pen_radius, pen_speed, pen_z_start, pen_z_stop;
+  double H, v_plate, pen_z;
+  unsigned long long plate_q, pen_q;  // running sums (two's complement)
+  long long plate_q_last, pen_q_last;
 };
 
 // Learned closure (not part of the paper): per-particle corrections
@@ -156,8 +174,8 @@ struct Dev {
   int* sample[2];
   int* fcell[2];                  // fluid cell (global index) of the current position
   unsigned long long* vq[2];      // volume quantum round(V 2^40 / V_cell)
-  double4* wallh[2];              // wall spring history [3][Npad] (FP64 mode)
-  float4* wallhf[2];              // wall spring history [3][Npad] (mixed)
+  double4* wallh[2];              // wall spring history [CGDEM_WALLS][Npad] (FP64 mode)
+  float4* wallhf[2];              // wall spring history [CGDEM_WALLS][Npad] (mixed)
   // Candidate lists.  Mixed: every sphere lists all its candidates (a pair
   // is evaluated from both sides).  FP64: a pair is listed once, by its
   // lower-index sphere (the owner); the partner receives the result in its
@@ -206,6 +224,7 @@ struct Dev {
   double* fl_K;                   // permeability
   double* fl_p;                   // dynamic pressure (kept: the next solve starts from it)
   double *fl_r, *fl_z, *fl_d, *fl_q, *fl_M, *fl_b;  // conjugate-gradient vectors, diagonal, right-hand side
+  StageDev* stage;                // per sample: moving boundaries of the preparation stages
   double* fl_d2;                  // the one-launch solve's second direction buffer
   double4* fl_T;                  // its face conductances per cell: upper x, y, z faces, outlet face
   double* fl_part;                // per-block partial sums [4][fl_blocks]
@@ -351,6 +370,48 @@ __device__ __forceinline__ bool bond_breaks_exact(double delta, double Rs, doubl
   if (!(delta < 0.0)) return false;
   double lhs = __dmul_rn(__dmul_rn(__dmul_rn(delta, delta), delta), __dmul_rn(Es, Es));
   double rhs = __dmul_rn(__dmul_rn(KC, __dmul_rn(gamma, gamma)), Rs);
+  return lhs < rhs;
+}
+
+// The moving boundaries follow the grains' drift: the top plate at the
+// velocity of the last force evaluation, the penetrometer at its speed,
+// turning back at pen_z_stop and removed back at pen_z_start.
+__device__ __forceinline__ void drift_boundaries(StageDev& W, double dt) {
+  if (W.plate_mode == 1) W.H = __dadd_rn(W.H, __dmul_rn(dt, W.v_plate));
+  if (W.pen_dir != 0) {
+    W.pen_z = __dadd_rn(W.pen_z, __dmul_rn(dt, __dmul_rn((double)W.pen_dir, W.pen_speed)));
+    if (W.pen_dir < 0 && W.pen_z <= W.pen_z_stop) W.pen_dir = 1;
+    else if (W.pen_dir > 0 && W.pen_z >= W.pen_z_start) W.pen_dir = 0;
+  }
+}
+
+// After a force evaluation: the sums of the forces on the plate and the
+// penetrometer become the evaluation's (the running sums restart at zero),
+// and a stress-controlled plate takes its velocity for the next drift.
+__device__ __forceinline__ void close_boundaries(StageDev& W, double Rc) {
+  const long long pq = (long long)atomicExch(&W.plate_q, 0ull);
+  const long long tq = (long long)atomicExch(&W.pen_q, 0ull);
+  W.plate_q_last = pq;
+  W.pen_q_last = tq;
+  if (W.plate_mode == 1) {
+    const double stress = __ddiv_rn(__dmul_rn((double)pq, 9.094947017729282379150390625e-13),
+                                    __dmul_rn(__dmul_rn(3.14159265358979323846, Rc), Rc));
+    double v = __dmul_rn(W.plate_gain, __dsub_rn(stress, W.plate_stress));
+    if (v > W.plate_vmax) v = W.plate_vmax;
+    if (v < -W.plate_vmax) v = -W.plate_vmax;
+    W.v_plate = v;
+  }
+}
+
+// Original-JKR separation test (point S of Fig. 1, the turning point of
+// Eq. 13): delta < delta_S = C_S (pi^2 gamma^2 R* / E*^2)^(1/3), C_S =
+// 4^(-2/3) - 2 4^(-1/6), cubed as in bond_breaks_exact.
+__device__ __forceinline__ bool contact_separates_exact(double delta, double Rs, double Es,
+                                                        double gamma) {
+  const double KS = -16.654957426838293;  // C_S^3 pi^2
+  if (!(delta < 0.0)) return false;
+  double lhs = __dmul_rn(__dmul_rn(__dmul_rn(delta, delta), delta), __dmul_rn(Es, Es));
+  double rhs = __dmul_rn(__dmul_rn(KS, __dmul_rn(gamma, gamma)), Rs);
   return lhs < rhs;
 }
 

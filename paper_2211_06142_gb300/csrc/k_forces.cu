@@ -86,21 +86,35 @@ __device__ __forceinline__ float m_pow(float a, float b) { return exp2f(b * __lo
 // (Table 1, point A) and u^2 = a / a_A, Eq. 13 reads u^4 - u = delta / d_A
 // with d_A = a_A^2 / R*, and Eq. 12 reads F = pi gamma R* (16/3 u^6 - 8 u^3).
 // Newton from above converges monotonically (the quartic is convex and
-// increasing for u > 4^(-1/3); the stable branch starts at u_C = (3/4)^(1/3)).
+// increasing for u > u_S = 4^(-1/3), point S; the modified JKR's branch
+// starts at u_C = (3/4)^(1/3), point C).  The original JKR (orig) also runs
+// between S and C, D_S <= D < D_C: there Newton starts from u_S + t with
+// 6 u_S^2 t^2 = D - D_S, the root of the quartic's expansion at S to second
+// order, which lies above the root (the cubic and quartic terms are positive).
 template <typename T>
-__device__ __forceinline__ void jkr_solve(T delta, T Rs, T Es, T gamma, T* a_out, T* F_out) {
+__device__ __forceinline__ T jkr_start(T D, bool orig) {
+  const T uS = T(0.6299605249474366), DS = T(-0.4724703937105774), DC = T(-0.22714007410401746);
+  if (orig && D < DC) {
+    const T t2 = m_div(D - DS, T(2.381101577952299));  // (D - D_S) / (6 u_S^2)
+    return uS + (t2 > T(0) ? m_sqrt(t2) : T(0));
+  }
+  return D >= T(0) ? m_sqrt(m_sqrt(D + T(1))) + T(0.05) : T(1);
+}
+
+template <typename T>
+__device__ __forceinline__ void jkr_solve(T delta, T Rs, T Es, T gamma, bool orig, T* a_out, T* F_out) {
   const T pi = Consts<T>::pi();
   T aA = m_cbrt(m_div(T(4) * pi * gamma * Rs * Rs, Es));
   T dA = m_div(aA * aA, Rs);
   T D = m_div(delta, dA);
-  T u = D >= T(0) ? m_sqrt(m_sqrt(D + T(1))) + T(0.05) : T(1);
+  T u = jkr_start<T>(D, orig);
 #pragma unroll
   for (int it = 0; it < Consts<T>::newton_iters; ++it) {
     T u3 = u * u * u;
     u -= m_div(u3 * u - u - D, T(4) * u3 - T(1));
   }
-  const T uC = T(0.90856029641606983);  // (3/4)^(1/3)
-  if (u < uC) u = uC;
+  const T uLo = orig ? T(0.6299605249474366) : T(0.90856029641606983);  // u_S or u_C
+  if (u < uLo) u = uLo;
   T u3 = u * u * u;
   *a_out = u * u * aA;
   *F_out = pi * gamma * Rs * (T(16) / T(3) * u3 * u3 - T(8) * u3);
@@ -112,10 +126,11 @@ __device__ __forceinline__ void jkr_solve(T delta, T Rs, T Es, T gamma, T* a_out
 template <typename T>
 __device__ __forceinline__ void contact_law(T delta, V3<T> n, V3<T> vrel, V3<T> vc, T Rs, T ms,
                                             T gamma, bool bonded, T Es, T Gs, T beta, T mu, T dt,
-                                            int coulomb_mode, V3<T>& xi, V3<T>& Fi, V3<T>& Ft) {
+                                            int coulomb_mode, V3<T>& xi, V3<T>& Fi, V3<T>& Ft,
+                                            bool orig = false) {
   T a, Fne;
   if (bonded && gamma > T(0)) {
-    jkr_solve<T>(delta, Rs, Es, gamma, &a, &Fne);
+    jkr_solve<T>(delta, Rs, Es, gamma, orig, &a, &Fne);
   } else {
     a = delta > T(0) ? m_sqrt(Rs * delta) : T(0);
     Fne = m_div(T(4) * Es * a * a * a, T(3) * Rs);
@@ -184,15 +199,16 @@ __device__ __forceinline__ void contact_law_mixed(float delta, V3<float> n, V3<f
                                                   V3<float>& Ft) {
   float a, Fne;
   if (bonded && gamma > 0.f) {
+    const bool orig = S.jkr_mode == 1;
     const float D = __fdividef(delta, dA);
-    float u = m_sqrt(m_sqrt(D + 1.f));
+    float u = (orig && D < -0.22714007410401746f) ? jkr_start<float>(D, true) : m_sqrt(m_sqrt(D + 1.f));
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
       const float u3 = u * u * u;
       u -= __fdividef(u3 * u - u - D, 4.f * u3 - 1.f);
     }
-    const float uC = 0.90856029641606983f;  // (3/4)^(1/3)
-    if (u < uC) u = uC;
+    const float uLo = orig ? 0.6299605249474366f : 0.90856029641606983f;  // u_S or u_C
+    if (u < uLo) u = uLo;
     const float u3 = u * u * u;
     a = u * u * m_sqrt(dA * Rs);
     Fne = PI_F * gamma * Rs * (16.f / 3.f * u3 * u3 - 8.f * u3);
@@ -296,29 +312,73 @@ __device__ __forceinline__ float s64_to_f(long long v) {
   return v < 0 ? -m : m;
 }
 
-// Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law).  A
-// float pre-check selects the walls within 5 % of the radius; only those load
-// their spring history and compute the overlap in FP64.  A sphere cannot move
-// 5 % of its radius in one step, so every wall with a non-zero history is
-// among them (and gets its history cleared when the contact ends).
+// Penetrometer contact (Sec. 3.1): the point of the tool (a solid cylinder
+// of radius rp on the axis, from its flat tip at height zt upwards) nearest
+// to the sphere's centre: beside the tool on its side, below the tip on its
+// face, below and outside it on the tip's rim.  Returns the overlap R -
+// distance and the unit vector n from the centre towards that point.
+__device__ __forceinline__ double tool_overlap(double x, double y, double z, double R, double r,
+                                               double rp, double zt, double n[3]) {
+  n[0] = n[1] = n[2] = 0.0;
+  if (z >= zt) {  // beside the tool: its side
+    if (!(r > 0.0)) return -1.0;
+    n[0] = -x / r;
+    n[1] = -y / r;
+    return __dsub_rn(R, __dsub_rn(r, rp));
+  }
+  const double dz = __dsub_rn(zt, z);
+  if (r <= rp) {  // under the tip's face
+    n[2] = 1.0;
+    return __dsub_rn(R, dz);
+  }
+  const double dr = __dsub_rn(r, rp);  // under and outside the rim
+  const double dist = sqrt(__dadd_rn(__dmul_rn(dr, dr), __dmul_rn(dz, dz)));
+  const double rd = __dmul_rn(r, dist);
+  n[0] = __ddiv_rn(__dmul_rn(-dr, x), rd);
+  n[1] = __ddiv_rn(__dmul_rn(-dr, y), rd);
+  n[2] = __ddiv_rn(dz, dist);
+  return __dsub_rn(R, dist);
+}
+
+// Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law): the
+// side, the bottom (open over the outlet), the top plate and the
+// penetrometer of a preparation stage, the last two moving along z (their
+// velocity enters the contact's relative velocity).  A float pre-check
+// selects the walls within 5 % of the radius; only those load their spring
+// history and compute the overlap in FP64.  A sphere cannot move 5 % of its
+// radius relative to a wall in one step (the boundaries move by v dt), so
+// every wall with a non-zero history is among them (and gets its history
+// cleared when the contact ends).  The forces the sphere exerts on the plate
+// and the penetrometer along z are summed in integer quanta of 2^-40 N.
 template <typename T, typename H>
-__device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, float xf, float yf,
-                                              float zf, V3<T> v, V3<T> w, T R, T m, T Es, T Gs,
+__device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, double4 P, float xf,
+                                              float yf, float zf, V3<T> v, V3<T> w, T R, T m, T Es, T Gs,
                                               T beta, T mu, T dt, H* hist_base, size_t stride,
                                               V3<T>& F, V3<T>& Tq) {
   const float Rf = (float)R;
   const float rf = sqrtf(xf * xf + yf * yf);
   const float near = -0.05f * Rf;
-  const float dw[3] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f, zf + Rf - s.H_f};
+  const int pen_dir = W.pen_dir;
+  float dtool = -1e30f;
+  if (pen_dir != 0) {
+    const float rp = (float)W.pen_radius, zt = (float)W.pen_z;
+    if (zf >= zt) dtool = Rf - (rf - rp);
+    else if (rf <= rp) dtool = Rf - (zt - zf);
+    else dtool = Rf - sqrtf((rf - rp) * (rf - rp) + (zt - zf) * (zt - zf));
+  }
+  const double Hw = W.H;
+  const float dw[CGDEM_WALLS] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f,
+                                 zf + Rf - (float)Hw, dtool};
   // most spheres are far from every wall: leave before any FP64 work (the
   // compiler would otherwise hoist the loop-invariant radius and its square
   // root out of the wall loop and run them for every sphere)
-  if (!(dw[0] > near) && !(dw[1] > near) && !(dw[2] > near)) return;
-  for (int wall = 0; wall < 3; ++wall) {
+  if (!(dw[0] > near) && !(dw[1] > near) && !(dw[2] > near) && !(dw[3] > near)) return;
+  for (int wall = 0; wall < CGDEM_WALLS; ++wall) {
     if (!(dw[wall] > near)) continue;
     const H h = hist_base[(size_t)wall * stride];
     V3<T> hist = v3<T>(h.x, h.y, h.z);
     double delta = -1.0;
+    double vw = 0.0;  // the wall's velocity along z
     V3<T> n = v3<T>(0, 0, 0);
     const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
     if (wall == 0) {
@@ -332,9 +392,15 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, flo
         delta = fabs(P.w) - P.z;
         n = v3<T>(0, 0, -1);
       }
-    } else {
-      delta = (P.z + fabs(P.w)) - s.H;
+    } else if (wall == 2) {
+      delta = (P.z + fabs(P.w)) - Hw;
       n = v3<T>(0, 0, 1);
+      vw = W.v_plate;
+    } else {
+      double nd[3];
+      delta = tool_overlap(P.x, P.y, P.z, fabs(P.w), sqrt(r2), W.pen_radius, W.pen_z, nd);
+      n = v3<T>(T(nd[0]), T(nd[1]), T(nd[2]));
+      vw = (double)pen_dir * W.pen_speed;
     }
     if (!(delta > 0.0)) {
       if (hist.x != T(0) || hist.y != T(0) || hist.z != T(0)) {
@@ -344,7 +410,7 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, flo
       }
       continue;
     }
-    V3<T> vrel = v3<T>(-v.x, -v.y, -v.z);
+    V3<T> vrel = v3<T>(-v.x, -v.y, T(vw) - v.z);
     V3<T> rw = v3<T>(R * w.x, R * w.y, R * w.z);
     V3<T> rwn = cross3(rw, n);
     V3<T> vc = v3<T>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
@@ -354,6 +420,10 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, double4 P, flo
     H hn;
     hn.x = hist.x; hn.y = hist.y; hn.z = hist.z; hn.w = 0;
     hist_base[(size_t)wall * stride] = hn;
+    if (wall >= 2) {  // the sphere pushes the plate or the tool with -F
+      const long long qz = __double2ll_rn(-(double)Fi.z * 1099511627776.0);
+      atomicAdd(wall == 2 ? &W.plate_q : &W.pen_q, (unsigned long long)qz);
+    }
     V3<T> nFt = cross3(n, Ft);
     F.x += Fi.x;
     F.y += Fi.y;
@@ -561,10 +631,10 @@ __device__ __forceinline__ void finish_step(
       }
       if (S.kind == CGDEM_CYLINDER) {
         if constexpr (MIXED)
-          wall_contacts<T, float4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+          wall_contacts<T, float4>(S, d.stage[si], P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
                                    d.wallhf[pc] + p, (size_t)d.Npad, F, Tq);
         else
-          wall_contacts<T, double4>(S, P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+          wall_contacts<T, double4>(S, d.stage[si], P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
                                     d.wallh[pc] + p, (size_t)d.Npad, F, Tq);
       }
       // gravity, buoyancy (Eq. 1) and drag (Eq. 8-11)
@@ -876,6 +946,13 @@ __device__ __forceinline__ void finish_step(
         ctl->cur = nxt;
         ctl->step = m_step;
       }
+      // the moving boundaries: this evaluation's forces on them, the plate's
+      // next velocity, and (a step that drifts the grains) their drift
+      for (int s = 0; s < d.n_samples; ++s) {
+        if (d.sp[s].kind != CGDEM_CYLINDER) continue;
+        close_boundaries(d.stage[s], d.sp[s].Rc);
+        if (MODE == MODE_MID) drift_boundaries(d.stage[s], d.sp[s].dt);
+      }
       ctl->epoch = epoch;
       ctl->blk_next = 0;
       ctl->block_counter = 0u;
@@ -1058,8 +1135,15 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
           const double delta = __dsub_rn(Sd, dist);
           double gam_d = S.gamma;  // gamma sqrt(c_g,i c_g,j) under the closure
-          if (use_c && bonded) gam_d = S.gamma * sqrt((double)o_cg * (double)d.clc[cur][q].y);
-          if (bonded && bond_breaks_exact(delta, Rs, S.Es, gam_d)) bonded = false;
+          const bool orig_mode = S.jkr_mode == 1;
+          if (use_c && (bonded || orig_mode)) gam_d = S.gamma * sqrt((double)o_cg * (double)d.clc[cur][q].y);
+          const bool orig = orig_mode && gam_d > 0.0;
+          if (bonded) {  // modified JKR: break at C for good; original JKR: separation at S
+            if (orig ? contact_separates_exact(delta, Rs, S.Es, gam_d) : bond_breaks_exact(delta, Rs, S.Es, gam_d))
+              bonded = false;
+          } else if (orig && touching) {
+            bonded = true;  // original JKR: the contact forms at A
+          }
           act = bonded || touching;
           if (act && dist > 0.0) {
             const double4 QV = d.vel[cur][q];
@@ -1077,7 +1161,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
             V3<double> Fi, Ft;
             V3<double> xid = v3<double>((double)xi.x, (double)xi.y, (double)xi.z);
             contact_law<double>(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S.Es, S.Gs, S.beta,
-                                S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft);
+                                S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft, orig);
             xi = v3<T>(xid.x, xid.y, xid.z);
             const V3<double> nFt = cross3(n, Ft);
             Fc = v3<T>(Fi.x, Fi.y, Fi.z);
@@ -1426,11 +1510,13 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
         // surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure
         float gam_f = S.gamma_f;
         double gam_d = S.gamma;
-        if (use_c && bonded) {
+        const bool orig_mode = S.jkr_mode == 1;
+        if (use_c && (bonded || orig_mode)) {
           const float qcg = d.clc[cur][q].y;
           gam_f = S.gamma_f * sqrtf(my_c.y * qcg);
           gam_d = S.gamma * sqrt((double)my_c.y * (double)qcg);
         }
+        const bool orig = orig_mode && gam_d > 0.0;
         double d2e = 0.0, Se = 0.0;
         bool have_exact = false;
         if (need_exact) {
@@ -1438,13 +1524,15 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           have_exact = true;
           touching = d2e < __dmul_rn(Se, Se);
         }
+        if (!bonded && orig && touching) bonded = true;  // original JKR: the contact forms at A
         float xs = 0.0f;  // (pi^2 gamma^2 R* / E*^2)^(1/3) of a bonded pair
         if (bonded) {
+          // modified JKR: break at C for good; original JKR: separation at S
           bool broken;
           float dC = 0.0f, bandf = 4.0f * S.dq_f;
           if (gam_f > 0.f) {
             xs = m_cbrt(__fdividef(PI_F * PI_F * gam_f * gam_f * Rs, S.Es_f * S.Es_f));
-            dC = -0.57235712127666594f * xs;
+            dC = (orig ? -1.1905507889761495f : -0.57235712127666594f) * xs;
             bandf += 2e-5f * fabsf(dC);
           }
           if (delta < dC - bandf) {
@@ -1460,7 +1548,8 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
             }
             const double Rid = fabs(A.w), Rjd = fabs(B.w);
             const double Rsd = __dmul_rn(Rid, Rjd) / __dadd_rn(Rid, Rjd);
-            broken = bond_breaks_exact(__dsub_rn(Se, sqrt(d2e)), Rsd, S.Es, gam_d);
+            const double de = __dsub_rn(Se, sqrt(d2e));
+            broken = orig ? contact_separates_exact(de, Rsd, S.Es, gam_d) : bond_breaks_exact(de, Rsd, S.Es, gam_d);
           }
           if (broken) bonded = false;
         }

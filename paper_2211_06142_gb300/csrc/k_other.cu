@@ -172,10 +172,10 @@ __global__ void k_rb_permute(Dev d) {
   d.vq[pn][p] = d.vq[pc][o];
   if (d.clc[0]) d.clc[nxt][p] = d.clc[cur][o];
   if (d.mixed && d.wallhf[0]) {
-    for (int w = 0; w < 3; ++w)
+    for (int w = 0; w < CGDEM_WALLS; ++w)
       d.wallhf[pn][(size_t)w * d.Npad + p] = d.wallhf[pc][(size_t)w * d.Npad + o];
   } else if (!d.mixed && d.wallh[0]) {
-    for (int w = 0; w < 3; ++w)
+    for (int w = 0; w < CGDEM_WALLS; ++w)
       d.wallh[pn][(size_t)w * d.Npad + p] = d.wallh[pc][(size_t)w * d.Npad + o];
   }
 }
@@ -467,7 +467,7 @@ __global__ void k_rb_permute2(Dev d) {
   d.vq[pc][s] = d.vq[pn][c];
   if (d.clc[0]) d.clc[cur][s] = d.clc[nxt][c];
   if (d.wallhf[0])
-    for (int w = 0; w < 3; ++w)
+    for (int w = 0; w < CGDEM_WALLS; ++w)
       d.wallhf[pc][(size_t)w * d.Npad + s] = d.wallhf[pn][(size_t)w * d.Npad + c];
 }
 
@@ -982,6 +982,7 @@ __global__ void k_after_drift(Dev d, int couple) {
   for (int s = 0; s < d.n_samples; ++s) {
     if (__uint_as_float(d.dmax2[s]) > d.sp[s].rebuild_q2) c->rebuild = 1;
     if ((c->step % d.sp[s].couple_every) == 0) any = true;
+    if (d.sp[s].kind == CGDEM_CYLINDER) drift_boundaries(d.stage[s], d.sp[s].dt);  // with the grains
   }
   if (couple && any) {
     c->vf_cur = (c->vf_cur + 1) % 3;
@@ -1072,7 +1073,7 @@ __global__ void k_init_state(Dev d) {
     d.clc[0][p] = make_float2(1.0f, 1.0f);
     d.clc[1][p] = make_float2(1.0f, 1.0f);
   }
-  for (int w = 0; w < 3; ++w) {
+  for (int w = 0; w < CGDEM_WALLS; ++w) {
     if (d.mixed && d.wallhf[cur]) d.wallhf[cur][(size_t)w * d.Npad + p] = make_float4(0, 0, 0, 0);
     if (!d.mixed && d.wallh[cur]) d.wallh[cur][(size_t)w * d.Npad + p] = make_double4(0, 0, 0, 0);
   }
@@ -1309,6 +1310,21 @@ void launch_kick_drift(const Dev& d, int couple, cudaStream_t s) {
   // the buffer after the (possibly rotated) current one must be zero
   const int Gc = nblk(d.Cf_total, 256);
   if (couple && Gc) k_vf_zero<<<Gc, 256, 0, s>>>(d, 1);
+}
+
+// Spring history of one wall cleared for the spheres of one sample.
+__global__ void k_clear_wall_history(Dev d, int sample, int wall) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.N) return;
+  const int pc = d.ctl->pcur;
+  if (d.sample[pc][p] != sample) return;
+  const size_t i = (size_t)wall * d.Npad + p;
+  if (d.mixed && d.wallhf[pc]) d.wallhf[pc][i] = make_float4(0, 0, 0, 0);
+  if (!d.mixed && d.wallh[pc]) d.wallh[pc][i] = make_double4(0, 0, 0, 0);
+}
+
+void launch_clear_wall_history(const Dev& d, int sample, int wall, cudaStream_t s) {
+  if (d.N) k_clear_wall_history<<<nblk(d.N, 256), 256, 0, s>>>(d, sample, wall);
 }
 
 void launch_kick_final(const Dev& d, cudaStream_t s) {

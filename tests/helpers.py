@@ -93,17 +93,26 @@ def normwise_error(Fg, Fo, scale):
 # or bond-break threshold in one of them; those are checked separately (every
 # differing pair must sit at a threshold) and left out of the force check.
 
-def jkr_radius_np(delta, Rs, Es, gamma):
-    """Contact radius on the stable branch of Eq. 13, by Newton on the reduced
-    quartic (test-side, for a bound)."""
+def jkr_radius_np(delta, Rs, Es, gamma, orig=False):
+    """Contact radius on the stable branch of Eq. 13 (from point C, or from
+    point S for the original JKR), by Newton on the reduced quartic
+    (test-side, for a bound)."""
     aA = (4 * np.pi * gamma * Rs * Rs / Es) ** (1 / 3)
     dA = aA * aA / Rs
     D = delta / dA
     u = np.where(D >= 0, (np.maximum(D, 0) + 1) ** 0.25 + 0.05, 1.0)
-    for _ in range(40):
+    for _ in range(60):
         u = u - (u ** 4 - u - D) / (4 * u ** 3 - 1)
-    u = np.maximum(u, 0.75 ** (1 / 3))
+    u = np.maximum(u, 0.25 ** (1 / 3) if orig else 0.75 ** (1 / 3))
     return u * u * aA
+
+
+def tool_overlap_np(x, R, rp, zt):
+    """Overlap of each sphere with the penetrometer (test-side, for a bound)."""
+    r = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
+    dz = zt - x[:, 2]
+    rim = np.sqrt(np.maximum(r - rp, 0) ** 2 + dz ** 2)
+    return np.where(x[:, 2] >= zt, R - (r - rp), np.where(r <= rp, R - dz, R - rim))
 
 
 def state_diff(s, g, o):
@@ -125,9 +134,11 @@ def fixed_quantum(s, skin):
     return 2.0 ** math.ceil(math.log2(reach / 2.0 ** 30))
 
 
-def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0):
+def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0, orig=False, H=None, tool=None):
     """Per-particle bounds on |F_gpu - F_oracle| and |T_gpu - T_oracle| after
-    several mixed steps (see above)."""
+    several mixed steps (see above); orig: the original JKR's branch for
+    the contacts in force; H: the top plate's height, if it moved; tool:
+    (radius, tip height) of a penetrometer, if one is in."""
     m = s.material
     Es = m["E"] / (2 * (1 - m["nu"] ** 2))
     Gs = m["E"] / (2 * (1 + m["nu"])) / (2 * (2 - m["nu"]))
@@ -155,7 +166,7 @@ def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0):
         a = np.sqrt(Rs * np.maximum(delta, 0))
         kn = 2 * Es * a
         if bond.any():
-            ab = jkr_radius_np(delta[bond], Rs[bond], Es, gamma)
+            ab = jkr_radius_np(delta[bond], Rs[bond], Es, gamma, orig)
             dFda = 4 * Es * ab ** 2 / Rs[bond] - 1.5 * np.sqrt(16 * np.pi * gamma * Es * ab)
             ddda = 2 * ab / Rs[bond] - np.sqrt(np.pi * gamma / (Es * ab))
             a[bond] = ab
@@ -171,8 +182,11 @@ def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0):
         x = o["x"]
         r = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
         dom = s.domain
-        for dw_ in (r + R - dom["Rc"], np.where(r >= dom["r_out"], R - x[:, 2], -1.0),
-                    x[:, 2] + R - dom["H"]):
+        walls = [r + R - dom["Rc"], np.where(r >= dom["r_out"], R - x[:, 2], -1.0),
+                 x[:, 2] + R - (dom["H"] if H is None else H)]
+        if tool is not None:
+            walls.append(tool_overlap_np(x, R, *tool))
+        for dw_ in walls:
             aw = np.sqrt(R * np.maximum(dw_, 0))
             kw = (2 * Es + 8 * Gs) * aw
             gw = cd * (np.sqrt(2 * Es * aw * mass) + np.sqrt(8 * Gs * aw * mass))
@@ -197,7 +211,7 @@ def agreeing_particles(n, gc, oc):
     return ok
 
 
-def check_mixed_forces(s, g, o, sim, gc, tau, k=1.0, rows=None, skin=None):
+def check_mixed_forces(s, g, o, sim, gc, tau, k=1.0, rows=None, skin=None, **bound_kw):
     """Forces and torques after several mixed steps within force_bound for
     the particles (of `rows`, default all) whose contacts agree; returns the
     number of particles left out."""
@@ -206,7 +220,7 @@ def check_mixed_forces(s, g, o, sim, gc, tau, k=1.0, rows=None, skin=None):
     if rows is not None:
         ok &= rows
     dq = fixed_quantum(s, default_skin(s) if skin is None else skin)
-    bF, bT = force_bound(s, o, sim, g, tau, k, dq)
+    bF, bT = force_bound(s, o, sim, g, tau, k, dq, **bound_kw)
     eF = np.linalg.norm(g["F"] - o["F"], axis=1)
     eT = np.linalg.norm(g["T"] - o["T"], axis=1)
     bad = ok & ((eF > bF) | (eT > bT))

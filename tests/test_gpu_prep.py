@@ -1,0 +1,144 @@
+"""The preparation stages (Sec. 3.1) on the GPU against the oracle, both
+precisions, through the C ABI.
+
+* Original JKR (the generation stage, Fig. 1) on a moving periodic packing
+  without initial bonds: contacts form when grains touch and separate at
+  point S.  Contact lists with their contact flags bit-exact in FP64;
+  forces within the per-step bar plus what the two runs' state difference
+  moves them (tests/helpers.py), which near S grows with the curve's slope.
+* Compression: the small cylinder under a stress-controlled top plate that
+  starts on the bed's highest grain; the plate's height, velocity and
+  stress follow the oracle's.
+* Perforation: the small cylinder, bonded (modified JKR), with a
+  penetrometer coming down from just above the bed; the tool's height and
+  the force on it follow the oracle's.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2211_06142_gb300 import cgdem
+from paper_2211_06142_gb300 import inputs as I
+from tests.helpers import (check_mixed_forces, default_dt, default_skin, oracle_params, small_cylinder,
+                           with_velocities)
+
+pytestmark = pytest.mark.gpu
+
+TAU = {cgdem.FP64: 1e-10, cgdem.MIXED: 1e-4}
+
+
+def contexts(s, prec, jkr_mode, bond, skin=None, g=None):
+    dt = default_dt(s)
+    skin = default_skin(s) if skin is None else skin
+    p = cgdem.sample_params(s, dt, skin, jkr_mode=jkr_mode)
+    if g is not None:
+        for i in range(3):
+            p.g[i] = g[i]
+    ctx = cgdem.Context([p], [len(s.R)], precision=prec, max_neighbors=64)
+    ctx.set_fluid_velocity(s.Us)
+    ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=bond)
+    op = oracle_params(s, dt, g=g)
+    op.jkr_mode = jkr_mode
+    sim = O.Sim(op, s.x, s.v, s.w, s.R, s.Us)
+    if bond:
+        sim.bond_touching()
+    sim.couple_fluid()
+    return ctx, sim, skin
+
+
+def compare(s, ctx, sim, prec, skin, **bound_kw):
+    g, o = ctx.get_state(), sim.state()
+    gc = ctx.get_contacts()
+    oi, oj, ob, _ = sim.contacts()
+    if prec == cgdem.FP64:
+        assert np.array_equal(gc[0], oi) and np.array_equal(gc[1], oj) and np.array_equal(gc[2], ob)
+    left = check_mixed_forces(s, g, o, sim, gc, TAU[prec], skin=skin, **bound_kw)
+    assert left <= (0 if prec == cgdem.FP64 else 0.02 * len(s.R))
+    return g, o
+
+
+@pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
+def test_original_jkr_contacts_form_and_separate(prec):
+    s = with_velocities(copy.copy(I.cached(I.small_periodic, 2000, 0)), 2e-2)
+    # the original JKR keeps a pair until |delta_S|: twice the skin of the tests
+    ctx, sim, skin = contexts(s, prec, 1, bond=False, skin=2 * default_skin(s))
+    ctx.compute_forces()
+    sim.compute_forces()
+    compare(s, ctx, sim, prec, skin, orig=True)
+    formed = broken = 0
+    before = set(zip(*(a.tolist() for a in sim.contacts()[:2])))
+    for n in (25, 25, 50):
+        ctx.step(n)
+        sim.step(n)
+        compare(s, ctx, sim, prec, skin, orig=True)
+        now = set(zip(*(a.tolist() for a in sim.contacts()[:2])))
+        formed += len(now - before)
+        broken += len(before - now)
+        before = now
+    assert formed > 0 and broken > 0  # both ends of Fig. 1's curve were exercised
+    oi, oj, ob, _ = sim.contacts()
+    assert np.all(ob == 1)  # under the original JKR every contact in force is a JKR contact
+    ctx.close()
+
+
+def bed_top(s):
+    return float((s.x[:, 2] + s.R).max())
+
+
+@pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
+def test_plate_compression_follows_the_oracle(prec):
+    s = small_cylinder()
+    ctx, sim, skin = contexts(s, prec, 1, bond=False, skin=2 * default_skin(s))
+    H0 = bed_top(s)
+    sigma = 2e4
+    A = np.pi * s.domain["Rc"] ** 2
+    kw = dict(jkr_mode=1, plate_mode=1, plate_H=H0, plate_stress=sigma, plate_gain=0.05 / sigma,
+              plate_vmax=0.05)
+    ctx.set_stage(0, cgdem.stage(**kw))
+    sim.set_stage(O.make_stage(**kw))
+    ctx.compute_forces()
+    sim.compute_forces()
+    travel = 0.0
+    for n in (50, 50, 100):
+        ctx.step(n)
+        sim.step(n)
+        gb, ob = ctx.boundaries()[0], sim.boundaries()
+        travel = H0 - ob["H"]
+        tolH = (1e-9 if prec == cgdem.FP64 else 1e-3) * travel + 1e-15
+        assert abs(gb["H"] - ob["H"]) <= tolH, (gb, ob)
+        tolS = (1e-8 if prec == cgdem.FP64 else 1e-3) * sigma
+        assert abs(gb["stress"] - ob["stress"]) <= tolS, (gb, ob)
+        assert abs(gb["v_plate"] - ob["v_plate"]) <= 0.05 / sigma * tolS + 1e-15
+        compare(s, ctx, sim, prec, skin, orig=True, H=ob["H"])
+    assert travel > 0 and ob["stress"] > 0  # the plate came down and carries the bed
+    assert ob["stress"] * A > 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
+def test_penetrometer_follows_the_oracle(prec):
+    s = small_cylinder()
+    ctx, sim, skin = contexts(s, prec, 0, bond=True)
+    top = bed_top(s)
+    rp = 0.25 * s.domain["Rc"]
+    kw = dict(jkr_mode=0, pen_mode=1, pen_radius=rp, pen_speed=2.0, pen_z_start=top + 1e-6,
+              pen_z_stop=0.5 * top)
+    ctx.set_stage(0, cgdem.stage(**kw))
+    sim.set_stage(O.make_stage(**kw))
+    ctx.compute_forces()
+    sim.compute_forces()
+    Fmax = 0.0
+    for n in (100, 100, 100):
+        ctx.step(n)
+        sim.step(n)
+        gb, ob = ctx.boundaries()[0], sim.boundaries()
+        assert gb["pen_dir"] == ob["pen_dir"] == -1
+        assert gb["pen_z"] == pytest.approx(ob["pen_z"], rel=1e-14)
+        Fmax = max(Fmax, ob["pen_force"])
+        tolF = (1e-8 if prec == cgdem.FP64 else 2e-3) * max(abs(ob["pen_force"]), 1e-300) + 1e-12
+        assert abs(gb["pen_force"] - ob["pen_force"]) <= tolF, (gb, ob)
+        compare(s, ctx, sim, prec, skin, tool=(rp, ob["pen_z"]))
+    assert Fmax > 0  # the tool met the bed
+    ctx.close()
