@@ -340,6 +340,62 @@ __device__ __forceinline__ double tool_overlap(double x, double y, double z, dou
   return __dsub_rn(R, dist);
 }
 
+// One Hertz contact of a sphere with a flat or curved wall moving at vw
+// along z: overlap delta, unit normal n from the centre towards the wall,
+// spring history h (cleared when the contact has ended).  Returns the force
+// on the sphere along z (0 without contact) and adds force and torque.
+template <typename T, typename H>
+__device__ __forceinline__ T wall_hertz(double delta, V3<T> n, double vw, const SampleDev& s, V3<T> v,
+                                        V3<T> w, T R, T m, T Es, T Gs, T beta, T mu, T dt, H* h,
+                                        V3<T>& F, V3<T>& Tq) {
+  const H h0 = *h;
+  V3<T> hist = v3<T>(h0.x, h0.y, h0.z);
+  if (!(delta > 0.0)) {
+    if (hist.x != T(0) || hist.y != T(0) || hist.z != T(0)) {
+      H z;
+      z.x = 0; z.y = 0; z.z = 0; z.w = 0;
+      *h = z;
+    }
+    return T(0);
+  }
+  V3<T> vrel = v3<T>(-v.x, -v.y, T(vw) - v.z);
+  V3<T> rw = v3<T>(R * w.x, R * w.y, R * w.z);
+  V3<T> rwn = cross3(rw, n);
+  V3<T> vc = v3<T>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
+  V3<T> Fi, Ft;
+  contact_law<T>(T(delta), n, vrel, vc, R, m, T(0), false, Es, Gs, beta, mu, dt, s.coulomb_mode,
+                 hist, Fi, Ft);
+  H hn;
+  hn.x = hist.x; hn.y = hist.y; hn.z = hist.z; hn.w = 0;
+  *h = hn;
+  V3<T> nFt = cross3(n, Ft);
+  F.x += Fi.x;
+  F.y += Fi.y;
+  F.z += Fi.z;
+  Tq.x += R * nFt.x;
+  Tq.y += R * nFt.y;
+  Tq.z += R * nFt.z;
+  return Fi.z;
+}
+
+// The penetrometer's contact, out of line: only the few spheres near an
+// active tool take it, and inline it would cost every sphere registers.
+template <typename T, typename H>
+__device__ __noinline__ void tool_contact(const SampleDev& s, StageDev* W, double4 P, double r, V3<T> v,
+                                          V3<T> w, T R, T m, T Es, T Gs, T beta, T mu, T dt, H* h,
+                                          V3<T>* F, V3<T>* Tq) {
+  double nd[3];
+  const double delta = tool_overlap(P.x, P.y, P.z, fabs(P.w), r, W->pen_radius, W->pen_z, nd);
+  V3<T> Fl = *F, Tl = *Tq;
+  const T fz = wall_hertz<T, H>(delta, v3<T>(T(nd[0]), T(nd[1]), T(nd[2])),
+                                (double)W->pen_dir * W->pen_speed, s, v, w, R, m, Es, Gs, beta, mu, dt,
+                                h, Fl, Tl);
+  *F = Fl;
+  *Tq = Tl;
+  if (delta > 0.0)  // the sphere pushes the tool with -F
+    atomicAdd(&W->pen_q, (unsigned long long)__double2ll_rn(-(double)fz * 1099511627776.0));
+}
+
 // Wall contacts of the cylinder (Sec. 3.1: Hertz particle-wall law): the
 // side, the bottom (open over the outlet), the top plate and the
 // penetrometer of a preparation stage, the last two moving along z (their
@@ -358,29 +414,27 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
   const float Rf = (float)R;
   const float rf = sqrtf(xf * xf + yf * yf);
   const float near = -0.05f * Rf;
-  const int pen_dir = W.pen_dir;
-  float dtool = -1e30f;
-  if (pen_dir != 0) {
+  const double Hw = W.H;
+  float dw[3] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f, zf + Rf - (float)Hw};
+  bool tool = false;
+  if (W.pen_dir != 0) {
     const float rp = (float)W.pen_radius, zt = (float)W.pen_z;
+    float dtool;
     if (zf >= zt) dtool = Rf - (rf - rp);
     else if (rf <= rp) dtool = Rf - (zt - zf);
     else dtool = Rf - sqrtf((rf - rp) * (rf - rp) + (zt - zf) * (zt - zf));
+    tool = dtool > near;
   }
-  const double Hw = W.H;
-  const float dw[CGDEM_WALLS] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f,
-                                 zf + Rf - (float)Hw, dtool};
   // most spheres are far from every wall: leave before any FP64 work (the
   // compiler would otherwise hoist the loop-invariant radius and its square
   // root out of the wall loop and run them for every sphere)
-  if (!(dw[0] > near) && !(dw[1] > near) && !(dw[2] > near) && !(dw[3] > near)) return;
-  for (int wall = 0; wall < CGDEM_WALLS; ++wall) {
+  if (!(dw[0] > near) && !(dw[1] > near) && !(dw[2] > near) && !tool) return;
+  const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
+  for (int wall = 0; wall < 3; ++wall) {
     if (!(dw[wall] > near)) continue;
-    const H h = hist_base[(size_t)wall * stride];
-    V3<T> hist = v3<T>(h.x, h.y, h.z);
     double delta = -1.0;
     double vw = 0.0;  // the wall's velocity along z
     V3<T> n = v3<T>(0, 0, 0);
-    const double r2 = __dadd_rn(__dmul_rn(P.x, P.x), __dmul_rn(P.y, P.y));
     if (wall == 0) {
       if (r2 > 0.0) {
         const double r = sqrt(r2);
@@ -392,46 +446,18 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
         delta = fabs(P.w) - P.z;
         n = v3<T>(0, 0, -1);
       }
-    } else if (wall == 2) {
+    } else {
       delta = (P.z + fabs(P.w)) - Hw;
       n = v3<T>(0, 0, 1);
       vw = W.v_plate;
-    } else {
-      double nd[3];
-      delta = tool_overlap(P.x, P.y, P.z, fabs(P.w), sqrt(r2), W.pen_radius, W.pen_z, nd);
-      n = v3<T>(T(nd[0]), T(nd[1]), T(nd[2]));
-      vw = (double)pen_dir * W.pen_speed;
     }
-    if (!(delta > 0.0)) {
-      if (hist.x != T(0) || hist.y != T(0) || hist.z != T(0)) {
-        H z;
-        z.x = 0; z.y = 0; z.z = 0; z.w = 0;
-        hist_base[(size_t)wall * stride] = z;
-      }
-      continue;
-    }
-    V3<T> vrel = v3<T>(-v.x, -v.y, T(vw) - v.z);
-    V3<T> rw = v3<T>(R * w.x, R * w.y, R * w.z);
-    V3<T> rwn = cross3(rw, n);
-    V3<T> vc = v3<T>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
-    V3<T> Fi, Ft;
-    contact_law<T>(T(delta), n, vrel, vc, R, m, T(0), false, Es, Gs, beta, mu, dt, s.coulomb_mode,
-                   hist, Fi, Ft);
-    H hn;
-    hn.x = hist.x; hn.y = hist.y; hn.z = hist.z; hn.w = 0;
-    hist_base[(size_t)wall * stride] = hn;
-    if (wall >= 2) {  // the sphere pushes the plate or the tool with -F
-      const long long qz = __double2ll_rn(-(double)Fi.z * 1099511627776.0);
-      atomicAdd(wall == 2 ? &W.plate_q : &W.pen_q, (unsigned long long)qz);
-    }
-    V3<T> nFt = cross3(n, Ft);
-    F.x += Fi.x;
-    F.y += Fi.y;
-    F.z += Fi.z;
-    Tq.x += R * nFt.x;
-    Tq.y += R * nFt.y;
-    Tq.z += R * nFt.z;
+    const T fz = wall_hertz<T, H>(delta, n, vw, s, v, w, R, m, Es, Gs, beta, mu, dt,
+                                  hist_base + (size_t)wall * stride, F, Tq);
+    if (wall == 2 && delta > 0.0)  // the sphere pushes the plate with -F
+      atomicAdd(&W.plate_q, (unsigned long long)__double2ll_rn(-(double)fz * 1099511627776.0));
   }
+  if (tool)
+    tool_contact<T, H>(s, &W, P, sqrt(r2), v, w, R, m, Es, Gs, beta, mu, dt, hist_base + 3 * stride, &F, &Tq);
 }
 
 // Fluid cell of a position with a float pre-check: the FP64 evaluation of

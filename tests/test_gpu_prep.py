@@ -121,9 +121,12 @@ def test_plate_compression_follows_the_oracle(prec):
 def test_penetrometer_follows_the_oracle(prec):
     s = small_cylinder()
     ctx, sim, skin = contexts(s, prec, 0, bond=True)
-    top = bed_top(s)
-    rp = 0.25 * s.domain["Rc"]
-    kw = dict(jkr_mode=0, pen_mode=1, pen_radius=rp, pen_speed=2.0, pen_z_start=top + 1e-6,
+    # a tool wider than the cavity over the outlet, starting just above the
+    # highest grain under it
+    rp = 0.4 * s.domain["Rc"]
+    under = np.hypot(s.x[:, 0], s.x[:, 1]) < rp + s.R
+    top = float((s.x[under, 2] + s.R[under]).max())
+    kw = dict(jkr_mode=0, pen_mode=1, pen_radius=rp, pen_speed=5.0, pen_z_start=top + 1e-6,
               pen_z_stop=0.5 * top)
     ctx.set_stage(0, cgdem.stage(**kw))
     sim.set_stage(O.make_stage(**kw))
