@@ -126,7 +126,7 @@ def test_penetrometer_follows_the_oracle(prec):
     rp = 0.4 * s.domain["Rc"]
     under = np.hypot(s.x[:, 0], s.x[:, 1]) < rp + s.R
     top = float((s.x[under, 2] + s.R[under]).max())
-    kw = dict(jkr_mode=0, pen_mode=1, pen_radius=rp, pen_speed=5.0, pen_z_start=top + 1e-6,
+    kw = dict(jkr_mode=0, pen_mode=1, pen_radius=rp, pen_speed=0.5, pen_z_start=top + 1e-6,
               pen_z_stop=0.5 * top)
     ctx.set_stage(0, cgdem.stage(**kw))
     sim.set_stage(O.make_stage(**kw))
