@@ -305,8 +305,11 @@ int cgdem_get_fluid(cgdem_ctx* ctx, double* p, double* U, double* gradp, int64_t
  * next step (the boundaries move from the next drift on; a new penetrometer
  * starts without spring history).  CGDEM_E_INVALID for a periodic sample
  * with moving boundaries, a plate above the sample's H, non-positive speeds
- * or radii where a boundary moves, or jkr_mode 1 with a skin below
- * 2 |delta_S| of the largest pair.  Synchronises stream. */
+ * or radii where a boundary moves, jkr_mode 1 with a skin below 2 |delta_S|
+ * of the largest pair, or a context with the learned closure (nor may such
+ * a context be created with jkr_mode 1).  The first call switches the
+ * context's force kernels to the ones that run the stages (a few per cent
+ * slower).  Synchronises stream. */
 int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stage, void* stream);
 
 /* Per sample, 6 doubles (HOST, out[6 * n_samples]): the top plate's height

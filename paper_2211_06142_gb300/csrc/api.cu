@@ -304,6 +304,9 @@ int layout(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_params* s
     return fail(ctx, CGDEM_E_INVALID, "particles_per_warp must be 0, 16 or 32");
   if (cfg->fluid_kernels != 0 && cfg->fluid_kernels != 1)
     return fail(ctx, CGDEM_E_INVALID, "fluid_kernels must be 0 or 1");
+  for (int k = 0; k < cfg->n_samples; ++k)
+    if (cfg->closure && sp[k].jkr_mode == 1)
+      return fail(ctx, CGDEM_E_INVALID, "the original JKR runs in contexts without the learned closure");
   if (cfg->closure && cfg->block_size != 128 && cfg->block_size > 0)
     return fail(ctx, CGDEM_E_INVALID, "a context with the learned closure runs blocks of 128 threads");
   const int S = cfg->n_samples;
@@ -842,6 +845,7 @@ int cgdem_create(const cgdem_config* cfg, const cgdem_sample_params* sp, const i
     cudaMemset(ctx->d.react[1], 0, sizeof(unsigned long long) * 3 * nc);
     ctx->d.fl_coop_blocks = cfg->fluid_kernels == 1 ? 0 : fluid_coop_blocks(ctx->d.Cf_total);
   }
+  for (const auto& q : ctx->sd) ctx->d.prep |= q.jkr_mode == 1 ? 1 : 0;
   {  // preparation stages: the top plate at the sample's H, no penetrometer
     std::vector<StageDev> st(ctx->sd.size());
     for (size_t k = 0; k < st.size(); ++k) {
@@ -1227,6 +1231,7 @@ int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stg, void* st
   const cgdem_sample_params& p = ctx->sp[sample];
   SampleDev& S = ctx->sd[sample];
   if (stg->jkr_mode != 0 && stg->jkr_mode != 1) return fail(ctx, CGDEM_E_INVALID, "jkr_mode must be 0 or 1");
+  if (ctx->d.clblob) return fail(ctx, CGDEM_E_INVALID, "preparation stages run in contexts without the learned closure");
   if (!(2.0 * jkr_reach(S.gamma, S.Es, 0.5 * p.r_max, stg->jkr_mode) < p.skin))
     return fail(ctx, CGDEM_E_INVALID, "skin %.3g must exceed twice the separation of the contact model",
                 p.skin);
@@ -1263,6 +1268,10 @@ int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stg, void* st
   if (S.kind == CGDEM_CYLINDER) launch_clear_wall_history(ctx->d, sample, 3, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  if (!ctx->d.prep) {  // from now on the force kernels that run the stages (graphs recaptured)
+    ctx->d.prep = 1;
+    drop_graphs(ctx);
+  }
   return CGDEM_OK;
 }
 

@@ -225,6 +225,7 @@ struct Dev {
   double* fl_p;                   // dynamic pressure (kept: the next solve starts from it)
   double *fl_r, *fl_z, *fl_d, *fl_q, *fl_M, *fl_b;  // conjugate-gradient vectors, diagonal, right-hand side
   StageDev* stage;                // per sample: moving boundaries of the preparation stages
+  int prep;                       // 1: the force kernels that run the preparation stages
   double* fl_d2;                  // the one-launch solve's second direction buffer
   double4* fl_T;                  // its face conductances per cell: upper x, y, z faces, outlet face
   double* fl_part;                // per-block partial sums [4][fl_blocks]

@@ -196,10 +196,9 @@ __device__ __forceinline__ void contact_law(T delta, V3<T> n, V3<T> vrel, V3<T> 
 __device__ __forceinline__ void contact_law_mixed(float delta, V3<float> n, V3<float> vrel, V3<float> vc,
                                                   float Rs, float ms, float gamma, bool bonded, float dA,
                                                   const SampleDev& S, V3<float>& xi, V3<float>& Fi,
-                                                  V3<float>& Ft) {
+                                                  V3<float>& Ft, bool orig) {
   float a, Fne;
   if (bonded && gamma > 0.f) {
-    const bool orig = S.jkr_mode == 1;
     const float D = __fdividef(delta, dA);
     float u = (orig && D < -0.22714007410401746f) ? jkr_start<float>(D, true) : m_sqrt(m_sqrt(D + 1.f));
 #pragma unroll
@@ -406,7 +405,7 @@ __device__ __noinline__ void tool_contact(const SampleDev& s, StageDev* W, doubl
 // every wall with a non-zero history is among them (and gets its history
 // cleared when the contact ends).  The forces the sphere exerts on the plate
 // and the penetrometer along z are summed in integer quanta of 2^-40 N.
-template <typename T, typename H>
+template <typename T, typename H, bool PREP>
 __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, double4 P, float xf,
                                               float yf, float zf, V3<T> v, V3<T> w, T R, T m, T Es, T Gs,
                                               T beta, T mu, T dt, H* hist_base, size_t stride,
@@ -414,10 +413,11 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
   const float Rf = (float)R;
   const float rf = sqrtf(xf * xf + yf * yf);
   const float near = -0.05f * Rf;
-  const double Hw = W.H;
-  float dw[3] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f, zf + Rf - (float)Hw};
+  const double Hw = PREP ? W.H : s.H;
+  float dw[3] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f,
+                 zf + Rf - (PREP ? (float)Hw : s.H_f)};
   bool tool = false;
-  if (W.pen_dir != 0) {
+  if (PREP && W.pen_dir != 0) {
     const float rp = (float)W.pen_radius, zt = (float)W.pen_z;
     float dtool;
     if (zf >= zt) dtool = Rf - (rf - rp);
@@ -449,14 +449,14 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
     } else {
       delta = (P.z + fabs(P.w)) - Hw;
       n = v3<T>(0, 0, 1);
-      vw = W.v_plate;
+      if (PREP) vw = W.v_plate;
     }
     const T fz = wall_hertz<T, H>(delta, n, vw, s, v, w, R, m, Es, Gs, beta, mu, dt,
                                   hist_base + (size_t)wall * stride, F, Tq);
-    if (wall == 2 && delta > 0.0)  // the sphere pushes the plate with -F
+    if (PREP && wall == 2 && delta > 0.0)  // the sphere pushes the plate with -F
       atomicAdd(&W.plate_q, (unsigned long long)__double2ll_rn(-(double)fz * 1099511627776.0));
   }
-  if (tool)
+  if (PREP && tool)
     tool_contact<T, H>(s, &W, P, sqrt(r2), v, w, R, m, Es, Gs, beta, mu, dt, hist_base + 3 * stride, &F, &Tq);
 }
 
@@ -581,7 +581,7 @@ struct Owner<false> {
 // the rebuild, porosity rotation, step counter, next rebuild condition).
 // valid: this thread owns sphere p (of sample si) and ends its step; F, Tq
 // and the closure sums hold its contact forces.
-template <bool MIXED, int MODE, bool CL>
+template <bool MIXED, int MODE, bool CL, bool PREP>
 __device__ __forceinline__ void finish_step(
     const Dev& d, Ctl* ctl, int cur, int nxt, int pc, int vfc, long long m_step, bool couple_next,
     uint32_t epoch, int lane, bool valid, int p, int si, const Owner<MIXED>& me,
@@ -657,10 +657,10 @@ __device__ __forceinline__ void finish_step(
       }
       if (S.kind == CGDEM_CYLINDER) {
         if constexpr (MIXED)
-          wall_contacts<T, float4>(S, d.stage[si], P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+          wall_contacts<T, float4, PREP>(S, d.stage[si], P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
                                    d.wallhf[pc] + p, (size_t)d.Npad, F, Tq);
         else
-          wall_contacts<T, double4>(S, d.stage[si], P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
+          wall_contacts<T, double4, PREP>(S, d.stage[si], P, xf, yf, zf, vi, wi, Ri, mi, Es, Gs, beta, mu, dt,
                                     d.wallh[pc] + p, (size_t)d.Npad, F, Tq);
       }
       // gravity, buoyancy (Eq. 1) and drag (Eq. 8-11)
@@ -974,7 +974,7 @@ __device__ __forceinline__ void finish_step(
       }
       // the moving boundaries: this evaluation's forces on them, the plate's
       // next velocity, and (a step that drifts the grains) their drift
-      for (int s = 0; s < d.n_samples; ++s) {
+      for (int s = 0; PREP && s < d.n_samples; ++s) {
         if (d.sp[s].kind != CGDEM_CYLINDER) continue;
         close_boundaries(d.stage[s], d.sp[s].Rc);
         if (MODE == MODE_MID) drift_boundaries(d.stage[s], d.sp[s].dt);
@@ -1002,7 +1002,7 @@ __device__ __forceinline__ void finish_step(
 // h_next: conditional handle of the next step's rebuild node when the launch
 // sits in a CUDA graph (0 otherwise); h_fluid: that of the step's Darcy-solve
 // node (0: none); the step's last warp sets both.
-template <int MODE, bool CL>
+template <int MODE, bool CL, bool PREP>
 __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
     k_forces_pairs(Dev d, cudaGraphConditionalHandle h_next,
     cudaGraphConditionalHandle h_fluid) {
@@ -1161,7 +1161,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
           const double delta = __dsub_rn(Sd, dist);
           double gam_d = S.gamma;  // gamma sqrt(c_g,i c_g,j) under the closure
-          const bool orig_mode = S.jkr_mode == 1;
+          const bool orig_mode = PREP && S.jkr_mode == 1;
           if (use_c && (bonded || orig_mode)) gam_d = S.gamma * sqrt((double)o_cg * (double)d.clc[cur][q].y);
           const bool orig = orig_mode && gam_d > 0.0;
           if (bonded) {  // modified JKR: break at C for good; original JKR: separation at S
@@ -1349,7 +1349,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
     }
   }
 
-  finish_step<false, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
+  finish_step<false, MODE, CL, PREP>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
                                F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
                                &bk_n, bk_s, bk_m, bk_c, h_next, h_fluid);
 }
@@ -1367,7 +1367,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
 // sphere's pairs in list order: no search for the owner of an entry, no
 // broadcast of its data and no segmented scan, and the sums stay
 // deterministic.
-template <int MODE, bool CL>
+template <int MODE, bool CL, bool PREP>
 __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
     k_forces_lanes(Dev d, cudaGraphConditionalHandle h_next,
     cudaGraphConditionalHandle h_fluid) {
@@ -1536,7 +1536,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
         // surface energy of the pair: gamma sqrt(c_g,i c_g,j) under the closure
         float gam_f = S.gamma_f;
         double gam_d = S.gamma;
-        const bool orig_mode = S.jkr_mode == 1;
+        const bool orig_mode = PREP && S.jkr_mode == 1;
         if (use_c && (bonded || orig_mode)) {
           const float qcg = d.clc[cur][q].y;
           gam_f = S.gamma_f * sqrtf(my_c.y * qcg);
@@ -1589,7 +1589,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
           const V3<float> vc = v3<float>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
           V3<float> Fi, Ft;
           contact_law_mixed(delta, nrm, vrel, vc, Rs, ms, gam_f, bonded, 2.5198420997897464f * xs, S, xi,
-                            Fi, Ft);  // d_A = 16^(1/3) xs
+                            Fi, Ft, orig);  // d_A = 16^(1/3) xs
           const V3<float> nFt = cross3(nrm, Ft);
           F.x += Fi.x;
           F.y += Fi.y;
@@ -1626,7 +1626,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
       Cacc += __shfl_down_sync(FULL, Cacc, 16);
     }
   }
-  finish_step<true, MODE, CL>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
+  finish_step<true, MODE, CL, PREP>(d, ctl, cur, nxt, pc, vfc, m_step, couple_next, epoch, lane, valid, p, si, me,
                               F, Tq, Zacc, Dacc, Cacc, my_c, use_c, feat, rec, net, cl_sm, cl_bar, cl_tmem,
                               &bk_n, bk_s, bk_m, bk_c, h_next, h_fluid);
 }
@@ -1652,24 +1652,34 @@ void launch_forces(const Dev& d, int mode, int block, cudaStream_t s, cudaGraphC
   const int grid = d.Npad * (32 / d.ppw) / B;
   const size_t sm = (cl && d.cl_smem) ? CL_SMEM : 0;
   if (d.N == 0) return;
+  // PREP: the kernels that also run the preparation stages (original JKR,
+  // moving plate and penetrometer), once a context has used them
   if (cl) {
     if (d.mixed) {
-      if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0, 0);
-      else if (mode == MODE_MID) k_forces_lanes<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next, h_fluid);
-      else k_forces_lanes<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0, 0);
+      if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, true, false><<<grid, B, sm, s>>>(d, 0, 0);
+      else if (mode == MODE_MID) k_forces_lanes<MODE_MID, true, false><<<grid, B, sm, s>>>(d, h_next, h_fluid);
+      else k_forces_lanes<MODE_CANON, true, false><<<grid, B, sm, s>>>(d, 0, 0);
     } else {
-      if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, true><<<grid, B, sm, s>>>(d, 0, 0);
-      else if (mode == MODE_MID) k_forces_pairs<MODE_MID, true><<<grid, B, sm, s>>>(d, h_next, h_fluid);
-      else k_forces_pairs<MODE_CANON, true><<<grid, B, sm, s>>>(d, 0, 0);
+      if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, true, false><<<grid, B, sm, s>>>(d, 0, 0);
+      else if (mode == MODE_MID) k_forces_pairs<MODE_MID, true, false><<<grid, B, sm, s>>>(d, h_next, h_fluid);
+      else k_forces_pairs<MODE_CANON, true, false><<<grid, B, sm, s>>>(d, 0, 0);
     }
+  } else if (d.mixed && d.prep) {
+    if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false, true><<<grid, B, 0, s>>>(d, 0, 0);
+    else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false, true><<<grid, B, 0, s>>>(d, h_next, h_fluid);
+    else k_forces_lanes<MODE_CANON, false, true><<<grid, B, 0, s>>>(d, 0, 0);
   } else if (d.mixed) {
-    if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0, 0);
-    else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next, h_fluid);
-    else k_forces_lanes<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0, 0);
+    if (mode == MODE_FORCES) k_forces_lanes<MODE_FORCES, false, false><<<grid, B, 0, s>>>(d, 0, 0);
+    else if (mode == MODE_MID) k_forces_lanes<MODE_MID, false, false><<<grid, B, 0, s>>>(d, h_next, h_fluid);
+    else k_forces_lanes<MODE_CANON, false, false><<<grid, B, 0, s>>>(d, 0, 0);
+  } else if (d.prep) {
+    if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, false, true><<<grid, B, 0, s>>>(d, 0, 0);
+    else if (mode == MODE_MID) k_forces_pairs<MODE_MID, false, true><<<grid, B, 0, s>>>(d, h_next, h_fluid);
+    else k_forces_pairs<MODE_CANON, false, true><<<grid, B, 0, s>>>(d, 0, 0);
   } else {
-    if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, false><<<grid, B, 0, s>>>(d, 0, 0);
-    else if (mode == MODE_MID) k_forces_pairs<MODE_MID, false><<<grid, B, 0, s>>>(d, h_next, h_fluid);
-    else k_forces_pairs<MODE_CANON, false><<<grid, B, 0, s>>>(d, 0, 0);
+    if (mode == MODE_FORCES) k_forces_pairs<MODE_FORCES, false, false><<<grid, B, 0, s>>>(d, 0, 0);
+    else if (mode == MODE_MID) k_forces_pairs<MODE_MID, false, false><<<grid, B, 0, s>>>(d, h_next, h_fluid);
+    else k_forces_pairs<MODE_CANON, false, false><<<grid, B, 0, s>>>(d, 0, 0);
   }
   if (mode == MODE_CANON) k_after_canon<<<1, 1, 0, s>>>(d);
 }
