@@ -500,7 +500,7 @@ struct ora_sim {
        and their sums */
     ora_stage stage;
     double H_cur, v_plate;
-    double pen_z;
+    double pen_z, v_pen;
     int pen_dir;
     int64_t *plate_qp, *pen_qp;
     int64_t plate_q, pen_q;
@@ -844,7 +844,7 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
                 n[1] = x[1] / r;
             }
         } else if (wall == 1) { /* bottom plane z = 0, open over the outlet r < r_out */
-            if (r >= p->r_out) {
+            if (s->stage.outlet_closed || r >= p->r_out) {
                 delta = R - x[2];
                 n[2] = -1.0;
             }
@@ -854,7 +854,7 @@ static void wall_forces(ora_sim* s, int64_t i, double Fi[3], double Ti[3]) {
             vw = s->v_plate;
         } else if (s->pen_dir != 0) { /* penetrometer */
             delta = tool_contact(x, R, s->stage.pen_radius, s->pen_z, n);
-            vw = s->pen_dir * s->stage.pen_speed;
+            vw = s->v_pen;
         }
         double* h = &s->wall_xi[12 * i + 3 * wall];
         if (!(delta > 0.0)) {
@@ -1047,6 +1047,19 @@ int ora_compute_forces(ora_sim* s) {
         }
         s->plate_q = pq;
         s->pen_q = tq;
+        /* the penetrometer's next velocity: up at its speed, down at its
+           speed reduced by the grains' push against the driving force */
+        if (s->pen_dir > 0) {
+            s->v_pen = s->stage.pen_speed;
+        } else if (s->pen_dir < 0) {
+            double f = 1.0;
+            if (s->stage.pen_force > 0.0) {
+                f = 1.0 - (double)tq * ORA_TWO_M40 / s->stage.pen_force;
+                if (f < 0.0) f = 0.0;
+                if (f > 1.0) f = 1.0;
+            }
+            s->v_pen = -s->stage.pen_speed * f;
+        }
         if (s->stage.plate_mode == 1) {
             double stress = (double)pq * ORA_TWO_M40 / (M_PI * p->Rc * p->Rc);
             double v = s->stage.plate_gain * (stress - s->stage.plate_stress);
@@ -1318,14 +1331,14 @@ int ora_set_forces(ora_sim* s, const double* F, const double* T) {
     return 0;
 }
 
-/* The boundaries move with the particles' drift: the plate at the velocity
- * of the last force evaluation, the penetrometer at its speed, turning back
- * at pen_z_stop and removed back at pen_z_start. */
+/* The boundaries move with the particles' drift at the velocities of the
+ * last force evaluation: the penetrometer turns back at pen_z_stop and is
+ * removed back at pen_z_start. */
 static void drift_boundaries(ora_sim* s) {
     const double dt = s->p.dt;
     if (s->stage.plate_mode == 1) s->H_cur += dt * s->v_plate;
     if (s->pen_dir != 0) {
-        s->pen_z += dt * ((double)s->pen_dir * s->stage.pen_speed);
+        s->pen_z += dt * s->v_pen;
         if (s->pen_dir < 0 && s->pen_z <= s->stage.pen_z_stop) s->pen_dir = 1;
         else if (s->pen_dir > 0 && s->pen_z >= s->stage.pen_z_start) s->pen_dir = 0;
     }
@@ -1335,12 +1348,19 @@ int ora_set_stage(ora_sim* s, const ora_stage* st) {
     if (!s || !st) return -1;
     if (st->jkr_mode != 0 && st->jkr_mode != 1) return -1;
     if (s->p.kind != 1 && (st->plate_mode != 0 || st->pen_mode != 0)) return -1;
+    if (st->pen_mode == 2 && s->pen_dir == 0) return -1; /* no tool to pull back */
     s->stage = *st;
     s->p.jkr_mode = st->jkr_mode;
     if (st->plate_H > 0.0) s->H_cur = st->plate_H;
     if (st->plate_mode != 1) s->v_plate = 0.0;
+    if (st->pen_mode == 2) { /* the tool goes back up from where it is */
+        s->pen_dir = 1;
+        s->v_pen = st->pen_speed;
+        return 0;
+    }
     s->pen_dir = st->pen_mode == 1 ? -1 : 0;
     s->pen_z = st->pen_z_start;
+    s->v_pen = st->pen_mode == 1 ? -st->pen_speed : 0.0;
     for (int64_t i = 0; i < s->n; ++i) { /* a new tool starts without spring history */
         double* h = &s->wall_xi[12 * i + 9];
         h[0] = h[1] = h[2] = 0.0;

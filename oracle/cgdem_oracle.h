@@ -83,8 +83,17 @@ typedef struct {
                              starts with its tip at pen_z_start, moves down at
                              pen_speed until the tip reaches pen_z_stop, then up
                              at the same speed until the tip is back at
-                             pen_z_start, where it is removed; 0: none */
+                             pen_z_start, where it is removed; 2: the tool in
+                             place goes back up from where it is (to pen_z_start);
+                             0: none */
     double pen_radius, pen_speed, pen_z_start, pen_z_stop;
+    double pen_force;     /* > 0: the driving force of the descent (Sec. 3.1: a
+                             constant moving force): after each force evaluation
+                             the descent's speed becomes pen_speed (1 - F / pen_force),
+                             clamped to [0, pen_speed], F the force of the grains
+                             on the tool along z; 0: always pen_speed */
+    int outlet_closed;    /* 1: the bottom plane is closed over the outlet too
+                             (the stages before the sand production) */
 } ora_stage;
 
 /* ---- closed forms and single-contact laws (pins and unit tests) ---- */

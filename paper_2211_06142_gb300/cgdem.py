@@ -49,7 +49,8 @@ class Stage(C.Structure):
         ("plate_mode", C.c_int), ("plate_H", C.c_double), ("plate_stress", C.c_double),
         ("plate_gain", C.c_double), ("plate_vmax", C.c_double),
         ("pen_mode", C.c_int), ("pen_radius", C.c_double), ("pen_speed", C.c_double),
-        ("pen_z_start", C.c_double), ("pen_z_stop", C.c_double),
+        ("pen_z_start", C.c_double), ("pen_z_stop", C.c_double), ("pen_force", C.c_double),
+        ("outlet_closed", C.c_int),
     ]
 
 

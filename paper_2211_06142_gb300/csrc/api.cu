@@ -1237,12 +1237,13 @@ int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stg, void* st
                 p.skin);
   if ((stg->plate_mode != 0 || stg->pen_mode != 0) && S.kind != CGDEM_CYLINDER)
     return fail(ctx, CGDEM_E_INVALID, "moving boundaries need a cylinder sample");
-  if ((stg->plate_mode != 0 && stg->plate_mode != 1) || (stg->pen_mode != 0 && stg->pen_mode != 1))
-    return fail(ctx, CGDEM_E_INVALID, "plate_mode and pen_mode must be 0 or 1");
+  if ((stg->plate_mode != 0 && stg->plate_mode != 1) || stg->pen_mode < 0 || stg->pen_mode > 2)
+    return fail(ctx, CGDEM_E_INVALID, "plate_mode must be 0 or 1, pen_mode 0, 1 or 2");
   if (stg->plate_H > S.H) return fail(ctx, CGDEM_E_INVALID, "plate_H above the sample's H");
   if (stg->plate_mode == 1 && !(stg->plate_gain > 0 && stg->plate_vmax > 0 && std::isfinite(stg->plate_stress)))
     return fail(ctx, CGDEM_E_INVALID, "a moving plate needs plate_gain > 0, plate_vmax > 0, a finite stress");
-  if (stg->pen_mode == 1 && !(stg->pen_radius > 0 && stg->pen_speed > 0 && stg->pen_z_stop < stg->pen_z_start))
+  if (stg->pen_mode != 0 && !(stg->pen_radius > 0 && stg->pen_speed > 0 && stg->pen_z_stop < stg->pen_z_start &&
+                              stg->pen_force >= 0))
     return fail(ctx, CGDEM_E_INVALID, "a penetrometer needs pen_radius > 0, pen_speed > 0, pen_z_stop < pen_z_start");
   cudaStream_t s = st(stream);
   StageDev W;
@@ -1254,18 +1255,27 @@ int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stg, void* st
   W.plate_vmax = stg->plate_vmax;
   if (stg->plate_H > 0) W.H = stg->plate_H;
   if (stg->plate_mode != 1) W.v_plate = 0.0;
+  if (stg->pen_mode == 2 && W.pen_dir == 0) return fail(ctx, CGDEM_E_INVALID, "no penetrometer to pull back");
   W.pen_radius = stg->pen_radius;
   W.pen_speed = stg->pen_speed;
   W.pen_z_start = stg->pen_z_start;
   W.pen_z_stop = stg->pen_z_stop;
-  W.pen_z = stg->pen_z_start;
-  W.pen_dir = stg->pen_mode == 1 ? -1 : 0;
+  W.pen_force = stg->pen_force;
+  if (stg->pen_mode == 2) {  // the tool goes back up from where it is
+    W.pen_dir = 1;
+    W.v_pen = stg->pen_speed;
+  } else {
+    W.pen_z = stg->pen_z_start;
+    W.pen_dir = stg->pen_mode == 1 ? -1 : 0;
+    W.v_pen = stg->pen_mode == 1 ? -stg->pen_speed : 0.0;
+  }
+  W.outlet_closed = stg->outlet_closed ? 1 : 0;
   CK(cudaMemcpyAsync(ctx->d.stage + sample, &W, sizeof W, cudaMemcpyHostToDevice, s));
   S.jkr_mode = stg->jkr_mode;
   ctx->sp[sample].jkr_mode = stg->jkr_mode;
   CK(cudaMemcpyAsync(&ctx->d.sp[sample].jkr_mode, &S.jkr_mode, sizeof(int), cudaMemcpyHostToDevice, s));
   // a new penetrometer starts without spring history
-  if (S.kind == CGDEM_CYLINDER) launch_clear_wall_history(ctx->d, sample, 3, s);
+  if (S.kind == CGDEM_CYLINDER && stg->pen_mode != 2) launch_clear_wall_history(ctx->d, sample, 3, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   if (!ctx->d.prep) {  // from now on the force kernels that run the stages (graphs recaptured)

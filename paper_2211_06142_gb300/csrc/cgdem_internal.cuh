@@ -101,9 +101,10 @@ struct SampleDev {
 struct StageDev {
   int plate_mode;
   int pen_dir;  // -1 down, +1 up, 0 no penetrometer
+  int outlet_closed;
   double plate_stress, plate_gain, plate_vmax;
-  double pen_radius, pen_speed, pen_z_start, pen_z_stop;
-  double H, v_plate, pen_z;
+  double pen_radius, pen_speed, pen_z_start, pen_z_stop, pen_force;
+  double H, v_plate, pen_z, v_pen;
   unsigned long long plate_q, pen_q;  // running sums (two's complement)
   long long plate_q_last, pen_q_last;
 };
@@ -374,13 +375,13 @@ __device__ __forceinline__ bool bond_breaks_exact(double delta, double Rs, doubl
   return lhs < rhs;
 }
 
-// The moving boundaries follow the grains' drift: the top plate at the
-// velocity of the last force evaluation, the penetrometer at its speed,
-// turning back at pen_z_stop and removed back at pen_z_start.
+// The moving boundaries follow the grains' drift at the velocities of the
+// last force evaluation: the penetrometer turns back at pen_z_stop and is
+// removed back at pen_z_start.
 __device__ __forceinline__ void drift_boundaries(StageDev& W, double dt) {
   if (W.plate_mode == 1) W.H = __dadd_rn(W.H, __dmul_rn(dt, W.v_plate));
   if (W.pen_dir != 0) {
-    W.pen_z = __dadd_rn(W.pen_z, __dmul_rn(dt, __dmul_rn((double)W.pen_dir, W.pen_speed)));
+    W.pen_z = __dadd_rn(W.pen_z, __dmul_rn(dt, W.v_pen));
     if (W.pen_dir < 0 && W.pen_z <= W.pen_z_stop) W.pen_dir = 1;
     else if (W.pen_dir > 0 && W.pen_z >= W.pen_z_start) W.pen_dir = 0;
   }
@@ -388,12 +389,26 @@ __device__ __forceinline__ void drift_boundaries(StageDev& W, double dt) {
 
 // After a force evaluation: the sums of the forces on the plate and the
 // penetrometer become the evaluation's (the running sums restart at zero),
-// and a stress-controlled plate takes its velocity for the next drift.
+// and the penetrometer and a stress-controlled plate take their velocities
+// for the next drift.
 __device__ __forceinline__ void close_boundaries(StageDev& W, double Rc) {
   const long long pq = (long long)atomicExch(&W.plate_q, 0ull);
   const long long tq = (long long)atomicExch(&W.pen_q, 0ull);
   W.plate_q_last = pq;
   W.pen_q_last = tq;
+  // the penetrometer's next velocity: up at its speed, down at its speed
+  // reduced by the grains' push against the driving force
+  if (W.pen_dir > 0) {
+    W.v_pen = W.pen_speed;
+  } else if (W.pen_dir < 0) {
+    double f = 1.0;
+    if (W.pen_force > 0.0) {
+      f = __dsub_rn(1.0, __ddiv_rn(__dmul_rn((double)tq, 9.094947017729282379150390625e-13), W.pen_force));
+      if (f < 0.0) f = 0.0;
+      if (f > 1.0) f = 1.0;
+    }
+    W.v_pen = __dmul_rn(-W.pen_speed, f);
+  }
   if (W.plate_mode == 1) {
     const double stress = __ddiv_rn(__dmul_rn((double)pq, 9.094947017729282379150390625e-13),
                                     __dmul_rn(__dmul_rn(3.14159265358979323846, Rc), Rc));

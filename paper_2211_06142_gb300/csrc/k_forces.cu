@@ -387,7 +387,7 @@ __device__ __noinline__ void tool_contact(const SampleDev& s, StageDev* W, doubl
   const double delta = tool_overlap(P.x, P.y, P.z, fabs(P.w), r, W->pen_radius, W->pen_z, nd);
   V3<T> Fl = *F, Tl = *Tq;
   const T fz = wall_hertz<T, H>(delta, v3<T>(T(nd[0]), T(nd[1]), T(nd[2])),
-                                (double)W->pen_dir * W->pen_speed, s, v, w, R, m, Es, Gs, beta, mu, dt,
+                                W->v_pen, s, v, w, R, m, Es, Gs, beta, mu, dt,
                                 h, Fl, Tl);
   *F = Fl;
   *Tq = Tl;
@@ -414,7 +414,8 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
   const float rf = sqrtf(xf * xf + yf * yf);
   const float near = -0.05f * Rf;
   const double Hw = PREP ? W.H : s.H;
-  float dw[3] = {rf + Rf - s.Rc_f, rf >= s.r_out_f * 0.999f ? Rf - zf : -1e30f,
+  const bool closed = PREP && W.outlet_closed;
+  float dw[3] = {rf + Rf - s.Rc_f, (closed || rf >= s.r_out_f * 0.999f) ? Rf - zf : -1e30f,
                  zf + Rf - (PREP ? (float)Hw : s.H_f)};
   bool tool = false;
   if (PREP && W.pen_dir != 0) {
@@ -442,7 +443,7 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
         n = v3<T>(T(P.x / r), T(P.y / r), T(0));
       }
     } else if (wall == 1) {
-      if (P.z < fabs(P.w) && sqrt(r2) >= s.r_out) {
+      if (P.z < fabs(P.w) && (closed || sqrt(r2) >= s.r_out)) {
         delta = fabs(P.w) - P.z;
         n = v3<T>(0, 0, -1);
       }

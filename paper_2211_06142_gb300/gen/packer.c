@@ -5,7 +5,8 @@
  * pair is pushed apart along its centre line by half the overlap until the
  * largest overlap is below tol * (mean radius).  Pure geometry: no contact
  * law, no dynamics.  Periodic cube (kind 0) or cylindrical annulus (kind 1:
- * r_out + R <= r <= Rc - R, z >= R, free top surface).
+ * r_out + R <= r <= Rc - R, or r <= Rc - R without a cavity (r_out = 0),
+ * z >= R, free top surface).
  */
 #include <math.h>
 #include <stdint.h>
@@ -25,7 +26,7 @@ static void constrain(int kind, double* p, double R, const double* geo) {
     }
     double Rc = geo[0], r_out = geo[1], h_bed = geo[2];
     double r = sqrt(p[0] * p[0] + p[1] * p[1]);
-    double rmin = r_out + R, rmax = Rc - R;
+    double rmin = r_out > 0.0 ? r_out + R : 0.0, rmax = Rc - R; /* r_out = 0: no cavity */
     if (rmax < rmin) rmax = rmin;
     double t = r < rmin ? rmin : (r > rmax ? rmax : r);
     if (r > 0) {

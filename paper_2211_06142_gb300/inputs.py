@@ -222,21 +222,24 @@ def periodic_sample(d: np.ndarray, phi: float, seed: int, nf: int = 8, U=(0.0, 0
 
 def cylinder_sample(d: np.ndarray, seed: int, d50: float = 0.25e-3, scale: float = 1.0,
                     phi: float = 0.55, U_in: float = 0.01, nf=(40, 40, 20), material=None,
-                    name="cylinder") -> Sample:
+                    name="cylinder", cavity: bool = True) -> Sample:
     """Sand-production sample: cylinder Rc = 40 d50, H = 30 d50 (x scale),
     central perforation outlet r_out = 3 d50 on the lower face, bed packed from
-    z = 0 to the height that holds the spheres at solid fraction phi."""
+    z = 0 to the height that holds the spheres at solid fraction phi, with the
+    perforation over the outlet left empty (cavity) or the bed whole (for the
+    preparation stages, whose penetrometer makes the perforation)."""
     rng = np.random.default_rng(seed + 2000)
     R = 0.5 * np.asarray(d, dtype=np.float64)
     Rc = 40.0 * d50 * scale
     H = 30.0 * d50 * scale
     r_out = 3.0 * d50
+    r_cav = r_out if cavity else 0.0
     Vs = float((4.0 / 3.0 * math.pi * R ** 3).sum())
-    h_bed = Vs / (phi * math.pi * (Rc ** 2 - r_out ** 2))
+    h_bed = Vs / (phi * math.pi * (Rc ** 2 - r_cav ** 2))
     if not h_bed <= H:
-        raise ValueError(f"{name}: the cylinder (Rc {Rc:.3g}, H {H:.3g}, cavity {r_out:.3g}) cannot hold "
+        raise ValueError(f"{name}: the cylinder (Rc {Rc:.3g}, H {H:.3g}, cavity {r_cav:.3g}) cannot hold "
                          f"the grains at solid fraction {phi}")
-    x = pack_cylinder(R, Rc, r_out, h_bed, rng)
+    x = pack_cylinder(R, Rc, r_cav, h_bed, rng)
     v = np.zeros_like(x)
     w = np.zeros_like(x)
     h = (2 * Rc / nf[0], 2 * Rc / nf[1], H / nf[2])

@@ -7,8 +7,8 @@ velocity, half the tangential stiffness), builds it, and runs the pins of
 the tangential law against it: at least one of them must fail.  The same
 for the preparation stages (the original JKR separating at C or solved on
 the modified branch, the plate's servo of the wrong sign, the tool's rim
-normal without its axial part, the tool turning back late) against the
-preparation pins.  Nothing here touches the CUDA library.
+normal without its axial part, the tool turning back late, its driving
+force ignored) against the preparation pins.  Nothing here touches the CUDA library.
 """
 import os
 import shutil
@@ -47,6 +47,8 @@ PREP_MUTATIONS = {
     "tool rim normal without its axial part": ("    n[2] = dz / dist;", "    n[2] = 0.0;"),
     "tool turning back late": ("if (s->pen_dir < 0 && s->pen_z <= s->stage.pen_z_stop) s->pen_dir = 1;",
                                "if (s->pen_dir < 0 && s->pen_z < s->stage.pen_z_stop - 1e-6) s->pen_dir = 1;"),
+    "tool's driving force ignored": ("                f = 1.0 - (double)tq * ORA_TWO_M40 / s->stage.pen_force;",
+                                     "                f = 1.0;"),
 }
 
 PINS = ("five_sevenths or frame_indifferent or tangent_plane or dashpot or mindlin or coulomb")

@@ -16,7 +16,9 @@ the sample to an overburden stress, and the penetrometer.
 * Penetrometer: the nearest point of the tool against a brute-force search
   over its surface; the stroke (down at constant speed, back up, removed);
   a sphere squeezed under the tip against the bottom carries the Hertz
-  force of its overlap, which the tool reports.
+  force of its overlap, which the tool reports; driven by a force, the tool
+  comes to rest where the grains push back with that force, and pulled
+  back it goes up from there.
 """
 import math
 
@@ -233,3 +235,31 @@ def test_penetrometer_squeezes_a_sphere_onto_the_bottom():
     F = 4 / 3 * ES * math.sqrt(R) * d ** 1.5
     assert b["pen_force"] == pytest.approx(F, rel=0.03)
     assert Fmax == pytest.approx(F, rel=0.03)
+
+
+def test_driven_penetrometer_stops_at_its_driving_force():
+    """With a driving force, the tip slows as the grains push back and comes
+    to rest where the push equals the driving force: on a sphere lying on the
+    bottom, where the sphere's Hertz force on each flat is that force."""
+    R = 1e-4
+    Fd = 5e-3
+    p = params(gamma=0.0, jkr_mode=0, e=0.3, Rc=2e-3, H=2e-3)
+    sim = O.Sim(p, [[0.0, 0.0, R]], [[0, 0, 0]], [[0, 0, 0]], [R])
+    sim.set_stage(O.make_stage(pen_mode=1, pen_radius=0.5e-3, pen_speed=2e-2, pen_z_start=2 * R + 1e-7,
+                               pen_z_stop=0.0, pen_force=Fd))
+    sim.compute_forces()
+    sim.step(40_000)
+    b = sim.boundaries()
+    delta = (3 * Fd / (4 * ES * math.sqrt(R))) ** (2 / 3)
+    assert b["pen_dir"] == -1  # still pressing: it never reached the stop
+    assert b["pen_force"] == pytest.approx(Fd, rel=1e-4)
+    assert b["pen_z"] == pytest.approx(2 * R - 2 * delta, abs=1e-4 * delta)
+    # pulled back from where it stands: up at its speed, removed at the start height
+    z = b["pen_z"]
+    sim.set_stage(O.make_stage(pen_mode=2, pen_radius=0.5e-3, pen_speed=2e-2, pen_z_start=2 * R + 1e-7,
+                               pen_z_stop=0.0, pen_force=Fd))
+    sim.step(10)
+    b = sim.boundaries()
+    assert b["pen_dir"] == 1 and b["pen_z"] == pytest.approx(z + 10 * 2e-2 * p.dt, rel=1e-9)
+    sim.step(5000)
+    assert sim.boundaries()["pen_dir"] == 0
