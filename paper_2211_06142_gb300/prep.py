@@ -89,7 +89,7 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     rec["compression"] = dict(steps=steps, seconds=sec, value=n * steps / sec, stress=b["stress"],
                               target=stress, H=b["H"], H_start=top,
                               porosity=porosity_under_plate(s.R, Rc, b["H"]),
-                              converged=abs(b["stress"] - stress) <= tol * stress)
+                              converged=bool(abs(b["stress"] - stress) <= tol * stress))
     # bonding: the modified JKR's bonds on the pairs touching now, the plate held
     st = ctx.get_state()
     ctx.init_particles(st["x"], st["v"], st["w"], s.R, bond_touching=True)
@@ -120,8 +120,8 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     r = np.hypot(st["x"][:, 0], st["x"][:, 1])
     inside = (r < pen_radius) & (st["x"][:, 2] < H)
     vol_in = float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / (math.pi * pen_radius ** 2 * H)
-    rec["perforation"] = dict(steps=steps, seconds=sec, value=n * steps / sec, removed=b["pen_dir"] == 0,
-                              deepest_tip=zmin, driving_force=pen_force, max_force=fmax,
+    rec["perforation"] = dict(steps=steps, seconds=sec, value=n * steps / sec, removed=bool(b["pen_dir"] == 0),
+                              deepest_tip=float(zmin), driving_force=float(pen_force), max_force=float(fmax),
                               bonds_after=int(bonds1.sum() // 2),
                               bonds_broken=int((bonds0.sum() - bonds1.sum()) // 2),
                               solid_fraction_in_hole=vol_in)
