@@ -93,6 +93,8 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     # bonding: the modified JKR's bonds on the pairs touching now, the plate held
     st = ctx.get_state()
     ctx.init_particles(st["x"], st["v"], st["w"], s.R, bond_touching=True)
+    ctx.set_stage(sample, cgdem.stage(jkr_mode=0, outlet_closed=1))
+    ctx.compute_forces()
     bonds0 = bonds_per_grain(ctx, n)
     rec["bonding"] = dict(bonds=int(bonds0.sum() // 2), per_grain_mean=float(bonds0.mean()),
                           per_grain_max=int(bonds0.max()))
