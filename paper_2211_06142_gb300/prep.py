@@ -120,8 +120,9 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     bonds1 = bonds_per_grain(ctx, n)
     st = ctx.get_state()
     r = np.hypot(st["x"][:, 0], st["x"][:, 1])
-    inside = (r < pen_radius) & (st["x"][:, 2] < H)
-    vol_in = float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / (math.pi * pen_radius ** 2 * H)
+    # the hole the tool left, between its deepest tip and the plate
+    inside = (r < pen_radius) & (st["x"][:, 2] > zmin) & (st["x"][:, 2] < H)
+    vol_in = float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / (math.pi * pen_radius ** 2 * (H - zmin))
     rec["perforation"] = dict(steps=steps, seconds=sec, value=n * steps / sec, removed=bool(b["pen_dir"] == 0),
                               deepest_tip=float(zmin), driving_force=float(pen_force), max_force=float(fmax),
                               bonds_after=int(bonds1.sum() // 2),
