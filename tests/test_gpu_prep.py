@@ -166,13 +166,14 @@ def test_preparation_sequence(prec):
     ctx.compute_forces()
     por0 = prep.porosity_under_plate(s.R, s.domain["Rc"], float((s.x[:, 2] + s.R).max()))
     rec = prep.prepare(ctx, s, gen_steps=3000, stress=2e5, vmax=0.2, max_compress_steps=40000,
-                       pen_radius=0.75e-3, pen_speed=0.5, chunk=200)
+                       pen_radius=0.75e-3, pen_speed=0.5, pen_z_stop=0.0, chunk=200)
     print(rec)
     c, b, f = rec["compression"], rec["bonding"], rec["perforation"]
     assert c["converged"] and abs(c["stress"] - 2e5) <= 0.02 * 2e5
     assert c["porosity"] < por0 - 0.1
     assert b["per_grain_mean"] > 3
     assert f["removed"] and f["bonds_broken"] > 0.05 * b["bonds"]
+    assert f["deepest_tip"] < 0.5 * c["H"]
     assert f["solid_fraction_in_hole"] < 0.5 * (1 - c["porosity"])
     assert ctx.boundaries()[0]["pen_dir"] == 0
     ctx.close()
