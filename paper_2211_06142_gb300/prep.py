@@ -105,7 +105,14 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     tool = dict(jkr_mode=0, outlet_closed=1, pen_radius=pen_radius, pen_speed=pen_speed, pen_z_start=H,
                 pen_z_stop=2.0 * float(s.R.max()) if pen_z_stop is None else pen_z_stop, pen_force=pen_force)
     ctx.set_stage(sample, cgdem.stage(pen_mode=1, **tool))
-    steps, sec, fmax, zmin, stalled = 0, 0.0, 0.0, H, 0
+    def fill(zlo):
+        # solid fraction of the tool's path between zlo and the plate (grain centres inside it)
+        x = ctx.get_state()["x"]
+        r = np.hypot(x[:, 0], x[:, 1])
+        inside = (r < pen_radius) & (x[:, 2] > zlo) & (x[:, 2] < H)
+        return float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / (math.pi * pen_radius ** 2 * (H - zlo))
+
+    steps, sec, fmax, zmin, stalled, at_depth = 0, 0.0, 0.0, H, 0, None
     while steps < max_pen_steps:
         sec += _run(ctx, torch, chunk, "perforation")
         steps += chunk
@@ -117,18 +124,17 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
             stalled = stalled + 1 if b["pen_z"] > zmin - 1e-3 * pen_radius else 0
             zmin = min(zmin, b["pen_z"])
             if stalled >= 4:
+                at_depth = fill(b["pen_z"])
                 ctx.set_stage(sample, cgdem.stage(pen_mode=2, **tool))
+        elif at_depth is None:  # turned at the stop height
+            at_depth = fill(b["pen_z"])
     bonds1 = bonds_per_grain(ctx, n)
-    st = ctx.get_state()
-    r = np.hypot(st["x"][:, 0], st["x"][:, 1])
-    # the hole the tool left, between its deepest tip and the plate
-    inside = (r < pen_radius) & (st["x"][:, 2] > zmin) & (st["x"][:, 2] < H)
-    vol_in = float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / (math.pi * pen_radius ** 2 * (H - zmin))
+    vol_in = fill(zmin)  # the hole the tool left, between its deepest tip and the plate
     rec["perforation"] = dict(steps=steps, seconds=sec, value=n * steps / sec, removed=bool(b["pen_dir"] == 0),
                               deepest_tip=float(zmin), driving_force=float(pen_force), max_force=float(fmax),
                               bonds_after=int(bonds1.sum() // 2),
                               bonds_broken=int((bonds0.sum() - bonds1.sum()) // 2),
-                              solid_fraction_in_hole=vol_in)
+                              solid_fraction_in_path_at_depth=at_depth, solid_fraction_in_hole=vol_in)
     # sand production starts with the outlet open
     ctx.set_stage(sample, cgdem.stage(jkr_mode=0, outlet_closed=0))
     return rec
