@@ -175,7 +175,7 @@ def test_preparation_sequence(prec):
     assert c["porosity"] < por0 - 0.1
     assert b["per_grain_mean"] > 3
     assert f["removed"] and f["bonds_broken"] > 0.05 * b["bonds"]
-    assert f["deepest_tip"] < c["H"] - 4 * float(s.R.max())
+    assert f["deepest_tip"] < 0.5 * c["H"]
     assert f["solid_fraction_in_path_at_depth"] < 0.02
     assert ctx.boundaries()[0]["pen_dir"] == 0
     ctx.close()
