@@ -57,8 +57,8 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
             pen_z_stop=None, max_pen_steps=400000, chunk=500):
     """Run the preparation stages on one cylinder sample of a context made
     with jkr_mode 1 and initialised without bonds.  The penetrometer is
-    driven by a force (by default 50 times the overburden stress on its
-    cross-section, about the bearing capacity of a frictional bed) and turns back at pen_z_stop (by default one largest
+    driven by a force (by default 10 times the overburden stress on its
+    cross-section) and turns back at pen_z_stop (by default one largest
     grain diameter above the bottom), or where it stalls against the grains
     under its tip.  Returns
     what each stage did (steps, seconds, particle-steps/s, and the stage's
@@ -101,7 +101,7 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
                           per_grain_max=int(bonds0.max()))
     # perforation: down the axis to the bottom, back up, removed
     H = b["H"]
-    pen_force = pen_force if pen_force is not None else 50.0 * stress * math.pi * pen_radius ** 2
+    pen_force = pen_force if pen_force is not None else 10.0 * stress * math.pi * pen_radius ** 2
     tool = dict(jkr_mode=0, outlet_closed=1, pen_radius=pen_radius, pen_speed=pen_speed, pen_z_start=H,
                 pen_z_stop=2.0 * float(s.R.max()) if pen_z_stop is None else pen_z_stop, pen_force=pen_force)
     ctx.set_stage(sample, cgdem.stage(pen_mode=1, **tool))

@@ -150,7 +150,8 @@ def test_penetrometer_follows_the_oracle(prec):
 
 @pytest.mark.parametrize("prec", [cgdem.FP64, cgdem.MIXED])
 def test_preparation_sequence(prec):
-    """The whole sequence of Sec. 3.1 on a small whole bed (no cavity):
+    """The whole sequence of Sec. 3.1 on a small whole bed (no cavity, 10,000
+    grains, about eight grains deep):
     generation with the original JKR, compression to the target stress,
     bonds on the touching pairs, perforation by a force-driven penetrometer
     and its removal.  What each stage must leave: the stress reached with
@@ -159,8 +160,8 @@ def test_preparation_sequence(prec):
     tool's path clear of grains (whether the hole stays open after the tool
     leaves depends on the cement's strength: reported, not asserted)."""
     from paper_2211_06142_gb300 import prep
-    d = I.fine_diameters(3000, 21)
-    s = I.cylinder_sample(d, 21, scale=0.3, nf=(12, 12, 6), U_in=0.0, name="prep", cavity=False)
+    d = I.fine_diameters(10000, 21)
+    s = I.cylinder_sample(d, 21, scale=0.35, nf=(14, 14, 7), U_in=0.0, name="prep", cavity=False)
     p = cgdem.sample_params(s, default_dt(s), default_skin(s), jkr_mode=1)
     ctx = cgdem.Context([p], [len(s.R)], precision=prec, max_neighbors=64)
     ctx.set_fluid_velocity(np.zeros_like(s.Us))
@@ -168,7 +169,7 @@ def test_preparation_sequence(prec):
     ctx.compute_forces()
     por0 = prep.porosity_under_plate(s.R, s.domain["Rc"], float((s.x[:, 2] + s.R).max()))
     rec = prep.prepare(ctx, s, gen_steps=3000, stress=2e5, vmax=0.2, max_compress_steps=40000,
-                       pen_radius=0.75e-3, pen_speed=0.5, pen_z_stop=0.0, chunk=200)
+                       pen_radius=0.75e-3, pen_speed=0.5, chunk=200)
     print(rec)
     c, b, f = rec["compression"], rec["bonding"], rec["perforation"]
     assert c["converged"] and abs(c["stress"] - 2e5) <= 0.02 * 2e5
