@@ -236,6 +236,13 @@ int cgdem_set_fluid_velocity(cgdem_ctx* ctx, const double* Us, void* stream);
  * d < Ri + Rj + skin), carrying tangential history and bond state by id pair. */
 int cgdem_build_contacts(cgdem_ctx* ctx, void* stream);
 
+/* Bond every pair that touches now, d^2 < (Ri + Rj)^2 in IEEE double (Sec.
+ * 3.1: the bonds of the modified JKR in the perforation stage, made on the
+ * compressed sample); the other contacts keep their state and every contact
+ * its tangential spring.  The candidate list of the current state holds
+ * every touching pair, so this needs no rebuild.  Asynchronous on stream. */
+int cgdem_bond_touching(cgdem_ctx* ctx, void* stream);
+
 /* Porosity: scatter the fixed-point volume quanta round(V_i 2^40 / V_cell)
  * of every active particle into its fluid cell (Eq. 6-7 porosity n);
  * n = clamp(1 - S 2^-40, n_min, 1).  Integer atomics: bit-reproducible. */

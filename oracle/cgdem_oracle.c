@@ -739,18 +739,29 @@ int64_t ora_pairs_bruteforce(const ora_params* p, int64_t n, const double* x, co
     return cnt;
 }
 
+static const ora_rec* find_rec(const ora_rec* rec, int64_t nrec, int32_t i, int32_t j);
+
 int ora_bond_touching(ora_sim* s) {
-    /* every touching pair (d^2 < (Ri+Rj)^2) becomes a bonded record */
+    /* every touching pair (d^2 < (Ri+Rj)^2) becomes bonded; the records of
+       other pairs keep their state, and every record its spring */
     pairlist l = {0};
     find_pairs(&s->p, s->n, s->x, s->R, s->active, 0.0, &l);
-    free(s->rec);
-    s->rec = (ora_rec*)calloc((size_t)(l.n > 0 ? l.n : 1), sizeof(ora_rec));
-    s->nrec = 0;
+    ora_rec* rec = (ora_rec*)calloc((size_t)(s->nrec + l.n > 0 ? s->nrec + l.n : 1), sizeof(ora_rec));
+    int64_t n = 0;
+    for (int64_t k = 0; k < s->nrec; ++k) rec[n++] = s->rec[k];
     for (int64_t k = 0; k < l.n; ++k) {
-        ora_rec r = {l.pi[k], l.pj[k], 1, 0, {0, 0, 0}};
-        s->rec[s->nrec++] = r;
+        ora_rec* old = (ora_rec*)find_rec(rec, s->nrec, l.pi[k], l.pj[k]);
+        if (old) {
+            old->bonded = 1;
+        } else {
+            ora_rec r = {l.pi[k], l.pj[k], 1, 0, {0, 0, 0}};
+            rec[n++] = r;
+        }
     }
-    qsort(s->rec, (size_t)s->nrec, sizeof(ora_rec), rec_cmp);
+    qsort(rec, (size_t)n, sizeof(ora_rec), rec_cmp);
+    free(s->rec);
+    s->rec = rec;
+    s->nrec = n;
     free(l.pi);
     free(l.pj);
     return 0;

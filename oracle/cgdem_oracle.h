@@ -142,7 +142,9 @@ ora_sim* ora_create(const ora_params* p, int64_t n,
                     const double* x, const double* v, const double* w,
                     const double* R, const double* Us /* [nf0*nf1*nf2*3] superficial velocity */);
 void ora_destroy(ora_sim* s);
-/* Bond every pair with delta >= 0 (Sec. 3.1 perforation stage reading). */
+/* Bond every touching pair, d^2 < (Ri + Rj)^2 (Sec. 3.1: the bonds of the
+ * perforation stage); the other records keep their state and every record
+ * its spring. */
 int ora_bond_touching(ora_sim* s);
 /* Cell sums of the void-fraction quanta at the current positions. */
 int ora_couple_fluid(ora_sim* s);

@@ -38,7 +38,7 @@ EXPORTS = [
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
     "cgdem_set_closure", "cgdem_closure_record", "cgdem_get_closure_data",
-    "cgdem_set_stage", "cgdem_get_boundaries",
+    "cgdem_set_stage", "cgdem_get_boundaries", "cgdem_bond_touching",
 ]
 
 
@@ -138,6 +138,7 @@ def lib():
             "cgdem_get_removed_step": (i, [vp, vp, vp]),
             "cgdem_set_psd_classes": (i, [vp, vp, i, vp]),
             "cgdem_set_stage": (i, [vp, i, vp, vp]),
+            "cgdem_bond_touching": (i, [vp, vp]),
             "cgdem_get_boundaries": (i, [vp, vp, i64, vp]),
             "cgdem_get_fluid": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "cgdem_get_produced_psd": (i, [vp, vp, vp, i64, vp]),
@@ -492,6 +493,10 @@ class Context:
         self._check(lib().cgdem_get_fluid(self.h, _ptr(p), _ptr(U), _ptr(g), _ptr(r), C.byref(it), self._s()),
                     "get_fluid")
         return p, U, g, r, it.value
+
+    def bond_touching(self):
+        """Bond every pair that touches now, keeping the other contacts and all springs."""
+        self._check(lib().cgdem_bond_touching(self.h, self._s()), "bond_touching")
 
     def set_stage(self, sample, st: Stage):
         """Start a preparation stage on one cylinder sample (cgdem_set_stage)."""

@@ -1224,6 +1224,14 @@ int cgdem_get_fluid(cgdem_ctx* ctx, double* p, double* U, double* gradp, int64_t
   return check_status(ctx, s);
 }
 
+int cgdem_bond_touching(cgdem_ctx* ctx, void* stream) {
+  int r = ready(ctx);
+  if (r) return r;
+  launch_bond_touching(ctx->d, st(stream));
+  CK(cudaGetLastError());
+  return CGDEM_OK;
+}
+
 int cgdem_set_stage(cgdem_ctx* ctx, int sample, const cgdem_stage* stg, void* stream) {
   int r = ready(ctx);
   if (r) return r;

@@ -91,9 +91,9 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
                               target=stress, H=b["H"], H_start=top,
                               porosity=porosity_under_plate(s.R, Rc, b["H"]),
                               converged=bool(abs(b["stress"] - stress) <= tol * stress))
-    # bonding: the modified JKR's bonds on the pairs touching now, the plate held
-    st = ctx.get_state()
-    ctx.init_particles(st["x"], st["v"], st["w"], s.R, bond_touching=True)
+    # bonding: the modified JKR's bonds on the pairs touching now (the contacts
+    # in force keep their state and springs), the plate held
+    ctx.bond_touching()
     ctx.set_stage(sample, cgdem.stage(jkr_mode=0, outlet_closed=1))
     ctx.compute_forces()
     bonds0 = bonds_per_grain(ctx, n)

@@ -8,7 +8,8 @@ precisions, through the C ABI.
   moves them (tests/helpers.py), which near S grows with the curve's slope.
 * Compression: the small cylinder, its outlet closed, under a
   stress-controlled top plate that starts on the bed's highest grain; the
-  plate's height, velocity and stress follow the oracle's.
+  plate's height, velocity and stress follow the oracle's; then the
+  touching pairs are bonded and the bed runs under the modified JKR.
 * Perforation: the small cylinder, bonded (modified JKR), with a
   penetrometer driven by a force coming down from just above the bed; the
   tool's height and the force on it follow the oracle's.
@@ -114,6 +115,17 @@ def test_plate_compression_follows_the_oracle(prec):
         compare(s, ctx, sim, prec, skin, orig=True, H=ob["H"])
     assert travel > 0 and ob["stress"] > 0  # the plate came down and carries the bed
     assert ob["stress"] * A > 0
+    # the compressed bed's touching pairs become the modified JKR's bonds,
+    # the contacts in force keeping their springs; then steps under it
+    ctx.bond_touching()
+    sim.bond_touching()
+    kw = dict(jkr_mode=0, outlet_closed=1)
+    ctx.set_stage(0, cgdem.stage(**kw))
+    sim.set_stage(O.make_stage(**kw))
+    ctx.step(50)
+    sim.step(50)
+    compare(s, ctx, sim, prec, skin, H=ob["H"])
+    assert (sim.contacts()[2] == 1).sum() > len(s.R)  # the bed is bonded
     ctx.close()
 
 
