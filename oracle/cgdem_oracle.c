@@ -804,33 +804,23 @@ static int pair_cmp(const void* a, const void* b) {
 }
 
 /* wall contacts of one particle (cylinder domain), Hertz without cohesion */
-/* Penetrometer contact (Sec. 3.1): the point of the tool (a solid cylinder
- * of radius rp on the axis, from its flat tip at height zt upwards) nearest
- * to the particle's centre x.  Beside the tool that point is on its side,
- * below the tip on the tip's face, and below and outside it on the tip's
- * rim.  Returns the overlap R - distance; n is the unit vector from the
- * centre towards that point. */
+/* Penetrometer contact (Sec. 3.1): the tool is a solid cylinder of radius
+ * rp on the axis with a hemispherical end whose lowest point is at height
+ * zt, every point within rp of the axis above zt + rp.  The tool's surface
+ * point nearest to a particle's centre x lies on the line from x to the
+ * nearest axis point, (0, 0, max(x_z, zt + rp)), at distance d - rp from x.
+ * Returns the overlap R - (d - rp); n is the unit vector from the centre
+ * towards the axis point (no contact when the centre lies on the axis). */
 static double tool_contact(const double x[3], double R, double rp, double zt, double n[3]) {
-    double r = sqrt(x[0] * x[0] + x[1] * x[1]);
+    double az = x[2] > zt + rp ? x[2] : zt + rp;
+    double dz = az - x[2];
+    double d = sqrt(x[0] * x[0] + x[1] * x[1] + dz * dz);
     n[0] = n[1] = n[2] = 0.0;
-    if (x[2] >= zt) { /* beside the tool: its side */
-        if (!(r > 0.0)) return -1.0;
-        n[0] = -x[0] / r;
-        n[1] = -x[1] / r;
-        return R - (r - rp);
-    }
-    double dz = zt - x[2];
-    if (r <= rp) { /* under the tip's face */
-        n[2] = 1.0;
-        return R - dz;
-    }
-    /* under and outside the rim: towards the nearest point of the rim circle */
-    double dr = r - rp;
-    double dist = sqrt(dr * dr + dz * dz);
-    n[0] = -dr * x[0] / (r * dist);
-    n[1] = -dr * x[1] / (r * dist);
-    n[2] = dz / dist;
-    return R - dist;
+    if (!(d > 0.0)) return -1.0;
+    n[0] = -x[0] / d;
+    n[1] = -x[1] / d;
+    n[2] = dz / d;
+    return R - (d - rp);
 }
 
 double ora_tool_overlap(const double x[3], double R, double rp, double zt, double n[3]) {

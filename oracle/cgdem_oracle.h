@@ -79,7 +79,8 @@ typedef struct {
     double plate_gain;    /* [m / (s Pa)] */
     double plate_vmax;    /* [m/s] */
     int pen_mode;         /* 1: a penetrometer (a rigid cylinder of radius
-                             pen_radius on the axis, from its flat tip upwards)
+                             pen_radius on the axis ending below in a hemisphere
+                             of the same radius, its tip the lowest point)
                              starts with its tip at pen_z_start, moves down at
                              pen_speed until the tip reaches pen_z_stop, then up
                              at the same speed until the tip is back at
@@ -154,8 +155,9 @@ int ora_compute_forces(ora_sim* s);
 int ora_step(ora_sim* s, int64_t nsteps);
 int ora_get_state(const ora_sim* s, double* x, double* v, double* w, double* F, double* T);
 /* Overlap R - distance between a particle (centre x, radius R) and the
- * penetrometer (radius rp, tip at height zt), and the unit vector n from the
- * centre towards the tool's nearest point. */
+ * penetrometer (a cylinder of radius rp on the axis ending in a hemisphere
+ * whose lowest point is at height zt), and the unit vector n from the centre
+ * towards the tool's nearest point. */
 double ora_tool_overlap(const double x[3], double R, double rp, double zt, double n[3]);
 /* Start a preparation stage (the boundaries move from the next drift on). */
 int ora_set_stage(ora_sim* s, const ora_stage* st);

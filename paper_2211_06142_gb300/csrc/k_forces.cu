@@ -311,32 +311,25 @@ __device__ __forceinline__ float s64_to_f(long long v) {
   return v < 0 ? -m : m;
 }
 
-// Penetrometer contact (Sec. 3.1): the point of the tool (a solid cylinder
-// of radius rp on the axis, from its flat tip at height zt upwards) nearest
-// to the sphere's centre: beside the tool on its side, below the tip on its
-// face, below and outside it on the tip's rim.  Returns the overlap R -
-// distance and the unit vector n from the centre towards that point.
-__device__ __forceinline__ double tool_overlap(double x, double y, double z, double R, double r,
-                                               double rp, double zt, double n[3]) {
+// Penetrometer contact (Sec. 3.1): the tool is a solid cylinder of radius
+// rp on the axis with a hemispherical end whose lowest point (the tip) is at
+// height zt, every point within rp of the axis above zt + rp.  Its surface
+// point nearest to the sphere's centre lies on the line from the centre to
+// the nearest axis point, (0, 0, max(z, zt + rp)), at distance d - rp.
+// Returns the overlap R - (d - rp) and the unit vector n from the centre
+// towards the axis point (no contact when the centre lies on the axis).
+__device__ __forceinline__ double tool_overlap(double x, double y, double z, double R, double rp, double zt,
+                                               double n[3]) {
+  const double zc = __dadd_rn(zt, rp);
+  const double az = z > zc ? z : zc;
+  const double dz = __dsub_rn(az, z);
+  const double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(dz, dz)));
   n[0] = n[1] = n[2] = 0.0;
-  if (z >= zt) {  // beside the tool: its side
-    if (!(r > 0.0)) return -1.0;
-    n[0] = -x / r;
-    n[1] = -y / r;
-    return __dsub_rn(R, __dsub_rn(r, rp));
-  }
-  const double dz = __dsub_rn(zt, z);
-  if (r <= rp) {  // under the tip's face
-    n[2] = 1.0;
-    return __dsub_rn(R, dz);
-  }
-  const double dr = __dsub_rn(r, rp);  // under and outside the rim
-  const double dist = sqrt(__dadd_rn(__dmul_rn(dr, dr), __dmul_rn(dz, dz)));
-  const double rd = __dmul_rn(r, dist);
-  n[0] = __ddiv_rn(__dmul_rn(-dr, x), rd);
-  n[1] = __ddiv_rn(__dmul_rn(-dr, y), rd);
-  n[2] = __ddiv_rn(dz, dist);
-  return __dsub_rn(R, dist);
+  if (!(d > 0.0)) return -1.0;
+  n[0] = __ddiv_rn(-x, d);
+  n[1] = __ddiv_rn(-y, d);
+  n[2] = __ddiv_rn(dz, d);
+  return __dsub_rn(R, __dsub_rn(d, rp));
 }
 
 // One Hertz contact of a sphere with a flat or curved wall moving at vw
@@ -384,7 +377,8 @@ __device__ __noinline__ void tool_contact(const SampleDev& s, StageDev* W, doubl
                                           V3<T> w, T R, T m, T Es, T Gs, T beta, T mu, T dt, H* h,
                                           V3<T>* F, V3<T>* Tq) {
   double nd[3];
-  const double delta = tool_overlap(P.x, P.y, P.z, fabs(P.w), r, W->pen_radius, W->pen_z, nd);
+  (void)r;
+  const double delta = tool_overlap(P.x, P.y, P.z, fabs(P.w), W->pen_radius, W->pen_z, nd);
   V3<T> Fl = *F, Tl = *Tq;
   const T fz = wall_hertz<T, H>(delta, v3<T>(T(nd[0]), T(nd[1]), T(nd[2])),
                                 W->v_pen, s, v, w, R, m, Es, Gs, beta, mu, dt,
@@ -419,12 +413,9 @@ __device__ __forceinline__ void wall_contacts(const SampleDev& s, StageDev& W, d
                  zf + Rf - (PREP ? (float)Hw : s.H_f)};
   bool tool = false;
   if (PREP && W.pen_dir != 0) {
-    const float rp = (float)W.pen_radius, zt = (float)W.pen_z;
-    float dtool;
-    if (zf >= zt) dtool = Rf - (rf - rp);
-    else if (rf <= rp) dtool = Rf - (zt - zf);
-    else dtool = Rf - sqrtf((rf - rp) * (rf - rp) + (zt - zf) * (zt - zf));
-    tool = dtool > near;
+    const float rp = (float)W.pen_radius, zc = (float)W.pen_z + rp;
+    const float dz = zf > zc ? 0.f : zc - zf;
+    tool = Rf + rp - sqrtf(rf * rf + dz * dz) > near;
   }
   // most spheres are far from every wall: leave before any FP64 work (the
   // compiler would otherwise hoist the loop-invariant radius and its square

@@ -108,11 +108,11 @@ def jkr_radius_np(delta, Rs, Es, gamma, orig=False):
 
 
 def tool_overlap_np(x, R, rp, zt):
-    """Overlap of each sphere with the penetrometer (test-side, for a bound)."""
-    r = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
-    dz = zt - x[:, 2]
-    rim = np.sqrt(np.maximum(r - rp, 0) ** 2 + dz ** 2)
-    return np.where(x[:, 2] >= zt, R - (r - rp), np.where(r <= rp, R - dz, R - rim))
+    """Overlap of each sphere with the penetrometer, a cylinder of radius rp
+    ending in a hemisphere with its lowest point at zt (test-side, for a
+    bound)."""
+    dz = np.maximum(zt + rp - x[:, 2], 0.0)
+    return R + rp - np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2 + dz ** 2)
 
 
 def state_diff(s, g, o):

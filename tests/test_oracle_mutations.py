@@ -6,9 +6,10 @@ tangential dashpot twice as strong, the spin left out of the contact
 velocity, half the tangential stiffness), builds it, and runs the pins of
 the tangential law against it: at least one of them must fail.  The same
 for the preparation stages (the original JKR separating at C or solved on
-the modified branch, the plate's servo of the wrong sign, the tool's rim
+the modified branch, the plate's servo of the wrong sign, the tool's
 normal without its axial part, the tool turning back late, its driving
-force ignored) against the preparation pins.  Nothing here touches the CUDA library.
+force ignored) against the preparation pins.  Nothing here touches the
+CUDA library.
 """
 import os
 import shutil
@@ -44,7 +45,7 @@ PREP_MUTATIONS = {
     "plate servo of the wrong sign": (
         "            double v = s->stage.plate_gain * (stress - s->stage.plate_stress);",
         "            double v = s->stage.plate_gain * (s->stage.plate_stress - stress);"),
-    "tool rim normal without its axial part": ("    n[2] = dz / dist;", "    n[2] = 0.0;"),
+    "tool normal without its axial part": ("    n[2] = dz / d;", "    n[2] = 0.0;"),
     "tool turning back late": ("if (s->pen_dir < 0 && s->pen_z <= s->stage.pen_z_stop) s->pen_dir = 1;",
                                "if (s->pen_dir < 0 && s->pen_z < s->stage.pen_z_stop - 1e-6) s->pen_dir = 1;"),
     "tool's driving force ignored": ("                f = 1.0 - (double)tq * ORA_TWO_M40 / s->stage.pen_force;",

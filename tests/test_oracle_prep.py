@@ -13,8 +13,8 @@ the sample to an overburden stress, and the penetrometer.
 * Top plate under a stress servo: one sphere between the bottom and the
   plate comes to rest where the plate's force, the target stress times the
   plate area, is the Hertz force of the sphere on each flat.
-* Penetrometer: the nearest point of the tool against a brute-force search
-  over its surface; the stroke (down at constant speed, back up, removed);
+* Penetrometer (a cylinder with a hemispherical end): the nearest point of
+  the tool against a brute-force search along its axis; the stroke (down at constant speed, back up, removed);
   a sphere squeezed under the tip against the bottom carries the Hertz
   force of its overlap, which the tool reports; driven by a force, the tool
   comes to rest where the grains push back with that force, and pulled
@@ -149,44 +149,33 @@ def test_plate_servo_rests_at_the_hertz_overlap():
 
 
 def tool_bruteforce(x, rp, zt):
-    """Nearest point of the tool's surface to x by a dense search: the side
-    (radius rp, from the tip up), the tip's face and its rim."""
-    best = (np.inf, None)
-    th = np.linspace(0, 2 * np.pi, 3601)
-    # side and rim: the nearest generator line is at the centre's azimuth;
-    # search azimuths and heights on a grid around it
-    phi = math.atan2(x[1], x[0])
-    for t in phi + np.linspace(-0.05, 0.05, 201):
-        zs = np.linspace(zt, zt + 4e-3, 40001)
-        pts = np.stack([np.full_like(zs, rp * math.cos(t)), np.full_like(zs, rp * math.sin(t)), zs], 1)
-        dd = np.linalg.norm(pts - x, axis=1)
-        k = int(np.argmin(dd))
-        if dd[k] < best[0]:
-            best = (dd[k], pts[k])
-    # tip face
-    for rho in np.linspace(0, rp, 401):
-        pts = np.stack([rho * np.cos(th), rho * np.sin(th), np.full_like(th, zt)], 1)
-        dd = np.linalg.norm(pts - x, axis=1)
-        k = int(np.argmin(dd))
-        if dd[k] < best[0]:
-            best = (dd[k], pts[k])
-    return best
+    """Nearest point of the tool's surface to x by a dense search over its
+    axis: the tool is every point within rp of the axis from zt + rp up, so
+    its surface point nearest to x lies rp from the nearest axis point,
+    towards x."""
+    zs = np.linspace(zt + rp, zt + rp + 6e-3, 600001)
+    dd = np.sqrt(x[0] ** 2 + x[1] ** 2 + (zs - x[2]) ** 2)
+    k = int(np.argmin(dd))
+    a = np.array([0.0, 0.0, zs[k]])
+    return dd[k] - rp, a + rp * (x - a) / dd[k]
 
 
 def test_penetrometer_nearest_point_against_brute_force():
     rng = np.random.default_rng(5)
     rp, zt, R = 0.85e-3, 2e-3, 1e-4
-    cases = [(1.2e-3, 0.3, 3e-3), (0.3e-3, 1.0, 1.9e-3), (0.95e-3, 2.0, 1.95e-3), (1.0e-3, -2.5, 2.0e-3)]
-    for _ in range(4):
-        cases.append((rng.uniform(0.9e-3, 1.2e-3), rng.uniform(-np.pi, np.pi), rng.uniform(1.8e-3, 2.6e-3)))
+    # beside the tool, under its tip on and off the axis, around the rim
+    cases = [(1.2e-3, 0.3, 3e-3), (0.3e-3, 1.0, 1.9e-3), (0.95e-3, 2.0, 1.95e-3), (1.0e-3, -2.5, 2.0e-3),
+             (1e-9, 0.0, 1.85e-3)]
+    for _ in range(6):
+        cases.append((rng.uniform(0.9e-3, 1.2e-3), rng.uniform(-np.pi, np.pi), rng.uniform(1.8e-3, 3.6e-3)))
     for r, a, z in cases:
         x = np.array([r * math.cos(a), r * math.sin(a), z])
         ov, n = O.tool_overlap(x, R, rp, zt)
         dist, q = tool_bruteforce(x, rp, zt)
-        assert R - ov == pytest.approx(dist, abs=2e-7)
+        assert R - ov == pytest.approx(dist, abs=2e-10)
         u = (q - x) / np.linalg.norm(q - x)
         assert np.linalg.norm(n) == pytest.approx(1.0, abs=1e-12)
-        assert np.dot(n, u) > 1 - 1e-3
+        assert np.dot(n, u) > 1 - 1e-9
 
 
 def test_penetrometer_stroke():
