@@ -133,11 +133,12 @@ def test_plate_compression_follows_the_oracle(prec):
 def test_penetrometer_follows_the_oracle(prec):
     s = small_cylinder()
     ctx, sim, skin = contexts(s, prec, 0, bond=True)
-    # a tool wider than the cavity over the outlet, starting just above the
-    # highest grain under it
+    # a tool wider than the cavity over the outlet, starting with its
+    # hemispherical end just above the first grain it will touch
     rp = 0.4 * s.domain["Rc"]
-    under = np.hypot(s.x[:, 0], s.x[:, 1]) < rp + s.R
-    top = float((s.x[under, 2] + s.R[under]).max())
+    r = np.hypot(s.x[:, 0], s.x[:, 1])
+    under = r < rp + s.R
+    top = float((s.x[under, 2] - rp + np.sqrt((rp + s.R[under]) ** 2 - r[under] ** 2)).max())
     kw = dict(jkr_mode=0, pen_mode=1, pen_radius=rp, pen_speed=0.5, pen_z_start=top + 1e-6,
               pen_z_stop=0.5 * top, pen_force=0.05)
     ctx.set_stage(0, cgdem.stage(**kw))
