@@ -134,11 +134,14 @@ def fixed_quantum(s, skin):
     return 2.0 ** math.ceil(math.log2(reach / 2.0 ** 30))
 
 
-def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0, orig=False, H=None, tool=None):
+def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0, orig=False, H=None, tool=None, vf=None):
     """Per-particle bounds on |F_gpu - F_oracle| and |T_gpu - T_oracle| after
     several mixed steps (see above); orig: the original JKR's branch for
     the contacts in force; H: the top plate's height, if it moved; tool:
-    (radius, tip height) of a penetrometer, if one is in."""
+    (radius, tip height) of a penetrometer, if one is in; vf: the two runs'
+    porosity cell sums, whose difference (a grain on the other side of a
+    cell face in one run) moves the drag of every grain in the cell by at
+    most (chi + 2) |dn| / n of it (Eq. 8-11: n^-chi, and u = U / n)."""
     m = s.material
     Es = m["E"] / (2 * (1 - m["nu"] ** 2))
     Gs = m["E"] / (2 * (1 + m["nu"])) / (2 * (2 - m["nu"]))
@@ -195,6 +198,11 @@ def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0, orig=False, H=None, tool=None)
     fd = np.linalg.norm(cl[:, 5:8], axis=1)
     slip = cl[:, 1]
     B += np.where(slip > 0, 2 * fd / np.maximum(slip, 1e-300), 0.0) * dv
+    if vf is not None:
+        n_min = 0.2
+        ng, no = (np.clip(1.0 - a.astype(np.float64) * 2.0 ** -40, n_min, 1.0) for a in vf)
+        cell = cl[:, 9].astype(np.int64)
+        B += 6.0 * fd * np.abs(ng[cell] - no[cell]) / no[cell]
     scale = sim.force_scale()
     bF = tau * scale + 2 * B
     return bF, R * bF

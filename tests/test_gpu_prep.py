@@ -55,7 +55,8 @@ def compare(s, ctx, sim, prec, skin, **bound_kw):
     oi, oj, ob, _ = sim.contacts()
     if prec == cgdem.FP64:
         assert np.array_equal(gc[0], oi) and np.array_equal(gc[1], oj) and np.array_equal(gc[2], ob)
-    left = check_mixed_forces(s, g, o, sim, gc, TAU[prec], skin=skin, **bound_kw)
+    vf = (ctx.get_voidfrac(s.grid.ncell), sim.voidfrac())
+    left = check_mixed_forces(s, g, o, sim, gc, TAU[prec], skin=skin, vf=vf, **bound_kw)
     assert left <= (0 if prec == cgdem.FP64 else 0.02 * len(s.R))
     return g, o
 
