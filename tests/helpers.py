@@ -177,7 +177,16 @@ def force_bound(s, o, sim, g, tau, k=1.0, dq=0.0, orig=False, H=None, tool=None,
         kt = 8 * Gs * a
         gn = cd * np.sqrt(2 * Es * a * ms)
         gt = cd * np.sqrt(kt * ms)
-        t = (kn + kt) * (dx[oi] + dx[oj] + (math.sqrt(3) + 1) * dq) + \
+        # the dashpots of a Hertz contact grow as delta^(1/4) (Eq. 32 with
+        # a = sqrt(R* delta)): at a fresh, small overlap their force moves by
+        # (gn |vn| + gt |vt|) / (4 delta) per unit of overlap
+        vr = o["v"][oj] - o["v"][oi]
+        nrm = d / np.maximum(dist, 1e-300)[:, None]
+        vn = np.abs((vr * nrm).sum(1))
+        vt = np.linalg.norm(vr - (vr * nrm).sum(1)[:, None] * nrm, axis=1) + Ri * np.linalg.norm(o["w"][oi], axis=1) \
+            + Rj * np.linalg.norm(o["w"][oj], axis=1)
+        ddamp = np.where(~bond & (delta > 0), (gn * vn + gt * vt) / (4 * np.maximum(delta, 1e-300)), 0.0)
+        t = (kn + kt + ddamp) * (dx[oi] + dx[oj] + (math.sqrt(3) + 1) * dq) + \
             (gn + gt) * (dv[oi] + dv[oj] + Ri * dw[oi] + Rj * dw[oj])
         np.add.at(B, oi, t)
         np.add.at(B, oj, t)
