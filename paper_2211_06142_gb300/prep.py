@@ -106,11 +106,15 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
                 pen_z_stop=2.0 * float(s.R.max()) if pen_z_stop is None else pen_z_stop, pen_force=pen_force)
     ctx.set_stage(sample, cgdem.stage(pen_mode=1, **tool))
     def fill(zlo):
-        # solid fraction of the tool's path between zlo and the plate (grain centres inside it)
+        # solid fraction of the space the tool fills with its tip at zlo, up to
+        # the plate (a cylinder ending in a hemisphere): the grains whose
+        # centres lie inside it
         x = ctx.get_state()["x"]
-        r = np.hypot(x[:, 0], x[:, 1])
-        inside = (r < pen_radius) & (x[:, 2] > zlo) & (x[:, 2] < H)
-        return float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / (math.pi * pen_radius ** 2 * (H - zlo))
+        az = np.maximum(x[:, 2], zlo + pen_radius)
+        dist = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2 + (az - x[:, 2]) ** 2)
+        inside = (dist < pen_radius) & (x[:, 2] < H)
+        vol = math.pi * pen_radius ** 2 * max(H - zlo - pen_radius, 0.0) + 2.0 / 3.0 * math.pi * pen_radius ** 3
+        return float((4.0 / 3.0 * math.pi * s.R[inside] ** 3).sum()) / vol
 
     steps, sec, fmax, zmin, stalled, at_depth = 0, 0.0, 0.0, H, 0, None
     while steps < max_pen_steps:
