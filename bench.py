@@ -365,6 +365,35 @@ def run_closure_cost(torch, device, barrier, K=2000):
     return out
 
 
+def run_prep(torch, device, barrier, stress=1.0e6, pen_speed=0.2):
+    """The preparation stages of Sec. 3.1 on the 200k-sphere cylinder's
+    bed packed whole, mixed precision: generation with the original JKR,
+    compression by the top plate to the paper's 1 MPa, bonds on the touching
+    pairs, perforation by a force-driven penetrometer of the paper's 1.7 mm
+    diameter, removal.  Particle-steps/s of each stage and what it left."""
+    from paper_2211_06142_gb300 import cgdem
+    from paper_2211_06142_gb300 import inputs as I
+    from paper_2211_06142_gb300 import prep
+    s = I.cached(I.whole_cylinder, 200_000, 1)
+    dt, skin = step_params(s)
+    p = cgdem.sample_params(s, dt, skin, jkr_mode=1)
+    ctx = cgdem.Context([p], [len(s.R)], precision=cgdem.MIXED, max_neighbors=48, device=device,
+                        cell_scale=0.5)
+    ctx.set_fluid_velocity(np.zeros_like(s.Us))
+    ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=False)
+    ctx.compute_forces()
+    por0 = prep.porosity_under_plate(s.R, s.domain["Rc"], float((s.x[:, 2] + s.R).max()))
+    barrier()
+    rec = prep.prepare(ctx, s, gen_steps=5000, stress=stress, vmax=0.2, max_compress_steps=60000,
+                       pen_speed=pen_speed, chunk=1000)
+    ctx.close()
+    rec = {k: ({kk: (float(vv) if isinstance(vv, (np.floating, np.integer)) else vv) for kk, vv in v.items()}
+               if isinstance(v, dict) else v) for k, v in rec.items()}
+    rec["workload"] = "200k-sphere cylinder, whole bed, mixed"
+    rec["porosity_packed"] = por0
+    return rec
+
+
 def run_darcy(torch, device, barrier, K=1000, couple_every=100, p_inlet=2000.0):
     """Cost of the two-way coupling: the 200k-sphere cylinder in mixed
     precision with the flow solved by Darcy's law after every porosity
@@ -710,6 +739,7 @@ def main():
             extras["batched"] = b
         extras["closure"] = run_closure_cost(torch, device, barrier, min(max(K, 500), 2000))
         extras["two_way_coupling"] = run_darcy(torch, device, barrier, min(max(K, 500), 2000))
+        extras["preparation"] = run_prep(torch, device, barrier)
         if rank == 0 and not args.no_sand:
             extras["sand"] = run_sand()
 

@@ -357,6 +357,12 @@ def small_periodic(n: int = 2000, seed: int = 0) -> Sample:
     return periodic_sample(fine_diameters(n, seed), 0.55, seed, name="periodic-2k")
 
 
+def whole_cylinder(n: int = 200_000, seed: int = 1) -> Sample:
+    """The 200k-sphere cylinder's bed packed whole, without the perforation
+    (the preparation stages make it), and no prescribed flow."""
+    return cylinder_sample(fine_diameters(n, seed), seed, U_in=0.0, name="cylinder-whole", cavity=False)
+
+
 def fine_cylinder(n: int = 200_000, seed: int = 1, U_in: float = 1e-4) -> Sample:
     """200,000 spheres, same PSD, in the 40x40x20-cell sand-production cylinder,
     with the paper's injection velocity of 1e-4 m/s (Sec. 3.1)."""
