@@ -365,17 +365,20 @@ def run_closure_cost(torch, device, barrier, K=2000):
     return out
 
 
-def run_prep(torch, device, barrier, stress=1.0e6, pen_speed=0.2):
+def run_prep(torch, device, barrier, pen_speed=0.2):
     """The preparation stages of Sec. 3.1 on the 200k-sphere cylinder's
     bed packed whole, mixed precision: generation with the original JKR,
-    compression by the top plate to the paper's 1 MPa, bonds on the touching
-    pairs, perforation by a force-driven penetrometer of the paper's 1.7 mm
+    compression by the top plate to the paper's overburden stress (scaled by
+    the grains' Young's modulus over Table 3's), bonds on the touching pairs,
+    perforation by a force-driven penetrometer of the paper's 1.7 mm
     diameter, removal.  Particle-steps/s of each stage and what it left."""
     from paper_2211_06142_gb300 import cgdem
     from paper_2211_06142_gb300 import inputs as I
     from paper_2211_06142_gb300 import prep
     s = I.cached(I.whole_cylinder, 200_000, 1)
-    dt, skin = step_params(s)
+    dt, _ = step_params(s)
+    skin = 0.05 * 2 * float(s.R.max())
+    stress = prep.scaled_stress(s.material["E"])
     p = cgdem.sample_params(s, dt, skin, jkr_mode=1)
     ctx = cgdem.Context([p], [len(s.R)], precision=cgdem.MIXED, max_neighbors=48, device=device,
                         cell_scale=0.5)
@@ -384,12 +387,13 @@ def run_prep(torch, device, barrier, stress=1.0e6, pen_speed=0.2):
     ctx.compute_forces()
     por0 = prep.porosity_under_plate(s.R, s.domain["Rc"], float((s.x[:, 2] + s.R).max()))
     barrier()
-    rec = prep.prepare(ctx, s, gen_steps=5000, stress=stress, vmax=0.2, max_compress_steps=60000,
+    rec = prep.prepare(ctx, s, gen_steps=5000, stress=stress, vmax=0.05, max_compress_steps=60000,
                        pen_speed=pen_speed, chunk=1000)
     ctx.close()
     rec = {k: ({kk: (float(vv) if isinstance(vv, (np.floating, np.integer)) else vv) for kk, vv in v.items()}
                if isinstance(v, dict) else v) for k, v in rec.items()}
     rec["workload"] = "200k-sphere cylinder, whole bed, mixed"
+    rec["stress_Pa"] = stress
     rec["porosity_packed"] = por0
     return rec
 

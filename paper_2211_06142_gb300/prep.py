@@ -25,6 +25,14 @@ from . import cgdem
 
 PAPER_STRESS = 1.0e6          # overburden stress of the compression [Pa] (Sec. 3.1)
 PAPER_PEN_DIAMETER = 1.7e-3   # penetrometer diameter [m] (Sec. 3.1)
+PAPER_E = 2.0e10              # Young's modulus of the grains [Pa] (Table 3)
+
+
+def scaled_stress(E):
+    """The paper's overburden stress for grains of Young's modulus E: the
+    same stress over modulus, so that the compression strains the contacts
+    as much as in the paper."""
+    return PAPER_STRESS * E / PAPER_E
 
 
 def porosity_under_plate(R, Rc, H):
