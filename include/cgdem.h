@@ -369,7 +369,8 @@ int cgdem_get_counters(cgdem_ctx* ctx, int64_t* steps, int64_t* rebuilds, int32_
  * whose rebuild falls due (0 when conditional nodes are unavailable: the
  * rebuild kernels are then captured plainly and counted in *step_kernels).
  * Kernels launched by a stretch of calls = the difference of step_kernels
- * + rebuild_kernels x the rebuilds done in it (cgdem_get_counters). */
+ * + rebuild_kernels x the rebuilds done in it (cgdem_get_counters).  The
+ * Darcy solves that conditional nodes run (fluid_mode 1) are not counted. */
 int cgdem_get_launch_counts(cgdem_ctx* ctx, int64_t* step_kernels, int32_t* rebuild_kernels);
 
 /* ---------------------------------------------------------------------
