@@ -387,7 +387,7 @@ def run_prep(torch, device, barrier, pen_speed=0.2):
     ctx.compute_forces()
     por0 = prep.porosity_under_plate(s.R, s.domain["Rc"], float((s.x[:, 2] + s.R).max()))
     barrier()
-    rec = prep.prepare(ctx, s, gen_steps=5000, stress=stress, vmax=0.1, max_compress_steps=150000,
+    rec = prep.prepare(ctx, s, gen_steps=5000, stress=stress, vmax=0.05, max_compress_steps=150000,
                        pen_speed=pen_speed, chunk=1000)
     ctx.close()
     rec = {k: ({kk: (float(vv) if isinstance(vv, (np.floating, np.integer)) else vv) for kk, vv in v.items()}

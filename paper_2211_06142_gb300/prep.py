@@ -84,7 +84,7 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     # compression: the plate from the highest grain down to the overburden stress
     st = ctx.get_state()
     top = min(float((st["x"][:, 2] + s.R).max()), s.domain["H"])
-    gain = gain if gain is not None else vmax / (0.1 * stress)
+    gain = gain if gain is not None else vmax / (0.5 * stress)
     ctx.set_stage(sample, cgdem.stage(jkr_mode=1, outlet_closed=1, plate_mode=1, plate_H=top,
                                       plate_stress=stress, plate_gain=gain, plate_vmax=vmax))
     steps, sec = 0, 0.0
