@@ -271,11 +271,14 @@ def run_batched(torch, cgdem, device, barrier, rank, world, K, W, tune=True):
             "Zbar": Zbar, "candidates_per_particle": Cbar}
 
 
-def run_sand(T=0.004, n_times=40):
+def run_sand(T=0.004, n_times=40, pair="200k"):
     """Produced sand (Eq. 40) of the coarse-grained models against the fine
-    200k-sphere cylinder over the same physical time T: RMSRE (Eq. 41) and
-    the relative error at T for SSW and SSP at k = 2 and 3, and for SSW at
-    k = 3 with the learned closure trained on this very pair of runs."""
+    cylinder over the same physical time T: RMSRE (Eq. 41) and the relative
+    error at T for SSW and SSP at k = 2 and 3, and for SSW at k = 3 with the
+    learned closure trained on this very pair of runs.  pair "200k": the
+    200k-sphere cylinder and its coarse models; pair "2m": the 2M-sphere
+    tiled cylinder (the 200k geometry scaled by 2.15) and its SSW k = 3
+    counterpart of about 72k parcels, plain and with the closure."""
     import math
     from paper_2211_06142_gb300 import cgdem
     from paper_2211_06142_gb300 import closure as CL
@@ -283,7 +286,14 @@ def run_sand(T=0.004, n_times=40):
     from paper_2211_06142_gb300 import sand as SD
     from paper_2211_06142_gb300 import workloads as Wl
     t0 = time.perf_counter()
-    fine = I.cached(I.fine_cylinder)
+    if pair == "200k":
+        fine = I.cached(I.fine_cylinder)
+        models = (("ssw", 2), ("ssw", 3), ("ssp", 2), ("ssp", 3))
+        coarse = lambda k, scheme: Wl.coarse_cylinder(k=k, scheme=scheme)  # noqa: E731
+    else:
+        fine = make_workload(1)
+        models = (("ssw", 3),)
+        coarse = lambda k, scheme: Wl.coarse_tiled_cylinder(k=k, scheme=scheme)  # noqa: E731
     # time to simulate T (plain runs, no recording), the coarse-graining speedup
     tf = time.perf_counter()
     SD.run(fine, T=T, n_times=1)
@@ -291,13 +301,14 @@ def run_sand(T=0.004, n_times=40):
     ref = SD.run(fine, T=T, n_times=n_times, record=True)
     mg = lambda a: [[round(float(v) * 1e6, 4) for v in row] for row in a]  # noqa: E731
     out = {"T_s": T, "times": n_times, "U_in_m_s": SD.U_SAND, "dt_over_rayleigh": SD.DT_FRAC,
+           "fine_spheres": len(fine.R),
            "fine_mass_mg": float(ref.mass[-1] * 1e6), "fine_steps": ref.steps, "fine_wall_s": t_fine,
            "psd_classes_mm": [round(float(v) * 1e3, 4) for v in SD.table2_edges()],
            "psd_window_fractions": list(SD.WINDOW_FRACTIONS),
            "fine_psd_windows_mg": mg(SD.psd_windows(ref)), "models": {}}
     ssw3 = None
-    for scheme, k in (("ssw", 2), ("ssw", 3), ("ssp", 2), ("ssp", 3)):
-        s = Wl.coarse_cylinder(k=k, scheme=scheme)
+    for scheme, k in models:
+        s = coarse(k, scheme)
         rec = scheme == "ssw" and k == 3
         tc = time.perf_counter()
         SD.run(s, k=k, scheme=Wl.SCHEME[scheme], T=T, n_times=1)
@@ -523,7 +534,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=True, fp64=True):
+def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=True, fp64=True, knobs=None):
     """Headline-style measurement of one workload: autotuned knobs, the mixed
     step timed over exactly K steps (CUDA events on the launching stream,
     clocks sampled meanwhile), the FP64 step beside it, the fused kernel's
@@ -532,12 +543,15 @@ def time_workload(torch, cgdem, s, K, W, barrier, device, world, local, tune_on=
     only every few tens of steps (when a sphere may have moved half the
     skin), so a short timed window holds more or fewer rebuilds than its
     share: the window's time is also reported with its rebuilds replaced by
-    the natural rate measured over a longer stretch (`amortised`)."""
+    the natural rate measured over a longer stretch (`amortised`).  knobs
+    (cell_scale, block, skin_frac, ppw), if given, replace the autotuner."""
     N = len(s.R)
     dt, skin = step_params(s)
     tune = {"cell_scale": 0.35, "block": 128, "skin_frac": 0.02, "ppw": 32, "cached": False,
             "trials": []}
-    if tune_on:
+    if knobs is not None:
+        tune.update(knobs)
+    elif tune_on:
         from paper_2211_06142_gb300 import autotune as A
         t0 = time.perf_counter()
         tune = A.autotune([cgdem.sample_params(s, dt, skin)], [N], (s.x, s.v, s.w, s.R), s.Us,
@@ -658,6 +672,18 @@ def fp64_roofline(n_act, force_ms):
             "counted_on": c.get("workload")}
 
 
+def make_scale_cube(seed):
+    """About 4.3M fine-PSD spheres in a periodic cube: 7^3 copies of one packed
+    periodic block of 12,500 (solid fraction 0.55), a uniform upward flow of
+    0.01 m/s, fluid cells of the 2,000-sphere cube's size (0.32 mm)."""
+    import math
+    from paper_2211_06142_gb300 import inputs as I
+    Rb = 0.5 * I.fine_diameters(12_500, 7 + seed)
+    Lb = (float((4.0 / 3.0 * math.pi * Rb ** 3).sum()) / 0.55) ** (1.0 / 3.0)
+    nf = int(round(7 * Lb / 0.3175e-3))
+    return I.cached(I.tiled_periodic, 12_500, 7, 7 + seed, nf)
+
+
 def run_e2e(torch, cgdem, s, knobs, skin, K, device, barrier, world):
     """The same metric end to end through the public API: pinned host
     buffers in, initialisation (porosity, contact list, bonds), K steps, the
@@ -698,9 +724,17 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-sand", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--sand-2m", action="store_true",
+                    help="only the produced-sand comparison of the 2M-sphere cylinder and its SSW k = 3 "
+                         "model with and without the learned closure (a few minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sand_2m:
+        from paper_2211_06142_gb300 import build as B
+        B.build()
+        print(json.dumps({"sand_2m": run_sand(pair="2m")}), flush=True)
         return
 
     import torch
@@ -741,6 +775,14 @@ def main():
                             tune=not args.no_tune)
             b["roofline_frac"] = b["force_kernel_gbs"] / measured_peaks()[0]["hbm_gbs"]
             extras["batched"] = b
+        # the 4.3M-sphere periodic cube at the headline's knobs, mixed and FP64
+        s4 = make_scale_cube(1 + rank)
+        hk = head["autotune"]
+        extras["scale_cube"] = time_workload(
+            torch, cgdem, s4, K, W, barrier, device, world, local,
+            knobs={k: hk[k] for k in ("cell_scale", "block", "skin_frac", "ppw")})
+        extras["scale_cube"]["workload"] = "periodic cube of 7^3 tiles of a 12,500-sphere packing, uniform flow"
+        del s4
         extras["closure"] = run_closure_cost(torch, device, barrier, min(max(K, 500), 2000))
         extras["two_way_coupling"] = run_darcy(torch, device, barrier, min(max(K, 500), 2000))
         extras["preparation"] = run_prep(torch, device, barrier)

@@ -278,13 +278,17 @@ def cached(fn, *args, **kw) -> Sample:
     return s
 
 
-def _tile_block(n_block: int, seed: int, phi: float = 0.55):
+def _tile_block(n_block: int, seed: int, phi: float = 0.55, d_map=None):
     """A periodic block of n_block fine-PSD spheres packed at solid fraction
     phi: diameters, positions in [0, L)^3 and L.  Copies of a periodic packing
     placed side by side form a packing of the larger region with no seams
-    (every contact across a block face is a contact across the period)."""
+    (every contact across a block face is a contact across the period).
+    d_map, if given, maps the fine diameters to the ones packed (a
+    coarse-graining rule)."""
     rng = np.random.default_rng(seed + 3000)
     d = fine_diameters(n_block, seed)
+    if d_map is not None:
+        d = np.asarray(d_map(d), np.float64)
     R = 0.5 * d
     L = (float((4.0 / 3.0 * math.pi * R ** 3).sum()) / phi) ** (1.0 / 3.0)
     x = pack_periodic(R, L, rng)
@@ -293,7 +297,7 @@ def _tile_block(n_block: int, seed: int, phi: float = 0.55):
 
 def tiled_cylinder(n_target: int = 2_000_000, scale: float = 2.15, seed: int = 4,
                    n_block: int = 65_536, d50: float = 0.25e-3, U_in: float = 1e-4,
-                   nf=(86, 86, 43)) -> Sample:
+                   nf=(86, 86, 43), d_map=None, h_bed: float = 0.0, name: str = "cylinder-tiled") -> Sample:
     """The sand-production cylinder scaled by `scale` in radius and height
     (radius 40 d50 scale, height 30 d50 scale, outlet 3 d50, fluid cells of
     the 200k-sphere cylinder's size), holding about n_target spheres of the
@@ -301,13 +305,17 @@ def tiled_cylinder(n_target: int = 2_000_000, scale: float = 2.15, seed: int = 4
     n_block spheres tile the region, and the spheres whose centres lie in
     the bed annulus (r_out + R <= r <= Rc - R, R <= z <= h_bed) are kept.
     Packing n_target spheres directly takes the host packer tens of minutes;
-    the tiled bed repeats the block's arrangement every block edge."""
-    Rb, xb, Lb = _tile_block(n_block, seed)
+    the tiled bed repeats the block's arrangement every block edge.
+    A coarse-grained counterpart packs its block with the diameters d_map
+    gives and fills the bed height h_bed of the fine sample (n_target is
+    then unused)."""
+    Rb, xb, Lb = _tile_block(n_block, seed, d_map=d_map)
     Vmean = float((4.0 / 3.0 * math.pi * Rb ** 3).mean())
     Rc = 40.0 * d50 * scale
     H = 30.0 * d50 * scale
     r_out = 3.0 * d50
-    h_bed = n_target * Vmean / (0.55 * math.pi * (Rc ** 2 - r_out ** 2))
+    if not h_bed > 0.0:
+        h_bed = n_target * Vmean / (0.55 * math.pi * (Rc ** 2 - r_out ** 2))
     if not h_bed <= H:
         raise ValueError("the scaled cylinder cannot hold n_target spheres at solid fraction 0.55")
     nxy = int(math.ceil(2 * Rc / Lb))
@@ -327,9 +335,20 @@ def tiled_cylinder(n_target: int = 2_000_000, scale: float = 2.15, seed: int = 4
     grid = FluidGrid(tuple(nf), (-Rc, -Rc, 0.0), h)
     mat = dict(rho=2650.0, E=1e8, nu=0.3, e=0.5, mu=0.5, gamma=0.5)
     dom = dict(kind=1, L=(2 * Rc, 2 * Rc, H), Rc=Rc, H=H, r_out=r_out)
-    return Sample(f"cylinder-tiled-{len(R)}", x, np.zeros_like(x), np.zeros_like(x), R, mat, dom,
+    return Sample(f"{name}-{len(R)}", x, np.zeros_like(x), np.zeros_like(x), R, mat, dom,
                   grid, radial_inflow_field(grid, U_in, Rc, r_out, h_bed),
-                  extra=dict(h_bed=h_bed, block_spheres=n_block, block_edge=Lb))
+                  extra=dict(h_bed=h_bed, block_spheres=len(Rb), block_edge=Lb))
+
+
+def tiled_bed_height(n_target: int = 2_000_000, scale: float = 2.15, seed: int = 4, n_block: int = 65_536,
+                     d50: float = 0.25e-3) -> float:
+    """The bed height tiled_cylinder fills with n_target fine spheres (the
+    block's mean sphere volume at solid fraction 0.55 over the annulus)."""
+    Rb = 0.5 * fine_diameters(n_block, seed)
+    Vmean = float((4.0 / 3.0 * math.pi * Rb ** 3).mean())
+    Rc = 40.0 * d50 * scale
+    r_out = 3.0 * d50
+    return n_target * Vmean / (0.55 * math.pi * (Rc ** 2 - r_out ** 2))
 
 
 def tiled_periodic(n_block: int = 12_500, reps: int = 2, seed: int = 8, nf: int = 16,

@@ -5,6 +5,9 @@ grain-level samples with the library's own coarse-graining rule
 * ``fine_cylinder``: 200k-sphere sand-production cylinder (k = 1).
 * ``coarse_cylinder``: the same sand at ratio k under SSW or SSP
   (N_g = N_p / k^3, gamma_g = k gamma), same domain and fluid grid.
+* ``coarse_tiled_cylinder``: the 2M-sphere tiled cylinder's coarse
+  counterpart at ratio k (about 74k SSW parcels at k = 3), same domain,
+  bed height and fluid grid.
 * ``ensemble``: a calibration sweep of many independent samples of uneven
   size, PSD, cohesion, coarse-graining ratio and domain kind.
 """
@@ -52,3 +55,17 @@ def coarse_cylinder(n_fine: int = 200_000, seed: int = 1, k: int = 2, scheme: st
                     U_in: float = 1e-4):
     """The sand-production cylinder coarse-grained at ratio k (SSW or SSP)."""
     return I.cached(_coarse_cylinder, n_fine, seed, k, scheme, U_in)
+
+
+def _coarse_tiled_cylinder(n_fine, scale, seed, k, scheme):
+    h_bed = I.tiled_bed_height(n_fine, scale, seed)
+    return I.tiled_cylinder(n_fine, scale, seed, d_map=lambda d: cgdem.cgdem_cg_scale_diameters(d, k, SCHEME[scheme]),
+                            h_bed=h_bed, name=f"cylinder-tiled-{scheme}-k{k}")
+
+
+def coarse_tiled_cylinder(n_fine: int = 2_000_000, scale: float = 2.15, seed: int = 4, k: int = 3,
+                          scheme: str = "ssw"):
+    """The tiled cylinder of n_fine spheres (``inputs.tiled_cylinder``) coarse-
+    grained at ratio k: its periodic block's grains mapped by the rule (N/k^3
+    parcels under SSW), tiled over the same bed height."""
+    return I.cached(_coarse_tiled_cylinder, n_fine, scale, seed, k, scheme)

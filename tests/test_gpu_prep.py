@@ -166,7 +166,10 @@ def test_penetrometer_follows_the_oracle(prec):
 def test_preparation_sequence(prec):
     """The whole sequence of Sec. 3.1 on a small whole bed (no cavity, 10,000
     grains, about eight grains deep):
-    generation with the original JKR, compression to the target stress,
+    generation with the original JKR, compression to the target stress (the
+    paper's overburden stress over Young's modulus, 5 kPa for these grains;
+    a stress far above it, with the default driving force that follows from
+    it, crushes grains between the tool and the bottom),
     bonds on the touching pairs, perforation by a force-driven penetrometer
     and its removal.  What each stage must leave: the stress reached with
     the plate at rest and the bed denser; every grain with bonds on average
@@ -182,12 +185,13 @@ def test_preparation_sequence(prec):
     ctx.init_particles(s.x, s.v, s.w, s.R, bond_touching=False)
     ctx.compute_forces()
     por0 = prep.porosity_under_plate(s.R, s.domain["Rc"], float((s.x[:, 2] + s.R).max()))
-    rec = prep.prepare(ctx, s, gen_steps=3000, stress=2e5, vmax=0.2, max_compress_steps=40000,
+    sigma = prep.scaled_stress(s.material["E"])
+    rec = prep.prepare(ctx, s, gen_steps=3000, stress=sigma, vmax=0.2, max_compress_steps=40000,
                        pen_radius=0.75e-3, pen_speed=0.5, chunk=200)
     print(rec)
     c, b, f = rec["compression"], rec["bonding"], rec["perforation"]
-    assert c["converged"] and abs(c["stress"] - 2e5) <= 0.02 * 2e5
-    assert c["porosity"] < por0 - 0.1
+    assert c["converged"] and abs(c["stress"] - sigma) <= 0.02 * sigma
+    assert c["porosity"] < por0 - 0.05
     assert b["per_grain_mean"] > 3
     assert f["removed"] and f["bonds_broken"] > 0.05 * b["bonds"]
     assert f["deepest_tip"] < 0.5 * c["H"]
