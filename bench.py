@@ -687,11 +687,14 @@ def make_scale_cube(seed):
 def run_e2e(torch, cgdem, s, knobs, skin, K, device, barrier, world):
     """The same metric end to end through the public API: pinned host
     buffers in, initialisation (porosity, contact list, bonds), K steps, the
-    state (x, v, w, F, T) read back, all inside the timed region."""
+    state (x, v, w, F, T) read back into pinned host buffers, all inside the
+    timed region.  The context (device workspace and its captured step
+    graphs) is created before it."""
     N = len(s.R)
     dt, _ = step_params(s)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
     hx, hv, hw, hR = pin(s.x), pin(s.v), pin(s.w), pin(s.R)
+    hout = {k: pin(np.zeros((N, 3))) for k in ("x", "v", "w", "F", "T")}
     p = cgdem.sample_params(s, dt, skin)
     ctx = cgdem.Context([p], [N], precision=cgdem.MIXED, max_neighbors=48, device=device,
                         block_size=knobs["block"], cell_scale=knobs["cell_scale"],
@@ -703,7 +706,7 @@ def run_e2e(torch, cgdem, s, knobs, skin, K, device, barrier, world):
     ctx.init_particles(hx, hv, hw, hR, bond_touching=True)
     ctx.compute_forces()
     ctx.step(K)
-    st = ctx.get_state()
+    st = ctx.get_state(out=hout)
     t1 = time.perf_counter()
     barrier()
     ctx.close()

@@ -271,6 +271,18 @@ int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream);
  * by the next readback or cgdem_status_sync. */
 int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream);
 
+/* Capture and upload on stream every CUDA graph that cgdem_step replays
+ * there (the opening half kick, the block of steps_per_graph steps, the
+ * blocks of the powers of two below it, the closing step), which cgdem_step
+ * otherwise does at its first call on that stream.  Needs no particles: a
+ * caller can pay the captures at creation instead of in the first step.
+ * Graphs are captured again after cgdem_set_closure, cgdem_closure_record
+ * and the first cgdem_set_stage, which change the kernels' variants.
+ * A context without particles (N = 0) captures nothing.  Errors:
+ * CGDEM_E_INVALID (null ctx), CGDEM_E_CUDA (capture or upload failed; the
+ * message says which). */
+int cgdem_prepare(cgdem_ctx* ctx, void* stream);
+
 /* ---------------------------------------------------------------------
  * Readback (HOST arrays, id order).  Synchronise stream.
  * ------------------------------------------------------------------- */

@@ -33,7 +33,7 @@ EXPORTS = [
     "cgdem_rayleigh_dt", "cgdem_cg_scale_diameters", "cgdem_workspace_size", "cgdem_create",
     "cgdem_destroy", "cgdem_last_error", "cgdem_status_sync", "cgdem_init_particles",
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
-    "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_get_state",
+    "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_prepare", "cgdem_get_state",
     "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step", "cgdem_set_psd_classes", "cgdem_get_produced_psd", "cgdem_get_fluid",
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
@@ -130,6 +130,7 @@ def lib():
             "cgdem_compute_forces": (i, [vp, vp]),
             "cgdem_integrate": (i, [vp, i, vp]),
             "cgdem_step": (i, [vp, i64, vp]),
+            "cgdem_prepare": (i, [vp, vp]),
             "cgdem_get_state": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "cgdem_get_contacts": (i, [vp, vp, vp, vp, i64, vp, vp]),
             "cgdem_get_contact_springs": (i, [vp, vp, vp, vp, i64, vp, vp]),
@@ -349,7 +350,9 @@ class Context:
 
     def __init__(self, params, counts, precision=MIXED, max_neighbors=48, block_size=128,
                  cell_scale=0.0, steps_per_graph=32, device="cuda:0", stream=None, closure=False,
-                 particles_per_warp=32, fluid_iters=0, fluid_tol=0.0, fluid_kernels=0):
+                 particles_per_warp=32, fluid_iters=0, fluid_tol=0.0, fluid_kernels=0, prepare=True):
+        """prepare: capture the step graphs on the context's stream now
+        (cgdem_prepare), so that the first step() replays them."""
         import torch
 
         if not torch.cuda.is_available():
@@ -381,6 +384,8 @@ class Context:
             raise CgdemError(r, "create failed")
         self.h = h
         self.stream = stream
+        if prepare:
+            self.prepare()
 
     def _s(self):
         if self.stream is not None:
@@ -433,11 +438,25 @@ class Context:
     def step(self, n=1):
         self._check(lib().cgdem_step(self.h, int(n), self._s()), "step")
 
+    def prepare(self):
+        """Capture and upload the step graphs on the context's stream."""
+        self._check(lib().cgdem_prepare(self.h, self._s()), "prepare")
+
     # ---- readback ----
-    def get_state(self):
-        out = [np.zeros((self.N, 3)) for _ in range(5)]
-        self._check(lib().cgdem_get_state(self.h, *[_ptr(a) for a in out], self._s()), "get_state")
-        return dict(zip(["x", "v", "w", "F", "T"], out))
+    def get_state(self, out=None):
+        """x, v, w, F, T in id order.  out: a dict of five (N, 3) float64
+        C-contiguous arrays to fill (pinned host memory makes the copies
+        several times faster than fresh pageable arrays)."""
+        keys = ["x", "v", "w", "F", "T"]
+        if out is None:
+            arrs = [np.zeros((self.N, 3)) for _ in keys]
+        else:
+            arrs = [out[k] for k in keys]
+            for a in arrs:
+                if a.dtype != np.float64 or a.shape != (self.N, 3) or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("get_state: out arrays must be float64, C-contiguous, of shape (N, 3)")
+        self._check(lib().cgdem_get_state(self.h, *[_ptr(a) for a in arrs], self._s()), "get_state")
+        return dict(zip(keys, arrs))
 
     def get_contacts(self):
         n = C.c_int64(0)

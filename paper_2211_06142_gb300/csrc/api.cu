@@ -25,6 +25,7 @@ void launch_clear_wall_history(const Dev& d, int sample, int wall, cudaStream_t 
 void launch_kick_final(const Dev& d, cudaStream_t s);
 void launch_cube_after_mid(const Dev& d, cudaStream_t s);
 void launch_init(const Dev& d, cudaStream_t s);
+void launch_init_check(const Dev& d, cudaStream_t s);
 void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
 void launch_fluid_mark(const Dev& d, cudaStream_t s);
@@ -172,6 +173,7 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   // (original JKR) of the largest pair < skin / 2
   if (p.jkr_mode != 0 && p.jkr_mode != 1) return fail(ctx, CGDEM_E_INVALID, "jkr_mode must be 0 or 1");
   s.jkr_mode = p.jkr_mode;
+  s.r_max = p.r_max;
   {
     const double dC = jkr_reach(s.gamma, s.Es, 0.5 * p.r_max, p.jkr_mode);
     if (!(2.0 * dC < p.skin))
@@ -895,16 +897,6 @@ int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const
   if (!ctx || (!x && ctx->d.N) || (!v && ctx->d.N) || (!w && ctx->d.N) || (!R && ctx->d.N))
     return CGDEM_E_INVALID;
   const size_t N = ctx->d.N;
-  for (int s = 0; s < ctx->d.n_samples; ++s) {
-    const SampleDev& S = ctx->sd[s];
-    for (int64_t i = S.first; i < S.first + S.count; ++i) {
-      if (!(R[i] > 0) || !(R[i] <= ctx->sp[s].r_max))
-        return fail(ctx, CGDEM_E_INVALID, "radius of particle %lld outside (0, r_max]", (long long)i);
-      if (!std::isfinite(x[3 * i] + x[3 * i + 1] + x[3 * i + 2] + v[3 * i] + v[3 * i + 1] +
-                         v[3 * i + 2] + w[3 * i] + w[3 * i + 1] + w[3 * i + 2]))
-        return fail(ctx, CGDEM_E_NONFINITE, "non-finite state of particle %lld", (long long)i);
-    }
-  }
   cudaStream_t s = st(stream);
   double* stg = ctx->d.staging;
   if (N) {
@@ -912,6 +904,21 @@ int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const
     CK(cudaMemcpyAsync(stg + 3 * N, v, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(stg + 6 * N, w, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(stg + 9 * N, R, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    // the inputs are checked on the device, before any kernel bins them: the
+    // lowest index with a radius outside (0, r_max], and the lowest with a
+    // non-finite position, velocity or angular velocity
+    long long* bad = &ctx->d.ctl->init_bad_r;
+    CK(cudaMemsetAsync(bad, 0x7f, 2 * sizeof(long long), s));
+    launch_init_check(ctx->d, s);
+    long long hb[2];
+    CK(cudaMemcpyAsync(hb, bad, sizeof hb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const long long i = std::min(hb[0], hb[1]);
+    if (i < (long long)N) {
+      if (hb[0] == i)
+        return fail(ctx, CGDEM_E_INVALID, "radius of particle %lld outside (0, r_max]", i);
+      return fail(ctx, CGDEM_E_NONFINITE, "non-finite state of particle %lld", i);
+    }
   }
   launch_init(ctx->d, s);
   for (int b = 0; b < 3; ++b)
@@ -975,6 +982,12 @@ int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream) {
   else return fail(ctx, CGDEM_E_INVALID, "half must be 0 or 1");
   CK(cudaGetLastError());
   return CGDEM_OK;
+}
+
+int cgdem_prepare(cgdem_ctx* ctx, void* stream) {
+  if (!ctx) return CGDEM_E_INVALID;
+  if (ctx->d.N == 0) return CGDEM_OK;
+  return prepare_parts(ctx, st(stream));
 }
 
 int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream) {

@@ -91,6 +91,7 @@ struct SampleDev {
   double psd_edge[CGDEM_PSD_MAX + 1];
   double psd_mq;
   int jkr_mode;  // 0 modified JKR, 1 original JKR (cgdem_sample_params)
+  double r_max;  // largest radius the sample admits
 };
 
 // A preparation stage's moving boundaries of one sample (cgdem_set_stage),
@@ -156,6 +157,9 @@ struct Ctl {
   // block sets when its wait gave up (the others then stop waiting too)
   unsigned fl_bar_count, fl_bar_gen;
   int fl_abort;
+  // input check of cgdem_init_particles: the lowest index of a particle with
+  // a radius outside (0, r_max] and of one with a non-finite state
+  long long init_bad_r, init_bad_f;
 };
 constexpr double DARCY_N_CAP = 0.95;  // the permeability's porosity cap
 

@@ -1026,6 +1026,32 @@ __global__ void k_step_inc(Dev d) { d.ctl->step += 1; }
 // ---------------------------------------------------------------------------
 
 // staging layout (doubles): x[3N] v[3N] w[3N] R[N]
+// The inputs of cgdem_init_particles: a radius outside (0, r_max] of its
+// sample, or a non-finite sum of the nine state components (summed x, y, z
+// of x, v, w in order), records the particle's index; the host reads the
+// lowest of each.
+__global__ void k_init_check(Dev d) {
+  const double* st = d.staging;
+  const long long N = d.N;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    int s = 0;
+    while (s + 1 < d.n_samples && p >= d.sp[s + 1].first) ++s;
+    const double R = st[9 * N + p];
+    if (!(R > 0.0) || !(R <= d.sp[s].r_max)) atomicMin(&d.ctl->init_bad_r, p);
+    double t = st[3 * p];
+    t = __dadd_rn(t, st[3 * p + 1]);
+    t = __dadd_rn(t, st[3 * p + 2]);
+    for (int k = 1; k < 3; ++k) {
+      const double* a = st + 3 * N * k + 3 * p;
+      t = __dadd_rn(t, a[0]);
+      t = __dadd_rn(t, a[1]);
+      t = __dadd_rn(t, a[2]);
+    }
+    if (!isfinite(t)) atomicMin(&d.ctl->init_bad_f, p);
+  }
+}
+
 __global__ void k_init_state(Dev d) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= d.N) return;
@@ -1370,6 +1396,11 @@ void launch_closure_set(const Dev& d, int enable, int record, cudaStream_t s) {
 
 void launch_closure_gather(const Dev& d, cudaStream_t s) {
   if (d.N) k_closure_gather<<<nblk(d.N, 256), 256, 0, s>>>(d);
+}
+
+void launch_init_check(const Dev& d, cudaStream_t s) {
+  const int g = nblk(d.N, 256);
+  if (d.N) k_init_check<<<g < 152 * 8 ? g : 152 * 8, 256, 0, s>>>(d);
 }
 
 void launch_init(const Dev& d, cudaStream_t s) {

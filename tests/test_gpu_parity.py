@@ -4,6 +4,8 @@ Bars: contact pair lists and porosity cell sums bit-exact; per-step forces
 normwise within 1e-10 (FP64) and 1e-4 (mixed) of the oracle, the norm being
 the sum of the magnitudes of every force term on the particle.
 """
+import re
+
 import numpy as np
 import pytest
 
@@ -382,3 +384,67 @@ def test_cube_porosity_coarse_grains(prec):
     if prec == cgdem.FP64:
         check_contacts(ctx, sim)
         assert np.array_equal(ctx.get_voidfrac(s.grid.ncell), sim.voidfrac())
+
+
+def test_init_rejects_a_bad_radius_or_state_by_the_lowest_index(periodic):
+    """init_particles checks its inputs on the device before anything bins
+    them: the lowest particle with a radius outside (0, r_max] or a
+    non-finite state is named (the radius test first at equal index), the
+    context stays uninitialised, and valid inputs then initialise it."""
+    s = periodic
+    ctx = cgdem.Context([cgdem.sample_params(s, default_dt(s), default_skin(s))], [len(s.R)],
+                        precision=cgdem.MIXED, max_neighbors=64)
+    ctx.set_fluid_velocity(s.Us)
+    cases = []
+    R = s.R.copy()
+    R[700] = 2.0 * s.R.max()
+    R[900] = -1.0
+    cases.append(((s.x, s.v, s.w, R), cgdem.CGDEM_E_INVALID, 700))
+    v = s.v.copy()
+    v[500, 1] = np.nan
+    cases.append(((s.x, v, s.w, R), cgdem.CGDEM_E_NONFINITE, 500))
+    w = s.w.copy()
+    w[300, 2] = np.inf
+    R2 = s.R.copy()
+    R2[300] = 0.0
+    cases.append(((s.x, s.v, w, R2), cgdem.CGDEM_E_INVALID, 300))
+    x = s.x.copy()
+    x[len(s.R) - 1, 0] = -np.inf
+    cases.append(((x, s.v, s.w, s.R), cgdem.CGDEM_E_NONFINITE, len(s.R) - 1))
+    for args, code, idx in cases:
+        with pytest.raises(cgdem.CgdemError) as e:
+            ctx.init_particles(*args)
+        assert e.value.code == code and re.search(rf"particle {idx}\b", str(e.value)), str(e.value)
+        with pytest.raises(cgdem.CgdemError) as e:
+            ctx.step(1)
+        assert e.value.code == cgdem.CGDEM_E_STATE
+    ctx.init_particles(s.x, s.v, s.w, s.R)
+    ctx.step(3)
+    assert np.isfinite(ctx.get_state()["x"]).all()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_prepared_graphs_give_the_same_steps(periodic, prec):
+    """A context that captured its step graphs at construction (prepare)
+    steps bit-identically to one that captures them at its first step, and
+    both read back into caller-provided arrays as into fresh ones."""
+    s = periodic
+    out = []
+    for prep in (True, False):
+        ctx = cgdem.Context([cgdem.sample_params(s, default_dt(s), default_skin(s))], [len(s.R)],
+                            precision=prec, max_neighbors=64, prepare=prep)
+        ctx.set_fluid_velocity(s.Us)
+        ctx.init_particles(s.x, s.v, s.w, s.R)
+        ctx.compute_forces()
+        ctx.step(45)
+        buf = {k: np.full((len(s.R), 3), np.nan) for k in ("x", "v", "w", "F", "T")}
+        got = ctx.get_state(out=buf)
+        assert all(got[k] is buf[k] for k in buf)
+        fresh = ctx.get_state()
+        for k in buf:
+            assert np.array_equal(buf[k], fresh[k])
+        out.append(fresh)
+        ctx.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
