@@ -271,6 +271,14 @@ int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream);
  * by the next readback or cgdem_status_sync. */
 int cgdem_step(cgdem_ctx* ctx, int64_t nsteps, void* stream);
 
+/* Self-check of the FP64 step's own reciprocal and cube root (Newton-
+ * Raphson iteration from a single-precision seed, used by the FP64 contact
+ * law for values that feed forces only).  x: n DEVICE doubles; out: 4 n
+ * DEVICE doubles, out[4i..4i+3] = the step's 1/x, CUDA's 1.0 / x, the
+ * step's cbrt(|x|), CUDA's cbrt(|x|).  Asynchronous on stream.  Errors:
+ * CGDEM_E_INVALID (n < 0, or a null pointer with n > 0), CGDEM_E_CUDA. */
+int cgdem_fp64_math_check(const double* x, int64_t n, double* out, void* stream);
+
 /* Capture and upload on stream every CUDA graph that cgdem_step replays
  * there (the opening half kick, the block of steps_per_graph steps, the
  * blocks of the powers of two below it, the closing step), which cgdem_step
@@ -287,7 +295,9 @@ int cgdem_prepare(cgdem_ctx* ctx, void* stream);
  * Readback (HOST arrays, id order).  Synchronise stream.
  * ------------------------------------------------------------------- */
 
-/* Any pointer may be NULL.  Arrays are [N,3]. */
+/* Any pointer may be NULL.  Arrays are [N,3], owned by the caller (pinned
+ * host memory makes the device-to-host copies faster).  Returns after the
+ * stream has synchronised. */
 int cgdem_get_state(cgdem_ctx* ctx, double* x, double* v, double* w, double* F, double* T,
                     void* stream);
 

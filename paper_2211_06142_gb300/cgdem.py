@@ -33,7 +33,8 @@ EXPORTS = [
     "cgdem_rayleigh_dt", "cgdem_cg_scale_diameters", "cgdem_workspace_size", "cgdem_create",
     "cgdem_destroy", "cgdem_last_error", "cgdem_status_sync", "cgdem_init_particles",
     "cgdem_set_fluid_velocity", "cgdem_build_contacts", "cgdem_couple_fluid",
-    "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_prepare", "cgdem_get_state",
+    "cgdem_compute_forces", "cgdem_integrate", "cgdem_step", "cgdem_prepare", "cgdem_fp64_math_check",
+    "cgdem_get_state",
     "cgdem_get_contacts", "cgdem_get_contact_springs", "cgdem_get_voidfrac", "cgdem_get_diagnostics", "cgdem_get_removed_step", "cgdem_set_psd_classes", "cgdem_get_produced_psd", "cgdem_get_fluid",
     "cgdem_get_counters", "cgdem_get_launch_counts", "cgdem_profile_step", "cgdem_touching_pairs_noalloc",
     "cgdem_mlp_workspace_size", "cgdem_mlp_forward", "cgdem_mlp_train_step", "cgdem_mlp_status",
@@ -131,6 +132,7 @@ def lib():
             "cgdem_integrate": (i, [vp, i, vp]),
             "cgdem_step": (i, [vp, i64, vp]),
             "cgdem_prepare": (i, [vp, vp]),
+            "cgdem_fp64_math_check": (i, [vp, i64, vp, vp]),
             "cgdem_get_state": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "cgdem_get_contacts": (i, [vp, vp, vp, vp, i64, vp, vp]),
             "cgdem_get_contact_springs": (i, [vp, vp, vp, vp, i64, vp, vp]),
@@ -183,6 +185,21 @@ def cgdem_cg_scale_diameters(d_fine, k, scheme):
     if r:
         raise CgdemError(r, "cg_scale_diameters")
     return out[: n.value].copy()
+
+
+def fp64_math_check(x):
+    """The FP64 step's reciprocal and cube root beside CUDA's, on the GPU:
+    returns (nr_rcp(x), 1/x, nr_cbrt(|x|), cbrt(|x|)) as numpy arrays."""
+    import torch
+
+    xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+    out = torch.empty(4 * xd.numel(), dtype=torch.float64, device="cuda")
+    r = lib().cgdem_fp64_math_check(C.c_void_p(xd.data_ptr()), xd.numel(), C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if r:
+        raise CgdemError(r, "fp64_math_check")
+    o = out.view(-1, 4).cpu().numpy()
+    return o[:, 0], o[:, 1], o[:, 2], o[:, 3]
 
 
 def cgdem_touching_pairs_noalloc(x_dev, R_dev, n, box_lo, box_hi, periodic, r_max, skin,

@@ -26,6 +26,7 @@ void launch_kick_final(const Dev& d, cudaStream_t s);
 void launch_cube_after_mid(const Dev& d, cudaStream_t s);
 void launch_init(const Dev& d, cudaStream_t s);
 void launch_init_check(const Dev& d, cudaStream_t s);
+void launch_fp64_math_check(const double* x, int64_t n, double* out, cudaStream_t s);
 void launch_gather_state(const Dev& d, cudaStream_t s);
 void launch_collect_contacts(const Dev& d, uint32_t* out, unsigned long long cap, cudaStream_t s);
 void launch_fluid_mark(const Dev& d, cudaStream_t s);
@@ -286,8 +287,11 @@ int derive_sample(cgdem_ctx* ctx, const cgdem_config* cfg, const cgdem_sample_pa
   s.psd_mq = std::ldexp(p.rho * (4.0 / 3.0 * PI) * p.r_max * p.r_max * p.r_max, -40);
   {
     const double cd = 2.0 * std::sqrt(5.0 / 6.0);
-    s.cdbn_f = (float)(cd * s.beta * std::sqrt(2.0 * s.Es));
-    s.cdbt_f = (float)(cd * s.beta * std::sqrt(8.0 * s.Gs));
+    s.cdbn = cd * s.beta * std::sqrt(2.0 * s.Es);
+    s.cdbt = cd * s.beta * std::sqrt(8.0 * s.Gs);
+    s.cdbn_f = (float)s.cdbn;
+    s.cdbt_f = (float)s.cdbt;
+    s.inv_Es = 1.0 / s.Es;
   }
   *out = s;
   return CGDEM_OK;
@@ -982,6 +986,12 @@ int cgdem_integrate(cgdem_ctx* ctx, int half, void* stream) {
   else return fail(ctx, CGDEM_E_INVALID, "half must be 0 or 1");
   CK(cudaGetLastError());
   return CGDEM_OK;
+}
+
+int cgdem_fp64_math_check(const double* x, int64_t n, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return CGDEM_E_INVALID;
+  launch_fp64_math_check(x, n, out, st(stream));
+  return cudaGetLastError() == cudaSuccess ? CGDEM_OK : CGDEM_E_CUDA;
 }
 
 int cgdem_prepare(cgdem_ctx* ctx, void* stream) {

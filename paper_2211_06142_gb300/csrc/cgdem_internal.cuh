@@ -78,6 +78,8 @@ struct SampleDev {
   // Eq. 32 and its tangential twin with the contact radius and reduced mass
   // factored out: gamma_n = cdbn sqrt(a m*), gamma_t = cdbt sqrt(a m*)
   float cdbn_f, cdbt_f;  // 2 sqrt(5/6) beta sqrt(2 E*), 2 sqrt(5/6) beta sqrt(8 G*)
+  double cdbn, cdbt;     // the same in FP64
+  double inv_Es;         // 1 / E*
   // produced sand by size class (Sec. 3.4): a grain of radius R stands for
   // fine grains of diameter 2 R / k; class c holds psd_edge[c] <= 2 R / k <
   // psd_edge[c + 1] (the first and last classes also take what lies below or

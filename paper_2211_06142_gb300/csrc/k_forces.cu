@@ -39,6 +39,12 @@ constexpr float PI_F = 3.14159265358979323846f;
 #ifndef CGDEM_FORCE_MINB
 #define CGDEM_FORCE_MINB 3  // resident 256-thread blocks per SM the register budget must allow
 #endif
+#ifndef CGDEM_PAIRS_MINB
+// the same for the FP64 kernel: it is bound by the FP64 pipe, and 128
+// registers a thread (two blocks) ran faster than 80 (three): 0.570 against
+// 0.610 ms on the 200k cylinder, 4.23 against 4.27 ms at 1.97M spheres
+#define CGDEM_PAIRS_MINB 2
+#endif
 constexpr int FORCE_BLOCK_MAX = 256;  // launches use 64, 128 or 256 threads (autotuned)
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -260,6 +266,144 @@ __device__ __forceinline__ void contact_law_mixed(float delta, V3<float> n, V3<f
     }
   }
   Fi = v3<float>(-Fn * n.x + Ft.x, -Fn * n.y + Ft.y, -Fn * n.z + Ft.z);
+}
+
+// Reciprocal and cube root in FP64 by Newton-Raphson iteration from an FP32
+// seed, in place of the IEEE divide and the library cube root, for results
+// that feed forces only (never an integer decision): the iteration converges
+// quadratically, so a seed good to about 2^-21 is good to about 2^-42 after
+// one step and to the rounding of the last step after two (within about one
+// ulp of the correctly rounded value).  The cube root's step uses the FP32
+// reciprocal of its derivative 3 x^2; the error that leaves in each step is
+// the derivative's (2^-21) times the step's own, so two steps still reach the
+// last bit.  Where the FP32 seed would not be a normal number they fall back
+// to the IEEE operation.
+__device__ __forceinline__ double nr_rcp(double b) {
+  const float bf = __double2float_rn(b);
+  if (!(fabsf(bf) >= 1e-30f && fabsf(bf) <= 1e30f)) return 1.0 / b;
+  double r = (double)__fdividef(1.0f, bf);
+  double e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-b, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ double nr_cbrt(double v) {
+  const float vf = __double2float_rn(v);
+  if (!(vf >= 1e-30f && vf <= 1e30f)) return cbrt(v);
+  double x = (double)m_cbrt(vf);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float xf = __double2float_rn(x);
+    const double r = (double)__fdividef(1.0f, 3.0f * xf * xf);
+    x = fma(-fma(x * x, x, -v), r, x);
+  }
+  return x;
+}
+
+// nr_rcp and nr_cbrt beside CUDA's 1 / x and cbrt(|x|) on n inputs:
+// out[4 i .. 4 i + 3] = nr_rcp(x), 1 / x, nr_cbrt(|x|), cbrt(|x|).
+__global__ void k_fp64_math_check(const double* x, int64_t n, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i], a = fabs(v);
+    out[4 * i] = nr_rcp(v);
+    out[4 * i + 1] = 1.0 / v;
+    out[4 * i + 2] = a > 0.0 ? nr_cbrt(a) : 0.0;
+    out[4 * i + 3] = cbrt(a);
+  }
+}
+
+void launch_fp64_math_check(const double* x, int64_t n, double* out, cudaStream_t s) {
+  if (n > 0) k_fp64_math_check<<<152 * 4, 256, 0, s>>>(x, n, out);
+}
+
+// The contact law of the FP64 step for the modified JKR and Hertz: the
+// terms of contact_law with the work shared as in the mixed law, in FP64.
+// The stable JKR branch (Eq. 12-13): a_A^3 = 4 pi gamma R*^2 / E* by nr_cbrt,
+// D = delta R* / a_A^2; u^4 - u = D is solved first in FP32 (three Newton
+// steps from (D + 1)^(1/4), to about 1e-7), then by two FP64 Newton steps
+// whose derivative reciprocal is taken in FP32 (the error left per step is
+// the reciprocal's 2^-21 times the step's own: 1e-7 -> 1e-13 -> 1e-19, and
+// 4 u^3 - 1 >= 2 on the branch, u >= u_C).  Damping (Eq. 32) and the
+// tangential dashpot share sqrt(a m*); the spring keeps its length with one
+// square root; the Coulomb test (Eq. 35) compares squares.
+__device__ __forceinline__ void contact_law_fp64(double delta, V3<double> n, V3<double> vrel, V3<double> vc,
+                                                 double Rs, double ms, double gamma, bool bonded,
+                                                 const SampleDev& S, V3<double>& xi, V3<double>& Fi,
+                                                 V3<double>& Ft) {
+  double a, Fne;
+  if (bonded && gamma > 0.0) {
+    const double aA = nr_cbrt(4.0 * PI_D * gamma * Rs * Rs * S.inv_Es);
+    const double D = delta * Rs * nr_rcp(aA * aA);
+    const float Df = __double2float_rn(D);
+    float uf = m_sqrt(m_sqrt(Df + 1.f));
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const float u3 = uf * uf * uf;
+      uf -= __fdividef(u3 * uf - uf - Df, 4.f * u3 - 1.f);
+    }
+    double u = (double)uf;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const double u3 = u * u * u;
+      const float u3f = __double2float_rn(u3);
+      const double r = (double)__fdividef(1.0f, 4.f * u3f - 1.f);
+      u = fma(-(fma(u3, u, -u) - D), r, u);
+    }
+    if (u < 0.90856029641606983) u = 0.90856029641606983;  // u_C
+    const double u3 = u * u * u;
+    a = u * u * aA;
+    Fne = PI_D * gamma * Rs * (16.0 / 3.0 * u3 * u3 - 8.0 * u3);
+  } else {
+    a = delta > 0.0 ? sqrt(Rs * delta) : 0.0;
+    Fne = (4.0 / 3.0) * S.Es * a * delta;
+  }
+  const double sq = sqrt(a * ms);
+  const double vn = dot3(vrel, n);
+  const double Fn = Fne - S.cdbn * sq * vn;  // Eq. 32
+  // tangential spring rotated into the tangent plane, Eq. 4
+  const double vcn = dot3(vc, n);
+  const V3<double> vt = v3<double>(vc.x - vcn * n.x, vc.y - vcn * n.y, vc.z - vcn * n.z);
+  const double old2 = dot3(xi, xi);
+  const double xn = dot3(xi, n);
+  xi.x -= xn * n.x;
+  xi.y -= xn * n.y;
+  xi.z -= xn * n.z;
+  const double nw2 = dot3(xi, xi);
+  if (nw2 > 0.0) {
+    const double sc = sqrt(old2 * nr_rcp(nw2));
+    xi.x *= sc;
+    xi.y *= sc;
+    xi.z *= sc;
+  } else {
+    xi = v3<double>(0, 0, 0);
+  }
+  const double dt = S.dt;
+  xi.x += vt.x * dt;
+  xi.y += vt.y * dt;
+  xi.z += vt.z * dt;
+  const double kt = 8.0 * S.Gs * a;
+  const double gt = S.cdbt * sq;
+  Ft = v3<double>(kt * xi.x + gt * vt.x, kt * xi.y + gt * vt.y, kt * xi.z + gt * vt.z);
+  const double FC = 3.0 * PI_D * gamma * Rs;  // Table 1
+  double Flim = S.coulomb_mode == 1 ? fabs(Fne) : (bonded ? Fne + 2.0 * FC : Fne);
+  if (Flim < 0.0) Flim = 0.0;
+  const double cap = S.mu * Flim;  // Eq. 35
+  const double ft2 = dot3(Ft, Ft);
+  if (ft2 > cap * cap) {
+    const double sc = cap * nr_rcp(sqrt(ft2));
+    Ft.x *= sc;
+    Ft.y *= sc;
+    Ft.z *= sc;
+    if (kt > 0.0) {
+      const double ik = nr_rcp(kt);
+      xi.x = (Ft.x - gt * vt.x) * ik;
+      xi.y = (Ft.y - gt * vt.y) * ik;
+      xi.z = (Ft.z - gt * vt.z) * ik;
+    }
+  }
+  Fi = v3<double>(-Fn * n.x + Ft.x, -Fn * n.y + Ft.y, -Fn * n.z + Ft.z);
 }
 
 // Di Felice drag (Eq. 8-11) written as (pi d^2 / 8) (0.63 sqrt(rho_f |w|)
@@ -995,7 +1139,7 @@ __device__ __forceinline__ void finish_step(
 // sits in a CUDA graph (0 otherwise); h_fluid: that of the step's Darcy-solve
 // node (0: none); the step's last warp sets both.
 template <int MODE, bool CL, bool PREP>
-__global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FORCE_MINB)
+__global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_PAIRS_MINB)
     k_forces_pairs(Dev d, cudaGraphConditionalHandle h_next,
     cudaGraphConditionalHandle h_fluid) {
   using T = double;
@@ -1167,10 +1311,10 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
             const double4 QV = d.vel[cur][q];
             const double4 QW = d.omg[cur][q];
             const double Ri = o.P.w, Rj = Q.w;
-            const double idist = 1.0 / dist;  // one FP64 division instead of three
+            const double idist = nr_rcp(dist);  // one reciprocal instead of three divisions
             const V3<double> n = v3<double>(dx * idist, dy * idist, dz * idist);
             // m* = m_i m_j / (m_i + m_j) = 1 / (1/m_i + 1/m_j), from the stored 1/m
-            const double ms = 1.0 / (o.V.w + QV.w);
+            const double ms = nr_rcp(o.V.w + QV.w);
             const V3<double> vrel = v3<double>(QV.x - o.V.x, QV.y - o.V.y, QV.z - o.V.z);
             const V3<double> rw = v3<double>(Ri * o.W.x + Rj * QW.x, Ri * o.W.y + Rj * QW.y,
                                              Ri * o.W.z + Rj * QW.z);
@@ -1178,8 +1322,11 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_FOR
             const V3<double> vc = v3<double>(vrel.x - rwn.x, vrel.y - rwn.y, vrel.z - rwn.z);
             V3<double> Fi, Ft;
             V3<double> xid = v3<double>((double)xi.x, (double)xi.y, (double)xi.z);
-            contact_law<double>(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S.Es, S.Gs, S.beta,
-                                S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft, orig);
+            if (orig)  // the original JKR's branch down to S (preparation stages)
+              contact_law<double>(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S.Es, S.Gs, S.beta,
+                                  S.mu, S.dt, S.coulomb_mode, xid, Fi, Ft, orig);
+            else
+              contact_law_fp64(delta, n, vrel, vc, Rs, ms, gam_d, bonded, S, xid, Fi, Ft);
             xi = v3<T>(xid.x, xid.y, xid.z);
             const V3<double> nFt = cross3(n, Ft);
             Fc = v3<T>(Fi.x, Fi.y, Fi.z);

@@ -114,3 +114,19 @@ def test_error_per_quantity(kind, prec):
     assert r["v"]["abs_max"] <= dt * tau * acc
     assert r["x"]["abs_max"] <= dt * dt * tau * acc
     ctx.close()
+
+
+def test_fp64_newton_reciprocal_and_cube_root_match_cuda():
+    """The FP64 contact law's reciprocal and cube root (Newton-Raphson from a
+    single-precision seed) agree with CUDA's correctly rounded 1 / x and its
+    cbrt to within 2 ulp, over the magnitudes the step meets and beyond
+    (1e-40 to 1e40, where the seed falls back to the IEEE operations at the
+    ends), both signs for the reciprocal."""
+    rng = np.random.default_rng(5)
+    x = 10.0 ** rng.uniform(-40, 40, 200_000) * rng.choice([-1.0, 1.0], 200_000)
+    x = np.concatenate([x, [1.0, -1.0, 3.0, 1e-30, 1e30, 2.0 ** -60, 7.0 / 3.0]])
+    r, r_ref, c, c_ref = cgdem.fp64_math_check(x)
+    ulp_r = np.abs(r - r_ref) / np.spacing(np.abs(r_ref))
+    ulp_c = np.abs(c - c_ref) / np.spacing(np.abs(c_ref))
+    assert ulp_r.max() <= 2.0, (ulp_r.max(), x[ulp_r.argmax()])
+    assert ulp_c.max() <= 2.0, (ulp_c.max(), x[ulp_c.argmax()])
