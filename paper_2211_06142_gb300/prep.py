@@ -68,7 +68,9 @@ def prepare(ctx, s, sample=0, gen_steps=2000, stress=PAPER_STRESS, vmax=0.05, ga
     driven by a force (by default 10 times the overburden stress on its
     cross-section) and turns back at pen_z_stop (by default one largest
     grain diameter above the bottom), or where it stalls against the grains
-    under its tip.  Returns
+    under its tip.  The stress should keep the paper's ratio to Young's
+    modulus (scaled_stress): far above it, the default driving force that
+    follows from it crushes grains between the tool and the bottom.  Returns
     what each stage did (steps, seconds, particle-steps/s, and the stage's
     own figures)."""
     import torch
