@@ -276,12 +276,33 @@ __device__ __forceinline__ void contact_law_mixed(float delta, V3<float> n, V3<f
 // ulp of the correctly rounded value).  The cube root's step uses the FP32
 // reciprocal of its derivative 3 x^2; the error that leaves in each step is
 // the derivative's (2^-21) times the step's own, so two steps still reach the
-// last bit.  Where the FP32 seed would not be a normal number they fall back
-// to the IEEE operation.
+// last bit.  Outside 2^-100 <= |x| < 2^101, where a seed could leave the
+// FP32 normal range, they fall back to the IEEE operation.
+//
+// The seeds move between FP64 and FP32 by integer operations on the bits
+// (seed_f truncates the mantissa; widen_f is exact for a normal float), and
+// tests of a double's sign, or the order of two non-negative doubles, compare
+// bit patterns as integers (exact): the FP64 step is bound by the FP64 pipe,
+// which runs conversions and floating-point compares as well as arithmetic.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool seed_range(double x) {
+  const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  return e - 923u <= 200u;
+}
+__device__ __forceinline__ float seed_f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = ((hi >> 20) & 0x7ffu) - 896u;
+  return __uint_as_float((hi & 0x80000000u) | (e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double widen_f(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned hi = (u & 0x80000000u) | ((((u >> 23) & 0xffu) + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 __device__ __forceinline__ double nr_rcp(double b) {
-  const float bf = __double2float_rn(b);
-  if (!(fabsf(bf) >= 1e-30f && fabsf(bf) <= 1e30f)) return 1.0 / b;
-  double r = (double)__fdividef(1.0f, bf);
+  if (!seed_range(b)) return 1.0 / b;
+  double r = widen_f(__fdividef(1.0f, seed_f(b)));
   double e = fma(-b, r, 1.0);
   r = fma(r, e, r);
   e = fma(-b, r, 1.0);
@@ -289,13 +310,12 @@ __device__ __forceinline__ double nr_rcp(double b) {
 }
 
 __device__ __forceinline__ double nr_cbrt(double v) {
-  const float vf = __double2float_rn(v);
-  if (!(vf >= 1e-30f && vf <= 1e30f)) return cbrt(v);
-  double x = (double)m_cbrt(vf);
+  if (!seed_range(v) || dbits(v) < 0) return cbrt(v);
+  double x = widen_f(m_cbrt(seed_f(v)));
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const float xf = __double2float_rn(x);
-    const double r = (double)__fdividef(1.0f, 3.0f * xf * xf);
+    const float xf = seed_f(x);
+    const double r = widen_f(__fdividef(1.0f, 3.0f * xf * xf));
     x = fma(-fma(x * x, x, -v), r, x);
   }
   return x;
@@ -333,30 +353,30 @@ __device__ __forceinline__ void contact_law_fp64(double delta, V3<double> n, V3<
                                                  const SampleDev& S, V3<double>& xi, V3<double>& Fi,
                                                  V3<double>& Ft) {
   double a, Fne;
-  if (bonded && gamma > 0.0) {
+  if (bonded && dbits(gamma) > 0) {
     const double aA = nr_cbrt(4.0 * PI_D * gamma * Rs * Rs * S.inv_Es);
     const double D = delta * Rs * nr_rcp(aA * aA);
-    const float Df = __double2float_rn(D);
+    const float Df = seed_range(D) ? seed_f(D) : __double2float_rn(D);
     float uf = m_sqrt(m_sqrt(Df + 1.f));
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
       const float u3 = uf * uf * uf;
       uf -= __fdividef(u3 * uf - uf - Df, 4.f * u3 - 1.f);
     }
-    double u = (double)uf;
+    double u = widen_f(uf);
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
       const double u3 = u * u * u;
-      const float u3f = __double2float_rn(u3);
-      const double r = (double)__fdividef(1.0f, 4.f * u3f - 1.f);
+      const double r = widen_f(__fdividef(1.0f, 4.f * seed_f(u3) - 1.f));
       u = fma(-(fma(u3, u, -u) - D), r, u);
     }
-    if (u < 0.90856029641606983) u = 0.90856029641606983;  // u_C
+    const double uC = 0.90856029641606983;  // u_C
+    if (dbits(u) < dbits(uC)) u = uC;
     const double u3 = u * u * u;
     a = u * u * aA;
     Fne = PI_D * gamma * Rs * (16.0 / 3.0 * u3 * u3 - 8.0 * u3);
   } else {
-    a = delta > 0.0 ? sqrt(Rs * delta) : 0.0;
+    a = dbits(delta) > 0 ? sqrt(Rs * delta) : 0.0;
     Fne = (4.0 / 3.0) * S.Es * a * delta;
   }
   const double sq = sqrt(a * ms);
@@ -371,7 +391,7 @@ __device__ __forceinline__ void contact_law_fp64(double delta, V3<double> n, V3<
   xi.y -= xn * n.y;
   xi.z -= xn * n.z;
   const double nw2 = dot3(xi, xi);
-  if (nw2 > 0.0) {
+  if (dbits(nw2) > 0) {
     const double sc = sqrt(old2 * nr_rcp(nw2));
     xi.x *= sc;
     xi.y *= sc;
@@ -388,15 +408,15 @@ __device__ __forceinline__ void contact_law_fp64(double delta, V3<double> n, V3<
   Ft = v3<double>(kt * xi.x + gt * vt.x, kt * xi.y + gt * vt.y, kt * xi.z + gt * vt.z);
   const double FC = 3.0 * PI_D * gamma * Rs;  // Table 1
   double Flim = S.coulomb_mode == 1 ? fabs(Fne) : (bonded ? Fne + 2.0 * FC : Fne);
-  if (Flim < 0.0) Flim = 0.0;
+  if (dbits(Flim) < 0) Flim = 0.0;
   const double cap = S.mu * Flim;  // Eq. 35
   const double ft2 = dot3(Ft, Ft);
-  if (ft2 > cap * cap) {
+  if (dbits(ft2) > dbits(cap * cap)) {
     const double sc = cap * nr_rcp(sqrt(ft2));
     Ft.x *= sc;
     Ft.y *= sc;
     Ft.z *= sc;
-    if (kt > 0.0) {
+    if (dbits(kt) > 0) {
       const double ik = nr_rcp(kt);
       xi.x = (Ft.x - gt * vt.x) * ik;
       xi.y = (Ft.y - gt * vt.y) * ik;
@@ -1277,11 +1297,11 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_PAI
 
       const int q = (int)(pf & REC_IDX);
       bool bonded = (pf & REC_BOND) != 0u;
-      const bool had_state = (pf & (REC_BOND | REC_ACTIVE)) != 0u || xi.x != T(0) ||
-                             xi.y != T(0) || xi.z != T(0);
+      const bool had_state = (pf & (REC_BOND | REC_ACTIVE)) != 0u ||
+                             ((dbits(xi.x) | dbits(xi.y) | dbits(xi.z)) & 0x7fffffffffffffffLL) != 0;
       bool act = false;
       const double4 Q = d.pos[cur][q];
-      if (Q.w > 0.0 && o.P.w > 0.0) {
+      if (dbits(Q.w) > 0 && dbits(o.P.w) > 0) {
         double dx = __dsub_rn(Q.x, o.P.x), dy = __dsub_rn(Q.y, o.P.y), dz = __dsub_rn(Q.z, o.P.z);
         if (S.kind == CGDEM_PERIODIC_BOX) {
           dx = min_image(dx, S.L[0]);
@@ -1291,7 +1311,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_PAI
         const double d2 =
             __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         const double Sd = __dadd_rn(o.P.w, Q.w);
-        const bool touching = d2 < __dmul_rn(Sd, Sd);
+        const bool touching = dbits(d2) < dbits(__dmul_rn(Sd, Sd));  // both >= 0
         if (bonded || touching) {
           const double dist = sqrt(d2);
           const double Rs = __dmul_rn(o.P.w, Q.w) / __dadd_rn(o.P.w, Q.w);
@@ -1307,7 +1327,7 @@ __global__ void __launch_bounds__(CL ? 128 : FORCE_BLOCK_MAX, CL ? 5 : CGDEM_PAI
             bonded = true;  // original JKR: the contact forms at A
           }
           act = bonded || touching;
-          if (act && dist > 0.0) {
+          if (act && dbits(dist) > 0) {
             const double4 QV = d.vel[cur][q];
             const double4 QW = d.omg[cur][q];
             const double Ri = o.P.w, Rj = Q.w;
