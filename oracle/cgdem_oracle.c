@@ -32,8 +32,7 @@
  * Parity unpinned (no value the paper prints or the mathematics fixes checks
  * these parts; the GPU is compared against them as written): the choice of
  * F_ne + 2 F_C as the Coulomb limit under cohesion (its positivity on the
- * JKR branch is pinned), the drag of a coarse grain, the cube porosity spread
- * (its volume conservation is pinned), the Kozeny-Carman permeability, the
+ * JKR branch is pinned), the drag of a coarse grain, the Kozeny-Carman permeability, the
  * plate's servo law (its equilibrium is pinned) and the closure hooks (not
  * part of the paper).
  */

@@ -3,8 +3,10 @@
 Each case plants one mistake in a scratch copy of the C oracle (a torque
 of the wrong sign, the spring turned the wrong way or not rescaled, the
 tangential dashpot twice as strong, the spin left out of the contact
-velocity, half the tangential stiffness), builds it, and runs the pins of
-the tangential law against it: at least one of them must fail.  The same
+velocity, half the tangential stiffness; the porosity cube spread with the
+sphere's diameter as its side, or its overlap measured from the wrong cell
+face), builds it, and runs the pins of the tangential law and the porosity
+spread against it: at least one of them must fail.  The same
 for the preparation stages (the original JKR separating at C or solved on
 the modified branch, the plate's servo of the wrong sign, the tool's
 normal without its axial part, the tool turning back late, its driving
@@ -32,6 +34,10 @@ MUTATIONS = {
         "        double rw[3] = {R * w[0], R * w[1], R * w[2]};",
         "        double rw[3] = {0.0 * w[0], 0.0 * w[1], 0.0 * w[2]};"),
     "half the tangential stiffness": ("    double kt = 8.0 * Gs * a;", "    double kt = 4.0 * Gs * a;"),
+    "cube spread with the sphere's diameter as its side": ("    double side = 2.0 * R * ORA_CUBE_SIDE;",
+                                                          "    double side = 2.0 * R;"),
+    "cube spread overlap measured from the wrong face": ("double o = fmin(hi[k], b1) - fmax(lo[k], b0);",
+                                                         "double o = fmin(hi[k], b1) - fmin(lo[k], b0);"),
 }
 
 # planted in the preparation stages, caught by tests/test_oracle_prep.py
@@ -52,7 +58,7 @@ PREP_MUTATIONS = {
                                      "                f = 1.0;"),
 }
 
-PINS = ("five_sevenths or frame_indifferent or tangent_plane or dashpot or mindlin or coulomb")
+PINS = ("five_sevenths or frame_indifferent or tangent_plane or dashpot or mindlin or coulomb or cube")
 
 
 @pytest.mark.parametrize("name", list(MUTATIONS) + list(PREP_MUTATIONS))

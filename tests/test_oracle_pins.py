@@ -391,6 +391,44 @@ def test_voidfrac_cube_overlap_conserves_volume():
     assert np.count_nonzero(S1) == 1 and S1[0] > 0
 
 
+@pytest.mark.parametrize("case", ["vertex", "face", "quarter", "wide"])
+def test_voidfrac_cube_spread_splits_by_the_overlap_fractions(case):
+    """The equal-volume cube's spread (R16) puts into each cell the fraction
+    of the sphere's volume that the cell cuts from the cube, worked out by
+    hand for symmetric placements: centred on a grid vertex, 1/8 in each of
+    8 cells; centred on a face, 1/2 and 1/2; a quarter side off a face, 3/4
+    and 1/4; a cube 1.5 cells wide centred in a cell, 1/6, 2/3, 1/6 along
+    each axis (27 cells, products of those).  Each part is rounded to one
+    quantum of 2^-40 cell volumes."""
+    nf, hf = 8, 1e-3
+    p = base_params(kind=0, L=(nf * hf,) * 3, nf=(nf,) * 3, hf=(hf,) * 3, inv_hf=(1 / hf,) * 3,
+                    V_cell=hf ** 3, vf_mode=1)
+    side = {"wide": 1.5 * hf}.get(case, 0.6 * hf)
+    R = (3.0 / (4.0 * math.pi)) ** (1 / 3) * side  # the sphere whose volume is side^3
+    V = side ** 3
+    h = hf
+    if case == "vertex":
+        x, want = (3 * h, 3 * h, 3 * h), {(i, j, k): 1 / 8 for i in (2, 3) for j in (2, 3) for k in (2, 3)}
+    elif case == "face":
+        x, want = (3 * h, 3.5 * h, 3.5 * h), {(2, 3, 3): 0.5, (3, 3, 3): 0.5}
+    elif case == "quarter":
+        x, want = (3 * h - side / 4, 3.5 * h, 3.5 * h), {(2, 3, 3): 0.75, (3, 3, 3): 0.25}
+    else:
+        f = {2: 1 / 6, 3: 2 / 3, 4: 1 / 6}
+        x = (3.5 * h,) * 3
+        want = {(i, j, k): f[i] * f[j] * f[k] for i in f for j in f for k in f}
+    S = O.voidfrac(p, np.array([x]), np.array([R]))
+    q = V / hf ** 3 * 2.0 ** 40  # the sphere's volume in quanta
+    got = {}
+    for c in np.flatnonzero(S):
+        iz, rem = divmod(int(c), nf * nf)
+        iy, ix = divmod(rem, nf)
+        got[(ix, iy, iz)] = int(S[c])
+    assert set(got) == set(want), (sorted(got), sorted(want))
+    for cell, frac in want.items():
+        assert abs(got[cell] - frac * q) <= 1.0, (cell, got[cell], frac * q)
+
+
 # ---------------------------------------------------------------- whole-step invariants (P8)
 
 def test_momentum_conservation_periodic():
