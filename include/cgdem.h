@@ -221,7 +221,12 @@ int cgdem_status_sync(cgdem_ctx* ctx, void* stream);
  * grain radii R [N] (N = sum of counts).  Forces, torques and all contact
  * history are reset to zero.  If bond_touching != 0, every pair with
  * d^2 < (Ri+Rj)^2 starts bonded (modified JKR, Sec. 2.3).  The porosity is
- * computed and the contact list built.  Synchronises stream. */
+ * computed and the contact list built.  Synchronises stream.  The inputs are
+ * checked on the device before anything uses them: CGDEM_E_INVALID names
+ * the lowest particle whose radius lies outside (0, r_max] of its sample,
+ * CGDEM_E_NONFINITE the lowest with a non-finite sum of its nine state
+ * components (the radius test first at equal index); the context's state is
+ * then left as it was. */
 int cgdem_init_particles(cgdem_ctx* ctx, const double* x, const double* v, const double* w,
                          const double* R, int bond_touching, void* stream);
 
