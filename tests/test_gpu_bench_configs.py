@@ -17,6 +17,8 @@ full sizes, against the FP64 oracle.
   evaluation and after 3 steps, in both precisions (mixed after 3 steps:
   within the per-step tolerance plus the first-order change of the forces
   that the two runs' state difference produces, tests/helpers.py).
+* The benchmark's 4.29M-sphere periodic cube at the knobs it is timed with:
+  the spheres well inside the 100,000 nearest its centre, the same checks.
 * The 64-member ensemble of the benchmark at its autotuned knobs, with and
   without the per-member skins balanced by drift rate: every member against
   the oracle at the first evaluation, six members after 12 steps.
@@ -286,6 +288,69 @@ def test_full_size_cylinder_at_bench_knobs(big, prec):
                 ko = inner[oi] & inner[oj]
                 Oc = set(zip(oi[ko].tolist(), oj[ko].tolist(), ob[ko].tolist()))
                 assert G == Oc
+    assert ctx.status() == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_scale_cube_at_bench_knobs(big, prec):
+    """The benchmark's 4.29M-sphere periodic cube at the knobs it is timed
+    with (the headline's autotuned ones): forces, torques and contacts of
+    the spheres well inside the 100,000 nearest the cube's centre (far from
+    the periodic wrap) against the oracle run on them, at the first force
+    evaluation and after 3 steps, as in the cylinder test above."""
+    import bench
+    _, _, _, tune = big
+    s = copy.copy(bench.make_scale_cube(1))
+    assert len(s.R) > 4_000_000
+    s.v = np.random.default_rng(4).normal(size=s.x.shape) * 1e-3
+    dt, _ = bench.step_params(s)
+    skin = tune["skin_frac"] * 2 * float(s.R.max())
+    ctx = context(s, prec, dt, skin, block=tune["block"], cell_scale=tune["cell_scale"],
+                  ppw=tune["ppw"], max_neighbors=48)
+    ctx.compute_forces()
+    c = 0.5 * np.asarray(s.domain["L"])
+    idx, rad = sub_block(s, c, 100_000)
+    assert rad < 0.4 * min(s.domain["L"])
+    rel = 1e-15 if prec == cgdem.FP64 else 1e-7
+    sim, ref = sub_oracle(s, idx, dt), sub_oracle(s, idx, dt, rel)
+    hop = max(2 * float(s.R.max()) + skin, float(np.linalg.norm(s.grid.h)))
+    loc = -np.ones(len(s.R), np.int64)
+    loc[idx] = np.arange(len(idx))
+    for steps in (0, 3):
+        if steps:
+            ctx.step(steps)
+            sim.step(steps)
+            ref.step(steps)
+        g = ctx.get_state()
+        gi, gj, gb = ctx.get_contacts()
+        o, r = sim.state(), ref.state()
+        inner = np.linalg.norm(s.x[idx] - c, axis=1) < rad - (steps + 1) * hop - 1e-4
+        assert inner.sum() > 1000
+        scale = sim.force_scale()[inner]
+        li, lj = loc[gi], loc[gj]
+        both = (li >= 0) & (lj >= 0)
+        if prec == cgdem.FP64 or steps == 0:
+            spread = normwise_error(r["F"][inner], o["F"][inner], scale)
+            e = normwise_error(g["F"][idx][inner], o["F"][inner], scale)
+            assert e <= max(TOL[prec], 10 * spread), (steps, e, spread)
+            tsc = scale * s.R[idx][inner]
+            spread_t = normwise_error(r["T"][inner], o["T"][inner], tsc)
+            et = normwise_error(g["T"][idx][inner], o["T"][inner], tsc)
+            assert et <= max(TOL[prec], 10 * spread_t), (steps, et, spread_t)
+            keep = both.copy()
+            keep[keep] &= inner[li[keep]] & inner[lj[keep]]
+            G = set(zip(li[keep].tolist(), lj[keep].tolist(), gb[keep].tolist()))
+            oi, oj, ob, _ = sim.contacts()
+            ko = inner[oi] & inner[oj]
+            assert G == set(zip(oi[ko].tolist(), oj[ko].tolist(), ob[ko].tolist()))
+        else:
+            sub = copy.copy(s)
+            sub.x, sub.v, sub.w, sub.R = s.x[idx], s.v[idx], s.w[idx], s.R[idx]
+            gs = {q: g[q][idx] for q in ("x", "v", "w", "F", "T")}
+            left = check_mixed_forces(sub, gs, o, sim, (li[both], lj[both], gb[both]), TOL[prec],
+                                      rows=inner, skin=skin)
+            assert left <= 0.02 * inner.sum()
     assert ctx.status() == 0
     ctx.close()
 
